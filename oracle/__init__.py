@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for the neural six-way lightmap hot path (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package.  It shares no
+code with the CUDA path (``paper_2604_03748_gb300``) and imports nothing from
+it; inputs arrive as plain numpy arrays and dataclass-like objects.
+
+Parity status per function (pins live in tests/test_oracle_*.py):
+  guide                 pinned (closed forms: empty, constant cube, linear field,
+                        symmetry, mask, HG normalisation)
+  reference_lightmaps   pinned (slab closed form, midpoint order)
+  net_forward           pinned (PyTorch float64 conv/convT/pool/LayerNorm,
+                        NAFBlock identity at beta=gamma=0)
+  shade                 pinned (axis lights select one plane; linearity)
+  paper-level quality   parity unpinned (no trained weights, no dataset)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library beside it (gcc, OpenMP, no FMA contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Camera(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eye", C.c_float * 3), ("target", C.c_float * 3),
+                ("up", C.c_float * 3), ("fov_y_deg", C.c_float), ("ortho_height", C.c_float),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
+                ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
+                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("margin", C.c_float)]
+
+
+class _Light(C.Structure):
+    _fields_ = [("dir", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+_P = np.ctypeslib.ndpointer
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = C.CDLL(_LIB_PATH)
+    dptr = C.POINTER(C.c_double)
+    lib.nslo_guide.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                               C.POINTER(_Camera), C.c_float, C.POINTER(_Opts), C.c_void_p,
+                               C.c_void_p, C.c_void_p]
+    lib.nslo_reference_lightmaps.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.POINTER(_Camera), C.c_double,
+                                             C.c_double, C.c_void_p]
+    lib.nslo_net_forward.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                                     C.c_double, C.c_void_p]
+    lib.nslo_shade.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(_Camera), C.POINTER(_Light),
+                               C.c_int, C.c_void_p]
+    lib.nslo_sample_sigma.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                      C.POINTER(C.c_float * 3)]
+    lib.nslo_sample_sigma.restype = C.c_double
+    lib.nslo_hg_phase.argtypes = [C.c_double, C.c_double]
+    lib.nslo_hg_phase.restype = C.c_double
+    lib.nslo_pcg_hash.argtypes = [C.c_uint32]
+    lib.nslo_pcg_hash.restype = C.c_uint32
+    lib.nslo_conv2d.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_int, C.c_int, C.c_void_p]
+    lib.nslo_conv_transpose2x2.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_void_p, C.c_int, C.c_void_p]
+    lib.nslo_maxpool2.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]
+    lib.nslo_layernorm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_double, C.c_void_p]
+    lib.nslo_dwconv3.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]
+    lib.nslo_nafblock.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+    lib.nslo_nafblock_params.argtypes = [C.c_int]
+    lib.nslo_nafblock_params.restype = C.c_int64
+    del dptr
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _cam(cam) -> _Camera:
+    c = _Camera()
+    c.kind = int(cam.kind)
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.target[:] = [float(v) for v in cam.target]
+    c.up[:] = [float(v) for v in cam.up]
+    c.fov_y_deg = float(cam.fov_y_deg)
+    c.ortho_height = float(cam.ortho_height)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+def _grid(density):
+    d = np.ascontiguousarray(density)
+    if d.dtype == np.float16:
+        d = d.astype(np.float32)  # exact widening
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    nz, ny, nx = d.shape
+    return d, nx, ny, nz
+
+
+def _mask(mask):
+    return None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+
+
+DEFAULT_OPTS = dict(tau_depth=0.01, t_min=1e-4, jitter=1, seed=0, frame=0, phase_g=0.0,
+                    surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5)
+
+
+def guide(density, mask, camera, step, sigma_scale=1.0, **opts):
+    """Alg. 1 guiding map.  Returns (guide[3,H,W] float64, samples[H,W] int64, flags[H,W] uint8)."""
+    lib = _load()
+    o = dict(DEFAULT_OPTS)
+    o.update(opts)
+    d, nx, ny, nz = _grid(density)
+    m = _mask(mask)
+    H, W = camera.height, camera.width
+    out = np.zeros((3, H, W), np.float64)
+    samples = np.zeros((H, W), np.int64)
+    flags = np.zeros((H, W), np.uint8)
+    op = _Opts()
+    op.tau_depth = o["tau_depth"]; op.t_min = o["t_min"]; op.jitter = int(o["jitter"])
+    op.seed = int(o["seed"]) & 0xFFFFFFFF; op.frame = int(o["frame"]) & 0xFFFFFFFF
+    op.phase_g = o["phase_g"]; op.surrogate_I[:] = list(o["surrogate_I"])
+    op.segment_exact = int(o["segment_exact"]); op.margin = o["margin"]
+    cam = _cam(camera)
+    rc = lib.nslo_guide(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(cam),
+                        float(step), C.byref(op), _ptr(out), _ptr(samples), _ptr(flags))
+    if rc != 0:
+        raise ValueError(f"nslo_guide failed ({rc})")
+    return out, samples, flags
+
+
+def reference_lightmaps(density, mask, camera, hf=0.25, sigma_scale=1.0, phase_g=0.0):
+    """Fine-step six-light single-scattering reference: [7,H,W] = +X,-X,+Y,-Y,+Z,-Z,T."""
+    lib = _load()
+    d, nx, ny, nz = _grid(density)
+    m = _mask(mask)
+    out = np.zeros((7, camera.height, camera.width), np.float64)
+    cam = _cam(camera)
+    rc = lib.nslo_reference_lightmaps(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale),
+                                      C.byref(cam), float(hf), float(phase_g), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_reference_lightmaps failed ({rc})")
+    return out
+
+
+def net_forward(guide_planes, params_flat, c0, depth_scale):
+    """Lightmap network forward in FP64.  guide [3,H,W] -> [8,H,W]."""
+    lib = _load()
+    g = np.ascontiguousarray(guide_planes, dtype=np.float64)
+    _, H, W = g.shape
+    p = np.ascontiguousarray(params_flat, dtype=np.float64)
+    out = np.zeros((8, H, W), np.float64)
+    rc = lib.nslo_net_forward(_ptr(g), H, W, _ptr(p), p.size, int(c0), float(depth_scale), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_net_forward failed ({rc})")
+    return out
+
+
+def shade(lightmaps, camera, lights):
+    lib = _load()
+    lm = np.ascontiguousarray(lightmaps, dtype=np.float64)
+    _, H, W = lm.shape
+    arr = (_Light * max(1, len(lights)))()
+    for i, li in enumerate(lights):
+        arr[i].dir[:] = [float(v) for v in li.dir]
+        arr[i].intensity[:] = [float(v) for v in li.intensity]
+    out = np.zeros((4, H, W), np.float64)
+    cam = _cam(camera)
+    rc = lib.nslo_shade(_ptr(lm), H, W, C.byref(cam), arr, len(lights), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_shade failed ({rc})")
+    return out
+
+
+def sample_sigma(density, mask, p, sigma_scale=1.0):
+    lib = _load()
+    d, nx, ny, nz = _grid(density)
+    m = _mask(mask)
+    pp = (C.c_float * 3)(*[float(v) for v in p])
+    return lib.nslo_sample_sigma(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(pp))
+
+
+def hg_phase(g, cos_theta):
+    return _load().nslo_hg_phase(float(g), float(cos_theta))
+
+
+def pcg_hash(v):
+    return int(_load().nslo_pcg_hash(int(v) & 0xFFFFFFFF))
+
+
+def conv2d(x, w, b, k):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    cin, H, W = x.shape
+    cout = w.shape[0]
+    b = None if b is None else np.ascontiguousarray(b, np.float64)
+    out = np.zeros((cout, H, W), np.float64)
+    lib.nslo_conv2d(_ptr(x), cin, H, W, _ptr(w), _ptr(b), cout, int(k), _ptr(out))
+    return out
+
+
+def conv_transpose2x2(x, w, b):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    cin, H, W = x.shape
+    cout = w.shape[1]
+    b = None if b is None else np.ascontiguousarray(b, np.float64)
+    out = np.zeros((cout, 2 * H, 2 * W), np.float64)
+    lib.nslo_conv_transpose2x2(_ptr(x), cin, H, W, _ptr(w), _ptr(b), cout, _ptr(out))
+    return out
+
+
+def maxpool2(x):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    c, H, W = x.shape
+    out = np.zeros((c, H // 2, W // 2), np.float64)
+    lib.nslo_maxpool2(_ptr(x), c, H, W, _ptr(out))
+    return out
+
+
+def layernorm(x, g, b, eps=1e-6):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    c, H, W = x.shape
+    out = np.zeros_like(x)
+    lib.nslo_layernorm(_ptr(x), c, H, W, _ptr(np.ascontiguousarray(g, np.float64)),
+                       _ptr(np.ascontiguousarray(b, np.float64)), float(eps), _ptr(out))
+    return out
+
+
+def dwconv3(x, w, b):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    c, H, W = x.shape
+    out = np.zeros_like(x)
+    lib.nslo_dwconv3(_ptr(x), c, H, W, _ptr(np.ascontiguousarray(w, np.float64)),
+                     _ptr(np.ascontiguousarray(b, np.float64)), _ptr(out))
+    return out
+
+
+def nafblock(x, params_flat):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    c, H, W = x.shape
+    p = np.ascontiguousarray(params_flat, np.float64)
+    if p.size != lib.nslo_nafblock_params(c):
+        raise ValueError("wrong NAFBlock parameter count")
+    out = np.zeros_like(x)
+    rc = lib.nslo_nafblock(_ptr(x), c, H, W, _ptr(p), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_nafblock failed ({rc})")
+    return out
+
+
+def nafblock_params(c):
+    return int(_load().nslo_nafblock_params(int(c)))
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,757 @@
+/* FP64 CPU oracle for the neural six-way lightmap hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  Plain, slow,
+ * direct loops; no blocking or fusion.  Each function cites the passage of the
+ * paper it follows.
+ *
+ * Precision.  All radiometric arithmetic is binary64.  The ray geometry that
+ * decides integers (the number of view samples N, the number of shadow samples
+ * K, the sample positions) is evaluated in binary32 with one rounding per
+ * operation in a fixed order, because the GPU kernel takes those decisions in
+ * binary32; both sides must take an integer decision in the same precision.
+ * Build with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Parity pins (tests): empty volume; constant cube closed form (front, top,
+ * bottom geometric sums, T = exp(-sigma L)); linear density field (trilinear is
+ * exact, optical depth is an arithmetic series); vertical flip symmetry;
+ * mask-all = empty; Henyey-Greenstein normalisation; convolution, transposed
+ * convolution, pooling and LayerNorm against PyTorch float64; NAFBlock with
+ * beta = gamma = 0 is the identity; shading selects one plane on axis lights
+ * and is linear; the fine-step reference against the slab closed form.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI_D 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* binary32 camera geometry (Sec. 4.2: view rays along -omega from x)        */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  float eye[3], r[3], u[3], f[3];
+  float ax, ay;           /* screen extents: ortho (height*W/H, height), persp 2tan(fov/2)*(W/H, 1) */
+  int kind, W, H;
+} cam_frame;
+
+/* Camera basis in binary64, rounded once to binary32: f = normalize(target -
+ * eye), r = normalize(f x up), u = r x f (right-handed, Y up world). */
+static void cam_setup(const nslo_camera* c, cam_frame* fr) {
+  double fx = (double)c->target[0] - (double)c->eye[0];
+  double fy = (double)c->target[1] - (double)c->eye[1];
+  double fz = (double)c->target[2] - (double)c->eye[2];
+  double fl = sqrt(fx * fx + fy * fy + fz * fz);
+  fx /= fl; fy /= fl; fz /= fl;
+  double ux = c->up[0], uy = c->up[1], uz = c->up[2];
+  double rx = fy * uz - fz * uy, ry = fz * ux - fx * uz, rz = fx * uy - fy * ux;
+  double rl = sqrt(rx * rx + ry * ry + rz * rz);
+  rx /= rl; ry /= rl; rz /= rl;
+  double vx = ry * fz - rz * fy, vy = rz * fx - rx * fz, vz = rx * fy - ry * fx;
+  for (int k = 0; k < 3; ++k) fr->eye[k] = c->eye[k];
+  fr->f[0] = (float)fx; fr->f[1] = (float)fy; fr->f[2] = (float)fz;
+  fr->r[0] = (float)rx; fr->r[1] = (float)ry; fr->r[2] = (float)rz;
+  fr->u[0] = (float)vx; fr->u[1] = (float)vy; fr->u[2] = (float)vz;
+  fr->kind = c->kind; fr->W = c->width; fr->H = c->height;
+  if (c->kind == 0) {
+    fr->ax = (float)(((double)c->ortho_height * (double)c->width) / (double)c->height);
+    fr->ay = c->ortho_height;
+  } else {
+    double k = 2.0 * tan(((double)c->fov_y_deg * PI_D / 180.0) * 0.5);
+    fr->ax = (float)((k * (double)c->width) / (double)c->height);
+    fr->ay = (float)k;
+  }
+}
+
+/* Pixel (i, j) -> ray origin o and unit direction d (binary32). */
+static void pixel_ray(const cam_frame* fr, int i, int j, float o[3], float d[3]) {
+  float sx = ((float)i + 0.5f) / (float)fr->W - 0.5f;
+  float sy = 0.5f - ((float)j + 0.5f) / (float)fr->H;
+  float a = sx * fr->ax;
+  float b = sy * fr->ay;
+  if (fr->kind == 0) {
+    for (int k = 0; k < 3; ++k) {
+      float t1 = a * fr->r[k];
+      float t2 = b * fr->u[k];
+      o[k] = (fr->eye[k] + t1) + t2;
+      d[k] = fr->f[k];
+    }
+  } else {
+    float v[3];
+    for (int k = 0; k < 3; ++k) {
+      float t1 = a * fr->r[k];
+      float t2 = b * fr->u[k];
+      v[k] = (fr->f[k] + t1) + t2;
+      o[k] = fr->eye[k];
+    }
+    float s0 = v[0] * v[0];
+    float s1 = v[1] * v[1];
+    float s2 = v[2] * v[2];
+    float len = sqrtf((s0 + s1) + s2);
+    for (int k = 0; k < 3; ++k) d[k] = v[k] / len;
+  }
+}
+
+/* Slab clip of the ray against the closed box [0,n]; returns 0 on a miss. */
+static int clip_box(const float o[3], const float d[3], const float n[3], float* tin,
+                    float* tout) {
+  float tn = -INFINITY, tf = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] != 0.0f) {
+      float ta = (0.0f - o[k]) / d[k];
+      float tb = (n[k] - o[k]) / d[k];
+      float lo = ta < tb ? ta : tb;
+      float hi = ta < tb ? tb : ta;
+      if (lo > tn) tn = lo;
+      if (hi < tf) tf = hi;
+    } else if (o[k] < 0.0f || o[k] > n[k]) {
+      return 0;
+    }
+  }
+  if (tn < 0.0f) tn = 0.0f;
+  if (!(tf > tn)) return 0;
+  *tin = tn;
+  *tout = tf;
+  return 1;
+}
+
+/* Distance from p to the exit of the closed box along unit direction s. */
+static float exit_distance(const float p[3], const float s[3], const float n[3]) {
+  float te = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    if (s[k] > 0.0f) {
+      float t = (n[k] - p[k]) / s[k];
+      if (t < te) te = t;
+    } else if (s[k] < 0.0f) {
+      float t = (0.0f - p[k]) / s[k];
+      if (t < te) te = t;
+    }
+  }
+  return te;
+}
+
+/* 32-bit PCG hash, from Jarzynski & Olano, "Hash Functions for GPU Rendering",
+ * JCGT 9(3), 2020: an LCG step followed by a random xorshift and a multiply. */
+uint32_t nslo_pcg_hash(uint32_t v) {
+  uint32_t state = v * 747796405u + 2891336453u;
+  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+/* Jitter u in [0,1) for pixel (i,j): top 24 bits of a hash chain. */
+static float pixel_jitter(const nslo_march_opts* op, int i, int j, int W) {
+  if (!op->jitter) return 0.0f;
+  uint32_t key = nslo_pcg_hash(op->frame + nslo_pcg_hash(op->seed));
+  uint32_t hv = nslo_pcg_hash((uint32_t)(j * W + i) + key);
+  return (float)(hv >> 8) * (1.0f / 16777216.0f);
+}
+
+/* ------------------------------------------------------------------------- */
+/* density field (Sec. 4.2: sigma_s stored in a 3D texture)                   */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  const float* rho;
+  const uint8_t* mask;
+  int nx, ny, nz;
+  double scale;
+  float n[3];
+} field;
+
+static double voxel(const field* F, int i, int j, int k) {
+  size_t idx = ((size_t)k * F->ny + j) * F->nx + i;
+  if (F->mask && F->mask[idx]) return 0.0;
+  return F->scale * (double)F->rho[idx];
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* sigma(p): 0 outside the closed box; trilinear interpolation of the masked,
+ * scaled voxels at q = p - 0.5 with clamp-to-edge indices inside it. */
+static double sigma_at(const field* F, const float p[3]) {
+  for (int k = 0; k < 3; ++k)
+    if (!(p[k] >= 0.0f && p[k] <= F->n[k])) return 0.0;
+  double q[3] = {(double)p[0] - 0.5, (double)p[1] - 0.5, (double)p[2] - 0.5};
+  int i0[3];
+  double t[3];
+  for (int k = 0; k < 3; ++k) {
+    double fl = floor(q[k]);
+    i0[k] = (int)fl;
+    t[k] = q[k] - fl;
+  }
+  int lim[3] = {F->nx - 1, F->ny - 1, F->nz - 1};
+  int ia[3], ib[3];
+  for (int k = 0; k < 3; ++k) {
+    ia[k] = clampi(i0[k], 0, lim[k]);
+    ib[k] = clampi(i0[k] + 1, 0, lim[k]);
+  }
+  double acc = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+        acc += w * voxel(F, dx ? ib[0] : ia[0], dy ? ib[1] : ia[1], dz ? ib[2] : ia[2]);
+      }
+  return acc;
+}
+
+double nslo_sample_sigma(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+                         double sigma_scale, const float p[3]) {
+  field F = {density, mask, nx, ny, nz, sigma_scale, {(float)nx, (float)ny, (float)nz}};
+  return sigma_at(&F, p);
+}
+
+/* Henyey-Greenstein phase function; cos_theta is the cosine between the light's
+ * propagation direction and the scattered direction (toward the camera). */
+double nslo_hg_phase(double g, double cos_theta) {
+  double den = 1.0 + g * g - 2.0 * g * cos_theta;
+  return (1.0 - g * g) / (4.0 * PI_D * den * sqrt(den));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Guiding map: Alg. 1 with the surrogate lights of Eq. approx                */
+/* ------------------------------------------------------------------------- */
+
+/* Transmittance from p toward direction s (front/top/bottom light) by a march
+ * at step h to the box exit: T = exp(-h sum_k sigma(p + k h s)).  Stops once
+ * the running transmittance is below t_min (checked after each step). */
+static double shadow_T(const field* F, const float p[3], const float s[3], float h,
+                       double t_min, double margin, int64_t* nsamp, int* near_flag) {
+  float te = exit_distance(p, s, F->n);
+  int K = 0;
+  if (te > 0.0f) {
+    float kf = floorf(te / h);
+    K = (int)kf;
+  }
+  double tau = 0.0, T = 1.0;
+  for (int k = 1; k <= K; ++k) {
+    float kh = (float)k * h;
+    float q[3];
+    for (int c = 0; c < 3; ++c) {
+      float st = kh * s[c];
+      q[c] = p[c] + st;
+    }
+    tau += sigma_at(F, q) * (double)h;
+    ++*nsamp;
+    T = exp(-tau);
+    if (t_min > 0.0) {
+      if (fabs(T - t_min) <= margin * t_min) *near_flag = 1;
+      if (T < t_min) break;
+    }
+  }
+  return T;
+}
+
+int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+               double sigma_scale, const nslo_camera* cam, float h,
+               const nslo_march_opts* op, double* guide, int64_t* samples, uint8_t* flags) {
+  if (!density || !cam || !op || !guide || nx <= 0 || ny <= 0 || nz <= 0 || !(h > 0.0f))
+    return 1;
+  field F = {density, mask, nx, ny, nz, sigma_scale, {(float)nx, (float)ny, (float)nz}};
+  cam_frame fr;
+  cam_setup(cam, &fr);
+  const int W = cam->width, H = cam->height;
+  const size_t plane = (size_t)W * H;
+  const double t_min = op->t_min, margin = op->margin;
+  const double g = op->phase_g;
+
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int j = 0; j < H; ++j) {
+    for (int i = 0; i < W; ++i) {
+      size_t pix = (size_t)j * W + i;
+      float o[3], d[3], tin, tout;
+      pixel_ray(&fr, i, j, o, d);
+      double L = 0.0, T = 1.0, D = 0.0;
+      int64_t ns = 0;
+      int near_term = 0, near_depth = 0;
+      if (clip_box(o, d, F.n, &tin, &tout)) {
+        float u = pixel_jitter(op, i, j, W);
+        float span = (tout - tin) / h;
+        int N = (int)floorf(span + u);
+        /* surrogate lights (Eq. approx): front = toward the camera (-d), top =
+         * camera up (+u), bottom = -u; HG cosines against the view ray. */
+        float s_top[3] = {fr.u[0], fr.u[1], fr.u[2]};
+        float s_bot[3] = {-fr.u[0], -fr.u[1], -fr.u[2]};
+        double cu = (double)d[0] * fr.u[0] + (double)d[1] * fr.u[1] + (double)d[2] * fr.u[2];
+        double P_f = nslo_hg_phase(g, -1.0);
+        double P_t = nslo_hg_phase(g, cu);
+        double P_b = nslo_hg_phase(g, -cu);
+        double tau = 0.0;
+        for (int n = 1; n <= N; ++n) {
+          float tn_off = ((float)n - u) * h;
+          float tn = tin + tn_off;
+          float p[3];
+          for (int c = 0; c < 3; ++c) {
+            float st = tn * d[c];
+            p[c] = o[c] + st;
+          }
+          double sg = sigma_at(&F, p);
+          ++ns;
+          if (D == 0.0) {
+            if (fabs(sg - (double)op->tau_depth) <= margin * (double)op->tau_depth) near_depth = 1;
+            if (sg > (double)op->tau_depth) D = (double)n * (double)h;
+          }
+          double A = op->segment_exact ? T * (1.0 - exp(-sg * (double)h)) : T * sg * (double)h;
+          double Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
+          double Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
+          double Ln = P_f * op->surrogate_I[0] * T + P_t * op->surrogate_I[1] * Tt +
+                      P_b * op->surrogate_I[2] * Tb;
+          L += A * Ln;
+          tau += sg * (double)h;
+          T = exp(-tau);
+          if (t_min > 0.0) {
+            if (fabs(T - t_min) <= margin * t_min) near_term = 1;
+            if (T < t_min) break;
+          }
+        }
+      }
+      guide[pix] = L;
+      guide[plane + pix] = T;
+      guide[2 * plane + pix] = D;
+      if (samples) samples[pix] = ns;
+      if (flags) flags[pix] = (uint8_t)(near_term | (near_depth << 1));
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fine-step six-light reference (single scattering, Sec. 3 Eq. RE/scatter)   */
+/* ------------------------------------------------------------------------- */
+
+/* Optical depth from p toward s to the box exit, midpoint rule with segments
+ * of length at most hf. */
+static double light_tau(const field* F, const float p[3], const double s[3], double hf) {
+  double pd[3] = {p[0], p[1], p[2]};
+  double te = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    if (s[k] > 0.0) te = fmin(te, ((double)F->n[k] - pd[k]) / s[k]);
+    else if (s[k] < 0.0) te = fmin(te, (0.0 - pd[k]) / s[k]);
+  }
+  if (!(te > 0.0)) return 0.0;
+  int M = (int)ceil(te / hf);
+  double hs = te / M, tau = 0.0;
+  for (int m = 1; m <= M; ++m) {
+    double t = ((double)m - 0.5) * hs;
+    float q[3] = {(float)(pd[0] + t * s[0]), (float)(pd[1] + t * s[1]), (float)(pd[2] + t * s[2])};
+    tau += sigma_at(F, q) * hs;
+  }
+  return tau;
+}
+
+int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+                             double sigma_scale, const nslo_camera* cam, double hf,
+                             double g, double* out) {
+  if (!density || !cam || !out || !(hf > 0.0)) return 1;
+  field F = {density, mask, nx, ny, nz, sigma_scale, {(float)nx, (float)ny, (float)nz}};
+  cam_frame fr;
+  cam_setup(cam, &fr);
+  const int W = cam->width, H = cam->height;
+  const size_t plane = (size_t)W * H;
+  /* toward-light directions in the camera frame: +X right, -X, +Y up, -Y,
+   * +Z back (behind the smoke, along the view direction), -Z front */
+  double dirs[6][3];
+  for (int k = 0; k < 3; ++k) {
+    dirs[0][k] = fr.r[k]; dirs[1][k] = -(double)fr.r[k];
+    dirs[2][k] = fr.u[k]; dirs[3][k] = -(double)fr.u[k];
+    dirs[4][k] = fr.f[k]; dirs[5][k] = -(double)fr.f[k];
+  }
+#pragma omp parallel for schedule(dynamic, 2)
+  for (int j = 0; j < H; ++j) {
+    for (int i = 0; i < W; ++i) {
+      size_t pix = (size_t)j * W + i;
+      float o[3], d[3], tin, tout;
+      pixel_ray(&fr, i, j, o, d);
+      double Lp[6] = {0, 0, 0, 0, 0, 0}, T = 1.0;
+      if (clip_box(o, d, F.n, &tin, &tout)) {
+        double chord = (double)tout - (double)tin;
+        int M = (int)ceil(chord / hf);
+        double hs = chord / M, tau = 0.0;
+        for (int m = 1; m <= M; ++m) {
+          double t = (double)tin + ((double)m - 0.5) * hs;
+          float p[3] = {(float)((double)o[0] + t * d[0]), (float)((double)o[1] + t * d[1]),
+                        (float)((double)o[2] + t * d[2])};
+          double sg = sigma_at(&F, p);
+          if (sg > 0.0) {
+            double w = T * (1.0 - exp(-sg * hs));
+            for (int l = 0; l < 6; ++l) {
+              double cth = dirs[l][0] * d[0] + dirs[l][1] * d[1] + dirs[l][2] * d[2];
+              Lp[l] += w * nslo_hg_phase(g, cth) * exp(-light_tau(&F, p, dirs[l], hf));
+            }
+          }
+          tau += sg * hs;
+          T = exp(-tau);
+        }
+      }
+      for (int l = 0; l < 6; ++l) out[l * plane + pix] = Lp[l];
+      out[6 * plane + pix] = T;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Network (Sec. 4.3): UNet encoder/decoder + four NAFBlock channel adapters  */
+/* ------------------------------------------------------------------------- */
+
+/* 'same' convolution, zero padding (k-1)/2, w [cout][cin][k][k], planar NCHW. */
+void nslo_conv2d(const double* in, int cin, int H, int W, const double* w, const double* b,
+                 int cout, int k, double* out) {
+  int pad = (k - 1) / 2;
+#pragma omp parallel for schedule(static)
+  for (int co = 0; co < cout; ++co) {
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        double acc = b ? b[co] : 0.0;
+        for (int ci = 0; ci < cin; ++ci)
+          for (int ky = 0; ky < k; ++ky) {
+            int yy = y + ky - pad;
+            if (yy < 0 || yy >= H) continue;
+            for (int kx = 0; kx < k; ++kx) {
+              int xx = x + kx - pad;
+              if (xx < 0 || xx >= W) continue;
+              acc += w[((size_t)(co * cin + ci) * k + ky) * k + kx] *
+                     in[((size_t)ci * H + yy) * W + xx];
+            }
+          }
+        out[((size_t)co * H + y) * W + x] = acc;
+      }
+  }
+}
+
+/* 2x2 stride-2 transposed convolution, w [cin][cout][2][2]: output pixel
+ * (2y+a, 2x+b) = bias + sum_ci w[ci][co][a][b] in[ci][y][x]. */
+void nslo_conv_transpose2x2(const double* in, int cin, int H, int W, const double* w,
+                            const double* b, int cout, double* out) {
+  int H2 = 2 * H, W2 = 2 * W;
+#pragma omp parallel for schedule(static)
+  for (int co = 0; co < cout; ++co)
+    for (int y = 0; y < H2; ++y)
+      for (int x = 0; x < W2; ++x) {
+        int a = y & 1, bb = x & 1;
+        double acc = b ? b[co] : 0.0;
+        for (int ci = 0; ci < cin; ++ci)
+          acc += w[((size_t)(ci * cout + co) * 2 + a) * 2 + bb] *
+                 in[((size_t)ci * H + y / 2) * W + x / 2];
+        out[((size_t)co * H2 + y) * W2 + x] = acc;
+      }
+}
+
+void nslo_maxpool2(const double* in, int C, int H, int W, double* out) {
+  int H2 = H / 2, W2 = W / 2;
+  for (int c = 0; c < C; ++c)
+    for (int y = 0; y < H2; ++y)
+      for (int x = 0; x < W2; ++x) {
+        const double* p = in + ((size_t)c * H + 2 * y) * W + 2 * x;
+        double m = p[0];
+        if (p[1] > m) m = p[1];
+        if (p[W] > m) m = p[W];
+        if (p[W + 1] > m) m = p[W + 1];
+        out[((size_t)c * H2 + y) * W2 + x] = m;
+      }
+}
+
+/* LayerNorm over channels at every pixel (NAFNet's LayerNorm2d): biased
+ * variance, eps inside the square root, then per-channel affine. */
+void nslo_layernorm(const double* in, int C, int H, int W, const double* g, const double* b,
+                    double eps, double* out) {
+  size_t plane = (size_t)H * W;
+  for (size_t p = 0; p < plane; ++p) {
+    double mu = 0.0;
+    for (int c = 0; c < C; ++c) mu += in[c * plane + p];
+    mu /= C;
+    double var = 0.0;
+    for (int c = 0; c < C; ++c) {
+      double dv = in[c * plane + p] - mu;
+      var += dv * dv;
+    }
+    var /= C;
+    double inv = 1.0 / sqrt(var + eps);
+    for (int c = 0; c < C; ++c) out[c * plane + p] = (in[c * plane + p] - mu) * inv * g[c] + b[c];
+  }
+}
+
+/* depthwise 3x3 'same' convolution, w [C][1][3][3] */
+void nslo_dwconv3(const double* in, int C, int H, int W, const double* w, const double* b,
+                  double* out) {
+  for (int c = 0; c < C; ++c)
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        double acc = b[c];
+        for (int ky = 0; ky < 3; ++ky) {
+          int yy = y + ky - 1;
+          if (yy < 0 || yy >= H) continue;
+          for (int kx = 0; kx < 3; ++kx) {
+            int xx = x + kx - 1;
+            if (xx < 0 || xx >= W) continue;
+            acc += w[c * 9 + ky * 3 + kx] * in[((size_t)c * H + yy) * W + xx];
+          }
+        }
+        out[((size_t)c * H + y) * W + x] = acc;
+      }
+}
+
+/* simple gate: first half of the channels times the second half */
+static void simple_gate(const double* in, int C2, size_t plane, double* out) {
+  int C = C2 / 2;
+  for (int c = 0; c < C; ++c)
+    for (size_t p = 0; p < plane; ++p) out[c * plane + p] = in[c * plane + p] * in[(c + C) * plane + p];
+}
+
+int64_t nslo_nafblock_params(int C) {
+  /* ln1 (2C), pw1 (2C*C + 2C), dw (2C*9 + 2C), sca (C*C + C), pw2 (C*C + C),
+   * beta (C), ln2 (2C), ffn1 (2C*C + 2C), ffn2 (C*C + C), gamma (C) */
+  return (int64_t)2 * C + (2 * C * C + 2 * C) + (18 * C + 2 * C) + (C * C + C) + (C * C + C) + C +
+         2 * C + (2 * C * C + 2 * C) + (C * C + C) + C;
+}
+
+/* NAFBlock (Chen et al. 2022, the adapter block named in Sec. 4.3):
+ *   y = x + beta  * pw2(SCA(SG(dw3x3(pw1(LN1(x))))))
+ *   z = y + gamma * ffn2(SG(ffn1(LN2(y))))
+ * SG(a|b) = a*b over the two channel halves; SCA(v) = v * (W_sca mean_HW(v) + b). */
+int nslo_nafblock(const double* in, int C, int H, int W, const double* P, double* out) {
+  size_t plane = (size_t)H * W;
+  const double *ln1w = P, *ln1b = P + C;
+  P += 2 * C;
+  const double *pw1w = P, *pw1b = P + 2 * C * C;
+  P += 2 * C * C + 2 * C;
+  const double *dww = P, *dwb = P + 18 * C;
+  P += 20 * C;
+  const double *scaw = P, *scab = P + C * C;
+  P += C * C + C;
+  const double *pw2w = P, *pw2b = P + C * C;
+  P += C * C + C;
+  const double* beta = P;
+  P += C;
+  const double *ln2w = P, *ln2b = P + C;
+  P += 2 * C;
+  const double *f1w = P, *f1b = P + 2 * C * C;
+  P += 2 * C * C + 2 * C;
+  const double *f2w = P, *f2b = P + C * C;
+  P += C * C + C;
+  const double* gamma = P;
+
+  double* t_ln = malloc(sizeof(double) * C * plane);
+  double* t_2c = malloc(sizeof(double) * 2 * C * plane);
+  double* t_2c_b = malloc(sizeof(double) * 2 * C * plane);
+  double* t_c = malloc(sizeof(double) * C * plane);
+  double* t_c2 = malloc(sizeof(double) * C * plane);
+  double* y = malloc(sizeof(double) * C * plane);
+  if (!t_ln || !t_2c || !t_2c_b || !t_c || !t_c2 || !y) return 2;
+
+  nslo_layernorm(in, C, H, W, ln1w, ln1b, 1e-6, t_ln);
+  nslo_conv2d(t_ln, C, H, W, pw1w, pw1b, 2 * C, 1, t_2c);
+  nslo_dwconv3(t_2c, 2 * C, H, W, dww, dwb, t_2c_b);
+  simple_gate(t_2c_b, 2 * C, plane, t_c);
+  /* simplified channel attention */
+  double* mean = malloc(sizeof(double) * C);
+  double* att = malloc(sizeof(double) * C);
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (size_t p = 0; p < plane; ++p) s += t_c[c * plane + p];
+    mean[c] = s / (double)plane;
+  }
+  for (int co = 0; co < C; ++co) {
+    double s = scab[co];
+    for (int ci = 0; ci < C; ++ci) s += scaw[co * C + ci] * mean[ci];
+    att[co] = s;
+  }
+  for (int c = 0; c < C; ++c)
+    for (size_t p = 0; p < plane; ++p) t_c[c * plane + p] *= att[c];
+  nslo_conv2d(t_c, C, H, W, pw2w, pw2b, C, 1, t_c2);
+  for (int c = 0; c < C; ++c)
+    for (size_t p = 0; p < plane; ++p) y[c * plane + p] = in[c * plane + p] + beta[c] * t_c2[c * plane + p];
+  /* feed-forward half */
+  nslo_layernorm(y, C, H, W, ln2w, ln2b, 1e-6, t_ln);
+  nslo_conv2d(t_ln, C, H, W, f1w, f1b, 2 * C, 1, t_2c);
+  simple_gate(t_2c, 2 * C, plane, t_c);
+  nslo_conv2d(t_c, C, H, W, f2w, f2b, C, 1, t_c2);
+  for (int c = 0; c < C; ++c)
+    for (size_t p = 0; p < plane; ++p) out[c * plane + p] = y[c * plane + p] + gamma[c] * t_c2[c * plane + p];
+  free(mean); free(att);
+  free(t_ln); free(t_2c); free(t_2c_b); free(t_c); free(t_c2); free(y);
+  return 0;
+}
+
+static void relu_inplace(double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (v[i] < 0.0) v[i] = 0.0;
+}
+
+typedef struct { const double* p; int64_t left; } cursor;
+
+static const double* take(cursor* c, int64_t n) {
+  if (c->left < n) return NULL;
+  const double* r = c->p;
+  c->p += n;
+  c->left -= n;
+  return r;
+}
+
+/* conv3x3 + ReLU with parameters from the cursor */
+static int conv3_relu(cursor* cur, const double* in, int cin, int H, int W, int cout, double* out) {
+  const double* w = take(cur, (int64_t)cout * cin * 9);
+  const double* b = take(cur, cout);
+  if (!w || !b) return 3;
+  nslo_conv2d(in, cin, H, W, w, b, cout, 3, out);
+  relu_inplace(out, (size_t)cout * H * W);
+  return 0;
+}
+
+/* The lightmap generator of Sec. 4.3 / Fig. 3: a four-level UNet (widths
+ * c0*{1,2,4,8}, two 3x3 conv+ReLU per level, 2x2 max-pool down, 2x2 stride-2
+ * transposed conv up, skip concatenated after the upsampled tensor) gives the
+ * shared feature F; four NAFBlock adapters (F&B, L&R, U&D, A&E) each end in a
+ * 1x1 conv to 2 channels.  Output planes [+X,-X,+Y,-Y,+Z,-Z,T,E]:
+ * L&R -> 0,1; U&D -> 2,3; F&B -> 4 (+Z back), 5 (-Z front); A&E -> 6,7.
+ * Input: the guide with its depth channel multiplied by depth_scale. */
+int nslo_net_forward(const double* guide, int H, int W, const double* params, int64_t n_params,
+                     int c0, double depth_scale, double* out) {
+  if (H % 8 || W % 8 || H <= 0 || W <= 0) return 1;
+  cursor cur = {params, n_params};
+  const int c1 = c0, c2 = 2 * c0, c3 = 4 * c0, c4 = 8 * c0;
+  size_t P0 = (size_t)H * W, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  double* x0 = malloc(sizeof(double) * 3 * P0);
+  double* a0 = malloc(sizeof(double) * c1 * P0);
+  double* s1 = malloc(sizeof(double) * c1 * P0);
+  double* p1 = malloc(sizeof(double) * c1 * P1);
+  double* a1 = malloc(sizeof(double) * c2 * P1);
+  double* s2 = malloc(sizeof(double) * c2 * P1);
+  double* p2 = malloc(sizeof(double) * c2 * P2);
+  double* a2 = malloc(sizeof(double) * c3 * P2);
+  double* s3 = malloc(sizeof(double) * c3 * P2);
+  double* p3 = malloc(sizeof(double) * c3 * P3);
+  double* a3 = malloc(sizeof(double) * c4 * P3);
+  double* bt = malloc(sizeof(double) * c4 * P3);
+  double* cat = malloc(sizeof(double) * 2 * c1 * P0 + sizeof(double) * c4 * P2);
+  double* d = malloc(sizeof(double) * c1 * P0 * 2 + sizeof(double) * c4 * P2);
+  double* F = malloc(sizeof(double) * c1 * P0);
+  double* z = malloc(sizeof(double) * c1 * P0);
+  int rc = 0;
+  if (!x0 || !a0 || !s1 || !p1 || !a1 || !s2 || !p2 || !a2 || !s3 || !p3 || !a3 || !bt || !cat ||
+      !d || !F || !z) { rc = 2; goto done; }
+
+  memcpy(x0, guide, sizeof(double) * 2 * P0);
+  for (size_t p = 0; p < P0; ++p) x0[2 * P0 + p] = guide[2 * P0 + p] * depth_scale;
+
+  /* encoder */
+  if ((rc = conv3_relu(&cur, x0, 3, H, W, c1, a0))) goto done;
+  if ((rc = conv3_relu(&cur, a0, c1, H, W, c1, s1))) goto done;
+  nslo_maxpool2(s1, c1, H, W, p1);
+  if ((rc = conv3_relu(&cur, p1, c1, H1, W1, c2, a1))) goto done;
+  if ((rc = conv3_relu(&cur, a1, c2, H1, W1, c2, s2))) goto done;
+  nslo_maxpool2(s2, c2, H1, W1, p2);
+  if ((rc = conv3_relu(&cur, p2, c2, H2, W2, c3, a2))) goto done;
+  if ((rc = conv3_relu(&cur, a2, c3, H2, W2, c3, s3))) goto done;
+  nslo_maxpool2(s3, c3, H2, W2, p3);
+  if ((rc = conv3_relu(&cur, p3, c3, H3, W3, c4, a3))) goto done;
+  if ((rc = conv3_relu(&cur, a3, c4, H3, W3, c4, bt))) goto done;
+
+  /* decoder: level 3 */
+  {
+    const double* w = take(&cur, (int64_t)c4 * c3 * 4);
+    const double* b = take(&cur, c3);
+    if (!w || !b) { rc = 3; goto done; }
+    nslo_conv_transpose2x2(bt, c4, H3, W3, w, b, c3, cat);           /* upsampled first */
+    memcpy(cat + (size_t)c3 * P2, s3, sizeof(double) * c3 * P2);     /* skip second */
+    if ((rc = conv3_relu(&cur, cat, 2 * c3, H2, W2, c3, d))) goto done;
+    if ((rc = conv3_relu(&cur, d, c3, H2, W2, c3, a2))) goto done;
+  }
+  /* level 2 */
+  {
+    const double* w = take(&cur, (int64_t)c3 * c2 * 4);
+    const double* b = take(&cur, c2);
+    if (!w || !b) { rc = 3; goto done; }
+    nslo_conv_transpose2x2(a2, c3, H2, W2, w, b, c2, cat);
+    memcpy(cat + (size_t)c2 * P1, s2, sizeof(double) * c2 * P1);
+    if ((rc = conv3_relu(&cur, cat, 2 * c2, H1, W1, c2, d))) goto done;
+    if ((rc = conv3_relu(&cur, d, c2, H1, W1, c2, a1))) goto done;
+  }
+  /* level 1 */
+  {
+    const double* w = take(&cur, (int64_t)c2 * c1 * 4);
+    const double* b = take(&cur, c1);
+    if (!w || !b) { rc = 3; goto done; }
+    nslo_conv_transpose2x2(a1, c2, H1, W1, w, b, c1, cat);
+    memcpy(cat + (size_t)c1 * P0, s1, sizeof(double) * c1 * P0);
+    if ((rc = conv3_relu(&cur, cat, 2 * c1, H, W, c1, d))) goto done;
+    if ((rc = conv3_relu(&cur, d, c1, H, W, c1, F))) goto done;
+  }
+  /* channel adapters, in the order F&B, L&R, U&D, A&E */
+  {
+    static const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
+    int64_t nb = nslo_nafblock_params(c1);
+    for (int a = 0; a < 4; ++a) {
+      const double* bp = take(&cur, nb);
+      const double* hw = take(&cur, 2 * c1);
+      const double* hb = take(&cur, 2);
+      if (!bp || !hw || !hb) { rc = 3; goto done; }
+      if ((rc = nslo_nafblock(F, c1, H, W, bp, z))) goto done;
+      for (int oc = 0; oc < 2; ++oc) {
+        double* dst = out + (size_t)plane_of[a][oc] * P0;
+        for (size_t p = 0; p < P0; ++p) {
+          double s = hb[oc];
+          for (int ci = 0; ci < c1; ++ci) s += hw[oc * c1 + ci] * z[ci * P0 + p];
+          dst[p] = s;
+        }
+      }
+    }
+  }
+  if (cur.left != 0) rc = 4;
+done:
+  free(x0); free(a0); free(s1); free(p1); free(a1); free(s2); free(p2); free(a2); free(s3);
+  free(p3); free(a3); free(bt); free(cat); free(d); free(F); free(z);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Six-way shading (Sec. 3, directional interpolation)                        */
+/* ------------------------------------------------------------------------- */
+
+/* rgb = sum_lights I * sum_{p in x,y,z} |w_p| L_p^{sign w_p} + E, with w the
+ * unit toward-light vector in the camera frame (X right, Y up, Z into the
+ * screen); A = clamp(1 - T, 0, 1). */
+int nslo_shade(const double* lm, int H, int W, const nslo_camera* cam, const nslo_light* lights,
+               int n_lights, double* rgba) {
+  if (!lm || !cam || !rgba || n_lights < 0 || (n_lights > 0 && !lights)) return 1;
+  cam_frame fr;
+  cam_setup(cam, &fr);
+  size_t P = (size_t)H * W;
+  double wts[64][6];
+  double inten[64][3];
+  if (n_lights > 64) return 1;
+  for (int l = 0; l < n_lights; ++l) {
+    double v[3] = {lights[l].dir[0], lights[l].dir[1], lights[l].dir[2]};
+    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nv > 0.0)) return 1;
+    for (int k = 0; k < 3; ++k) v[k] /= nv;
+    double w[3];
+    w[0] = v[0] * fr.r[0] + v[1] * fr.r[1] + v[2] * fr.r[2];
+    w[1] = v[0] * fr.u[0] + v[1] * fr.u[1] + v[2] * fr.u[2];
+    w[2] = v[0] * fr.f[0] + v[1] * fr.f[1] + v[2] * fr.f[2];
+    for (int p = 0; p < 3; ++p) {
+      wts[l][2 * p] = w[p] >= 0.0 ? w[p] : 0.0;      /* positive-direction plane */
+      wts[l][2 * p + 1] = w[p] < 0.0 ? -w[p] : 0.0;  /* negative-direction plane */
+    }
+    for (int c = 0; c < 3; ++c) inten[l][c] = lights[l].intensity[c];
+  }
+  for (size_t p = 0; p < P; ++p) {
+    double E = lm[7 * P + p];
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int l = 0; l < n_lights; ++l) {
+        double s = 0.0;
+        for (int q = 0; q < 6; ++q) s += wts[l][q] * lm[q * P + p];
+        acc += inten[l][c] * s;
+      }
+      rgba[c * P + p] = acc + E;
+    }
+    double a = 1.0 - lm[6 * P + p];
+    rgba[3 * P + p] = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+  }
+  return 0;
+}

@@ -1,0 +1,90 @@
+/* FP64 CPU oracle for the neural six-way lightmap hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA path: it is written from the paper (Sec. 3 six-way
+ * interpolation, Sec. 4.2 guiding map / Alg. 1 / Eq. approx, Sec. 4.3
+ * generator) and the readings listed in the design notes.
+ *
+ * Conventions: grids are [nz][ny][nx] (x fastest) in voxel units; images are
+ * planar [C][H][W], row 0 at the top.
+ */
+#ifndef NSL_ORACLE_H
+#define NSL_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int kind;               /* 0 orthographic, 1 perspective */
+  float eye[3], target[3], up[3];
+  float fov_y_deg, ortho_height;
+  int width, height;
+} nslo_camera;
+
+typedef struct {
+  float tau_depth;        /* depth threshold tau of Alg. 1 (per-voxel density) */
+  float t_min;            /* early termination of view and shadow rays (0 = off) */
+  int jitter;             /* 1: per-pixel hash jitter delta = u*h, 0: u = 0 */
+  uint32_t seed, frame;
+  float phase_g;          /* Henyey-Greenstein g (0 = isotropic 1/(4 pi)) */
+  float surrogate_I[3];   /* intensities of the front, top, bottom lights */
+  int segment_exact;      /* 0: A_n = T_{n-1} sigma_n h; 1: T_{n-1}(1-exp(-sigma_n h)) */
+  float margin;           /* relative margin for threshold-decision flags */
+} nslo_march_opts;
+
+typedef struct {
+  float dir[3];           /* toward the light, world space */
+  float intensity[3];
+} nslo_light;
+
+/* Guiding map (Alg. 1).  density: float32 [nz][ny][nx] (FP16 inputs are
+ * widened exactly by the caller); mask: uint8 or NULL (non-zero = obstacle).
+ * guide: double [3][H][W] = (L_scattering, T, D).  samples (nullable): int64
+ * [H][W] density evaluations per pixel.  flags (nullable): uint8 [H][W], bit0 =
+ * an early-termination decision lay within the margin, bit1 = a depth decision
+ * lay within the margin.  Returns 0 on success. */
+int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+               double sigma_scale, const nslo_camera* cam, float h,
+               const nslo_march_opts* opts, double* guide, int64_t* samples,
+               uint8_t* flags);
+
+/* Fine-step six-light single-scattering reference: 7 planes
+ * [+X,-X,+Y,-Y,+Z,-Z,T] in the camera frame, midpoint rule with step hf. */
+int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, int ny,
+                             int nz, double sigma_scale, const nslo_camera* cam,
+                             double hf, double phase_g, double* out);
+
+/* Lightmap network forward (UNet + 4 NAFBlock adapters), all FP64.
+ * guide: [3][H][W]; params: float64 values in the blob order; out: [8][H][W]. */
+int nslo_net_forward(const double* guide, int H, int W, const double* params,
+                     int64_t n_params, int c0, double depth_scale, double* out);
+
+/* Six-way shading: rgba [4][H][W]. */
+int nslo_shade(const double* lightmaps, int H, int W, const nslo_camera* cam,
+               const nslo_light* lights, int n_lights, double* rgba);
+
+/* primitives, exposed for pinning against closed forms and library routines */
+double nslo_sample_sigma(const float* density, const uint8_t* mask, int nx, int ny,
+                         int nz, double sigma_scale, const float p[3]);
+double nslo_hg_phase(double g, double cos_theta);
+uint32_t nslo_pcg_hash(uint32_t v);
+void nslo_conv2d(const double* in, int cin, int H, int W, const double* w,
+                 const double* b, int cout, int k, double* out);
+void nslo_conv_transpose2x2(const double* in, int cin, int H, int W, const double* w,
+                            const double* b, int cout, double* out);
+void nslo_maxpool2(const double* in, int C, int H, int W, double* out);
+void nslo_layernorm(const double* in, int C, int H, int W, const double* g,
+                    const double* b, double eps, double* out);
+void nslo_dwconv3(const double* in, int C, int H, int W, const double* w,
+                  const double* b, double* out);
+int nslo_nafblock(const double* in, int C, int H, int W, const double* params,
+                  double* out);
+int64_t nslo_nafblock_params(int C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

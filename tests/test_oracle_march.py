@@ -1,0 +1,251 @@
+"""Pins of the FP64 oracle's guiding-map march (Sec. 4.2, Alg. 1, Eq. approx)
+against closed forms, invariants and textbook special cases.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2604_03748_gb300 import inputs as I
+
+FOUR_PI = 4.0 * math.pi
+
+
+def axis_camera(n, W, H, eye_z_off=18.0, height=None):
+    """Orthographic camera looking along -z at an n^3 box, up = +y."""
+    h = float(n if height is None else height)
+    return I.Camera(I.ORTHO, (n / 2, n / 2, n + eye_z_off), (n / 2, n / 2, 0.0), (0.0, 1.0, 0.0),
+                    40.0, h, W, H)
+
+
+def cube_closed_form(sig, h, M, Kt, Kb, t_min=0.0, segment_exact=False, Pf=1 / FOUR_PI,
+                     Pt=1 / FOUR_PI, Pb=1 / FOUR_PI):
+    """Alg. 1 on a constant box: every sample has sigma = sig, the view ray holds
+    M samples, the vertical shadow rays Kt / Kb samples (truncated at t_min)."""
+    def trunc(K):
+        if t_min <= 0:
+            return K
+        for k in range(1, K + 1):
+            if math.exp(-k * sig * h) < t_min:
+                return k
+        return K
+    Kt, Kb = trunc(Kt), trunc(Kb)
+    Meff = trunc(M)
+    a = (1 - math.exp(-sig * h)) if segment_exact else sig * h
+    q = math.exp(-sig * h)
+    front = sum(q ** (2 * (n - 1)) for n in range(1, Meff + 1))
+    geo = sum(q ** (n - 1) for n in range(1, Meff + 1))
+    L = a * (Pf * front + (Pt * q ** Kt + Pb * q ** Kb) * geo)
+    return L, q ** Meff
+
+
+def test_empty_volume(orc):
+    vol = np.zeros((16, 16, 16), np.float32)
+    cam = I.perspective_camera(16, 3, 24, 16)
+    g, s, f = orc.guide(vol, None, cam, 2.0)
+    assert np.all(g[0] == 0.0) and np.all(g[1] == 1.0) and np.all(g[2] == 0.0)
+
+
+def test_mask_everywhere_equals_empty(orc):
+    vol = I.blob_fbm_volume(16, 4)
+    mask = np.ones_like(vol, dtype=np.uint8)
+    cam = I.perspective_camera(16, 4, 16, 16)
+    g, _, _ = orc.guide(vol, mask, cam, 2.0)
+    assert np.all(g[0] == 0.0) and np.all(g[1] == 1.0) and np.all(g[2] == 0.0)
+
+
+def test_miss_rays(orc):
+    vol = np.full((8, 8, 8), 0.5, np.float32)
+    # camera looking away from the box: every ray misses
+    cam = I.Camera(I.ORTHO, (4.0, 4.0, 20.0), (4.0, 4.0, 40.0), (0.0, 1.0, 0.0), 40.0, 8.0, 8, 8)
+    g, s, _ = orc.guide(vol, None, cam, 1.0)
+    assert np.all(g[0] == 0) and np.all(g[1] == 1) and np.all(g[2] == 0) and np.all(s == 0)
+
+
+@pytest.mark.parametrize("jitter", [0, 1])
+@pytest.mark.parametrize("segment_exact", [0, 1])
+def test_constant_cube_closed_form(orc, jitter, segment_exact):
+    n, h, sig = 32, 4.0, 0.05
+    W = H = 16
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = axis_camera(n, W, H)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=jitter, t_min=0.0, segment_exact=segment_exact,
+                        seed=7, frame=3)
+    M = n // int(h)
+    for j in range(H):
+        y = 31 - 2 * j                      # pixel-centre height
+        Kt, Kb = int((n - y) // h), int(y // h)
+        L, T = cube_closed_form(float(np.float32(sig)), h, M, Kt, Kb, segment_exact=segment_exact)
+        np.testing.assert_allclose(g[0, j], L, rtol=1e-12)
+        np.testing.assert_allclose(g[1, j], T, rtol=1e-12)
+        np.testing.assert_allclose(g[1, j], math.exp(-float(np.float32(sig)) * n), rtol=1e-12)
+        assert np.all(g[2, j] == h)         # first sample already exceeds tau_depth
+
+
+def test_constant_cube_with_early_termination(orc):
+    n, h, sig = 32, 4.0, 0.9
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = axis_camera(n, 16, 16)
+    g, s, _ = orc.guide(vol, None, cam, h, jitter=1, t_min=1e-4)
+    s32 = float(np.float32(sig))
+    for j in range(16):
+        y = 31 - 2 * j
+        Kt, Kb = int((n - y) // h), int(y // h)
+        L, T = cube_closed_form(s32, h, n // 4, Kt, Kb, t_min=1e-4)
+        np.testing.assert_allclose(g[0, j], L, rtol=1e-12)
+        np.testing.assert_allclose(g[1, j], T, rtol=1e-12)
+    # T stops at the first value below t_min: exp(-3*3.6) = 2.0e-5
+    assert np.allclose(g[1], math.exp(-3 * h * s32))
+
+
+def test_phase_function_in_guide(orc):
+    """HG g != 0: front light is back-scatter (cos = -1), top/bottom are at 90 deg
+    for an orthographic camera."""
+    n, h, sig = 32, 4.0, 0.05
+    gg = float(np.float32(0.6))  # the option travels as binary32
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = axis_camera(n, 16, 16)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0, phase_g=gg)
+    hg = lambda c: (1 - gg * gg) / (FOUR_PI * (1 + gg * gg - 2 * gg * c) ** 1.5)
+    for j in (0, 5, 15):
+        y = 31 - 2 * j
+        L, _ = cube_closed_form(float(np.float32(sig)), h, 8, int((n - y) // h), int(y // h),
+                                Pf=hg(-1.0), Pt=hg(0.0), Pb=hg(0.0))
+        np.testing.assert_allclose(g[0, j], L, rtol=1e-12)
+
+
+def test_surrogate_intensities_are_linear(orc):
+    vol = I.blob_fbm_volume(16, 5)
+    cam = I.perspective_camera(16, 5, 16, 16)
+    base = dict(jitter=1, t_min=0.0)
+    parts = []
+    for k in range(3):
+        Iv = [0.0, 0.0, 0.0]
+        Iv[k] = 1.0
+        parts.append(orc.guide(vol, None, cam, 2.0, surrogate_I=tuple(Iv), **base)[0][0])
+    full = orc.guide(vol, None, cam, 2.0, surrogate_I=(1.0, 1.0, 1.0), **base)[0][0]
+    np.testing.assert_allclose(parts[0] + parts[1] + parts[2], full, rtol=1e-12, atol=1e-15)
+    assert np.all(parts[0] >= 0) and parts[0].max() > 0
+
+
+def test_trilinear_exact_on_linear_field(orc):
+    """Trilinear interpolation reproduces a linear function exactly inside the
+    voxel-centre hull and clamps to the edge voxels outside it (still inside the box)."""
+    n = 10
+    a, bx, by, bz = 0.3, 0.02, -0.01, 0.05
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vol = (a + bx * i + by * j + bz * k).astype(np.float64)
+    vol32 = vol.astype(np.float32)
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        p = rng.uniform(0.0, n, size=3).astype(np.float32)
+        c = np.clip(p.astype(np.float64) - 0.5, 0, n - 1)
+        ci = np.floor(c).astype(int)
+        # exact value of the float32 voxel data's trilinear interpolant
+        ref = 0.0
+        t = c - ci
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                    ref += w * float(vol32[min(ci[2] + dz, n - 1), min(ci[1] + dy, n - 1), min(ci[0] + dx, n - 1)])
+        lin = a + bx * c[0] + by * c[1] + bz * c[2]
+        got = orc.sample_sigma(vol32, None, p)
+        assert abs(got - ref) < 1e-12
+        assert abs(got - lin) < 1e-6  # float32 voxel data
+    # outside the closed box -> 0, on its faces -> edge value
+    assert orc.sample_sigma(vol32, None, (n + 1e-3, 5, 5)) == 0.0
+    assert orc.sample_sigma(vol32, None, (-1e-3, 5, 5)) == 0.0
+    assert orc.sample_sigma(vol32, None, (0.0, 0.0, 0.0)) == pytest.approx(float(vol32[0, 0, 0]), abs=1e-12)
+
+
+def test_linear_field_optical_depth_series(orc):
+    """Density linear in z, camera along -z without jitter: the view samples sit
+    at z = n - m h, so -ln T is an arithmetic series of the clamped linear field."""
+    n, h = 32, 2.0
+    a, bz = 0.01, 0.004
+    k = np.arange(n)
+    vol = np.broadcast_to((a + bz * k)[:, None, None], (n, n, n)).astype(np.float32).copy()
+    cam = axis_camera(n, 8, 8)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0)
+    zs = n - h * np.arange(1, n // int(h) + 1)
+    sig = [a + bz * min(max(z - 0.5, 0.0), n - 1) for z in zs]
+    tau = h * sum(sig)
+    np.testing.assert_allclose(-np.log(g[1]), tau, rtol=1e-9)
+
+
+def test_step_refinement_converges(orc):
+    """-ln T approaches the integral of the trilinear field as h -> 0, with error O(h)."""
+    n = 32
+    a, bz = 0.01, 0.004
+    k = np.arange(n)
+    vol = np.broadcast_to((a + bz * k)[:, None, None], (n, n, n)).astype(np.float32).copy()
+    # exact integral over z in [0, n] of a + bz*clamp(z-0.5, 0, n-1)
+    exact = a * n + bz * (0.5 * (n - 1) ** 2 + 0.5 * (n - 1))
+    errs = []
+    for h in (4.0, 2.0, 1.0, 0.5, 0.25):
+        g, _, _ = orc.guide(vol, None, axis_camera(n, 8, 8), h, jitter=0, t_min=0.0)
+        errs.append(abs(-np.log(g[1]).mean() - exact))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert e1 < e0 and 0.3 < e1 / e0 < 0.7
+
+
+def test_jitter_unbiased_sample_count():
+    """Averaged over the jitter u in [0,1), N = floor(chord/h + u) has mean chord/h."""
+    chord, h = 37.3, 4.0
+    us = (np.arange(1 << 16) + 0.5) / (1 << 16)
+    N = np.floor(chord / h + us)
+    assert abs(N.mean() - chord / h) < 1e-4
+
+
+def test_vertical_flip_symmetry(orc):
+    """Flipping the grid about the horizontal mid-plane flips the guide rows; top
+    and bottom lights swap roles, their sum is invariant."""
+    vol = I.blob_fbm_volume(24, 6)
+    n = 24
+    cam = I.Camera(I.ORTHO, (12.0, 12.0, 40.0), (12.0, 12.0, 0.0), (0.0, 1.0, 0.0), 40.0, 24.0, 16, 16)
+    g1, _, _ = orc.guide(vol, None, cam, 2.0, jitter=0, t_min=0.0)
+    g2, _, _ = orc.guide(vol[:, ::-1, :].copy(), None, cam, 2.0, jitter=0, t_min=0.0)
+    np.testing.assert_allclose(g2[:, ::-1, :], g1, rtol=1e-12, atol=1e-15)
+
+
+def test_hg_phase_normalisation(orc):
+    from scipy.integrate import quad
+    assert orc.hg_phase(0.0, 0.3) == pytest.approx(1 / FOUR_PI, rel=1e-15)
+    for g in (-0.7, -0.2, 0.0, 0.3, 0.8):
+        tot = 2 * math.pi * quad(lambda mu: orc.hg_phase(g, mu), -1, 1, epsabs=1e-13)[0]
+        mean_cos = 2 * math.pi * quad(lambda mu: mu * orc.hg_phase(g, mu), -1, 1, epsabs=1e-13)[0]
+        assert tot == pytest.approx(1.0, abs=1e-9)
+        assert mean_cos == pytest.approx(g, abs=1e-9)
+
+
+def test_pcg_hash_reference_values(orc):
+    """The hash is the published 32-bit PCG output permutation; check bijectivity on
+    a sample and a value computed by hand from its definition (LCG step,
+    xorshift by 4 + top 4 bits, multiply, xorshift by 22)."""
+    v = 0
+    state = (v * 747796405 + 2891336453) & 0xFFFFFFFF
+    word = (((state >> ((state >> 28) + 4)) ^ state) * 277803737) & 0xFFFFFFFF
+    assert orc.pcg_hash(0) == ((word >> 22) ^ word)
+    outs = {orc.pcg_hash(i) for i in range(5000)}
+    assert len(outs) == 5000
+
+
+def test_depth_channel(orc):
+    """D = n h at the first sample whose density exceeds tau (literal Alg. 1)."""
+    n, h = 32, 2.0
+    vol = np.zeros((n, n, n), np.float32)
+    vol[:10] = 0.5          # dense slab at the back (z < 10)
+    cam = axis_camera(n, 8, 8)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0)
+    # samples at z = 32 - 2m; sigma(z) > 0.01 first where the trilinear ramp of
+    # the slab edge (voxel 9 -> 10 between z = 9.5 and 10.5) exceeds tau: z = 10
+    # gives sigma = 0.25 at m = 11.
+    assert np.all(g[2] == 11 * h)
+
+
+def test_sample_counts_and_flags_small(orc):
+    pf = I.config_plain_64()
+    g, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    assert s.sum() > 0 and s.max() <= 28 * (1 + 2 * 16) + 28
+    assert f.mean() < 1e-3
+    assert np.all(g[1] > 0) and np.all(g[1] <= 1) and np.all(g[0] >= 0)
