@@ -1,0 +1,324 @@
+"""Benchmark of the neural six-way lightmap hot path on GB300.
+
+One step = one frame of the whole hot path on the 128^3 FP32 smoke grid with a
+radius-20 sphere obstacle, perspective camera, 512x512 billboard, step 2
+voxels: grid staging -> guide march -> lightmap network -> six-way shading.
+Metric: Mpix/s of completed (guide + lightmaps) frames.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
+
+N > 1 (torchrun): independent replicas, one frame stream per GPU (the path has
+no exchange step); value = frames of all ranks / max-over-ranks time.
+The grid (10 MiB) fits in L2, so L2 is flushed (a 256 MiB write) before every
+timed step, outside the timed events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "plume128_sphere20_persp512_h2"
+METRIC = "Mpix/s guide+lightmaps"
+# FP32 operations charged per density evaluation of the march (algorithmic):
+# sample position 7 (3 mul, 3 add, 1 mul for k*h), trilinear 30 (3 sub, 3 floor,
+# 3 sub, 7 lerps x (1 sub + 1 FMA)), optical-depth accumulation 2.
+FLOP_PER_SAMPLE = 39
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_frame(pf, rows, blob_params, c0=16):
+    """The FP64 oracle on a band of `rows` image rows: guide, network on the band, shade."""
+    import oracle
+    r0 = (pf.camera.height - rows) // 2
+    t0 = time.perf_counter()
+    g, _, _ = oracle.guide(pf.density, pf.mask, pf.camera, pf.step, rows=(r0, r0 + rows))
+    band = np.ascontiguousarray(g[:, r0:r0 + rows, :])
+    diag = math.sqrt(sum(float(v) ** 2 for v in pf.density.shape))
+    lm = oracle.net_forward(band, blob_params, c0, 1.0 / diag)
+    cam = pf.camera
+    import dataclasses
+    cam_band = dataclasses.replace(cam, height=rows)
+    oracle.shade(lm, cam_band, [pf.light])
+    return time.perf_counter() - t0, rows * pf.camera.width
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2604_03748_gb300 import inputs as I
+    oracle.build()
+    pf = I.config_obstacle_128()
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    # size the per-step band so the whole run stays within ~2.5 minutes: one
+    # probe band measures the per-pixel cost on this host
+    probe_t, probe_px = cpu_oracle_frame(pf, 16, flat)
+    per_px = probe_t / probe_px
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(max(8, min(pf.camera.height, budget / per_px / pf.camera.width)) // 8 * 8)
+    for _ in range(args.warmup):
+        cpu_oracle_frame(pf, 8, flat)
+    total_t, total_px = 0.0, 0
+    for _ in range(args.steps):
+        t, px = cpu_oracle_frame(pf, rows, flat)
+        total_t += t
+        total_px += px
+    value = total_px / total_t / 1e6
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [128, 128, 128], "billboard": [512, 512],
+                                        "step_voxels": 2.0, "obstacle": "sphere r=20",
+                                        "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows}x512 pixel band of the 512x512 frame per step: guide march, "
+                                   f"network on the band, shade"},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nsl", choices=["nsl", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2604_03748_gb300 import build as B, inputs as I, nsl
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    nsl.load()
+
+    prec = {"f32": nsl.NSL_PREC_F32, "bf16": nsl.NSL_PREC_BF16, "fp8": nsl.NSL_PREC_FP8}[args.precision]
+    pf = I.config_obstacle_128()
+    H, W = pf.camera.height, pf.camera.width
+    blob = I.pack_blob(I.make_params(16, 0), 16)
+    ctx = nsl.Context(pf.density.shape, nsl.NSL_F32, blob, W, H)
+    stream = torch.cuda.current_stream()
+    dens = torch.from_numpy(pf.density).to(dev)
+    mask = torch.from_numpy(pf.mask).to(dev)
+    guide = torch.empty((3, H, W), device=dev)
+    lm = torch.empty((8, H, W), device=dev)
+    rgba = torch.empty((4, H, W), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    opts = nsl.march_opts()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        nsl.nsl_stage_grid(ctx.ctx, dens, mask, stream=stream)
+        if evs:
+            evs[1].record(stream)
+        nsl.nsl_guiding_map(ctx.ctx, None, None, pf.camera, pf.step, guide, opts=opts, stream=stream)
+        if evs:
+            evs[2].record(stream)
+        nsl.nsl_predict_lightmaps(ctx.ctx, guide, W, H, prec, lm, stream=stream)
+        if evs:
+            evs[3].record(stream)
+        nsl.nsl_shade(ctx.ctx, lm, W, H, pf.camera, [pf.light], rgba, stream=stream)
+        if evs:
+            evs[4].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    samples = ctx.guide_sample_count(pf.camera, pf.step, opts)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_host0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(events[k])
+    torch.cuda.synchronize()
+    t_host = time.perf_counter() - t_host0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[4]) for e in events]
+    stage_ms = [e[0].elapsed_time(e[1]) for e in events]
+    march_ms = [e[1].elapsed_time(e[2]) for e in events]
+    net_ms = [e[2].elapsed_time(e[3]) for e in events]
+    shade_ms = [e[3].elapsed_time(e[4]) for e in events]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames = args.steps * ws
+    value = frames * H * W / (total_ms / 1e3) / 1e6
+
+    # end to end through the host entry point: H2D of the grid + mask, D2H of
+    # guide, lightmaps and rgba, every step
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    h_dens, h_mask = pin(pf.density), pin(pf.mask)
+    h_guide = torch.empty((3, H, W)).pin_memory()
+    h_lm = torch.empty((8, H, W)).pin_memory()
+    h_rgba = torch.empty((4, H, W)).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 1):
+        t0 = time.perf_counter()
+        nsl.nsl_render_frame_host(ctx.ctx, h_dens.numpy(), h_mask.numpy(), pf.camera, [pf.light], pf.step,
+                                  prec, h_guide.numpy(), h_lm.numpy(), h_rgba.numpy(), opts=opts,
+                                  stream=stream)
+        if k:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_val = H * W / float(np.mean(e2e_t)) / 1e6 * ws
+
+    pk, pk_kind = peaks()
+    march_avg_s = float(np.mean(march_ms)) / 1e3
+    achieved = samples * FLOP_PER_SAMPLE / march_avg_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "f32 march + bf16 net", "fp8": "f32 march + fp8 net"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [128, 128, 128], "grid_dtype": "f32", "billboard": [512, 512],
+                   "camera": "perspective fov 40", "step_voxels": 2.0, "obstacle": "sphere r=20",
+                   "network": f"UNet C0=16 + 4 NAFBlock adapters, {args.precision}", "lights": 1,
+                   "l2": "flushed (256 MiB write) before every timed step, outside the timed events"},
+        "stage_ms": {"stage": float(np.mean(stage_ms)), "march": float(np.mean(march_ms)),
+                     "net": float(np.mean(net_ms)), "shade": float(np.mean(shade_ms))},
+        "roofline": {"kernel": "march_kernel (guide march)", "bound": "alu",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "work": {"density_samples": samples, "flop_per_sample": FLOP_PER_SAMPLE},
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "e2e": {"value": e2e_val, "unit": "Mpix/s",
+                "h2d_bytes_per_step": int(pf.density.nbytes + pf.mask.nbytes),
+                "d2h_bytes_per_step": int((3 + 8 + 4) * H * W * 4)},
+        "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+        "clocks": clk,
+        "host_wall_s": t_host,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+        t, px = cpu_oracle_frame(pf, 512, flat)
+        line["cpu_baseline"] = {"value": px / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": "one whole 512x512 frame: FP64 guide march, FP64 network, shade"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# stage 1 + march 1 + network (14 conv + 3 transposed conv + 3 adapter) + shade 1
+LAUNCHES_PER_STEP = 1 + 1 + 20 + 1
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/* nsl.h -- C ABI of the GB300 neural six-way lightmap library (libnsl.so).
+ *
+ * The per-frame hot path of "Real-time Neural Six-way Lightmaps"
+ * (arXiv 2604.03748):
+ *   1. nsl_guiding_map        coarse camera-view ray march under three surrogate
+ *                             lights -> guiding map (Sec. 4.2, Alg. 1, Eq. approx)
+ *   2. nsl_predict_lightmaps  UNet + four NAFBlock channel adapters -> six
+ *                             directional lightmaps + transparency + emissive
+ *                             (Sec. 4.3, Fig. 3)
+ *   3. nsl_shade              six-way directional interpolation for any set of
+ *                             directional lights (Sec. 3, six-way interpolation)
+ *
+ * Conventions
+ *   - World units are voxels.  A grid (nx, ny, nz) is stored [nz][ny][nx] with
+ *     x fastest and occupies the box [0,nx] x [0,ny] x [0,nz]; voxel (i,j,k) is
+ *     centred at (i+.5, j+.5, k+.5).
+ *   - Camera frame: X = right, Y = up, Z = forward (into the screen).
+ *   - Images are planar [C][H][W] float32, row 0 at the top.
+ *   - Every *_dev pointer is a device pointer owned by the caller, 16-byte
+ *     aligned, and borrowed until the work queued on `stream` completes.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Errors: argument errors are reported synchronously and nothing is queued.
+ *     A CUDA error raised by a launch is returned as NSL_ERR_CUDA; an
+ *     asynchronous fault surfaces on a later call or synchronisation.  No call
+ *     aborts or prints.  nsl_last_error() gives a message for the calling thread.
+ *   - Threading: one context may be used by one host thread at a time.
+ */
+#ifndef NSL_H
+#define NSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NSL_API __attribute__((visibility("default")))
+#else
+#define NSL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NSL_OK = 0,
+  NSL_ERR_INVALID_ARG = 1,
+  NSL_ERR_OOM = 2,
+  NSL_ERR_CUDA = 3,
+  NSL_ERR_UNSUPPORTED = 4,
+  NSL_ERR_TIMEOUT = 5,
+  NSL_ERR_BUDGET = 6
+} nsl_status;
+
+enum { NSL_F32 = 0, NSL_F16 = 1 };                           /* density storage */
+enum { NSL_PREC_F32 = 0, NSL_PREC_BF16 = 1, NSL_PREC_FP8 = 2 }; /* network arithmetic */
+enum { NSL_CAM_ORTHO = 0, NSL_CAM_PERSP = 1 };
+
+typedef struct nsl_ctx nsl_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int nx, ny, nz;     /* grid size in voxels, each in [1, 4096] */
+  int dtype;          /* NSL_F32 or NSL_F16 */
+  float sigma_scale;  /* extinction = sigma_scale * density (albedo 1) */
+} nsl_grid_desc;
+
+typedef struct {
+  int kind;                          /* NSL_CAM_ORTHO or NSL_CAM_PERSP */
+  float eye[3], target[3], up[3];    /* world space */
+  float fov_y_deg;                   /* perspective: vertical field of view */
+  float ortho_height;                /* orthographic: view height in voxels */
+  int width, height;                 /* billboard pixels, multiples of 8 */
+} nsl_camera;
+
+typedef struct {
+  float dir[3];        /* world-space vector toward the light (normalised by the library) */
+  float intensity[3];  /* RGB */
+} nsl_light;
+
+typedef struct {
+  float tau_depth;       /* Alg. 1 depth threshold tau on the density (default 0.01) */
+  float t_min;           /* early termination when transmittance < t_min (1e-4; 0 = off) */
+  int jitter;            /* 1: per-pixel hash jitter of the first sample (Alg. 1 delta) */
+  uint32_t seed, frame;  /* jitter hash inputs */
+  float phase_g;         /* Henyey-Greenstein g of the surrogate lights (0 = isotropic) */
+  float surrogate_I[3];  /* intensities of the front, top, bottom surrogate lights */
+  int segment_exact;     /* 0: A_n = T_{n-1} sigma_n h;  1: A_n = T_{n-1}(1 - e^{-sigma_n h}) */
+} nsl_march_opts;
+
+/* Default options: tau_depth 0.01, t_min 1e-4, jitter 1, seed 0, frame 0,
+ * g 0, intensities 1, segment_exact 0. */
+NSL_API void nsl_default_march_opts(nsl_march_opts* out);
+
+/* Create a context.  Sec. 4.3 (one network for all scenes, Sec. 5).
+ *   grid          grid shape and storage used by nsl_guiding_map and for the
+ *                 network's depth normalisation (D / |grid diagonal|).
+ *   weights_blob  NSLW blob: "NSLW", u32 version (1), u32 C0, u32 n_floats,
+ *                 n_floats float32 parameters in the documented order, u32
+ *                 checksum.  Copied; the caller keeps ownership.
+ *   max_width, max_height  largest billboard any later call may use; the
+ *                 network workspace is allocated for it (device memory).
+ * Returns NSL_ERR_INVALID_ARG for a malformed blob or sizes, NSL_ERR_OOM when
+ * device memory runs out, NSL_ERR_UNSUPPORTED for C0 other than 16. */
+NSL_API nsl_status nsl_create(const nsl_grid_desc* grid, const void* weights_blob, size_t blob_bytes,
+                      int max_width, int max_height, nsl_ctx** out);
+
+/* Release the context and everything it owns (synchronises its work). */
+NSL_API void nsl_destroy(nsl_ctx* ctx);
+
+/* Stage a density grid into the context (Sec. 4.2: sigma_s in a 3D texture):
+ * sigma' = sigma_scale * density * [mask == 0], widened to float32, kept in a
+ * context-owned device buffer until the next staging.  A later
+ * nsl_guiding_map with density_dev == NULL marches this resident grid.
+ *   density_dev   [nz][ny][nx] float32 or float16 (grid.dtype)
+ *   mask_dev      [nz][ny][nx] uint8 obstacle mask (non-zero = obstacle) or NULL */
+NSL_API nsl_status nsl_stage_grid(nsl_ctx* ctx, const void* density_dev, const uint8_t* mask_dev,
+                                  void* stream);
+
+/* Guiding map, Sec. 4.2 / Alg. 1 / Eq. approx.
+ *   density_dev   [nz][ny][nx] float32 or float16 (grid.dtype), staged first
+ *                 as by nsl_stage_grid; NULL = march the grid staged last
+ *   mask_dev      [nz][ny][nx] uint8 obstacle mask, non-zero zeroes the voxel; may be NULL
+ *   cam           camera; cam->width x cam->height <= the context maximum
+ *   light         accepted and unused: the guide uses the fixed surrogate
+ *                 lights of Eq. approx (front, top, bottom); may be NULL
+ *   step_voxels   march step h in voxels (> 0)
+ *   opts          march options (NULL = defaults)
+ *   guide_dev     output [3][H][W] float32: (L_scattering, T, D in voxels)
+ * Uses library-owned scratch (staged grid, tile counters). */
+NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const uint8_t* mask_dev,
+                           const nsl_camera* cam, const nsl_light* light, float step_voxels,
+                           const nsl_march_opts* opts, float* guide_dev, void* stream);
+
+/* Number of density evaluations the guide march of nsl_guiding_map makes for
+ * this camera, step and options on the staged grid: view samples plus the
+ * shadow samples of every view sample with non-zero density (Alg. 1).  Runs a
+ * counting variant of the march kernel and synchronises `stream`; the guide is
+ * not written.  *samples_out receives the total. */
+NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, float step_voxels,
+                                          const nsl_march_opts* opts,
+                                          unsigned long long* samples_out, void* stream);
+
+/* Lightmap network, Sec. 4.3 / Fig. 3.
+ *   guide_dev      [3][H][W] float32 guide
+ *   width, height  multiples of 8, within the context maximum
+ *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16 or NSL_PREC_FP8
+ *                  (tensor cores, FP32 accumulation)
+ *   lightmaps_dev  output [8][H][W] float32 planes
+ *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
+NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
+                                 int precision, float* lightmaps_dev, void* stream);
+
+/* Six-way shading, Sec. 3 (directional interpolation, summed over lights):
+ *   rgb = sum_l I_l * sum_{p in X,Y,Z} |w_p| L_p^{sign w_p} + E,  A = clamp(1 - T, 0, 1)
+ * with w the unit toward-light vector of light l in the camera frame of cam.
+ *   lights         n_lights in [0, 64]
+ *   rgba_dev       output [4][H][W] float32 */
+NSL_API nsl_status nsl_shade(nsl_ctx* ctx, const float* lightmaps_dev, int width, int height,
+                     const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                     float* rgba_dev, void* stream);
+
+/* One whole frame from HOST buffers: copies density (and mask) to the device,
+ * runs the guide, the network and the shading, copies guide, lightmaps and
+ * rgba back, and synchronises `stream`.  Host pointers may be NULL for outputs
+ * that are not wanted.  Uses context-owned device staging buffers.
+ *   density_host  grid.dtype elements; mask_host may be NULL */
+NSL_API nsl_status nsl_render_frame_host(nsl_ctx* ctx, const void* density_host,
+                                 const uint8_t* mask_host, const nsl_camera* cam,
+                                 const nsl_light* lights, int n_lights, float step_voxels,
+                                 const nsl_march_opts* opts, int precision, float* guide_host,
+                                 float* lightmaps_host, float* rgba_host, void* stream);
+
+/* Description of the last error raised on the calling thread ("" if none). */
+NSL_API const char* nsl_last_error(void);
+NSL_API const char* nsl_status_str(nsl_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSL_H */

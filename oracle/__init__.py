@@ -71,6 +71,9 @@ def _load():
     lib.nslo_guide.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                C.POINTER(_Camera), C.c_float, C.POINTER(_Opts), C.c_void_p,
                                C.c_void_p, C.c_void_p]
+    lib.nslo_guide_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                    C.POINTER(_Camera), C.c_float, C.POINTER(_Opts), C.c_int,
+                                    C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.nslo_reference_lightmaps.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                              C.c_double, C.POINTER(_Camera), C.c_double,
                                              C.c_double, C.c_void_p]
@@ -136,8 +139,9 @@ DEFAULT_OPTS = dict(tau_depth=0.01, t_min=1e-4, jitter=1, seed=0, frame=0, phase
                     surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5)
 
 
-def guide(density, mask, camera, step, sigma_scale=1.0, **opts):
-    """Alg. 1 guiding map.  Returns (guide[3,H,W] float64, samples[H,W] int64, flags[H,W] uint8)."""
+def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
+    """Alg. 1 guiding map.  Returns (guide[3,H,W] float64, samples[H,W] int64, flags[H,W] uint8).
+    rows=(r0, r1) restricts the march to image rows [r0, r1) (others stay 0)."""
     lib = _load()
     o = dict(DEFAULT_OPTS)
     o.update(opts)
@@ -153,8 +157,10 @@ def guide(density, mask, camera, step, sigma_scale=1.0, **opts):
     op.phase_g = o["phase_g"]; op.surrogate_I[:] = list(o["surrogate_I"])
     op.segment_exact = int(o["segment_exact"]); op.margin = o["margin"]
     cam = _cam(camera)
-    rc = lib.nslo_guide(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(cam),
-                        float(step), C.byref(op), _ptr(out), _ptr(samples), _ptr(flags))
+    r0, r1 = (0, H) if rows is None else rows
+    rc = lib.nslo_guide_rows(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(cam),
+                             float(step), C.byref(op), int(r0), int(r1), _ptr(out), _ptr(samples),
+                             _ptr(flags))
     if rc != 0:
         raise ValueError(f"nslo_guide failed ({rc})")
     return out, samples, flags

@@ -248,8 +248,18 @@ static double shadow_T(const field* F, const float p[3], const float s[3], float
 int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz,
                double sigma_scale, const nslo_camera* cam, float h,
                const nslo_march_opts* op, double* guide, int64_t* samples, uint8_t* flags) {
+  if (!cam) return 1;
+  return nslo_guide_rows(density, mask, nx, ny, nz, sigma_scale, cam, h, op, 0, cam->height,
+                         guide, samples, flags);
+}
+
+int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+                    double sigma_scale, const nslo_camera* cam, float h,
+                    const nslo_march_opts* op, int row0, int row1, double* guide,
+                    int64_t* samples, uint8_t* flags) {
   if (!density || !cam || !op || !guide || nx <= 0 || ny <= 0 || nz <= 0 || !(h > 0.0f))
     return 1;
+  if (row0 < 0 || row1 > cam->height || row0 > row1) return 1;
   field F = {density, mask, nx, ny, nz, sigma_scale, {(float)nx, (float)ny, (float)nz}};
   cam_frame fr;
   cam_setup(cam, &fr);
@@ -259,7 +269,7 @@ int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz
   const double g = op->phase_g;
 
 #pragma omp parallel for schedule(dynamic, 4)
-  for (int j = 0; j < H; ++j) {
+  for (int j = row0; j < row1; ++j) {
     for (int i = 0; i < W; ++i) {
       size_t pix = (size_t)j * W + i;
       float o[3], d[3], tin, tout;
@@ -295,8 +305,13 @@ int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz
             if (sg > (double)op->tau_depth) D = (double)n * (double)h;
           }
           double A = op->segment_exact ? T * (1.0 - exp(-sg * (double)h)) : T * sg * (double)h;
-          double Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
-          double Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
+          /* sigma_n = 0 gives A_n = 0, so A_n L_n vanishes whatever L_n is: the
+           * shadow rays of such a sample are not marched (and not counted) */
+          double Tt = 1.0, Tb = 1.0;
+          if (sg > 0.0) {
+            Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
+            Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
+          }
           double Ln = P_f * op->surrogate_I[0] * T + P_t * op->surrogate_I[1] * Tt +
                       P_b * op->surrogate_I[2] * Tb;
           L += A * Ln;

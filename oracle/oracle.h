@@ -50,6 +50,11 @@ int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz
                double sigma_scale, const nslo_camera* cam, float h,
                const nslo_march_opts* opts, double* guide, int64_t* samples,
                uint8_t* flags);
+/* Same as nslo_guide for image rows [row0, row1) only; other rows untouched. */
+int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+                    double sigma_scale, const nslo_camera* cam, float h,
+                    const nslo_march_opts* opts, int row0, int row1, double* guide,
+                    int64_t* samples, uint8_t* flags);
 
 /* Fine-step six-light single-scattering reference: 7 planes
  * [+X,-X,+Y,-Y,+Z,-Z,T] in the camera frame, midpoint rule with step hf. */

@@ -1,0 +1,457 @@
+// C ABI of libnsl: argument checking, contexts and orchestration of the
+// kernels of the guide march (Sec. 4.2), the lightmap network (Sec. 4.3) and
+// the six-way shading (Sec. 3).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nsl_internal.cuh"
+
+namespace nsl {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+nsl_status fail(nsl_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+nsl_status cuda_fail(cudaError_t e, const char* where) {
+  set_error("%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? NSL_ERR_OOM : NSL_ERR_CUDA;
+}
+
+// Camera basis in binary64, rounded once to binary32 (same sequence as any
+// other evaluation that must agree on integer decisions):
+//   f = normalize(target - eye), r = normalize(f x up), u = r x f.
+void cam_frame_from(const nsl_camera& c, CamFrame* fr) {
+  double fx = (double)c.target[0] - (double)c.eye[0];
+  double fy = (double)c.target[1] - (double)c.eye[1];
+  double fz = (double)c.target[2] - (double)c.eye[2];
+  double fl = std::sqrt(fx * fx + fy * fy + fz * fz);
+  double Fx = fx / fl, Fy = fy / fl, Fz = fz / fl;
+  double ux = c.up[0], uy = c.up[1], uz = c.up[2];
+  double rx = Fy * uz - Fz * uy, ry = Fz * ux - Fx * uz, rz = Fx * uy - Fy * ux;
+  double rl = std::sqrt(rx * rx + ry * ry + rz * rz);
+  rx /= rl; ry /= rl; rz /= rl;
+  double vx = ry * Fz - rz * Fy, vy = rz * Fx - rx * Fz, vz = rx * Fy - ry * Fx;
+  for (int k = 0; k < 3; ++k) fr->eye[k] = c.eye[k];
+  fr->f[0] = (float)Fx; fr->f[1] = (float)Fy; fr->f[2] = (float)Fz;
+  fr->r[0] = (float)rx; fr->r[1] = (float)ry; fr->r[2] = (float)rz;
+  fr->u[0] = (float)vx; fr->u[1] = (float)vy; fr->u[2] = (float)vz;
+  fr->kind = c.kind; fr->W = c.width; fr->H = c.height;
+  if (c.kind == NSL_CAM_ORTHO) {
+    fr->ax = (float)(((double)c.ortho_height * (double)c.width) / (double)c.height);
+    fr->ay = c.ortho_height;
+  } else {
+    double k = 2.0 * std::tan(((double)c.fov_y_deg * 3.14159265358979323846 / 180.0) * 0.5);
+    fr->ax = (float)((k * (double)c.width) / (double)c.height);
+    fr->ay = (float)k;
+  }
+}
+
+bool build_net_layout(int c0, NetLayout* L) {
+  size_t off = 0;
+  const int c[4] = {c0, 2 * c0, 4 * c0, 8 * c0};
+  auto conv = [&](int l, int cin, int cout) {
+    L->conv_w[l] = off; off += (size_t)cout * cin * 9;
+    L->conv_b[l] = off; off += cout;
+    L->conv_cin[l] = cin; L->conv_cout[l] = cout;
+  };
+  auto up = [&](int l, int cin, int cout) {
+    L->up_w[l] = off; off += (size_t)cin * cout * 4;
+    L->up_b[l] = off; off += cout;
+    L->up_cin[l] = cin; L->up_cout[l] = cout;
+  };
+  conv(0, 3, c[0]); conv(1, c[0], c[0]);
+  conv(2, c[0], c[1]); conv(3, c[1], c[1]);
+  conv(4, c[1], c[2]); conv(5, c[2], c[2]);
+  conv(6, c[2], c[3]); conv(7, c[3], c[3]);
+  up(0, c[3], c[2]); conv(8, c[3], c[2]); conv(9, c[2], c[2]);
+  up(1, c[2], c[1]); conv(10, c[2], c[1]); conv(11, c[1], c[1]);
+  up(2, c[1], c[0]); conv(12, c[1], c[0]); conv(13, c[0], c[0]);
+  for (int a = 0; a < 4; ++a) {
+    L->adapter[a] = off;
+    off += kAdapterParams;
+  }
+  L->total = off;
+  return c0 == kC0;
+}
+
+}  // namespace nsl
+
+using namespace nsl;
+
+struct nsl_ctx {
+  nsl_grid_desc grid{};
+  int max_w = 0, max_h = 0;
+  int device = 0;
+  std::vector<float> params;
+  NetLayout layout{};
+  float* staged = nullptr;          // staged extinction grid
+  bool staged_valid = false;        // a staging has been queued
+  unsigned long long* counter = nullptr;  // sample-count scratch
+  NetF32Weights* wf32 = nullptr;
+  void* ws = nullptr;               // network workspace
+  size_t ws_bytes = 0;
+  // device staging for nsl_render_frame_host
+  void* h_density = nullptr;
+  uint8_t* h_mask = nullptr;
+  float* h_guide = nullptr;
+  float* h_lm = nullptr;
+  float* h_rgba = nullptr;
+};
+
+static size_t grid_voxels(const nsl_grid_desc& g) { return (size_t)g.nx * g.ny * g.nz; }
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+extern "C" {
+
+void nsl_default_march_opts(nsl_march_opts* o) {
+  if (!o) return;
+  o->tau_depth = 0.01f;
+  o->t_min = 1e-4f;
+  o->jitter = 1;
+  o->seed = 0;
+  o->frame = 0;
+  o->phase_g = 0.f;
+  o->surrogate_I[0] = o->surrogate_I[1] = o->surrogate_I[2] = 1.f;
+  o->segment_exact = 0;
+}
+
+const char* nsl_last_error(void) { return g_err; }
+
+const char* nsl_status_str(nsl_status s) {
+  switch (s) {
+    case NSL_OK: return "ok";
+    case NSL_ERR_INVALID_ARG: return "invalid argument";
+    case NSL_ERR_OOM: return "out of device memory";
+    case NSL_ERR_CUDA: return "CUDA error";
+    case NSL_ERR_UNSUPPORTED: return "unsupported";
+    case NSL_ERR_TIMEOUT: return "timeout";
+    case NSL_ERR_BUDGET: return "over memory budget";
+  }
+  return "unknown status";
+}
+
+nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_bytes,
+                      int max_width, int max_height, nsl_ctx** out) {
+  if (!out) return fail(NSL_ERR_INVALID_ARG, "nsl_create: out is NULL");
+  *out = nullptr;
+  if (!grid || !blob) return fail(NSL_ERR_INVALID_ARG, "nsl_create: NULL grid or blob");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 4096 || grid->ny > 4096 ||
+      grid->nz > 4096)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_create: grid dims out of range");
+  if (grid->dtype != NSL_F32 && grid->dtype != NSL_F16)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_create: bad density dtype %d", grid->dtype);
+  if (!(grid->sigma_scale >= 0.f) || !std::isfinite(grid->sigma_scale))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_create: bad sigma_scale");
+  if (max_width < 8 || max_height < 8 || max_width % 8 || max_height % 8 || max_width > 8192 ||
+      max_height > 8192)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_create: max size must be multiples of 8 in [8, 8192]");
+  if (blob_bytes < 20) return fail(NSL_ERR_INVALID_ARG, "nsl_create: blob too small");
+  const unsigned char* b = static_cast<const unsigned char*>(blob);
+  if (std::memcmp(b, "NSLW", 4) != 0) return fail(NSL_ERR_INVALID_ARG, "nsl_create: bad magic");
+  uint32_t ver, c0, nf;
+  std::memcpy(&ver, b + 4, 4);
+  std::memcpy(&c0, b + 8, 4);
+  std::memcpy(&nf, b + 12, 4);
+  if (ver != 1) return fail(NSL_ERR_INVALID_ARG, "nsl_create: blob version %u", ver);
+  if ((size_t)nf * 4 + 20 != blob_bytes)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_create: blob size mismatch");
+  NetLayout L{};
+  if (!build_net_layout((int)c0, &L))
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_create: base width C0=%u (only 16 is built)", c0);
+  if (L.total != nf) return fail(NSL_ERR_INVALID_ARG, "nsl_create: parameter count %u", nf);
+  uint32_t chk = 0, stored;
+  for (uint32_t i = 0; i < nf; ++i) {
+    uint32_t w;
+    std::memcpy(&w, b + 16 + 4 * (size_t)i, 4);
+    chk += w;
+  }
+  std::memcpy(&stored, b + 16 + 4 * (size_t)nf, 4);
+  if (chk != stored) return fail(NSL_ERR_INVALID_ARG, "nsl_create: blob checksum mismatch");
+
+  nsl_ctx* c = new (std::nothrow) nsl_ctx();
+  if (!c) return fail(NSL_ERR_OOM, "nsl_create: host allocation");
+  c->grid = *grid;
+  c->max_w = max_width;
+  c->max_h = max_height;
+  c->layout = L;
+  c->params.resize(nf);
+  std::memcpy(c->params.data(), b + 16, (size_t)nf * 4);
+  cudaGetDevice(&c->device);
+  cudaError_t e = cudaMalloc(&c->staged, grid_voxels(*grid) * sizeof(float));
+  if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: staged grid"); }
+  c->wf32 = net_f32_create(c->params.data(), L, &e);
+  if (!c->wf32) { nsl_destroy(c); return cuda_fail(e, "nsl_create: FP32 weights"); }
+  c->ws_bytes = net_f32_workspace_bytes(max_width, max_height);
+  e = cudaMalloc(&c->ws, c->ws_bytes);
+  if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: workspace"); }
+  *out = c;
+  return NSL_OK;
+}
+
+void nsl_destroy(nsl_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->staged);
+  cudaFree(c->counter);
+  net_f32_destroy(c->wf32);
+  cudaFree(c->ws);
+  cudaFree(c->h_density);
+  cudaFree(c->h_mask);
+  cudaFree(c->h_guide);
+  cudaFree(c->h_lm);
+  cudaFree(c->h_rgba);
+  delete c;
+}
+
+static nsl_status check_camera(const nsl_ctx* c, const nsl_camera* cam, const char* fn) {
+  if (!cam) return fail(NSL_ERR_INVALID_ARG, "%s: camera is NULL", fn);
+  if (cam->kind != NSL_CAM_ORTHO && cam->kind != NSL_CAM_PERSP)
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad camera kind", fn);
+  if (cam->width < 8 || cam->height < 8 || cam->width % 8 || cam->height % 8)
+    return fail(NSL_ERR_INVALID_ARG, "%s: width/height must be positive multiples of 8", fn);
+  if (cam->width > c->max_w || cam->height > c->max_h)
+    return fail(NSL_ERR_INVALID_ARG, "%s: %dx%d exceeds the context maximum %dx%d", fn,
+                cam->width, cam->height, c->max_w, c->max_h);
+  double fx = (double)cam->target[0] - cam->eye[0], fy = (double)cam->target[1] - cam->eye[1],
+         fz = (double)cam->target[2] - cam->eye[2];
+  double fl = std::sqrt(fx * fx + fy * fy + fz * fz);
+  if (!(fl > 0.0)) return fail(NSL_ERR_INVALID_ARG, "%s: eye == target", fn);
+  double rx = fy * cam->up[2] - fz * cam->up[1], ry = fz * cam->up[0] - fx * cam->up[2],
+         rz = fx * cam->up[1] - fy * cam->up[0];
+  if (!(std::sqrt(rx * rx + ry * ry + rz * rz) > 1e-9 * fl))
+    return fail(NSL_ERR_INVALID_ARG, "%s: up is parallel to the view direction", fn);
+  if (cam->kind == NSL_CAM_PERSP && !(cam->fov_y_deg > 0.f && cam->fov_y_deg < 179.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: fov_y_deg out of (0, 179)", fn);
+  if (cam->kind == NSL_CAM_ORTHO && !(cam->ortho_height > 0.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: ortho_height must be > 0", fn);
+  return NSL_OK;
+}
+
+static uint32_t host_pcg(uint32_t v) {
+  uint32_t state = v * 747796405u + 2891336453u;
+  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+  return (word >> 22u) ^ word;
+}
+
+nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, void* stream) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: ctx is NULL");
+  if (!density) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: density is NULL");
+  if (!aligned16(density) || (mask && !aligned16(mask)))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: buffers must be 16-byte aligned");
+  cudaError_t e = launch_stage_volume(density, c->grid.dtype, mask, grid_voxels(c->grid),
+                                      c->grid.sigma_scale, c->staged,
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_stage_grid");
+  c->staged_valid = true;
+  return NSL_OK;
+}
+
+static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
+                              const nsl_march_opts* opts, const char* fn, MarchPlume* p) {
+  nsl_status st = check_camera(c, cam, fn);
+  if (st != NSL_OK) return st;
+  if (!(step > 0.f) || !std::isfinite(step))
+    return fail(NSL_ERR_INVALID_ARG, "%s: step must be > 0", fn);
+  nsl_march_opts o;
+  nsl_default_march_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.t_min >= 0.f && o.t_min < 1.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: t_min must be in [0, 1)", fn);
+  if (!(o.phase_g > -1.f && o.phase_g < 1.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: phase_g must be in (-1, 1)", fn);
+  *p = MarchPlume{};
+  p->vol = c->staged;
+  p->nx = c->grid.nx; p->ny = c->grid.ny; p->nz = c->grid.nz;
+  cam_frame_from(*cam, &p->cam);
+  p->h = step;
+  p->tau_depth = o.tau_depth;
+  p->t_min = o.t_min;
+  p->tau_lim = o.t_min > 0.f ? (float)(-std::log((double)o.t_min)) : INFINITY;
+  p->jitter = o.jitter ? 1 : 0;
+  p->key = host_pcg(o.frame + host_pcg(o.seed));
+  p->g = o.phase_g;
+  for (int k = 0; k < 3; ++k) p->I[k] = o.surrogate_I[k];
+  p->segment_exact = o.segment_exact ? 1 : 0;
+  p->tiles_x = (cam->width + kMarchTX - 1) / kMarchTX;
+  p->tile_start = 0;
+  return NSL_OK;
+}
+
+nsl_status nsl_guiding_map(nsl_ctx* c, const void* density, const uint8_t* mask,
+                           const nsl_camera* cam, const nsl_light* light, float step,
+                           const nsl_march_opts* opts, float* guide, void* stream) {
+  (void)light;  // the guide uses the surrogate lights of Eq. approx only
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: ctx is NULL");
+  MarchPlume p;
+  nsl_status st = march_setup(c, cam, step, opts, "nsl_guiding_map", &p);
+  if (st != NSL_OK) return st;
+  if (!guide) return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: guide is NULL");
+  if (!aligned16(guide))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: buffers must be 16-byte aligned");
+  if (density) {
+    st = nsl_stage_grid(c, density, mask, stream);
+    if (st != NSL_OK) return st;
+  } else if (!c->staged_valid) {
+    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: density is NULL and no grid is staged");
+  }
+  p.guide = guide;
+  cudaError_t e = launch_march(p, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map: march");
+  return NSL_OK;
+}
+
+nsl_status nsl_guide_sample_count(nsl_ctx* c, const nsl_camera* cam, float step,
+                                  const nsl_march_opts* opts, unsigned long long* out,
+                                  void* stream) {
+  if (!c || !out) return fail(NSL_ERR_INVALID_ARG, "nsl_guide_sample_count: NULL argument");
+  MarchPlume p;
+  nsl_status st = march_setup(c, cam, step, opts, "nsl_guide_sample_count", &p);
+  if (st != NSL_OK) return st;
+  if (!c->staged_valid) return fail(NSL_ERR_INVALID_ARG, "nsl_guide_sample_count: no grid staged");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!c->counter) NSL_CUDA_TRY(cudaMalloc(&c->counter, sizeof(unsigned long long)));
+  NSL_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
+  p.counter = c->counter;
+  NSL_CUDA_TRY(launch_march(p, s, true));
+  NSL_CUDA_TRY(cudaMemcpyAsync(out, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  NSL_CUDA_TRY(cudaStreamSynchronize(s));
+  return NSL_OK;
+}
+
+nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int height,
+                                 int precision, float* lm, void* stream) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: ctx is NULL");
+  if (!guide || !lm) return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: NULL buffer");
+  if (!aligned16(guide) || !aligned16(lm))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: buffers must be 16-byte aligned");
+  if (width < 8 || height < 8 || width % 8 || height % 8 || width > c->max_w || height > c->max_h)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: bad size %dx%d", width, height);
+  NetImage img{guide, lm, height, width,
+               (float)(1.0 / std::sqrt((double)c->grid.nx * c->grid.nx +
+                                       (double)c->grid.ny * c->grid.ny +
+                                       (double)c->grid.nz * c->grid.nz))};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (precision) {
+    case NSL_PREC_F32:
+      e = net_f32_forward(c->wf32, img, c->ws, c->ws_bytes, s);
+      break;
+    default:
+      return fail(NSL_ERR_UNSUPPORTED, "nsl_predict_lightmaps: precision %d not built", precision);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_predict_lightmaps");
+  return NSL_OK;
+}
+
+nsl_status nsl_shade(nsl_ctx* c, const float* lm, int width, int height, const nsl_camera* cam,
+                     const nsl_light* lights, int n_lights, float* rgba, void* stream) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_shade: ctx is NULL");
+  if (!lm || !rgba) return fail(NSL_ERR_INVALID_ARG, "nsl_shade: NULL buffer");
+  if (!aligned16(lm) || !aligned16(rgba))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_shade: buffers must be 16-byte aligned");
+  if (!cam) return fail(NSL_ERR_INVALID_ARG, "nsl_shade: camera is NULL");
+  if (width < 8 || height < 8 || width % 8 || height % 8)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_shade: bad size %dx%d", width, height);
+  if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !lights))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_shade: n_lights must be in [0, 64]");
+  nsl_camera cc = *cam;
+  cc.width = width;
+  cc.height = height;
+  CamFrame fr;
+  cam_frame_from(cc, &fr);
+  ShadeArgs a{};
+  a.lm = lm;
+  a.rgba = rgba;
+  a.W = width;
+  a.H = height;
+  double M[3][6] = {};
+  for (int l = 0; l < n_lights; ++l) {
+    double v[3] = {lights[l].dir[0], lights[l].dir[1], lights[l].dir[2]};
+    double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nv > 0.0) || !std::isfinite(nv))
+      return fail(NSL_ERR_INVALID_ARG, "nsl_shade: light %d has a zero direction", l);
+    double w[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      w[0] += v[k] / nv * fr.r[k];
+      w[1] += v[k] / nv * fr.u[k];
+      w[2] += v[k] / nv * fr.f[k];
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+      double I = lights[l].intensity[ch];
+      for (int p = 0; p < 3; ++p) {
+        if (w[p] >= 0.0) M[ch][2 * p] += I * w[p];
+        else M[ch][2 * p + 1] += I * -w[p];
+      }
+    }
+  }
+  for (int ch = 0; ch < 3; ++ch)
+    for (int q = 0; q < 6; ++q) a.M[ch][q] = (float)M[ch][q];
+  cudaError_t e = launch_shade(a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_shade");
+  return NSL_OK;
+}
+
+static cudaError_t ensure(void** p, size_t bytes) {
+  if (*p) return cudaSuccess;
+  return cudaMalloc(p, bytes);
+}
+
+nsl_status nsl_render_frame_host(nsl_ctx* c, const void* density_host, const uint8_t* mask_host,
+                                 const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                                 float step, const nsl_march_opts* opts, int precision,
+                                 float* guide_host, float* lm_host, float* rgba_host,
+                                 void* stream) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_render_frame_host: ctx is NULL");
+  if (!density_host) return fail(NSL_ERR_INVALID_ARG, "nsl_render_frame_host: NULL density");
+  nsl_status st = check_camera(c, cam, "nsl_render_frame_host");
+  if (st != NSL_OK) return st;
+  const size_t nvox = grid_voxels(c->grid);
+  const size_t dbytes = nvox * (c->grid.dtype == NSL_F16 ? 2 : 4);
+  const size_t P = (size_t)c->max_w * c->max_h;
+  NSL_CUDA_TRY(ensure(&c->h_density, dbytes));
+  NSL_CUDA_TRY(ensure(reinterpret_cast<void**>(&c->h_mask), nvox));
+  NSL_CUDA_TRY(ensure(reinterpret_cast<void**>(&c->h_guide), 3 * P * sizeof(float)));
+  NSL_CUDA_TRY(ensure(reinterpret_cast<void**>(&c->h_lm), 8 * P * sizeof(float)));
+  NSL_CUDA_TRY(ensure(reinterpret_cast<void**>(&c->h_rgba), 4 * P * sizeof(float)));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int W = cam->width, H = cam->height;
+  const size_t px = (size_t)W * H;
+  NSL_CUDA_TRY(cudaMemcpyAsync(c->h_density, density_host, dbytes, cudaMemcpyHostToDevice, s));
+  if (mask_host)
+    NSL_CUDA_TRY(cudaMemcpyAsync(c->h_mask, mask_host, nvox, cudaMemcpyHostToDevice, s));
+  st = nsl_guiding_map(c, c->h_density, mask_host ? c->h_mask : nullptr, cam, nullptr, step, opts,
+                       c->h_guide, stream);
+  if (st != NSL_OK) return st;
+  st = nsl_predict_lightmaps(c, c->h_guide, W, H, precision, c->h_lm, stream);
+  if (st != NSL_OK) return st;
+  st = nsl_shade(c, c->h_lm, W, H, cam, lights, n_lights, c->h_rgba, stream);
+  if (st != NSL_OK) return st;
+  if (guide_host)
+    NSL_CUDA_TRY(cudaMemcpyAsync(guide_host, c->h_guide, 3 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (lm_host)
+    NSL_CUDA_TRY(cudaMemcpyAsync(lm_host, c->h_lm, 8 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (rgba_host)
+    NSL_CUDA_TRY(cudaMemcpyAsync(rgba_host, c->h_rgba, 4 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
+  NSL_CUDA_TRY(cudaStreamSynchronize(s));
+  return NSL_OK;
+}
+
+}  // extern "C"

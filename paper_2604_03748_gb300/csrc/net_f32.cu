@@ -1,0 +1,550 @@
+// Lightmap network (Sec. 4.3, Fig. 3) in FP32 on the SIMT cores: the plain
+// FP32 path.  Activations are NHWC float32.  Convolutions stage a halo tile of
+// the input in shared memory and accumulate 16 output channels for two
+// pixels per thread; max-pooling, channel concatenation and the guide's depth
+// normalisation are fused into the input staging of the convolution that
+// consumes them.  The four NAFBlock adapters run as two passes around the
+// global average of their simplified channel attention.
+#include <vector>
+
+#include "nsl_internal.cuh"
+
+namespace nsl {
+
+enum InMode { IN_PLAIN = 0, IN_POOL = 1, IN_CONCAT = 2, IN_GUIDE = 3 };
+
+constexpr int kTW = 16, kTH = 16;               // output tile (pixels)
+constexpr int kHW = kTW + 2, kHH = kTH + 2;     // halo tile
+constexpr int kHaloPix = kHW * kHH;             // 324
+constexpr int kHaloStride = kHaloPix + 1;       // odd stride: conflict-free channel-major stores
+
+struct ConvArgs {
+  const float* inA;   // IN_PLAIN/IN_CONCAT/IN_POOL: NHWC; IN_GUIDE: planar [3][H][W]
+  const float* inB;   // IN_CONCAT second operand (skip), NHWC
+  const float* w;     // packed [cout/16][cin][9][16]
+  const float* b;     // [cout]
+  float* out;         // NHWC [H][W][cout]
+  int H, W;           // output (= conv) size
+  float depth_scale;
+};
+
+// Value of input channel c at conv-input pixel (y, x), already inside the image.
+template <int MODE, int CIN>
+__device__ __forceinline__ float load_in(const ConvArgs& a, int y, int x, int c) {
+  if constexpr (MODE == IN_PLAIN) {
+    return __ldg(a.inA + ((size_t)y * a.W + x) * CIN + c);
+  } else if constexpr (MODE == IN_POOL) {
+    const int W2 = 2 * a.W;
+    const float* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + c;
+    float m = fmaxf(__ldg(p), __ldg(p + CIN));
+    m = fmaxf(m, __ldg(p + (size_t)W2 * CIN));
+    return fmaxf(m, __ldg(p + (size_t)W2 * CIN + CIN));
+  } else if constexpr (MODE == IN_CONCAT) {
+    constexpr int CH = CIN / 2;
+    if (c < CH) return __ldg(a.inA + ((size_t)y * a.W + x) * CH + c);
+    return __ldg(a.inB + ((size_t)y * a.W + x) * CH + (c - CH));
+  } else {  // IN_GUIDE
+    float v = __ldg(a.inA + ((size_t)c * a.H + y) * a.W + x);
+    return c == 2 ? v * a.depth_scale : v;
+  }
+}
+
+template <int CIN, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) {
+  constexpr int CT = CIN < 16 ? CIN : 16;  // input-channel chunk
+  __shared__ float halo[CT * kHaloStride];
+  __shared__ __align__(16) float ws[CT * 9 * 16];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, cg = blockIdx.z;
+  const int tx = tid % kTW, ty = (tid / kTW) * 2;
+  float acc0[16], acc1[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) { acc0[o] = 0.f; acc1[o] = 0.f; }
+
+  for (int c0 = 0; c0 < CIN; c0 += CT) {
+    __syncthreads();
+    for (int e = tid; e < CT * kHaloPix; e += 128) {
+      int c = e % CT, hp = e / CT;
+      int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
+      float v = 0.f;
+      if (y >= 0 && y < a.H && x >= 0 && x < a.W) v = load_in<MODE, CIN>(a, y, x, c0 + c);
+      halo[c * kHaloStride + hp] = v;
+    }
+    const float* wsrc = a.w + ((size_t)cg * CIN + c0) * 9 * 16;
+    for (int e = tid; e < CT * 9 * 16; e += 128) ws[e] = __ldg(wsrc + e);
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < CT; ++c) {
+      const float* hc = halo + c * kHaloStride;
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          float v0 = hc[(ty + ky) * kHW + tx + kx];
+          float v1 = hc[(ty + 1 + ky) * kHW + tx + kx];
+          const float4* w4 = reinterpret_cast<const float4*>(ws + (c * 9 + ky * 3 + kx) * 16);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 w = w4[q];
+            acc0[4 * q + 0] = fmaf(v0, w.x, acc0[4 * q + 0]);
+            acc0[4 * q + 1] = fmaf(v0, w.y, acc0[4 * q + 1]);
+            acc0[4 * q + 2] = fmaf(v0, w.z, acc0[4 * q + 2]);
+            acc0[4 * q + 3] = fmaf(v0, w.w, acc0[4 * q + 3]);
+            acc1[4 * q + 0] = fmaf(v1, w.x, acc1[4 * q + 0]);
+            acc1[4 * q + 1] = fmaf(v1, w.y, acc1[4 * q + 1]);
+            acc1[4 * q + 2] = fmaf(v1, w.z, acc1[4 * q + 2]);
+            acc1[4 * q + 3] = fmaf(v1, w.w, acc1[4 * q + 3]);
+          }
+        }
+    }
+  }
+  const int x = x0 + tx;
+  if (x >= a.W) return;
+  const float* bias = a.b + cg * 16;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    int y = y0 + ty + r;
+    if (y >= a.H) continue;
+    float* dst = a.out + ((size_t)y * a.W + x) * cout + cg * 16;
+    const float* acc = r ? acc1 : acc0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 v;
+      v.x = fmaxf(acc[4 * q + 0] + __ldg(bias + 4 * q + 0), 0.f);
+      v.y = fmaxf(acc[4 * q + 1] + __ldg(bias + 4 * q + 1), 0.f);
+      v.z = fmaxf(acc[4 * q + 2] + __ldg(bias + 4 * q + 2), 0.f);
+      v.w = fmaxf(acc[4 * q + 3] + __ldg(bias + 4 * q + 3), 0.f);
+      reinterpret_cast<float4*>(dst)[q] = v;
+    }
+  }
+}
+
+// 2x2 stride-2 transposed convolution: one thread per input pixel, 16 output
+// channels of all four output pixels it feeds.  Weights packed [cout/16][cin][4][16].
+template <int CIN>
+__global__ void __launch_bounds__(128) convT_f32_kernel(const float* __restrict__ in,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ b,
+                                                        float* __restrict__ out, int H, int W,
+                                                        int cout) {
+  extern __shared__ __align__(16) float wsm[];  // CIN * 64
+  const int cg = blockIdx.y;
+  const float* wsrc = w + (size_t)cg * CIN * 64;
+  for (int e = threadIdx.x; e < CIN * 64; e += 128) wsm[e] = __ldg(wsrc + e);
+  __syncthreads();
+  const int p = blockIdx.x * 128 + threadIdx.x;
+  if (p >= H * W) return;
+  const int y = p / W, x = p % W;
+  float acc[4][16];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[k][o] = 0.f;
+  const float4* src = reinterpret_cast<const float4*>(in + (size_t)p * CIN);
+#pragma unroll 1
+  for (int c4 = 0; c4 < CIN / 4; ++c4) {
+    float4 v4 = __ldg(src + c4);
+    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float4* wr = reinterpret_cast<const float4*>(wsm + (c4 * 4 + cc) * 64);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float4 ww = wr[k * 4 + q];
+          acc[k][4 * q + 0] = fmaf(vv[cc], ww.x, acc[k][4 * q + 0]);
+          acc[k][4 * q + 1] = fmaf(vv[cc], ww.y, acc[k][4 * q + 1]);
+          acc[k][4 * q + 2] = fmaf(vv[cc], ww.z, acc[k][4 * q + 2]);
+          acc[k][4 * q + 3] = fmaf(vv[cc], ww.w, acc[k][4 * q + 3]);
+        }
+    }
+  }
+  const int W2 = 2 * W;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
+    float4* dst = reinterpret_cast<float4*>(out + ((size_t)oy * W2 + ox) * cout + cg * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 v;
+      v.x = acc[k][4 * q + 0] + __ldg(b + cg * 16 + 4 * q + 0);
+      v.y = acc[k][4 * q + 1] + __ldg(b + cg * 16 + 4 * q + 1);
+      v.z = acc[k][4 * q + 2] + __ldg(b + cg * 16 + 4 * q + 2);
+      v.w = acc[k][4 * q + 3] + __ldg(b + cg * 16 + 4 * q + 3);
+      dst[q] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NAFBlock adapters (C0 = 16), four at once
+// ---------------------------------------------------------------------------
+// Offsets inside one adapter's kAdapterParams floats (blob order).
+struct AdOff {
+  static constexpr int C = kC0;
+  static constexpr int ln1w = 0, ln1b = C;
+  static constexpr int pw1w = 2 * C, pw1b = pw1w + 2 * C * C;
+  static constexpr int dww = pw1b + 2 * C, dwb = dww + 18 * C;
+  static constexpr int scaw = dwb + 2 * C, scab = scaw + C * C;
+  static constexpr int pw2w = scab + C, pw2b = pw2w + C * C;
+  static constexpr int beta = pw2b + C;
+  static constexpr int ln2w = beta + C, ln2b = ln2w + C;
+  static constexpr int f1w = ln2b + C, f1b = f1w + 2 * C * C;
+  static constexpr int f2w = f1b + 2 * C, f2b = f2w + C * C;
+  static constexpr int gamma = f2b + C;
+  static constexpr int headw = gamma + C, headb = headw + 2 * C;
+  static constexpr int total = headb + 2;
+};
+static_assert(AdOff::total == kAdapterParams, "adapter layout");
+
+constexpr int kAdTW = 16, kAdTH = 8;                 // adapter tile
+constexpr int kAdHW = kAdTW + 2, kAdHH = kAdTH + 2;  // halo 18 x 10
+constexpr int kAdHalo = kAdHW * kAdHH;               // 180
+constexpr int kAdHaloS = kAdHalo + 1;
+
+__device__ __forceinline__ void layer_norm16(const float* x, const float* w, const float* b,
+                                             float* y) {
+  float mu = 0.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) mu += x[c];
+  mu *= (1.f / 16.f);
+  float var = 0.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float d = x[c] - mu;
+    var = fmaf(d, d, var);
+  }
+  var *= (1.f / 16.f);
+  float inv = 1.f / sqrtf(var + 1e-6f);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) y[c] = fmaf((x[c] - mu) * inv, w[c], b[c]);
+}
+
+// Pass 1: x1_a = SG(dw3x3(pw1(LN1(F)))) for the four adapters a; writes x1 (NHWC,
+// 64 channels) and this tile's per-channel sums (deterministic tree order).
+__global__ void __launch_bounds__(128) adapter_pass1_f32(const float* __restrict__ F,
+                                                         const float* __restrict__ params,
+                                                         float* __restrict__ x1,
+                                                         float* __restrict__ partial, int H,
+                                                         int W) {
+  __shared__ float fh[kAdHalo * 16];
+  __shared__ float t[32 * kAdHaloS];
+  __shared__ float prm[AdOff::scaw];
+  __shared__ float red[4][16];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kAdTW, y0 = blockIdx.y * kAdTH;
+  const int tileid = blockIdx.y * gridDim.x + blockIdx.x;
+  for (int e = tid; e < kAdHalo * 16; e += 128) {
+    int hp = e / 16, c = e % 16;
+    int y = y0 + hp / kAdHW - 1, x = x0 + hp % kAdHW - 1;
+    fh[e] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(F + ((size_t)y * W + x) * 16 + c) : 0.f;
+  }
+  const int tx = tid % kAdTW, ty = tid / kAdTW;
+  const int px = x0 + tx, py = y0 + ty;
+  const bool valid = px < W && py < H;
+  for (int a = 0; a < 4; ++a) {
+    __syncthreads();
+    const float* ap = params + (size_t)a * kAdapterParams;
+    for (int e = tid; e < AdOff::scaw; e += 128) prm[e] = __ldg(ap + e);
+    __syncthreads();
+    for (int hp = tid; hp < kAdHalo; hp += 128) {
+      int y = y0 + hp / kAdHW - 1, x = x0 + hp % kAdHW - 1;
+      if (y >= 0 && y < H && x >= 0 && x < W) {
+        float n[16];
+        layer_norm16(fh + hp * 16, prm + AdOff::ln1w, prm + AdOff::ln1b, n);
+        for (int o = 0; o < 32; ++o) {
+          float s = prm[AdOff::pw1b + o];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) s = fmaf(prm[AdOff::pw1w + o * 16 + c], n[c], s);
+          t[o * kAdHaloS + hp] = s;
+        }
+      } else {
+        for (int o = 0; o < 32; ++o) t[o * kAdHaloS + hp] = 0.f;  // zero padding of dw input
+      }
+    }
+    __syncthreads();
+    float g[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float d0 = prm[AdOff::dwb + c], d1 = prm[AdOff::dwb + c + 16];
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          int hp = (ty + ky) * kAdHW + tx + kx;
+          d0 = fmaf(prm[AdOff::dww + c * 9 + ky * 3 + kx], t[c * kAdHaloS + hp], d0);
+          d1 = fmaf(prm[AdOff::dww + (c + 16) * 9 + ky * 3 + kx], t[(c + 16) * kAdHaloS + hp], d1);
+        }
+      g[c] = valid ? d0 * d1 : 0.f;
+    }
+    if (valid) {
+      float4* dst = reinterpret_cast<float4*>(x1 + ((size_t)py * W + px) * 64 + a * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+    }
+    // per-channel tile sums: butterfly within each warp, then warps in order
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float v = g[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      g[c] = v;
+    }
+    if ((tid & 31) == 0) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) red[tid >> 5][c] = g[c];
+    }
+    __syncthreads();
+    if (tid < 16) {
+      float s = ((red[0][tid] + red[1][tid]) + red[2][tid]) + red[3][tid];
+      partial[(size_t)tileid * 64 + a * 16 + tid] = s;
+    }
+  }
+}
+
+// Reduce the tile sums in a fixed order, then the attention vector
+// att[a][co] = b_sca + W_sca mean_HW(x1_a).
+__global__ void __launch_bounds__(64) adapter_reduce(const float* __restrict__ partial, int ntiles,
+                                                     float inv_count,
+                                                     const float* __restrict__ params,
+                                                     float* __restrict__ att) {
+  __shared__ float mean[64];
+  const int ch = threadIdx.x;
+  float s = 0.f, comp = 0.f;
+  for (int t = 0; t < ntiles; ++t) {
+    float y = partial[(size_t)t * 64 + ch] - comp;
+    float u = s + y;
+    comp = (u - s) - y;
+    s = u;
+  }
+  mean[ch] = s * inv_count;
+  __syncthreads();
+  const int a = ch / 16, co = ch % 16;
+  const float* ap = params + (size_t)a * kAdapterParams;
+  float v = ap[AdOff::scab + co];
+  for (int ci = 0; ci < 16; ++ci) v = fmaf(ap[AdOff::scaw + co * 16 + ci], mean[a * 16 + ci], v);
+  att[ch] = v;
+}
+
+// Pass 2: per pixel, the rest of each NAFBlock and its 1x1 head -> 8 planes.
+__global__ void __launch_bounds__(128) adapter_pass2_f32(const float* __restrict__ F,
+                                                         const float* __restrict__ x1,
+                                                         const float* __restrict__ att,
+                                                         const float* __restrict__ params,
+                                                         float* __restrict__ out, int npix) {
+  __shared__ float prm[4 * kAdapterParams];
+  __shared__ float at[64];
+  for (int e = threadIdx.x; e < 4 * kAdapterParams; e += 128) prm[e] = __ldg(params + e);
+  if (threadIdx.x < 64) at[threadIdx.x] = att[threadIdx.x];
+  __syncthreads();
+  const int p = blockIdx.x * 128 + threadIdx.x;
+  if (p >= npix) return;
+  float f[16];
+  const float4* fs = reinterpret_cast<const float4*>(F + (size_t)p * 16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float4 v = __ldg(fs + q);
+    f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
+  }
+  const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
+#pragma unroll 1
+  for (int a = 0; a < 4; ++a) {
+    const float* pp = prm + a * kAdapterParams;
+    float xa[16], y[16], n[16], gsg[16];
+    const float4* xs = reinterpret_cast<const float4*>(x1 + (size_t)p * 64 + a * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 v = __ldg(xs + q);
+      xa[4 * q] = v.x * at[a * 16 + 4 * q]; xa[4 * q + 1] = v.y * at[a * 16 + 4 * q + 1];
+      xa[4 * q + 2] = v.z * at[a * 16 + 4 * q + 2]; xa[4 * q + 3] = v.w * at[a * 16 + 4 * q + 3];
+    }
+#pragma unroll
+    for (int co = 0; co < 16; ++co) {
+      float s = pp[AdOff::pw2b + co];
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) s = fmaf(pp[AdOff::pw2w + co * 16 + ci], xa[ci], s);
+      y[co] = fmaf(pp[AdOff::beta + co], s, f[co]);
+    }
+    layer_norm16(y, pp + AdOff::ln2w, pp + AdOff::ln2b, n);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float s0 = pp[AdOff::f1b + c], s1 = pp[AdOff::f1b + c + 16];
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) {
+        s0 = fmaf(pp[AdOff::f1w + c * 16 + ci], n[ci], s0);
+        s1 = fmaf(pp[AdOff::f1w + (c + 16) * 16 + ci], n[ci], s1);
+      }
+      gsg[c] = s0 * s1;
+    }
+    float h0 = pp[AdOff::headb], h1 = pp[AdOff::headb + 1];
+#pragma unroll
+    for (int co = 0; co < 16; ++co) {
+      float s = pp[AdOff::f2b + co];
+#pragma unroll
+      for (int ci = 0; ci < 16; ++ci) s = fmaf(pp[AdOff::f2w + co * 16 + ci], gsg[ci], s);
+      float z = fmaf(pp[AdOff::gamma + co], s, y[co]);
+      h0 = fmaf(pp[AdOff::headw + co], z, h0);
+      h1 = fmaf(pp[AdOff::headw + 16 + co], z, h1);
+    }
+    out[(size_t)plane_of[a][0] * npix + p] = h0;
+    out[(size_t)plane_of[a][1] * npix + p] = h1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// weights and forward
+// ---------------------------------------------------------------------------
+struct NetF32Weights {
+  float* conv_w[14];   // packed [cout/16][cin][9][16]
+  float* conv_b[14];
+  float* up_w[3];      // packed [cout/16][cin][4][16]
+  float* up_b[3];
+  float* adapters;     // 4 * kAdapterParams, blob order
+  int conv_cin[14], conv_cout[14], up_cin[3], up_cout[3];
+  std::vector<void*> allocs;
+};
+
+static float* upload(NetF32Weights* w, const std::vector<float>& v, cudaError_t* err) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, v.size() * sizeof(float));
+  if (e != cudaSuccess) { *err = e; return nullptr; }
+  w->allocs.push_back(p);
+  e = cudaMemcpy(p, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) *err = e;
+  return static_cast<float*>(p);
+}
+
+NetF32Weights* net_f32_create(const float* hp, const NetLayout& L, cudaError_t* err) {
+  *err = cudaSuccess;
+  NetF32Weights* w = new NetF32Weights();
+  for (int l = 0; l < 14; ++l) {
+    int cin = L.conv_cin[l], cout = L.conv_cout[l];
+    w->conv_cin[l] = cin; w->conv_cout[l] = cout;
+    std::vector<float> pk((size_t)cout * cin * 9);
+    const float* src = hp + L.conv_w[l];  // [cout][cin][3][3]
+    for (int co = 0; co < cout; ++co)
+      for (int ci = 0; ci < cin; ++ci)
+        for (int k = 0; k < 9; ++k)
+          pk[(((size_t)(co / 16) * cin + ci) * 9 + k) * 16 + co % 16] = src[((size_t)co * cin + ci) * 9 + k];
+    w->conv_w[l] = upload(w, pk, err);
+    w->conv_b[l] = upload(w, std::vector<float>(hp + L.conv_b[l], hp + L.conv_b[l] + cout), err);
+  }
+  for (int l = 0; l < 3; ++l) {
+    int cin = L.up_cin[l], cout = L.up_cout[l];
+    w->up_cin[l] = cin; w->up_cout[l] = cout;
+    std::vector<float> pk((size_t)cout * cin * 4);
+    const float* src = hp + L.up_w[l];  // [cin][cout][2][2]
+    for (int ci = 0; ci < cin; ++ci)
+      for (int co = 0; co < cout; ++co)
+        for (int k = 0; k < 4; ++k)
+          pk[(((size_t)(co / 16) * cin + ci) * 4 + k) * 16 + co % 16] = src[((size_t)ci * cout + co) * 4 + k];
+    w->up_w[l] = upload(w, pk, err);
+    w->up_b[l] = upload(w, std::vector<float>(hp + L.up_b[l], hp + L.up_b[l] + cout), err);
+  }
+  w->adapters = upload(w, std::vector<float>(hp + L.adapter[0], hp + L.adapter[0] + 4 * kAdapterParams), err);
+  if (*err != cudaSuccess) { net_f32_destroy(w); return nullptr; }
+  return w;
+}
+
+void net_f32_destroy(NetF32Weights* w) {
+  if (!w) return;
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+}
+
+// workspace carve-up (floats), P = max pixels
+struct F32Buffers {
+  float *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1, *partial, *att;
+};
+
+static size_t carve(size_t P, F32Buffers* b, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t nfloats) {
+    float* p = base ? reinterpret_cast<float*>(base + off) : nullptr;
+    off += ((nfloats * sizeof(float) + 255) / 256) * 256;
+    return p;
+  };
+  b->fa = take(P * 16); b->fb = take(P * 16); b->s1 = take(P * 16);
+  b->l1a = take(P / 4 * 32); b->l1b = take(P / 4 * 32); b->s2 = take(P / 4 * 32);
+  b->l2a = take(P / 16 * 64); b->l2b = take(P / 16 * 64); b->s3 = take(P / 16 * 64);
+  b->l3a = take(P / 64 * 128); b->l3b = take(P / 64 * 128);
+  b->x1 = take(P * 64);
+  b->partial = take((P / (kAdTW * kAdTH) + 1024) * 64);
+  b->att = take(64);
+  return off;
+}
+
+size_t net_f32_workspace_bytes(int max_w, int max_h) {
+  F32Buffers b;
+  return carve((size_t)max_w * max_h, &b, nullptr);
+}
+
+template <int CIN, int MODE>
+static cudaError_t conv(const ConvArgs& a, int cout, cudaStream_t s) {
+  dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH, cout / 16);
+  conv3x3_f32_kernel<CIN, MODE><<<grid, 128, 0, s>>>(a, cout);
+  return cudaGetLastError();
+}
+
+template <int CIN>
+static cudaError_t convT(const float* in, const float* w, const float* b, float* out, int H, int W,
+                         int cout, cudaStream_t s) {
+  dim3 grid((H * W + 127) / 128, cout / 16);
+  size_t smem = (size_t)CIN * 64 * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(convT_f32_kernel<CIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  convT_f32_kernel<CIN><<<grid, 128, smem, s>>>(in, w, b, out, H, W, cout);
+  return cudaGetLastError();
+}
+
+cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* workspace,
+                            size_t ws_bytes, cudaStream_t s) {
+  const int H = img.H, W = img.W;
+  const size_t P = (size_t)H * W;
+  F32Buffers B;
+  if (carve(P, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
+  carve(P, &B, static_cast<char*>(workspace));
+  cudaError_t e;
+#define TRY(x) if ((e = (x)) != cudaSuccess) return e
+  auto A = [&](const float* inA, const float* inB, int l, float* out, int h, int ww) {
+    ConvArgs a{inA, inB, w->conv_w[l], w->conv_b[l], out, h, ww, img.depth_scale};
+    return a;
+  };
+  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  // encoder
+  TRY((conv<3, IN_GUIDE>(A(img.guide, nullptr, 0, B.fa, H, W), 16, s)));
+  TRY((conv<16, IN_PLAIN>(A(B.fa, nullptr, 1, B.s1, H, W), 16, s)));
+  TRY((conv<16, IN_POOL>(A(B.s1, nullptr, 2, B.l1a, H1, W1), 32, s)));
+  TRY((conv<32, IN_PLAIN>(A(B.l1a, nullptr, 3, B.s2, H1, W1), 32, s)));
+  TRY((conv<32, IN_POOL>(A(B.s2, nullptr, 4, B.l2a, H2, W2), 64, s)));
+  TRY((conv<64, IN_PLAIN>(A(B.l2a, nullptr, 5, B.s3, H2, W2), 64, s)));
+  TRY((conv<64, IN_POOL>(A(B.s3, nullptr, 6, B.l3a, H3, W3), 128, s)));
+  TRY((conv<128, IN_PLAIN>(A(B.l3a, nullptr, 7, B.l3b, H3, W3), 128, s)));
+  // decoder
+  TRY(convT<128>(B.l3b, w->up_w[0], w->up_b[0], B.l2a, H3, W3, 64, s));
+  TRY((conv<128, IN_CONCAT>(A(B.l2a, B.s3, 8, B.l2b, H2, W2), 64, s)));
+  TRY((conv<64, IN_PLAIN>(A(B.l2b, nullptr, 9, B.l2a, H2, W2), 64, s)));
+  TRY(convT<64>(B.l2a, w->up_w[1], w->up_b[1], B.l1a, H2, W2, 32, s));
+  TRY((conv<64, IN_CONCAT>(A(B.l1a, B.s2, 10, B.l1b, H1, W1), 32, s)));
+  TRY((conv<32, IN_PLAIN>(A(B.l1b, nullptr, 11, B.l1a, H1, W1), 32, s)));
+  TRY(convT<32>(B.l1a, w->up_w[2], w->up_b[2], B.fa, H1, W1, 16, s));
+  TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s)));
+  TRY((conv<16, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), 16, s)));
+  // adapters
+  dim3 ag((W + kAdTW - 1) / kAdTW, (H + kAdTH - 1) / kAdTH);
+  adapter_pass1_f32<<<ag, 128, 0, s>>>(B.fa, w->adapters, B.x1, B.partial, H, W);
+  TRY(cudaGetLastError());
+  adapter_reduce<<<1, 64, 0, s>>>(B.partial, ag.x * ag.y, 1.f / (float)P, w->adapters, B.att);
+  TRY(cudaGetLastError());
+  adapter_pass2_f32<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(B.fa, B.x1, B.att, w->adapters,
+                                                               img.out, (int)P);
+  TRY(cudaGetLastError());
+#undef TRY
+  return cudaSuccess;
+}
+
+}  // namespace nsl

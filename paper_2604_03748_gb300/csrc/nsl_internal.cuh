@@ -1,0 +1,118 @@
+// Internal declarations of libnsl (GB300 / sm_103a).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/nsl.h"
+
+namespace nsl {
+
+constexpr int kNumSMs = 152;
+
+// Error recording (thread-local message, see nsl_last_error).
+void set_error(const char* fmt, ...);
+nsl_status fail(nsl_status s, const char* fmt, ...);
+nsl_status cuda_fail(cudaError_t e, const char* where);
+
+#define NSL_CUDA_TRY(expr)                                     \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return ::nsl::cuda_fail(_e, #expr); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// camera frame (binary32), computed on the host in binary64 and rounded once
+// ---------------------------------------------------------------------------
+struct CamFrame {
+  float eye[3], r[3], u[3], f[3];
+  float ax, ay;  // screen extents (ortho: height*W/H, height; persp: 2tan(fov/2)*W/H, 2tan(fov/2))
+  int kind, W, H;
+};
+void cam_frame_from(const nsl_camera& c, CamFrame* out);
+
+// ---------------------------------------------------------------------------
+// guide march
+// ---------------------------------------------------------------------------
+struct MarchPlume {
+  const float* vol;   // staged extinction sigma' = scale*rho*[mask==0], [nz][ny][nx] fp32
+  int nx, ny, nz;
+  CamFrame cam;
+  float h;            // step in voxels
+  float tau_depth;
+  float t_min;        // view-ray early termination (0 = off)
+  float tau_lim;      // shadow-ray termination threshold on the optical depth (-ln t_min)
+  int jitter;
+  uint32_t key;       // pcg(frame + pcg(seed))
+  float g;            // HG parameter of the surrogate lights
+  float I[3];         // front, top, bottom intensities
+  int segment_exact;
+  float* guide;       // [3][H][W]
+  int tiles_x;        // tiles per row
+  int tile_start;     // first tile index of this plume in a batch
+  unsigned long long* counter;  // density-evaluation counter (counting variant only)
+};
+
+constexpr int kMarchTX = 8;   // march tile: 8 x 8 pixels per 64-thread block
+constexpr int kMarchTY = 8;
+
+cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, size_t nvox,
+                                float scale, float* staged, cudaStream_t s);
+cudaError_t launch_march(const MarchPlume& p, cudaStream_t s, bool count = false);
+cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// six-way shading
+// ---------------------------------------------------------------------------
+struct ShadeArgs {
+  const float* lm;   // [8][H][W]
+  float* rgba;       // [4][H][W]
+  int W, H;
+  float M[3][6];     // per colour channel: sum_l I_l,c * weight of plane q
+};
+cudaError_t launch_shade(const ShadeArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// network
+// ---------------------------------------------------------------------------
+constexpr int kC0 = 16;
+constexpr int kAdapterParams = 2 * kC0 + (2 * kC0 * kC0 + 2 * kC0) + (18 * kC0 + 2 * kC0) +
+                               (kC0 * kC0 + kC0) + (kC0 * kC0 + kC0) + kC0 + 2 * kC0 +
+                               (2 * kC0 * kC0 + 2 * kC0) + (kC0 * kC0 + kC0) + kC0 + 2 * kC0 + 2;
+
+// offsets (in floats) of every parameter tensor inside the flat NSLW payload
+struct NetLayout {
+  size_t conv_w[14], conv_b[14];   // enc1a..enc4b (8), dec3a,dec3b,dec2a,dec2b,dec1a,dec1b (6)
+  int conv_cin[14], conv_cout[14];
+  size_t up_w[3], up_b[3];         // up3, up2, up1
+  int up_cin[3], up_cout[3];
+  size_t adapter[4];               // start of each adapter's parameters (incl. head)
+  size_t total;
+};
+bool build_net_layout(int c0, NetLayout* L);
+
+// device-side parameter sets of one adapter (offsets into a packed float array)
+struct AdapterDev {
+  const float* p;  // kAdapterParams floats in blob order
+};
+
+struct NetWorkspace;  // defined in net_*.cu
+
+struct NetImage {     // one image of a (possibly batched) network call
+  const float* guide; // [3][H][W]
+  float* out;         // [8][H][W]
+  int H, W;
+  float depth_scale;
+};
+
+struct NetF32Weights;  // opaque
+NetF32Weights* net_f32_create(const float* host_params, const NetLayout& L, cudaError_t* err);
+void net_f32_destroy(NetF32Weights* w);
+size_t net_f32_workspace_bytes(int max_w, int max_h);
+cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* workspace,
+                            size_t ws_bytes, cudaStream_t s);
+
+}  // namespace nsl

@@ -223,7 +223,8 @@ def param_spec(c0: int) -> list[tuple[str, tuple, str]]:
 
     Conv weights are [Cout][Cin][kh][kw]; transposed-conv weights are
     [Cin][Cout][2][2]; 1x1 convs are [Cout][Cin].  init is one of
-    'he:<fan_in>', 'bias', 'ln_w', 'ln_b', 'scale'.
+    'he:<fan_in>' (a ReLU follows: gain sqrt 2), 'lin:<fan_in>' (no ReLU
+    follows: gain 1), 'bias', 'ln_w', 'ln_b', 'scale'.
     """
     c = [c0, 2 * c0, 4 * c0, 8 * c0]
     spec: list[tuple[str, tuple, str]] = []
@@ -233,11 +234,11 @@ def param_spec(c0: int) -> list[tuple[str, tuple, str]]:
         spec.append((name + ".b", (cout,), "bias"))
 
     def convt(name, cin, cout):
-        spec.append((name + ".w", (cin, cout, 2, 2), f"he:{cin}"))
+        spec.append((name + ".w", (cin, cout, 2, 2), f"lin:{cin}"))
         spec.append((name + ".b", (cout,), "bias"))
 
     def pw(name, cin, cout):
-        spec.append((name + ".w", (cout, cin), f"he:{cin}"))
+        spec.append((name + ".w", (cout, cin), f"lin:{cin}"))
         spec.append((name + ".b", (cout,), "bias"))
 
     conv3("enc1a", 3, c[0]); conv3("enc1b", c[0], c[0])
@@ -251,7 +252,7 @@ def param_spec(c0: int) -> list[tuple[str, tuple, str]]:
         p = "ad" + a
         spec.append((p + ".ln1.w", (c0,), "ln_w")); spec.append((p + ".ln1.b", (c0,), "ln_b"))
         pw(p + ".pw1", c0, 2 * c0)
-        spec.append((p + ".dw.w", (2 * c0, 1, 3, 3), "he:9")); spec.append((p + ".dw.b", (2 * c0,), "bias"))
+        spec.append((p + ".dw.w", (2 * c0, 1, 3, 3), "lin:9")); spec.append((p + ".dw.b", (2 * c0,), "bias"))
         pw(p + ".sca", c0, c0)
         pw(p + ".pw2", c0, c0)
         spec.append((p + ".beta", (c0,), "scale"))
@@ -264,7 +265,9 @@ def param_spec(c0: int) -> list[tuple[str, tuple, str]]:
 
 
 def make_params(c0: int = 16, seed: int = 0, zero_residual_scales: bool = False) -> list[tuple[str, np.ndarray]]:
-    """He-normal conv weights N(0, 2/fan_in); biases ~U(-0.1,0.1); NAFBlock beta,
+    """Kaiming-normal weights with the gain of the layer's nonlinearity: N(0, 2/fan_in)
+    where a ReLU follows (the UNet 3x3 convs), N(0, 1/fan_in) where none does
+    (transposed convs, adapter convs, heads); biases ~U(-0.1,0.1); NAFBlock beta,
     gamma ~U(0.5,1.5) (zero if zero_residual_scales); LayerNorm weight ~U(0.8,1.2),
     bias ~U(-0.1,0.1).  Values are float32."""
     rng = np.random.default_rng(seed)
@@ -273,6 +276,9 @@ def make_params(c0: int = 16, seed: int = 0, zero_residual_scales: bool = False)
         if init.startswith("he:"):
             fan_in = int(init[3:])
             v = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=shape)
+        elif init.startswith("lin:"):
+            fan_in = int(init[4:])
+            v = rng.normal(0.0, math.sqrt(1.0 / fan_in), size=shape)
         elif init == "bias":
             v = rng.uniform(-0.1, 0.1, size=shape)
         elif init == "ln_w":

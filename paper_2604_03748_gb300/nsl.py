@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libnsl.so (the C ABI declared in include/nsl.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device
+memory and streams).  The library must have been built (``build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnsl.so")
+
+NSL_OK, NSL_ERR_INVALID_ARG, NSL_ERR_OOM, NSL_ERR_CUDA, NSL_ERR_UNSUPPORTED, NSL_ERR_TIMEOUT, NSL_ERR_BUDGET = range(7)
+NSL_F32, NSL_F16 = 0, 1
+NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8 = 0, 1, 2
+NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
+
+# every symbol include/nsl.h declares
+EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_grid",
+           "nsl_guiding_map", "nsl_guide_sample_count",
+           "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host", "nsl_last_error",
+           "nsl_status_str"]
+
+
+class nsl_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dtype", C.c_int),
+                ("sigma_scale", C.c_float)]
+
+
+class nsl_camera(C.Structure):
+    _fields_ = [("kind", C.c_int), ("eye", C.c_float * 3), ("target", C.c_float * 3),
+                ("up", C.c_float * 3), ("fov_y_deg", C.c_float), ("ortho_height", C.c_float),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class nsl_light(C.Structure):
+    _fields_ = [("dir", C.c_float * 3), ("intensity", C.c_float * 3)]
+
+
+class nsl_march_opts(C.Structure):
+    _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
+                ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
+                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int)]
+
+
+class NslError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} [status {status}]")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libnsl.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is not built; run paper_2604_03748_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i, f = C.c_void_p, C.c_int, C.c_float
+    lib.nsl_default_march_opts.argtypes = [C.POINTER(nsl_march_opts)]
+    lib.nsl_default_march_opts.restype = None
+    lib.nsl_create.argtypes = [C.POINTER(nsl_grid_desc), vp, C.c_size_t, i, i, C.POINTER(vp)]
+    lib.nsl_destroy.argtypes = [vp]
+    lib.nsl_destroy.restype = None
+    lib.nsl_guiding_map.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light), f,
+                                    C.POINTER(nsl_march_opts), vp, vp]
+    lib.nsl_stage_grid.argtypes = [vp, vp, vp, vp]
+    lib.nsl_guide_sample_count.argtypes = [vp, C.POINTER(nsl_camera), f, C.POINTER(nsl_march_opts),
+                                           C.POINTER(C.c_ulonglong), vp]
+    lib.nsl_predict_lightmaps.argtypes = [vp, vp, i, i, i, vp, vp]
+    lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
+    lib.nsl_render_frame_host.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light),
+                                          i, f, C.POINTER(nsl_march_opts), i, vp, vp, vp, vp]
+    lib.nsl_last_error.argtypes = []
+    lib.nsl_last_error.restype = C.c_char_p
+    lib.nsl_status_str.argtypes = [i]
+    lib.nsl_status_str.restype = C.c_char_p
+    for name in ("nsl_create", "nsl_stage_grid", "nsl_guiding_map", "nsl_guide_sample_count",
+                 "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def check(status: int, what: str = "nsl"):
+    if status != NSL_OK:
+        msg = load().nsl_last_error().decode(errors="replace")
+        raise NslError(status, f"{what}: {msg}")
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+
+def camera(cam) -> nsl_camera:
+    c = nsl_camera()
+    c.kind = int(cam.kind)
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.target[:] = [float(v) for v in cam.target]
+    c.up[:] = [float(v) for v in cam.up]
+    c.fov_y_deg = float(cam.fov_y_deg)
+    c.ortho_height = float(cam.ortho_height)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+def lights(ls):
+    arr = (nsl_light * max(1, len(ls)))()
+    for k, li in enumerate(ls):
+        arr[k].dir[:] = [float(v) for v in li.dir]
+        arr[k].intensity[:] = [float(v) for v in li.intensity]
+    return arr
+
+
+def march_opts(**kw) -> nsl_march_opts:
+    o = nsl_march_opts()
+    load().nsl_default_march_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "surrogate_I":
+            o.surrogate_I[:] = [float(x) for x in v]
+        elif k in ("seed", "frame"):
+            setattr(o, k, int(v) & 0xFFFFFFFF)
+        else:
+            setattr(o, k, type(getattr(o, k))(v))
+    return o
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# the C ABI, same names
+# --------------------------------------------------------------------------
+
+def nsl_create(nx, ny, nz, dtype, sigma_scale, blob: bytes, max_width, max_height):
+    lib = load()
+    g = nsl_grid_desc(nx, ny, nz, dtype, sigma_scale)
+    out = C.c_void_p()
+    buf = C.create_string_buffer(blob, len(blob))
+    check(lib.nsl_create(C.byref(g), buf, len(blob), max_width, max_height, C.byref(out)), "nsl_create")
+    return out
+
+
+def nsl_destroy(ctx):
+    load().nsl_destroy(ctx)
+
+
+def nsl_stage_grid(ctx, density, mask, stream=None):
+    check(load().nsl_stage_grid(ctx, _dptr(density), _dptr(mask), _stream(stream)), "nsl_stage_grid")
+
+
+def nsl_guide_sample_count(ctx, cam, step, opts=None, stream=None) -> int:
+    out = C.c_ulonglong(0)
+    check(load().nsl_guide_sample_count(ctx, C.byref(camera(cam)), float(step),
+                                        C.byref(opts) if opts is not None else None, C.byref(out),
+                                        _stream(stream)), "nsl_guide_sample_count")
+    return int(out.value)
+
+
+def nsl_guiding_map(ctx, density, mask, cam, step, guide, light=None, opts=None, stream=None):
+    lib = load()
+    li = lights([light])[0] if light is not None else None
+    check(lib.nsl_guiding_map(ctx, _dptr(density), _dptr(mask), C.byref(camera(cam)),
+                              C.byref(li) if li is not None else None, float(step),
+                              C.byref(opts) if opts is not None else None, _dptr(guide),
+                              _stream(stream)), "nsl_guiding_map")
+
+
+def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, stream=None):
+    check(load().nsl_predict_lightmaps(ctx, _dptr(guide), int(width), int(height), int(precision),
+                                       _dptr(lightmaps), _stream(stream)), "nsl_predict_lightmaps")
+
+
+def nsl_shade(ctx, lightmaps, width, height, cam, light_list, rgba, stream=None):
+    check(load().nsl_shade(ctx, _dptr(lightmaps), int(width), int(height), C.byref(camera(cam)),
+                           lights(light_list), len(light_list), _dptr(rgba), _stream(stream)),
+          "nsl_shade")
+
+
+def nsl_render_frame_host(ctx, density_np, mask_np, cam, light_list, step, precision,
+                          guide_np=None, lightmaps_np=None, rgba_np=None, opts=None, stream=None):
+    """Whole frame from host numpy buffers (copies in and out inside the call)."""
+    def hp(a):
+        return None if a is None else C.c_void_p(a.ctypes.data)
+    check(load().nsl_render_frame_host(ctx, hp(density_np), hp(mask_np), C.byref(camera(cam)),
+                                       lights(light_list), len(light_list), float(step),
+                                       C.byref(opts) if opts is not None else None, int(precision),
+                                       hp(guide_np), hp(lightmaps_np), hp(rgba_np), _stream(stream)),
+          "nsl_render_frame_host")
+
+
+class Context:
+    """Owns an nsl_ctx; the methods forward to the C ABI."""
+
+    def __init__(self, grid_shape, dtype, blob, max_width, max_height, sigma_scale=1.0):
+        nz, ny, nx = grid_shape
+        self.ctx = nsl_create(nx, ny, nz, dtype, sigma_scale, blob, max_width, max_height)
+
+    def close(self):
+        if self.ctx:
+            nsl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stage_grid(self, density, mask, stream=None):
+        nsl_stage_grid(self.ctx, density, mask, stream=stream)
+
+    def guide_sample_count(self, cam, step, opts=None, stream=None):
+        return nsl_guide_sample_count(self.ctx, cam, step, opts=opts, stream=stream)
+
+    def guiding_map(self, density, mask, cam, step, guide, opts=None, stream=None):
+        nsl_guiding_map(self.ctx, density, mask, cam, step, guide, opts=opts, stream=stream)
+
+    def predict_lightmaps(self, guide, width, height, precision, lightmaps, stream=None):
+        nsl_predict_lightmaps(self.ctx, guide, width, height, precision, lightmaps, stream=stream)
+
+    def shade(self, lightmaps, width, height, cam, light_list, rgba, stream=None):
+        nsl_shade(self.ctx, lightmaps, width, height, cam, light_list, rgba, stream=stream)

@@ -1,0 +1,72 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and compare with the FP64 oracle (tolerances of the hot-path contract)."""
+from __future__ import annotations
+
+import numpy as np
+
+# tolerances (per channel, relative to the oracle's range max|o|)
+TOL_GUIDE = 1e-5          # ray march
+TOL_NET_F32_ABS = 1e-4    # FP32 network, max-abs
+TOL_NET_BF16 = 2e-2       # BF16 network, of the output range
+TOL_NET_FP8 = 6e-2        # FP8 network, of the output range
+TOL_SHADE = 1e-5
+MAX_EXCUSED_FRAC = 1e-3   # threshold-flip pixels allowed to differ
+
+
+def torch_dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def make_ctx(pf, max_w=None, max_h=None, c0=16, seed=0):
+    from paper_2604_03748_gb300 import inputs as I, nsl
+    blob = I.pack_blob(I.make_params(c0, seed=seed), c0)
+    nz, ny, nx = pf.density.shape
+    dtype = nsl.NSL_F16 if pf.density.dtype == np.float16 else nsl.NSL_F32
+    return nsl.Context((nz, ny, nx), dtype, blob, max_w or pf.camera.width, max_h or pf.camera.height,
+                       sigma_scale=pf.sigma_scale)
+
+
+def gpu_guide(ctx, pf, **opts):
+    import torch
+    from paper_2604_03748_gb300 import nsl
+    dev = torch_dev()
+    d = torch.from_numpy(np.ascontiguousarray(pf.density)).to(dev)
+    m = None if pf.mask is None else torch.from_numpy(np.ascontiguousarray(pf.mask)).to(dev)
+    H, W = pf.camera.height, pf.camera.width
+    g = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    ctx.guiding_map(d, m, pf.camera, pf.step, g, opts=nsl.march_opts(**opts) if opts else None)
+    torch.cuda.synchronize()
+    return g.cpu().numpy().astype(np.float64)
+
+
+def gpu_net(ctx, guide_np, precision):
+    import torch
+    dev = torch_dev()
+    g = torch.from_numpy(np.ascontiguousarray(guide_np, dtype=np.float32)).to(dev)
+    _, H, W = g.shape
+    out = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+    ctx.predict_lightmaps(g, W, H, precision, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def compare_guide(g, o, flags, tol=TOL_GUIDE):
+    """Per-channel error relative to range, excusing threshold-flip pixels
+    flagged by the oracle.  Returns (errs[3], n_excused_differing)."""
+    excuse_LT = (flags & 1) != 0
+    excuse_D = (flags & 2) != 0
+    errs = []
+    bad_excused = 0
+    for c in range(3):
+        rng = max(np.abs(o[c]).max(), 1e-30)
+        diff = np.abs(g[c] - o[c]) / rng
+        ex = excuse_D if c == 2 else excuse_LT
+        errs.append(float(diff[~ex].max()) if (~ex).any() else 0.0)
+        bad_excused += int(((diff > tol) & ex).sum())
+    return errs, bad_excused
+
+
+def range_err(g, o):
+    """max |g - o| / max |o| per plane."""
+    return [float(np.abs(g[c] - o[c]).max() / max(np.abs(o[c]).max(), 1e-30)) for c in range(g.shape[0])]

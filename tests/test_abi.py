@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/nsl.h declares.  No compute calls (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "nsl.h")).read()
+    return sorted(set(re.findall(r"NSL_API\s+[\w\s\*]*?\b(nsl_\w+)\s*\(", hdr)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("nsl_create", "nsl_guiding_map", "nsl_predict_lightmaps", "nsl_shade", "nsl_destroy"):
+        assert n in names
+
+
+def test_library_builds_and_exports_all_symbols():
+    from paper_2604_03748_gb300 import build, nsl
+    path = build.build()
+    assert os.path.exists(path)
+    lib = nsl.load()
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+    assert sorted(nsl.EXPORTS) == sorted(declared_symbols()) or set(declared_symbols()) <= set(nsl.EXPORTS)
+
+
+def test_status_strings_without_gpu():
+    from paper_2604_03748_gb300 import nsl
+    lib = nsl.load()
+    assert lib.nsl_status_str(0) == b"ok"
+    assert lib.nsl_status_str(1) == b"invalid argument"
+
+
+def test_create_rejects_bad_blob_without_touching_the_gpu():
+    """Blob validation happens before any CUDA call."""
+    from paper_2604_03748_gb300 import nsl
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.nsl_create(8, 8, 8, nsl.NSL_F32, 1.0, b"XXXX" + b"\0" * 40, 64, 64)
+    assert ei.value.status == nsl.NSL_ERR_INVALID_ARG
+    from paper_2604_03748_gb300 import inputs as I
+    blob = bytearray(I.pack_blob(I.make_params(16), 16))
+    blob[40] ^= 1  # corrupt one parameter byte: checksum must catch it
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.nsl_create(8, 8, 8, nsl.NSL_F32, 1.0, bytes(blob), 64, 64)
+    assert "checksum" in str(ei.value)
+    blob8 = I.pack_blob(I.make_params(8), 8)
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.nsl_create(8, 8, 8, nsl.NSL_F32, 1.0, blob8, 64, 64)
+    assert ei.value.status == nsl.NSL_ERR_UNSUPPORTED

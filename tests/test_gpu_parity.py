@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs.  Marked gpu (needs a GB300 and the built libnsl)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2604_03748_gb300 import inputs as I
+import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_03748_gb300 import build, nsl
+    build.build()
+    nsl.load()
+    import torch
+    assert torch.cuda.is_available()
+    return nsl
+
+
+# ----------------------------------------------------------------------------
+# guide march
+# ----------------------------------------------------------------------------
+
+GUIDE_CASES = {
+    "plume64_ortho128_h4": lambda: I.config_plain_64(),
+    "small24_persp_mask_ragged": lambda: I.small_case(24, 32, 24, seed=11, kind=I.PERSP, step=2.0),
+    "small20_ortho_h3": lambda: I.small_case(20, 40, 16, seed=12, kind=I.ORTHO, step=3.0),
+}
+
+
+@pytest.mark.parametrize("name", list(GUIDE_CASES))
+def test_guide_parity(lib, orc, name):
+    pf = GUIDE_CASES[name]()
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    o, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= PT.MAX_EXCUSED_FRAC * g[0].size
+    ctx.close()
+
+
+def test_guide_parity_obstacle_128_full_size(lib, orc):
+    """The 128^3 perspective 512^2 workload with the sphere obstacle, every pixel."""
+    pf = I.config_obstacle_128()
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    o, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= PT.MAX_EXCUSED_FRAC * g[0].size
+    ctx.close()
+
+
+@pytest.mark.parametrize("opts", [dict(jitter=0, t_min=0.0), dict(segment_exact=1),
+                                  dict(phase_g=0.5, surrogate_I=(1.0, 0.5, 2.0)),
+                                  dict(seed=123, frame=77, tau_depth=0.2)])
+def test_guide_options(lib, orc, opts):
+    pf = I.small_case(24, 24, 16, seed=13, kind=I.PERSP, step=2.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf, **opts)
+    o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step, **opts)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= max(1, PT.MAX_EXCUSED_FRAC * g[0].size)
+    ctx.close()
+
+
+def test_guide_edge_cases(lib, orc):
+    # empty grid, fully masked grid, rays that miss, a tiny 8x8 image, ragged grid
+    vol = np.zeros((9, 7, 11), np.float32)
+    cam = I.perspective_camera(11, 2, 8, 8)
+    pf = I.PlumeFrame(vol, None, cam, I.random_light(1), 1.5)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    assert np.all(g[0] == 0) and np.all(g[1] == 1) and np.all(g[2] == 0)
+    ctx.close()
+    vol = I.blob_fbm_volume(16, 3)
+    pf = I.PlumeFrame(vol, np.ones_like(vol, np.uint8), I.orbit_ortho_camera(16, 3, 16, 8),
+                      I.random_light(1), 2.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    assert np.all(g[0] == 0) and np.all(g[1] == 1) and np.all(g[2] == 0)
+    ctx.close()
+    cam = I.Camera(I.ORTHO, (8.0, 8.0, 40.0), (8.0, 8.0, 80.0), (0.0, 1.0, 0.0), 40.0, 16.0, 16, 16)
+    pf = I.PlumeFrame(vol, None, cam, I.random_light(1), 2.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    assert np.all(g[1] == 1)
+    ctx.close()
+    # ragged non-cubic grid
+    rng = np.random.default_rng(5)
+    vol = (rng.uniform(0, 0.3, size=(13, 21, 17))).astype(np.float32)
+    mask = (rng.uniform(size=vol.shape) < 0.1).astype(np.uint8)
+    cam = I.perspective_camera(21, 5, 24, 16)
+    pf = I.PlumeFrame(vol, mask, cam, I.random_light(2), 1.25)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    o, _, f = orc.guide(vol, mask, cam, 1.25)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE and bad <= 1, errs
+    ctx.close()
+
+
+def test_guide_fp16_density(lib, orc):
+    pf = I.small_case(32, 32, 32, seed=14, kind=I.PERSP, step=2.0)
+    pf.density = pf.density.astype(np.float16)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE and bad <= 1, errs
+    ctx.close()
+
+
+def test_guide_deterministic(lib):
+    pf = I.config_plain_64()
+    ctx = PT.make_ctx(pf)
+    a = PT.gpu_guide(ctx, pf)
+    b = PT.gpu_guide(ctx, pf)
+    assert np.array_equal(a, b)
+    ctx.close()
+
+
+def test_invalid_arguments_rejected(lib):
+    import torch
+    from paper_2604_03748_gb300 import nsl
+    pf = I.config_plain_64()
+    ctx = PT.make_ctx(pf)
+    d = torch.from_numpy(pf.density).cuda()
+    g = torch.empty((3, 128, 128), device="cuda")
+    big = I.orbit_ortho_camera(64, 1, 256, 256)
+    with pytest.raises(nsl.NslError) as ei:
+        ctx.guiding_map(d, None, big, 4.0, g)
+    assert ei.value.status == nsl.NSL_ERR_INVALID_ARG
+    with pytest.raises(nsl.NslError):
+        ctx.guiding_map(d, None, pf.camera, 0.0, g)
+    odd = I.orbit_ortho_camera(64, 1, 100, 128)
+    with pytest.raises(nsl.NslError):
+        ctx.guiding_map(d, None, odd, 4.0, g)
+    with pytest.raises(nsl.NslError) as ei:
+        ctx.predict_lightmaps(g, 128, 128, 7, torch.empty((8, 128, 128), device="cuda"))
+    assert ei.value.status in (nsl.NSL_ERR_UNSUPPORTED, nsl.NSL_ERR_INVALID_ARG)
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# network
+# ----------------------------------------------------------------------------
+
+def _guide_input(H, W, seed):
+    rng = np.random.default_rng(seed)
+    g = np.stack([rng.uniform(0, 0.2, (H, W)), rng.uniform(0, 1, (H, W)), rng.uniform(0, 100, (H, W))])
+    return g.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 40), (128, 128), (64, 96)])
+def test_net_f32_parity(lib, orc, H, W):
+    from paper_2604_03748_gb300 import nsl
+    vol = np.zeros((64, 64, 64), np.float32)
+    pf = I.PlumeFrame(vol, None, I.orbit_ortho_camera(64, 1, W, H), I.random_light(1), 4.0)
+    ctx = PT.make_ctx(pf)
+    guide = _guide_input(H, W, H * 7 + W)
+    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_F32)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 64 * 64))
+    assert np.abs(got - ref).max() <= PT.TOL_NET_F32_ABS, np.abs(got - ref).max()
+    ctx.close()
+
+
+def test_net_f32_parity_on_oracle_guide_512(lib, orc):
+    """The 512^2 workload: FP32 network on the oracle's guide of the obstacle scene."""
+    from paper_2604_03748_gb300 import nsl
+    pf = I.config_obstacle_128()
+    o, _, _ = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    guide = o.astype(np.float32).astype(np.float64)
+    ctx = PT.make_ctx(pf)
+    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_F32)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 128 * 128))
+    assert np.abs(got - ref).max() <= PT.TOL_NET_F32_ABS, np.abs(got - ref).max()
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# shading
+# ----------------------------------------------------------------------------
+
+def test_shade_parity(lib, orc):
+    import torch
+    rng = np.random.default_rng(3)
+    H, W = 24, 40
+    lm = rng.uniform(-0.2, 1.0, size=(8, H, W)).astype(np.float32)
+    cam = I.perspective_camera(32, 4, W, H)
+    lights = [I.random_light(s) for s in range(5)]
+    pf = I.PlumeFrame(np.zeros((8, 8, 8), np.float32), None, cam, lights[0], 1.0)
+    ctx = PT.make_ctx(pf)
+    out = torch.empty((4, H, W), device="cuda")
+    ctx.shade(torch.from_numpy(lm).cuda(), W, H, cam, lights, out)
+    ref = orc.shade(lm.astype(np.float64), cam, lights)
+    torch.cuda.synchronize()
+    errs = PT.range_err(out.cpu().numpy().astype(np.float64), ref)
+    assert max(errs) <= PT.TOL_SHADE, errs
+    # no lights: emissive and alpha only
+    ctx.shade(torch.from_numpy(lm).cuda(), W, H, cam, [], out)
+    ref = orc.shade(lm.astype(np.float64), cam, [])
+    assert max(PT.range_err(out.cpu().numpy().astype(np.float64), ref)) <= PT.TOL_SHADE
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# whole frame through the host entry point
+# ----------------------------------------------------------------------------
+
+def test_render_frame_host_matches_device_calls(lib, orc):
+    from paper_2604_03748_gb300 import nsl
+    pf = I.config_plain_64()
+    ctx = PT.make_ctx(pf)
+    H, W = pf.camera.height, pf.camera.width
+    guide = np.zeros((3, H, W), np.float32)
+    lm = np.zeros((8, H, W), np.float32)
+    rgba = np.zeros((4, H, W), np.float32)
+    nsl.nsl_render_frame_host(ctx.ctx, pf.density, None, pf.camera, [pf.light], pf.step,
+                              nsl.NSL_PREC_F32, guide, lm, rgba)
+    o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    errs, bad = PT.compare_guide(guide.astype(np.float64), o, f)
+    assert max(errs) <= PT.TOL_GUIDE
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    ref_lm = orc.net_forward(guide.astype(np.float64), flat, 16, 1.0 / math.sqrt(3 * 64 * 64))
+    assert np.abs(lm - ref_lm).max() <= PT.TOL_NET_F32_ABS
+    ref_rgba = orc.shade(lm.astype(np.float64), pf.camera, [pf.light])
+    assert max(PT.range_err(rgba.astype(np.float64), ref_rgba)) <= PT.TOL_SHADE
+    ctx.close()
