@@ -267,14 +267,14 @@ def main():
     h_lm = torch.empty((8, H, W)).pin_memory()
     h_rgba = torch.empty((4, H, W)).pin_memory()
     e2e_t = []
-    for k in range(args.e2e_steps + 1):
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         t0 = time.perf_counter()
         nsl.nsl_render_frame_host(ctx.ctx, h_dens.numpy(), h_mask.numpy(), pf.camera, [pf.light], pf.step,
                                   prec, h_guide.numpy(), h_lm.numpy(), h_rgba.numpy(), opts=opts,
                                   stream=stream)
         if k:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_val = H * W / float(np.mean(e2e_t)) / 1e6 * ws
+    e2e_val = H * W / float(np.mean(e2e_t)) / 1e6 * ws if e2e_t else None
 
     pk, pk_kind = peaks()
     march_avg_s = float(np.mean(march_ms)) / 1e3

@@ -105,8 +105,11 @@ struct nsl_ctx {
   bool staged_valid = false;        // a staging has been queued
   unsigned long long* counter = nullptr;  // sample-count scratch
   NetF32Weights* wf32 = nullptr;
-  void* ws = nullptr;               // network workspace
+  NetTcWeights* wtc = nullptr;      // tensor-core weights (built on first BF16 call)
+  void* ws = nullptr;               // network workspace (shared by both precisions)
   size_t ws_bytes = 0;
+  unsigned int* err_host = nullptr; // device-written error word (mapped host memory)
+  unsigned int* err_dev = nullptr;
   // device staging for nsl_render_frame_host
   void* h_density = nullptr;
   uint8_t* h_mask = nullptr;
@@ -200,8 +203,17 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   c->wf32 = net_f32_create(c->params.data(), L, &e);
   if (!c->wf32) { nsl_destroy(c); return cuda_fail(e, "nsl_create: FP32 weights"); }
   c->ws_bytes = net_f32_workspace_bytes(max_width, max_height);
+  {
+    size_t tcb = net_tc_workspace_bytes(max_width, max_height);
+    if (tcb > c->ws_bytes) c->ws_bytes = tcb;
+  }
   e = cudaMalloc(&c->ws, c->ws_bytes);
   if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: workspace"); }
+  e = cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(unsigned int), cudaHostAllocMapped);
+  if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: error word"); }
+  *c->err_host = 0;
+  e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->err_dev), c->err_host, 0);
+  if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: error word"); }
   *out = c;
   return NSL_OK;
 }
@@ -212,7 +224,9 @@ void nsl_destroy(nsl_ctx* c) {
   cudaFree(c->staged);
   cudaFree(c->counter);
   net_f32_destroy(c->wf32);
+  net_tc_destroy(c->wtc);
   cudaFree(c->ws);
+  if (c->err_host) cudaFreeHost(c->err_host);
   cudaFree(c->h_density);
   cudaFree(c->h_mask);
   cudaFree(c->h_guide);
@@ -350,9 +364,23 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
                                        (double)c->grid.nz * c->grid.nz))};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
+  // a bounded wait that gave up in an earlier tensor-core launch is reported here
+  if (c->err_host && *reinterpret_cast<volatile unsigned int*>(c->err_host) != 0) {
+    unsigned int code = *c->err_host;
+    *c->err_host = 0;
+    return fail(NSL_ERR_TIMEOUT, "nsl_predict_lightmaps: an earlier tensor-core launch timed out "
+                "waiting on an mbarrier (code 0x%x)", code);
+  }
   switch (precision) {
     case NSL_PREC_F32:
       e = net_f32_forward(c->wf32, img, c->ws, c->ws_bytes, s);
+      break;
+    case NSL_PREC_BF16:
+      if (!c->wtc) {
+        c->wtc = net_tc_create(c->params.data(), c->layout, &e);
+        if (!c->wtc) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");
+      }
+      e = net_tc_forward(c->wtc, c->wf32, img, c->ws, c->ws_bytes, c->err_dev, s);
       break;
     default:
       return fail(NSL_ERR_UNSUPPORTED, "nsl_predict_lightmaps: precision %d not built", precision);

@@ -13,6 +13,14 @@ namespace nsl {
 
 enum InMode { IN_PLAIN = 0, IN_POOL = 1, IN_CONCAT = 2, IN_GUIDE = 3 };
 
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
 constexpr int kTW = 16, kTH = 16;               // output tile (pixels)
 constexpr int kHW = kTW + 2, kHH = kTH + 2;     // halo tile
 constexpr int kHaloPix = kHW * kHH;             // 324
@@ -23,7 +31,7 @@ struct ConvArgs {
   const float* inB;   // IN_CONCAT second operand (skip), NHWC
   const float* w;     // packed [cout/16][cin][9][16]
   const float* b;     // [cout]
-  float* out;         // NHWC [H][W][cout]
+  void* out;          // NHWC [H][W][cout], float or bf16
   int H, W;           // output (= conv) size
   float depth_scale;
 };
@@ -49,7 +57,7 @@ __device__ __forceinline__ float load_in(const ConvArgs& a, int y, int x, int c)
   }
 }
 
-template <int CIN, int MODE>
+template <int CIN, int MODE, typename TOut>
 __global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) {
   constexpr int CT = CIN < 16 ? CIN : 16;  // input-channel chunk
   __shared__ float halo[CT * kHaloStride];
@@ -105,16 +113,26 @@ __global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) 
   for (int r = 0; r < 2; ++r) {
     int y = y0 + ty + r;
     if (y >= a.H) continue;
-    float* dst = a.out + ((size_t)y * a.W + x) * cout + cg * 16;
+    TOut* dst = static_cast<TOut*>(a.out) + ((size_t)y * a.W + x) * cout + cg * 16;
     const float* acc = r ? acc1 : acc0;
+    if constexpr (sizeof(TOut) == 4) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float4 v;
-      v.x = fmaxf(acc[4 * q + 0] + __ldg(bias + 4 * q + 0), 0.f);
-      v.y = fmaxf(acc[4 * q + 1] + __ldg(bias + 4 * q + 1), 0.f);
-      v.z = fmaxf(acc[4 * q + 2] + __ldg(bias + 4 * q + 2), 0.f);
-      v.w = fmaxf(acc[4 * q + 3] + __ldg(bias + 4 * q + 3), 0.f);
-      reinterpret_cast<float4*>(dst)[q] = v;
+      for (int q = 0; q < 4; ++q) {
+        float4 v;
+        v.x = fmaxf(acc[4 * q + 0] + __ldg(bias + 4 * q + 0), 0.f);
+        v.y = fmaxf(acc[4 * q + 1] + __ldg(bias + 4 * q + 1), 0.f);
+        v.z = fmaxf(acc[4 * q + 2] + __ldg(bias + 4 * q + 2), 0.f);
+        v.w = fmaxf(acc[4 * q + 3] + __ldg(bias + 4 * q + 3), 0.f);
+        reinterpret_cast<float4*>(dst)[q] = v;
+      }
+    } else {
+      __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        h[q] = __floats2bfloat162_rn(fmaxf(acc[2 * q] + __ldg(bias + 2 * q), 0.f),
+                                     fmaxf(acc[2 * q + 1] + __ldg(bias + 2 * q + 1), 0.f));
+      reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
+      reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
     }
   }
 }
@@ -223,11 +241,11 @@ __device__ __forceinline__ void layer_norm16(const float* x, const float* w, con
 
 // Pass 1: x1_a = SG(dw3x3(pw1(LN1(F)))) for the four adapters a; writes x1 (NHWC,
 // 64 channels) and this tile's per-channel sums (deterministic tree order).
-__global__ void __launch_bounds__(128) adapter_pass1_f32(const float* __restrict__ F,
-                                                         const float* __restrict__ params,
-                                                         float* __restrict__ x1,
-                                                         float* __restrict__ partial, int H,
-                                                         int W) {
+template <typename TA>
+__global__ void __launch_bounds__(128) adapter_pass1(const TA* __restrict__ F,
+                                                     const float* __restrict__ params,
+                                                     TA* __restrict__ x1,
+                                                     float* __restrict__ partial, int H, int W) {
   __shared__ float fh[kAdHalo * 16];
   __shared__ float t[32 * kAdHaloS];
   __shared__ float prm[AdOff::scaw];
@@ -238,7 +256,7 @@ __global__ void __launch_bounds__(128) adapter_pass1_f32(const float* __restrict
   for (int e = tid; e < kAdHalo * 16; e += 128) {
     int hp = e / 16, c = e % 16;
     int y = y0 + hp / kAdHW - 1, x = x0 + hp % kAdHW - 1;
-    fh[e] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(F + ((size_t)y * W + x) * 16 + c) : 0.f;
+    fh[e] = (y >= 0 && y < H && x >= 0 && x < W) ? to_float(F[((size_t)y * W + x) * 16 + c]) : 0.f;
   }
   const int tx = tid % kAdTW, ty = tid / kAdTW;
   const int px = x0 + tx, py = y0 + ty;
@@ -279,9 +297,9 @@ __global__ void __launch_bounds__(128) adapter_pass1_f32(const float* __restrict
       g[c] = valid ? d0 * d1 : 0.f;
     }
     if (valid) {
-      float4* dst = reinterpret_cast<float4*>(x1 + ((size_t)py * W + px) * 64 + a * 16);
+      TA* dst = x1 + ((size_t)py * W + px) * 64 + a * 16;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) dst[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+      for (int c = 0; c < 16; ++c) dst[c] = from_float<TA>(g[c]);
     }
     // per-channel tile sums: butterfly within each warp, then warps in order
 #pragma unroll
@@ -328,11 +346,12 @@ __global__ void __launch_bounds__(64) adapter_reduce(const float* __restrict__ p
 }
 
 // Pass 2: per pixel, the rest of each NAFBlock and its 1x1 head -> 8 planes.
-__global__ void __launch_bounds__(128) adapter_pass2_f32(const float* __restrict__ F,
-                                                         const float* __restrict__ x1,
-                                                         const float* __restrict__ att,
-                                                         const float* __restrict__ params,
-                                                         float* __restrict__ out, int npix) {
+template <typename TA>
+__global__ void __launch_bounds__(128) adapter_pass2(const TA* __restrict__ F,
+                                                     const TA* __restrict__ x1,
+                                                     const float* __restrict__ att,
+                                                     const float* __restrict__ params,
+                                                     float* __restrict__ out, int npix) {
   __shared__ float prm[4 * kAdapterParams];
   __shared__ float at[64];
   for (int e = threadIdx.x; e < 4 * kAdapterParams; e += 128) prm[e] = __ldg(params + e);
@@ -341,24 +360,15 @@ __global__ void __launch_bounds__(128) adapter_pass2_f32(const float* __restrict
   const int p = blockIdx.x * 128 + threadIdx.x;
   if (p >= npix) return;
   float f[16];
-  const float4* fs = reinterpret_cast<const float4*>(F + (size_t)p * 16);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float4 v = __ldg(fs + q);
-    f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
-  }
+  for (int c = 0; c < 16; ++c) f[c] = to_float(F[(size_t)p * 16 + c]);
   const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
 #pragma unroll 1
   for (int a = 0; a < 4; ++a) {
     const float* pp = prm + a * kAdapterParams;
     float xa[16], y[16], n[16], gsg[16];
-    const float4* xs = reinterpret_cast<const float4*>(x1 + (size_t)p * 64 + a * 16);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float4 v = __ldg(xs + q);
-      xa[4 * q] = v.x * at[a * 16 + 4 * q]; xa[4 * q + 1] = v.y * at[a * 16 + 4 * q + 1];
-      xa[4 * q + 2] = v.z * at[a * 16 + 4 * q + 2]; xa[4 * q + 3] = v.w * at[a * 16 + 4 * q + 3];
-    }
+    for (int c = 0; c < 16; ++c) xa[c] = to_float(x1[(size_t)p * 64 + a * 16 + c]) * at[a * 16 + c];
 #pragma unroll
     for (int co = 0; co < 16; ++co) {
       float s = pp[AdOff::pw2b + co];
@@ -447,6 +457,10 @@ NetF32Weights* net_f32_create(const float* hp, const NetLayout& L, cudaError_t* 
   return w;
 }
 
+const float* net_f32_conv_w(const NetF32Weights* w, int l) { return w->conv_w[l]; }
+const float* net_f32_conv_b(const NetF32Weights* w, int l) { return w->conv_b[l]; }
+const float* net_f32_adapters(const NetF32Weights* w) { return w->adapters; }
+
 void net_f32_destroy(NetF32Weights* w) {
   if (!w) return;
   for (void* p : w->allocs) cudaFree(p);
@@ -480,11 +494,44 @@ size_t net_f32_workspace_bytes(int max_w, int max_h) {
   return carve((size_t)max_w * max_h, &b, nullptr);
 }
 
-template <int CIN, int MODE>
+template <int CIN, int MODE, typename TOut = float>
 static cudaError_t conv(const ConvArgs& a, int cout, cudaStream_t s) {
   dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH, cout / 16);
-  conv3x3_f32_kernel<CIN, MODE><<<grid, 128, 0, s>>>(a, cout);
+  conv3x3_f32_kernel<CIN, MODE, TOut><<<grid, 128, 0, s>>>(a, cout);
   return cudaGetLastError();
+}
+
+// First layer (guide -> C0) on the SIMT cores with a bf16 NHWC output: the
+// tensor-core path starts at the second layer (K = 27 is too narrow a GEMM).
+cudaError_t simt_first_conv_bf16(const NetF32Weights* w, const NetImage& img, __nv_bfloat16* out,
+                                 cudaStream_t s) {
+  ConvArgs a{img.guide, nullptr, net_f32_conv_w(w, 0), net_f32_conv_b(w, 0), out, img.H, img.W,
+             img.depth_scale};
+  return conv<3, IN_GUIDE, __nv_bfloat16>(a, 16, s);
+}
+
+template <typename TA>
+cudaError_t adapters_forward(const NetF32Weights* w, const TA* F, TA* x1, float* partial, float* att,
+                             float* out, int H, int W, cudaStream_t s) {
+  dim3 ag((W + kAdTW - 1) / kAdTW, (H + kAdTH - 1) / kAdTH);
+  const float* prm = net_f32_adapters(w);
+  adapter_pass1<TA><<<ag, 128, 0, s>>>(F, prm, x1, partial, H, W);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t P = (size_t)H * W;
+  adapter_reduce<<<1, 64, 0, s>>>(partial, ag.x * ag.y, 1.f / (float)P, prm, att);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  adapter_pass2<TA><<<(unsigned)((P + 127) / 128), 128, 0, s>>>(F, x1, att, prm, out, (int)P);
+  return cudaGetLastError();
+}
+template cudaError_t adapters_forward<float>(const NetF32Weights*, const float*, float*, float*,
+                                             float*, float*, int, int, cudaStream_t);
+template cudaError_t adapters_forward<__nv_bfloat16>(const NetF32Weights*, const __nv_bfloat16*,
+                                                     __nv_bfloat16*, float*, float*, float*, int,
+                                                     int, cudaStream_t);
+
+size_t adapter_partial_floats(int max_w, int max_h) {
+  return (size_t)((max_w + kAdTW - 1) / kAdTW) * ((max_h + kAdTH - 1) / kAdTH) * 64;
 }
 
 template <int CIN>
@@ -535,14 +582,7 @@ cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* w
   TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s)));
   TRY((conv<16, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), 16, s)));
   // adapters
-  dim3 ag((W + kAdTW - 1) / kAdTW, (H + kAdTH - 1) / kAdTH);
-  adapter_pass1_f32<<<ag, 128, 0, s>>>(B.fa, w->adapters, B.x1, B.partial, H, W);
-  TRY(cudaGetLastError());
-  adapter_reduce<<<1, 64, 0, s>>>(B.partial, ag.x * ag.y, 1.f / (float)P, w->adapters, B.att);
-  TRY(cudaGetLastError());
-  adapter_pass2_f32<<<(unsigned)((P + 127) / 128), 128, 0, s>>>(B.fa, B.x1, B.att, w->adapters,
-                                                               img.out, (int)P);
-  TRY(cudaGetLastError());
+  TRY(adapters_forward<float>(w, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
 #undef TRY
   return cudaSuccess;
 }

@@ -1,0 +1,727 @@
+// Lightmap network convolutions on the 5th-generation tensor cores (sm_103a):
+// implicit-GEMM 3x3 convolutions and 2x2 stride-2 transposed convolutions with
+// BF16 operands and FP32 accumulation in tensor memory (Sec. 4.3 UNet).
+//
+// 3x3 convolution as a GEMM: M = 128 output pixels (a 16-row x 8-column patch),
+// N = output channels, K = 9 taps x Cin.  The input patch plus its one-pixel
+// halo (18 x 10 pixels) is staged once in shared memory as "core-matrix"
+// planes: for each group of 8 channels, the 180 halo pixels lie 16 bytes apart.
+// With that layout the A operand of tap (dy, dx) is the same planes read from a
+// start address shifted by (dy*10 + dx) pixels: 8 consecutive halo pixels form
+// one 8x16-byte core matrix, consecutive patch rows are 160 bytes apart (the
+// stride-dimension offset), and the two 8-channel halves of a 16-channel K step
+// are one plane apart (the leading-dimension offset).  No im2col copy exists.
+//
+// Weights (the B operand, K-major) are pre-packed on the host into the same
+// core-matrix order, one 16-channel K slice per (tap, channel chunk), and
+// copied into shared memory once per CTA with a bulk async copy.  A CTA is
+// persistent over M tiles: while the tensor core works on tile i (accumulator
+// buffer i%2 in TMEM), the CTA's 128 threads read tile i-1's accumulators out
+// of TMEM (tcgen05.ld), add the bias, apply ReLU, convert to BF16 and store
+// NHWC rows, and stage tile i+1's halo.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel records an error
+// code in a host-visible word, frees its TMEM and returns.
+#include <cstring>
+#include <vector>
+
+#include "nsl_internal.cuh"
+
+namespace nsl {
+
+namespace {
+
+enum TcMode { TC_PLAIN = 0, TC_POOL = 1, TC_CONCAT = 2 };
+
+constexpr int kPatchW = 8, kPatchH = 16;                     // M tile = 128 pixels
+constexpr int kHaloW = kPatchW + 2, kHaloH = kPatchH + 2;    // 10 x 18
+constexpr int kHaloPix = kHaloW * kHaloH;                    // 180
+constexpr int kPlane = kHaloPix * 16;                        // bytes per 8-channel plane
+constexpr long long kWaitCycles = 4000000000LL;              // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after ~2 s without the phase completing.  The outcome is
+// made warp-uniform, since the TMEM loads that follow are warp-collective.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  bool done = mbar_try_wait(b, parity);
+  if (!done) {
+    const long long t0 = clock64();
+    while (!(done = mbar_try_wait(b, parity))) {
+      if (clock64() - t0 > kWaitCycles) break;
+    }
+  }
+  return __all_sync(0xffffffffu, done);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle (canonical K-major core-matrix
+// layout): start address, leading-dimension (K) byte offset, stride-dimension
+// (M/N) byte offset, all in 16-byte units; bit 46 = descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(b))
+      : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit accumulators: thread t of the warp gets row
+// (32*(warp%4) + t), columns [col, col+16).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
+      "14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint4 bf16x8_max(uint4 a, uint4 b) {
+  uint4 r;
+  const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
+  const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&b);
+  __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(&r);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) pr[i] = __hmax2(pa[i], pb[i]);
+  return r;
+}
+
+__device__ __forceinline__ uint4 ldg128(const void* p) {
+  return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+__device__ __forceinline__ void record_error(unsigned int* err, unsigned int code) {
+  if (err) atomicOr_system(err, code);
+}
+
+struct TcConvArgs {
+  const __nv_bfloat16* inA;  // NHWC input (POOL: at 2H x 2W; CONCAT: first CIN/2 channels)
+  const __nv_bfloat16* inB;  // CONCAT: last CIN/2 channels (the skip tensor)
+  const uint8_t* wpack;      // [n tiles][9 taps][CIN/16][NT rows x 32 bytes]
+  const float* bias;         // [COUT]
+  __nv_bfloat16* out;        // NHWC [H][W][COUT]
+  int H, W;                  // convolution (output) size
+  int tiles_x, tiles_y;      // M tiles per row / column
+  unsigned int* err;
+};
+
+// Stage the halo of M tile `tile` into `halo` (CIN/8 planes of 180 x 16 bytes).
+template <int CIN, int MODE>
+__device__ __forceinline__ void load_halo(const TcConvArgs& a, int tile, uint8_t* halo) {
+  constexpr int G = CIN / 8;
+  const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
+  for (int e = threadIdx.x; e < kHaloPix * G; e += blockDim.x) {
+    const int hp = e / G, g = e % G;
+    const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+      if constexpr (MODE == TC_PLAIN) {
+        v = ldg128(a.inA + ((size_t)y * a.W + x) * CIN + g * 8);
+      } else if constexpr (MODE == TC_CONCAT) {
+        constexpr int CH = CIN / 2;
+        if (g < G / 2)
+          v = ldg128(a.inA + ((size_t)y * a.W + x) * CH + g * 8);
+        else
+          v = ldg128(a.inB + ((size_t)y * a.W + x) * CH + (g - G / 2) * 8);
+      } else {  // TC_POOL: 2x2 max of the finer level
+        const size_t W2 = 2 * (size_t)a.W;
+        const __nv_bfloat16* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 8;
+        v = bf16x8_max(bf16x8_max(ldg128(p), ldg128(p + CIN)),
+                       bf16x8_max(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
+      }
+    }
+    *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = v;
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void conv_epilogue(const TcConvArgs& a, int tile, uint32_t tacc,
+                                              int n0, int cout) {
+  const int warp = threadIdx.x >> 5;
+  const int m = threadIdx.x;  // accumulator row = pixel of the patch
+  const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+  const bool valid = y < a.H && x < a.W;
+  __nv_bfloat16* dst = a.out + ((size_t)y * a.W + x) * cout + n0;
+#pragma unroll
+  for (int c = 0; c < NT; c += 16) {
+    float v[16];
+    tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c, v);
+    __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      h[q] = __floats2bfloat162_rn(fmaxf(v[2 * q] + __ldg(a.bias + n0 + c + 2 * q), 0.f),
+                                   fmaxf(v[2 * q + 1] + __ldg(a.bias + n0 + c + 2 * q + 1), 0.f));
+    if (valid) {
+      reinterpret_cast<uint4*>(dst + c)[0] = reinterpret_cast<const uint4*>(h)[0];
+      reinterpret_cast<uint4*>(dst + c)[1] = reinterpret_cast<const uint4*>(h)[1];
+    }
+  }
+}
+
+// N tile of a 3x3 layer: all output channels up to 64, and 32 when Cin = 128
+// so that weights + two halo buffers fit in 227 KB of shared memory.
+__host__ __device__ constexpr int conv_nt(int cin, int cout) {
+  return cin >= 128 ? 32 : (cout > 64 ? 64 : cout);
+}
+
+template <int CIN, int COUT, int NT>
+struct ConvCfg {
+  static constexpr int G = CIN / 8;
+  static constexpr int KS = CIN / 16;                    // 16-channel K steps per tap
+  static constexpr int WBYTES = 9 * CIN * NT * 2;        // B operand of one N tile
+  static constexpr int HBYTES = G * kPlane;              // one halo buffer
+  static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;
+  static constexpr int SMEM = WBYTES + 2 * HBYTES + 64;  // + barriers and TMEM slot
+};
+
+template <int CIN, int COUT, int NT, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
+  using Cfg = ConvCfg<CIN, COUT, NT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* wsm = smem;
+  uint8_t* halo = smem + Cfg::WBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + 2 * Cfg::HBYTES);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nt = blockIdx.y;
+  const int ntiles = a.tiles_x * a.tiles_y;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, Cfg::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], Cfg::WBYTES);
+    const uint8_t* src = a.wpack + (size_t)nt * Cfg::WBYTES;
+    for (int off = 0; off < Cfg::WBYTES; off += 32768) {
+      const int n = Cfg::WBYTES - off < 32768 ? Cfg::WBYTES - off : 32768;
+      bulk_g2s(wsm + off, src + off, (uint32_t)n, &bars[0]);
+    }
+  }
+  bool ok = mbar_wait(&bars[0], 0);
+  if (!ok) record_error(a.err, 1u);
+
+  constexpr uint32_t idesc = idesc_bf16(128, NT);
+  uint32_t phase[2] = {0u, 0u};
+  int buf = 0, prev = -1, prevbuf = 0;
+  for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    load_halo<CIN, MODE>(a, tile, halo + buf * Cfg::HBYTES);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t hb = smem_u32(halo + buf * Cfg::HBYTES), wb = smem_u32(wsm);
+      const uint32_t d = tmem + (uint32_t)(buf * NT);
+      int kk = 0;
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+#pragma unroll
+        for (int j = 0; j < Cfg::KS; ++j, ++kk) {
+          const uint64_t ad = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
+          const uint64_t bd = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
+          mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(&bars[1 + buf]);
+    }
+    if (prev >= 0) {
+      if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+        record_error(a.err, 2u);
+        ok = false;
+      } else {
+        tc_fence_after();
+        conv_epilogue<NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+      }
+      phase[prevbuf] ^= 1u;
+    }
+    prev = tile;
+    prevbuf = buf;
+    buf ^= 1;
+  }
+  if (ok && prev >= 0) {
+    if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+      record_error(a.err, 2u);
+    } else {
+      tc_fence_after();
+      conv_epilogue<NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// 2x2 stride-2 transposed convolution: M = 128 input pixels (16 x 8 patch),
+// N = 4 x COUT ordered [sub-position (a,b)][co], K = CIN.  Output pixel
+// (2y+a, 2x+b) channel co = bias + sum_ci W[ci][co][a][b] in(y, x)[ci].
+// ---------------------------------------------------------------------------
+struct TcConvTArgs {
+  const __nv_bfloat16* in;   // NHWC [H][W][CIN]
+  const uint8_t* wpack;      // [CIN/16][N rows x 32 bytes]
+  const float* bias;         // [COUT]
+  __nv_bfloat16* out;        // NHWC [2H][2W][COUT]
+  int H, W, tiles_x, tiles_y;
+  unsigned int* err;
+};
+
+template <int CIN, int COUT>
+struct ConvTCfg {
+  static constexpr int N = 4 * COUT;
+  static constexpr int G = CIN / 8;
+  static constexpr int APLANE = 128 * 16;
+  static constexpr int WBYTES = CIN * N * 2;
+  static constexpr int ABYTES = G * APLANE;
+  static constexpr int TMEM_COLS = 2 * N > 512 ? 512 : (2 * N < 32 ? 32 : 2 * N);
+  static constexpr int NBUF = 2 * N > 512 ? 1 : 2;
+  static constexpr int SMEM = WBYTES + 2 * ABYTES + 64;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs a) {
+  using Cfg = ConvTCfg<CIN, COUT>;
+  constexpr int N = Cfg::N;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* wsm = smem;
+  uint8_t* abuf = smem + Cfg::WBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + 2 * Cfg::ABYTES);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int ntiles = a.tiles_x * a.tiles_y;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, Cfg::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], Cfg::WBYTES);
+    for (int off = 0; off < Cfg::WBYTES; off += 32768) {
+      const int n = Cfg::WBYTES - off < 32768 ? Cfg::WBYTES - off : 32768;
+      bulk_g2s(wsm + off, a.wpack + off, (uint32_t)n, &bars[0]);
+    }
+  }
+  bool ok = mbar_wait(&bars[0], 0);
+  if (!ok) record_error(a.err, 4u);
+
+  constexpr uint32_t idesc = idesc_bf16(128, N);
+  uint32_t phase[2] = {0u, 0u};
+  int buf = 0, prev = -1, prevbuf = 0;
+
+  auto epilogue = [&](int tile, int b) {
+    const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+    const int m = tid;
+    const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+    const bool valid = y < a.H && x < a.W;
+    const uint32_t tacc = tmem + (uint32_t)(b * N) + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tmem_ld16(tacc + c, v);
+      const int k = c / COUT, co = c % COUT;
+      const int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
+      __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        h[q] = __floats2bfloat162_rn(v[2 * q] + __ldg(a.bias + co + 2 * q),
+                                     v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1));
+      if (valid) {
+        __nv_bfloat16* dst = a.out + ((size_t)oy * (2 * a.W) + ox) * COUT + co;
+        reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
+        reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
+      }
+    }
+  };
+
+  for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    // stage the 128 input pixels of the patch: plane g holds channels 8g..8g+7
+    {
+      const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+      uint8_t* dstb = abuf + buf * Cfg::ABYTES;
+      for (int e = tid; e < 128 * Cfg::G; e += blockDim.x) {
+        const int m = e / Cfg::G, g = e % Cfg::G;
+        const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (y < a.H && x < a.W) v = ldg128(a.in + ((size_t)y * a.W + x) * CIN + g * 8);
+        *reinterpret_cast<uint4*>(dstb + g * Cfg::APLANE + m * 16) = v;
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (Cfg::NBUF == 1 && prev >= 0) {
+      // single accumulator: drain the previous tile before the next MMAs
+      if (!mbar_wait(&bars[1], phase[0])) { record_error(a.err, 8u); ok = false; break; }
+      tc_fence_after();
+      epilogue(prev, 0);
+      phase[0] ^= 1u;
+      prev = -1;
+      tc_fence_before();
+      __syncthreads();
+    }
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ab = smem_u32(abuf + buf * Cfg::ABYTES), wb = smem_u32(wsm);
+      const uint32_t d = tmem + (uint32_t)((Cfg::NBUF == 2 ? buf : 0) * N);
+#pragma unroll
+      for (int j = 0; j < CIN / 16; ++j) {
+        const uint64_t ad = smem_desc(ab + (uint32_t)(2 * j * Cfg::APLANE), Cfg::APLANE, 128);
+        const uint64_t bd = smem_desc(wb + (uint32_t)(j * N * 32), N * 16, 128);
+        mma_bf16(d, ad, bd, idesc, j > 0 ? 1u : 0u);
+      }
+      mma_commit(&bars[1 + (Cfg::NBUF == 2 ? buf : 0)]);
+    }
+    if (Cfg::NBUF == 2 && prev >= 0) {
+      if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+        record_error(a.err, 8u);
+        ok = false;
+      } else {
+        tc_fence_after();
+        epilogue(prev, prevbuf);
+      }
+      phase[prevbuf] ^= 1u;
+    }
+    prev = tile;
+    prevbuf = Cfg::NBUF == 2 ? buf : 0;
+    buf ^= 1;
+  }
+  if (ok && prev >= 0) {
+    if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+      record_error(a.err, 8u);
+    } else {
+      tc_fence_after();
+      epilogue(prev, prevbuf);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+// Kernel launch configuration: persistent grid of (CTAs per SM) x SMs, where
+// the CTAs per SM are limited so that their TMEM allocations fit in 512 columns.
+struct Launch {
+  int smem = 0;
+  int per_sm = 1;
+};
+
+template <typename K>
+static cudaError_t configure(K kernel, int smem_needed, int tmem_cols, Launch* L) {
+  const int tmem_fit = 512 / tmem_cols;
+  int smem = smem_needed;
+  // shared memory per SM is 228 KB (1 KB reserved per CTA): pad the request so
+  // that no more CTAs than the TMEM can hold become resident at once
+  const int cap = 233472 / (tmem_fit + 1) - 1024 + 128;
+  if (tmem_fit < 16 && smem < cap) smem = cap;
+  smem = (smem + 127) / 128 * 128;
+  if (smem > 232448) smem = 232448;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  L->smem = smem;
+  L->per_sm = occ < tmem_fit ? occ : tmem_fit;
+  return cudaSuccess;
+}
+
+// Pack a 3x3 conv weight [cout][cin][3][3] (float) into the B-operand tiles.
+static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uint8_t>& out) {
+  const int KS = cin / 16;
+  const size_t slice = (size_t)NT * 32;
+  out.assign((size_t)(cout / NT) * 9 * KS * slice, 0);
+  for (int nt = 0; nt < cout / NT; ++nt)
+    for (int tap = 0; tap < 9; ++tap)
+      for (int j = 0; j < KS; ++j) {
+        uint8_t* s = out.data() + (((size_t)nt * 9 + tap) * KS + j) * slice;
+        for (int n = 0; n < NT; ++n)
+          for (int k = 0; k < 16; ++k) {
+            const int co = nt * NT + n, ci = j * 16 + k;
+            const float v = w[((size_t)co * cin + ci) * 9 + tap];
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            const size_t off = (size_t)(k / 8) * NT * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+            std::memcpy(s + off, &b, 2);
+          }
+      }
+}
+
+// Pack a transposed-conv weight [cin][cout][2][2] into B tiles with rows
+// n = (2a+b)*cout + co and K = cin.
+static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& out) {
+  const int N = 4 * cout;
+  const size_t slice = (size_t)N * 32;
+  out.assign((size_t)(cin / 16) * slice, 0);
+  for (int j = 0; j < cin / 16; ++j) {
+    uint8_t* s = out.data() + j * slice;
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < 16; ++k) {
+        const int kpos = n / cout, co = n % cout, ci = j * 16 + k;
+        const float v = w[((size_t)ci * cout + co) * 4 + kpos];
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        const size_t off = (size_t)(k / 8) * N * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        std::memcpy(s + off, &b, 2);
+      }
+  }
+}
+
+}  // namespace
+
+struct NetTcWeights {
+  uint8_t* conv_w[14] = {};  // layer 0 stays on the SIMT path
+  float* conv_b[14] = {};
+  int conv_nt[14] = {};
+  uint8_t* up_w[3] = {};
+  float* up_b[3] = {};
+  std::vector<void*> allocs;
+};
+
+template <typename T>
+static T* dev_copy(NetTcWeights* w, const T* src, size_t n, cudaError_t* err) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) { *err = e; return nullptr; }
+  w->allocs.push_back(p);
+  e = cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) *err = e;
+  return static_cast<T*>(p);
+}
+
+NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, cudaError_t* err) {
+  *err = cudaSuccess;
+  NetTcWeights* w = new NetTcWeights();
+  std::vector<uint8_t> pk;
+  for (int l = 1; l < 14; ++l) {
+    const int cin = L.conv_cin[l], cout = L.conv_cout[l];
+    const int NT = conv_nt(cin, cout);
+    w->conv_nt[l] = NT;
+    pack_conv(hp + L.conv_w[l], cin, cout, NT, pk);
+    w->conv_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
+  }
+  for (int l = 0; l < 3; ++l) {
+    pack_convT(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk);
+    w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
+  }
+  if (*err != cudaSuccess) { net_tc_destroy(w); return nullptr; }
+  return w;
+}
+
+void net_tc_destroy(NetTcWeights* w) {
+  if (!w) return;
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+}
+
+namespace {
+struct TcBuffers {
+  __nv_bfloat16 *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1;
+  float *partial, *att;
+};
+
+size_t carve_tc(size_t P, size_t partial_floats, TcBuffers* b, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += (bytes + 255) / 256 * 256;
+    return p;
+  };
+  auto bf = [&](size_t n) { return reinterpret_cast<__nv_bfloat16*>(take(n * 2)); };
+  b->fa = bf(P * 16); b->fb = bf(P * 16); b->s1 = bf(P * 16);
+  b->l1a = bf(P / 4 * 32); b->l1b = bf(P / 4 * 32); b->s2 = bf(P / 4 * 32);
+  b->l2a = bf(P / 16 * 64); b->l2b = bf(P / 16 * 64); b->s3 = bf(P / 16 * 64);
+  b->l3a = bf(P / 64 * 128); b->l3b = bf(P / 64 * 128);
+  b->x1 = bf(P * 64);
+  b->partial = reinterpret_cast<float*>(take(partial_floats * 4));
+  b->att = reinterpret_cast<float*>(take(64 * 4));
+  return off;
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t run_conv(const NetTcWeights* w, int l, const __nv_bfloat16* inA,
+                     const __nv_bfloat16* inB, __nv_bfloat16* out, int H, int W,
+                     unsigned int* err, cudaStream_t s) {
+  constexpr int NT = conv_nt(CIN, COUT);
+  using Cfg = ConvCfg<CIN, COUT, NT>;
+  static_assert(Cfg::SMEM <= 232448, "shared memory budget");
+  static Launch L;
+  static bool init = false;
+  if (!init) {
+    cudaError_t e = configure(conv3x3_tc_kernel<CIN, COUT, NT, MODE>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  TcConvArgs a{inA, inB, w->conv_w[l], w->conv_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
+               (H + kPatchH - 1) / kPatchH, err};
+  const int ntiles = a.tiles_x * a.tiles_y;
+  int grid = kNumSMs * L.per_sm / (COUT / NT);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  conv3x3_tc_kernel<CIN, COUT, NT, MODE><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t run_convT(const NetTcWeights* w, int l, const __nv_bfloat16* in, __nv_bfloat16* out,
+                      int H, int W, unsigned int* err, cudaStream_t s) {
+  using Cfg = ConvTCfg<CIN, COUT>;
+  static Launch L;
+  static bool init = false;
+  if (!init) {
+    cudaError_t e = configure(convT_tc_kernel<CIN, COUT>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  TcConvTArgs a{in, w->up_w[l], w->up_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
+                (H + kPatchH - 1) / kPatchH, err};
+  const int ntiles = a.tiles_x * a.tiles_y;
+  int grid = kNumSMs * L.per_sm;
+  if (grid > ntiles) grid = ntiles;
+  convT_tc_kernel<CIN, COUT><<<grid, 128, L.smem, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+size_t net_tc_workspace_bytes(int max_w, int max_h) {
+  TcBuffers b;
+  return carve_tc((size_t)max_w * max_h, adapter_partial_floats(max_w, max_h), &b, nullptr);
+}
+
+cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
+                           void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
+  const int H = img.H, W = img.W;
+  const size_t P = (size_t)H * W;
+  TcBuffers B;
+  const size_t pf = adapter_partial_floats(W, H);
+  if (carve_tc(P, pf, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
+  carve_tc(P, pf, &B, static_cast<char*>(workspace));
+  cudaError_t e;
+#define TRY(x) if ((e = (x)) != cudaSuccess) return e
+  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  TRY(simt_first_conv_bf16(wf, img, B.fa, s));
+  TRY((run_conv<16, 16, TC_PLAIN>(w, 1, B.fa, nullptr, B.s1, H, W, err, s)));
+  TRY((run_conv<16, 32, TC_POOL>(w, 2, B.s1, nullptr, B.l1a, H1, W1, err, s)));
+  TRY((run_conv<32, 32, TC_PLAIN>(w, 3, B.l1a, nullptr, B.s2, H1, W1, err, s)));
+  TRY((run_conv<32, 64, TC_POOL>(w, 4, B.s2, nullptr, B.l2a, H2, W2, err, s)));
+  TRY((run_conv<64, 64, TC_PLAIN>(w, 5, B.l2a, nullptr, B.s3, H2, W2, err, s)));
+  TRY((run_conv<64, 128, TC_POOL>(w, 6, B.s3, nullptr, B.l3a, H3, W3, err, s)));
+  TRY((run_conv<128, 128, TC_PLAIN>(w, 7, B.l3a, nullptr, B.l3b, H3, W3, err, s)));
+  TRY((run_convT<128, 64>(w, 0, B.l3b, B.l2a, H3, W3, err, s)));
+  TRY((run_conv<128, 64, TC_CONCAT>(w, 8, B.l2a, B.s3, B.l2b, H2, W2, err, s)));
+  TRY((run_conv<64, 64, TC_PLAIN>(w, 9, B.l2b, nullptr, B.l2a, H2, W2, err, s)));
+  TRY((run_convT<64, 32>(w, 1, B.l2a, B.l1a, H2, W2, err, s)));
+  TRY((run_conv<64, 32, TC_CONCAT>(w, 10, B.l1a, B.s2, B.l1b, H1, W1, err, s)));
+  TRY((run_conv<32, 32, TC_PLAIN>(w, 11, B.l1b, nullptr, B.l1a, H1, W1, err, s)));
+  TRY((run_convT<32, 16>(w, 2, B.l1a, B.fa, H1, W1, err, s)));
+  TRY((run_conv<32, 16, TC_CONCAT>(w, 12, B.fa, B.s1, B.fb, H, W, err, s)));
+  TRY((run_conv<16, 16, TC_PLAIN>(w, 13, B.fb, nullptr, B.fa, H, W, err, s)));
+  TRY(adapters_forward<__nv_bfloat16>(wf, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+#undef TRY
+  return cudaSuccess;
+}
+
+}  // namespace nsl

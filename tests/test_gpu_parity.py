@@ -186,6 +186,39 @@ def test_net_f32_parity_on_oracle_guide_512(lib, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 40), (128, 128), (64, 96), (24, 136)])
+def test_net_bf16_parity(lib, orc, H, W):
+    """BF16 tensor-core network vs the FP64 oracle: within 2e-2 of each plane's range."""
+    from paper_2604_03748_gb300 import nsl
+    vol = np.zeros((64, 64, 64), np.float32)
+    pf = I.PlumeFrame(vol, None, I.orbit_ortho_camera(64, 1, W, H), I.random_light(1), 4.0)
+    ctx = PT.make_ctx(pf)
+    guide = _guide_input(H, W, H * 5 + W)
+    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 64 * 64))
+    errs = PT.range_err(got, ref)
+    assert max(errs) <= PT.TOL_NET_BF16, errs
+    ctx.close()
+
+
+def test_net_bf16_parity_on_oracle_guide_512(lib, orc):
+    """The 512^2 workload: BF16 network on the oracle's guide of the obstacle scene."""
+    from paper_2604_03748_gb300 import nsl
+    pf = I.config_obstacle_128()
+    o, _, _ = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    guide = o.astype(np.float32).astype(np.float64)
+    ctx = PT.make_ctx(pf)
+    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
+    again = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
+    assert np.array_equal(got, again)          # deterministic
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 128 * 128))
+    errs = PT.range_err(got, ref)
+    assert max(errs) <= PT.TOL_NET_BF16, errs
+    ctx.close()
+
+
 # ----------------------------------------------------------------------------
 # shading
 # ----------------------------------------------------------------------------
