@@ -170,7 +170,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nsl", choices=["nsl", "reference"])
-    ap.add_argument("--precision", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     args = ap.parse_args()
@@ -194,7 +194,8 @@ def main():
         torch.distributed.barrier()
     nsl.load()
 
-    prec = {"f32": nsl.NSL_PREC_F32, "bf16": nsl.NSL_PREC_BF16, "fp8": nsl.NSL_PREC_FP8}[args.precision]
+    prec = {"f32": nsl.NSL_PREC_F32, "bf16": nsl.NSL_PREC_BF16, "f16": nsl.NSL_PREC_F16,
+            "fp8": nsl.NSL_PREC_FP8}[args.precision]
     pf = I.config_obstacle_128()
     H, W = pf.camera.height, pf.camera.width
     blob = I.pack_blob(I.make_params(16, 0), 16)
@@ -283,7 +284,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "bf16": "f32 march + bf16 net", "fp8": "f32 march + fp8 net"}[args.precision],
+        "dtype": {"f32": "f32", "bf16": "f32 march + bf16 net", "f16": "f32 march + f16 net",
+                  "fp8": "f32 march + fp8 net"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [128, 128, 128], "grid_dtype": "f32", "billboard": [512, 512],
                    "camera": "perspective fov 40", "step_voxels": 2.0, "obstacle": "sphere r=20",

@@ -53,7 +53,9 @@ typedef enum {
 } nsl_status;
 
 enum { NSL_F32 = 0, NSL_F16 = 1 };                           /* density storage */
-enum { NSL_PREC_F32 = 0, NSL_PREC_BF16 = 1, NSL_PREC_FP8 = 2 }; /* network arithmetic */
+/* network arithmetic: FP32 SIMT; or tensor cores with FP32 accumulation and
+ * BF16, FP8 E4M3 or FP16 operands */
+enum { NSL_PREC_F32 = 0, NSL_PREC_BF16 = 1, NSL_PREC_FP8 = 2, NSL_PREC_F16 = 3 };
 enum { NSL_CAM_ORTHO = 0, NSL_CAM_PERSP = 1 };
 
 typedef struct nsl_ctx nsl_ctx; /* opaque, library-owned */
@@ -143,8 +145,8 @@ NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, f
 /* Lightmap network, Sec. 4.3 / Fig. 3.
  *   guide_dev      [3][H][W] float32 guide
  *   width, height  multiples of 8, within the context maximum
- *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16 or NSL_PREC_FP8
- *                  (tensor cores, FP32 accumulation)
+ *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16, NSL_PREC_F16 or
+ *                  NSL_PREC_FP8 (tensor cores, FP32 accumulation)
  *   lightmaps_dev  output [8][H][W] float32 planes
  *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,

@@ -105,7 +105,7 @@ struct nsl_ctx {
   bool staged_valid = false;        // a staging has been queued
   unsigned long long* counter = nullptr;  // sample-count scratch
   NetF32Weights* wf32 = nullptr;
-  NetTcWeights* wtc = nullptr;      // tensor-core weights (built on first BF16 call)
+  NetTcWeights* wtc[2] = {};        // tensor-core weights: [0] FP16, [1] BF16 (built on first use)
   void* ws = nullptr;               // network workspace (shared by both precisions)
   size_t ws_bytes = 0;
   unsigned int* err_host = nullptr; // device-written error word (mapped host memory)
@@ -224,7 +224,8 @@ void nsl_destroy(nsl_ctx* c) {
   cudaFree(c->staged);
   cudaFree(c->counter);
   net_f32_destroy(c->wf32);
-  net_tc_destroy(c->wtc);
+  net_tc_destroy(c->wtc[0]);
+  net_tc_destroy(c->wtc[1]);
   cudaFree(c->ws);
   if (c->err_host) cudaFreeHost(c->err_host);
   cudaFree(c->h_density);
@@ -376,12 +377,15 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
       e = net_f32_forward(c->wf32, img, c->ws, c->ws_bytes, s);
       break;
     case NSL_PREC_BF16:
-      if (!c->wtc) {
-        c->wtc = net_tc_create(c->params.data(), c->layout, &e);
-        if (!c->wtc) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");
+    case NSL_PREC_F16: {
+      const int elem = precision == NSL_PREC_BF16 ? 1 : 0;
+      if (!c->wtc[elem]) {
+        c->wtc[elem] = net_tc_create(c->params.data(), c->layout, elem, &e);
+        if (!c->wtc[elem]) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");
       }
-      e = net_tc_forward(c->wtc, c->wf32, img, c->ws, c->ws_bytes, c->err_dev, s);
+      e = net_tc_forward(c->wtc[elem], c->wf32, img, c->ws, c->ws_bytes, c->err_dev, s);
       break;
+    }
     default:
       return fail(NSL_ERR_UNSUPPORTED, "nsl_predict_lightmaps: precision %d not built", precision);
   }

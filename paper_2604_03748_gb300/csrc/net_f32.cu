@@ -15,10 +15,24 @@ enum InMode { IN_PLAIN = 0, IN_POOL = 1, IN_CONCAT = 2, IN_GUIDE = 3 };
 
 __device__ __forceinline__ float to_float(float v) { return v; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
 template <typename T> __device__ __forceinline__ T from_float(float v);
 template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_float<__half>(float v) {
+  return __float2half_rn(v);
+}
+// two floats rounded to a packed pair of 16-bit values
+template <typename T> __device__ __forceinline__ uint32_t pack_pair(float a, float b);
+template <> __device__ __forceinline__ uint32_t pack_pair<__nv_bfloat16>(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack_pair<__half>(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
 }
 
 constexpr int kTW = 16, kTH = 16;               // output tile (pixels)
@@ -126,11 +140,11 @@ __global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) 
         reinterpret_cast<float4*>(dst)[q] = v;
       }
     } else {
-      __align__(16) __nv_bfloat162 h[8];
+      __align__(16) uint32_t h[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        h[q] = __floats2bfloat162_rn(fmaxf(acc[2 * q] + __ldg(bias + 2 * q), 0.f),
-                                     fmaxf(acc[2 * q + 1] + __ldg(bias + 2 * q + 1), 0.f));
+        h[q] = pack_pair<TOut>(fmaxf(acc[2 * q] + __ldg(bias + 2 * q), 0.f),
+                               fmaxf(acc[2 * q + 1] + __ldg(bias + 2 * q + 1), 0.f));
       reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
       reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
     }
@@ -501,14 +515,19 @@ static cudaError_t conv(const ConvArgs& a, int cout, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// First layer (guide -> C0) on the SIMT cores with a bf16 NHWC output: the
+// First layer (guide -> C0) on the SIMT cores with a 16-bit NHWC output: the
 // tensor-core path starts at the second layer (K = 27 is too narrow a GEMM).
-cudaError_t simt_first_conv_bf16(const NetF32Weights* w, const NetImage& img, __nv_bfloat16* out,
+template <typename T>
+cudaError_t simt_first_conv_half(const NetF32Weights* w, const NetImage& img, T* out,
                                  cudaStream_t s) {
   ConvArgs a{img.guide, nullptr, net_f32_conv_w(w, 0), net_f32_conv_b(w, 0), out, img.H, img.W,
              img.depth_scale};
-  return conv<3, IN_GUIDE, __nv_bfloat16>(a, 16, s);
+  return conv<3, IN_GUIDE, T>(a, 16, s);
 }
+template cudaError_t simt_first_conv_half<__nv_bfloat16>(const NetF32Weights*, const NetImage&,
+                                                         __nv_bfloat16*, cudaStream_t);
+template cudaError_t simt_first_conv_half<__half>(const NetF32Weights*, const NetImage&, __half*,
+                                                  cudaStream_t);
 
 template <typename TA>
 cudaError_t adapters_forward(const NetF32Weights* w, const TA* F, TA* x1, float* partial, float* att,
@@ -529,6 +548,8 @@ template cudaError_t adapters_forward<float>(const NetF32Weights*, const float*,
 template cudaError_t adapters_forward<__nv_bfloat16>(const NetF32Weights*, const __nv_bfloat16*,
                                                      __nv_bfloat16*, float*, float*, float*, int,
                                                      int, cudaStream_t);
+template cudaError_t adapters_forward<__half>(const NetF32Weights*, const __half*, __half*, float*,
+                                              float*, float*, int, int, cudaStream_t);
 
 size_t adapter_partial_floats(int max_w, int max_h) {
   return (size_t)((max_w + kAdTW - 1) / kAdTW) * ((max_h + kAdTH - 1) / kAdTH) * 64;

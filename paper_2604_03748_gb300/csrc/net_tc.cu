@@ -119,13 +119,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+// Instruction descriptor of kind::f16: D f32, A and B of format `fmt` (0 FP16,
+// 1 BF16; both operands always the same type), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16kind(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+__device__ __forceinline__ void mma_f16kind(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -157,11 +158,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint4 bf16x8_max(uint4 a, uint4 b) {
+// 16-bit operand types of kind::f16: BF16 (format code 1) and FP16 (code 0).
+template <typename T> struct Half;
+template <> struct Half<__nv_bfloat16> {
+  using T2 = __nv_bfloat162;
+  static constexpr uint32_t kFmt = 1;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+  static __host__ __device__ __forceinline__ __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+};
+template <> struct Half<__half> {
+  using T2 = __half2;
+  static constexpr uint32_t kFmt = 0;
+  static __device__ __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+  static __host__ __device__ __forceinline__ __half from(float v) { return __float2half_rn(v); }
+};
+
+template <typename T>
+__device__ __forceinline__ uint4 half8_max(uint4 a, uint4 b) {
+  using T2 = typename Half<T>::T2;
   uint4 r;
-  const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
-  const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&b);
-  __nv_bfloat162* pr = reinterpret_cast<__nv_bfloat162*>(&r);
+  const T2* pa = reinterpret_cast<const T2*>(&a);
+  const T2* pb = reinterpret_cast<const T2*>(&b);
+  T2* pr = reinterpret_cast<T2*>(&r);
 #pragma unroll
   for (int i = 0; i < 4; ++i) pr[i] = __hmax2(pa[i], pb[i]);
   return r;
@@ -175,20 +193,21 @@ __device__ __forceinline__ void record_error(unsigned int* err, unsigned int cod
   if (err) atomicOr_system(err, code);
 }
 
+template <typename T>
 struct TcConvArgs {
-  const __nv_bfloat16* inA;  // NHWC input (POOL: at 2H x 2W; CONCAT: first CIN/2 channels)
-  const __nv_bfloat16* inB;  // CONCAT: last CIN/2 channels (the skip tensor)
+  const T* inA;              // NHWC input (POOL: at 2H x 2W; CONCAT: first CIN/2 channels)
+  const T* inB;              // CONCAT: last CIN/2 channels (the skip tensor)
   const uint8_t* wpack;      // [n tiles][9 taps][CIN/16][NT rows x 32 bytes]
   const float* bias;         // [COUT]
-  __nv_bfloat16* out;        // NHWC [H][W][COUT]
+  T* out;                    // NHWC [H][W][COUT]
   int H, W;                  // convolution (output) size
   int tiles_x, tiles_y;      // M tiles per row / column
   unsigned int* err;
 };
 
 // Stage the halo of M tile `tile` into `halo` (CIN/8 planes of 180 x 16 bytes).
-template <int CIN, int MODE>
-__device__ __forceinline__ void load_halo(const TcConvArgs& a, int tile, uint8_t* halo) {
+template <typename T, int CIN, int MODE>
+__device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint8_t* halo) {
   constexpr int G = CIN / 8;
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
@@ -207,33 +226,33 @@ __device__ __forceinline__ void load_halo(const TcConvArgs& a, int tile, uint8_t
           v = ldg128(a.inB + ((size_t)y * a.W + x) * CH + (g - G / 2) * 8);
       } else {  // TC_POOL: 2x2 max of the finer level
         const size_t W2 = 2 * (size_t)a.W;
-        const __nv_bfloat16* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 8;
-        v = bf16x8_max(bf16x8_max(ldg128(p), ldg128(p + CIN)),
-                       bf16x8_max(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
+        const T* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 8;
+        v = half8_max<T>(half8_max<T>(ldg128(p), ldg128(p + CIN)),
+                         half8_max<T>(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
       }
     }
     *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = v;
   }
 }
 
-template <int NT>
-__device__ __forceinline__ void conv_epilogue(const TcConvArgs& a, int tile, uint32_t tacc,
+template <typename T, int NT>
+__device__ __forceinline__ void conv_epilogue(const TcConvArgs<T>& a, int tile, uint32_t tacc,
                                               int n0, int cout) {
   const int warp = threadIdx.x >> 5;
   const int m = threadIdx.x;  // accumulator row = pixel of the patch
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
   const bool valid = y < a.H && x < a.W;
-  __nv_bfloat16* dst = a.out + ((size_t)y * a.W + x) * cout + n0;
+  T* dst = a.out + ((size_t)y * a.W + x) * cout + n0;
 #pragma unroll
   for (int c = 0; c < NT; c += 16) {
     float v[16];
     tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c, v);
-    __align__(16) __nv_bfloat162 h[8];
+    __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      h[q] = __floats2bfloat162_rn(fmaxf(v[2 * q] + __ldg(a.bias + n0 + c + 2 * q), 0.f),
-                                   fmaxf(v[2 * q + 1] + __ldg(a.bias + n0 + c + 2 * q + 1), 0.f));
+      h[q] = Half<T>::pack(fmaxf(v[2 * q] + __ldg(a.bias + n0 + c + 2 * q), 0.f),
+                           fmaxf(v[2 * q + 1] + __ldg(a.bias + n0 + c + 2 * q + 1), 0.f));
     if (valid) {
       reinterpret_cast<uint4*>(dst + c)[0] = reinterpret_cast<const uint4*>(h)[0];
       reinterpret_cast<uint4*>(dst + c)[1] = reinterpret_cast<const uint4*>(h)[1];
@@ -257,8 +276,8 @@ struct ConvCfg {
   static constexpr int SMEM = WBYTES + 2 * HBYTES + 64;  // + barriers and TMEM slot
 };
 
-template <int CIN, int COUT, int NT, int MODE>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
+template <typename T, int CIN, int COUT, int NT, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   using Cfg = ConvCfg<CIN, COUT, NT>;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* wsm = smem;
@@ -292,11 +311,11 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 1u);
 
-  constexpr uint32_t idesc = idesc_bf16(128, NT);
+  constexpr uint32_t idesc = idesc_f16kind(Half<T>::kFmt, 128, NT);
   uint32_t phase[2] = {0u, 0u};
   int buf = 0, prev = -1, prevbuf = 0;
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-    load_halo<CIN, MODE>(a, tile, halo + buf * Cfg::HBYTES);
+    load_halo<T, CIN, MODE>(a, tile, halo + buf * Cfg::HBYTES);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -312,7 +331,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
         for (int j = 0; j < Cfg::KS; ++j, ++kk) {
           const uint64_t ad = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
           const uint64_t bd = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
-          mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          mma_f16kind(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
         }
       }
       mma_commit(&bars[1 + buf]);
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
         ok = false;
       } else {
         tc_fence_after();
-        conv_epilogue<NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+        conv_epilogue<T, NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
       }
       phase[prevbuf] ^= 1u;
     }
@@ -336,7 +355,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
       record_error(a.err, 2u);
     } else {
       tc_fence_after();
-      conv_epilogue<NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+      conv_epilogue<T, NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
     }
   }
   tc_fence_before();
@@ -349,11 +368,12 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs a) {
 // N = 4 x COUT ordered [sub-position (a,b)][co], K = CIN.  Output pixel
 // (2y+a, 2x+b) channel co = bias + sum_ci W[ci][co][a][b] in(y, x)[ci].
 // ---------------------------------------------------------------------------
+template <typename T>
 struct TcConvTArgs {
-  const __nv_bfloat16* in;   // NHWC [H][W][CIN]
+  const T* in;               // NHWC [H][W][CIN]
   const uint8_t* wpack;      // [CIN/16][N rows x 32 bytes]
   const float* bias;         // [COUT]
-  __nv_bfloat16* out;        // NHWC [2H][2W][COUT]
+  T* out;                    // NHWC [2H][2W][COUT]
   int H, W, tiles_x, tiles_y;
   unsigned int* err;
 };
@@ -370,8 +390,8 @@ struct ConvTCfg {
   static constexpr int SMEM = WBYTES + 2 * ABYTES + 64;
 };
 
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs a) {
+template <typename T, int CIN, int COUT>
+__global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   using Cfg = ConvTCfg<CIN, COUT>;
   constexpr int N = Cfg::N;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -403,7 +423,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs a) {
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 4u);
 
-  constexpr uint32_t idesc = idesc_bf16(128, N);
+  constexpr uint32_t idesc = idesc_f16kind(Half<T>::kFmt, 128, N);
   uint32_t phase[2] = {0u, 0u};
   int buf = 0, prev = -1, prevbuf = 0;
 
@@ -419,13 +439,13 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs a) {
       tmem_ld16(tacc + c, v);
       const int k = c / COUT, co = c % COUT;
       const int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
-      __align__(16) __nv_bfloat162 h[8];
+      __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        h[q] = __floats2bfloat162_rn(v[2 * q] + __ldg(a.bias + co + 2 * q),
-                                     v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1));
+        h[q] = Half<T>::pack(v[2 * q] + __ldg(a.bias + co + 2 * q),
+                             v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1));
       if (valid) {
-        __nv_bfloat16* dst = a.out + ((size_t)oy * (2 * a.W) + ox) * COUT + co;
+        T* dst = a.out + ((size_t)oy * (2 * a.W) + ox) * COUT + co;
         reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
         reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
       }
@@ -466,7 +486,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs a) {
       for (int j = 0; j < CIN / 16; ++j) {
         const uint64_t ad = smem_desc(ab + (uint32_t)(2 * j * Cfg::APLANE), Cfg::APLANE, 128);
         const uint64_t bd = smem_desc(wb + (uint32_t)(j * N * 32), N * 16, 128);
-        mma_bf16(d, ad, bd, idesc, j > 0 ? 1u : 0u);
+        mma_f16kind(d, ad, bd, idesc, j > 0 ? 1u : 0u);
       }
       mma_commit(&bars[1 + (Cfg::NBUF == 2 ? buf : 0)]);
     }
@@ -530,6 +550,7 @@ static cudaError_t configure(K kernel, int smem_needed, int tmem_cols, Launch* L
 }
 
 // Pack a 3x3 conv weight [cout][cin][3][3] (float) into the B-operand tiles.
+template <typename T>
 static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uint8_t>& out) {
   const int KS = cin / 16;
   const size_t slice = (size_t)NT * 32;
@@ -542,7 +563,7 @@ static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uin
           for (int k = 0; k < 16; ++k) {
             const int co = nt * NT + n, ci = j * 16 + k;
             const float v = w[((size_t)co * cin + ci) * 9 + tap];
-            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            T b = Half<T>::from(v);
             const size_t off = (size_t)(k / 8) * NT * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
             std::memcpy(s + off, &b, 2);
           }
@@ -551,6 +572,7 @@ static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uin
 
 // Pack a transposed-conv weight [cin][cout][2][2] into B tiles with rows
 // n = (2a+b)*cout + co and K = cin.
+template <typename T>
 static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& out) {
   const int N = 4 * cout;
   const size_t slice = (size_t)N * 32;
@@ -561,7 +583,7 @@ static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& 
       for (int k = 0; k < 16; ++k) {
         const int kpos = n / cout, co = n % cout, ci = j * 16 + k;
         const float v = w[((size_t)ci * cout + co) * 4 + kpos];
-        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        T b = Half<T>::from(v);
         const size_t off = (size_t)(k / 8) * N * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
         std::memcpy(s + off, &b, 2);
       }
@@ -571,6 +593,7 @@ static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& 
 }  // namespace
 
 struct NetTcWeights {
+  int elem = 0;              // 0 FP16 operands, 1 BF16 operands
   uint8_t* conv_w[14] = {};  // layer 0 stays on the SIMT path
   float* conv_b[14] = {};
   int conv_nt[14] = {};
@@ -579,34 +602,41 @@ struct NetTcWeights {
   std::vector<void*> allocs;
 };
 
-template <typename T>
-static T* dev_copy(NetTcWeights* w, const T* src, size_t n, cudaError_t* err) {
+template <typename V>
+static V* dev_copy(NetTcWeights* w, const V* src, size_t n, cudaError_t* err) {
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  cudaError_t e = cudaMalloc(&p, n * sizeof(V));
   if (e != cudaSuccess) { *err = e; return nullptr; }
   w->allocs.push_back(p);
-  e = cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(p, src, n * sizeof(V), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) *err = e;
-  return static_cast<T*>(p);
+  return static_cast<V*>(p);
 }
 
-NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, cudaError_t* err) {
-  *err = cudaSuccess;
-  NetTcWeights* w = new NetTcWeights();
+template <typename T>
+static void fill_weights(NetTcWeights* w, const float* hp, const NetLayout& L, cudaError_t* err) {
   std::vector<uint8_t> pk;
   for (int l = 1; l < 14; ++l) {
     const int cin = L.conv_cin[l], cout = L.conv_cout[l];
     const int NT = conv_nt(cin, cout);
     w->conv_nt[l] = NT;
-    pack_conv(hp + L.conv_w[l], cin, cout, NT, pk);
+    pack_conv<T>(hp + L.conv_w[l], cin, cout, NT, pk);
     w->conv_w[l] = dev_copy(w, pk.data(), pk.size(), err);
     w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
   }
   for (int l = 0; l < 3; ++l) {
-    pack_convT(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk);
+    pack_convT<T>(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk);
     w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
     w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
   }
+}
+
+NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, int elem, cudaError_t* err) {
+  *err = cudaSuccess;
+  NetTcWeights* w = new NetTcWeights();
+  w->elem = elem;
+  if (elem == 1) fill_weights<__nv_bfloat16>(w, hp, L, err);
+  else fill_weights<__half>(w, hp, L, err);
   if (*err != cudaSuccess) { net_tc_destroy(w); return nullptr; }
   return w;
 }
@@ -618,110 +648,119 @@ void net_tc_destroy(NetTcWeights* w) {
 }
 
 namespace {
+template <typename T>
 struct TcBuffers {
-  __nv_bfloat16 *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1;
+  T *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1;
   float *partial, *att;
 };
 
-size_t carve_tc(size_t P, size_t partial_floats, TcBuffers* b, char* base) {
+template <typename T>
+size_t carve_tc(size_t P, size_t partial_floats, TcBuffers<T>* b, char* base) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
     off += (bytes + 255) / 256 * 256;
     return p;
   };
-  auto bf = [&](size_t n) { return reinterpret_cast<__nv_bfloat16*>(take(n * 2)); };
-  b->fa = bf(P * 16); b->fb = bf(P * 16); b->s1 = bf(P * 16);
-  b->l1a = bf(P / 4 * 32); b->l1b = bf(P / 4 * 32); b->s2 = bf(P / 4 * 32);
-  b->l2a = bf(P / 16 * 64); b->l2b = bf(P / 16 * 64); b->s3 = bf(P / 16 * 64);
-  b->l3a = bf(P / 64 * 128); b->l3b = bf(P / 64 * 128);
-  b->x1 = bf(P * 64);
+  auto hf = [&](size_t n) { return reinterpret_cast<T*>(take(n * sizeof(T))); };
+  b->fa = hf(P * 16); b->fb = hf(P * 16); b->s1 = hf(P * 16);
+  b->l1a = hf(P / 4 * 32); b->l1b = hf(P / 4 * 32); b->s2 = hf(P / 4 * 32);
+  b->l2a = hf(P / 16 * 64); b->l2b = hf(P / 16 * 64); b->s3 = hf(P / 16 * 64);
+  b->l3a = hf(P / 64 * 128); b->l3b = hf(P / 64 * 128);
+  b->x1 = hf(P * 64);
   b->partial = reinterpret_cast<float*>(take(partial_floats * 4));
   b->att = reinterpret_cast<float*>(take(64 * 4));
   return off;
 }
 
-template <int CIN, int COUT, int MODE>
-cudaError_t run_conv(const NetTcWeights* w, int l, const __nv_bfloat16* inA,
-                     const __nv_bfloat16* inB, __nv_bfloat16* out, int H, int W,
-                     unsigned int* err, cudaStream_t s) {
+template <typename T, int CIN, int COUT, int MODE>
+cudaError_t run_conv(const NetTcWeights* w, int l, const T* inA, const T* inB, T* out, int H,
+                     int W, unsigned int* err, cudaStream_t s) {
   constexpr int NT = conv_nt(CIN, COUT);
   using Cfg = ConvCfg<CIN, COUT, NT>;
   static_assert(Cfg::SMEM <= 232448, "shared memory budget");
   static Launch L;
   static bool init = false;
   if (!init) {
-    cudaError_t e = configure(conv3x3_tc_kernel<CIN, COUT, NT, MODE>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    cudaError_t e =
+        configure(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
     if (e != cudaSuccess) return e;
     init = true;
   }
-  TcConvArgs a{inA, inB, w->conv_w[l], w->conv_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
-               (H + kPatchH - 1) / kPatchH, err};
+  TcConvArgs<T> a{inA, inB, w->conv_w[l], w->conv_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
+                  (H + kPatchH - 1) / kPatchH, err};
   const int ntiles = a.tiles_x * a.tiles_y;
   int grid = kNumSMs * L.per_sm / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  conv3x3_tc_kernel<CIN, COUT, NT, MODE><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
+  conv3x3_tc_kernel<T, CIN, COUT, NT, MODE><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
-cudaError_t run_convT(const NetTcWeights* w, int l, const __nv_bfloat16* in, __nv_bfloat16* out,
-                      int H, int W, unsigned int* err, cudaStream_t s) {
+template <typename T, int CIN, int COUT>
+cudaError_t run_convT(const NetTcWeights* w, int l, const T* in, T* out, int H, int W,
+                      unsigned int* err, cudaStream_t s) {
   using Cfg = ConvTCfg<CIN, COUT>;
   static Launch L;
   static bool init = false;
   if (!init) {
-    cudaError_t e = configure(convT_tc_kernel<CIN, COUT>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
     if (e != cudaSuccess) return e;
     init = true;
   }
-  TcConvTArgs a{in, w->up_w[l], w->up_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
-                (H + kPatchH - 1) / kPatchH, err};
+  TcConvTArgs<T> a{in, w->up_w[l], w->up_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
+                   (H + kPatchH - 1) / kPatchH, err};
   const int ntiles = a.tiles_x * a.tiles_y;
   int grid = kNumSMs * L.per_sm;
   if (grid > ntiles) grid = ntiles;
-  convT_tc_kernel<CIN, COUT><<<grid, 128, L.smem, s>>>(a);
+  convT_tc_kernel<T, CIN, COUT><<<grid, 128, L.smem, s>>>(a);
   return cudaGetLastError();
 }
-}  // namespace
 
-size_t net_tc_workspace_bytes(int max_w, int max_h) {
-  TcBuffers b;
-  return carve_tc((size_t)max_w * max_h, adapter_partial_floats(max_w, max_h), &b, nullptr);
-}
-
-cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
-                           void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
+template <typename T>
+cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
+                    void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
   const int H = img.H, W = img.W;
   const size_t P = (size_t)H * W;
-  TcBuffers B;
+  TcBuffers<T> B;
   const size_t pf = adapter_partial_floats(W, H);
   if (carve_tc(P, pf, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
   carve_tc(P, pf, &B, static_cast<char*>(workspace));
   cudaError_t e;
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
   const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
-  TRY(simt_first_conv_bf16(wf, img, B.fa, s));
-  TRY((run_conv<16, 16, TC_PLAIN>(w, 1, B.fa, nullptr, B.s1, H, W, err, s)));
-  TRY((run_conv<16, 32, TC_POOL>(w, 2, B.s1, nullptr, B.l1a, H1, W1, err, s)));
-  TRY((run_conv<32, 32, TC_PLAIN>(w, 3, B.l1a, nullptr, B.s2, H1, W1, err, s)));
-  TRY((run_conv<32, 64, TC_POOL>(w, 4, B.s2, nullptr, B.l2a, H2, W2, err, s)));
-  TRY((run_conv<64, 64, TC_PLAIN>(w, 5, B.l2a, nullptr, B.s3, H2, W2, err, s)));
-  TRY((run_conv<64, 128, TC_POOL>(w, 6, B.s3, nullptr, B.l3a, H3, W3, err, s)));
-  TRY((run_conv<128, 128, TC_PLAIN>(w, 7, B.l3a, nullptr, B.l3b, H3, W3, err, s)));
-  TRY((run_convT<128, 64>(w, 0, B.l3b, B.l2a, H3, W3, err, s)));
-  TRY((run_conv<128, 64, TC_CONCAT>(w, 8, B.l2a, B.s3, B.l2b, H2, W2, err, s)));
-  TRY((run_conv<64, 64, TC_PLAIN>(w, 9, B.l2b, nullptr, B.l2a, H2, W2, err, s)));
-  TRY((run_convT<64, 32>(w, 1, B.l2a, B.l1a, H2, W2, err, s)));
-  TRY((run_conv<64, 32, TC_CONCAT>(w, 10, B.l1a, B.s2, B.l1b, H1, W1, err, s)));
-  TRY((run_conv<32, 32, TC_PLAIN>(w, 11, B.l1b, nullptr, B.l1a, H1, W1, err, s)));
-  TRY((run_convT<32, 16>(w, 2, B.l1a, B.fa, H1, W1, err, s)));
-  TRY((run_conv<32, 16, TC_CONCAT>(w, 12, B.fa, B.s1, B.fb, H, W, err, s)));
-  TRY((run_conv<16, 16, TC_PLAIN>(w, 13, B.fb, nullptr, B.fa, H, W, err, s)));
-  TRY(adapters_forward<__nv_bfloat16>(wf, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  TRY(simt_first_conv_half<T>(wf, img, B.fa, s));
+  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 1, B.fa, nullptr, B.s1, H, W, err, s)));
+  TRY((run_conv<T, 16, 32, TC_POOL>(w, 2, B.s1, nullptr, B.l1a, H1, W1, err, s)));
+  TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 3, B.l1a, nullptr, B.s2, H1, W1, err, s)));
+  TRY((run_conv<T, 32, 64, TC_POOL>(w, 4, B.s2, nullptr, B.l2a, H2, W2, err, s)));
+  TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 5, B.l2a, nullptr, B.s3, H2, W2, err, s)));
+  TRY((run_conv<T, 64, 128, TC_POOL>(w, 6, B.s3, nullptr, B.l3a, H3, W3, err, s)));
+  TRY((run_conv<T, 128, 128, TC_PLAIN>(w, 7, B.l3a, nullptr, B.l3b, H3, W3, err, s)));
+  TRY((run_convT<T, 128, 64>(w, 0, B.l3b, B.l2a, H3, W3, err, s)));
+  TRY((run_conv<T, 128, 64, TC_CONCAT>(w, 8, B.l2a, B.s3, B.l2b, H2, W2, err, s)));
+  TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 9, B.l2b, nullptr, B.l2a, H2, W2, err, s)));
+  TRY((run_convT<T, 64, 32>(w, 1, B.l2a, B.l1a, H2, W2, err, s)));
+  TRY((run_conv<T, 64, 32, TC_CONCAT>(w, 10, B.l1a, B.s2, B.l1b, H1, W1, err, s)));
+  TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 11, B.l1b, nullptr, B.l1a, H1, W1, err, s)));
+  TRY((run_convT<T, 32, 16>(w, 2, B.l1a, B.fa, H1, W1, err, s)));
+  TRY((run_conv<T, 32, 16, TC_CONCAT>(w, 12, B.fa, B.s1, B.fb, H, W, err, s)));
+  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 13, B.fb, nullptr, B.fa, H, W, err, s)));
+  TRY(adapters_forward<T>(wf, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
 #undef TRY
   return cudaSuccess;
+}
+}  // namespace
+
+size_t net_tc_workspace_bytes(int max_w, int max_h) {
+  TcBuffers<__half> b;
+  return carve_tc((size_t)max_w * max_h, adapter_partial_floats(max_w, max_h), &b, nullptr);
+}
+
+cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
+                           void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
+  if (w->elem == 1) return forward<__nv_bfloat16>(w, wf, img, workspace, ws_bytes, err, s);
+  return forward<__half>(w, wf, img, workspace, ws_bytes, err, s);
 }
 
 }  // namespace nsl

@@ -119,16 +119,19 @@ const float* net_f32_conv_b(const NetF32Weights* w, int l);
 const float* net_f32_adapters(const NetF32Weights* w);       // 4 adapters, blob order
 
 // SIMT pieces shared with the tensor-core path
-cudaError_t simt_first_conv_bf16(const NetF32Weights* w, const NetImage& img, __nv_bfloat16* out,
+template <typename T>
+cudaError_t simt_first_conv_half(const NetF32Weights* w, const NetImage& img, T* out,
                                  cudaStream_t s);
 template <typename TA>
 cudaError_t adapters_forward(const NetF32Weights* w, const TA* F, TA* x1, float* partial,
                              float* att, float* out, int H, int W, cudaStream_t s);
 size_t adapter_partial_floats(int max_w, int max_h);
 
-// tensor-core (tcgen05) network, BF16 operands, FP32 accumulation in TMEM
+// tensor-core (tcgen05) network, 16-bit operands (elem 0 = FP16, 1 = BF16),
+// FP32 accumulation in TMEM
 struct NetTcWeights;
-NetTcWeights* net_tc_create(const float* host_params, const NetLayout& L, cudaError_t* err);
+NetTcWeights* net_tc_create(const float* host_params, const NetLayout& L, int elem,
+                            cudaError_t* err);
 void net_tc_destroy(NetTcWeights* w);
 size_t net_tc_workspace_bytes(int max_w, int max_h);
 cudaError_t net_tc_forward(const NetTcWeights* wt, const NetF32Weights* wf, const NetImage& img,

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libnsl.so")
 
 NSL_OK, NSL_ERR_INVALID_ARG, NSL_ERR_OOM, NSL_ERR_CUDA, NSL_ERR_UNSUPPORTED, NSL_ERR_TIMEOUT, NSL_ERR_BUDGET = range(7)
 NSL_F32, NSL_F16 = 0, 1
-NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8 = 0, 1, 2
+NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8, NSL_PREC_F16 = 0, 1, 2, 3
 NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
 
 # every symbol include/nsl.h declares

@@ -186,36 +186,40 @@ def test_net_f32_parity_on_oracle_guide_512(lib, orc):
     ctx.close()
 
 
+HALF_PRECISIONS = [("f16", 3, "TOL_NET_F16"), ("bf16", 1, "TOL_NET_BF16")]
+
+
+@pytest.mark.parametrize("prec", HALF_PRECISIONS, ids=[p[0] for p in HALF_PRECISIONS])
 @pytest.mark.parametrize("H,W", [(8, 8), (16, 40), (128, 128), (64, 96), (24, 136)])
-def test_net_bf16_parity(lib, orc, H, W):
-    """BF16 tensor-core network vs the FP64 oracle: within 2e-2 of each plane's range."""
-    from paper_2604_03748_gb300 import nsl
+def test_net_half_parity(lib, orc, H, W, prec):
+    """Tensor-core network (16-bit operands, FP32 accumulation) vs the FP64 oracle,
+    per plane relative to the oracle's range."""
     vol = np.zeros((64, 64, 64), np.float32)
     pf = I.PlumeFrame(vol, None, I.orbit_ortho_camera(64, 1, W, H), I.random_light(1), 4.0)
     ctx = PT.make_ctx(pf)
     guide = _guide_input(H, W, H * 5 + W)
-    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
+    got = PT.gpu_net(ctx, guide, prec[1])
     flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
     ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 64 * 64))
     errs = PT.range_err(got, ref)
-    assert max(errs) <= PT.TOL_NET_BF16, errs
+    assert max(errs) <= getattr(PT, prec[2]), errs
     ctx.close()
 
 
-def test_net_bf16_parity_on_oracle_guide_512(lib, orc):
-    """The 512^2 workload: BF16 network on the oracle's guide of the obstacle scene."""
-    from paper_2604_03748_gb300 import nsl
+@pytest.mark.parametrize("prec", HALF_PRECISIONS, ids=[p[0] for p in HALF_PRECISIONS])
+def test_net_half_parity_on_oracle_guide_512(lib, orc, prec):
+    """The 512^2 workload: tensor-core network on the oracle's guide of the obstacle scene."""
     pf = I.config_obstacle_128()
     o, _, _ = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
     guide = o.astype(np.float32).astype(np.float64)
     ctx = PT.make_ctx(pf)
-    got = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
-    again = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16)
+    got = PT.gpu_net(ctx, guide, prec[1])
+    again = PT.gpu_net(ctx, guide, prec[1])
     assert np.array_equal(got, again)          # deterministic
     flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
     ref = orc.net_forward(guide, flat, 16, 1.0 / math.sqrt(3 * 128 * 128))
     errs = PT.range_err(got, ref)
-    assert max(errs) <= PT.TOL_NET_BF16, errs
+    assert max(errs) <= getattr(PT, prec[2]), errs
     ctx.close()
 
 
@@ -232,14 +236,18 @@ def test_shade_parity(lib, orc):
     lights = [I.random_light(s) for s in range(5)]
     pf = I.PlumeFrame(np.zeros((8, 8, 8), np.float32), None, cam, lights[0], 1.0)
     ctx = PT.make_ctx(pf)
-    out = torch.empty((4, H, W), device="cuda")
-    ctx.shade(torch.from_numpy(lm).cuda(), W, H, cam, lights, out)
-    ref = orc.shade(lm.astype(np.float64), cam, lights)
+    lm_dev = torch.from_numpy(lm).cuda()
+    out = torch.full((4, H, W), float("nan"), device="cuda")
+    ctx.shade(lm_dev, W, H, cam, lights, out)
     torch.cuda.synchronize()
-    errs = PT.range_err(out.cpu().numpy().astype(np.float64), ref)
+    got = out.cpu().numpy().astype(np.float64)
+    ref = orc.shade(lm.astype(np.float64), cam, lights)
+    errs = PT.range_err(got, ref)
     assert max(errs) <= PT.TOL_SHADE, errs
     # no lights: emissive and alpha only
-    ctx.shade(torch.from_numpy(lm).cuda(), W, H, cam, [], out)
+    out.fill_(float("nan"))
+    ctx.shade(lm_dev, W, H, cam, [], out)
+    torch.cuda.synchronize()
     ref = orc.shade(lm.astype(np.float64), cam, [])
     assert max(PT.range_err(out.cpu().numpy().astype(np.float64), ref)) <= PT.TOL_SHADE
     ctx.close()
