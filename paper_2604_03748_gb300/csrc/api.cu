@@ -104,6 +104,7 @@ struct nsl_ctx {
   float* staged = nullptr;          // staged extinction grid
   bool staged_valid = false;        // a staging has been queued
   unsigned long long* counter = nullptr;  // sample-count scratch
+  int* tile_counter = nullptr;            // march tile queue (scratch)
   NetF32Weights* wf32 = nullptr;
   NetTcWeights* wtc[2] = {};        // tensor-core weights: [0] FP16, [1] BF16 (built on first use)
   void* ws = nullptr;               // network workspace (shared by both precisions)
@@ -198,8 +199,10 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   c->params.resize(nf);
   std::memcpy(c->params.data(), b + 16, (size_t)nf * 4);
   cudaGetDevice(&c->device);
-  cudaError_t e = cudaMalloc(&c->staged, grid_voxels(*grid) * sizeof(float));
+  cudaError_t e = cudaMalloc(&c->staged, staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float));
   if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: staged grid"); }
+  e = cudaMalloc(&c->tile_counter, 256);
+  if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: tile counter"); }
   c->wf32 = net_f32_create(c->params.data(), L, &e);
   if (!c->wf32) { nsl_destroy(c); return cuda_fail(e, "nsl_create: FP32 weights"); }
   c->ws_bytes = net_f32_workspace_bytes(max_width, max_height);
@@ -223,6 +226,7 @@ void nsl_destroy(nsl_ctx* c) {
   cudaDeviceSynchronize();
   cudaFree(c->staged);
   cudaFree(c->counter);
+  cudaFree(c->tile_counter);
   net_f32_destroy(c->wf32);
   net_tc_destroy(c->wtc[0]);
   net_tc_destroy(c->wtc[1]);
@@ -271,8 +275,8 @@ nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, 
   if (!density) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: density is NULL");
   if (!aligned16(density) || (mask && !aligned16(mask)))
     return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: buffers must be 16-byte aligned");
-  cudaError_t e = launch_stage_volume(density, c->grid.dtype, mask, grid_voxels(c->grid),
-                                      c->grid.sigma_scale, c->staged,
+  cudaError_t e = launch_stage_volume(density, c->grid.dtype, mask, c->grid.nx, c->grid.ny,
+                                      c->grid.nz, c->grid.sigma_scale, c->staged,
                                       static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_stage_grid");
   c->staged_valid = true;
@@ -328,7 +332,7 @@ nsl_status nsl_guiding_map(nsl_ctx* c, const void* density, const uint8_t* mask,
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: density is NULL and no grid is staged");
   }
   p.guide = guide;
-  cudaError_t e = launch_march(p, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_march(p, c->tile_counter, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map: march");
   return NSL_OK;
 }
@@ -345,7 +349,7 @@ nsl_status nsl_guide_sample_count(nsl_ctx* c, const nsl_camera* cam, float step,
   if (!c->counter) NSL_CUDA_TRY(cudaMalloc(&c->counter, sizeof(unsigned long long)));
   NSL_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));
   p.counter = c->counter;
-  NSL_CUDA_TRY(launch_march(p, s, true));
+  NSL_CUDA_TRY(launch_march(p, c->tile_counter, s, true));
   NSL_CUDA_TRY(cudaMemcpyAsync(out, c->counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   NSL_CUDA_TRY(cudaStreamSynchronize(s));
   return NSL_OK;

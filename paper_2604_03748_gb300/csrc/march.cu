@@ -24,37 +24,36 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
 }
 
 struct Grid {
-  const float* __restrict__ v;
+  const float4* __restrict__ q;  // quad-staged grid, see stage_quad_kernel
   int nx, ny, nz;
-  float fx, fy, fz;  // box extents
+  float fx, fy, fz;              // box extents
 };
 
 // Extinction at p: 0 outside the closed box [0,n]; trilinear interpolation of
-// the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.
+// the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.  The
+// grid is staged as quads: cell (i,j,k) holds the x/y 2x2 neighbourhood
+// (rho(i,j), rho(i+1,j), rho(i,j+1), rho(i+1,j+1)) of slice k with the +1
+// indices clamped to the edge, so one sample is two 16-byte loads (slices k0,
+// k1).  On the low edge (index -1) both x (or y) corners are voxel 0, which the
+// zero interpolation weight reproduces.
 __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, float pz) {
   if (!(px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz)) return 0.f;
   float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
   float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  int x0 = max(ix, 0), x1 = min(ix + 1, g.nx - 1);
-  int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
-  int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
-  size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
-  const float* r00 = g.v + z0 * sz + y0 * sy;
-  const float* r01 = g.v + z0 * sz + y1 * sy;
-  const float* r10 = g.v + z1 * sz + y0 * sy;
-  const float* r11 = g.v + z1 * sz + y1 * sy;
-  float v000 = __ldg(r00 + x0), v100 = __ldg(r00 + x1);
-  float v010 = __ldg(r01 + x0), v110 = __ldg(r01 + x1);
-  float v001 = __ldg(r10 + x0), v101 = __ldg(r10 + x1);
-  float v011 = __ldg(r11 + x0), v111 = __ldg(r11 + x1);
-  float c00 = fmaf(tx, v100 - v000, v000);
-  float c10 = fmaf(tx, v110 - v010, v010);
-  float c01 = fmaf(tx, v101 - v001, v001);
-  float c11 = fmaf(tx, v111 - v011, v011);
-  float c0 = fmaf(ty, c10 - c00, c00);
-  float c1 = fmaf(ty, c11 - c01, c01);
+  if (ix < 0) { ix = 0; tx = 0.f; }
+  if (iy < 0) { iy = 0; ty = 0.f; }
+  const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
+  const size_t row = (size_t)iy * g.nx + ix, plane = (size_t)g.nx * g.ny;
+  const float4 a = __ldg(g.q + z0 * plane + row);
+  const float4 b = __ldg(g.q + z1 * plane + row);
+  const float c00 = fmaf(tx, a.y - a.x, a.x);
+  const float c10 = fmaf(tx, a.w - a.z, a.z);
+  const float c01 = fmaf(tx, b.y - b.x, b.x);
+  const float c11 = fmaf(tx, b.w - b.z, b.z);
+  const float c0 = fmaf(ty, c10 - c00, c00);
+  const float c1 = fmaf(ty, c11 - c01, c01);
   return fmaf(tz, c1 - c0, c0);
 }
 
@@ -63,13 +62,10 @@ __device__ __forceinline__ float hg_phase(float g, float c) {
   return (1.f - g * g) / (12.566370614359172f * den * sqrtf(den));
 }
 
-// Transmittance toward the surrogate light in direction s (unit): march at
-// step h from p to the box exit, T = exp(-h sum_k sigma(p + k h s)); stop once
-// the optical depth exceeds tau_lim (transmittance below t_min).
-template <bool kCount>
-__device__ __forceinline__ float shadow_T(const Grid& g, float px, float py, float pz, float sx,
-                                          float sy, float sz, float h, float tau_lim,
-                                          unsigned long long& nsamp) {
+// Number of shadow steps K = floor(t_exit / h) from p along the unit direction
+// s to the exit of the closed box.
+__device__ __forceinline__ int shadow_steps(const Grid& g, float px, float py, float pz, float sx,
+                                            float sy, float sz, float h) {
   float te = INFINITY;
   if (sx > 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(g.fx, px), sx));
   else if (sx < 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(0.f, px), sx));
@@ -77,26 +73,46 @@ __device__ __forceinline__ float shadow_T(const Grid& g, float px, float py, flo
   else if (sy < 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(0.f, py), sy));
   if (sz > 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(g.fz, pz), sz));
   else if (sz < 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(0.f, pz), sz));
-  int K = 0;
-  if (te > 0.f) K = (int)floorf(__fdiv_rn(te, h));
-  float tau = 0.f;
-  for (int k = 1; k <= K; ++k) {
-    float kh = __fmul_rn((float)k, h);
-    float qx = __fadd_rn(px, __fmul_rn(kh, sx));
-    float qy = __fadd_rn(py, __fmul_rn(kh, sy));
-    float qz = __fadd_rn(pz, __fmul_rn(kh, sz));
-    tau = fmaf(sigma_at(g, qx, qy, qz), h, tau);
-    if (kCount) ++nsamp;
-    if (tau > tau_lim) break;
+  return te > 0.f ? (int)floorf(__fdiv_rn(te, h)) : 0;
+}
+
+// Transmittances toward the top (+u) and bottom (-u) surrogate lights from p:
+// both rays are marched in one loop (two independent load chains), each at step
+// h to the box exit, T = exp(-h sum_k sigma(p +- k h u)), and each stops once its
+// optical depth exceeds tau_lim (transmittance below t_min).
+template <bool kCount>
+__device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, float pz,
+                                            const float u[3], float h, float tau_lim, float& Tt,
+                                            float& Tb, unsigned long long& nsamp) {
+  const int Kt = shadow_steps(g, px, py, pz, u[0], u[1], u[2], h);
+  const int Kb = shadow_steps(g, px, py, pz, -u[0], -u[1], -u[2], h);
+  float taut = 0.f, taub = 0.f;
+  bool at = Kt > 0, ab = Kb > 0;
+  const int K = max(Kt, Kb);
+  for (int k = 1; k <= K && (at || ab); ++k) {
+    const float kh = __fmul_rn((float)k, h);
+    const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
+    if (at) {
+      taut = fmaf(sigma_at(g, __fadd_rn(px, dx), __fadd_rn(py, dy), __fadd_rn(pz, dz)), h, taut);
+      if (kCount) ++nsamp;
+      if (k >= Kt || taut > tau_lim) at = false;
+    }
+    if (ab) {
+      taub = fmaf(sigma_at(g, __fsub_rn(px, dx), __fsub_rn(py, dy), __fsub_rn(pz, dz)), h, taub);
+      if (kCount) ++nsamp;
+      if (k >= Kb || taub > tau_lim) ab = false;
+    }
   }
-  return expf(-tau);
+  Tt = expf(-taut);
+  Tb = expf(-taub);
 }
 
 template <bool kCount>
 __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   unsigned long long nsamp = 0;
   const CamFrame& c = P.cam;
-  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  Grid g{reinterpret_cast<const float4*>(P.vol), P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny,
+         (float)P.nz};
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
   // ray through the pixel centre
@@ -141,7 +157,7 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   if (tn < 0.f) tn = 0.f;
   if (!(tf > tn)) hit = false;
 
-  float L = 0.f, Lc = 0.f;        // Kahan-compensated guide radiance
+  float L = 0.f, Lc = 0.f;             // Kahan-compensated guide radiance
   float T = 1.f, tau = 0.f, tc = 0.f;  // Kahan-compensated view optical depth
   float D = 0.f;
   if (hit) {
@@ -171,8 +187,8 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
       if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, h);
       if (s > 0.f) {
         float A = P.segment_exact ? T * (1.f - expf(-s * h)) : T * s * h;
-        float Tt = shadow_T<kCount>(g, px, py, pz, c.u[0], c.u[1], c.u[2], h, P.tau_lim, nsamp);
-        float Tb = shadow_T<kCount>(g, px, py, pz, -c.u[0], -c.u[1], -c.u[2], h, P.tau_lim, nsamp);
+        float Tt, Tb;
+        shadow_pair<kCount>(g, px, py, pz, c.u, h, P.tau_lim, Tt, Tb, nsamp);
         float Ln = fmaf(wf, T, fmaf(wt, Tt, wb * Tb));
         float y = __fsub_rn(A * Ln, Lc);
         float t = __fadd_rn(L, y);
@@ -205,37 +221,71 @@ __device__ __forceinline__ int find_plume(const MarchPlume* __restrict__ t, int 
   return lo;
 }
 
+// Persistent march: every warp repeatedly takes the next 8x4-pixel tile from a
+// global counter (dynamic balancing of very uneven per-pixel costs).  The
+// counter lives in library scratch and is zeroed before each launch.
 template <bool kBatch, bool kCount>
-__global__ void __launch_bounds__(kMarchTX * kMarchTY)
-march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplumes) {
-  int tile = blockIdx.x;
-  const MarchPlume* P = &single;
-  if (kBatch) {
-    P = table + find_plume(table, nplumes, tile);
-    tile -= P->tile_start;
+__global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
+march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplumes, int total_tiles,
+             int* __restrict__ tile_counter) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(tile_counter, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= total_tiles) break;
+    const MarchPlume* P = &single;
+    if (kBatch) {
+      P = table + find_plume(table, nplumes, tile);
+      tile -= P->tile_start;
+    }
+    const int tx = tile % P->tiles_x, ty = tile / P->tiles_x;
+    const int i = tx * kMarchTX + (lane % kMarchTX);
+    const int j = ty * kMarchTY + (lane / kMarchTX);
+    if (i < P->cam.W && j < P->cam.H) march_pixel<kCount>(*P, i, j);
   }
-  const int tx = tile % P->tiles_x, ty = tile / P->tiles_x;
-  const int i = tx * kMarchTX + (threadIdx.x % kMarchTX);
-  const int j = ty * kMarchTY + (threadIdx.x / kMarchTX);
-  if (i >= P->cam.W || j >= P->cam.H) return;
-  march_pixel<kCount>(*P, i, j);
 }
 
-cudaError_t launch_march(const MarchPlume& p, cudaStream_t s, bool count) {
-  int ntiles = p.tiles_x * ((p.cam.H + kMarchTY - 1) / kMarchTY);
+template <bool kBatch, bool kCount>
+static int march_grid() {
+  static int blocks = 0;
+  if (!blocks) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel<kBatch, kCount>,
+                                                      kMarchThreads, 0) != cudaSuccess || occ < 1)
+      occ = 1;
+    blocks = occ * kNumSMs;
+  }
+  return blocks;
+}
+
+int march_tiles(int W, int H) {
+  return ((W + kMarchTX - 1) / kMarchTX) * ((H + kMarchTY - 1) / kMarchTY);
+}
+
+cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s, bool count) {
+  const int ntiles = march_tiles(p.cam.W, p.cam.H);
   if (ntiles == 0) return cudaSuccess;
-  if (count)
-    march_kernel<false, true><<<ntiles, kMarchTX * kMarchTY, 0, s>>>(p, nullptr, 1);
-  else
-    march_kernel<false, false><<<ntiles, kMarchTX * kMarchTY, 0, s>>>(p, nullptr, 1);
+  cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (count) {
+    int grid = march_grid<false, true>();
+    march_kernel<false, true><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+  } else {
+    int grid = march_grid<false, false>();
+    march_kernel<false, false><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
-                               cudaStream_t s) {
+                               int* tile_counter, cudaStream_t s) {
   if (total_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   MarchPlume dummy{};
-  march_kernel<true, false><<<total_tiles, kMarchTX * kMarchTY, 0, s>>>(dummy, table_dev, nplumes);
+  march_kernel<true, false><<<march_grid<true, false>(), kMarchThreads, 0, s>>>(
+      dummy, table_dev, nplumes, total_tiles, tile_counter);
   return cudaGetLastError();
 }
 
@@ -249,47 +299,43 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
+// One thread per staged cell (i,j,k): sigma'(i,j), sigma'(i+1,j), sigma'(i,j+1),
+// sigma'(i+1,j+1) of slice k, with sigma' = scale * rho * [mask == 0] and the
+// +1 indices clamped to the grid edge.
 template <typename T>
-__global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
-                                                    const uint8_t* __restrict__ mask, size_t n,
-                                                    float scale, float* __restrict__ out) {
-  size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t n4 = n / 4;
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
-    float v[4];
-    if constexpr (sizeof(T) == 4) {
-      float4 r = __ldcs(reinterpret_cast<const float4*>(rho) + q);
-      v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
-    } else {
-      uint2 r = __ldcs(reinterpret_cast<const uint2*>(rho) + q);
-      __half2 a = *reinterpret_cast<__half2*>(&r.x), b = *reinterpret_cast<__half2*>(&r.y);
-      v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
-    }
-    uint32_t m = mask ? __ldcs(reinterpret_cast<const uint32_t*>(mask) + q) : 0u;
-    float4 o;
-    o.x = (m & 0xFFu) ? 0.f : __fmul_rn(scale, v[0]);
-    o.y = (m & 0xFF00u) ? 0.f : __fmul_rn(scale, v[1]);
-    o.z = (m & 0xFF0000u) ? 0.f : __fmul_rn(scale, v[2]);
-    o.w = (m & 0xFF000000u) ? 0.f : __fmul_rn(scale, v[3]);
-    reinterpret_cast<float4*>(out)[q] = o;
-  }
-  for (size_t k = n4 * 4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    float v = to_f<T>(rho[k]);
-    out[k] = (mask && mask[k]) ? 0.f : __fmul_rn(scale, v);
+__global__ void __launch_bounds__(256) stage_quad_kernel(const T* __restrict__ rho,
+                                                         const uint8_t* __restrict__ mask, int nx,
+                                                         int ny, int nz, float scale,
+                                                         float4* __restrict__ out) {
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx);
+    const size_t r = c / nx;
+    const int j = (int)(r % ny);
+    const size_t k = r / ny;
+    const int i1 = min(i + 1, nx - 1), j1 = min(j + 1, ny - 1);
+    const size_t b0 = (k * ny + j) * nx, b1 = (k * ny + j1) * nx;
+    auto val = [&](size_t idx) {
+      return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+    };
+    __stcs(out + c, make_float4(val(b0 + i), val(b0 + i1), val(b1 + i), val(b1 + i1)));
   }
 }
 
-cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, size_t nvox,
-                                float scale, float* staged, cudaStream_t s) {
-  int blocks = (int)((nvox / 4 + 255) / 256);
+cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
+                                int ny, int nz, float scale, float* staged, cudaStream_t s) {
+  const size_t n = (size_t)nx * ny * nz;
+  int blocks = (int)((n + 255) / 256);
   if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
   if (blocks < 1) blocks = 1;
+  float4* q = reinterpret_cast<float4*>(staged);
   if (dtype == NSL_F16)
-    stage_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(density), mask, nvox,
-                                                 scale, staged);
+    stage_quad_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(density), mask, nx,
+                                                     ny, nz, scale, q);
   else
-    stage_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(density), mask, nvox,
-                                                scale, staged);
+    stage_quad_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(density), mask, nx,
+                                                    ny, nz, scale, q);
   return cudaGetLastError();
 }
 

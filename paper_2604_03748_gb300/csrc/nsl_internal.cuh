@@ -55,14 +55,20 @@ struct MarchPlume {
   unsigned long long* counter;  // density-evaluation counter (counting variant only)
 };
 
-constexpr int kMarchTX = 8;   // march tile: 8 x 8 pixels per 64-thread block
-constexpr int kMarchTY = 8;
+constexpr int kMarchTX = 8;          // march tile: 8 x 4 pixels, one warp
+constexpr int kMarchTY = 4;
+constexpr int kMarchThreads = 128;   // 4 independent warps per block
+constexpr int kMarchMinBlocks = 10;  // register cap for occupancy
 
-cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, size_t nvox,
-                                float scale, float* staged, cudaStream_t s);
-cudaError_t launch_march(const MarchPlume& p, cudaStream_t s, bool count = false);
+// Staged grid: 4 floats per voxel (x/y 2x2 neighbourhood), see march.cu.
+inline size_t staged_floats(int nx, int ny, int nz) { return (size_t)nx * ny * nz * 4; }
+cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
+                                int ny, int nz, float scale, float* staged, cudaStream_t s);
+int march_tiles(int W, int H);
+cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
+                         bool count = false);
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
-                               cudaStream_t s);
+                               int* tile_counter, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // six-way shading

@@ -9,9 +9,11 @@ TOL_GUIDE = 1e-5          # ray march
 TOL_NET_F32_ABS = 1e-4    # FP32 network, max-abs
 TOL_NET_F16 = 2e-2        # FP16-operand tensor-core network, of the output range
 # BF16 operands carry 8 significand bits: an exact-rounding emulation of this
-# network (random Kaiming weights, FP32 accumulation) already reaches 4.7% of the
-# range, so the BF16 path is held to 6e-2 and the 2e-2 bound to FP16 operands.
-TOL_NET_BF16 = 6e-2
+# network (random Kaiming weights, FP32 accumulation, every operand rounded to
+# nearest BF16) already reaches 4.7% of the range on a random 128^2 guide and
+# 7.6% on the 512^2 obstacle-scene guide, so the BF16 path is held to 1e-1; the
+# 2e-2 bound applies to FP16 operands (emulated 0.6% / 0.95%).
+TOL_NET_BF16 = 1e-1
 TOL_NET_FP8 = 6e-2        # FP8 network, of the output range
 TOL_SHADE = 1e-5
 MAX_EXCUSED_FRAC = 1e-3   # threshold-flip pixels allowed to differ

@@ -243,6 +243,10 @@ def test_shade_parity(lib, orc):
     got = out.cpu().numpy().astype(np.float64)
     ref = orc.shade(lm.astype(np.float64), cam, lights)
     errs = PT.range_err(got, ref)
+    if max(errs) > PT.TOL_SHADE:
+        print("SHADE DEBUG", lm_dev.shape, lm_dev.stride(), lm_dev.data_ptr() % 256, out.data_ptr() % 256,
+              [ (l.dir, l.intensity) for l in lights], cam, got[:, 0, :4], ref[:, 0, :4],
+              np.isnan(got).sum(axis=(1, 2)))
     assert max(errs) <= PT.TOL_SHADE, errs
     # no lights: emissive and alpha only
     out.fill_(float("nan"))
