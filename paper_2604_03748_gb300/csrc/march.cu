@@ -23,35 +23,71 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
   return (word >> 22u) ^ word;
 }
 
+// Staged grid layouts (all hold sigma' = scale * rho * [mask == 0], float32):
+//   kLayoutLinear  one float per voxel; a sample reads 8 corners
+//   kLayoutXPair   float2 per voxel (rho(i), rho(i+1)) along x; a sample reads
+//                  4 x 8 bytes
+//   kLayoutQuad    float4 per voxel, the x/y 2x2 neighbourhood of its slice; a
+//                  sample reads 2 x 16 bytes
+// The +1 neighbours are clamped to the grid edge, so on the low edge (index -1)
+// the corner pair holds voxels (0, 1) while both corners should be voxel 0: a
+// zero interpolation weight reproduces that exactly.
 struct Grid {
-  const float4* __restrict__ q;  // quad-staged grid, see stage_quad_kernel
+  const float* __restrict__ v;
   int nx, ny, nz;
-  float fx, fy, fz;              // box extents
+  float fx, fy, fz;  // box extents
 };
 
 // Extinction at p: 0 outside the closed box [0,n]; trilinear interpolation of
-// the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.  The
-// grid is staged as quads: cell (i,j,k) holds the x/y 2x2 neighbourhood
-// (rho(i,j), rho(i+1,j), rho(i,j+1), rho(i+1,j+1)) of slice k with the +1
-// indices clamped to the edge, so one sample is two 16-byte loads (slices k0,
-// k1).  On the low edge (index -1) both x (or y) corners are voxel 0, which the
-// zero interpolation weight reproduces.
+// the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.
 __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, float pz) {
   if (!(px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz)) return 0.f;
   float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
   float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  if (ix < 0) { ix = 0; tx = 0.f; }
-  if (iy < 0) { iy = 0; ty = 0.f; }
   const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
-  const size_t row = (size_t)iy * g.nx + ix, plane = (size_t)g.nx * g.ny;
-  const float4 a = __ldg(g.q + z0 * plane + row);
-  const float4 b = __ldg(g.q + z1 * plane + row);
-  const float c00 = fmaf(tx, a.y - a.x, a.x);
-  const float c10 = fmaf(tx, a.w - a.z, a.z);
-  const float c01 = fmaf(tx, b.y - b.x, b.x);
-  const float c11 = fmaf(tx, b.w - b.z, b.z);
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+  float c00, c10, c01, c11;
+  if constexpr (kMarchLayout == kLayoutLinear) {
+    const int x0 = max(ix, 0), x1 = min(ix + 1, g.nx - 1);
+    const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
+    const float* r00 = g.v + (z0 * plane + (unsigned)(y0 * g.nx));
+    const float* r01 = g.v + (z0 * plane + (unsigned)(y1 * g.nx));
+    const float* r10 = g.v + (z1 * plane + (unsigned)(y0 * g.nx));
+    const float* r11 = g.v + (z1 * plane + (unsigned)(y1 * g.nx));
+    const float v000 = __ldg(r00 + x0), v100 = __ldg(r00 + x1);
+    const float v010 = __ldg(r01 + x0), v110 = __ldg(r01 + x1);
+    const float v001 = __ldg(r10 + x0), v101 = __ldg(r10 + x1);
+    const float v011 = __ldg(r11 + x0), v111 = __ldg(r11 + x1);
+    c00 = fmaf(tx, v100 - v000, v000);
+    c10 = fmaf(tx, v110 - v010, v010);
+    c01 = fmaf(tx, v101 - v001, v001);
+    c11 = fmaf(tx, v111 - v011, v011);
+  } else if constexpr (kMarchLayout == kLayoutXPair) {
+    if (ix < 0) { ix = 0; tx = 0.f; }
+    const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
+    const float2* q = reinterpret_cast<const float2*>(g.v);
+    const float2 a0 = __ldg(q + (z0 * plane + (unsigned)(y0 * g.nx + ix)));
+    const float2 a1 = __ldg(q + (z0 * plane + (unsigned)(y1 * g.nx + ix)));
+    const float2 b0 = __ldg(q + (z1 * plane + (unsigned)(y0 * g.nx + ix)));
+    const float2 b1 = __ldg(q + (z1 * plane + (unsigned)(y1 * g.nx + ix)));
+    c00 = fmaf(tx, a0.y - a0.x, a0.x);
+    c10 = fmaf(tx, a1.y - a1.x, a1.x);
+    c01 = fmaf(tx, b0.y - b0.x, b0.x);
+    c11 = fmaf(tx, b1.y - b1.x, b1.x);
+  } else {
+    if (ix < 0) { ix = 0; tx = 0.f; }
+    if (iy < 0) { iy = 0; ty = 0.f; }
+    const float4* q = reinterpret_cast<const float4*>(g.v);
+    const unsigned row = (unsigned)(iy * g.nx + ix);
+    const float4 a = __ldg(q + (z0 * plane + row));
+    const float4 b = __ldg(q + (z1 * plane + row));
+    c00 = fmaf(tx, a.y - a.x, a.x);
+    c10 = fmaf(tx, a.w - a.z, a.z);
+    c01 = fmaf(tx, b.y - b.x, b.x);
+    c11 = fmaf(tx, b.w - b.z, b.z);
+  }
   const float c0 = fmaf(ty, c10 - c00, c00);
   const float c1 = fmaf(ty, c11 - c01, c01);
   return fmaf(tz, c1 - c0, c0);
@@ -111,8 +147,7 @@ template <bool kCount>
 __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   unsigned long long nsamp = 0;
   const CamFrame& c = P.cam;
-  Grid g{reinterpret_cast<const float4*>(P.vol), P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny,
-         (float)P.nz};
+  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
   // ray through the pixel centre
@@ -299,14 +334,13 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
-// One thread per staged cell (i,j,k): sigma'(i,j), sigma'(i+1,j), sigma'(i,j+1),
-// sigma'(i+1,j+1) of slice k, with sigma' = scale * rho * [mask == 0] and the
-// +1 indices clamped to the grid edge.
+// One thread per staged cell (i,j,k), writing the layout kMarchLayout of
+// sigma' = scale * rho * [mask == 0] with the +1 neighbours clamped to the edge.
 template <typename T>
-__global__ void __launch_bounds__(256) stage_quad_kernel(const T* __restrict__ rho,
-                                                         const uint8_t* __restrict__ mask, int nx,
-                                                         int ny, int nz, float scale,
-                                                         float4* __restrict__ out) {
+__global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
+                                                    const uint8_t* __restrict__ mask, int nx,
+                                                    int ny, int nz, float scale,
+                                                    float* __restrict__ out) {
   const size_t n = (size_t)nx * ny * nz;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
@@ -319,7 +353,13 @@ __global__ void __launch_bounds__(256) stage_quad_kernel(const T* __restrict__ r
     auto val = [&](size_t idx) {
       return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
     };
-    __stcs(out + c, make_float4(val(b0 + i), val(b0 + i1), val(b1 + i), val(b1 + i1)));
+    if constexpr (kMarchLayout == kLayoutLinear)
+      __stcs(out + c, val(b0 + i));
+    else if constexpr (kMarchLayout == kLayoutXPair)
+      __stcs(reinterpret_cast<float2*>(out) + c, make_float2(val(b0 + i), val(b0 + i1)));
+    else
+      __stcs(reinterpret_cast<float4*>(out) + c,
+             make_float4(val(b0 + i), val(b0 + i1), val(b1 + i), val(b1 + i1)));
   }
 }
 
@@ -329,13 +369,12 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
   int blocks = (int)((n + 255) / 256);
   if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
   if (blocks < 1) blocks = 1;
-  float4* q = reinterpret_cast<float4*>(staged);
   if (dtype == NSL_F16)
-    stage_quad_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(density), mask, nx,
-                                                     ny, nz, scale, q);
+    stage_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(density), mask, nx, ny,
+                                                 nz, scale, staged);
   else
-    stage_quad_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(density), mask, nx,
-                                                    ny, nz, scale, q);
+    stage_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(density), mask, nx, ny,
+                                                nz, scale, staged);
   return cudaGetLastError();
 }
 

@@ -55,13 +55,23 @@ struct MarchPlume {
   unsigned long long* counter;  // density-evaluation counter (counting variant only)
 };
 
+#ifndef NSL_MARCH_MIN_BLOCKS
+#define NSL_MARCH_MIN_BLOCKS 6
+#endif
 constexpr int kMarchTX = 8;          // march tile: 8 x 4 pixels, one warp
 constexpr int kMarchTY = 4;
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
-constexpr int kMarchMinBlocks = 10;  // register cap for occupancy
+constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
-// Staged grid: 4 floats per voxel (x/y 2x2 neighbourhood), see march.cu.
-inline size_t staged_floats(int nx, int ny, int nz) { return (size_t)nx * ny * nz * 4; }
+// Staged grid layout (see march.cu): 0 linear, 1 x-pairs, 2 x/y quads.
+constexpr int kLayoutLinear = 0, kLayoutXPair = 1, kLayoutQuad = 2;
+#ifndef NSL_MARCH_LAYOUT
+#define NSL_MARCH_LAYOUT 2
+#endif
+constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
+inline size_t staged_floats(int nx, int ny, int nz) {
+  return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : kMarchLayout == kLayoutXPair ? 2 : 4);
+}
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s);
 int march_tiles(int W, int H);
