@@ -203,9 +203,9 @@ def main():
     stream = torch.cuda.current_stream()
     dens = torch.from_numpy(pf.density).to(dev)
     mask = torch.from_numpy(pf.mask).to(dev)
-    guide = torch.empty((3, H, W), device=dev)
-    lm = torch.empty((8, H, W), device=dev)
-    rgba = torch.empty((4, H, W), device=dev)
+    guide = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    lm = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+    rgba = torch.empty((4, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
     opts = nsl.march_opts()
 
@@ -264,9 +264,9 @@ def main():
     # guide, lightmaps and rgba, every step
     pin = lambda a: torch.from_numpy(a).pin_memory()
     h_dens, h_mask = pin(pf.density), pin(pf.mask)
-    h_guide = torch.empty((3, H, W)).pin_memory()
-    h_lm = torch.empty((8, H, W)).pin_memory()
-    h_rgba = torch.empty((4, H, W)).pin_memory()
+    h_guide = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    h_lm = torch.empty((8, H, W), dtype=torch.float32).pin_memory()
+    h_rgba = torch.empty((4, H, W), dtype=torch.float32).pin_memory()
     e2e_t = []
     for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         t0 = time.perf_counter()

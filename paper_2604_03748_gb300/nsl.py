@@ -133,12 +133,22 @@ def march_opts(**kw) -> nsl_march_opts:
     return o
 
 
-def _dptr(t):
+def _dptr(t, dtypes=None):
+    """Device pointer of a contiguous CUDA tensor whose dtype is one of `dtypes`
+    (names such as 'float32'); the C ABI takes plain pointers, so a wrong element
+    type would otherwise be read or written silently."""
     if t is None:
         return None
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
+    if dtypes is not None and str(t.dtype).replace("torch.", "") not in dtypes:
+        raise ValueError(f"expected a tensor of dtype {' or '.join(dtypes)}, got {t.dtype}")
     return C.c_void_p(t.data_ptr())
+
+
+F32 = ("float32",)
+GRID_TYPES = ("float32", "float16")
+U8 = ("uint8",)
 
 
 def _stream(stream):
@@ -166,7 +176,8 @@ def nsl_destroy(ctx):
 
 
 def nsl_stage_grid(ctx, density, mask, stream=None):
-    check(load().nsl_stage_grid(ctx, _dptr(density), _dptr(mask), _stream(stream)), "nsl_stage_grid")
+    check(load().nsl_stage_grid(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), _stream(stream)),
+          "nsl_stage_grid")
 
 
 def nsl_guide_sample_count(ctx, cam, step, opts=None, stream=None) -> int:
@@ -180,20 +191,20 @@ def nsl_guide_sample_count(ctx, cam, step, opts=None, stream=None) -> int:
 def nsl_guiding_map(ctx, density, mask, cam, step, guide, light=None, opts=None, stream=None):
     lib = load()
     li = lights([light])[0] if light is not None else None
-    check(lib.nsl_guiding_map(ctx, _dptr(density), _dptr(mask), C.byref(camera(cam)),
+    check(lib.nsl_guiding_map(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), C.byref(camera(cam)),
                               C.byref(li) if li is not None else None, float(step),
-                              C.byref(opts) if opts is not None else None, _dptr(guide),
+                              C.byref(opts) if opts is not None else None, _dptr(guide, F32),
                               _stream(stream)), "nsl_guiding_map")
 
 
 def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, stream=None):
-    check(load().nsl_predict_lightmaps(ctx, _dptr(guide), int(width), int(height), int(precision),
-                                       _dptr(lightmaps), _stream(stream)), "nsl_predict_lightmaps")
+    check(load().nsl_predict_lightmaps(ctx, _dptr(guide, F32), int(width), int(height), int(precision),
+                                       _dptr(lightmaps, F32), _stream(stream)), "nsl_predict_lightmaps")
 
 
 def nsl_shade(ctx, lightmaps, width, height, cam, light_list, rgba, stream=None):
-    check(load().nsl_shade(ctx, _dptr(lightmaps), int(width), int(height), C.byref(camera(cam)),
-                           lights(light_list), len(light_list), _dptr(rgba), _stream(stream)),
+    check(load().nsl_shade(ctx, _dptr(lightmaps, F32), int(width), int(height), C.byref(camera(cam)),
+                           lights(light_list), len(light_list), _dptr(rgba, F32), _stream(stream)),
           "nsl_shade")
 
 

@@ -132,7 +132,7 @@ def test_invalid_arguments_rejected(lib):
     pf = I.config_plain_64()
     ctx = PT.make_ctx(pf)
     d = torch.from_numpy(pf.density).cuda()
-    g = torch.empty((3, 128, 128), device="cuda")
+    g = torch.empty((3, 128, 128), dtype=torch.float32, device="cuda")
     big = I.orbit_ortho_camera(64, 1, 256, 256)
     with pytest.raises(nsl.NslError) as ei:
         ctx.guiding_map(d, None, big, 4.0, g)
@@ -143,7 +143,9 @@ def test_invalid_arguments_rejected(lib):
     with pytest.raises(nsl.NslError):
         ctx.guiding_map(d, None, odd, 4.0, g)
     with pytest.raises(nsl.NslError) as ei:
-        ctx.predict_lightmaps(g, 128, 128, 7, torch.empty((8, 128, 128), device="cuda"))
+        ctx.predict_lightmaps(g, 128, 128, 7, torch.empty((8, 128, 128), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):       # a float64 output buffer is refused by the binding
+        ctx.guiding_map(d, None, pf.camera, 4.0, torch.empty((3, 128, 128), dtype=torch.float64, device="cuda"))
     assert ei.value.status in (nsl.NSL_ERR_UNSUPPORTED, nsl.NSL_ERR_INVALID_ARG)
     ctx.close()
 
@@ -237,30 +239,12 @@ def test_shade_parity(lib, orc):
     pf = I.PlumeFrame(np.zeros((8, 8, 8), np.float32), None, cam, lights[0], 1.0)
     ctx = PT.make_ctx(pf)
     lm_dev = torch.from_numpy(lm).cuda()
-    out = torch.full((4, H, W), float("nan"), device="cuda")
+    out = torch.full((4, H, W), float("nan"), dtype=torch.float32, device="cuda")
     ctx.shade(lm_dev, W, H, cam, lights, out)
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     ref = orc.shade(lm.astype(np.float64), cam, lights)
     errs = PT.range_err(got, ref)
-    if max(errs) > PT.TOL_SHADE:
-        from paper_2604_03748_gb300 import nsl
-        print("SHADE DEBUG stream", torch.cuda.current_stream(), "lasterr", nsl.load().nsl_last_error(),
-              "nan/plane", np.isnan(got).sum(axis=(1, 2)), "lm ok", np.array_equal(lm_dev.cpu().numpy(), lm))
-        for rep in range(2):
-            out.fill_(float("nan"))
-            torch.cuda.synchronize()
-            ctx.shade(lm_dev, W, H, cam, lights, out)
-            torch.cuda.synchronize()
-            g2 = out.cpu().numpy().astype(np.float64)
-            print("SHADE DEBUG rep", rep, PT.range_err(g2, ref), np.isnan(g2).sum(axis=(1, 2)))
-        ctx2 = PT.make_ctx(pf)
-        out.fill_(float("nan"))
-        ctx2.shade(lm_dev, W, H, cam, lights, out)
-        torch.cuda.synchronize()
-        g3 = out.cpu().numpy().astype(np.float64)
-        print("SHADE DEBUG ctx2", PT.range_err(g3, ref), np.isnan(g3).sum(axis=(1, 2)))
-        ctx2.close()
     assert max(errs) <= PT.TOL_SHADE, errs
     # no lights: emissive and alpha only
     out.fill_(float("nan"))

@@ -7,7 +7,6 @@ import torch.nn.functional as Fn
 
 from paper_2604_03748_gb300 import inputs as I
 
-torch.set_default_dtype(torch.float64)
 
 
 def T(a):
@@ -155,7 +154,7 @@ def torch_unet_forward(guide, params, c0, depth_scale):
     d = c3(c3(torch.cat([u, s2], 1), "dec2a"), "dec2b")
     u = Fn.conv_transpose2d(d, P["up1.w"], P["up1.b"], stride=2)
     F = c3(c3(torch.cat([u, s1], 1), "dec1a"), "dec1b")
-    out = torch.zeros(8, F.shape[2], F.shape[3])
+    out = torch.zeros(8, F.shape[2], F.shape[3], dtype=torch.float64)
     planes = {"FB": (4, 5), "LR": (0, 1), "UD": (2, 3), "AE": (6, 7)}
     for a in I.ADAPTERS:
         p = "ad" + a
