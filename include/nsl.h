@@ -133,6 +133,32 @@ NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const 
                            const nsl_camera* cam, const nsl_light* light, float step_voxels,
                            const nsl_march_opts* opts, float* guide_dev, void* stream);
 
+/* Guide march without any device allocation by the library (the paper has no
+ * counterpart of this entry point).  It is meant for callers that cannot call
+ * cudaMalloc at all: a render thread whose frame budget cannot absorb the device
+ * synchronisation an allocation may cause, an engine whose own allocator owns
+ * every byte of device memory, or code that has no context to keep between
+ * frames.  It computes exactly what nsl_guiding_map computes, with the same
+ * kernels; the staged grid and the tile counter live in one static device
+ * array of 32 MiB + 256 bytes inside libnsl, which every GPU that loads the
+ * library holds until the process exits.
+ *   grid          shape, storage and sigma_scale of density_dev
+ *   density_dev, mask_dev, cam, step_voxels, opts, guide_dev, stream
+ *                 as for nsl_guiding_map (no light argument)
+ * Limits: the grid may hold at most 2,097,152 voxels (16 bytes each in the
+ * staged layout: 128^3 fits); larger grids return NSL_ERR_INVALID_ARG with a
+ * message, and nothing is queued.  No cudaMalloc, cudaFree or other allocating
+ * call is made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (every call restages the grid and zeroes the
+ * counter first); calls that overlap on the GPU (different streams, or devices
+ * sharing nothing but this rule) race on it, so serialise them. */
+NSL_API nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const void* density_dev,
+                                           const uint8_t* mask_dev, const nsl_camera* cam,
+                                           float step_voxels, const nsl_march_opts* opts,
+                                           float* guide_dev, void* stream);
+
 /* Number of density evaluations the guide march of nsl_guiding_map makes for
  * this camera, step and options on the staged grid: view samples plus the
  * shadow samples of every view sample with non-zero density (Alg. 1).  Runs a

@@ -20,7 +20,7 @@ NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
 
 # every symbol include/nsl.h declares
 EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_grid",
-           "nsl_guiding_map", "nsl_guide_sample_count",
+           "nsl_guiding_map", "nsl_guiding_map_noalloc", "nsl_guide_sample_count",
            "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host", "nsl_last_error",
            "nsl_status_str"]
 
@@ -72,6 +72,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_guiding_map.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light), f,
                                     C.POINTER(nsl_march_opts), vp, vp]
     lib.nsl_stage_grid.argtypes = [vp, vp, vp, vp]
+    lib.nsl_guiding_map_noalloc.argtypes = [C.POINTER(nsl_grid_desc), vp, vp, C.POINTER(nsl_camera),
+                                            f, C.POINTER(nsl_march_opts), vp, vp]
     lib.nsl_guide_sample_count.argtypes = [vp, C.POINTER(nsl_camera), f, C.POINTER(nsl_march_opts),
                                            C.POINTER(C.c_ulonglong), vp]
     lib.nsl_predict_lightmaps.argtypes = [vp, vp, i, i, i, vp, vp]
@@ -82,7 +84,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_last_error.restype = C.c_char_p
     lib.nsl_status_str.argtypes = [i]
     lib.nsl_status_str.restype = C.c_char_p
-    for name in ("nsl_create", "nsl_stage_grid", "nsl_guiding_map", "nsl_guide_sample_count",
+    for name in ("nsl_create", "nsl_stage_grid", "nsl_guiding_map", "nsl_guiding_map_noalloc",
+                 "nsl_guide_sample_count",
                  "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -195,6 +198,17 @@ def nsl_guiding_map(ctx, density, mask, cam, step, guide, light=None, opts=None,
                               C.byref(li) if li is not None else None, float(step),
                               C.byref(opts) if opts is not None else None, _dptr(guide, F32),
                               _stream(stream)), "nsl_guiding_map")
+
+
+def nsl_guiding_map_noalloc(grid_shape, dtype, sigma_scale, density, mask, cam, step, guide,
+                            opts=None, stream=None):
+    """Guide march whose scratch is the library's static device array (no allocation)."""
+    nz, ny, nx = grid_shape
+    g = nsl_grid_desc(nx, ny, nz, dtype, sigma_scale)
+    check(load().nsl_guiding_map_noalloc(C.byref(g), _dptr(density, GRID_TYPES), _dptr(mask, U8),
+                                         C.byref(camera(cam)), float(step),
+                                         C.byref(opts) if opts is not None else None,
+                                         _dptr(guide, F32), _stream(stream)), "nsl_guiding_map_noalloc")
 
 
 def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, stream=None):
