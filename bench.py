@@ -293,7 +293,7 @@ def main():
                    "l2": "flushed (256 MiB write) before every timed step, outside the timed events"},
         "stage_ms": {"stage": float(np.mean(stage_ms)), "march": float(np.mean(march_ms)),
                      "net": float(np.mean(net_ms)), "shade": float(np.mean(shade_ms))},
-        "roofline": {"kernel": "march_kernel (guide march)", "bound": "alu",
+        "roofline": {"kernel": "guide march (view pass + segment pass + finish pass)", "bound": "alu",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "work": {"density_samples": samples, "flop_per_sample": FLOP_PER_SAMPLE},

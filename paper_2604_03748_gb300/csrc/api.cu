@@ -105,6 +105,8 @@ struct nsl_ctx {
   bool staged_valid = false;        // a staging has been queued
   unsigned long long* counter = nullptr;  // sample-count scratch
   int* tile_counter = nullptr;            // march tile queue (scratch)
+  void* seg_scratch = nullptr;            // segmented-march scratch
+  size_t seg_bytes = 0;
   NetF32Weights* wf32 = nullptr;
   NetTcWeights* wtc[2] = {};        // tensor-core weights: [0] FP16, [1] BF16 (built on first use)
   void* ws = nullptr;               // network workspace (shared by both precisions)
@@ -227,6 +229,7 @@ void nsl_destroy(nsl_ctx* c) {
   cudaFree(c->staged);
   cudaFree(c->counter);
   cudaFree(c->tile_counter);
+  cudaFree(c->seg_scratch);
   net_f32_destroy(c->wf32);
   net_tc_destroy(c->wtc[0]);
   net_tc_destroy(c->wtc[1]);
@@ -332,7 +335,28 @@ nsl_status nsl_guiding_map(nsl_ctx* c, const void* density, const uint8_t* mask,
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: density is NULL and no grid is staged");
   }
   p.guide = guide;
-  cudaError_t e = launch_march(p, c->tile_counter, static_cast<cudaStream_t>(stream));
+  // segmented-march scratch, grown on demand: per pixel the step count, per
+  // (segment, pixel) the optical depth, its compensation and the partial radiance
+  const int maxseg = march_max_segments(c->grid.nx, c->grid.ny, c->grid.nz, step, kMarchSegLen);
+  const size_t P = (size_t)cam->width * cam->height;
+  const size_t need = P * sizeof(int) + 3 * (size_t)maxseg * P * sizeof(float) + 1024;
+  if (need > c->seg_bytes) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NSL_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(c->seg_scratch);
+    c->seg_scratch = nullptr;
+    c->seg_bytes = 0;
+    NSL_CUDA_TRY(cudaMalloc(&c->seg_scratch, need));
+    c->seg_bytes = need;
+  }
+  char* base = static_cast<char*>(c->seg_scratch);
+  p.seg_len = kMarchSegLen;
+  p.seg_nef = reinterpret_cast<int*>(base);
+  base += (P * sizeof(int) + 255) / 256 * 256;
+  p.seg_tau = reinterpret_cast<float*>(base);
+  p.seg_comp = p.seg_tau + (size_t)maxseg * P;
+  p.seg_L = p.seg_comp + (size_t)maxseg * P;
+  cudaError_t e = launch_march_segmented(p, maxseg, c->tile_counter, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map: march");
   return NSL_OK;
 }

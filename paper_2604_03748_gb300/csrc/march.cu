@@ -12,6 +12,8 @@
 // one IEEE rounding per operation in a fixed order (__fadd_rn & co. are never
 // contracted into FMAs), so that the counts agree bit for bit with any other
 // binary32 evaluation of the same sequence.
+#include <cmath>
+
 #include "nsl_internal.cuh"
 
 namespace nsl {
@@ -93,6 +95,49 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
   return fmaf(tz, c1 - c0, c0);
 }
 
+// Two-stage form of sigma_at for software pipelining (quad layout): fetch()
+// computes the cell and issues its two 16-byte loads with every index clamped
+// into the grid, so it is always safe to issue ahead; interp() finishes the
+// trilinear blend and applies the box test.  The value equals sigma_at's.
+struct Fetch {
+  float4 a, b;
+  float tx, ty, tz;
+  bool in;
+};
+
+__device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float pz) {
+  Fetch f;
+  f.in = px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz;
+  float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
+  float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+  f.tx = __fsub_rn(qx, flx);
+  f.ty = __fsub_rn(qy, fly);
+  f.tz = __fsub_rn(qz, flz);
+  int ix = (int)flx, iy = (int)fly, iz = (int)flz;
+  if (ix < 0) { ix = 0; f.tx = 0.f; }
+  if (iy < 0) { iy = 0; f.ty = 0.f; }
+  ix = min(ix, g.nx - 1);
+  iy = min(iy, g.ny - 1);
+  const int z0 = min(max(iz, 0), g.nz - 1), z1 = min(max(iz + 1, 0), g.nz - 1);
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+  const unsigned row = (unsigned)(iy * g.nx + ix);
+  const float4* q = reinterpret_cast<const float4*>(g.v);
+  f.a = __ldg(q + (z0 * plane + row));
+  f.b = __ldg(q + (z1 * plane + row));
+  return f;
+}
+
+__device__ __forceinline__ float interp(const Fetch& f) {
+  const float c00 = fmaf(f.tx, f.a.y - f.a.x, f.a.x);
+  const float c10 = fmaf(f.tx, f.a.w - f.a.z, f.a.z);
+  const float c01 = fmaf(f.tx, f.b.y - f.b.x, f.b.x);
+  const float c11 = fmaf(f.tx, f.b.w - f.b.z, f.b.z);
+  const float c0 = fmaf(f.ty, c10 - c00, c00);
+  const float c1 = fmaf(f.ty, c11 - c01, c01);
+  const float v = fmaf(f.tz, c1 - c0, c0);
+  return f.in ? v : 0.f;
+}
+
 __device__ __forceinline__ float hg_phase(float g, float c) {
   float den = 1.f + g * g - 2.f * g * c;
   return (1.f - g * g) / (12.566370614359172f * den * sqrtf(den));
@@ -125,6 +170,41 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
   float taut = 0.f, taub = 0.f;
   bool at = Kt > 0, ab = Kb > 0;
   const int K = max(Kt, Kb);
+#if NSL_MARCH_PIPELINE
+  if (kMarchLayout == kLayoutQuad && K > 0) {
+    // loads of step k+1 are issued before step k is consumed
+    float kh = h;
+    Fetch ft = fetch(g, __fadd_rn(px, __fmul_rn(kh, u[0])), __fadd_rn(py, __fmul_rn(kh, u[1])),
+                     __fadd_rn(pz, __fmul_rn(kh, u[2])));
+    Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kh, u[0])), __fsub_rn(py, __fmul_rn(kh, u[1])),
+                     __fsub_rn(pz, __fmul_rn(kh, u[2])));
+    for (int k = 1; k <= K; ++k) {
+      Fetch nt = ft, nb = fb;
+      if (k < K) {
+        kh = __fmul_rn((float)(k + 1), h);
+        const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
+        if (at && k < Kt) nt = fetch(g, __fadd_rn(px, dx), __fadd_rn(py, dy), __fadd_rn(pz, dz));
+        if (ab && k < Kb) nb = fetch(g, __fsub_rn(px, dx), __fsub_rn(py, dy), __fsub_rn(pz, dz));
+      }
+      if (at) {
+        taut = fmaf(interp(ft), h, taut);
+        if (kCount) ++nsamp;
+        if (k >= Kt || taut > tau_lim) at = false;
+      }
+      if (ab) {
+        taub = fmaf(interp(fb), h, taub);
+        if (kCount) ++nsamp;
+        if (k >= Kb || taub > tau_lim) ab = false;
+      }
+      if (!(at || ab)) break;
+      ft = nt;
+      fb = nb;
+    }
+    Tt = expf(-taut);
+    Tb = expf(-taub);
+    return;
+  }
+#endif
   for (int k = 1; k <= K && (at || ab); ++k) {
     const float kh = __fmul_rn((float)k, h);
     const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
@@ -143,6 +223,119 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
   Tb = expf(-taub);
 }
 
+// One pixel's view ray: origin, direction, the clipped interval, the jitter u,
+// the sample count N and the surrogate-light weights (phase x intensity).
+struct Ray {
+  float o[3], d[3];
+  float tn, tf, u;
+  int N;
+  bool hit;
+  float wf, wt, wb;
+};
+
+__device__ __forceinline__ Ray ray_setup(const MarchPlume& P, const Grid& g, int i, int j) {
+  const CamFrame& c = P.cam;
+  Ray r;
+  // ray through the pixel centre
+  const float sxs = __fsub_rn(__fdiv_rn(__fadd_rn((float)i, 0.5f), (float)c.W), 0.5f);
+  const float sys = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn((float)j, 0.5f), (float)c.H));
+  const float a = __fmul_rn(sxs, c.ax), b = __fmul_rn(sys, c.ay);
+  if (c.kind == NSL_CAM_ORTHO) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      r.o[k] = __fadd_rn(__fadd_rn(c.eye[k], __fmul_rn(a, c.r[k])), __fmul_rn(b, c.u[k]));
+      r.d[k] = c.f[k];
+    }
+  } else {
+    float v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[k] = __fadd_rn(__fadd_rn(c.f[k], __fmul_rn(a, c.r[k])), __fmul_rn(b, c.u[k]));
+      r.o[k] = c.eye[k];
+    }
+    const float len = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])),
+                                           __fmul_rn(v[2], v[2])));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.d[k] = __fdiv_rn(v[k], len);
+  }
+  // slab clip against the closed box
+  const float n3[3] = {g.fx, g.fy, g.fz};
+  float tn = -INFINITY, tf = INFINITY;
+  r.hit = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (r.d[k] != 0.f) {
+      const float ta = __fdiv_rn(__fsub_rn(0.f, r.o[k]), r.d[k]);
+      const float tb = __fdiv_rn(__fsub_rn(n3[k], r.o[k]), r.d[k]);
+      const float lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+      if (lo > tn) tn = lo;
+      if (hi < tf) tf = hi;
+    } else if (r.o[k] < 0.f || r.o[k] > n3[k]) {
+      r.hit = false;
+    }
+  }
+  if (tn < 0.f) tn = 0.f;
+  if (!(tf > tn)) r.hit = false;
+  r.tn = tn;
+  r.tf = tf;
+  r.u = 0.f;
+  r.N = 0;
+  if (r.hit) {
+    if (P.jitter) {
+      const uint32_t hv = pcg_hash((uint32_t)(j * c.W + i) + P.key);
+      r.u = __fmul_rn((float)(hv >> 8), 1.0f / 16777216.0f);
+    }
+    r.N = (int)floorf(__fadd_rn(__fdiv_rn(__fsub_rn(tf, tn), P.h), r.u));
+  }
+  // surrogate lights: front (toward the camera), top (+up), bottom (-up)
+  float Pf = 0.07957747154594767f, Pt = Pf, Pb = Pf;
+  if (P.g != 0.f) {
+    const float cu = r.d[0] * c.u[0] + r.d[1] * c.u[1] + r.d[2] * c.u[2];
+    Pf = hg_phase(P.g, -1.f);
+    Pt = hg_phase(P.g, cu);
+    Pb = hg_phase(P.g, -cu);
+  }
+  r.wf = Pf * P.I[0];
+  r.wt = Pt * P.I[1];
+  r.wb = Pb * P.I[2];
+  return r;
+}
+
+// position of view sample n: t_n = t_in + (n - u) h
+__device__ __forceinline__ void view_point(const Ray& r, int n, float h, float& px, float& py,
+                                           float& pz) {
+  const float t = __fadd_rn(r.tn, __fmul_rn(__fsub_rn((float)n, r.u), h));
+  px = __fadd_rn(r.o[0], __fmul_rn(t, r.d[0]));
+  py = __fadd_rn(r.o[1], __fmul_rn(t, r.d[1]));
+  pz = __fadd_rn(r.o[2], __fmul_rn(t, r.d[2]));
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
+  const float y = __fsub_rn(v, comp);
+  const float t = __fadd_rn(sum, y);
+  comp = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
+// One view step n with sigma = s > 0: A_n, the three surrogate lights, L_n;
+// accumulates A_n L_n into (L, Lc) and the optical depth into (tau, tc).
+template <bool kCount>
+__device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, const Ray& r,
+                                          float px, float py, float pz, float s, float& T,
+                                          float& tau, float& tc, float& L, float& Lc,
+                                          unsigned long long& nsamp) {
+  const float h = P.h;
+  const float A = P.segment_exact ? T * (1.f - expf(-s * h)) : T * s * h;
+  float Tt, Tb;
+  shadow_pair<kCount>(g, px, py, pz, P.cam.u, h, P.tau_lim, Tt, Tb, nsamp);
+  const float Ln = fmaf(r.wf, T, fmaf(r.wt, Tt, r.wb * Tb));
+  kahan_add(L, Lc, A * Ln);
+  kahan_add(tau, tc, s * h);
+  T = expf(-tau);
+}
+
+// Single-pass march of one pixel (Alg. 1): used by the sample-count variant and
+// the allocation-free entry point.
 template <bool kCount>
 __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   unsigned long long nsamp = 0;
@@ -150,92 +343,19 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
-  // ray through the pixel centre
-  float sxs = __fsub_rn(__fdiv_rn(__fadd_rn((float)i, 0.5f), (float)c.W), 0.5f);
-  float sys = __fsub_rn(0.5f, __fdiv_rn(__fadd_rn((float)j, 0.5f), (float)c.H));
-  float a = __fmul_rn(sxs, c.ax), b = __fmul_rn(sys, c.ay);
-  float o[3], d[3];
-  if (c.kind == NSL_CAM_ORTHO) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      o[k] = __fadd_rn(__fadd_rn(c.eye[k], __fmul_rn(a, c.r[k])), __fmul_rn(b, c.u[k]));
-      d[k] = c.f[k];
-    }
-  } else {
-    float v[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      v[k] = __fadd_rn(__fadd_rn(c.f[k], __fmul_rn(a, c.r[k])), __fmul_rn(b, c.u[k]));
-      o[k] = c.eye[k];
-    }
-    float len = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(v[1], v[1])),
-                                     __fmul_rn(v[2], v[2])));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = __fdiv_rn(v[k], len);
-  }
-  // slab clip against the closed box
-  float n3[3] = {g.fx, g.fy, g.fz};
-  float tn = -INFINITY, tf = INFINITY;
-  bool hit = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (d[k] != 0.f) {
-      float ta = __fdiv_rn(__fsub_rn(0.f, o[k]), d[k]);
-      float tb = __fdiv_rn(__fsub_rn(n3[k], o[k]), d[k]);
-      float lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
-      if (lo > tn) tn = lo;
-      if (hi < tf) tf = hi;
-    } else if (o[k] < 0.f || o[k] > n3[k]) {
-      hit = false;
-    }
-  }
-  if (tn < 0.f) tn = 0.f;
-  if (!(tf > tn)) hit = false;
-
+  const Ray r = ray_setup(P, g, i, j);
   float L = 0.f, Lc = 0.f;             // Kahan-compensated guide radiance
   float T = 1.f, tau = 0.f, tc = 0.f;  // Kahan-compensated view optical depth
   float D = 0.f;
-  if (hit) {
-    const float h = P.h;
-    float u = 0.f;
-    if (P.jitter) {
-      uint32_t hv = pcg_hash((uint32_t)(j * c.W + i) + P.key);
-      u = __fmul_rn((float)(hv >> 8), 1.0f / 16777216.0f);
-    }
-    const int N = (int)floorf(__fadd_rn(__fdiv_rn(__fsub_rn(tf, tn), h), u));
-    // surrogate lights: front (toward the camera), top (+up), bottom (-up)
-    float Pf = 0.07957747154594767f, Pt = Pf, Pb = Pf;
-    if (P.g != 0.f) {
-      float cu = d[0] * c.u[0] + d[1] * c.u[1] + d[2] * c.u[2];
-      Pf = hg_phase(P.g, -1.f);
-      Pt = hg_phase(P.g, cu);
-      Pb = hg_phase(P.g, -cu);
-    }
-    const float wf = Pf * P.I[0], wt = Pt * P.I[1], wb = Pb * P.I[2];
-    for (int n = 1; n <= N; ++n) {
-      float tn_n = __fadd_rn(tn, __fmul_rn(__fsub_rn((float)n, u), h));
-      float px = __fadd_rn(o[0], __fmul_rn(tn_n, d[0]));
-      float py = __fadd_rn(o[1], __fmul_rn(tn_n, d[1]));
-      float pz = __fadd_rn(o[2], __fmul_rn(tn_n, d[2]));
-      float s = sigma_at(g, px, py, pz);
-      if (kCount) ++nsamp;
-      if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, h);
-      if (s > 0.f) {
-        float A = P.segment_exact ? T * (1.f - expf(-s * h)) : T * s * h;
-        float Tt, Tb;
-        shadow_pair<kCount>(g, px, py, pz, c.u, h, P.tau_lim, Tt, Tb, nsamp);
-        float Ln = fmaf(wf, T, fmaf(wt, Tt, wb * Tb));
-        float y = __fsub_rn(A * Ln, Lc);
-        float t = __fadd_rn(L, y);
-        Lc = __fsub_rn(__fsub_rn(t, L), y);
-        L = t;
-        float yy = __fsub_rn(s * h, tc);
-        float tt = __fadd_rn(tau, yy);
-        tc = __fsub_rn(__fsub_rn(tt, tau), yy);
-        tau = tt;
-        T = expf(-tau);
-        if (T < P.t_min) break;
-      }
+  for (int n = 1; n <= r.N; ++n) {
+    float px, py, pz;
+    view_point(r, n, P.h, px, py, pz);
+    const float s = sigma_at(g, px, py, pz);
+    if (kCount) ++nsamp;
+    if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, P.h);
+    if (s > 0.f) {
+      view_step<kCount>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+      if (T < P.t_min) break;
     }
   }
   if (kCount) {
@@ -245,6 +365,81 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   P.guide[pix] = L;
   P.guide[plane + pix] = T;
   P.guide[2 * plane + pix] = D;
+}
+
+// ---------------------------------------------------------------------------
+// Segmented march.  The serial chain of one pixel (every view step with its two
+// shadow marches) is split into segments of S view steps handled by different
+// threads.  Pass 1 marches the view ray alone and records the compensated
+// optical depth (tau, tc) at every segment start, the number of processed
+// steps, T and D; pass 2 marches each (pixel, segment) with its shadow rays
+// from the recorded state, which reproduces the single-pass T_{n-1} bit for
+// bit; pass 3 adds the segment partials of each pixel in order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void march_view_pixel(const MarchPlume& P, int i, int j) {
+  const CamFrame& c = P.cam;
+  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const size_t plane = (size_t)c.W * c.H;
+  const size_t pix = (size_t)j * c.W + i;
+  const Ray r = ray_setup(P, g, i, j);
+  const int S = P.seg_len;
+  float T = 1.f, tau = 0.f, tc = 0.f, D = 0.f;
+  int nef = 0;
+  for (int n = 1; n <= r.N; ++n) {
+    if ((n - 1) % S == 0) {
+      const size_t k = (size_t)((n - 1) / S) * plane + pix;
+      P.seg_tau[k] = tau;
+      P.seg_comp[k] = tc;
+    }
+    float px, py, pz;
+    view_point(r, n, P.h, px, py, pz);
+    const float s = sigma_at(g, px, py, pz);
+    if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, P.h);
+    nef = n;
+    if (s > 0.f) {
+      kahan_add(tau, tc, s * P.h);
+      T = expf(-tau);
+      if (T < P.t_min) break;
+    }
+  }
+  P.guide[plane + pix] = T;
+  P.guide[2 * plane + pix] = D;
+  P.seg_nef[pix] = nef;
+}
+
+__device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j, int seg) {
+  const CamFrame& c = P.cam;
+  const size_t plane = (size_t)c.W * c.H;
+  const size_t pix = (size_t)j * c.W + i;
+  const int S = P.seg_len;
+  const int nef = P.seg_nef[pix];
+  const int first = seg * S + 1;
+  if (first > nef) return;
+  const int last = min(first + S - 1, nef);
+  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const Ray r = ray_setup(P, g, i, j);
+  const size_t k = (size_t)seg * plane + pix;
+  float tau = P.seg_tau[k], tc = P.seg_comp[k];
+  float T = expf(-tau);
+  float L = 0.f, Lc = 0.f;
+  unsigned long long nsamp = 0;
+  for (int n = first; n <= last; ++n) {
+    float px, py, pz;
+    view_point(r, n, P.h, px, py, pz);
+    const float s = sigma_at(g, px, py, pz);
+    if (s > 0.f) view_step<false>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+  }
+  P.seg_L[k] = L;
+}
+
+__device__ __forceinline__ void march_finish_pixel(const MarchPlume& P, int i, int j) {
+  const CamFrame& c = P.cam;
+  const size_t plane = (size_t)c.W * c.H;
+  const size_t pix = (size_t)j * c.W + i;
+  const int nseg = (P.seg_nef[pix] + P.seg_len - 1) / P.seg_len;
+  float L = 0.f, Lc = 0.f;
+  for (int s = 0; s < nseg; ++s) kahan_add(L, Lc, P.seg_L[(size_t)s * plane + pix]);
+  P.guide[pix] = L;
 }
 
 __device__ __forceinline__ int find_plume(const MarchPlume* __restrict__ t, int n, int tile) {
@@ -321,6 +516,65 @@ cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int tot
   MarchPlume dummy{};
   march_kernel<true, false><<<march_grid<true, false>(), kMarchThreads, 0, s>>>(
       dummy, table_dev, nplumes, total_tiles, tile_counter);
+  return cudaGetLastError();
+}
+
+// pass 1 and pass 3: one thread per pixel, warps over 8x4 tiles
+template <int kPass>
+__global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPlume P, int ntiles) {
+  const int lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * (kMarchThreads / 32) + (threadIdx.x >> 5);
+  if (tile >= ntiles) return;
+  const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
+  const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+  if (i >= P.cam.W || j >= P.cam.H) return;
+  if (kPass == 1) march_view_pixel(P, i, j);
+  else march_finish_pixel(P, i, j);
+}
+
+// pass 2: warps take (tile, segment) items from a queue, segment-major
+__global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
+march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ counter) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;
+    const int seg = item / ntiles, tile = item % ntiles;
+    const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
+    const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+    if (i < P.cam.W && j < P.cam.H) march_segment(P, i, j, seg);
+  }
+}
+
+int march_max_segments(int nx, int ny, int nz, float h, int seg_len) {
+  const double diag = std::sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+  const double nmax = std::floor(diag / h + 1.0) + 1.0;
+  return (int)std::ceil(nmax / seg_len) + 1;
+}
+
+cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
+                                   cudaStream_t s) {
+  const int ntiles = march_tiles(p.cam.W, p.cam.H);
+  if (ntiles == 0) return cudaSuccess;
+  const int warps_per_block = kMarchThreads / 32;
+  const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
+  march_pixel_pass_kernel<1><<<blocks, kMarchThreads, 0, s>>>(p, ntiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+  static int grid = 0;
+  if (!grid) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_kernel, kMarchThreads, 0) !=
+            cudaSuccess || occ < 1)
+      occ = 1;
+    grid = occ * kNumSMs;
+  }
+  march_segment_kernel<<<grid, kMarchThreads, 0, s>>>(p, ntiles, ntiles * max_segments, tile_counter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  march_pixel_pass_kernel<3><<<blocks, kMarchThreads, 0, s>>>(p, ntiles);
   return cudaGetLastError();
 }
 

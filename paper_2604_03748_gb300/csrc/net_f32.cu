@@ -210,213 +210,6 @@ __global__ void __launch_bounds__(128) convT_f32_kernel(const float* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// NAFBlock adapters (C0 = 16), four at once
-// ---------------------------------------------------------------------------
-// Offsets inside one adapter's kAdapterParams floats (blob order).
-struct AdOff {
-  static constexpr int C = kC0;
-  static constexpr int ln1w = 0, ln1b = C;
-  static constexpr int pw1w = 2 * C, pw1b = pw1w + 2 * C * C;
-  static constexpr int dww = pw1b + 2 * C, dwb = dww + 18 * C;
-  static constexpr int scaw = dwb + 2 * C, scab = scaw + C * C;
-  static constexpr int pw2w = scab + C, pw2b = pw2w + C * C;
-  static constexpr int beta = pw2b + C;
-  static constexpr int ln2w = beta + C, ln2b = ln2w + C;
-  static constexpr int f1w = ln2b + C, f1b = f1w + 2 * C * C;
-  static constexpr int f2w = f1b + 2 * C, f2b = f2w + C * C;
-  static constexpr int gamma = f2b + C;
-  static constexpr int headw = gamma + C, headb = headw + 2 * C;
-  static constexpr int total = headb + 2;
-};
-static_assert(AdOff::total == kAdapterParams, "adapter layout");
-
-constexpr int kAdTW = 16, kAdTH = 8;                 // adapter tile
-constexpr int kAdHW = kAdTW + 2, kAdHH = kAdTH + 2;  // halo 18 x 10
-constexpr int kAdHalo = kAdHW * kAdHH;               // 180
-constexpr int kAdHaloS = kAdHalo + 1;
-
-__device__ __forceinline__ void layer_norm16(const float* x, const float* w, const float* b,
-                                             float* y) {
-  float mu = 0.f;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) mu += x[c];
-  mu *= (1.f / 16.f);
-  float var = 0.f;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    float d = x[c] - mu;
-    var = fmaf(d, d, var);
-  }
-  var *= (1.f / 16.f);
-  float inv = 1.f / sqrtf(var + 1e-6f);
-#pragma unroll
-  for (int c = 0; c < 16; ++c) y[c] = fmaf((x[c] - mu) * inv, w[c], b[c]);
-}
-
-// Pass 1: x1_a = SG(dw3x3(pw1(LN1(F)))) for the four adapters a; writes x1 (NHWC,
-// 64 channels) and this tile's per-channel sums (deterministic tree order).
-template <typename TA>
-__global__ void __launch_bounds__(128) adapter_pass1(const TA* __restrict__ F,
-                                                     const float* __restrict__ params,
-                                                     TA* __restrict__ x1,
-                                                     float* __restrict__ partial, int H, int W) {
-  __shared__ float fh[kAdHalo * 16];
-  __shared__ float t[32 * kAdHaloS];
-  __shared__ float prm[AdOff::scaw];
-  __shared__ float red[4][16];
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kAdTW, y0 = blockIdx.y * kAdTH;
-  const int tileid = blockIdx.y * gridDim.x + blockIdx.x;
-  for (int e = tid; e < kAdHalo * 16; e += 128) {
-    int hp = e / 16, c = e % 16;
-    int y = y0 + hp / kAdHW - 1, x = x0 + hp % kAdHW - 1;
-    fh[e] = (y >= 0 && y < H && x >= 0 && x < W) ? to_float(F[((size_t)y * W + x) * 16 + c]) : 0.f;
-  }
-  const int tx = tid % kAdTW, ty = tid / kAdTW;
-  const int px = x0 + tx, py = y0 + ty;
-  const bool valid = px < W && py < H;
-  for (int a = 0; a < 4; ++a) {
-    __syncthreads();
-    const float* ap = params + (size_t)a * kAdapterParams;
-    for (int e = tid; e < AdOff::scaw; e += 128) prm[e] = __ldg(ap + e);
-    __syncthreads();
-    for (int hp = tid; hp < kAdHalo; hp += 128) {
-      int y = y0 + hp / kAdHW - 1, x = x0 + hp % kAdHW - 1;
-      if (y >= 0 && y < H && x >= 0 && x < W) {
-        float n[16];
-        layer_norm16(fh + hp * 16, prm + AdOff::ln1w, prm + AdOff::ln1b, n);
-        for (int o = 0; o < 32; ++o) {
-          float s = prm[AdOff::pw1b + o];
-#pragma unroll
-          for (int c = 0; c < 16; ++c) s = fmaf(prm[AdOff::pw1w + o * 16 + c], n[c], s);
-          t[o * kAdHaloS + hp] = s;
-        }
-      } else {
-        for (int o = 0; o < 32; ++o) t[o * kAdHaloS + hp] = 0.f;  // zero padding of dw input
-      }
-    }
-    __syncthreads();
-    float g[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float d0 = prm[AdOff::dwb + c], d1 = prm[AdOff::dwb + c + 16];
-#pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-          int hp = (ty + ky) * kAdHW + tx + kx;
-          d0 = fmaf(prm[AdOff::dww + c * 9 + ky * 3 + kx], t[c * kAdHaloS + hp], d0);
-          d1 = fmaf(prm[AdOff::dww + (c + 16) * 9 + ky * 3 + kx], t[(c + 16) * kAdHaloS + hp], d1);
-        }
-      g[c] = valid ? d0 * d1 : 0.f;
-    }
-    if (valid) {
-      TA* dst = x1 + ((size_t)py * W + px) * 64 + a * 16;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) dst[c] = from_float<TA>(g[c]);
-    }
-    // per-channel tile sums: butterfly within each warp, then warps in order
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float v = g[c];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      g[c] = v;
-    }
-    if ((tid & 31) == 0) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) red[tid >> 5][c] = g[c];
-    }
-    __syncthreads();
-    if (tid < 16) {
-      float s = ((red[0][tid] + red[1][tid]) + red[2][tid]) + red[3][tid];
-      partial[(size_t)tileid * 64 + a * 16 + tid] = s;
-    }
-  }
-}
-
-// Reduce the tile sums in a fixed order, then the attention vector
-// att[a][co] = b_sca + W_sca mean_HW(x1_a).
-__global__ void __launch_bounds__(64) adapter_reduce(const float* __restrict__ partial, int ntiles,
-                                                     float inv_count,
-                                                     const float* __restrict__ params,
-                                                     float* __restrict__ att) {
-  __shared__ float mean[64];
-  const int ch = threadIdx.x;
-  float s = 0.f, comp = 0.f;
-  for (int t = 0; t < ntiles; ++t) {
-    float y = partial[(size_t)t * 64 + ch] - comp;
-    float u = s + y;
-    comp = (u - s) - y;
-    s = u;
-  }
-  mean[ch] = s * inv_count;
-  __syncthreads();
-  const int a = ch / 16, co = ch % 16;
-  const float* ap = params + (size_t)a * kAdapterParams;
-  float v = ap[AdOff::scab + co];
-  for (int ci = 0; ci < 16; ++ci) v = fmaf(ap[AdOff::scaw + co * 16 + ci], mean[a * 16 + ci], v);
-  att[ch] = v;
-}
-
-// Pass 2: per pixel, the rest of each NAFBlock and its 1x1 head -> 8 planes.
-template <typename TA>
-__global__ void __launch_bounds__(128) adapter_pass2(const TA* __restrict__ F,
-                                                     const TA* __restrict__ x1,
-                                                     const float* __restrict__ att,
-                                                     const float* __restrict__ params,
-                                                     float* __restrict__ out, int npix) {
-  __shared__ float prm[4 * kAdapterParams];
-  __shared__ float at[64];
-  for (int e = threadIdx.x; e < 4 * kAdapterParams; e += 128) prm[e] = __ldg(params + e);
-  if (threadIdx.x < 64) at[threadIdx.x] = att[threadIdx.x];
-  __syncthreads();
-  const int p = blockIdx.x * 128 + threadIdx.x;
-  if (p >= npix) return;
-  float f[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) f[c] = to_float(F[(size_t)p * 16 + c]);
-  const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
-#pragma unroll 1
-  for (int a = 0; a < 4; ++a) {
-    const float* pp = prm + a * kAdapterParams;
-    float xa[16], y[16], n[16], gsg[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) xa[c] = to_float(x1[(size_t)p * 64 + a * 16 + c]) * at[a * 16 + c];
-#pragma unroll
-    for (int co = 0; co < 16; ++co) {
-      float s = pp[AdOff::pw2b + co];
-#pragma unroll
-      for (int ci = 0; ci < 16; ++ci) s = fmaf(pp[AdOff::pw2w + co * 16 + ci], xa[ci], s);
-      y[co] = fmaf(pp[AdOff::beta + co], s, f[co]);
-    }
-    layer_norm16(y, pp + AdOff::ln2w, pp + AdOff::ln2b, n);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float s0 = pp[AdOff::f1b + c], s1 = pp[AdOff::f1b + c + 16];
-#pragma unroll
-      for (int ci = 0; ci < 16; ++ci) {
-        s0 = fmaf(pp[AdOff::f1w + c * 16 + ci], n[ci], s0);
-        s1 = fmaf(pp[AdOff::f1w + (c + 16) * 16 + ci], n[ci], s1);
-      }
-      gsg[c] = s0 * s1;
-    }
-    float h0 = pp[AdOff::headb], h1 = pp[AdOff::headb + 1];
-#pragma unroll
-    for (int co = 0; co < 16; ++co) {
-      float s = pp[AdOff::f2b + co];
-#pragma unroll
-      for (int ci = 0; ci < 16; ++ci) s = fmaf(pp[AdOff::f2w + co * 16 + ci], gsg[ci], s);
-      float z = fmaf(pp[AdOff::gamma + co], s, y[co]);
-      h0 = fmaf(pp[AdOff::headw + co], z, h0);
-      h1 = fmaf(pp[AdOff::headw + 16 + co], z, h1);
-    }
-    out[(size_t)plane_of[a][0] * npix + p] = h0;
-    out[(size_t)plane_of[a][1] * npix + p] = h1;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // weights and forward
 // ---------------------------------------------------------------------------
 struct NetF32Weights {
@@ -424,7 +217,7 @@ struct NetF32Weights {
   float* conv_b[14];
   float* up_w[3];      // packed [cout/16][cin][4][16]
   float* up_b[3];
-  float* adapters;     // 4 * kAdapterParams, blob order
+  AdapterParamSet adp; // folded adapter parameters
   int conv_cin[14], conv_cout[14], up_cin[3], up_cout[3];
   std::vector<void*> allocs;
 };
@@ -466,14 +259,14 @@ NetF32Weights* net_f32_create(const float* hp, const NetLayout& L, cudaError_t* 
     w->up_w[l] = upload(w, pk, err);
     w->up_b[l] = upload(w, std::vector<float>(hp + L.up_b[l], hp + L.up_b[l] + cout), err);
   }
-  w->adapters = upload(w, std::vector<float>(hp + L.adapter[0], hp + L.adapter[0] + 4 * kAdapterParams), err);
+  adapter_params_from(hp + L.adapter[0], &w->adp.p1, &w->adp.sca, &w->adp.p2);
   if (*err != cudaSuccess) { net_f32_destroy(w); return nullptr; }
   return w;
 }
 
 const float* net_f32_conv_w(const NetF32Weights* w, int l) { return w->conv_w[l]; }
 const float* net_f32_conv_b(const NetF32Weights* w, int l) { return w->conv_b[l]; }
-const float* net_f32_adapters(const NetF32Weights* w) { return w->adapters; }
+const AdapterParamSet& net_f32_adapter_params(const NetF32Weights* w) { return w->adp; }
 
 void net_f32_destroy(NetF32Weights* w) {
   if (!w) return;
@@ -498,7 +291,7 @@ static size_t carve(size_t P, F32Buffers* b, char* base) {
   b->l2a = take(P / 16 * 64); b->l2b = take(P / 16 * 64); b->s3 = take(P / 16 * 64);
   b->l3a = take(P / 64 * 128); b->l3b = take(P / 64 * 128);
   b->x1 = take(P * 64);
-  b->partial = take((P / (kAdTW * kAdTH) + 1024) * 64);
+  b->partial = take(adapter_partial_floats((int)P, 1) + (P / 128 + 1024) * 64);
   b->att = take(64);
   return off;
 }
@@ -529,31 +322,6 @@ template cudaError_t simt_first_conv_half<__nv_bfloat16>(const NetF32Weights*, c
 template cudaError_t simt_first_conv_half<__half>(const NetF32Weights*, const NetImage&, __half*,
                                                   cudaStream_t);
 
-template <typename TA>
-cudaError_t adapters_forward(const NetF32Weights* w, const TA* F, TA* x1, float* partial, float* att,
-                             float* out, int H, int W, cudaStream_t s) {
-  dim3 ag((W + kAdTW - 1) / kAdTW, (H + kAdTH - 1) / kAdTH);
-  const float* prm = net_f32_adapters(w);
-  adapter_pass1<TA><<<ag, 128, 0, s>>>(F, prm, x1, partial, H, W);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t P = (size_t)H * W;
-  adapter_reduce<<<1, 64, 0, s>>>(partial, ag.x * ag.y, 1.f / (float)P, prm, att);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  adapter_pass2<TA><<<(unsigned)((P + 127) / 128), 128, 0, s>>>(F, x1, att, prm, out, (int)P);
-  return cudaGetLastError();
-}
-template cudaError_t adapters_forward<float>(const NetF32Weights*, const float*, float*, float*,
-                                             float*, float*, int, int, cudaStream_t);
-template cudaError_t adapters_forward<__nv_bfloat16>(const NetF32Weights*, const __nv_bfloat16*,
-                                                     __nv_bfloat16*, float*, float*, float*, int,
-                                                     int, cudaStream_t);
-template cudaError_t adapters_forward<__half>(const NetF32Weights*, const __half*, __half*, float*,
-                                              float*, float*, int, int, cudaStream_t);
-
-size_t adapter_partial_floats(int max_w, int max_h) {
-  return (size_t)((max_w + kAdTW - 1) / kAdTW) * ((max_h + kAdTH - 1) / kAdTH) * 64;
-}
 
 template <int CIN>
 static cudaError_t convT(const float* in, const float* w, const float* b, float* out, int H, int W,
@@ -603,7 +371,7 @@ cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* w
   TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s)));
   TRY((conv<16, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), 16, s)));
   // adapters
-  TRY(adapters_forward<float>(w, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  TRY(adapters_run<float>(w->adp, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
 #undef TRY
   return cudaSuccess;
 }

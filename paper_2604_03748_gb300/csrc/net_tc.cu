@@ -38,6 +38,10 @@ constexpr int kHaloW = kPatchW + 2, kHaloH = kPatchH + 2;    // 10 x 18
 constexpr int kHaloPix = kHaloW * kHaloH;                    // 180
 constexpr int kPlane = kHaloPix * 16;                        // bytes per 8-channel plane
 constexpr long long kWaitCycles = 4000000000LL;              // ~2 s at 2 GHz
+#ifndef NSL_CONV_CTAS_PER_SM
+#define NSL_CONV_CTAS_PER_SM 2
+#endif
+constexpr int kConvCtasPerSM = NSL_CONV_CTAS_PER_SM;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -189,6 +193,20 @@ __device__ __forceinline__ uint4 ldg128(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void record_error(unsigned int* err, unsigned int code) {
   if (err) atomicOr_system(err, code);
 }
@@ -206,6 +224,37 @@ struct TcConvArgs {
 };
 
 // Stage the halo of M tile `tile` into `halo` (CIN/8 planes of 180 x 16 bytes).
+template <typename T, int CIN, int MODE>
+__device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint8_t* halo);
+
+// Stage the halo of M tile `tile` with asynchronous 16-byte copies (zero fill
+// outside the image); the max-pool mode reduces 2x2 pixels in registers.
+template <typename T, int CIN, int MODE>
+__device__ __forceinline__ void load_halo_async(const TcConvArgs<T>& a, int tile, uint8_t* halo) {
+  if constexpr (MODE == TC_POOL) {
+    load_halo<T, CIN, MODE>(a, tile, halo);
+  } else {
+    constexpr int G = CIN / 8;
+    const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+    const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
+    for (int e = threadIdx.x; e < kHaloPix * G; e += blockDim.x) {
+      const int hp = e / G, g = e % G;
+      const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+      const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const int yc = in ? y : 0, xc = in ? x : 0;
+      const T* src;
+      if constexpr (MODE == TC_PLAIN) {
+        src = a.inA + ((size_t)yc * a.W + xc) * CIN + g * 8;
+      } else {
+        constexpr int CH = CIN / 2;
+        src = g < G / 2 ? a.inA + ((size_t)yc * a.W + xc) * CH + g * 8
+                        : a.inB + ((size_t)yc * a.W + xc) * CH + (g - G / 2) * 8;
+      }
+      cp_async16(halo + g * kPlane + hp * 16, src, in ? 16u : 0u);
+    }
+  }
+}
+
 template <typename T, int CIN, int MODE>
 __device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint8_t* halo) {
   constexpr int G = CIN / 8;
@@ -272,21 +321,27 @@ struct ConvCfg {
   static constexpr int KS = CIN / 16;                    // 16-channel K steps per tap
   static constexpr int WBYTES = 9 * CIN * NT * 2;        // B operand of one N tile
   static constexpr int HBYTES = G * kPlane;              // one halo buffer
+  // halo buffers in flight: as many as fit next to the weights (2..4)
+  static constexpr int STAGES =
+      (WBYTES + 4 * HBYTES + 64 <= 110 * 1024) ? 4 : ((WBYTES + 3 * HBYTES + 64 <= 227 * 1024) ? 3 : 2);
   static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;
-  static constexpr int SMEM = WBYTES + 2 * HBYTES + 64;  // + barriers and TMEM slot
+  static constexpr int SMEM = WBYTES + STAGES * HBYTES + 64;  // + barriers and TMEM slot
 };
 
 template <typename T, int CIN, int COUT, int NT, int MODE>
 __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   using Cfg = ConvCfg<CIN, COUT, NT>;
+  constexpr int S = Cfg::STAGES;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* wsm = smem;
   uint8_t* halo = smem + Cfg::WBYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + 2 * Cfg::HBYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + S * Cfg::HBYTES);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = blockIdx.y;
   const int ntiles = a.tiles_x * a.tiles_y;
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -308,21 +363,29 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       bulk_g2s(wsm + off, src + off, (uint32_t)n, &bars[0]);
     }
   }
+  // prefetch the first S-1 halos while the weights arrive
+  auto issue = [&](int k) {
+    if (k < nmine) load_halo_async<T, CIN, MODE>(a, blockIdx.x + k * gridDim.x, halo + (k % S) * Cfg::HBYTES);
+    cp_async_commit();  // one group per k, possibly empty, keeps the group count uniform
+  };
+#pragma unroll 1
+  for (int k = 0; k < S - 1; ++k) issue(k);
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 1u);
 
   constexpr uint32_t idesc = idesc_f16kind(Half<T>::kFmt, 128, NT);
   uint32_t phase[2] = {0u, 0u};
-  int buf = 0, prev = -1, prevbuf = 0;
-  for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-    load_halo<T, CIN, MODE>(a, tile, halo + buf * Cfg::HBYTES);
+#pragma unroll 1
+  for (int k = 0; ok && k < nmine; ++k) {
+    const int buf = k % S, acc = k & 1;
+    cp_async_wait<S - 2>();  // this thread's copies of tile k have landed
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t hb = smem_u32(halo + buf * Cfg::HBYTES), wb = smem_u32(wsm);
-      const uint32_t d = tmem + (uint32_t)(buf * NT);
+      const uint32_t d = tmem + (uint32_t)(acc * NT);
       int kk = 0;
 #pragma unroll 1
       for (int tap = 0; tap < 9; ++tap) {
@@ -334,30 +397,34 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
           mma_f16kind(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
         }
       }
-      mma_commit(&bars[1 + buf]);
+      mma_commit(&bars[1 + acc]);
     }
-    if (prev >= 0) {
-      if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+    if (k > 0) {
+      const int pacc = acc ^ 1;
+      if (!mbar_wait(&bars[1 + pacc], phase[pacc])) {
         record_error(a.err, 2u);
         ok = false;
-      } else {
-        tc_fence_after();
-        conv_epilogue<T, NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+        break;
       }
-      phase[prevbuf] ^= 1u;
+      phase[pacc] ^= 1u;
+      tc_fence_after();
+      conv_epilogue<T, NT>(a, blockIdx.x + (k - 1) * gridDim.x, tmem + (uint32_t)(pacc * NT),
+                           nt * NT, COUT);
     }
-    prev = tile;
-    prevbuf = buf;
-    buf ^= 1;
+    // the buffer of tile k-1 is free again (its MMAs completed): refill it
+    issue(k + S - 1);
   }
-  if (ok && prev >= 0) {
-    if (!mbar_wait(&bars[1 + prevbuf], phase[prevbuf])) {
+  if (ok && nmine > 0) {
+    const int pacc = (nmine - 1) & 1;
+    if (!mbar_wait(&bars[1 + pacc], phase[pacc])) {
       record_error(a.err, 2u);
     } else {
       tc_fence_after();
-      conv_epilogue<T, NT>(a, prev, tmem + (uint32_t)(prevbuf * NT), nt * NT, COUT);
+      conv_epilogue<T, NT>(a, blockIdx.x + (nmine - 1) * gridDim.x, tmem + (uint32_t)(pacc * NT),
+                           nt * NT, COUT);
     }
   }
+  cp_async_wait<0>();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
@@ -690,7 +757,12 @@ cudaError_t run_conv(const NetTcWeights* w, int l, const T* inA, const T* inB, T
   TcConvArgs<T> a{inA, inB, w->conv_w[l], w->conv_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
                   (H + kPatchH - 1) / kPatchH, err};
   const int ntiles = a.tiles_x * a.tiles_y;
-  int grid = kNumSMs * L.per_sm / (COUT / NT);
+  // enough CTAs to cover every SM, each pipelining >= 4 tiles when there are
+  // that many: per-SM residency is capped at kConvCtasPerSM
+  const int per_sm = L.per_sm < kConvCtasPerSM ? L.per_sm : kConvCtasPerSM;
+  int grid = kNumSMs * per_sm / (COUT / NT);
+  if (grid > (ntiles + 3) / 4) grid = (ntiles + 3) / 4;
+  if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
   conv3x3_tc_kernel<T, CIN, COUT, NT, MODE><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
@@ -746,7 +818,7 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
   TRY((run_convT<T, 32, 16>(w, 2, B.l1a, B.fa, H1, W1, err, s)));
   TRY((run_conv<T, 32, 16, TC_CONCAT>(w, 12, B.fa, B.s1, B.fb, H, W, err, s)));
   TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 13, B.fb, nullptr, B.fa, H, W, err, s)));
-  TRY(adapters_forward<T>(wf, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  TRY(adapters_run<T>(net_f32_adapter_params(wf), B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
 #undef TRY
   return cudaSuccess;
 }

@@ -53,13 +53,29 @@ struct MarchPlume {
   int tiles_x;        // tiles per row
   int tile_start;     // first tile index of this plume in a batch
   unsigned long long* counter;  // density-evaluation counter (counting variant only)
+  // segmented march scratch ([segment][pixel]) and the segment length S
+  int seg_len;
+  int* seg_nef;       // [pixel] processed view steps
+  float* seg_tau;     // [segment][pixel] optical depth at the segment start
+  float* seg_comp;    // [segment][pixel] its Kahan compensation
+  float* seg_L;       // [segment][pixel] partial guide radiance
 };
 
-#ifndef NSL_MARCH_MIN_BLOCKS
-#define NSL_MARCH_MIN_BLOCKS 6
+#ifndef NSL_MARCH_PIPELINE
+#define NSL_MARCH_PIPELINE 0
 #endif
-constexpr int kMarchTX = 8;          // march tile: 8 x 4 pixels, one warp
-constexpr int kMarchTY = 4;
+#ifndef NSL_MARCH_MIN_BLOCKS
+#define NSL_MARCH_MIN_BLOCKS 8
+#endif
+#ifndef NSL_MARCH_SEG
+#define NSL_MARCH_SEG 8
+#endif
+constexpr int kMarchSegLen = NSL_MARCH_SEG;  // view steps per segment of the segmented march
+#ifndef NSL_MARCH_TX
+#define NSL_MARCH_TX 8
+#endif
+constexpr int kMarchTX = NSL_MARCH_TX;  // march tile: TX x (32/TX) pixels, one warp
+constexpr int kMarchTY = 32 / kMarchTX;
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
@@ -77,6 +93,9 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
 int march_tiles(int W, int H);
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
                          bool count = false);
+int march_max_segments(int nx, int ny, int nz, float h, int seg_len);
+cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
+                                   cudaStream_t s);
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
                                int* tile_counter, cudaStream_t s);
 
@@ -132,16 +151,48 @@ cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* w
                             size_t ws_bytes, cudaStream_t s);
 const float* net_f32_conv_w(const NetF32Weights* w, int l);  // SIMT-packed conv weights
 const float* net_f32_conv_b(const NetF32Weights* w, int l);
-const float* net_f32_adapters(const NetF32Weights* w);       // 4 adapters, blob order
 
 // SIMT pieces shared with the tensor-core path
 template <typename T>
 cudaError_t simt_first_conv_half(const NetF32Weights* w, const NetImage& img, T* out,
                                  cudaStream_t s);
-template <typename TA>
-cudaError_t adapters_forward(const NetF32Weights* w, const TA* F, TA* x1, float* partial,
-                             float* att, float* out, int H, int W, cudaStream_t s);
+
+// NAFBlock adapters (adapters.cu): weights as kernel parameters, LayerNorm
+// affines folded into the following 1x1 convolutions.
+struct AdapterP1 {            // pass 1: pw1 (LN1 folded), depthwise 3x3
+  float w1[4][2 * kC0][kC0];
+  float b1[4][2 * kC0];
+  float dww[4][2 * kC0][9];
+  float dwb[4][2 * kC0];
+};
+struct AdapterSCA {           // simplified channel attention 1x1
+  float w[4][kC0][kC0];
+  float b[4][kC0];
+};
+struct AdapterP2 {            // pass 2: pw2, beta, ffn1 (LN2 folded), ffn2, gamma, head
+  float w2[4][kC0][kC0];
+  float b2[4][kC0];
+  float beta[4][kC0];
+  float f1[4][2 * kC0][kC0];
+  float fb1[4][2 * kC0];
+  float f2[4][kC0][kC0];
+  float fb2[4][kC0];
+  float gamma[4][kC0];
+  float hw[4][2][kC0];
+  float hb[4][2];
+};
+struct AdapterParamSet {
+  AdapterP1 p1;
+  AdapterSCA sca;
+  AdapterP2 p2;
+};
+void adapter_params_from(const float* adapters_blob, AdapterP1* p1, AdapterSCA* sca,
+                         AdapterP2* p2);
 size_t adapter_partial_floats(int max_w, int max_h);
+template <typename TA>
+cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float* partial,
+                         float* att, float* out, int H, int W, cudaStream_t s);
+const AdapterParamSet& net_f32_adapter_params(const NetF32Weights* w);
 
 // tensor-core (tcgen05) network, 16-bit operands (elem 0 = FP16, 1 = BF16),
 // FP32 accumulation in TMEM
