@@ -140,14 +140,14 @@ NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const 
  * every byte of device memory, or code that has no context to keep between
  * frames.  It computes exactly what nsl_guiding_map computes, with the same
  * kernels; the staged grid and the tile counter live in one static device
- * array of 32 MiB + 256 bytes inside libnsl, which every GPU that loads the
+ * array of 40 MiB + 256 bytes inside libnsl, which every GPU that loads the
  * library holds until the process exits.
  *   grid          shape, storage and sigma_scale of density_dev
  *   density_dev, mask_dev, cam, step_voxels, opts, guide_dev, stream
  *                 as for nsl_guiding_map (no light argument)
- * Limits: the grid may hold at most 2,097,152 voxels (16 bytes each in the
- * staged layout: 128^3 fits); larger grids return NSL_ERR_INVALID_ARG with a
- * message, and nothing is queued.  No cudaMalloc, cudaFree or other allocating
+ * Limits: the staged grid takes 16 bytes per cell of (nx+1)(ny+1)(nz+2) cells
+ * and must fit in 40 MiB (136^3 fits; 137^3 does not); larger grids return
+ * NSL_ERR_INVALID_ARG with a message, and nothing is queued.  No cudaMalloc, cudaFree or other allocating
  * call is made.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it: make that
  * first call before any stream capture.  All calls share the one array and it

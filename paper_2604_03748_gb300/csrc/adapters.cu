@@ -26,6 +26,8 @@ constexpr int kTW = 16, kTH = 8;        // pass-1 tile (128 pixels)
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kHalo = kHW * kHH;        // 180
 constexpr int kHaloS = kHalo + 1;
+constexpr int kXS = C + 4;              // padded row of the normalised halo: 80 bytes,
+                                        // conflict-free 16-byte accesses per quarter warp
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
                                                       const __grid_constant__ AdapterP1 P,
                                                       TA* __restrict__ x1,
                                                       float* __restrict__ partial, int H, int W) {
-  __shared__ __align__(16) float xh[kHalo * C];     // normalised halo
+  __shared__ __align__(16) float xh[kHalo * kXS];   // normalised halo
   __shared__ float t[2 * C * kHaloS];               // pw1 output of one adapter
   __shared__ float red[4][C];
   __shared__ bool inside[kHalo];
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
       for (int c = 0; c < C; ++c) v[c] = 0.f;
     }
     normalise16(v, n);
-    float4* dst = reinterpret_cast<float4*>(xh + hp * C);
+    float4* dst = reinterpret_cast<float4*>(xh + hp * kXS);
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = make_float4(n[4 * q], n[4 * q + 1], n[4 * q + 2], n[4 * q + 3]);
   }
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
     // (the depthwise convolution pads its input with zeros)
     for (int hp = tid; hp < kHalo; hp += 128) {
       float n[C];
-      const float4* src = reinterpret_cast<const float4*>(xh + hp * C);
+      const float4* src = reinterpret_cast<const float4*>(xh + hp * kXS);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float4 v = src[q];

@@ -48,10 +48,10 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
   float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
-  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
   float c00, c10, c01, c11;
   if constexpr (kMarchLayout == kLayoutLinear) {
+    const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
+    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
     const int x0 = max(ix, 0), x1 = min(ix + 1, g.nx - 1);
     const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
     const float* r00 = g.v + (z0 * plane + (unsigned)(y0 * g.nx));
@@ -67,6 +67,8 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
     c01 = fmaf(tx, v101 - v001, v001);
     c11 = fmaf(tx, v111 - v011, v011);
   } else if constexpr (kMarchLayout == kLayoutXPair) {
+    const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
+    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
     if (ix < 0) { ix = 0; tx = 0.f; }
     const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
     const float2* q = reinterpret_cast<const float2*>(g.v);
@@ -79,12 +81,13 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
     c01 = fmaf(tx, b0.y - b0.x, b0.x);
     c11 = fmaf(tx, b1.y - b1.x, b1.x);
   } else {
-    if (ix < 0) { ix = 0; tx = 0.f; }
-    if (iy < 0) { iy = 0; ty = 0.f; }
-    const float4* q = reinterpret_cast<const float4*>(g.v);
-    const unsigned row = (unsigned)(iy * g.nx + ix);
-    const float4 a = __ldg(q + (z0 * plane + row));
-    const float4 b = __ldg(q + (z1 * plane + row));
+    // padded quads: cell (ix+1, iy+1, iz+1) of a (nx+1) x (ny+1) x (nz+2) array,
+    // every index of a point inside the box is in range
+    const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+    const float4* q = reinterpret_cast<const float4*>(g.v) +
+                      ((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1));
+    const float4 a = __ldg(q);
+    const float4 b = __ldg(q + pl);
     c00 = fmaf(tx, a.y - a.x, a.x);
     c10 = fmaf(tx, a.w - a.z, a.z);
     c01 = fmaf(tx, b.y - b.x, b.x);
@@ -113,17 +116,14 @@ __device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float 
   f.tx = __fsub_rn(qx, flx);
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
-  int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  if (ix < 0) { ix = 0; f.tx = 0.f; }
-  if (iy < 0) { iy = 0; f.ty = 0.f; }
-  ix = min(ix, g.nx - 1);
-  iy = min(iy, g.ny - 1);
-  const int z0 = min(max(iz, 0), g.nz - 1), z1 = min(max(iz + 1, 0), g.nz - 1);
-  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-  const unsigned row = (unsigned)(iy * g.nx + ix);
-  const float4* q = reinterpret_cast<const float4*>(g.v);
-  f.a = __ldg(q + (z0 * plane + row));
-  f.b = __ldg(q + (z1 * plane + row));
+  // clamp into the padded array so that a speculative fetch is always in range
+  const int ix = min(max((int)flx, -1), g.nx - 1), iy = min(max((int)fly, -1), g.ny - 1);
+  const int iz = min(max((int)flz, -1), g.nz - 1);
+  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+  const float4* q = reinterpret_cast<const float4*>(g.v) +
+                    ((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1));
+  f.a = __ldg(q);
+  f.b = __ldg(q + pl);
   return f;
 }
 
@@ -588,13 +588,36 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
-// One thread per staged cell (i,j,k), writing the layout kMarchLayout of
-// sigma' = scale * rho * [mask == 0] with the +1 neighbours clamped to the edge.
+// One thread per staged cell, writing the layout kMarchLayout of sigma' =
+// scale * rho * [mask == 0] with out-of-grid neighbours clamped to the edge.
+// The quad layout is padded: cell (a, b, c) of an (nx+1) x (ny+1) x (nz+2) array
+// holds the x/y 2x2 neighbourhood whose low corner is voxel (a-1, b-1) of slice
+// c-1, every index clamped into the grid.
 template <typename T>
 __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
                                                     const uint8_t* __restrict__ mask, int nx,
                                                     int ny, int nz, float scale,
                                                     float* __restrict__ out) {
+  auto val = [&](size_t idx) {
+    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+  };
+  if constexpr (kMarchLayout == kLayoutQuad) {
+    const int px = nx + 1, py = ny + 1, pz = nz + 2;
+    const size_t n = (size_t)px * py * pz;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * blockDim.x) {
+      const int a = (int)(c % px);
+      const size_t r = c / px;
+      const int b = (int)(r % py);
+      const int k = min(max((int)(r / py) - 1, 0), nz - 1);
+      const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
+      const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+      const size_t b0 = ((size_t)k * ny + j0) * nx, b1 = ((size_t)k * ny + j1) * nx;
+      __stcs(reinterpret_cast<float4*>(out) + c,
+             make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1)));
+    }
+    return;
+  }
   const size_t n = (size_t)nx * ny * nz;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (size_t)gridDim.x * blockDim.x) {
@@ -604,22 +627,16 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
     const size_t k = r / ny;
     const int i1 = min(i + 1, nx - 1), j1 = min(j + 1, ny - 1);
     const size_t b0 = (k * ny + j) * nx, b1 = (k * ny + j1) * nx;
-    auto val = [&](size_t idx) {
-      return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
-    };
     if constexpr (kMarchLayout == kLayoutLinear)
       __stcs(out + c, val(b0 + i));
     else if constexpr (kMarchLayout == kLayoutXPair)
       __stcs(reinterpret_cast<float2*>(out) + c, make_float2(val(b0 + i), val(b0 + i1)));
-    else
-      __stcs(reinterpret_cast<float4*>(out) + c,
-             make_float4(val(b0 + i), val(b0 + i1), val(b1 + i), val(b1 + i1)));
   }
 }
 
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s) {
-  const size_t n = (size_t)nx * ny * nz;
+  const size_t n = staged_floats(nx, ny, nz) / 4;
   int blocks = (int)((n + 255) / 256);
   if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
   if (blocks < 1) blocks = 1;

@@ -10,10 +10,11 @@
 
 namespace nsl {
 
-// Scratch bytes: 32 MiB for the staged grid (at 16 bytes per voxel in the
-// x/y-quad layout that is 2,097,152 voxels, e.g. 128^3) plus 256 bytes for the
-// tile counter.  Every GPU that loads the library holds this array until exit.
-constexpr size_t kNoAllocGridBytes = size_t(32) << 20;
+// Scratch bytes: 40 MiB for the staged grid (16 bytes per cell of the padded
+// x/y-quad layout, (nx+1)(ny+1)(nz+2) cells: 128^3 takes 34.6 MB) plus 256 bytes
+// for the tile counter.  Every GPU that loads the library holds this array until
+// exit.
+constexpr size_t kNoAllocGridBytes = size_t(40) << 20;
 constexpr size_t kNoAllocBytes = kNoAllocGridBytes + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

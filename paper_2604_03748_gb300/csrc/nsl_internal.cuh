@@ -86,7 +86,8 @@ constexpr int kLayoutLinear = 0, kLayoutXPair = 1, kLayoutQuad = 2;
 #endif
 constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
 inline size_t staged_floats(int nx, int ny, int nz) {
-  return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : kMarchLayout == kLayoutXPair ? 2 : 4);
+  if (kMarchLayout == kLayoutQuad) return (size_t)(nx + 1) * (ny + 1) * (nz + 2) * 4;  // padded
+  return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : 2);
 }
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s);

@@ -50,7 +50,7 @@ def test_noalloc_rejects_oversize_grid():
     nsl.load()
     pf = I.config_plain_64()
     g = torch.empty((3, 128, 128), dtype=torch.float32, device="cuda:0")
-    d = torch.empty((129, 128, 128), dtype=torch.float32, device="cuda:0")  # 2,113,536 voxels > 2,097,152
+    d = torch.empty((140, 140, 140), dtype=torch.float32, device="cuda:0")  # 45.2 MB staged > 40 MiB
     with pytest.raises(nsl.NslError) as ei:
         nsl.nsl_guiding_map_noalloc(d.shape, nsl.NSL_F32, 1.0, d, None, pf.camera, 4.0, g)
     assert ei.value.status == nsl.NSL_ERR_INVALID_ARG
