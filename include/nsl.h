@@ -198,6 +198,72 @@ NSL_API nsl_status nsl_render_frame_host(nsl_ctx* ctx, const void* density_host,
                                  const nsl_march_opts* opts, int precision, float* guide_host,
                                  float* lightmaps_host, float* rgba_host, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched frames: many plumes of different grid and billboard sizes per call.
+ * Every stage runs as one launch over all plumes (staging, the guide march,
+ * each network layer, shading), so the launch count does not grow with the
+ * number of plumes.  Same arithmetic as the single-plume calls.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const void* density_dev;   /* [nz][ny][nx], grid.dtype */
+  const uint8_t* mask_dev;   /* obstacle mask or NULL */
+  nsl_grid_desc grid;
+  nsl_camera camera;         /* billboard size = camera.width x camera.height */
+  float step_voxels;         /* march step h */
+  nsl_light light;           /* light for the shading of this plume */
+  float* guide_dev;          /* out [3][H][W] */
+  float* lightmaps_dev;      /* out [8][H][W] */
+  float* rgba_dev;           /* out [4][H][W], or NULL to skip the shading */
+} nsl_plume;
+
+typedef struct nsl_batch nsl_batch;
+
+/* Create a batch context for up to max_plumes (<= 64) plumes per call with
+ * the network weights of an NSLW blob (see nsl_create).  Device buffers are
+ * sized by the first call and grow when a later call needs more. */
+NSL_API nsl_status nsl_batch_create(const void* weights_blob, size_t blob_bytes, int max_plumes,
+                                    nsl_batch** out);
+NSL_API void nsl_batch_destroy(nsl_batch* b);
+
+/* Guide, lightmaps and (where rgba_dev is set) shading for n plumes, with one
+ * set of march options for all; precision NSL_PREC_F16 or NSL_PREC_BF16.
+ * Asynchronous on `stream`; the caller owns every buffer of `plumes`. */
+NSL_API nsl_status nsl_batch_render(nsl_batch* b, const nsl_plume* plumes, int n,
+                                    const nsl_march_opts* opts, int precision, void* stream);
+
+/* Capture one nsl_batch_render of exactly these plumes into a CUDA graph
+ * (after one ordinary render, so that nothing is allocated while capturing);
+ * `stream` must not be the legacy default stream.  nsl_batch_launch_graph
+ * replays it; between replays nsl_batch_update_graph may change cameras,
+ * lights, sigma scales and march options (buffers, grid and billboard sizes
+ * and steps must stay those of the capture, else NSL_ERR_INVALID_ARG); call it
+ * only once the previous replay has completed.  All calls on one batch must be
+ * ordered on one stream (or synchronised): they share its scratch buffers. */
+NSL_API nsl_status nsl_batch_capture_graph(nsl_batch* b, const nsl_plume* plumes, int n,
+                                           const nsl_march_opts* opts, int precision,
+                                           void* stream);
+NSL_API nsl_status nsl_batch_update_graph(nsl_batch* b, const nsl_plume* plumes, int n,
+                                          const nsl_march_opts* opts);
+NSL_API nsl_status nsl_batch_launch_graph(nsl_batch* b, void* stream);
+
+/* Tuning knobs of the batched path: view steps per segment of the march (1..64),
+ * march CTAs per SM (0 = occupancy maximum), convolution CTAs per SM (1..4).
+ * Changing them (nsl_batch_autotune does) drops a captured graph, as does a
+ * render that has to grow a device buffer; capture again afterwards. */
+NSL_API nsl_status nsl_batch_set_tuning(nsl_batch* b, int seg_len, int march_blocks_per_sm,
+                                        int conv_ctas_per_sm);
+NSL_API nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blocks_per_sm,
+                                        int* conv_ctas_per_sm);
+
+/* Autotuner: renders the batch under each candidate setting of the tuning
+ * knobs, times it with CUDA events (median of 3) and keeps the fastest.  With
+ * a cache path (JSON lines), a result stored for the same batch signature
+ * (sizes, steps, precision) is applied without timing and new results are
+ * appended.  Synchronises `stream`; *best_ms (may be NULL) gets the time. */
+NSL_API nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
+                                      const nsl_march_opts* opts, int precision,
+                                      const char* cache_path, void* stream, float* best_ms);
+
 /* Description of the last error raised on the calling thread ("" if none). */
 NSL_API const char* nsl_last_error(void);
 NSL_API const char* nsl_status_str(nsl_status s);

@@ -98,17 +98,16 @@ __device__ __forceinline__ void normalise16(const float* x, float* y) {
 // Pass 1: one CTA per 16x8 tile; the 18x10 halo of F is normalised once and
 // shared by the four adapters.
 template <typename TA>
-__global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
-                                                      const __grid_constant__ AdapterP1 P,
-                                                      TA* __restrict__ x1,
-                                                      float* __restrict__ partial, int H, int W) {
+__device__ __forceinline__ void adapters_pass1_tile(const TA* __restrict__ F, const AdapterP1& P,
+                                                    TA* __restrict__ x1,
+                                                    float* __restrict__ partial, int H, int W,
+                                                    int bx, int by, int tileid) {
   __shared__ __align__(16) float xh[kHalo * kXS];   // normalised halo
   __shared__ float t[2 * C * kHaloS];               // pw1 output of one adapter
   __shared__ float red[4][C];
   __shared__ bool inside[kHalo];
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
-  const int tileid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int x0 = bx * kTW, y0 = by * kTH;
   for (int hp = tid; hp < kHalo; hp += 128) {
     const int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
     const bool in = y >= 0 && y < H && x >= 0 && x < W;
@@ -185,12 +184,67 @@ __global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
   }
 }
 
+template <typename TA>
+__global__ void __launch_bounds__(128) adapters_pass1(const TA* __restrict__ F,
+                                                      const __grid_constant__ AdapterP1 P,
+                                                      TA* __restrict__ x1,
+                                                      float* __restrict__ partial, int H, int W) {
+  adapters_pass1_tile<TA>(F, P, x1, partial, H, W, blockIdx.x, blockIdx.y,
+                          blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// grouped: tiles numbered image after image
+template <typename TA>
+struct AdapterGroupArgs {
+  AdapterImg<TA> img[kMaxGroup];
+  int tile_start[kMaxGroup + 1];
+  int px_start[kMaxGroup + 1];
+  int nimg;
+};
+
+__device__ __forceinline__ int group_of(const int* start, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(128) adapters_pass1_group(const __grid_constant__ AdapterGroupArgs<TA> G,
+                                                            const __grid_constant__ AdapterP1 P) {
+  const int k = group_of(G.tile_start, G.nimg, blockIdx.x);
+  const AdapterImg<TA>& im = G.img[k];
+  const int t = blockIdx.x - G.tile_start[k];
+  const int tx = (im.W + kTW - 1) / kTW;
+  adapters_pass1_tile<TA>(im.F, P, im.x1, im.partial, im.H, im.W, t % tx, t / tx, t);
+}
+
 // Deterministic reduction of the tile sums: 16 lanes per channel each sum a
 // fixed stride of tiles (Kahan), then a fixed tree; att = W_sca mean + b_sca.
+__device__ __forceinline__ void adapters_reduce_body(const float* __restrict__ partial, int ntiles,
+                                                     float inv_count, const AdapterSCA& S,
+                                                     float* __restrict__ att);
+
 __global__ void __launch_bounds__(1024) adapters_reduce(const float* __restrict__ partial,
                                                         int ntiles, float inv_count,
                                                         const __grid_constant__ AdapterSCA S,
                                                         float* __restrict__ att) {
+  adapters_reduce_body(partial, ntiles, inv_count, S, att);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(1024) adapters_reduce_group(const __grid_constant__ AdapterGroupArgs<TA> G,
+                                                              const __grid_constant__ AdapterSCA S) {
+  const AdapterImg<TA>& im = G.img[blockIdx.x];
+  adapters_reduce_body(im.partial, G.tile_start[blockIdx.x + 1] - G.tile_start[blockIdx.x],
+                       1.f / ((float)im.H * (float)im.W), S, im.att);
+}
+
+__device__ __forceinline__ void adapters_reduce_body(const float* __restrict__ partial, int ntiles,
+                                                     float inv_count, const AdapterSCA& S,
+                                                     float* __restrict__ att) {
   __shared__ float part[16][4 * C];
   __shared__ float mean[4 * C];
   const int ch = threadIdx.x % (4 * C), lane = threadIdx.x / (4 * C);  // 64 channels x 16 lanes
@@ -223,6 +277,12 @@ __global__ void __launch_bounds__(1024) adapters_reduce(const float* __restrict_
 
 // Pass 2: one thread per pixel, the four adapters in turn, output planes.
 template <typename TA>
+__device__ __forceinline__ void adapters_pass2_pixel(const TA* __restrict__ F,
+                                                     const TA* __restrict__ x1, const float* at,
+                                                     const AdapterP2& P, float* __restrict__ out,
+                                                     int npix, int p);
+
+template <typename TA>
 __global__ void __launch_bounds__(128) adapters_pass2(const TA* __restrict__ F,
                                                       const TA* __restrict__ x1,
                                                       const float* __restrict__ att,
@@ -233,6 +293,29 @@ __global__ void __launch_bounds__(128) adapters_pass2(const TA* __restrict__ F,
   __syncthreads();
   const int p = blockIdx.x * 128 + threadIdx.x;
   if (p >= npix) return;
+  adapters_pass2_pixel<TA>(F, x1, at, P, out, npix, p);
+}
+
+// grouped: each image's pixels start a fresh 128-pixel block (px_start counts blocks)
+template <typename TA>
+__global__ void __launch_bounds__(128) adapters_pass2_group(const __grid_constant__ AdapterGroupArgs<TA> G,
+                                                            const __grid_constant__ AdapterP2 P) {
+  __shared__ float at[4 * C];
+  const int k = group_of(G.px_start, G.nimg, blockIdx.x);
+  const AdapterImg<TA>& im = G.img[k];
+  if (threadIdx.x < 4 * C) at[threadIdx.x] = im.att[threadIdx.x];
+  __syncthreads();
+  const int npix = im.H * im.W;
+  const int p = (blockIdx.x - G.px_start[k]) * 128 + threadIdx.x;
+  if (p >= npix) return;
+  adapters_pass2_pixel<TA>(im.F, im.x1, at, P, im.out, npix, p);
+}
+
+template <typename TA>
+__device__ __forceinline__ void adapters_pass2_pixel(const TA* __restrict__ F,
+                                                     const TA* __restrict__ x1, const float* at,
+                                                     const AdapterP2& P, float* __restrict__ out,
+                                                     int npix, int p) {
   float f[C];
   load16(F + (size_t)p * C, f);
   constexpr int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
@@ -337,6 +420,36 @@ cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float*
   adapters_pass2<TA><<<(unsigned)((P + 127) / 128), 128, 0, s>>>(F, x1, att, prm.p2, out, (int)P);
   return cudaGetLastError();
 }
+
+template <typename TA>
+cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
+                               cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  AdapterGroupArgs<TA> G{};
+  G.nimg = n;
+  int tiles = 0, blocks = 0;
+  for (int k = 0; k < n; ++k) {
+    G.img[k] = imgs[k];
+    G.tile_start[k] = tiles;
+    G.px_start[k] = blocks;
+    tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
+    blocks += (imgs[k].W * imgs[k].H + 127) / 128;
+  }
+  G.tile_start[n] = tiles;
+  G.px_start[n] = blocks;
+  adapters_pass1_group<TA><<<tiles, 128, 0, s>>>(G, prm.p1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adapters_reduce_group<TA><<<n, 1024, 0, s>>>(G, prm.sca);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  adapters_pass2_group<TA><<<blocks, 128, 0, s>>>(G, prm.p2);
+  return cudaGetLastError();
+}
+template cudaError_t adapters_run_group<__nv_bfloat16>(const AdapterParamSet&,
+                                                       const AdapterImg<__nv_bfloat16>*, int,
+                                                       cudaStream_t);
+template cudaError_t adapters_run_group<__half>(const AdapterParamSet&, const AdapterImg<__half>*,
+                                                int, cudaStream_t);
 
 template cudaError_t adapters_run<float>(const AdapterParamSet&, const float*, float*, float*,
                                          float*, float*, int, int, cudaStream_t);

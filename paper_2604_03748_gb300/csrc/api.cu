@@ -286,10 +286,11 @@ nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, 
   return NSL_OK;
 }
 
-static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
-                              const nsl_march_opts* opts, const char* fn, MarchPlume* p) {
-  nsl_status st = check_camera(c, cam, fn);
-  if (st != NSL_OK) return st;
+}  // extern "C"
+
+namespace nsl {
+nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, float step,
+                            const nsl_march_opts* opts, const char* fn, MarchPlume* p) {
   if (!(step > 0.f) || !std::isfinite(step))
     return fail(NSL_ERR_INVALID_ARG, "%s: step must be > 0", fn);
   nsl_march_opts o;
@@ -300,9 +301,8 @@ static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
   if (!(o.phase_g > -1.f && o.phase_g < 1.f))
     return fail(NSL_ERR_INVALID_ARG, "%s: phase_g must be in (-1, 1)", fn);
   *p = MarchPlume{};
-  p->vol = c->staged;
-  p->nx = c->grid.nx; p->ny = c->grid.ny; p->nz = c->grid.nz;
-  cam_frame_from(*cam, &p->cam);
+  p->nx = grid.nx; p->ny = grid.ny; p->nz = grid.nz;
+  cam_frame_from(cam, &p->cam);
   p->h = step;
   p->tau_depth = o.tau_depth;
   p->t_min = o.t_min;
@@ -312,8 +312,74 @@ static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
   p->g = o.phase_g;
   for (int k = 0; k < 3; ++k) p->I[k] = o.surrogate_I[k];
   p->segment_exact = o.segment_exact ? 1 : 0;
-  p->tiles_x = (cam->width + kMarchTX - 1) / kMarchTX;
+  p->tiles_x = (cam.width + kMarchTX - 1) / kMarchTX;
   p->tile_start = 0;
+  return NSL_OK;
+}
+
+nsl_status check_camera_basic(const nsl_camera* cam, const char* fn) {
+  if (!cam) return fail(NSL_ERR_INVALID_ARG, "%s: camera is NULL", fn);
+  if (cam->kind != NSL_CAM_ORTHO && cam->kind != NSL_CAM_PERSP)
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad camera kind", fn);
+  if (cam->width < 8 || cam->height < 8 || cam->width % 8 || cam->height % 8 ||
+      cam->width > 8192 || cam->height > 8192)
+    return fail(NSL_ERR_INVALID_ARG, "%s: width/height must be multiples of 8 in [8, 8192]", fn);
+  double fx = (double)cam->target[0] - cam->eye[0], fy = (double)cam->target[1] - cam->eye[1],
+         fz = (double)cam->target[2] - cam->eye[2];
+  double fl = std::sqrt(fx * fx + fy * fy + fz * fz);
+  if (!(fl > 0.0)) return fail(NSL_ERR_INVALID_ARG, "%s: eye == target", fn);
+  double rx = fy * cam->up[2] - fz * cam->up[1], ry = fz * cam->up[0] - fx * cam->up[2],
+         rz = fx * cam->up[1] - fy * cam->up[0];
+  if (!(std::sqrt(rx * rx + ry * ry + rz * rz) > 1e-9 * fl))
+    return fail(NSL_ERR_INVALID_ARG, "%s: up is parallel to the view direction", fn);
+  if (cam->kind == NSL_CAM_PERSP && !(cam->fov_y_deg > 0.f && cam->fov_y_deg < 179.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: fov_y_deg out of (0, 179)", fn);
+  if (cam->kind == NSL_CAM_ORTHO && !(cam->ortho_height > 0.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: ortho_height must be > 0", fn);
+  return NSL_OK;
+}
+
+// rgb_c = sum_q M[c][q] L_q + E: per colour channel the sum over lights of the
+// light's intensity times the |w_p| weight of each of the six planes
+nsl_status shade_matrix(const nsl_camera& cam, const nsl_light* lights, int n_lights,
+                        float Mout[3][6], const char* fn) {
+  CamFrame fr;
+  cam_frame_from(cam, &fr);
+  double M[3][6] = {};
+  for (int l = 0; l < n_lights; ++l) {
+    double v[3] = {lights[l].dir[0], lights[l].dir[1], lights[l].dir[2]};
+    double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nv > 0.0) || !std::isfinite(nv))
+      return fail(NSL_ERR_INVALID_ARG, "%s: light %d has a zero direction", fn, l);
+    double w[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      w[0] += v[k] / nv * fr.r[k];
+      w[1] += v[k] / nv * fr.u[k];
+      w[2] += v[k] / nv * fr.f[k];
+    }
+    for (int ch = 0; ch < 3; ++ch) {
+      double I = lights[l].intensity[ch];
+      for (int p = 0; p < 3; ++p) {
+        if (w[p] >= 0.0) M[ch][2 * p] += I * w[p];
+        else M[ch][2 * p + 1] += I * -w[p];
+      }
+    }
+  }
+  for (int ch = 0; ch < 3; ++ch)
+    for (int q = 0; q < 6; ++q) Mout[ch][q] = (float)M[ch][q];
+  return NSL_OK;
+}
+}  // namespace nsl
+
+extern "C" {
+
+static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
+                              const nsl_march_opts* opts, const char* fn, MarchPlume* p) {
+  nsl_status st = check_camera(c, cam, fn);
+  if (st != NSL_OK) return st;
+  st = fill_march_plume(c->grid, *cam, step, opts, fn, p);
+  if (st != NSL_OK) return st;
+  p->vol = c->staged;
   return NSL_OK;
 }
 
@@ -435,35 +501,13 @@ nsl_status nsl_shade(nsl_ctx* c, const float* lm, int width, int height, const n
   nsl_camera cc = *cam;
   cc.width = width;
   cc.height = height;
-  CamFrame fr;
-  cam_frame_from(cc, &fr);
   ShadeArgs a{};
   a.lm = lm;
   a.rgba = rgba;
   a.W = width;
   a.H = height;
-  double M[3][6] = {};
-  for (int l = 0; l < n_lights; ++l) {
-    double v[3] = {lights[l].dir[0], lights[l].dir[1], lights[l].dir[2]};
-    double nv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    if (!(nv > 0.0) || !std::isfinite(nv))
-      return fail(NSL_ERR_INVALID_ARG, "nsl_shade: light %d has a zero direction", l);
-    double w[3] = {0, 0, 0};
-    for (int k = 0; k < 3; ++k) {
-      w[0] += v[k] / nv * fr.r[k];
-      w[1] += v[k] / nv * fr.u[k];
-      w[2] += v[k] / nv * fr.f[k];
-    }
-    for (int ch = 0; ch < 3; ++ch) {
-      double I = lights[l].intensity[ch];
-      for (int p = 0; p < 3; ++p) {
-        if (w[p] >= 0.0) M[ch][2 * p] += I * w[p];
-        else M[ch][2 * p + 1] += I * -w[p];
-      }
-    }
-  }
-  for (int ch = 0; ch < 3; ++ch)
-    for (int q = 0; q < 6; ++q) a.M[ch][q] = (float)M[ch][q];
+  nsl_status st = shade_matrix(cc, lights, n_lights, a.M, "nsl_shade");
+  if (st != NSL_OK) return st;
   cudaError_t e = launch_shade(a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_shade");
   return NSL_OK;

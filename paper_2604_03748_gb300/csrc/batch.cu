@@ -1,0 +1,531 @@
+// Batched frames: many plumes of different grid and billboard sizes per call.
+// Every stage is one launch over all plumes -- staging, the three passes of
+// the segmented guide march, each network layer (grouped tensor-core
+// convolutions and adapters), shading -- so the launch count does not grow
+// with the number of plumes.  The per-plume tables the kernels read live in one
+// device block that is refreshed from one pinned host block per call, which
+// lets a captured CUDA graph pick up new cameras, lights and options on every
+// replay.  An autotuner picks the segment length of the march, the march grid
+// and the convolutions' CTAs per SM by timing candidates on the actual batch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nsl_internal.cuh"
+
+using namespace nsl;
+
+namespace {
+
+struct Tables {                       // one pinned host block, mirrored on the device
+  MarchPlume march[kMaxGroup];
+  int tile_starts[kMaxGroup + 1];
+  int item_starts[kMaxGroup + 1];
+  int tile_counts[kMaxGroup];
+  StageItem stage[kMaxGroup];
+  int stage_starts[kMaxGroup + 1];
+  ShadeArgs shade[kMaxGroup];
+  int shade_starts[kMaxGroup + 1];
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Pinned host copies of the tables: a ring for ordinary renders (a slot is
+// rewritten only after the copy that last read it has run) and one slot owned
+// by the captured graph, whose copy node reads it at every replay.
+constexpr int kRing = 3;
+constexpr int kGraphSlot = kRing;
+
+// Launch totals baked into a captured graph; a table update must keep them.
+struct Totals {
+  int n, tiles, items, sblocks, nshade, hblocks, precision;
+  bool operator==(const Totals& o) const {
+    return n == o.n && tiles == o.tiles && items == o.items && sblocks == o.sblocks &&
+           nshade == o.nshade && hblocks == o.hblocks && precision == o.precision;
+  }
+};
+
+}  // namespace
+
+struct nsl_batch {
+  int max_plumes = 0;
+  std::vector<float> params;
+  NetLayout layout{};
+  NetF32Weights* wf = nullptr;
+  NetTcWeights* wtc[2] = {};
+  // device memory, grown on demand (never while a graph is being captured)
+  void* staged = nullptr;  size_t staged_bytes = 0;
+  void* seg = nullptr;     size_t seg_bytes = 0;
+  void* net = nullptr;     size_t net_bytes = 0;
+  Tables* host[kRing + 1] = {};    // pinned
+  cudaEvent_t host_done[kRing] = {};
+  int next_slot = 0;
+  Tables* dev = nullptr;
+  int* counter = nullptr;
+  unsigned int* err_host = nullptr;
+  unsigned int* err_dev = nullptr;
+  // tuning
+  int seg_len = kMarchSegLen;
+  int seg_blocks_per_sm = 0;       // 0 = occupancy maximum
+  int conv_ctas = 2;
+  // captured graph
+  cudaGraphExec_t exec = nullptr;
+  bool capturing = false;
+  Totals graph_totals{};
+  std::vector<nsl_plume> graph_plumes;  // buffers and sizes of the capture
+};
+
+namespace {
+
+void drop_graph(nsl_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_plumes.clear();
+}
+
+// Grow a device region; a captured graph that points into the old region is
+// dropped (a later nsl_batch_launch_graph reports that there is none).
+nsl_status grow(nsl_batch* b, void** p, size_t* have, size_t need, cudaStream_t s,
+                const char* what) {
+  if (need <= *have) return NSL_OK;
+  if (b->capturing)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch: %s would grow during graph capture or update", what);
+  NSL_CUDA_TRY(cudaStreamSynchronize(s));
+  drop_graph(b);
+  cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  NSL_CUDA_TRY(cudaMalloc(p, need));
+  *have = need;
+  return NSL_OK;
+}
+
+nsl_status validate_plume(const nsl_plume& pl, int k) {
+  char fn[64];
+  std::snprintf(fn, sizeof fn, "nsl_batch: plume %d", k);
+  const nsl_grid_desc& g = pl.grid;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > 4096 || g.ny > 4096 || g.nz > 4096 ||
+      (g.dtype != NSL_F32 && g.dtype != NSL_F16) || !(g.sigma_scale >= 0.f))
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad grid", fn);
+  if (!pl.density_dev || !pl.guide_dev || !pl.lightmaps_dev)
+    return fail(NSL_ERR_INVALID_ARG, "%s: NULL buffer", fn);
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(pl.density_dev) |
+                         reinterpret_cast<uintptr_t>(pl.mask_dev) |
+                         reinterpret_cast<uintptr_t>(pl.guide_dev) |
+                         reinterpret_cast<uintptr_t>(pl.lightmaps_dev) |
+                         reinterpret_cast<uintptr_t>(pl.rgba_dev);
+  if (bits & 15u) return fail(NSL_ERR_INVALID_ARG, "%s: buffers must be 16-byte aligned", fn);
+  return check_camera_basic(&pl.camera, fn);
+}
+
+// Fill host table slot `T` for this batch and size every device region.
+nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const nsl_march_opts* opts,
+                   int precision, cudaStream_t s, std::vector<NetImage>* imgs,
+                   std::vector<void*>* ws, Totals* tot) {
+  if (n < 1 || n > b->max_plumes || n > kMaxGroup)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch: n must be in [1, %d]", b->max_plumes);
+  if (precision != NSL_PREC_BF16 && precision != NSL_PREC_F16)
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: batched network needs NSL_PREC_BF16 or NSL_PREC_F16");
+  size_t staged = 0, seg = 0, net = 0;
+  std::vector<size_t> off_staged(n), off_seg(n), off_net(n);
+  std::vector<int> maxseg(n);
+  for (int k = 0; k < n; ++k) {
+    nsl_status st = validate_plume(pl[k], k);
+    if (st != NSL_OK) return st;
+    const nsl_grid_desc& g = pl[k].grid;
+    const size_t P = (size_t)pl[k].camera.width * pl[k].camera.height;
+    off_staged[k] = staged;
+    staged += align256(staged_floats(g.nx, g.ny, g.nz) * sizeof(float));
+    maxseg[k] = march_max_segments(g.nx, g.ny, g.nz, pl[k].step_voxels, b->seg_len);
+    off_seg[k] = seg;
+    seg += align256(P * sizeof(int)) + align256(3 * (size_t)maxseg[k] * P * sizeof(float));
+    off_net[k] = net;
+    net += align256(net_tc_workspace_bytes(pl[k].camera.width, pl[k].camera.height));
+  }
+  nsl_status st = grow(b, &b->staged, &b->staged_bytes, staged, s, "staged grids");
+  if (st != NSL_OK) return st;
+  if ((st = grow(b, &b->seg, &b->seg_bytes, seg, s, "march scratch")) != NSL_OK) return st;
+  if ((st = grow(b, &b->net, &b->net_bytes, net, s, "network workspace")) != NSL_OK) return st;
+
+  int tiles = 0, items = 0, sblocks = 0, hblocks = 0, nshade = 0;
+  imgs->clear();
+  ws->clear();
+  for (int k = 0; k < n; ++k) {
+    const nsl_plume& p = pl[k];
+    MarchPlume& m = T.march[k];
+    st = fill_march_plume(p.grid, p.camera, p.step_voxels, opts, "nsl_batch", &m);
+    if (st != NSL_OK) return st;
+    const size_t P = (size_t)p.camera.width * p.camera.height;
+    float* staged_k = reinterpret_cast<float*>(static_cast<char*>(b->staged) + off_staged[k]);
+    m.vol = staged_k;
+    m.guide = p.guide_dev;
+    m.seg_len = b->seg_len;
+    char* sb = static_cast<char*>(b->seg) + off_seg[k];
+    m.seg_nef = reinterpret_cast<int*>(sb);
+    m.seg_tau = reinterpret_cast<float*>(sb + align256(P * sizeof(int)));
+    m.seg_comp = m.seg_tau + (size_t)maxseg[k] * P;
+    m.seg_L = m.seg_comp + (size_t)maxseg[k] * P;
+    const int nt = march_tiles(p.camera.width, p.camera.height);
+    T.tile_starts[k] = tiles;
+    T.item_starts[k] = items;
+    T.tile_counts[k] = nt;
+    tiles += nt;
+    items += nt * maxseg[k];
+    StageItem& si = T.stage[k];
+    si = StageItem{p.density_dev, p.mask_dev, staged_k, p.grid.nx, p.grid.ny, p.grid.nz,
+                   p.grid.dtype, p.grid.sigma_scale};
+    T.stage_starts[k] = sblocks;
+    sblocks += stage_batch_blocks(si);
+    if (p.rgba_dev) {
+      ShadeArgs& a = T.shade[nshade];
+      a = ShadeArgs{};
+      a.lm = p.lightmaps_dev;
+      a.rgba = p.rgba_dev;
+      a.W = p.camera.width;
+      a.H = p.camera.height;
+      st = shade_matrix(p.camera, &p.light, 1, a.M, "nsl_batch");
+      if (st != NSL_OK) return st;
+      T.shade_starts[nshade] = hblocks;
+      hblocks += (int)((P / 4 + 255) / 256);
+      ++nshade;
+    }
+    const double diag = std::sqrt((double)p.grid.nx * p.grid.nx + (double)p.grid.ny * p.grid.ny +
+                                  (double)p.grid.nz * p.grid.nz);
+    imgs->push_back(NetImage{p.guide_dev, p.lightmaps_dev, p.camera.height, p.camera.width,
+                             (float)(1.0 / diag)});
+    ws->push_back(static_cast<char*>(b->net) + off_net[k]);
+  }
+  T.tile_starts[n] = tiles;
+  T.item_starts[n] = items;
+  T.stage_starts[n] = sblocks;
+  T.shade_starts[nshade] = hblocks;
+  *tot = Totals{n, tiles, items, sblocks, nshade, hblocks, precision};
+  return NSL_OK;
+}
+
+nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts* opts,
+                  int precision, cudaStream_t s) {
+  if (*reinterpret_cast<volatile unsigned int*>(b->err_host) != 0) {
+    const unsigned code = *b->err_host;
+    *b->err_host = 0;
+    return fail(NSL_ERR_TIMEOUT, "nsl_batch: an earlier tensor-core launch timed out (code 0x%x)", code);
+  }
+  // host slot: the graph's own while capturing, else the next ring slot once
+  // the copy that last read it has run
+  int slot = kGraphSlot;
+  if (!b->capturing) {
+    slot = b->next_slot;
+    b->next_slot = (b->next_slot + 1) % kRing;
+    NSL_CUDA_TRY(cudaEventSynchronize(b->host_done[slot]));
+  }
+  Tables& T = *b->host[slot];
+  std::vector<NetImage> imgs;
+  std::vector<void*> ws;
+  Totals tot{};
+  nsl_status st = prepare(b, T, pl, n, opts, precision, s, &imgs, &ws, &tot);
+  if (st != NSL_OK) return st;
+  const int nshade = tot.nshade;
+  NSL_CUDA_TRY(cudaMemcpyAsync(b->dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, s));
+  if (!b->capturing) NSL_CUDA_TRY(cudaEventRecord(b->host_done[slot], s));
+  else b->graph_totals = tot;
+  cudaError_t e = launch_stage_batch(b->dev->stage, b->dev->stage_starts, n, T.stage_starts[n], s);
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: staging");
+  int per_sm = march_segment_blocks_max();
+  if (b->seg_blocks_per_sm > 0 && b->seg_blocks_per_sm < per_sm) per_sm = b->seg_blocks_per_sm;
+  e = launch_march_segmented_batch(b->dev->march, b->dev->tile_starts, b->dev->item_starts,
+                                   b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
+                                   per_sm * kNumSMs, b->counter, s);
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: march");
+  const int elem = precision == NSL_PREC_BF16 ? 1 : 0;
+  if (!b->wtc[elem]) {
+    if (b->capturing) return fail(NSL_ERR_INVALID_ARG, "nsl_batch: weights not built before capture");
+    b->wtc[elem] = net_tc_create(b->params.data(), b->layout, elem, &e);
+    if (!b->wtc[elem]) return cuda_fail(e, "nsl_batch: tensor-core weights");
+  }
+  const int saved = net_tc_ctas_per_sm();
+  net_tc_set_ctas_per_sm(b->conv_ctas);
+  e = net_tc_forward_group(b->wtc[elem], b->wf, imgs.data(), ws.data(), n, b->err_dev, s);
+  net_tc_set_ctas_per_sm(saved);
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: network");
+  if (nshade) {
+    e = launch_shade_batch(b->dev->shade, b->dev->shade_starts, nshade, T.shade_starts[nshade], s);
+    if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: shading");
+  }
+  return NSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nsl_status nsl_batch_create(const void* blob, size_t blob_bytes, int max_plumes, nsl_batch** out) {
+  if (!out) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: out is NULL");
+  *out = nullptr;
+  if (!blob || blob_bytes < 20) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: bad blob");
+  if (max_plumes < 1 || max_plumes > kMaxGroup)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: max_plumes must be in [1, %d]", kMaxGroup);
+  const unsigned char* bb = static_cast<const unsigned char*>(blob);
+  uint32_t ver, c0, nf;
+  if (std::memcmp(bb, "NSLW", 4) != 0) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: bad magic");
+  std::memcpy(&ver, bb + 4, 4);
+  std::memcpy(&c0, bb + 8, 4);
+  std::memcpy(&nf, bb + 12, 4);
+  if (ver != 1 || (size_t)nf * 4 + 20 != blob_bytes)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: blob version or size mismatch");
+  NetLayout L{};
+  if (!build_net_layout((int)c0, &L)) return fail(NSL_ERR_UNSUPPORTED, "nsl_batch_create: C0=%u", c0);
+  if (L.total != nf) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: parameter count");
+  uint32_t chk = 0, stored;
+  for (uint32_t i = 0; i < nf; ++i) {
+    uint32_t w;
+    std::memcpy(&w, bb + 16 + 4 * (size_t)i, 4);
+    chk += w;
+  }
+  std::memcpy(&stored, bb + 16 + 4 * (size_t)nf, 4);
+  if (chk != stored) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: blob checksum mismatch");
+  nsl_batch* b = new nsl_batch();
+  b->max_plumes = max_plumes;
+  b->layout = L;
+  b->params.resize(nf);
+  std::memcpy(b->params.data(), bb + 16, (size_t)nf * 4);
+  cudaError_t e;
+  b->wf = net_f32_create(b->params.data(), L, &e);
+  if (!b->wf) { nsl_batch_destroy(b); return cuda_fail(e, "nsl_batch_create: weights"); }
+  for (int i = 0; i <= kRing; ++i) {
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&b->host[i]), sizeof(Tables), cudaHostAllocDefault)) != cudaSuccess ||
+        (i < kRing && (e = cudaEventCreateWithFlags(&b->host_done[i], cudaEventDisableTiming)) != cudaSuccess)) {
+      nsl_batch_destroy(b);
+      return cuda_fail(e, "nsl_batch_create: host tables");
+    }
+    std::memset(b->host[i], 0, sizeof(Tables));
+  }
+  if ((e = cudaMalloc(reinterpret_cast<void**>(&b->dev), sizeof(Tables))) != cudaSuccess ||
+      (e = cudaMalloc(reinterpret_cast<void**>(&b->counter), 256)) != cudaSuccess ||
+      (e = cudaHostAlloc(reinterpret_cast<void**>(&b->err_host), sizeof(unsigned int), cudaHostAllocMapped)) != cudaSuccess) {
+    nsl_batch_destroy(b);
+    return cuda_fail(e, "nsl_batch_create: allocation");
+  }
+  *b->err_host = 0;
+  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&b->err_dev), b->err_host, 0)) != cudaSuccess) {
+    nsl_batch_destroy(b);
+    return cuda_fail(e, "nsl_batch_create: error word");
+  }
+  *out = b;
+  return NSL_OK;
+}
+
+void nsl_batch_destroy(nsl_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  drop_graph(b);
+  net_f32_destroy(b->wf);
+  net_tc_destroy(b->wtc[0]);
+  net_tc_destroy(b->wtc[1]);
+  cudaFree(b->staged);
+  cudaFree(b->seg);
+  cudaFree(b->net);
+  cudaFree(b->dev);
+  cudaFree(b->counter);
+  for (int i = 0; i <= kRing; ++i) {
+    if (b->host[i]) cudaFreeHost(b->host[i]);
+    if (i < kRing && b->host_done[i]) cudaEventDestroy(b->host_done[i]);
+  }
+  if (b->err_host) cudaFreeHost(b->err_host);
+  delete b;
+}
+
+nsl_status nsl_batch_render(nsl_batch* b, const nsl_plume* plumes, int n,
+                            const nsl_march_opts* opts, int precision, void* stream) {
+  if (!b || !plumes) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_render: NULL argument");
+  return render(b, plumes, n, opts, precision, static_cast<cudaStream_t>(stream));
+}
+
+nsl_status nsl_batch_capture_graph(nsl_batch* b, const nsl_plume* plumes, int n,
+                                   const nsl_march_opts* opts, int precision, void* stream) {
+  if (!b || !plumes) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_capture_graph: NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!s) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_capture_graph: needs a non-default stream");
+  // one ordinary render first: every buffer, weight set and launch configuration
+  // is created outside the capture
+  nsl_status st = render(b, plumes, n, opts, precision, s);
+  if (st != NSL_OK) return st;
+  NSL_CUDA_TRY(cudaStreamSynchronize(s));
+  drop_graph(b);
+  NSL_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  b->capturing = true;
+  st = render(b, plumes, n, opts, precision, s);
+  b->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != NSL_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_batch_capture_graph: end capture");
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(e, "nsl_batch_capture_graph: instantiate");
+  }
+  b->graph_plumes.assign(plumes, plumes + n);
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_update_graph(nsl_batch* b, const nsl_plume* plumes, int n,
+                                  const nsl_march_opts* opts) {
+  if (!b || !plumes || !b->exec)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_update_graph: no captured graph");
+  if (n != (int)b->graph_plumes.size())
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_update_graph: the graph was captured for %d plumes",
+                (int)b->graph_plumes.size());
+  // the launches, kernel arguments and buffers baked into the graph must stay
+  // valid: same buffers, grid and billboard sizes and step; cameras (pose,
+  // projection), lights, sigma scales and march options may change
+  for (int k = 0; k < n; ++k) {
+    const nsl_plume &a = plumes[k], &c = b->graph_plumes[k];
+    if (a.density_dev != c.density_dev || a.mask_dev != c.mask_dev || a.guide_dev != c.guide_dev ||
+        a.lightmaps_dev != c.lightmaps_dev || a.rgba_dev != c.rgba_dev || a.grid.nx != c.grid.nx ||
+        a.grid.ny != c.grid.ny || a.grid.nz != c.grid.nz || a.grid.dtype != c.grid.dtype ||
+        a.camera.width != c.camera.width || a.camera.height != c.camera.height ||
+        a.step_voxels != c.step_voxels)
+      return fail(NSL_ERR_INVALID_ARG,
+                  "nsl_batch_update_graph: plume %d changes a buffer, a size or the step of the capture", k);
+  }
+  std::vector<NetImage> imgs;
+  std::vector<void*> ws;
+  Totals tot{};
+  Tables scratch;
+  b->capturing = true;  // refuse any growth
+  nsl_status st = prepare(b, scratch, plumes, n, opts, b->graph_totals.precision, nullptr, &imgs, &ws, &tot);
+  b->capturing = false;
+  if (st != NSL_OK) return st;
+  if (!(tot == b->graph_totals))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_update_graph: launch sizes differ from the capture");
+  std::memcpy(b->host[kGraphSlot], &scratch, sizeof(Tables));
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_launch_graph(nsl_batch* b, void* stream) {
+  if (!b || !b->exec) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_launch_graph: no captured graph");
+  NSL_CUDA_TRY(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_set_tuning(nsl_batch* b, int seg_len, int march_blocks_per_sm,
+                                int conv_ctas_per_sm) {
+  if (!b) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_set_tuning: NULL batch");
+  if (seg_len < 1 || seg_len > 64 || march_blocks_per_sm < 0 || march_blocks_per_sm > 16 ||
+      conv_ctas_per_sm < 1 || conv_ctas_per_sm > 4)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_set_tuning: value out of range");
+  // a captured graph holds the old segment layout and launch shapes
+  if (seg_len != b->seg_len || march_blocks_per_sm != b->seg_blocks_per_sm ||
+      conv_ctas_per_sm != b->conv_ctas) {
+    cudaDeviceSynchronize();
+    drop_graph(b);
+  }
+  b->seg_len = seg_len;
+  b->seg_blocks_per_sm = march_blocks_per_sm;
+  b->conv_ctas = conv_ctas_per_sm;
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blocks_per_sm,
+                                int* conv_ctas_per_sm) {
+  if (!b || !seg_len || !march_blocks_per_sm || !conv_ctas_per_sm)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_get_tuning: NULL argument");
+  *seg_len = b->seg_len;
+  *march_blocks_per_sm = b->seg_blocks_per_sm;
+  *conv_ctas_per_sm = b->conv_ctas;
+  return NSL_OK;
+}
+
+// Autotuner: time each candidate (segment length x march blocks per SM x conv
+// CTAs per SM) on this batch with CUDA events (median of 3 after one warm-up)
+// and keep the fastest; with a cache path, a result recorded for the same batch
+// signature is reused and new results are appended.
+nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
+                              const nsl_march_opts* opts, int precision, const char* cache_path,
+                              void* stream, float* best_ms) {
+  if (!b || !plumes) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_autotune: NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // batch signature: sizes, steps and precision
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) { h = (h ^ v) * 1099511628211ull; };
+  mix((unsigned long long)n);
+  mix((unsigned long long)precision);
+  for (int k = 0; k < n; ++k) {
+    mix((unsigned long long)plumes[k].grid.nx);
+    mix((unsigned long long)plumes[k].grid.ny);
+    mix((unsigned long long)plumes[k].grid.nz);
+    mix((unsigned long long)plumes[k].camera.width);
+    mix((unsigned long long)plumes[k].camera.height);
+    unsigned int sb;
+    std::memcpy(&sb, &plumes[k].step_voxels, 4);
+    mix(sb);
+  }
+  char key[32];
+  std::snprintf(key, sizeof key, "%016llx", h);
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[256];
+      while (std::fgets(line, sizeof line, f)) {
+        char k2[32];
+        int a, c, d;
+        float ms;
+        if (std::sscanf(line, " {\"key\": \"%31[0-9a-f]\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
+                              "\"conv_ctas_per_sm\": %d, \"ms\": %f}", k2, &a, &c, &d, &ms) == 5 &&
+            std::strcmp(k2, key) == 0) {
+          std::fclose(f);
+          if (best_ms) *best_ms = ms;
+          return nsl_batch_set_tuning(b, a, c, d);
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  const int seg_lens[] = {4, 8, 16};
+  const int conv_ctas[] = {1, 2, 4};
+  const int occ = march_segment_blocks_max();
+  std::vector<int> march_bps = {0};
+  for (int v : {4, 6}) if (v < occ) march_bps.push_back(v);
+  cudaEvent_t e0, e1;
+  NSL_CUDA_TRY(cudaEventCreate(&e0));
+  NSL_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bs = b->seg_len, bm = b->seg_blocks_per_sm, bc = b->conv_ctas;
+  nsl_status st = NSL_OK;
+  for (int sl : seg_lens)
+    for (int mb : march_bps)
+      for (int cc : conv_ctas) {
+        nsl_batch_set_tuning(b, sl, mb, cc);
+        float t[3];
+        for (int r = 0; r < 4 && st == NSL_OK; ++r) {
+          cudaEventRecord(e0, s);
+          st = render(b, plumes, n, opts, precision, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+        }
+        if (st != NSL_OK) break;
+        float a = t[0], c = t[1], d = t[2], med = a > c ? (c > d ? c : (a > d ? d : a)) : (a > d ? a : (c > d ? d : c));
+        if (med < best) { best = med; bs = sl; bm = mb; bc = cc; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NSL_OK) return st;
+  nsl_batch_set_tuning(b, bs, bm, bc);
+  if (best_ms) *best_ms = best;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "{\"key\": \"%s\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
+                      "\"conv_ctas_per_sm\": %d, \"ms\": %.4f}\n", key, bs, bm, bc, best);
+      std::fclose(f);
+    }
+  }
+  return NSL_OK;
+}
+
+}  // extern "C"

@@ -579,6 +579,88 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
 }
 
 // ---------------------------------------------------------------------------
+// batched forms: many plumes of different sizes per launch (device tables)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_start(const int* __restrict__ starts, int n, int v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(starts + mid) <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// pass 1 / pass 3 over the tiles of all plumes (tile_starts[p] = first tile of plume p)
+template <int kPass>
+__global__ void __launch_bounds__(kMarchThreads) march_pass_batch_kernel(
+    const MarchPlume* __restrict__ table, const int* __restrict__ tile_starts, int nplumes,
+    int total_tiles) {
+  const int lane = threadIdx.x & 31;
+  const int gt = blockIdx.x * (kMarchThreads / 32) + (threadIdx.x >> 5);
+  if (gt >= total_tiles) return;
+  const int k = find_start(tile_starts, nplumes, gt);
+  const MarchPlume& P = table[k];
+  const int tile = gt - __ldg(tile_starts + k);
+  const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
+  const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+  if (i >= P.cam.W || j >= P.cam.H) return;
+  if (kPass == 1) march_view_pixel(P, i, j);
+  else march_finish_pixel(P, i, j);
+}
+
+// pass 2 over (plume, segment, tile) items: item_starts[p] = first item of plume
+// p, whose items are segment-major over its tiles
+__global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks) march_segment_batch_kernel(
+    const MarchPlume* __restrict__ table, const int* __restrict__ item_starts,
+    const int* __restrict__ tile_counts, int nplumes, int nitems, int* __restrict__ counter) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;
+    const int k = find_start(item_starts, nplumes, item);
+    const MarchPlume& P = table[k];
+    const int local = item - __ldg(item_starts + k), nt = __ldg(tile_counts + k);
+    const int seg = local / nt, tile = local % nt;
+    const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
+    const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+    if (i < P.cam.W && j < P.cam.H) march_segment(P, i, j, seg);
+  }
+}
+
+cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int* tile_starts_dev,
+                                         const int* item_starts_dev, const int* tile_counts_dev,
+                                         int nplumes, int total_tiles, int total_items,
+                                         int seg_blocks, int* counter, cudaStream_t s) {
+  if (total_tiles == 0) return cudaSuccess;
+  const int wpb = kMarchThreads / 32;
+  const int blocks = (total_tiles + wpb - 1) / wpb;
+  march_pass_batch_kernel<1><<<blocks, kMarchThreads, 0, s>>>(table_dev, tile_starts_dev, nplumes,
+                                                             total_tiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+  march_segment_batch_kernel<<<seg_blocks, kMarchThreads, 0, s>>>(
+      table_dev, item_starts_dev, tile_counts_dev, nplumes, total_items, counter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  march_pass_batch_kernel<3><<<blocks, kMarchThreads, 0, s>>>(table_dev, tile_starts_dev, nplumes,
+                                                             total_tiles);
+  return cudaGetLastError();
+}
+
+int march_segment_blocks_max() {
+  static int occ = 0;
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_batch_kernel,
+                                                      kMarchThreads, 0) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+  }
+  return occ;
+}
+
+// ---------------------------------------------------------------------------
 // grid staging: sigma' = scale * rho * [mask == 0], FP16 widened exactly
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -626,7 +708,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
     const int j = (int)(r % ny);
     const size_t k = r / ny;
     const int i1 = min(i + 1, nx - 1), j1 = min(j + 1, ny - 1);
-    const size_t b0 = (k * ny + j) * nx, b1 = (k * ny + j1) * nx;
+    const size_t b0 = (k * ny + j) * nx;
+    (void)j1;
     if constexpr (kMarchLayout == kLayoutLinear)
       __stcs(out + c, val(b0 + i));
     else if constexpr (kMarchLayout == kLayoutXPair)
@@ -689,6 +772,100 @@ cudaError_t launch_shade(const ShadeArgs& a, cudaStream_t s) {
   int blocks = (int)((P4 + 255) / 256);
   if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
   shade_kernel<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// batched staging and shading: blocks numbered plume after plume
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stage_cells(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                            int nx, int ny, int nz, float scale, float* __restrict__ out,
+                                            size_t c0, size_t c1) {
+  auto val = [&](size_t idx) {
+    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+  };
+  const int px = nx + 1, py = ny + 1;
+  for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const int a = (int)(c % px);
+    const size_t r = c / px;
+    const int b = (int)(r % py);
+    const int k = min(max((int)(r / py) - 1, 0), nz - 1);
+    const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
+    const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+    const size_t b0 = ((size_t)k * ny + j0) * nx, b1 = ((size_t)k * ny + j1) * nx;
+    __stcs(reinterpret_cast<float4*>(out) + c,
+           make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1)));
+  }
+}
+
+constexpr int kStageChunk = 2048;  // staged cells per block
+
+__global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __restrict__ items,
+                                                          const int* __restrict__ block_starts,
+                                                          int n) {
+  const int k = find_start(block_starts, n, blockIdx.x);
+  const StageItem& it = items[k];
+  const size_t cells = (size_t)(it.nx + 1) * (it.ny + 1) * (it.nz + 2);
+  const size_t c0 = (size_t)(blockIdx.x - __ldg(block_starts + k)) * kStageChunk;
+  const size_t c1 = c0 + kStageChunk < cells ? c0 + kStageChunk : cells;
+  if (it.dtype == NSL_F16)
+    stage_cells<__half>(static_cast<const __half*>(it.density), it.mask, it.nx, it.ny, it.nz,
+                        it.scale, it.out, c0, c1);
+  else
+    stage_cells<float>(static_cast<const float*>(it.density), it.mask, it.nx, it.ny, it.nz,
+                       it.scale, it.out, c0, c1);
+}
+
+int stage_batch_blocks(const StageItem& it) {
+  const size_t cells = (size_t)(it.nx + 1) * (it.ny + 1) * (it.nz + 2);
+  return (int)((cells + kStageChunk - 1) / kStageChunk);
+}
+
+cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_starts_dev, int n,
+                               int total_blocks, cudaStream_t s) {
+  static_assert(kMarchLayout == kLayoutQuad, "batched staging writes the padded quad layout");
+  if (total_blocks == 0) return cudaSuccess;
+  stage_batch_kernel<<<total_blocks, 256, 0, s>>>(items_dev, block_starts_dev, n);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) shade_batch_kernel(const ShadeArgs* __restrict__ items,
+                                                          const int* __restrict__ block_starts,
+                                                          int n) {
+  const int k = find_start(block_starts, n, blockIdx.x);
+  const ShadeArgs& a = items[k];
+  const size_t P4 = (size_t)a.W * a.H / 4;
+  const size_t q = (size_t)(blockIdx.x - __ldg(block_starts + k)) * 256 + threadIdx.x;
+  if (q >= P4) return;
+  const float4* lm = reinterpret_cast<const float4*>(a.lm);
+  float4* out = reinterpret_cast<float4*>(a.rgba);
+  float4 L[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) L[c] = __ldcs(lm + c * P4 + q);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float4 acc = L[7];
+#pragma unroll
+    for (int pl = 0; pl < 6; ++pl) {
+      const float m = a.M[c][pl];
+      acc.x = fmaf(m, L[pl].x, acc.x); acc.y = fmaf(m, L[pl].y, acc.y);
+      acc.z = fmaf(m, L[pl].z, acc.z); acc.w = fmaf(m, L[pl].w, acc.w);
+    }
+    __stcs(out + c * P4 + q, acc);
+  }
+  float4 al;
+  al.x = fminf(fmaxf(1.f - L[6].x, 0.f), 1.f);
+  al.y = fminf(fmaxf(1.f - L[6].y, 0.f), 1.f);
+  al.z = fminf(fmaxf(1.f - L[6].z, 0.f), 1.f);
+  al.w = fminf(fmaxf(1.f - L[6].w, 0.f), 1.f);
+  __stcs(out + 3 * P4 + q, al);
+}
+
+cudaError_t launch_shade_batch(const ShadeArgs* items_dev, const int* block_starts_dev, int n,
+                               int total_blocks, cudaStream_t s) {
+  if (total_blocks == 0) return cudaSuccess;
+  shade_batch_kernel<<<total_blocks, 256, 0, s>>>(items_dev, block_starts_dev, n);
   return cudaGetLastError();
 }
 

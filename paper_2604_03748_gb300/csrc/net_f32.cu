@@ -72,12 +72,41 @@ __device__ __forceinline__ float load_in(const ConvArgs& a, int y, int x, int c)
 }
 
 template <int CIN, int MODE, typename TOut>
+__device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, int bx, int by,
+                                                 int cg);
+
+template <int CIN, int MODE, typename TOut>
 __global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) {
+  conv3x3_f32_tile<CIN, MODE, TOut>(a, cout, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// grouped first layer: 16x16 tiles numbered image after image
+struct ConvGroupArgs {
+  ConvArgs img[kMaxGroup];
+  int tile_start[kMaxGroup + 1];
+  int nimg;
+};
+
+template <typename TOut>
+__global__ void __launch_bounds__(128) first_conv_group_kernel(const __grid_constant__ ConvGroupArgs G) {
+  int lo = 0, hi = G.nimg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (G.tile_start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const ConvArgs& a = G.img[lo];
+  const int t = blockIdx.x - G.tile_start[lo], tx = (a.W + kTW - 1) / kTW;
+  conv3x3_f32_tile<3, IN_GUIDE, TOut>(a, 16, t % tx, t / tx, 0);
+}
+
+template <int CIN, int MODE, typename TOut>
+__device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, int bx, int by,
+                                                 int cg) {
   constexpr int CT = CIN < 16 ? CIN : 16;  // input-channel chunk
   __shared__ float halo[CT * kHaloStride];
   __shared__ __align__(16) float ws[CT * 9 * 16];
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, cg = blockIdx.z;
+  const int x0 = bx * kTW, y0 = by * kTH;
   const int tx = tid % kTW, ty = (tid / kTW) * 2;
   float acc0[16], acc1[16];
 #pragma unroll
@@ -317,6 +346,27 @@ cudaError_t simt_first_conv_half(const NetF32Weights* w, const NetImage& img, T*
              img.depth_scale};
   return conv<3, IN_GUIDE, T>(a, 16, s);
 }
+template <typename T>
+cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, T* const* outs,
+                                  int n, cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  ConvGroupArgs G{};
+  G.nimg = n;
+  int tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    G.img[k] = ConvArgs{imgs[k].guide, nullptr, net_f32_conv_w(w, 0), net_f32_conv_b(w, 0), outs[k],
+                        imgs[k].H, imgs[k].W, imgs[k].depth_scale};
+    G.tile_start[k] = tiles;
+    tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
+  }
+  G.tile_start[n] = tiles;
+  first_conv_group_kernel<T><<<tiles, 128, 0, s>>>(G);
+  return cudaGetLastError();
+}
+template cudaError_t simt_first_conv_group<__nv_bfloat16>(const NetF32Weights*, const NetImage*,
+                                                          __nv_bfloat16* const*, int, cudaStream_t);
+template cudaError_t simt_first_conv_group<__half>(const NetF32Weights*, const NetImage*,
+                                                   __half* const*, int, cudaStream_t);
 template cudaError_t simt_first_conv_half<__nv_bfloat16>(const NetF32Weights*, const NetImage&,
                                                          __nv_bfloat16*, cudaStream_t);
 template cudaError_t simt_first_conv_half<__half>(const NetF32Weights*, const NetImage&, __half*,

@@ -211,26 +211,47 @@ __device__ __forceinline__ void record_error(unsigned int* err, unsigned int cod
   if (err) atomicOr_system(err, code);
 }
 
+// One image of a (grouped) layer launch.  A launch covers up to kMaxGroup
+// images of any sizes that share the layer's weights; tiles are numbered
+// image after image (tile_start is the image's first global tile).
 template <typename T>
-struct TcConvArgs {
+struct ConvImg {
   const T* inA;              // NHWC input (POOL: at 2H x 2W; CONCAT: first CIN/2 channels)
   const T* inB;              // CONCAT: last CIN/2 channels (the skip tensor)
-  const uint8_t* wpack;      // [n tiles][9 taps][CIN/16][NT rows x 32 bytes]
-  const float* bias;         // [COUT]
   T* out;                    // NHWC [H][W][COUT]
   int H, W;                  // convolution (output) size
-  int tiles_x, tiles_y;      // M tiles per row / column
+  int tiles_x;               // M tiles per row
+  int tile_start;
+};
+
+template <typename T>
+struct TcConvArgs {
+  ConvImg<T> img[kMaxGroup];
+  int nimg, total_tiles;
+  const uint8_t* wpack;      // [n tiles][9 taps][CIN/16][NT rows x 32 bytes]
+  const float* bias;         // [COUT]
   unsigned int* err;
 };
 
+// image of global tile t (uniform across the CTA) and the tile inside it
+template <typename A>
+__device__ __forceinline__ int image_of(const A& a, int t) {
+  int lo = 0, hi = a.nimg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.img[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Stage the halo of M tile `tile` into `halo` (CIN/8 planes of 180 x 16 bytes).
 template <typename T, int CIN, int MODE>
-__device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint8_t* halo);
+__device__ __forceinline__ void load_halo(const ConvImg<T>& a, int tile, uint8_t* halo);
 
 // Stage the halo of M tile `tile` with asynchronous 16-byte copies (zero fill
 // outside the image); the max-pool mode reduces 2x2 pixels in registers.
 template <typename T, int CIN, int MODE>
-__device__ __forceinline__ void load_halo_async(const TcConvArgs<T>& a, int tile, uint8_t* halo) {
+__device__ __forceinline__ void load_halo_async(const ConvImg<T>& a, int tile, uint8_t* halo) {
   if constexpr (MODE == TC_POOL) {
     load_halo<T, CIN, MODE>(a, tile, halo);
   } else {
@@ -256,7 +277,7 @@ __device__ __forceinline__ void load_halo_async(const TcConvArgs<T>& a, int tile
 }
 
 template <typename T, int CIN, int MODE>
-__device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint8_t* halo) {
+__device__ __forceinline__ void load_halo(const ConvImg<T>& a, int tile, uint8_t* halo) {
   constexpr int G = CIN / 8;
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
@@ -285,8 +306,8 @@ __device__ __forceinline__ void load_halo(const TcConvArgs<T>& a, int tile, uint
 }
 
 template <typename T, int NT>
-__device__ __forceinline__ void conv_epilogue(const TcConvArgs<T>& a, int tile, uint32_t tacc,
-                                              int n0, int cout) {
+__device__ __forceinline__ void conv_epilogue(const ConvImg<T>& a, const float* __restrict__ bias,
+                                              int tile, uint32_t tacc, int n0, int cout) {
   const int warp = threadIdx.x >> 5;
   const int m = threadIdx.x;  // accumulator row = pixel of the patch
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
@@ -300,8 +321,8 @@ __device__ __forceinline__ void conv_epilogue(const TcConvArgs<T>& a, int tile, 
     __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      h[q] = Half<T>::pack(fmaxf(v[2 * q] + __ldg(a.bias + n0 + c + 2 * q), 0.f),
-                           fmaxf(v[2 * q + 1] + __ldg(a.bias + n0 + c + 2 * q + 1), 0.f));
+      h[q] = Half<T>::pack(fmaxf(v[2 * q] + __ldg(bias + n0 + c + 2 * q), 0.f),
+                           fmaxf(v[2 * q + 1] + __ldg(bias + n0 + c + 2 * q + 1), 0.f));
     if (valid) {
       reinterpret_cast<uint4*>(dst + c)[0] = reinterpret_cast<const uint4*>(h)[0];
       reinterpret_cast<uint4*>(dst + c)[1] = reinterpret_cast<const uint4*>(h)[1];
@@ -339,7 +360,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = blockIdx.y;
-  const int ntiles = a.tiles_x * a.tiles_y;
+  const int ntiles = a.total_tiles;
   // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
   const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -365,7 +386,10 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   }
   // prefetch the first S-1 halos while the weights arrive
   auto issue = [&](int k) {
-    if (k < nmine) load_halo_async<T, CIN, MODE>(a, blockIdx.x + k * gridDim.x, halo + (k % S) * Cfg::HBYTES);
+    if (k < nmine) {
+      const int t = blockIdx.x + k * gridDim.x, im = image_of(a, t);
+      load_halo_async<T, CIN, MODE>(a.img[im], t - a.img[im].tile_start, halo + (k % S) * Cfg::HBYTES);
+    }
     cp_async_commit();  // one group per k, possibly empty, keeps the group count uniform
   };
 #pragma unroll 1
@@ -408,8 +432,9 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       }
       phase[pacc] ^= 1u;
       tc_fence_after();
-      conv_epilogue<T, NT>(a, blockIdx.x + (k - 1) * gridDim.x, tmem + (uint32_t)(pacc * NT),
-                           nt * NT, COUT);
+      const int t = blockIdx.x + (k - 1) * gridDim.x, im = image_of(a, t);
+      conv_epilogue<T, NT>(a.img[im], a.bias, t - a.img[im].tile_start,
+                           tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
     }
     // the buffer of tile k-1 is free again (its MMAs completed): refill it
     issue(k + S - 1);
@@ -420,8 +445,9 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       record_error(a.err, 2u);
     } else {
       tc_fence_after();
-      conv_epilogue<T, NT>(a, blockIdx.x + (nmine - 1) * gridDim.x, tmem + (uint32_t)(pacc * NT),
-                           nt * NT, COUT);
+      const int t = blockIdx.x + (nmine - 1) * gridDim.x, im = image_of(a, t);
+      conv_epilogue<T, NT>(a.img[im], a.bias, t - a.img[im].tile_start,
+                           tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
     }
   }
   cp_async_wait<0>();
@@ -436,12 +462,18 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
 // (2y+a, 2x+b) channel co = bias + sum_ci W[ci][co][a][b] in(y, x)[ci].
 // ---------------------------------------------------------------------------
 template <typename T>
-struct TcConvTArgs {
+struct ConvTImg {
   const T* in;               // NHWC [H][W][CIN]
+  T* out;                    // NHWC [2H][2W][COUT]
+  int H, W, tiles_x, tile_start;
+};
+
+template <typename T>
+struct TcConvTArgs {
+  ConvTImg<T> img[kMaxGroup];
+  int nimg, total_tiles;
   const uint8_t* wpack;      // [CIN/16][N rows x 32 bytes]
   const float* bias;         // [COUT]
-  T* out;                    // NHWC [2H][2W][COUT]
-  int H, W, tiles_x, tiles_y;
   unsigned int* err;
 };
 
@@ -467,7 +499,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + 2 * Cfg::ABYTES);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int ntiles = a.tiles_x * a.tiles_y;
+  const int ntiles = a.total_tiles;
 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -494,11 +526,14 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   uint32_t phase[2] = {0u, 0u};
   int buf = 0, prev = -1, prevbuf = 0;
 
-  auto epilogue = [&](int tile, int b) {
-    const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  auto epilogue = [&](int gtile, int b) {
+    const int imi = image_of(a, gtile);
+    const ConvTImg<T>& im = a.img[imi];
+    const int tile = gtile - im.tile_start;
+    const int ty = tile / im.tiles_x, tx = tile % im.tiles_x;
     const int m = tid;
     const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
-    const bool valid = y < a.H && x < a.W;
+    const bool valid = y < im.H && x < im.W;
     const uint32_t tacc = tmem + (uint32_t)(b * N) + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c = 0; c < N; c += 16) {
@@ -512,7 +547,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
         h[q] = Half<T>::pack(v[2 * q] + __ldg(a.bias + co + 2 * q),
                              v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1));
       if (valid) {
-        T* dst = a.out + ((size_t)oy * (2 * a.W) + ox) * COUT + co;
+        T* dst = im.out + ((size_t)oy * (2 * im.W) + ox) * COUT + co;
         reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
         reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
       }
@@ -522,13 +557,16 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
     // stage the 128 input pixels of the patch: plane g holds channels 8g..8g+7
     {
-      const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+      const int imi = image_of(a, tile);
+      const ConvTImg<T>& im = a.img[imi];
+      const int lt = tile - im.tile_start;
+      const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
       uint8_t* dstb = abuf + buf * Cfg::ABYTES;
       for (int e = tid; e < 128 * Cfg::G; e += blockDim.x) {
         const int m = e / Cfg::G, g = e % Cfg::G;
         const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (y < a.H && x < a.W) v = ldg128(a.in + ((size_t)y * a.W + x) * CIN + g * 8);
+        if (y < im.H && x < im.W) v = ldg128(im.in + ((size_t)y * im.W + x) * CIN + g * 8);
         *reinterpret_cast<uint4*>(dstb + g * Cfg::APLANE + m * 16) = v;
       }
     }
@@ -740,9 +778,13 @@ size_t carve_tc(size_t P, size_t partial_floats, TcBuffers<T>* b, char* base) {
   return off;
 }
 
+int g_conv_ctas_per_sm = kConvCtasPerSM;
+
+// One grouped layer launch: `ins`, `skips`, `outs` hold each image's buffers,
+// `H`, `W` each image's convolution size.
 template <typename T, int CIN, int COUT, int MODE>
-cudaError_t run_conv(const NetTcWeights* w, int l, const T* inA, const T* inB, T* out, int H,
-                     int W, unsigned int* err, cudaStream_t s) {
+cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, const T* const* skips,
+                     T* const* outs, const int* H, const int* W, unsigned int* err, cudaStream_t s) {
   constexpr int NT = conv_nt(CIN, COUT);
   using Cfg = ConvCfg<CIN, COUT, NT>;
   static_assert(Cfg::SMEM <= 232448, "shared memory budget");
@@ -754,12 +796,21 @@ cudaError_t run_conv(const NetTcWeights* w, int l, const T* inA, const T* inB, T
     if (e != cudaSuccess) return e;
     init = true;
   }
-  TcConvArgs<T> a{inA, inB, w->conv_w[l], w->conv_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
-                  (H + kPatchH - 1) / kPatchH, err};
-  const int ntiles = a.tiles_x * a.tiles_y;
+  TcConvArgs<T> a{};
+  a.nimg = n;
+  int ntiles = 0;
+  for (int k = 0; k < n; ++k) {
+    const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
+    a.img[k] = ConvImg<T>{ins[k], skips ? skips[k] : nullptr, outs[k], H[k], W[k], tx, ntiles};
+    ntiles += tx * ty;
+  }
+  a.total_tiles = ntiles;
+  a.wpack = w->conv_w[l];
+  a.bias = w->conv_b[l];
+  a.err = err;
   // enough CTAs to cover every SM, each pipelining >= 4 tiles when there are
-  // that many: per-SM residency is capped at kConvCtasPerSM
-  const int per_sm = L.per_sm < kConvCtasPerSM ? L.per_sm : kConvCtasPerSM;
+  // that many; per-SM residency is capped by the tunable CTAs-per-SM
+  const int per_sm = L.per_sm < g_conv_ctas_per_sm ? L.per_sm : g_conv_ctas_per_sm;
   int grid = kNumSMs * per_sm / (COUT / NT);
   if (grid > (ntiles + 3) / 4) grid = (ntiles + 3) / 4;
   if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
@@ -770,8 +821,8 @@ cudaError_t run_conv(const NetTcWeights* w, int l, const T* inA, const T* inB, T
 }
 
 template <typename T, int CIN, int COUT>
-cudaError_t run_convT(const NetTcWeights* w, int l, const T* in, T* out, int H, int W,
-                      unsigned int* err, cudaStream_t s) {
+cudaError_t run_convT(const NetTcWeights* w, int l, int n, const T* const* ins, T* const* outs,
+                      const int* H, const int* W, unsigned int* err, cudaStream_t s) {
   using Cfg = ConvTCfg<CIN, COUT>;
   static Launch L;
   static bool init = false;
@@ -780,9 +831,18 @@ cudaError_t run_convT(const NetTcWeights* w, int l, const T* in, T* out, int H, 
     if (e != cudaSuccess) return e;
     init = true;
   }
-  TcConvTArgs<T> a{in, w->up_w[l], w->up_b[l], out, H, W, (W + kPatchW - 1) / kPatchW,
-                   (H + kPatchH - 1) / kPatchH, err};
-  const int ntiles = a.tiles_x * a.tiles_y;
+  TcConvTArgs<T> a{};
+  a.nimg = n;
+  int ntiles = 0;
+  for (int k = 0; k < n; ++k) {
+    const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
+    a.img[k] = ConvTImg<T>{ins[k], outs[k], H[k], W[k], tx, ntiles};
+    ntiles += tx * ty;
+  }
+  a.total_tiles = ntiles;
+  a.wpack = w->up_w[l];
+  a.bias = w->up_b[l];
+  a.err = err;
   int grid = kNumSMs * L.per_sm;
   if (grid > ntiles) grid = ntiles;
   convT_tc_kernel<T, CIN, COUT><<<grid, 128, L.smem, s>>>(a);
@@ -790,35 +850,49 @@ cudaError_t run_convT(const NetTcWeights* w, int l, const T* in, T* out, int H, 
 }
 
 template <typename T>
-cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
-                    void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
-  const int H = img.H, W = img.W;
-  const size_t P = (size_t)H * W;
-  TcBuffers<T> B;
-  const size_t pf = adapter_partial_floats(W, H);
-  if (carve_tc(P, pf, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
-  carve_tc(P, pf, &B, static_cast<char*>(workspace));
+cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs,
+                    void* const* ws, int n, unsigned int* err, cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  TcBuffers<T> B[kMaxGroup];
+  int Hs[4][kMaxGroup], Ws[4][kMaxGroup];
+  for (int k = 0; k < n; ++k) {
+    const size_t P = (size_t)imgs[k].H * imgs[k].W;
+    carve_tc(P, adapter_partial_floats(imgs[k].W, imgs[k].H), &B[k], static_cast<char*>(ws[k]));
+    for (int lv = 0; lv < 4; ++lv) {
+      Hs[lv][k] = imgs[k].H >> lv;
+      Ws[lv][k] = imgs[k].W >> lv;
+    }
+  }
+  // per-layer pointer lists
+  const T* in[kMaxGroup];
+  const T* sk[kMaxGroup];
+  T* out[kMaxGroup];
   cudaError_t e;
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
-  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
-  TRY(simt_first_conv_half<T>(wf, img, B.fa, s));
-  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 1, B.fa, nullptr, B.s1, H, W, err, s)));
-  TRY((run_conv<T, 16, 32, TC_POOL>(w, 2, B.s1, nullptr, B.l1a, H1, W1, err, s)));
-  TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 3, B.l1a, nullptr, B.s2, H1, W1, err, s)));
-  TRY((run_conv<T, 32, 64, TC_POOL>(w, 4, B.s2, nullptr, B.l2a, H2, W2, err, s)));
-  TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 5, B.l2a, nullptr, B.s3, H2, W2, err, s)));
-  TRY((run_conv<T, 64, 128, TC_POOL>(w, 6, B.s3, nullptr, B.l3a, H3, W3, err, s)));
-  TRY((run_conv<T, 128, 128, TC_PLAIN>(w, 7, B.l3a, nullptr, B.l3b, H3, W3, err, s)));
-  TRY((run_convT<T, 128, 64>(w, 0, B.l3b, B.l2a, H3, W3, err, s)));
-  TRY((run_conv<T, 128, 64, TC_CONCAT>(w, 8, B.l2a, B.s3, B.l2b, H2, W2, err, s)));
-  TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 9, B.l2b, nullptr, B.l2a, H2, W2, err, s)));
-  TRY((run_convT<T, 64, 32>(w, 1, B.l2a, B.l1a, H2, W2, err, s)));
-  TRY((run_conv<T, 64, 32, TC_CONCAT>(w, 10, B.l1a, B.s2, B.l1b, H1, W1, err, s)));
-  TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 11, B.l1b, nullptr, B.l1a, H1, W1, err, s)));
-  TRY((run_convT<T, 32, 16>(w, 2, B.l1a, B.fa, H1, W1, err, s)));
-  TRY((run_conv<T, 32, 16, TC_CONCAT>(w, 12, B.fa, B.s1, B.fb, H, W, err, s)));
-  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 13, B.fb, nullptr, B.fa, H, W, err, s)));
-  TRY(adapters_run<T>(net_f32_adapter_params(wf), B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+#define SET(IN, SKIP, OUT) for (int k = 0; k < n; ++k) { in[k] = B[k].IN; sk[k] = SKIP; out[k] = B[k].OUT; }
+  for (int k = 0; k < n; ++k) out[k] = B[k].fa;
+  TRY(simt_first_conv_group<T>(wf, imgs, out, n, s));
+  SET(fa, nullptr, s1);  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  SET(s1, nullptr, l1a); TRY((run_conv<T, 16, 32, TC_POOL>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(l1a, nullptr, s2); TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(s2, nullptr, l2a); TRY((run_conv<T, 32, 64, TC_POOL>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(l2a, nullptr, s3); TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(s3, nullptr, l3a); TRY((run_conv<T, 64, 128, TC_POOL>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  SET(l3a, nullptr, l3b); TRY((run_conv<T, 128, 128, TC_PLAIN>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64>(w, 0, n, in, out, Hs[3], Ws[3], err, s)));
+  SET(l2a, B[k].s3, l2b); TRY((run_conv<T, 128, 64, TC_CONCAT>(w, 8, n, in, sk, out, Hs[2], Ws[2], err, s)));
+  SET(l2b, nullptr, l2a); TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32>(w, 1, n, in, out, Hs[2], Ws[2], err, s)));
+  SET(l1a, B[k].s2, l1b); TRY((run_conv<T, 64, 32, TC_CONCAT>(w, 10, n, in, sk, out, Hs[1], Ws[1], err, s)));
+  SET(l1b, nullptr, l1a); TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16>(w, 2, n, in, out, Hs[1], Ws[1], err, s)));
+  SET(fa, B[k].s1, fb);  TRY((run_conv<T, 32, 16, TC_CONCAT>(w, 12, n, in, sk, out, Hs[0], Ws[0], err, s)));
+  SET(fb, nullptr, fa);  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  AdapterImg<T> ai[kMaxGroup];
+  for (int k = 0; k < n; ++k)
+    ai[k] = AdapterImg<T>{B[k].fa, B[k].x1, B[k].partial, B[k].att, imgs[k].out, imgs[k].H, imgs[k].W};
+  TRY(adapters_run_group<T>(net_f32_adapter_params(wf), ai, n, s));
+#undef SET
 #undef TRY
   return cudaSuccess;
 }
@@ -831,8 +905,19 @@ size_t net_tc_workspace_bytes(int max_w, int max_h) {
 
 cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
                            void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
-  if (w->elem == 1) return forward<__nv_bfloat16>(w, wf, img, workspace, ws_bytes, err, s);
-  return forward<__half>(w, wf, img, workspace, ws_bytes, err, s);
+  if (net_tc_workspace_bytes(img.W, img.H) > ws_bytes) return cudaErrorInvalidValue;
+  void* ws[1] = {workspace};
+  return net_tc_forward_group(w, wf, &img, ws, 1, err, s);
 }
+
+cudaError_t net_tc_forward_group(const NetTcWeights* w, const NetF32Weights* wf,
+                                 const NetImage* imgs, void* const* ws, int n, unsigned int* err,
+                                 cudaStream_t s) {
+  if (w->elem == 1) return forward<__nv_bfloat16>(w, wf, imgs, ws, n, err, s);
+  return forward<__half>(w, wf, imgs, ws, n, err, s);
+}
+
+void net_tc_set_ctas_per_sm(int v) { g_conv_ctas_per_sm = v < 1 ? 1 : (v > 4 ? 4 : v); }
+int net_tc_ctas_per_sm() { return g_conv_ctas_per_sm; }
 
 }  // namespace nsl

@@ -11,6 +11,7 @@
 namespace nsl {
 
 constexpr int kNumSMs = 152;
+constexpr int kMaxGroup = 64;   // images per grouped network launch / plumes per batch launch
 
 // Error recording (thread-local message, see nsl_last_error).
 void set_error(const char* fmt, ...);
@@ -97,8 +98,29 @@ cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
 int march_max_segments(int nx, int ny, int nz, float h, int seg_len);
 cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
                                    cudaStream_t s);
+// batched forms (device tables; see march.cu)
+struct StageItem {
+  const void* density;
+  const uint8_t* mask;
+  float* out;            // padded quad staging of this plume
+  int nx, ny, nz, dtype;
+  float scale;
+};
+int stage_batch_blocks(const StageItem& it);
+cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_starts_dev, int n,
+                               int total_blocks, cudaStream_t s);
+cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int* tile_starts_dev,
+                                         const int* item_starts_dev, const int* tile_counts_dev,
+                                         int nplumes, int total_tiles, int total_items,
+                                         int seg_blocks, int* counter, cudaStream_t s);
+int march_segment_blocks_max();
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
                                int* tile_counter, cudaStream_t s);
+
+// host helpers shared by the single-plume and batched entry points (api.cu)
+nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, float step,
+                            const nsl_march_opts* opts, const char* fn, MarchPlume* p);
+nsl_status check_camera_basic(const nsl_camera* cam, const char* fn);
 
 // ---------------------------------------------------------------------------
 // six-way shading
@@ -110,6 +132,10 @@ struct ShadeArgs {
   float M[3][6];     // per colour channel: sum_l I_l,c * weight of plane q
 };
 cudaError_t launch_shade(const ShadeArgs& a, cudaStream_t s);
+nsl_status shade_matrix(const nsl_camera& cam, const nsl_light* lights, int n_lights,
+                        float M[3][6], const char* fn);
+cudaError_t launch_shade_batch(const ShadeArgs* items_dev, const int* block_starts_dev, int n,
+                               int total_blocks, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // network
@@ -193,6 +219,22 @@ size_t adapter_partial_floats(int max_w, int max_h);
 template <typename TA>
 cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float* partial,
                          float* att, float* out, int H, int W, cudaStream_t s);
+// the same for a group of images (one launch per pass)
+template <typename TA>
+struct AdapterImg {
+  const TA* F;
+  TA* x1;
+  float* partial;   // per-tile channel sums of this image
+  float* att;       // 64 attention values of this image
+  float* out;       // [8][H][W]
+  int H, W;
+};
+template <typename TA>
+cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, T* const* outs,
+                                  int n, cudaStream_t s);
 const AdapterParamSet& net_f32_adapter_params(const NetF32Weights* w);
 
 // tensor-core (tcgen05) network, 16-bit operands (elem 0 = FP16, 1 = BF16),
@@ -205,5 +247,13 @@ size_t net_tc_workspace_bytes(int max_w, int max_h);
 cudaError_t net_tc_forward(const NetTcWeights* wt, const NetF32Weights* wf, const NetImage& img,
                            void* workspace, size_t ws_bytes, unsigned int* err_flag,
                            cudaStream_t s);
+// grouped forward: n <= kMaxGroup images, image k uses workspace ws[k] of at
+// least net_tc_workspace_bytes(W_k, H_k) bytes; every layer is one launch.
+cudaError_t net_tc_forward_group(const NetTcWeights* wt, const NetF32Weights* wf,
+                                 const NetImage* imgs, void* const* ws, int n,
+                                 unsigned int* err_flag, cudaStream_t s);
+// runtime tunable: CTAs per SM of the tensor-core convolutions (1..4)
+void net_tc_set_ctas_per_sm(int v);
+int net_tc_ctas_per_sm();
 
 }  // namespace nsl

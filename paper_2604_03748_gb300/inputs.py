@@ -357,3 +357,79 @@ def small_case(n: int = 24, width: int = 32, height: int = 24, seed: int = 11, k
     else:
         cam = orbit_ortho_camera(n, seed, width, height)
     return PlumeFrame(vol, mask, cam, random_light(seed), step, meta={"name": f"small{n}"})
+
+
+def blob_fbm_volume_fast(n: int, seed: int, device=None):
+    """blob_fbm_volume evaluated with torch (GPU when given): the same recipe and
+    random draws, computed in float32 tensors; used for large batches."""
+    import torch
+    dev = torch.device(device or "cpu")
+    rng = np.random.default_rng(1_000_003 * seed + 17)
+    blobs = []
+    for _ in range(8):
+        centre = rng.uniform(0.25, 0.75, size=3) * n
+        widths = rng.uniform(0.05, 0.2, size=3) * n
+        rot = _random_rotation(rng)
+        amp = rng.uniform(0.5, 1.5)
+        blobs.append((centre, widths, rot, amp))
+    c = torch.arange(n, dtype=torch.float32, device=dev) + 0.5
+    zz, yy, xx = torch.meshgrid(c, c, c, indexing="ij")
+    pts = torch.stack([xx, yy, zz], dim=-1)
+    dens = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+    for centre, widths, rot, amp in blobs:
+        local = (pts - torch.tensor(centre, dtype=torch.float32, device=dev)) @ torch.tensor(rot, dtype=torch.float32, device=dev)
+        dens += float(amp) * torch.exp(-0.5 * ((local / torch.tensor(widths, dtype=torch.float32, device=dev)) ** 2).sum(-1))
+    # fBm with the same lattice draws as fbm()
+    rng2 = np.random.default_rng(seed)
+    total = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+    amp, norm, freq = 1.0, 0.0, 1.0 / (n / 4.0)
+    for _ in range(4):
+        grads = torch.tensor(_lattice_gradients(rng2, 64), device=dev)
+        off = rng2.uniform(0, 64, size=3).astype(np.float32)
+        px, py, pz = xx * freq + float(off[0]), yy * freq + float(off[1]), zz * freq + float(off[2])
+        x0, y0, z0 = torch.floor(px), torch.floor(py), torch.floor(pz)
+        fx, fy, fz = px - x0, py - y0, pz - z0
+        ix, iy, iz = x0.long() % 64, y0.long() % 64, z0.long() % 64
+        fade = lambda t: t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+        ux, uy, uz = fade(fx), fade(fy), fade(fz)
+        acc = torch.zeros_like(total)
+        for dz in (0, 1):
+            wz = uz if dz else 1.0 - uz
+            for dy in (0, 1):
+                wy = uy if dy else 1.0 - uy
+                for dx in (0, 1):
+                    wx = ux if dx else 1.0 - ux
+                    g = grads[(iz + dz) % 64, (iy + dy) % 64, (ix + dx) % 64]
+                    acc += wx * wy * wz * (g[..., 0] * (fx - dx) + g[..., 1] * (fy - dy) + g[..., 2] * (fz - dz))
+        total += amp * acc
+        norm += amp
+        amp *= 0.5
+        freq *= 2.0
+    noise = torch.clamp(total / norm * 1.6, -1.0, 1.0)
+    return torch.clamp(dens * (0.5 + 0.5 * noise), 0.0, 2.0)
+
+
+@dataclass
+class BatchPlume:
+    n: int
+    width: int
+    height: int
+    seed: int
+    camera: Camera
+    light: Light
+    step: float
+
+
+def batch_plumes_spec(count: int = 64, seed: int = 4, sizes=(32, 48, 64, 96, 128, 192),
+                      billboards=(64, 128, 256, 512), step: float = 2.0) -> list:
+    """The batched workload: `count` plumes with grid sizes drawn uniformly from
+    `sizes` (cubic) and square billboards from `billboards`, each with its own
+    seeded perspective camera and light."""
+    rng = np.random.default_rng(11_000_003 * seed + 1)
+    out = []
+    for k in range(count):
+        n = int(rng.choice(sizes))
+        b = int(rng.choice(billboards))
+        s = int(rng.integers(0, 1 << 30))
+        out.append(BatchPlume(n, b, b, s, perspective_camera(n, s, b, b), random_light(s), step))
+    return out

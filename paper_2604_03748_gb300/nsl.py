@@ -22,7 +22,9 @@ NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
 EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_grid",
            "nsl_guiding_map", "nsl_guiding_map_noalloc", "nsl_guide_sample_count",
            "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host", "nsl_last_error",
-           "nsl_status_str"]
+           "nsl_status_str", "nsl_batch_create", "nsl_batch_destroy", "nsl_batch_render",
+           "nsl_batch_capture_graph", "nsl_batch_update_graph", "nsl_batch_launch_graph",
+           "nsl_batch_set_tuning", "nsl_batch_get_tuning", "nsl_batch_autotune"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -44,6 +46,12 @@ class nsl_march_opts(C.Structure):
     _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
                 ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
                 ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int)]
+
+
+class nsl_plume(C.Structure):
+    _fields_ = [("density_dev", C.c_void_p), ("mask_dev", C.c_void_p), ("grid", nsl_grid_desc),
+                ("camera", nsl_camera), ("step_voxels", C.c_float), ("light", nsl_light),
+                ("guide_dev", C.c_void_p), ("lightmaps_dev", C.c_void_p), ("rgba_dev", C.c_void_p)]
 
 
 class NslError(RuntimeError):
@@ -80,6 +88,21 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
     lib.nsl_render_frame_host.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light),
                                           i, f, C.POINTER(nsl_march_opts), i, vp, vp, vp, vp]
+    lib.nsl_batch_create.argtypes = [vp, C.c_size_t, i, C.POINTER(vp)]
+    lib.nsl_batch_destroy.argtypes = [vp]
+    lib.nsl_batch_destroy.restype = None
+    lib.nsl_batch_render.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts), i, vp]
+    lib.nsl_batch_capture_graph.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts), i, vp]
+    lib.nsl_batch_update_graph.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts)]
+    lib.nsl_batch_launch_graph.argtypes = [vp, vp]
+    lib.nsl_batch_set_tuning.argtypes = [vp, i, i, i]
+    lib.nsl_batch_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.nsl_batch_autotune.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts), i,
+                                       C.c_char_p, vp, C.POINTER(C.c_float)]
+    for name in ("nsl_batch_create", "nsl_batch_render", "nsl_batch_capture_graph",
+                 "nsl_batch_update_graph", "nsl_batch_launch_graph", "nsl_batch_set_tuning",
+                 "nsl_batch_get_tuning", "nsl_batch_autotune"):
+        getattr(lib, name).restype = C.c_int
     lib.nsl_last_error.argtypes = []
     lib.nsl_last_error.restype = C.c_char_p
     lib.nsl_status_str.argtypes = [i]
@@ -266,3 +289,85 @@ class Context:
 
     def shade(self, lightmaps, width, height, cam, light_list, rgba, stream=None):
         nsl_shade(self.ctx, lightmaps, width, height, cam, light_list, rgba, stream=stream)
+
+
+# --------------------------------------------------------------------------
+# batched frames
+# --------------------------------------------------------------------------
+
+def plume_array(items):
+    """items: sequence of dicts with density, mask, grid_dtype, sigma_scale,
+    camera, step, light, guide, lightmaps, rgba (torch tensors / descriptions)."""
+    arr = (nsl_plume * len(items))()
+    for k, it in enumerate(items):
+        p = arr[k]
+        d = it["density"]
+        nz, ny, nx = d.shape
+        p.density_dev = _dptr(d, GRID_TYPES)
+        p.mask_dev = _dptr(it.get("mask"), U8)
+        p.grid = nsl_grid_desc(nx, ny, nz, NSL_F16 if str(d.dtype).endswith("float16") else NSL_F32,
+                               float(it.get("sigma_scale", 1.0)))
+        p.camera = camera(it["camera"])
+        p.step_voxels = float(it["step"])
+        p.light = lights([it["light"]])[0]
+        p.guide_dev = _dptr(it["guide"], F32)
+        p.lightmaps_dev = _dptr(it["lightmaps"], F32)
+        p.rgba_dev = _dptr(it.get("rgba"), F32)
+    return arr
+
+
+class Batch:
+    """Owns an nsl_batch; the methods forward to the C ABI."""
+
+    def __init__(self, blob: bytes, max_plumes: int = 64):
+        lib = load()
+        out = C.c_void_p()
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib.nsl_batch_create(buf, len(blob), int(max_plumes), C.byref(out)), "nsl_batch_create")
+        self.b = out
+
+    def close(self):
+        if self.b:
+            load().nsl_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, plumes, precision, opts=None, stream=None):
+        arr = plume_array(plumes)
+        check(load().nsl_batch_render(self.b, arr, len(plumes), C.byref(opts) if opts else None,
+                                      int(precision), _stream(stream)), "nsl_batch_render")
+
+    def capture_graph(self, plumes, precision, stream, opts=None):
+        arr = plume_array(plumes)
+        check(load().nsl_batch_capture_graph(self.b, arr, len(plumes), C.byref(opts) if opts else None,
+                                             int(precision), _stream(stream)), "nsl_batch_capture_graph")
+
+    def update_graph(self, plumes, opts=None):
+        arr = plume_array(plumes)
+        check(load().nsl_batch_update_graph(self.b, arr, len(plumes), C.byref(opts) if opts else None),
+              "nsl_batch_update_graph")
+
+    def launch_graph(self, stream):
+        check(load().nsl_batch_launch_graph(self.b, _stream(stream)), "nsl_batch_launch_graph")
+
+    def set_tuning(self, seg_len, march_blocks_per_sm, conv_ctas_per_sm):
+        check(load().nsl_batch_set_tuning(self.b, int(seg_len), int(march_blocks_per_sm),
+                                          int(conv_ctas_per_sm)), "nsl_batch_set_tuning")
+
+    def get_tuning(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        check(load().nsl_batch_get_tuning(self.b, C.byref(a), C.byref(b), C.byref(c)), "nsl_batch_get_tuning")
+        return a.value, b.value, c.value
+
+    def autotune(self, plumes, precision, cache_path=None, opts=None, stream=None):
+        arr = plume_array(plumes)
+        ms = C.c_float(0)
+        check(load().nsl_batch_autotune(self.b, arr, len(plumes), C.byref(opts) if opts else None,
+                                        int(precision), cache_path.encode() if cache_path else None,
+                                        _stream(stream), C.byref(ms)), "nsl_batch_autotune")
+        return ms.value
