@@ -107,7 +107,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_frame(pf, rows, blob_params, c0=16):
+def range_errs(got, ref):
+    """max |got - ref| / max |ref| per plane (the oracle's range)."""
+    return [float(np.abs(got[c].astype(np.float64) - ref[c]).max() / max(np.abs(ref[c]).max(), 1e-30))
+            for c in range(ref.shape[0])]
+
+
+def cpu_oracle_frame(pf, rows, blob_params, c0=16, keep=False):
     """The FP64 oracle on a band of `rows` image rows: guide, network on the band, shade."""
     import oracle
     r0 = (pf.camera.height - rows) // 2
@@ -120,7 +126,10 @@ def cpu_oracle_frame(pf, rows, blob_params, c0=16):
     import dataclasses
     cam_band = dataclasses.replace(cam, height=rows)
     oracle.shade(lm, cam_band, [pf.light])
-    return time.perf_counter() - t0, rows * pf.camera.width
+    t = time.perf_counter() - t0
+    if keep:
+        return t, rows * pf.camera.width, (band, lm)
+    return t, rows * pf.camera.width
 
 
 def run_reference(args):
@@ -173,6 +182,9 @@ def main():
     ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--forms", default="batched",
+                    help="comma list of systems forms measured after the primary line's "
+                         "workload ('batched', or 'none')")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -301,26 +313,168 @@ def main():
         "e2e": {"value": e2e_val, "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(pf.density.nbytes + pf.mask.nbytes),
                 "d2h_bytes_per_step": int((3 + 8 + 4) * H * W * 4)},
-        "gpu_launches": args.steps * LAUNCHES_PER_STEP,
+        "gpu_launches": args.steps * launches_per_step(args.precision),
         "clocks": clk,
         "host_wall_s": t_host,
     }
+    ctx.close()
+    forms = [f for f in args.forms.split(",") if f and f != "none"]
+    if "batched" in forms:
+        line["batched"] = bench_batched(nsl, I, dev, stream, flush, args, rank == 0 and ws == 1
+                                        and not args.no_cpu_baseline)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
-        t, px = cpu_oracle_frame(pf, 512, flat)
+        t, px, ref = cpu_oracle_frame(pf, 512, flat, keep=True)
         line["cpu_baseline"] = {"value": px / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(),
                                 "kind": "oracle",
                                 "sample": "one whole 512x512 frame: FP64 guide march, FP64 network, shade"}
+        # error of this run's last frame against that oracle frame, per channel,
+        # relative to the oracle's range (guide: march; lightmaps: end to end,
+        # i.e. the network's precision on top of the march)
+        line["err_vs_oracle"] = {
+            "guide": range_errs(guide.cpu().numpy(), ref[0]),
+            "lightmaps": range_errs(lm.cpu().numpy(), ref[1]),
+        }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-# stage 1 + march 1 + network (14 conv + 3 transposed conv + 3 adapter) + shade 1
-LAUNCHES_PER_STEP = 1 + 1 + 20 + 1
+def launches_per_step(precision):
+    """Kernels of one single-plume step: staging 1, guide march 3 (view pass,
+    segment pass, finish pass), network, shading 1.  Tensor-core network: SIMT
+    first convolution 1 + 13 tensor-core convolutions + 3 transposed
+    convolutions + adapters 3 = 20; FP32 network: 14 convolutions + 3
+    transposed convolutions + adapters 3 = 20."""
+    return 1 + 3 + 20 + 1
+
+
+def bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
+    """Batched form: 64 plumes (seed 4) with grids drawn from {32..192}^3 FP32 and
+    billboards from {64..512}^2, each with its own perspective camera and light,
+    rendered by one captured CUDA graph per step (staging, guide march, grouped
+    BF16 network, shading over all plumes), tuning from the autotuner.  The same
+    64 plumes through the plain single-plume path with the FP32 network give
+    the comparison figure."""
+    import torch
+    stream = torch.cuda.Stream()          # graph capture needs a non-default stream
+    with torch.cuda.stream(stream):
+        return _bench_batched(nsl, I, dev, stream, flush, args, with_oracle)
+
+
+def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
+    import torch
+    spec = I.batch_plumes_spec(64, seed=4)
+    blob = I.pack_blob(I.make_params(16, 0), 16)
+    items = []
+    for p in spec:
+        H, W = p.camera.height, p.camera.width
+        items.append(dict(
+            density=I.blob_fbm_volume_fast(p.n, p.seed, device=dev).contiguous(), mask=None,
+            sigma_scale=1.0, camera=p.camera, step=p.step, light=p.light,
+            guide=torch.empty((3, H, W), dtype=torch.float32, device=dev),
+            lightmaps=torch.empty((8, H, W), dtype=torch.float32, device=dev),
+            rgba=torch.empty((4, H, W), dtype=torch.float32, device=dev)))
+    pixels = sum(p.camera.width * p.camera.height for p in spec)
+    out = {"workload": "64 plumes, grids U{32,48,64,96,128,192}^3 f32, billboards U{64,128,256,512}^2, "
+                       "perspective fov 40, step 2 voxels, seed 4",
+           "pixels_per_step": pixels, "voxels": int(sum(p.n ** 3 for p in spec))}
+    b = nsl.Batch(blob, 64)
+    for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16)):
+        tune_ms = b.autotune(items, prec, stream=stream)
+        tuning = b.get_tuning()
+        b.capture_graph(items, prec, stream)
+        for _ in range(max(3, args.warmup)):
+            flush.zero_()
+            b.launch_graph(stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            b.launch_graph(stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(c) for a, c in ev]))
+        out[name] = {"value": pixels / (ms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
+                     "tuning": {"seg_len": tuning[0], "march_blocks_per_sm": tuning[1],
+                                "conv_ctas_per_sm": tuning[2], "autotune_ms": tune_ms},
+                     "launches_per_step": 1 + 3 + 20 + 1}
+    b.close()
+
+    # the plain single-plume path with the FP32 network on the same plumes
+    ctxs = {}
+    for p in spec:
+        if p.n not in ctxs:
+            ctxs[p.n] = nsl.Context((p.n, p.n, p.n), nsl.NSL_F32, blob, 512, 512)
+    opts = nsl.march_opts()
+
+    def plain_pass():
+        for p, it in zip(spec, items):
+            c = ctxs[p.n].ctx
+            nsl.nsl_stage_grid(c, it["density"], None, stream=stream)
+            nsl.nsl_guiding_map(c, None, None, p.camera, p.step, it["guide"], opts=opts, stream=stream)
+            nsl.nsl_predict_lightmaps(c, it["guide"], p.camera.width, p.camera.height, nsl.NSL_PREC_F32,
+                                      it["lightmaps"], stream=stream)
+            nsl.nsl_shade(c, it["lightmaps"], p.camera.width, p.camera.height, p.camera, [p.light],
+                          it["rgba"], stream=stream)
+
+    for _ in range(2):
+        flush.zero_()
+        plain_pass()
+    torch.cuda.synchronize()
+    reps = max(1, min(5, args.steps))
+    tms = []
+    for _ in range(reps):
+        flush.zero_()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plain_pass()
+        c.record(stream)
+        torch.cuda.synchronize()
+        tms.append(a.elapsed_time(c))
+    ms = float(np.mean(tms))
+    out["plain_f32_single_plume"] = {"value": pixels / (ms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
+                                     "launches_per_step": 64 * (1 + 3 + 20 + 1)}
+    out["speedup_bf16_vs_plain_f32"] = out["bf16"]["value"] / out["plain_f32_single_plume"]["value"]
+    for c in ctxs.values():
+        c.close()
+
+    if with_oracle:
+        # FP64 oracle on the two smallest plumes of the batch: timed (CPU
+        # baseline of this form) and compared with the batch's BF16 and F16 output
+        import oracle
+        flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+        order = sorted(range(len(spec)), key=lambda k: (spec[k].n ** 3 * spec[k].camera.width ** 2, k))[:2]
+        b = nsl.Batch(blob, 64)
+        res = {}
+        for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16)):
+            b.render(items, prec, stream=stream)
+            torch.cuda.synchronize()
+            res[name] = [(items[k]["guide"].cpu().numpy(), items[k]["lightmaps"].cpu().numpy()) for k in order]
+        b.close()
+        t0 = time.perf_counter()
+        px = 0
+        errs = {"plumes": [f"n={spec[k].n} {spec[k].camera.width}x{spec[k].camera.height}" for k in order]}
+        for j, k in enumerate(order):
+            p = spec[k]
+            dens = items[k]["density"].cpu().numpy()
+            g, _, _ = oracle.guide(dens, None, p.camera, p.step)
+            lm = oracle.net_forward(g, flat, 16, 1.0 / math.sqrt(3.0 * p.n * p.n))
+            px += p.camera.width * p.camera.height
+            for name in ("bf16", "f16"):
+                e = errs.setdefault(name, {"guide": [], "lightmaps": []})
+                e["guide"].append(max(range_errs(res[name][j][0], g)))
+                e["lightmaps"].append(max(range_errs(res[name][j][1], lm)))
+        t = time.perf_counter() - t0
+        out["err_vs_oracle"] = errs
+        out["cpu_baseline"] = {"value": px / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": "the two smallest plumes of the batch, whole "
+                                                           "frames: FP64 guide march and network"}
+    return out
 
 if __name__ == "__main__":
     sys.exit(main())
