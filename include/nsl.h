@@ -264,6 +264,94 @@ NSL_API nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int
                                       const nsl_march_opts* opts, int precision,
                                       const char* cache_path, void* stream, float* best_ms);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a frame-request loop over plumes kept resident on the device.
+ *
+ * Plumes are registered with their density on the host.  A plume is admitted
+ * (its grid uploaded and staged, its guide / lightmap / RGBA state allocated)
+ * when a request for it is scheduled and the device bytes it needs fit in the
+ * HBM budget; otherwise the least recently used idle plumes are evicted first.
+ * One scheduler thread batches queued requests of different grid and billboard
+ * sizes as they arrive: whenever one of `streams` batch slots is free it takes
+ * the oldest queued requests (at most one per plume, up to max_batch, within
+ * the slot's scratch) and launches them as one batched render on that slot's
+ * stream, so batches overlap on the device and later arrivals join the next
+ * free slot (continuous batching).  Requests for one plume run in arrival order.
+ * Each frame is the guide march, the network and shading of nsl_batch_render
+ * with the server's march options; results are bitwise the same whichever
+ * batch a request lands in.  The paper has no serving layer: this is a systems
+ * form around its per-frame method.
+ * ------------------------------------------------------------------------- */
+typedef struct nsl_server nsl_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;         /* device bytes for resident plumes + slot scratch */
+  size_t scratch_bytes_per_stream; /* march + network scratch of one batch slot (0: budget/8) */
+  int streams;                     /* batch slots in flight at once, 1..4 */
+  int max_batch;                   /* requests per batch, 1..64 */
+  int precision;                   /* NSL_PREC_F16 or NSL_PREC_BF16 */
+  nsl_march_opts march;            /* march options of every frame */
+} nsl_server_opts;
+
+typedef struct {
+  uint64_t submitted, completed, failed, queued, running;
+  uint64_t batches, admissions, evictions;
+  double pixels_completed;         /* billboard pixels of completed requests */
+  int resident_plumes;
+  size_t resident_bytes;           /* staged grids + state of resident plumes */
+  size_t used_bytes;               /* resident_bytes + slot scratch and upload buffers */
+  size_t budget_bytes;
+  double p50_ms, p99_ms, max_ms;   /* submit -> lightmaps ready, completed requests */
+  double mean_batch;               /* requests per launched batch */
+  double busy_s;                   /* first submit -> last completion */
+} nsl_server_stats;
+
+/* Defaults: 40 GiB budget, 2 streams, batches of up to 64, FP16 network. */
+NSL_API void nsl_default_server_opts(nsl_server_opts* o);
+NSL_API nsl_status nsl_server_create(const void* weights_blob, size_t blob_bytes,
+                                     const nsl_server_opts* opts, nsl_server** out);
+/* Waits for work in flight, then frees everything (host registrations too). */
+NSL_API void nsl_server_destroy(nsl_server* s);
+
+/* Register a plume.  density_host (grid->dtype elements, [nz][ny][nx]) and
+ * mask_host (nullable) must stay valid until the plume is removed: they are
+ * re-read whenever the plume is admitted again after an eviction; the server
+ * page-locks them for fast uploads.  Requests may use billboards up to
+ * max_width x max_height.  NSL_ERR_BUDGET if the plume alone cannot fit. */
+NSL_API nsl_status nsl_server_add_plume(nsl_server* s, const nsl_grid_desc* grid,
+                                        const void* density_host, const uint8_t* mask_host,
+                                        float step_voxels, int max_width, int max_height,
+                                        int* plume_id);
+/* NSL_ERR_INVALID_ARG while the plume has queued or running requests. */
+NSL_API nsl_status nsl_server_remove_plume(nsl_server* s, int plume_id);
+
+/* Queue one frame of a plume (thread-safe).  lightmaps_dev ([8][H][W]) and
+ * rgba_dev ([4][H][W]) are optional caller buffers for this request's output;
+ * NULL writes the plume's resident state instead (see nsl_server_plume_state).
+ * The server's streams do not wait on the caller's: output buffers must be
+ * ready (no pending work on them) at submit and stay allocated until the
+ * request completes.  The latency clock starts here. */
+NSL_API nsl_status nsl_server_submit(nsl_server* s, int plume_id, const nsl_camera* cam,
+                                     const nsl_light* light, float* lightmaps_dev, float* rgba_dev,
+                                     uint64_t* request_id);
+/* Block until the request completes (NSL_OK, latency in ms), fails (its error),
+ * or timeout_ms passes (NSL_ERR_TIMEOUT; the request carries on). */
+NSL_API nsl_status nsl_server_wait(nsl_server* s, uint64_t request_id, double timeout_ms,
+                                   double* latency_ms);
+/* Block until nothing is queued or running (NSL_ERR_TIMEOUT after timeout_ms). */
+NSL_API nsl_status nsl_server_drain(nsl_server* s, double timeout_ms);
+/* Device pointers of a plume's resident guide / lightmaps / RGBA state: the
+ * last request's [3|8|4][H][W] planes (its width and height) at the start of
+ * buffers sized for the plume's largest billboard; NULL and *resident = 0
+ * when evicted.  Valid until the next request
+ * for the plume is scheduled or the plume is evicted. */
+NSL_API nsl_status nsl_server_plume_state(nsl_server* s, int plume_id, const float** guide_dev,
+                                          const float** lightmaps_dev, const float** rgba_dev,
+                                          int* resident);
+NSL_API nsl_status nsl_server_get_stats(nsl_server* s, nsl_server_stats* out);
+/* Clears the latency record and counters (not the resident set). */
+NSL_API nsl_status nsl_server_reset_stats(nsl_server* s);
+
 /* Description of the last error raised on the calling thread ("" if none). */
 NSL_API const char* nsl_last_error(void);
 NSL_API const char* nsl_status_str(nsl_status s);

@@ -102,14 +102,14 @@ nsl_status grow(nsl_batch* b, void** p, size_t* have, size_t need, cudaStream_t 
   return NSL_OK;
 }
 
-nsl_status validate_plume(const nsl_plume& pl, int k) {
+nsl_status validate_plume(const nsl_plume& pl, int k, bool prestaged) {
   char fn[64];
   std::snprintf(fn, sizeof fn, "nsl_batch: plume %d", k);
   const nsl_grid_desc& g = pl.grid;
   if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > 4096 || g.ny > 4096 || g.nz > 4096 ||
       (g.dtype != NSL_F32 && g.dtype != NSL_F16) || !(g.sigma_scale >= 0.f))
     return fail(NSL_ERR_INVALID_ARG, "%s: bad grid", fn);
-  if (!pl.density_dev || !pl.guide_dev || !pl.lightmaps_dev)
+  if ((!pl.density_dev && !prestaged) || !pl.guide_dev || !pl.lightmaps_dev)
     return fail(NSL_ERR_INVALID_ARG, "%s: NULL buffer", fn);
   const uintptr_t bits = reinterpret_cast<uintptr_t>(pl.density_dev) |
                          reinterpret_cast<uintptr_t>(pl.mask_dev) |
@@ -120,10 +120,27 @@ nsl_status validate_plume(const nsl_plume& pl, int k) {
   return check_camera_basic(&pl.camera, fn);
 }
 
+}  // namespace
+
+namespace nsl {
+// Device scratch one plume takes in a batch: segment starts of the march and
+// the network workspace (each rounded up to 256 bytes).
+void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes) {
+  const size_t P = (size_t)p.camera.width * p.camera.height;
+  const int maxseg = march_max_segments(p.grid.nx, p.grid.ny, p.grid.nz, p.step_voxels, seg_len);
+  *seg_bytes = align256(P * sizeof(int)) + align256(3 * (size_t)maxseg * P * sizeof(float));
+  *net_bytes = align256(net_tc_workspace_bytes(p.camera.width, p.camera.height));
+}
+}  // namespace nsl
+
+namespace {
+
 // Fill host table slot `T` for this batch and size every device region.
+// Where prestaged[k] is set, plume k's grid is already staged there (padded
+// quad layout) and is not staged again.
 nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const nsl_march_opts* opts,
                    int precision, cudaStream_t s, std::vector<NetImage>* imgs,
-                   std::vector<void*>* ws, Totals* tot) {
+                   std::vector<void*>* ws, Totals* tot, const float* const* prestaged) {
   if (n < 1 || n > b->max_plumes || n > kMaxGroup)
     return fail(NSL_ERR_INVALID_ARG, "nsl_batch: n must be in [1, %d]", b->max_plumes);
   if (precision != NSL_PREC_BF16 && precision != NSL_PREC_F16)
@@ -132,17 +149,18 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
   std::vector<size_t> off_staged(n), off_seg(n), off_net(n);
   std::vector<int> maxseg(n);
   for (int k = 0; k < n; ++k) {
-    nsl_status st = validate_plume(pl[k], k);
+    nsl_status st = validate_plume(pl[k], k, prestaged && prestaged[k]);
     if (st != NSL_OK) return st;
     const nsl_grid_desc& g = pl[k].grid;
-    const size_t P = (size_t)pl[k].camera.width * pl[k].camera.height;
     off_staged[k] = staged;
-    staged += align256(staged_floats(g.nx, g.ny, g.nz) * sizeof(float));
+    if (!(prestaged && prestaged[k])) staged += align256(staged_floats(g.nx, g.ny, g.nz) * sizeof(float));
     maxseg[k] = march_max_segments(g.nx, g.ny, g.nz, pl[k].step_voxels, b->seg_len);
+    size_t sb, nb;
+    batch_plume_scratch(pl[k], b->seg_len, &sb, &nb);
     off_seg[k] = seg;
-    seg += align256(P * sizeof(int)) + align256(3 * (size_t)maxseg[k] * P * sizeof(float));
+    seg += sb;
     off_net[k] = net;
-    net += align256(net_tc_workspace_bytes(pl[k].camera.width, pl[k].camera.height));
+    net += nb;
   }
   nsl_status st = grow(b, &b->staged, &b->staged_bytes, staged, s, "staged grids");
   if (st != NSL_OK) return st;
@@ -158,7 +176,9 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     st = fill_march_plume(p.grid, p.camera, p.step_voxels, opts, "nsl_batch", &m);
     if (st != NSL_OK) return st;
     const size_t P = (size_t)p.camera.width * p.camera.height;
-    float* staged_k = reinterpret_cast<float*>(static_cast<char*>(b->staged) + off_staged[k]);
+    const bool pre = prestaged && prestaged[k];
+    float* staged_k = pre ? const_cast<float*>(prestaged[k])
+                          : reinterpret_cast<float*>(static_cast<char*>(b->staged) + off_staged[k]);
     m.vol = staged_k;
     m.guide = p.guide_dev;
     m.seg_len = b->seg_len;
@@ -177,7 +197,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     si = StageItem{p.density_dev, p.mask_dev, staged_k, p.grid.nx, p.grid.ny, p.grid.nz,
                    p.grid.dtype, p.grid.sigma_scale};
     T.stage_starts[k] = sblocks;
-    sblocks += stage_batch_blocks(si);
+    if (!pre) sblocks += stage_batch_blocks(si);
     if (p.rgba_dev) {
       ShadeArgs& a = T.shade[nshade];
       a = ShadeArgs{};
@@ -206,7 +226,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
 }
 
 nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts* opts,
-                  int precision, cudaStream_t s) {
+                  int precision, cudaStream_t s, const float* const* prestaged = nullptr) {
   if (*reinterpret_cast<volatile unsigned int*>(b->err_host) != 0) {
     const unsigned code = *b->err_host;
     *b->err_host = 0;
@@ -224,7 +244,7 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
   std::vector<NetImage> imgs;
   std::vector<void*> ws;
   Totals tot{};
-  nsl_status st = prepare(b, T, pl, n, opts, precision, s, &imgs, &ws, &tot);
+  nsl_status st = prepare(b, T, pl, n, opts, precision, s, &imgs, &ws, &tot, prestaged);
   if (st != NSL_OK) return st;
   const int nshade = tot.nshade;
   NSL_CUDA_TRY(cudaMemcpyAsync(b->dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, s));
@@ -257,6 +277,23 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
 }
 
 }  // namespace
+
+namespace nsl {
+nsl_status batch_render_prestaged(nsl_batch* b, const nsl_plume* plumes, const float* const* staged,
+                                  int n, const nsl_march_opts* opts, int precision, cudaStream_t s) {
+  return render(b, plumes, n, opts, precision, s, staged);
+}
+
+// Allocate the march and network scratch up front so that batches that fit in
+// it never reallocate (and never synchronise the device).
+nsl_status batch_reserve(nsl_batch* b, size_t seg_bytes, size_t net_bytes, cudaStream_t s) {
+  nsl_status st = grow(b, &b->seg, &b->seg_bytes, seg_bytes, s, "march scratch");
+  if (st != NSL_OK) return st;
+  return grow(b, &b->net, &b->net_bytes, net_bytes, s, "network workspace");
+}
+
+int batch_seg_len(const nsl_batch* b) { return b->seg_len; }
+}  // namespace nsl
 
 extern "C" {
 
@@ -399,7 +436,8 @@ nsl_status nsl_batch_update_graph(nsl_batch* b, const nsl_plume* plumes, int n,
   Totals tot{};
   Tables scratch;
   b->capturing = true;  // refuse any growth
-  nsl_status st = prepare(b, scratch, plumes, n, opts, b->graph_totals.precision, nullptr, &imgs, &ws, &tot);
+  nsl_status st = prepare(b, scratch, plumes, n, opts, b->graph_totals.precision, nullptr, &imgs, &ws,
+                          &tot, nullptr);
   b->capturing = false;
   if (st != NSL_OK) return st;
   if (!(tot == b->graph_totals))

@@ -254,6 +254,13 @@ cudaError_t net_tc_forward_group(const NetTcWeights* wt, const NetF32Weights* wf
                                  unsigned int* err_flag, cudaStream_t s);
 // runtime tunable: CTAs per SM of the tensor-core convolutions (1..4)
 void net_tc_set_ctas_per_sm(int v);
+
+// ---- batched frames (batch.cu), used by the server ----
+void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes);
+nsl_status batch_render_prestaged(nsl_batch* b, const nsl_plume* plumes, const float* const* staged,
+                                  int n, const nsl_march_opts* opts, int precision, cudaStream_t s);
+nsl_status batch_reserve(nsl_batch* b, size_t seg_bytes, size_t net_bytes, cudaStream_t s);
+int batch_seg_len(const nsl_batch* b);
 int net_tc_ctas_per_sm();
 
 }  // namespace nsl

@@ -433,3 +433,31 @@ def batch_plumes_spec(count: int = 64, seed: int = 4, sizes=(32, 48, 64, 96, 128
         s = int(rng.integers(0, 1 << 30))
         out.append(BatchPlume(n, b, b, s, perspective_camera(n, s, b, b), random_light(s), step))
     return out
+
+
+def serving_plumes_spec(count: int = 256, seed: int = 5, sizes=(32, 48, 64, 96, 128, 192, 256),
+                        billboards=(64, 128, 256, 512, 1024), step: float = 2.0) -> list:
+    """The serving workload's resident plumes: grid sizes drawn uniformly from
+    `sizes` (cubic), square billboards from `billboards`, seeded per plume."""
+    rng = np.random.default_rng(13_000_019 * seed + 7)
+    out = []
+    for k in range(count):
+        n = int(rng.choice(sizes))
+        b = int(rng.choice(billboards))
+        s = int(rng.integers(0, 1 << 30))
+        out.append(BatchPlume(n, b, b, s, perspective_camera(n, s, b, b), random_light(s), step))
+    return out
+
+
+def poisson_requests(count_plumes: int, rate_hz: float, duration_s: float, seed: int = 5):
+    """Seeded Poisson arrivals: (arrival time in s, plume index, camera seed,
+    light seed) with exponential inter-arrival times of mean 1/rate_hz and the
+    plume drawn uniformly."""
+    rng = np.random.default_rng(17_000_023 * seed + 9)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate_hz))
+        if t >= duration_s:
+            return out
+        out.append((t, int(rng.integers(0, count_plumes)), int(rng.integers(0, 1 << 30)),
+                    int(rng.integers(0, 1 << 30))))

@@ -24,7 +24,11 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host", "nsl_last_error",
            "nsl_status_str", "nsl_batch_create", "nsl_batch_destroy", "nsl_batch_render",
            "nsl_batch_capture_graph", "nsl_batch_update_graph", "nsl_batch_launch_graph",
-           "nsl_batch_set_tuning", "nsl_batch_get_tuning", "nsl_batch_autotune"]
+           "nsl_batch_set_tuning", "nsl_batch_get_tuning", "nsl_batch_autotune",
+           "nsl_default_server_opts", "nsl_server_create", "nsl_server_destroy",
+           "nsl_server_add_plume", "nsl_server_remove_plume", "nsl_server_submit", "nsl_server_wait",
+           "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
+           "nsl_server_reset_stats"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -52,6 +56,24 @@ class nsl_plume(C.Structure):
     _fields_ = [("density_dev", C.c_void_p), ("mask_dev", C.c_void_p), ("grid", nsl_grid_desc),
                 ("camera", nsl_camera), ("step_voxels", C.c_float), ("light", nsl_light),
                 ("guide_dev", C.c_void_p), ("lightmaps_dev", C.c_void_p), ("rgba_dev", C.c_void_p)]
+
+
+class nsl_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("scratch_bytes_per_stream", C.c_size_t),
+                ("streams", C.c_int), ("max_batch", C.c_int), ("precision", C.c_int),
+                ("march", nsl_march_opts)]
+
+
+class nsl_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("queued", C.c_uint64), ("running", C.c_uint64), ("batches", C.c_uint64),
+                ("admissions", C.c_uint64), ("evictions", C.c_uint64), ("pixels_completed", C.c_double),
+                ("resident_plumes", C.c_int), ("resident_bytes", C.c_size_t), ("used_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("mean_batch", C.c_double), ("busy_s", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class NslError(RuntimeError):
@@ -102,6 +124,26 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("nsl_batch_create", "nsl_batch_render", "nsl_batch_capture_graph",
                  "nsl_batch_update_graph", "nsl_batch_launch_graph", "nsl_batch_set_tuning",
                  "nsl_batch_get_tuning", "nsl_batch_autotune"):
+        getattr(lib, name).restype = C.c_int
+    lib.nsl_default_server_opts.argtypes = [C.POINTER(nsl_server_opts)]
+    lib.nsl_default_server_opts.restype = None
+    lib.nsl_server_create.argtypes = [vp, C.c_size_t, C.POINTER(nsl_server_opts), C.POINTER(vp)]
+    lib.nsl_server_destroy.argtypes = [vp]
+    lib.nsl_server_destroy.restype = None
+    lib.nsl_server_add_plume.argtypes = [vp, C.POINTER(nsl_grid_desc), vp, vp, C.c_float, i, i,
+                                         C.POINTER(C.c_int)]
+    lib.nsl_server_remove_plume.argtypes = [vp, i]
+    lib.nsl_server_submit.argtypes = [vp, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), vp, vp,
+                                      C.POINTER(C.c_uint64)]
+    lib.nsl_server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(C.c_double)]
+    lib.nsl_server_drain.argtypes = [vp, C.c_double]
+    lib.nsl_server_plume_state.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                           C.POINTER(C.c_int)]
+    lib.nsl_server_get_stats.argtypes = [vp, C.POINTER(nsl_server_stats)]
+    lib.nsl_server_reset_stats.argtypes = [vp]
+    for name in ("nsl_server_create", "nsl_server_add_plume", "nsl_server_remove_plume",
+                 "nsl_server_submit", "nsl_server_wait", "nsl_server_drain", "nsl_server_plume_state",
+                 "nsl_server_get_stats", "nsl_server_reset_stats"):
         getattr(lib, name).restype = C.c_int
     lib.nsl_last_error.argtypes = []
     lib.nsl_last_error.restype = C.c_char_p
@@ -371,3 +413,95 @@ class Batch:
                                         int(precision), cache_path.encode() if cache_path else None,
                                         _stream(stream), C.byref(ms)), "nsl_batch_autotune")
         return ms.value
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+def server_opts(**kw) -> nsl_server_opts:
+    o = nsl_server_opts()
+    load().nsl_default_server_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "march":
+            o.march = v
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owns an nsl_server; the methods forward to the C ABI.  Host density
+    arrays handed to add_plume are kept referenced here until removal."""
+
+    def __init__(self, blob: bytes, opts: nsl_server_opts | None = None):
+        lib = load()
+        out = C.c_void_p()
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib.nsl_server_create(buf, len(blob), C.byref(opts) if opts else None, C.byref(out)),
+              "nsl_server_create")
+        self.s = out
+        self._keep = {}
+
+    def close(self):
+        if self.s:
+            load().nsl_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_plume(self, density, mask, step, max_width, max_height, sigma_scale=1.0) -> int:
+        import numpy as np
+        density = np.ascontiguousarray(density)
+        nz, ny, nx = density.shape
+        dt = NSL_F16 if density.dtype == np.float16 else NSL_F32
+        if density.dtype not in (np.float16, np.float32):
+            raise ValueError("density must be float32 or float16")
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        g = nsl_grid_desc(nx, ny, nz, dt, float(sigma_scale))
+        pid = C.c_int()
+        check(load().nsl_server_add_plume(self.s, C.byref(g), C.c_void_p(density.ctypes.data),
+                                          None if m is None else C.c_void_p(m.ctypes.data), float(step),
+                                          int(max_width), int(max_height), C.byref(pid)),
+              "nsl_server_add_plume")
+        self._keep[pid.value] = (density, m)
+        return pid.value
+
+    def remove_plume(self, pid):
+        check(load().nsl_server_remove_plume(self.s, int(pid)), "nsl_server_remove_plume")
+        self._keep.pop(pid, None)
+
+    def submit(self, pid, cam, light, lightmaps=None, rgba=None) -> int:
+        rid = C.c_uint64()
+        c = camera(cam)
+        lt = lights([light])
+        check(load().nsl_server_submit(self.s, int(pid), C.byref(c), lt, _dptr(lightmaps, F32), _dptr(rgba, F32),
+                                       C.byref(rid)), "nsl_server_submit")
+        return rid.value
+
+    def wait(self, rid, timeout_ms=60000.0) -> float:
+        lat = C.c_double()
+        check(load().nsl_server_wait(self.s, C.c_uint64(rid), float(timeout_ms), C.byref(lat)), "nsl_server_wait")
+        return lat.value
+
+    def drain(self, timeout_ms=120000.0):
+        check(load().nsl_server_drain(self.s, float(timeout_ms)), "nsl_server_drain")
+
+    def plume_state(self, pid):
+        g, lm, rgba, res = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_int()
+        check(load().nsl_server_plume_state(self.s, int(pid), C.byref(g), C.byref(lm), C.byref(rgba),
+                                            C.byref(res)), "nsl_server_plume_state")
+        return g.value, lm.value, rgba.value, bool(res.value)
+
+    def stats(self) -> dict:
+        st = nsl_server_stats()
+        check(load().nsl_server_get_stats(self.s, C.byref(st)), "nsl_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        check(load().nsl_server_reset_stats(self.s), "nsl_server_reset_stats")
