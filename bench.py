@@ -182,9 +182,9 @@ def main():
     ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--forms", default="batched,serving",
-                    help="comma list of systems forms measured after the primary line's "
-                         "workload ('batched', 'serving', or 'none')")
+    ap.add_argument("--forms", default="animated,batched,serving",
+                    help="comma list of further workloads measured after the primary line's "
+                         "('animated', 'batched', 'serving', or 'none')")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of each Poisson arrival run of the serving form")
     args = ap.parse_args()
@@ -321,6 +321,8 @@ def main():
     }
     ctx.close()
     forms = [f for f in args.forms.split(",") if f and f != "none"]
+    if "animated" in forms:
+        line["animated"] = bench_animated(nsl, I, dev, args, rank == 0 and ws == 1 and not args.no_cpu_baseline)
     if "serving" in forms:
         line["serving"] = bench_serving(nsl, I, dev, args)
     if "batched" in forms:
@@ -344,6 +346,67 @@ def main():
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_animated(nsl, I, dev, args, with_oracle):
+    """Animated form: 300 frames of a 256^3 FP16 plume advected along a seeded
+    curl-noise velocity (generated on the GPU before timing), camera on a
+    seeded spline, light turning 1 degree per frame; 1024x1024 billboard, step
+    4 voxels.  Every frame stages its own grid, marches the guide, runs the
+    network and shades, timed with CUDA events per frame."""
+    import torch
+    t0 = time.perf_counter()
+    seq = I.animated_sequence(256, 300, seed=3, width=1024, height=1024, step=4.0, device=dev)
+    gen_s = time.perf_counter() - t0
+    W = H = 1024
+    blob = I.pack_blob(I.make_params(16, 0), 16)
+    ctx = nsl.Context((256, 256, 256), nsl.NSL_F16, blob, W, H)
+    stream = torch.cuda.current_stream()
+    guide = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    lm = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+    rgba = torch.empty((4, H, W), dtype=torch.float32, device=dev)
+    opts = nsl.march_opts()
+    out = {"workload": "256^3 f16 plume, 300 frames (curl-noise advection, seed 3), perspective 1024x1024 "
+                       "on a spline, light turning 1 deg/frame, step 4 voxels",
+           "generation_s": gen_s, "frames": 300}
+    for name, prec in (("f16", nsl.NSL_PREC_F16), ("bf16", nsl.NSL_PREC_BF16)):
+        def frame(t, evs=None):
+            if evs:
+                evs[0].record(stream)
+            nsl.nsl_stage_grid(ctx.ctx, seq.frames[t], None, stream=stream)
+            nsl.nsl_guiding_map(ctx.ctx, None, None, seq.cameras[t], seq.step, guide, opts=opts, stream=stream)
+            nsl.nsl_predict_lightmaps(ctx.ctx, guide, W, H, prec, lm, stream=stream)
+            nsl.nsl_shade(ctx.ctx, lm, W, H, seq.cameras[t], [seq.lights[t]], rgba, stream=stream)
+            if evs:
+                evs[1].record(stream)
+        for t in range(3):
+            frame(t)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(300)]
+        for t in range(300):
+            frame(t, evs[t])
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in evs])
+        out[name] = {"value": 300 * W * H / (ms.sum() / 1e3) / 1e6, "unit": "Mpix/s",
+                     "ms_per_frame": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)),
+                     "p99_ms": float(np.percentile(ms, 99)), "max_ms": float(ms.max())}
+    if with_oracle:
+        # FP64 oracle guide on a 64-row band of frame 150 against this run's guide
+        import oracle
+        frame(150)
+        torch.cuda.synchronize()
+        g = guide.cpu().numpy()
+        host = seq.frames[150].cpu().numpy()
+        t1 = time.perf_counter()
+        o, _, _ = oracle.guide(host, None, seq.cameras[150], seq.step, rows=(480, 544))
+        dt = time.perf_counter() - t1
+        out["err_vs_oracle"] = {"guide_band_frame150": range_errs(g[:, 480:544], o[:, 480:544])}
+        out["cpu_baseline"] = {"value": 64 * W / dt / 1e6, "unit": "Mpix/s (guide only)", "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": "FP64 guide march of rows 480..543 of frame 150"}
+    ctx.close()
+    del seq
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_serving(nsl, I, dev, args):

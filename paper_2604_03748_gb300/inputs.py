@@ -461,3 +461,119 @@ def poisson_requests(count_plumes: int, rate_hz: float, duration_s: float, seed:
             return out
         out.append((t, int(rng.integers(0, count_plumes)), int(rng.integers(0, 1 << 30)),
                     int(rng.integers(0, 1 << 30))))
+
+
+def fbm_torch(n: int, seed: int, device=None, octaves: int = 4, base_period: float | None = None):
+    """fbm() evaluated with torch (float32, on `device`): same lattice draws,
+    same recipe, values in [-1, 1]."""
+    import torch
+    dev = torch.device(device or "cpu")
+    rng = np.random.default_rng(seed)
+    if base_period is None:
+        base_period = n / 4.0
+    c = torch.arange(n, dtype=torch.float32, device=dev) + 0.5
+    zz, yy, xx = torch.meshgrid(c, c, c, indexing="ij")
+    total = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+    amp, norm, freq = 1.0, 0.0, 1.0 / base_period
+    fade = lambda t: t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    for _ in range(octaves):
+        grads = torch.tensor(_lattice_gradients(rng, 64), device=dev)
+        off = rng.uniform(0, 64, size=3).astype(np.float32)
+        px, py, pz = xx * freq + float(off[0]), yy * freq + float(off[1]), zz * freq + float(off[2])
+        x0, y0, z0 = torch.floor(px), torch.floor(py), torch.floor(pz)
+        fx, fy, fz = px - x0, py - y0, pz - z0
+        ix, iy, iz = x0.long() % 64, y0.long() % 64, z0.long() % 64
+        ux, uy, uz = fade(fx), fade(fy), fade(fz)
+        acc = torch.zeros_like(total)
+        for dz in (0, 1):
+            wz = uz if dz else 1.0 - uz
+            for dy in (0, 1):
+                wy = uy if dy else 1.0 - uy
+                for dx in (0, 1):
+                    wx = ux if dx else 1.0 - ux
+                    g = grads[(iz + dz) % 64, (iy + dy) % 64, (ix + dx) % 64]
+                    acc += wx * wy * wz * (g[..., 0] * (fx - dx) + g[..., 1] * (fy - dy) + g[..., 2] * (fz - dz))
+        total += amp * acc
+        norm += amp
+        amp *= 0.5
+        freq *= 2.0
+    return torch.clamp(total / norm * 1.6, -1.0, 1.0)
+
+
+def _catmull_rom(p0, p1, p2, p3, t):
+    t2, t3 = t * t, t * t * t
+    return 0.5 * ((2.0 * p1) + (-p0 + p2) * t + (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3) * t2
+                  + (-p0 + 3.0 * p1 - 3.0 * p2 + p3) * t3)
+
+
+@dataclass
+class AnimatedSequence:
+    n: int
+    frames: dict           # frame index -> torch float16 tensor [n][n][n] on the device
+    cameras: list          # Camera per frame
+    lights: list           # Light per frame
+    step: float
+
+
+def animated_sequence(n: int = 256, count: int = 300, seed: int = 3, width: int = 1024,
+                      height: int = 1024, step: float = 4.0, device=None, keep=None) -> AnimatedSequence:
+    """The animated workload.  Frame 0 is the blob x fBm generator (seed); each
+    later frame advects the previous one semi-Lagrangian (trilinear, zero
+    outside the box) along a static divergence-free velocity, the curl of three
+    seeded fBm potentials (2 octaves, base period n/2) scaled to a maximum speed
+    of 1 voxel per frame, then re-injects 3% of frame 0 (rho <- 0.97 rho_adv +
+    0.03 rho_0, clamped to [0, 2]); frames are stored as FP16.  The camera
+    (perspective, fov 40) follows a closed Catmull-Rom spline through 8 seeded
+    points 2.5 n from the centre (azimuth U[0, 2 pi), elevation U[-45, 45]
+    degrees); the light starts at a seeded direction and turns 1 degree per frame
+    about the world Y axis.  `keep` limits which frames are kept (all if None)."""
+    import torch
+    import torch.nn.functional as F
+    dev = torch.device(device or "cuda")
+    rho0 = blob_fbm_volume_fast(n, seed, device=dev)
+    psi = [fbm_torch(n, 7_000_001 * seed + 101 + k, dev, octaves=2, base_period=n / 2.0) for k in range(3)]
+    d = [torch.gradient(p) for p in psi]          # each: (d/dz, d/dy, d/dx)
+    vx = d[2][1] - d[1][0]                        # d psi_z/dy - d psi_y/dz
+    vy = d[0][0] - d[2][2]                        # d psi_x/dz - d psi_z/dx
+    vz = d[1][2] - d[0][1]                        # d psi_y/dx - d psi_x/dy
+    vmax = torch.sqrt(vx * vx + vy * vy + vz * vz).max()
+    vx, vy, vz = vx / vmax, vy / vmax, vz / vmax
+    del psi, d
+    c = torch.arange(n, dtype=torch.float32, device=dev) + 0.5
+    zz, yy, xx = torch.meshgrid(c, c, c, indexing="ij")
+    # departure points x - v(x), as grid_sample coordinates (-1 at 0, +1 at n)
+    grid = torch.stack([(xx - vx) / n * 2 - 1, (yy - vy) / n * 2 - 1, (zz - vz) / n * 2 - 1], dim=-1)[None]
+    del zz, yy, xx, vx, vy, vz
+    keep = set(range(count)) if keep is None else set(keep)
+    frames = {}
+    rho = rho0
+    for t in range(count):
+        if t in keep:
+            frames[t] = rho.to(torch.float16)
+        if t + 1 < count:
+            adv = F.grid_sample(rho[None, None], grid, mode="bilinear", padding_mode="zeros",
+                                align_corners=False)[0, 0]
+            rho = torch.clamp(0.97 * adv + 0.03 * rho0, 0.0, 2.0)
+    rng = np.random.default_rng(19_000_033 * seed + 5)
+    ctr = np.array([n / 2.0] * 3)
+    pts = []
+    for _ in range(8):
+        az = rng.uniform(0, 2 * math.pi)
+        el = math.radians(rng.uniform(-45.0, 45.0))
+        pts.append(ctr + 2.5 * n * np.array([math.cos(el) * math.cos(az), math.sin(el), math.cos(el) * math.sin(az)]))
+    cams = []
+    for t in range(count):
+        s = 8.0 * t / count
+        i = int(math.floor(s))
+        u = s - i
+        eye = _catmull_rom(pts[(i - 1) % 8], pts[i % 8], pts[(i + 1) % 8], pts[(i + 2) % 8], u)
+        cams.append(Camera(PERSP, tuple(map(float, eye)), tuple(map(float, ctr)), (0.0, 1.0, 0.0), 40.0, 0.0,
+                           width, height))
+    l0 = random_light(seed)
+    lights = []
+    for t in range(count):
+        a = math.radians(float(t))
+        x, y, z = l0.dir
+        lights.append(Light((math.cos(a) * x + math.sin(a) * z, y, -math.sin(a) * x + math.cos(a) * z),
+                            l0.intensity))
+    return AnimatedSequence(n, frames, cams, lights, step)
