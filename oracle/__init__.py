@@ -11,6 +11,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   reference_lightmaps   pinned (slab closed form, midpoint order)
   net_forward           pinned (PyTorch float64 conv/convT/pool/LayerNorm,
                         NAFBlock identity at beta=gamma=0)
+  net_forward_q8        pinned (E4M3 and binary16 rounding against PyTorch's
+                        float8_e4m3fn / float16 casts and brute force over all
+                        E4M3 codes; the quantised network against a PyTorch
+                        float64 assembly using those casts)
   shade                 pinned (axis lights select one plane; linearity)
   paper-level quality   parity unpinned (no trained weights, no dataset)
 """
@@ -79,6 +83,17 @@ def _load():
                                              C.c_double, C.c_void_p]
     lib.nslo_net_forward.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                      C.c_double, C.c_void_p]
+    lib.nslo_net_forward_q8.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                                        C.c_double, C.c_void_p]
+    lib.nslo_round_f16.argtypes = [C.c_double]
+    lib.nslo_round_f16.restype = C.c_double
+    lib.nslo_e4m3_rn.argtypes = [C.c_double]
+    lib.nslo_e4m3_rn.restype = C.c_double
+    lib.nslo_q8_tensor.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_float)]
+    lib.nslo_q8_tensor.restype = None
+    lib.nslo_q8_weights.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_void_p,
+                                    C.c_void_p]
+    lib.nslo_q8_weights.restype = None
     lib.nslo_shade.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(_Camera), C.POINTER(_Light),
                                C.c_int, C.c_void_p]
     lib.nslo_sample_sigma.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
@@ -178,6 +193,48 @@ def reference_lightmaps(density, mask, camera, hf=0.25, sigma_scale=1.0, phase_g
     if rc != 0:
         raise ValueError(f"nslo_reference_lightmaps failed ({rc})")
     return out
+
+
+def net_forward_q8(guide_planes, params_flat, c0, depth_scale):
+    """The network with FP8 E4M3 convolutions (see nslo_net_forward_q8)."""
+    lib = _load()
+    g = np.ascontiguousarray(guide_planes, dtype=np.float64)
+    _, H, W = g.shape
+    p = np.ascontiguousarray(params_flat, dtype=np.float64)
+    out = np.zeros((8, H, W), np.float64)
+    rc = lib.nslo_net_forward_q8(_ptr(g), H, W, _ptr(p), p.size, int(c0), float(depth_scale), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_net_forward_q8 failed ({rc})")
+    return out
+
+
+def round_f16(x):
+    lib = _load()
+    return np.vectorize(lambda v: lib.nslo_round_f16(float(v)), otypes=[np.float64])(x)
+
+
+def e4m3_rn(x):
+    lib = _load()
+    return np.vectorize(lambda v: lib.nslo_e4m3_rn(float(v)), otypes=[np.float64])(x)
+
+
+def q8_tensor(x):
+    """(codes, dequantisation factor) of a tensor of binary16 values."""
+    lib = _load()
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    codes = np.zeros_like(a)
+    deq = C.c_float()
+    lib.nslo_q8_tensor(_ptr(a), a.size, _ptr(codes), C.byref(deq))
+    return codes, deq.value
+
+
+def q8_weights(w, cout, count, so, sj):
+    lib = _load()
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    codes = np.zeros_like(a)
+    s = np.zeros(cout, np.float32)
+    lib.nslo_q8_weights(_ptr(a), int(cout), int(count), int(so), int(sj), _ptr(codes), _ptr(s))
+    return codes, s
 
 
 def net_forward(guide_planes, params_flat, c0, depth_scale):

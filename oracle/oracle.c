@@ -616,6 +616,32 @@ static int conv3_relu(cursor* cur, const double* in, int cin, int H, int W, int 
   return 0;
 }
 
+/* The four channel adapters (F&B, L&R, U&D, A&E in that order), each a
+ * NAFBlock on F followed by a 1x1 conv to two output planes. */
+static int adapters_forward(cursor* cur, const double* F, int c1, int H, int W, double* z,
+                            double* out) {
+  static const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
+  const size_t P0 = (size_t)H * W;
+  int64_t nb = nslo_nafblock_params(c1);
+  for (int a = 0; a < 4; ++a) {
+    const double* bp = take(cur, nb);
+    const double* hw = take(cur, 2 * c1);
+    const double* hb = take(cur, 2);
+    if (!bp || !hw || !hb) return 3;
+    int rc = nslo_nafblock(F, c1, H, W, bp, z);
+    if (rc) return rc;
+    for (int oc = 0; oc < 2; ++oc) {
+      double* dst = out + (size_t)plane_of[a][oc] * P0;
+      for (size_t p = 0; p < P0; ++p) {
+        double s = hb[oc];
+        for (int ci = 0; ci < c1; ++ci) s += hw[oc * c1 + ci] * z[ci * P0 + p];
+        dst[p] = s;
+      }
+    }
+  }
+  return 0;
+}
+
 /* The lightmap generator of Sec. 4.3 / Fig. 3: a four-level UNet (widths
  * c0*{1,2,4,8}, two 3x3 conv+ReLU per level, 2x2 max-pool down, 2x2 stride-2
  * transposed conv up, skip concatenated after the upsampled tensor) gives the
@@ -696,26 +722,226 @@ int nslo_net_forward(const double* guide, int H, int W, const double* params, in
     if ((rc = conv3_relu(&cur, cat, 2 * c1, H, W, c1, d))) goto done;
     if ((rc = conv3_relu(&cur, d, c1, H, W, c1, F))) goto done;
   }
-  /* channel adapters, in the order F&B, L&R, U&D, A&E */
-  {
-    static const int plane_of[4][2] = {{4, 5}, {0, 1}, {2, 3}, {6, 7}};
-    int64_t nb = nslo_nafblock_params(c1);
-    for (int a = 0; a < 4; ++a) {
-      const double* bp = take(&cur, nb);
-      const double* hw = take(&cur, 2 * c1);
-      const double* hb = take(&cur, 2);
-      if (!bp || !hw || !hb) { rc = 3; goto done; }
-      if ((rc = nslo_nafblock(F, c1, H, W, bp, z))) goto done;
-      for (int oc = 0; oc < 2; ++oc) {
-        double* dst = out + (size_t)plane_of[a][oc] * P0;
-        for (size_t p = 0; p < P0; ++p) {
-          double s = hb[oc];
-          for (int ci = 0; ci < c1; ++ci) s += hw[oc * c1 + ci] * z[ci * P0 + p];
-          dst[p] = s;
-        }
-      }
+  /* channel adapters */
+  if ((rc = adapters_forward(&cur, F, c1, H, W, z, out))) goto done;
+  if (cur.left != 0) rc = 4;
+done:
+  free(x0); free(a0); free(s1); free(p1); free(a1); free(s2); free(p2); free(a2); free(s3);
+  free(p3); free(a3); free(bt); free(cat); free(d); free(F); free(z);
+  return rc;
+}
+
+
+/* ------------------------------------------------------------------------- */
+/* FP8 E4M3 network (precision form; no counterpart in the paper)            */
+/* ------------------------------------------------------------------------- */
+
+/* IEEE binary16 rounding (round to nearest, ties to even) of a finite double:
+ * 10 fraction bits, exponent range down to 2^-14, subnormal quantum 2^-24;
+ * magnitudes that round above 65504 become infinite. */
+double nslo_round_f16(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  const double a = fabs(x);
+  int e;
+  frexp(a, &e);            /* a = f 2^e, f in [0.5, 1): a in [2^(e-1), 2^e) */
+  int E = e - 1;
+  if (E < -14) E = -14;
+  const double q = ldexp(1.0, E - 10);
+  double r = rint(a / q) * q;   /* the quotient is exact; rint rounds half to even */
+  if (r > 65504.0) r = INFINITY;
+  return copysign(r, x);
+}
+
+/* OCP FP8 E4M3 ("fn": no infinities) rounding, to nearest with ties to even
+ * and saturation to the largest finite magnitude: exponent bias 7, 3 fraction
+ * bits, normal range [2^-6, 448], subnormal quantum 2^-9. */
+double nslo_e4m3_rn(double x) {
+  if (x == 0.0 || isnan(x)) return x;
+  const double a = fabs(x);
+  int e;
+  frexp(a, &e);
+  int E = e - 1;
+  if (E < -6) E = -6;
+  const double q = ldexp(1.0, E - 3);
+  double r = rint(a / q) * q;
+  if (r > 448.0) r = 448.0;
+  return copysign(r, x);
+}
+
+/* Per-tensor activation scale as the kernels compute it, in binary32:
+ * quantised x = E4M3(x * (448 / amax)), dequantisation factor amax / 448
+ * (both 1 for an all-zero tensor). */
+static void q8_scales(double amax, float* inv, float* deq) {
+  const float a = (float)amax;
+  if (a > 0.f) {
+    *inv = 448.0f / a;
+    *deq = a / 448.0f;
+  } else {
+    *inv = 1.0f;
+    *deq = 1.0f;
+  }
+}
+
+/* Quantise a whole tensor (its values are binary16 numbers) with its own amax. */
+void nslo_q8_tensor(const double* x, size_t n, double* codes, float* deq) {
+  double amax = 0.0;
+  for (size_t i = 0; i < n; ++i) amax = fmax(amax, fabs(x[i]));
+  float inv;
+  q8_scales(amax, &inv, deq);
+  for (size_t i = 0; i < n; ++i) {
+    const float v = (float)x[i] * inv;          /* binary32 product, as on the device */
+    codes[i] = nslo_e4m3_rn((double)v);
+  }
+}
+
+/* Per-output-channel weight quantisation in binary32: for output channel co,
+ * s[co] = max |w| / 448 over the channel's weights, code = E4M3(w / s[co]).
+ * Element (co, j) of the channel sits at w[co * so + j * sj] for j < count. */
+void nslo_q8_weights(const double* w, int cout, int count, int64_t so, int64_t sj, double* codes,
+                     float* s) {
+  for (int co = 0; co < cout; ++co) {
+    float amax = 0.f;
+    for (int j = 0; j < count; ++j) amax = fmaxf(amax, fabsf((float)w[co * so + j * sj]));
+    const float sc = amax > 0.f ? amax / 448.0f : 1.0f;
+    s[co] = sc;
+    for (int j = 0; j < count; ++j) {
+      const float v = (float)w[co * so + j * sj] / sc;
+      codes[co * so + j * sj] = nslo_e4m3_rn((double)v);
     }
   }
+}
+
+/* One FP8 3x3 convolution: input tensor x (binary16 values) quantised with its
+ * amax, weights per output channel; the exact sum of code products is scaled
+ * by deq * s[co], the bias added, ReLU applied, and the result rounded to
+ * binary16 as the stored activation. */
+static int conv3_q8(cursor* cur, const double* x, int cin, int H, int W, int cout, double* out) {
+  const double* w = take(cur, (int64_t)cout * cin * 9);
+  const double* b = take(cur, cout);
+  if (!w || !b) return 3;
+  const size_t P = (size_t)H * W;
+  double* xq = malloc(sizeof(double) * cin * P);
+  double* wq = malloc(sizeof(double) * cout * cin * 9);
+  double* zb = calloc((size_t)cout, sizeof(double));
+  float* s = malloc(sizeof(float) * cout);
+  if (!xq || !wq || !zb || !s) { free(xq); free(wq); free(zb); free(s); return 2; }
+  float deq;
+  nslo_q8_tensor(x, (size_t)cin * P, xq, &deq);
+  nslo_q8_weights(w, cout, cin * 9, (int64_t)cin * 9, 1, wq, s);
+  nslo_conv2d(xq, cin, H, W, wq, zb, cout, 3, out);
+  for (int co = 0; co < cout; ++co) {
+    const double f = (double)deq * (double)s[co];
+    for (size_t p = 0; p < P; ++p) {
+      const double v = out[co * P + p] * f + b[co];
+      out[co * P + p] = nslo_round_f16(v > 0.0 ? v : 0.0);
+    }
+  }
+  free(xq); free(wq); free(zb); free(s);
+  return 0;
+}
+
+/* One FP8 2x2 stride-2 transposed convolution (no activation), same scheme;
+ * weights [cin][cout][2][2] quantised per output channel over ci and the four
+ * kernel positions. */
+static int convT_q8(cursor* cur, const double* x, int cin, int H, int W, int cout, double* out) {
+  const double* w = take(cur, (int64_t)cin * cout * 4);
+  const double* b = take(cur, cout);
+  if (!w || !b) return 3;
+  const size_t P = (size_t)H * W, P4 = 4 * P;
+  double* xq = malloc(sizeof(double) * cin * P);
+  double* wq = malloc(sizeof(double) * cin * cout * 4);
+  double* zb = calloc((size_t)cout, sizeof(double));
+  float* s = malloc(sizeof(float) * cout);
+  if (!xq || !wq || !zb || !s) { free(xq); free(wq); free(zb); free(s); return 2; }
+  float deq;
+  nslo_q8_tensor(x, (size_t)cin * P, xq, &deq);
+  /* output channel co owns the elements ((ci * cout + co) * 4 + k) */
+  for (int co = 0; co < cout; ++co) {
+    float amax = 0.f;
+    for (int ci = 0; ci < cin; ++ci)
+      for (int k = 0; k < 4; ++k) amax = fmaxf(amax, fabsf((float)w[((size_t)ci * cout + co) * 4 + k]));
+    const float sc = amax > 0.f ? amax / 448.0f : 1.0f;
+    s[co] = sc;
+    for (int ci = 0; ci < cin; ++ci)
+      for (int k = 0; k < 4; ++k) {
+        const size_t i = ((size_t)ci * cout + co) * 4 + k;
+        wq[i] = nslo_e4m3_rn((double)((float)w[i] / sc));
+      }
+  }
+  nslo_conv_transpose2x2(xq, cin, H, W, wq, zb, cout, out);
+  for (int co = 0; co < cout; ++co) {
+    const double f = (double)deq * (double)s[co];
+    for (size_t p = 0; p < P4; ++p) out[co * P4 + p] = nslo_round_f16(out[co * P4 + p] * f + b[co]);
+  }
+  free(xq); free(wq); free(zb); free(s);
+  return 0;
+}
+
+/* The network with FP8 E4M3 convolutions: the first 3x3 convolution (3 input
+ * channels) in full precision, every later 3x3 and transposed convolution with
+ * per-tensor activation and per-output-channel weight scales, FP32-class
+ * accumulation, activations stored as binary16 between layers; the adapters
+ * in full precision on the binary16 feature map. */
+int nslo_net_forward_q8(const double* guide, int H, int W, const double* params, int64_t n_params,
+                        int c0, double depth_scale, double* out) {
+  if (H % 8 || W % 8 || H <= 0 || W <= 0) return 1;
+  cursor cur = {params, n_params};
+  const int c1 = c0, c2 = 2 * c0, c3 = 4 * c0, c4 = 8 * c0;
+  size_t P0 = (size_t)H * W, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  double* x0 = malloc(sizeof(double) * 3 * P0);
+  double* a0 = malloc(sizeof(double) * c1 * P0);
+  double* s1 = malloc(sizeof(double) * c1 * P0);
+  double* p1 = malloc(sizeof(double) * c1 * P1);
+  double* a1 = malloc(sizeof(double) * c2 * P1);
+  double* s2 = malloc(sizeof(double) * c2 * P1);
+  double* p2 = malloc(sizeof(double) * c2 * P2);
+  double* a2 = malloc(sizeof(double) * c3 * P2);
+  double* s3 = malloc(sizeof(double) * c3 * P2);
+  double* p3 = malloc(sizeof(double) * c3 * P3);
+  double* a3 = malloc(sizeof(double) * c4 * P3);
+  double* bt = malloc(sizeof(double) * c4 * P3);
+  double* cat = malloc(sizeof(double) * 2 * c1 * P0 + sizeof(double) * c4 * P2);
+  double* d = malloc(sizeof(double) * c1 * P0 * 2 + sizeof(double) * c4 * P2);
+  double* F = malloc(sizeof(double) * c1 * P0);
+  double* z = malloc(sizeof(double) * c1 * P0);
+  int rc = 0;
+  if (!x0 || !a0 || !s1 || !p1 || !a1 || !s2 || !p2 || !a2 || !s3 || !p3 || !a3 || !bt || !cat ||
+      !d || !F || !z) { rc = 2; goto done; }
+
+  memcpy(x0, guide, sizeof(double) * 2 * P0);
+  for (size_t p = 0; p < P0; ++p) x0[2 * P0 + p] = guide[2 * P0 + p] * depth_scale;
+
+  /* first convolution in full precision, stored as binary16 */
+  if ((rc = conv3_relu(&cur, x0, 3, H, W, c1, a0))) goto done;
+  for (size_t i = 0; i < (size_t)c1 * P0; ++i) a0[i] = nslo_round_f16(a0[i]);
+  /* encoder */
+  if ((rc = conv3_q8(&cur, a0, c1, H, W, c1, s1))) goto done;
+  nslo_maxpool2(s1, c1, H, W, p1);
+  if ((rc = conv3_q8(&cur, p1, c1, H1, W1, c2, a1))) goto done;
+  if ((rc = conv3_q8(&cur, a1, c2, H1, W1, c2, s2))) goto done;
+  nslo_maxpool2(s2, c2, H1, W1, p2);
+  if ((rc = conv3_q8(&cur, p2, c2, H2, W2, c3, a2))) goto done;
+  if ((rc = conv3_q8(&cur, a2, c3, H2, W2, c3, s3))) goto done;
+  nslo_maxpool2(s3, c3, H2, W2, p3);
+  if ((rc = conv3_q8(&cur, p3, c3, H3, W3, c4, a3))) goto done;
+  if ((rc = conv3_q8(&cur, a3, c4, H3, W3, c4, bt))) goto done;
+  /* decoder: the concatenation (upsampled first, skip second) is one tensor
+   * with one activation scale */
+  if ((rc = convT_q8(&cur, bt, c4, H3, W3, c3, cat))) goto done;
+  memcpy(cat + (size_t)c3 * P2, s3, sizeof(double) * c3 * P2);
+  if ((rc = conv3_q8(&cur, cat, 2 * c3, H2, W2, c3, d))) goto done;
+  if ((rc = conv3_q8(&cur, d, c3, H2, W2, c3, a2))) goto done;
+  if ((rc = convT_q8(&cur, a2, c3, H2, W2, c2, cat))) goto done;
+  memcpy(cat + (size_t)c2 * P1, s2, sizeof(double) * c2 * P1);
+  if ((rc = conv3_q8(&cur, cat, 2 * c2, H1, W1, c2, d))) goto done;
+  if ((rc = conv3_q8(&cur, d, c2, H1, W1, c2, a1))) goto done;
+  if ((rc = convT_q8(&cur, a1, c2, H1, W1, c1, cat))) goto done;
+  memcpy(cat + (size_t)c1 * P0, s1, sizeof(double) * c1 * P0);
+  if ((rc = conv3_q8(&cur, cat, 2 * c1, H, W, c1, d))) goto done;
+  if ((rc = conv3_q8(&cur, d, c1, H, W, c1, F))) goto done;
+  /* channel adapters on the binary16 feature map */
+  if ((rc = adapters_forward(&cur, F, c1, H, W, z, out))) goto done;
   if (cur.left != 0) rc = 4;
 done:
   free(x0); free(a0); free(s1); free(p1); free(a1); free(s2); free(p2); free(a2); free(s3);

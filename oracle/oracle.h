@@ -11,6 +11,7 @@
  */
 #ifndef NSL_ORACLE_H
 #define NSL_ORACLE_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -66,6 +67,19 @@ int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, 
  * guide: [3][H][W]; params: float64 values in the blob order; out: [8][H][W]. */
 int nslo_net_forward(const double* guide, int H, int W, const double* params,
                      int64_t n_params, int c0, double depth_scale, double* out);
+
+/* The same network with FP8 E4M3 convolutions (every 3x3 and transposed
+ * convolution after the first): per-tensor activation scales amax/448 and
+ * per-output-channel weight scales, both in binary32, exact products summed,
+ * activations rounded to binary16 between layers. */
+int nslo_net_forward_q8(const double* guide, int H, int W, const double* params,
+                        int64_t n_params, int c0, double depth_scale, double* out);
+/* rounding primitives of that path */
+double nslo_round_f16(double x);
+double nslo_e4m3_rn(double x);
+void nslo_q8_tensor(const double* x, size_t n, double* codes, float* deq);
+void nslo_q8_weights(const double* w, int cout, int count, int64_t so, int64_t sj, double* codes,
+                     float* s);
 
 /* Six-way shading: rgba [4][H][W]. */
 int nslo_shade(const double* lightmaps, int H, int W, const nslo_camera* cam,
