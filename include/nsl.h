@@ -226,7 +226,8 @@ NSL_API nsl_status nsl_batch_create(const void* weights_blob, size_t blob_bytes,
 NSL_API void nsl_batch_destroy(nsl_batch* b);
 
 /* Guide, lightmaps and (where rgba_dev is set) shading for n plumes, with one
- * set of march options for all; precision NSL_PREC_F16 or NSL_PREC_BF16.
+ * set of march options for all; precision NSL_PREC_F16, NSL_PREC_BF16 or
+ * NSL_PREC_FP8.
  * Asynchronous on `stream`; the caller owns every buffer of `plumes`. */
 NSL_API nsl_status nsl_batch_render(nsl_batch* b, const nsl_plume* plumes, int n,
                                     const nsl_march_opts* opts, int precision, void* stream);
@@ -289,7 +290,7 @@ typedef struct {
   size_t scratch_bytes_per_stream; /* march + network scratch of one batch slot (0: budget/8) */
   int streams;                     /* batch slots in flight at once, 1..4 */
   int max_batch;                   /* requests per batch, 1..64 */
-  int precision;                   /* NSL_PREC_F16 or NSL_PREC_BF16 */
+  int precision;                   /* NSL_PREC_F16, NSL_PREC_BF16 or NSL_PREC_FP8 */
   nsl_march_opts march;            /* march options of every frame */
 } nsl_server_opts;
 

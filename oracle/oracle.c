@@ -768,14 +768,20 @@ double nslo_e4m3_rn(double x) {
   return copysign(r, x);
 }
 
-/* Per-tensor activation scale as the kernels compute it, in binary32:
- * quantised x = E4M3(x * (448 / amax)), dequantisation factor amax / 448
- * (both 1 for an all-zero tensor). */
+/* Per-tensor activation scale: the smallest power of two s = 2^k with
+ * amax <= 448 s, so quantised x = E4M3(x / s) (an exact scaling) and the
+ * dequantisation factor is s; s = 1 for an all-zero tensor.  A power of two
+ * keeps the scale, and so every quantisation decision, unchanged under tiny
+ * changes of amax.  With amax = f 2^e, f in [0.5, 1): k = e - 9 if f <= 0.875
+ * (448 = 0.875 * 2^9), else e - 8. */
 static void q8_scales(double amax, float* inv, float* deq) {
   const float a = (float)amax;
   if (a > 0.f) {
-    *inv = 448.0f / a;
-    *deq = a / 448.0f;
+    int e;
+    const float f = frexpf(a, &e);
+    const int k = e - 9 + (f > 0.875f ? 1 : 0);
+    *inv = ldexpf(1.0f, -k);
+    *deq = ldexpf(1.0f, k);
   } else {
     *inv = 1.0f;
     *deq = 1.0f;
@@ -789,7 +795,7 @@ void nslo_q8_tensor(const double* x, size_t n, double* codes, float* deq) {
   float inv;
   q8_scales(amax, &inv, deq);
   for (size_t i = 0; i < n; ++i) {
-    const float v = (float)x[i] * inv;          /* binary32 product, as on the device */
+    const float v = (float)x[i] * inv;          /* exact: inv is a power of two */
     codes[i] = nslo_e4m3_rn((double)v);
   }
 }
@@ -879,9 +885,9 @@ static int convT_q8(cursor* cur, const double* x, int cin, int H, int W, int cou
 
 /* The network with FP8 E4M3 convolutions: the first 3x3 convolution (3 input
  * channels) in full precision, every later 3x3 and transposed convolution with
- * per-tensor activation and per-output-channel weight scales, FP32-class
- * accumulation, activations stored as binary16 between layers; the adapters
- * in full precision on the binary16 feature map. */
+ * per-tensor power-of-two activation scales and per-output-channel weight
+ * scales, exact sums of code products, activations stored as binary16 between
+ * layers; the adapters in full precision on the binary16 feature map. */
 int nslo_net_forward_q8(const double* guide, int H, int W, const double* params, int64_t n_params,
                         int c0, double depth_scale, double* out) {
   if (H % 8 || W % 8 || H <= 0 || W <= 0) return 1;

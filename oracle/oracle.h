@@ -69,9 +69,10 @@ int nslo_net_forward(const double* guide, int H, int W, const double* params,
                      int64_t n_params, int c0, double depth_scale, double* out);
 
 /* The same network with FP8 E4M3 convolutions (every 3x3 and transposed
- * convolution after the first): per-tensor activation scales amax/448 and
- * per-output-channel weight scales, both in binary32, exact products summed,
- * activations rounded to binary16 between layers. */
+ * convolution after the first): per-tensor power-of-two activation scales
+ * (the smallest 2^k with amax <= 448 * 2^k) and per-output-channel weight
+ * scales max|w|/448 in binary32, exact products summed, activations rounded
+ * to binary16 between layers. */
 int nslo_net_forward_q8(const double* guide, int H, int W, const double* params,
                         int64_t n_params, int c0, double depth_scale, double* out);
 /* rounding primitives of that path */

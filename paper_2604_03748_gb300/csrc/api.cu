@@ -108,7 +108,7 @@ struct nsl_ctx {
   void* seg_scratch = nullptr;            // segmented-march scratch
   size_t seg_bytes = 0;
   NetF32Weights* wf32 = nullptr;
-  NetTcWeights* wtc[2] = {};        // tensor-core weights: [0] FP16, [1] BF16 (built on first use)
+  NetTcWeights* wtc[3] = {};        // tensor-core weights: [0] FP16, [1] BF16, [2] FP8 (built on first use)
   void* ws = nullptr;               // network workspace (shared by both precisions)
   size_t ws_bytes = 0;
   unsigned int* err_host = nullptr; // device-written error word (mapped host memory)
@@ -233,6 +233,7 @@ void nsl_destroy(nsl_ctx* c) {
   net_f32_destroy(c->wf32);
   net_tc_destroy(c->wtc[0]);
   net_tc_destroy(c->wtc[1]);
+  net_tc_destroy(c->wtc[2]);
   cudaFree(c->ws);
   if (c->err_host) cudaFreeHost(c->err_host);
   cudaFree(c->h_density);
@@ -471,8 +472,9 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
       e = net_f32_forward(c->wf32, img, c->ws, c->ws_bytes, s);
       break;
     case NSL_PREC_BF16:
-    case NSL_PREC_F16: {
-      const int elem = precision == NSL_PREC_BF16 ? 1 : 0;
+    case NSL_PREC_F16:
+    case NSL_PREC_FP8: {
+      const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
       if (!c->wtc[elem]) {
         c->wtc[elem] = net_tc_create(c->params.data(), c->layout, elem, &e);
         if (!c->wtc[elem]) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");

@@ -54,7 +54,7 @@ struct nsl_batch {
   std::vector<float> params;
   NetLayout layout{};
   NetF32Weights* wf = nullptr;
-  NetTcWeights* wtc[2] = {};
+  NetTcWeights* wtc[3] = {};         // FP16, BF16, FP8
   // device memory, grown on demand (never while a graph is being captured)
   void* staged = nullptr;  size_t staged_bytes = 0;
   void* seg = nullptr;     size_t seg_bytes = 0;
@@ -143,8 +143,8 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
                    std::vector<void*>* ws, Totals* tot, const float* const* prestaged) {
   if (n < 1 || n > b->max_plumes || n > kMaxGroup)
     return fail(NSL_ERR_INVALID_ARG, "nsl_batch: n must be in [1, %d]", b->max_plumes);
-  if (precision != NSL_PREC_BF16 && precision != NSL_PREC_F16)
-    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: batched network needs NSL_PREC_BF16 or NSL_PREC_F16");
+  if (precision != NSL_PREC_BF16 && precision != NSL_PREC_F16 && precision != NSL_PREC_FP8)
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: batched network needs NSL_PREC_BF16, F16 or FP8");
   size_t staged = 0, seg = 0, net = 0;
   std::vector<size_t> off_staged(n), off_seg(n), off_net(n);
   std::vector<int> maxseg(n);
@@ -258,7 +258,7 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
                                    b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
                                    per_sm * kNumSMs, b->counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: march");
-  const int elem = precision == NSL_PREC_BF16 ? 1 : 0;
+  const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
   if (!b->wtc[elem]) {
     if (b->capturing) return fail(NSL_ERR_INVALID_ARG, "nsl_batch: weights not built before capture");
     b->wtc[elem] = net_tc_create(b->params.data(), b->layout, elem, &e);
@@ -360,6 +360,7 @@ void nsl_batch_destroy(nsl_batch* b) {
   net_f32_destroy(b->wf);
   net_tc_destroy(b->wtc[0]);
   net_tc_destroy(b->wtc[1]);
+  net_tc_destroy(b->wtc[2]);
   cudaFree(b->staged);
   cudaFree(b->seg);
   cudaFree(b->net);

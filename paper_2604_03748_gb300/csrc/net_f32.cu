@@ -48,6 +48,7 @@ struct ConvArgs {
   void* out;          // NHWC [H][W][cout], float or bf16
   int H, W;           // output (= conv) size
   float depth_scale;
+  float* amax = nullptr;  // 16-bit output only: max of the stored values (FP8 path), or null
 };
 
 // Value of input channel c at conv-input pixel (y, x), already inside the image.
@@ -150,6 +151,22 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
     }
   }
   const int x = x0 + tx;
+  if constexpr (sizeof(TOut) == 2) {
+    // maximum of this tile's stored outputs (every thread of the warp takes part)
+    if (a.amax) {
+      float mx = 0.f;
+      const float* bias = a.b + cg * 16;
+      for (int r = 0; r < 2; ++r) {
+        if (x >= a.W || y0 + ty + r >= a.H) continue;
+        const float* acc = r ? acc1 : acc0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(acc[q] + __ldg(bias + q), 0.f));
+      }
+      mx = __half2float(__float2half_rn(mx));
+      const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      if ((threadIdx.x & 31) == 0 && bits) atomicMax(reinterpret_cast<unsigned int*>(a.amax), bits);
+    }
+  }
   if (x >= a.W) return;
   const float* bias = a.b + cg * 16;
 #pragma unroll
@@ -348,14 +365,14 @@ cudaError_t simt_first_conv_half(const NetF32Weights* w, const NetImage& img, T*
 }
 template <typename T>
 cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, T* const* outs,
-                                  int n, cudaStream_t s) {
+                                  float* const* amax, int n, cudaStream_t s) {
   if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
   ConvGroupArgs G{};
   G.nimg = n;
   int tiles = 0;
   for (int k = 0; k < n; ++k) {
     G.img[k] = ConvArgs{imgs[k].guide, nullptr, net_f32_conv_w(w, 0), net_f32_conv_b(w, 0), outs[k],
-                        imgs[k].H, imgs[k].W, imgs[k].depth_scale};
+                        imgs[k].H, imgs[k].W, imgs[k].depth_scale, amax ? amax[k] : nullptr};
     G.tile_start[k] = tiles;
     tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
   }
@@ -364,9 +381,10 @@ cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, 
   return cudaGetLastError();
 }
 template cudaError_t simt_first_conv_group<__nv_bfloat16>(const NetF32Weights*, const NetImage*,
-                                                          __nv_bfloat16* const*, int, cudaStream_t);
+                                                          __nv_bfloat16* const*, float* const*, int,
+                                                          cudaStream_t);
 template cudaError_t simt_first_conv_group<__half>(const NetF32Weights*, const NetImage*,
-                                                   __half* const*, int, cudaStream_t);
+                                                   __half* const*, float* const*, int, cudaStream_t);
 template cudaError_t simt_first_conv_half<__nv_bfloat16>(const NetF32Weights*, const NetImage&,
                                                          __nv_bfloat16*, cudaStream_t);
 template cudaError_t simt_first_conv_half<__half>(const NetF32Weights*, const NetImage&, __half*,

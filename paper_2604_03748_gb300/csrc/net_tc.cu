@@ -22,6 +22,7 @@
 //
 // Every wait on an mbarrier is bounded; on timeout the kernel records an error
 // code in a host-visible word, frees its TMEM and returns.
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -139,6 +140,17 @@ __device__ __forceinline__ void mma_f16kind(uint32_t d, uint64_t a, uint64_t b, 
       : "memory");
 }
 
+// kind::f8f6f4 with both operands FP8 E4M3 (format code 0 in the same
+// instruction-descriptor fields), FP32 accumulation; K = 32 per instruction.
+__device__ __forceinline__ void mma_f8kind(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -193,6 +205,72 @@ __device__ __forceinline__ uint4 ldg128(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// E4M3 code of a finite float, rounded to nearest with ties to even and
+// saturated at 448, from the format's definition (exponent bias 7, 3 fraction
+// bits, subnormal quantum 2^-9, S.1111.111 = NaN is never produced).  Written
+// out with integer operations so that ties, which power-of-two scaling of
+// FP16 values makes common, are broken exactly as the definition says.
+__device__ __forceinline__ uint32_t e4m3_rne(float v) {
+  const uint32_t bits = __float_as_uint(v);
+  const uint32_t sign = (bits >> 24) & 0x80u;
+  const uint32_t a = bits & 0x7fffffffu;
+  const int e = (int)(a >> 23) - 127;          // unbiased exponent of a normal float
+  if (e < -6) {
+    // E4M3 subnormal range: integer multiple of 2^-9, rounded to nearest even
+    const int m = __float2int_rn(__uint_as_float(a) * 512.0f);  // exact scaling
+    return sign | (uint32_t)m;                 // m = 8 is the code of 2^-6
+  }
+  uint32_t r = (a >> 20) & 7u;                 // top three fraction bits
+  const uint32_t rem = a & 0xfffffu, half = 0x80000u;
+  int E = e;
+  if (rem > half || (rem == half && (r & 1u))) {
+    if (++r == 8u) { r = 0u; ++E; }
+  }
+  if (E > 8 || (E == 8 && r == 7u)) return sign | 0x7eu;  // saturate at 448
+  return sign | ((uint32_t)(E + 7) << 3) | r;
+}
+
+// FP8 path: 16 FP16 activations (two 16-byte words, channel order) times the
+// tensor's inverse scale (a power of two), each rounded to nearest-even E4M3
+// with saturation; byte c of the result is channel c.
+__device__ __forceinline__ uint4 q8_pack16(uint4 lo, uint4 hi, float inv) {
+  const __half* h0 = reinterpret_cast<const __half*>(&lo);
+  const __half* h1 = reinterpret_cast<const __half*>(&hi);
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = 4 * q + c;
+      const float v = __fmul_rn(__half2float(i < 8 ? h0[i] : h1[i - 8]), inv);
+      acc |= e4m3_rne(v) << (8 * c);
+    }
+    w[q] = acc;
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Per-tensor activation scale: the smallest power of two s = 2^k with
+// amax <= 448 s (448 = 0.875 * 2^9, so with amax = f 2^e, f in [0.5, 1):
+// k = e - 9 if f <= 0.875, else e - 8); s = 1 for an all-zero tensor.
+// Quantising multiplies by 2^-k (exact), dequantising by 2^k.  A power of two
+// leaves every quantisation decision unchanged under tiny changes of amax.
+__device__ __forceinline__ int q8_exp(float amax) {
+  if (!(amax > 0.f)) return 0;
+  int e;
+  const float f = frexpf(amax, &e);
+  return e - 9 + (f > 0.875f ? 1 : 0);
+}
+__device__ __forceinline__ float q8_inv(float amax) { return ldexpf(1.f, -q8_exp(amax)); }
+__device__ __forceinline__ float q8_deq(float amax) { return ldexpf(1.f, q8_exp(amax)); }
+
+// Warp-wide max of non-negative values folded into a tensor's amax word.
+__device__ __forceinline__ void amax_publish(float* slot, float v) {
+  const unsigned bits = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+  if ((threadIdx.x & 31) == 0 && bits) atomicMax(reinterpret_cast<unsigned int*>(slot), bits);
+}
+
 // 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
@@ -222,14 +300,20 @@ struct ConvImg {
   int H, W;                  // convolution (output) size
   int tiles_x;               // M tiles per row
   int tile_start;
+  // FP8 path: amax words of the input tensor (two for a concatenation) and of
+  // the output tensor (accumulated here)
+  const float* amax_a;
+  const float* amax_b;
+  float* amax_out;
 };
 
 template <typename T>
 struct TcConvArgs {
   ConvImg<T> img[kMaxGroup];
   int nimg, total_tiles;
-  const uint8_t* wpack;      // [n tiles][9 taps][CIN/16][NT rows x 32 bytes]
+  const uint8_t* wpack;      // [n tiles][9 taps][K steps][NT rows x 32 bytes]
   const float* bias;         // [COUT]
+  const float* wscale;       // FP8 path: per-output-channel weight scales [COUT]
   unsigned int* err;
 };
 
@@ -305,28 +389,86 @@ __device__ __forceinline__ void load_halo(const ConvImg<T>& a, int tile, uint8_t
   }
 }
 
-template <typename T, int NT>
+// FP8 path: stage the halo as planes of 16 E4M3 channels (CIN/16 planes),
+// quantising the FP16 activations with the input tensor's scale on the way.
+template <int CIN, int MODE>
+__device__ __forceinline__ void load_halo_q8(const ConvImg<__half>& a, int tile, uint8_t* halo) {
+  constexpr int GR = CIN / 16;
+  const float am = a.amax_b ? fmaxf(__ldg(a.amax_a), __ldg(a.amax_b)) : __ldg(a.amax_a);
+  const float inv = q8_inv(am);
+  const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
+  for (int e = threadIdx.x; e < kHaloPix * GR; e += blockDim.x) {
+    const int hp = e / GR, g = e % GR;
+    const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+      uint4 lo, hi;
+      if constexpr (MODE == TC_PLAIN) {
+        const __half* p = a.inA + ((size_t)y * a.W + x) * CIN + g * 16;
+        lo = ldg128(p);
+        hi = ldg128(p + 8);
+      } else if constexpr (MODE == TC_CONCAT) {
+        constexpr int CH = CIN / 2;
+        const __half* p = g < GR / 2 ? a.inA + ((size_t)y * a.W + x) * CH + g * 16
+                                     : a.inB + ((size_t)y * a.W + x) * CH + (g - GR / 2) * 16;
+        lo = ldg128(p);
+        hi = ldg128(p + 8);
+      } else {  // TC_POOL
+        const size_t W2 = 2 * (size_t)a.W;
+        const __half* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 16;
+        lo = half8_max<__half>(half8_max<__half>(ldg128(p), ldg128(p + CIN)),
+                               half8_max<__half>(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
+        hi = half8_max<__half>(half8_max<__half>(ldg128(p + 8), ldg128(p + CIN + 8)),
+                               half8_max<__half>(ldg128(p + W2 * CIN + 8), ldg128(p + W2 * CIN + CIN + 8)));
+      }
+      v = q8_pack16(lo, hi, inv);
+    }
+    *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = v;
+  }
+}
+
+template <typename T, int NT, bool Q8>
 __device__ __forceinline__ void conv_epilogue(const ConvImg<T>& a, const float* __restrict__ bias,
-                                              int tile, uint32_t tacc, int n0, int cout) {
+                                              const float* __restrict__ wscale, int tile,
+                                              uint32_t tacc, int n0, int cout) {
   const int warp = threadIdx.x >> 5;
   const int m = threadIdx.x;  // accumulator row = pixel of the patch
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
   const bool valid = y < a.H && x < a.W;
   T* dst = a.out + ((size_t)y * a.W + x) * cout + n0;
+  float deq = 1.f, mx = 0.f;
+  if constexpr (Q8)
+    deq = q8_deq(a.amax_b ? fmaxf(__ldg(a.amax_a), __ldg(a.amax_b)) : __ldg(a.amax_a));
 #pragma unroll
   for (int c = 0; c < NT; c += 16) {
     float v[16];
     tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c, v);
     __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      h[q] = Half<T>::pack(fmaxf(v[2 * q] + __ldg(bias + n0 + c + 2 * q), 0.f),
-                           fmaxf(v[2 * q + 1] + __ldg(bias + n0 + c + 2 * q + 1), 0.f));
+    for (int q = 0; q < 8; ++q) {
+      float r0, r1;
+      if constexpr (Q8) {
+        r0 = fmaxf(fmaf(v[2 * q], __fmul_rn(deq, __ldg(wscale + n0 + c + 2 * q)),
+                        __ldg(bias + n0 + c + 2 * q)), 0.f);
+        r1 = fmaxf(fmaf(v[2 * q + 1], __fmul_rn(deq, __ldg(wscale + n0 + c + 2 * q + 1)),
+                        __ldg(bias + n0 + c + 2 * q + 1)), 0.f);
+        mx = fmaxf(mx, fmaxf(r0, r1));
+      } else {
+        r0 = fmaxf(v[2 * q] + __ldg(bias + n0 + c + 2 * q), 0.f);
+        r1 = fmaxf(v[2 * q + 1] + __ldg(bias + n0 + c + 2 * q + 1), 0.f);
+      }
+      h[q] = Half<T>::pack(r0, r1);
+    }
     if (valid) {
       reinterpret_cast<uint4*>(dst + c)[0] = reinterpret_cast<const uint4*>(h)[0];
       reinterpret_cast<uint4*>(dst + c)[1] = reinterpret_cast<const uint4*>(h)[1];
     }
+  }
+  if constexpr (Q8) {
+    // the stored (FP16-rounded) maximum: rounding is monotonic
+    amax_publish(a.amax_out, valid ? __half2float(__float2half_rn(mx)) : 0.f);
   }
 }
 
@@ -336,11 +478,15 @@ __host__ __device__ constexpr int conv_nt(int cin, int cout) {
   return cin >= 128 ? 32 : (cout > 64 ? 64 : cout);
 }
 
-template <int CIN, int COUT, int NT>
+template <int CIN, int COUT, int NT, bool Q8 = false>
 struct ConvCfg {
-  static constexpr int G = CIN / 8;
-  static constexpr int KS = CIN / 16;                    // 16-channel K steps per tap
-  static constexpr int WBYTES = 9 * CIN * NT * 2;        // B operand of one N tile
+  // a plane holds 16 bytes per halo pixel: 8 FP16/BF16 channels or 16 FP8 ones;
+  // one MMA consumes two planes (K = 16 or 32).  FP8 with 16 channels stages
+  // a zero second plane.
+  static constexpr int GR = Q8 ? CIN / 16 : CIN / 8;     // planes holding channels
+  static constexpr int G = GR < 2 ? 2 : GR;              // planes staged
+  static constexpr int KS = G / 2;                       // K steps per tap
+  static constexpr int WBYTES = 9 * KS * NT * 32;        // B operand of one N tile
   static constexpr int HBYTES = G * kPlane;              // one halo buffer
   // halo buffers in flight: as many as fit next to the weights (2..4)
   static constexpr int STAGES =
@@ -349,9 +495,9 @@ struct ConvCfg {
   static constexpr int SMEM = WBYTES + STAGES * HBYTES + 64;  // + barriers and TMEM slot
 };
 
-template <typename T, int CIN, int COUT, int NT, int MODE>
+template <typename T, int CIN, int COUT, int NT, int MODE, bool Q8>
 __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
-  using Cfg = ConvCfg<CIN, COUT, NT>;
+  using Cfg = ConvCfg<CIN, COUT, NT, Q8>;
   constexpr int S = Cfg::STAGES;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* wsm = smem;
@@ -384,11 +530,20 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       bulk_g2s(wsm + off, src + off, (uint32_t)n, &bars[0]);
     }
   }
+  if constexpr (Q8 && Cfg::GR < Cfg::G) {
+    // FP8 with 16 input channels: the second plane of every halo buffer is zero
+    for (int e = tid; e < S * kPlane / 16; e += blockDim.x)
+      *reinterpret_cast<uint4*>(halo + (e / (kPlane / 16)) * Cfg::HBYTES + kPlane + (e % (kPlane / 16)) * 16) =
+          make_uint4(0, 0, 0, 0);
+  }
   // prefetch the first S-1 halos while the weights arrive
   auto issue = [&](int k) {
     if (k < nmine) {
       const int t = blockIdx.x + k * gridDim.x, im = image_of(a, t);
-      load_halo_async<T, CIN, MODE>(a.img[im], t - a.img[im].tile_start, halo + (k % S) * Cfg::HBYTES);
+      if constexpr (Q8)
+        load_halo_q8<CIN, MODE>(a.img[im], t - a.img[im].tile_start, halo + (k % S) * Cfg::HBYTES);
+      else
+        load_halo_async<T, CIN, MODE>(a.img[im], t - a.img[im].tile_start, halo + (k % S) * Cfg::HBYTES);
     }
     cp_async_commit();  // one group per k, possibly empty, keeps the group count uniform
   };
@@ -397,7 +552,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 1u);
 
-  constexpr uint32_t idesc = idesc_f16kind(Half<T>::kFmt, 128, NT);
+  // E4M3 has format code 0 in the f8f6f4 descriptor, like FP16 in the f16 one
+  constexpr uint32_t idesc = idesc_f16kind(Q8 ? 0u : Half<T>::kFmt, 128, NT);
   uint32_t phase[2] = {0u, 0u};
 #pragma unroll 1
   for (int k = 0; ok && k < nmine; ++k) {
@@ -418,7 +574,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
         for (int j = 0; j < Cfg::KS; ++j, ++kk) {
           const uint64_t ad = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
           const uint64_t bd = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
-          mma_f16kind(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          if constexpr (Q8) mma_f8kind(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          else mma_f16kind(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
         }
       }
       mma_commit(&bars[1 + acc]);
@@ -433,8 +590,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       phase[pacc] ^= 1u;
       tc_fence_after();
       const int t = blockIdx.x + (k - 1) * gridDim.x, im = image_of(a, t);
-      conv_epilogue<T, NT>(a.img[im], a.bias, t - a.img[im].tile_start,
-                           tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
+                               tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
     }
     // the buffer of tile k-1 is free again (its MMAs completed): refill it
     issue(k + S - 1);
@@ -446,8 +603,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
     } else {
       tc_fence_after();
       const int t = blockIdx.x + (nmine - 1) * gridDim.x, im = image_of(a, t);
-      conv_epilogue<T, NT>(a.img[im], a.bias, t - a.img[im].tile_start,
-                           tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
+                               tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
     }
   }
   cp_async_wait<0>();
@@ -466,32 +623,36 @@ struct ConvTImg {
   const T* in;               // NHWC [H][W][CIN]
   T* out;                    // NHWC [2H][2W][COUT]
   int H, W, tiles_x, tile_start;
+  const float* amax_in;      // FP8 path: amax words of input and output
+  float* amax_out;
 };
 
 template <typename T>
 struct TcConvTArgs {
   ConvTImg<T> img[kMaxGroup];
   int nimg, total_tiles;
-  const uint8_t* wpack;      // [CIN/16][N rows x 32 bytes]
+  const uint8_t* wpack;      // [K steps][N rows x 32 bytes]
   const float* bias;         // [COUT]
+  const float* wscale;       // FP8 path: per-output-channel weight scales [COUT]
   unsigned int* err;
 };
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool Q8 = false>
 struct ConvTCfg {
   static constexpr int N = 4 * COUT;
-  static constexpr int G = CIN / 8;
+  static constexpr int G = Q8 ? CIN / 16 : CIN / 8;     // 16-byte planes (CIN >= 32)
   static constexpr int APLANE = 128 * 16;
-  static constexpr int WBYTES = CIN * N * 2;
+  static constexpr int WBYTES = (G / 2) * N * 32;
   static constexpr int ABYTES = G * APLANE;
   static constexpr int TMEM_COLS = 2 * N > 512 ? 512 : (2 * N < 32 ? 32 : 2 * N);
   static constexpr int NBUF = 2 * N > 512 ? 1 : 2;
   static constexpr int SMEM = WBYTES + 2 * ABYTES + 64;
 };
 
-template <typename T, int CIN, int COUT>
+template <typename T, int CIN, int COUT, bool Q8>
 __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
-  using Cfg = ConvTCfg<CIN, COUT>;
+  using Cfg = ConvTCfg<CIN, COUT, Q8>;
+  static_assert(!Q8 || CIN >= 32, "FP8 transposed convolution needs K >= 32");
   constexpr int N = Cfg::N;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* wsm = smem;
@@ -522,7 +683,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 4u);
 
-  constexpr uint32_t idesc = idesc_f16kind(Half<T>::kFmt, 128, N);
+  constexpr uint32_t idesc = idesc_f16kind(Q8 ? 0u : Half<T>::kFmt, 128, N);
   uint32_t phase[2] = {0u, 0u};
   int buf = 0, prev = -1, prevbuf = 0;
 
@@ -535,6 +696,8 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
     const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
     const bool valid = y < im.H && x < im.W;
     const uint32_t tacc = tmem + (uint32_t)(b * N) + ((uint32_t)(warp * 32) << 16);
+    float deq = 1.f, mx = 0.f;
+    if constexpr (Q8) deq = q8_deq(__ldg(im.amax_in));
 #pragma unroll 1
     for (int c = 0; c < N; c += 16) {
       float v[16];
@@ -543,15 +706,26 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
       const int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
       __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        h[q] = Half<T>::pack(v[2 * q] + __ldg(a.bias + co + 2 * q),
-                             v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1));
+      for (int q = 0; q < 8; ++q) {
+        float r0, r1;
+        if constexpr (Q8) {
+          r0 = fmaf(v[2 * q], __fmul_rn(deq, __ldg(a.wscale + co + 2 * q)), __ldg(a.bias + co + 2 * q));
+          r1 = fmaf(v[2 * q + 1], __fmul_rn(deq, __ldg(a.wscale + co + 2 * q + 1)),
+                    __ldg(a.bias + co + 2 * q + 1));
+          mx = fmaxf(mx, fmaxf(fabsf(r0), fabsf(r1)));
+        } else {
+          r0 = v[2 * q] + __ldg(a.bias + co + 2 * q);
+          r1 = v[2 * q + 1] + __ldg(a.bias + co + 2 * q + 1);
+        }
+        h[q] = Half<T>::pack(r0, r1);
+      }
       if (valid) {
         T* dst = im.out + ((size_t)oy * (2 * im.W) + ox) * COUT + co;
         reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(h)[0];
         reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
       }
     }
+    if constexpr (Q8) amax_publish(im.amax_out, valid ? __half2float(__float2half_rn(mx)) : 0.f);
   };
 
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -562,11 +736,20 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
       const int lt = tile - im.tile_start;
       const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
       uint8_t* dstb = abuf + buf * Cfg::ABYTES;
+      float inv = 1.f;
+      if constexpr (Q8) inv = q8_inv(__ldg(im.amax_in));
       for (int e = tid; e < 128 * Cfg::G; e += blockDim.x) {
         const int m = e / Cfg::G, g = e % Cfg::G;
         const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (y < im.H && x < im.W) v = ldg128(im.in + ((size_t)y * im.W + x) * CIN + g * 8);
+        if (y < im.H && x < im.W) {
+          if constexpr (Q8) {
+            const T* p = im.in + ((size_t)y * im.W + x) * CIN + g * 16;
+            v = q8_pack16(ldg128(p), ldg128(p + 8), inv);
+          } else {
+            v = ldg128(im.in + ((size_t)y * im.W + x) * CIN + g * 8);
+          }
+        }
         *reinterpret_cast<uint4*>(dstb + g * Cfg::APLANE + m * 16) = v;
       }
     }
@@ -588,10 +771,11 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
       const uint32_t ab = smem_u32(abuf + buf * Cfg::ABYTES), wb = smem_u32(wsm);
       const uint32_t d = tmem + (uint32_t)((Cfg::NBUF == 2 ? buf : 0) * N);
 #pragma unroll
-      for (int j = 0; j < CIN / 16; ++j) {
+      for (int j = 0; j < Cfg::G / 2; ++j) {
         const uint64_t ad = smem_desc(ab + (uint32_t)(2 * j * Cfg::APLANE), Cfg::APLANE, 128);
         const uint64_t bd = smem_desc(wb + (uint32_t)(j * N * 32), N * 16, 128);
-        mma_f16kind(d, ad, bd, idesc, j > 0 ? 1u : 0u);
+        if constexpr (Q8) mma_f8kind(d, ad, bd, idesc, j > 0 ? 1u : 0u);
+        else mma_f16kind(d, ad, bd, idesc, j > 0 ? 1u : 0u);
       }
       mma_commit(&bars[1 + (Cfg::NBUF == 2 ? buf : 0)]);
     }
@@ -695,15 +879,95 @@ static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& 
   }
 }
 
+// Nearest-even E4M3 code of a float with saturation to the largest finite
+// magnitude (448): exponent bias 7, 3 fraction bits, subnormal quantum 2^-9,
+// S.1111.111 reserved for NaN.
+static uint8_t e4m3_code(float v) {
+  const uint8_t sign = std::signbit(v) ? 0x80 : 0x00;
+  const double a = std::fabs((double)v);
+  if (a == 0.0) return sign;
+  int e;
+  std::frexp(a, &e);
+  int E = e - 1;                                  // a in [2^E, 2^(E+1))
+  if (E < -6) E = -6;
+  double r = std::nearbyint(a / std::ldexp(1.0, E - 3));  // in [0, 16]
+  if (r >= 16.0) { r = 8.0; ++E; }
+  int field, mant;
+  if (r < 8.0) { field = 0; mant = (int)r; }      // subnormal (only when E = -6)
+  else { field = E + 7; mant = (int)r - 8; }
+  if (field > 15 || (field == 15 && mant == 7)) { field = 15; mant = 6; }  // saturate at 448
+  return (uint8_t)(sign | (field << 3) | mant);
+}
+
+// Per-output-channel scale (max |w| / 448 in binary32; 1 for an all-zero
+// channel) and the codes of w / scale.
+static float channel_scale(const float* w, int count, long stride) {
+  float amax = 0.f;
+  for (int j = 0; j < count; ++j) amax = std::fmax(amax, std::fabs(w[(long)j * stride]));
+  return amax > 0.f ? amax / 448.0f : 1.0f;
+}
+
+// FP8 packing of a 3x3 conv weight [cout][cin][3][3]: per (N tile, tap, K step
+// of 32 channels) a slice of NT rows x 32 bytes, K core matrix k/16 at
+// NT*16 bytes, rows grouped by 8 (128 bytes); channels >= cin are zero.
+static void pack_conv_q8(const float* w, int cin, int cout, int NT, std::vector<uint8_t>& out,
+                         std::vector<float>& scale) {
+  const int KS = cin < 32 ? 1 : cin / 32;
+  const size_t slice = (size_t)NT * 32;
+  out.assign((size_t)(cout / NT) * 9 * KS * slice, 0);
+  scale.resize(cout);
+  for (int co = 0; co < cout; ++co) scale[co] = channel_scale(w + (size_t)co * cin * 9, cin * 9, 1);
+  for (int nt = 0; nt < cout / NT; ++nt)
+    for (int tap = 0; tap < 9; ++tap)
+      for (int j = 0; j < KS; ++j) {
+        uint8_t* s = out.data() + (((size_t)nt * 9 + tap) * KS + j) * slice;
+        for (int n = 0; n < NT; ++n)
+          for (int k = 0; k < 32; ++k) {
+            const int co = nt * NT + n, ci = j * 32 + k;
+            if (ci >= cin) continue;
+            const float v = w[((size_t)co * cin + ci) * 9 + tap] / scale[co];
+            s[(size_t)(k / 16) * NT * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 16)] = e4m3_code(v);
+          }
+      }
+}
+
+// FP8 packing of a transposed-conv weight [cin][cout][2][2]: rows
+// n = (2a+b)*cout + co, K = cin in steps of 32; scale per output channel over
+// ci and the four kernel positions.
+static void pack_convT_q8(const float* w, int cin, int cout, std::vector<uint8_t>& out,
+                          std::vector<float>& scale) {
+  const int N = 4 * cout;
+  const size_t slice = (size_t)N * 32;
+  out.assign((size_t)(cin / 32) * slice, 0);
+  scale.resize(cout);
+  for (int co = 0; co < cout; ++co) {
+    float amax = 0.f;
+    for (int ci = 0; ci < cin; ++ci)
+      for (int k = 0; k < 4; ++k) amax = std::fmax(amax, std::fabs(w[((size_t)ci * cout + co) * 4 + k]));
+    scale[co] = amax > 0.f ? amax / 448.0f : 1.0f;
+  }
+  for (int j = 0; j < cin / 32; ++j) {
+    uint8_t* s = out.data() + j * slice;
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < 32; ++k) {
+        const int kpos = n / cout, co = n % cout, ci = j * 32 + k;
+        const float v = w[((size_t)ci * cout + co) * 4 + kpos] / scale[co];
+        s[(size_t)(k / 16) * N * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 16)] = e4m3_code(v);
+      }
+  }
+}
+
 }  // namespace
 
 struct NetTcWeights {
-  int elem = 0;              // 0 FP16 operands, 1 BF16 operands
+  int elem = 0;              // 0 FP16 operands, 1 BF16 operands, 2 FP8 E4M3 operands
   uint8_t* conv_w[14] = {};  // layer 0 stays on the SIMT path
   float* conv_b[14] = {};
+  float* conv_s[14] = {};    // FP8: per-output-channel weight scales
   int conv_nt[14] = {};
   uint8_t* up_w[3] = {};
   float* up_b[3] = {};
+  float* up_s[3] = {};
   std::vector<void*> allocs;
 };
 
@@ -736,11 +1000,32 @@ static void fill_weights(NetTcWeights* w, const float* hp, const NetLayout& L, c
   }
 }
 
+static void fill_weights_q8(NetTcWeights* w, const float* hp, const NetLayout& L, cudaError_t* err) {
+  std::vector<uint8_t> pk;
+  std::vector<float> sc;
+  for (int l = 1; l < 14; ++l) {
+    const int cin = L.conv_cin[l], cout = L.conv_cout[l];
+    const int NT = conv_nt(cin, cout);
+    w->conv_nt[l] = NT;
+    pack_conv_q8(hp + L.conv_w[l], cin, cout, NT, pk, sc);
+    w->conv_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->conv_s[l] = dev_copy(w, sc.data(), sc.size(), err);
+    w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
+  }
+  for (int l = 0; l < 3; ++l) {
+    pack_convT_q8(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk, sc);
+    w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->up_s[l] = dev_copy(w, sc.data(), sc.size(), err);
+    w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
+  }
+}
+
 NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, int elem, cudaError_t* err) {
   *err = cudaSuccess;
   NetTcWeights* w = new NetTcWeights();
   w->elem = elem;
-  if (elem == 1) fill_weights<__nv_bfloat16>(w, hp, L, err);
+  if (elem == 2) fill_weights_q8(w, hp, L, err);
+  else if (elem == 1) fill_weights<__nv_bfloat16>(w, hp, L, err);
   else fill_weights<__half>(w, hp, L, err);
   if (*err != cudaSuccess) { net_tc_destroy(w); return nullptr; }
   return w;
@@ -757,7 +1042,9 @@ template <typename T>
 struct TcBuffers {
   T *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1;
   float *partial, *att;
+  float* amax;               // FP8 path: [kMaxGroup][kAmaxSlots] tensor maxima (first image's region)
 };
+constexpr int kAmaxSlots = 32;
 
 template <typename T>
 size_t carve_tc(size_t P, size_t partial_floats, TcBuffers<T>* b, char* base) {
@@ -775,6 +1062,7 @@ size_t carve_tc(size_t P, size_t partial_floats, TcBuffers<T>* b, char* base) {
   b->x1 = hf(P * 64);
   b->partial = reinterpret_cast<float*>(take(partial_floats * 4));
   b->att = reinterpret_cast<float*>(take(64 * 4));
+  b->amax = reinterpret_cast<float*>(take((size_t)kMaxGroup * kAmaxSlots * 4));
   return off;
 }
 
@@ -782,17 +1070,25 @@ int g_conv_ctas_per_sm = kConvCtasPerSM;
 
 // One grouped layer launch: `ins`, `skips`, `outs` hold each image's buffers,
 // `H`, `W` each image's convolution size.
-template <typename T, int CIN, int COUT, int MODE>
+// FP8 tensor-maximum slots (per image): 0 = first conv output, l = conv l
+// output (1..13), 14 + j = transposed conv j output.
+struct AmaxSlots {
+  float* base = nullptr;     // [n][kAmaxSlots], null outside the FP8 path
+  int a = -1, b = -1, out = -1;
+};
+
+template <typename T, int CIN, int COUT, int MODE, bool Q8>
 cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, const T* const* skips,
-                     T* const* outs, const int* H, const int* W, unsigned int* err, cudaStream_t s) {
+                     T* const* outs, const int* H, const int* W, AmaxSlots am, unsigned int* err,
+                     cudaStream_t s) {
   constexpr int NT = conv_nt(CIN, COUT);
-  using Cfg = ConvCfg<CIN, COUT, NT>;
+  using Cfg = ConvCfg<CIN, COUT, NT, Q8>;
   static_assert(Cfg::SMEM <= 232448, "shared memory budget");
   static Launch L;
   static bool init = false;
   if (!init) {
     cudaError_t e =
-        configure(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+        configure(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
     if (e != cudaSuccess) return e;
     init = true;
   }
@@ -801,12 +1097,16 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   int ntiles = 0;
   for (int k = 0; k < n; ++k) {
     const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
-    a.img[k] = ConvImg<T>{ins[k], skips ? skips[k] : nullptr, outs[k], H[k], W[k], tx, ntiles};
+    float* ab = am.base ? am.base + (size_t)k * kAmaxSlots : nullptr;
+    a.img[k] = ConvImg<T>{ins[k], skips ? skips[k] : nullptr, outs[k], H[k], W[k], tx, ntiles,
+                          ab ? ab + am.a : nullptr, (ab && am.b >= 0) ? ab + am.b : nullptr,
+                          ab ? ab + am.out : nullptr};
     ntiles += tx * ty;
   }
   a.total_tiles = ntiles;
   a.wpack = w->conv_w[l];
   a.bias = w->conv_b[l];
+  a.wscale = w->conv_s[l];
   a.err = err;
   // enough CTAs to cover every SM, each pipelining >= 4 tiles when there are
   // that many; per-SM residency is capped by the tunable CTAs-per-SM
@@ -816,18 +1116,18 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  conv3x3_tc_kernel<T, CIN, COUT, NT, MODE><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
+  conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int CIN, int COUT>
+template <typename T, int CIN, int COUT, bool Q8>
 cudaError_t run_convT(const NetTcWeights* w, int l, int n, const T* const* ins, T* const* outs,
-                      const int* H, const int* W, unsigned int* err, cudaStream_t s) {
-  using Cfg = ConvTCfg<CIN, COUT>;
+                      const int* H, const int* W, AmaxSlots am, unsigned int* err, cudaStream_t s) {
+  using Cfg = ConvTCfg<CIN, COUT, Q8>;
   static Launch L;
   static bool init = false;
   if (!init) {
-    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT, Q8>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
     if (e != cudaSuccess) return e;
     init = true;
   }
@@ -836,20 +1136,23 @@ cudaError_t run_convT(const NetTcWeights* w, int l, int n, const T* const* ins, 
   int ntiles = 0;
   for (int k = 0; k < n; ++k) {
     const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
-    a.img[k] = ConvTImg<T>{ins[k], outs[k], H[k], W[k], tx, ntiles};
+    float* ab = am.base ? am.base + (size_t)k * kAmaxSlots : nullptr;
+    a.img[k] = ConvTImg<T>{ins[k], outs[k], H[k], W[k], tx, ntiles, ab ? ab + am.a : nullptr,
+                           ab ? ab + am.out : nullptr};
     ntiles += tx * ty;
   }
   a.total_tiles = ntiles;
   a.wpack = w->up_w[l];
   a.bias = w->up_b[l];
+  a.wscale = w->up_s[l];
   a.err = err;
   int grid = kNumSMs * L.per_sm;
   if (grid > ntiles) grid = ntiles;
-  convT_tc_kernel<T, CIN, COUT><<<grid, 128, L.smem, s>>>(a);
+  convT_tc_kernel<T, CIN, COUT, Q8><<<grid, 128, L.smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool Q8>
 cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs,
                     void* const* ws, int n, unsigned int* err, cudaStream_t s) {
   if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
@@ -868,26 +1171,41 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
   const T* sk[kMaxGroup];
   T* out[kMaxGroup];
   cudaError_t e;
+  // FP8: every image's tensor maxima live in the first image's workspace,
+  // cleared once per forward
+  float* amax = Q8 ? B[0].amax : nullptr;
+  if (Q8 && (e = cudaMemsetAsync(amax, 0, (size_t)n * kAmaxSlots * sizeof(float), s)) != cudaSuccess)
+    return e;
+  auto slots = [&](int ia, int ib, int io) {
+    AmaxSlots m;
+    m.base = amax;
+    m.a = ia;
+    m.b = ib;
+    m.out = io;
+    return m;
+  };
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
 #define SET(IN, SKIP, OUT) for (int k = 0; k < n; ++k) { in[k] = B[k].IN; sk[k] = SKIP; out[k] = B[k].OUT; }
   for (int k = 0; k < n; ++k) out[k] = B[k].fa;
-  TRY(simt_first_conv_group<T>(wf, imgs, out, n, s));
-  SET(fa, nullptr, s1);  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
-  SET(s1, nullptr, l1a); TRY((run_conv<T, 16, 32, TC_POOL>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
-  SET(l1a, nullptr, s2); TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
-  SET(s2, nullptr, l2a); TRY((run_conv<T, 32, 64, TC_POOL>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
-  SET(l2a, nullptr, s3); TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
-  SET(s3, nullptr, l3a); TRY((run_conv<T, 64, 128, TC_POOL>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
-  SET(l3a, nullptr, l3b); TRY((run_conv<T, 128, 128, TC_PLAIN>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
-  SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64>(w, 0, n, in, out, Hs[3], Ws[3], err, s)));
-  SET(l2a, B[k].s3, l2b); TRY((run_conv<T, 128, 64, TC_CONCAT>(w, 8, n, in, sk, out, Hs[2], Ws[2], err, s)));
-  SET(l2b, nullptr, l2a); TRY((run_conv<T, 64, 64, TC_PLAIN>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
-  SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32>(w, 1, n, in, out, Hs[2], Ws[2], err, s)));
-  SET(l1a, B[k].s2, l1b); TRY((run_conv<T, 64, 32, TC_CONCAT>(w, 10, n, in, sk, out, Hs[1], Ws[1], err, s)));
-  SET(l1b, nullptr, l1a); TRY((run_conv<T, 32, 32, TC_PLAIN>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
-  SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16>(w, 2, n, in, out, Hs[1], Ws[1], err, s)));
-  SET(fa, B[k].s1, fb);  TRY((run_conv<T, 32, 16, TC_CONCAT>(w, 12, n, in, sk, out, Hs[0], Ws[0], err, s)));
-  SET(fb, nullptr, fa);  TRY((run_conv<T, 16, 16, TC_PLAIN>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  float* first_amax[kMaxGroup];
+  for (int k = 0; k < n; ++k) first_amax[k] = Q8 ? amax + (size_t)k * kAmaxSlots : nullptr;
+  TRY(simt_first_conv_group<T>(wf, imgs, out, Q8 ? first_amax : nullptr, n, s));
+  SET(fa, nullptr, s1);  TRY((run_conv<T, 16, 16, TC_PLAIN, Q8>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], slots(0, -1, 1), err, s)));
+  SET(s1, nullptr, l1a); TRY((run_conv<T, 16, 32, TC_POOL, Q8>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], slots(1, -1, 2), err, s)));
+  SET(l1a, nullptr, s2); TRY((run_conv<T, 32, 32, TC_PLAIN, Q8>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], slots(2, -1, 3), err, s)));
+  SET(s2, nullptr, l2a); TRY((run_conv<T, 32, 64, TC_POOL, Q8>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], slots(3, -1, 4), err, s)));
+  SET(l2a, nullptr, s3); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], slots(4, -1, 5), err, s)));
+  SET(s3, nullptr, l3a); TRY((run_conv<T, 64, 128, TC_POOL, Q8>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], slots(5, -1, 6), err, s)));
+  SET(l3a, nullptr, l3b); TRY((run_conv<T, 128, 128, TC_PLAIN, Q8>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], slots(6, -1, 7), err, s)));
+  SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64, Q8>(w, 0, n, in, out, Hs[3], Ws[3], slots(7, -1, 14), err, s)));
+  SET(l2a, B[k].s3, l2b); TRY((run_conv<T, 128, 64, TC_CONCAT, Q8>(w, 8, n, in, sk, out, Hs[2], Ws[2], slots(14, 5, 8), err, s)));
+  SET(l2b, nullptr, l2a); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], slots(8, -1, 9), err, s)));
+  SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32, Q8>(w, 1, n, in, out, Hs[2], Ws[2], slots(9, -1, 15), err, s)));
+  SET(l1a, B[k].s2, l1b); TRY((run_conv<T, 64, 32, TC_CONCAT, Q8>(w, 10, n, in, sk, out, Hs[1], Ws[1], slots(15, 3, 10), err, s)));
+  SET(l1b, nullptr, l1a); TRY((run_conv<T, 32, 32, TC_PLAIN, Q8>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], slots(10, -1, 11), err, s)));
+  SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16, Q8>(w, 2, n, in, out, Hs[1], Ws[1], slots(11, -1, 16), err, s)));
+  SET(fa, B[k].s1, fb);  TRY((run_conv<T, 32, 16, TC_CONCAT, Q8>(w, 12, n, in, sk, out, Hs[0], Ws[0], slots(16, 1, 12), err, s)));
+  SET(fb, nullptr, fa);  TRY((run_conv<T, 16, 16, TC_PLAIN, Q8>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], slots(12, -1, 13), err, s)));
   AdapterImg<T> ai[kMaxGroup];
   for (int k = 0; k < n; ++k)
     ai[k] = AdapterImg<T>{B[k].fa, B[k].x1, B[k].partial, B[k].att, imgs[k].out, imgs[k].H, imgs[k].W};
@@ -913,8 +1231,9 @@ cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const
 cudaError_t net_tc_forward_group(const NetTcWeights* w, const NetF32Weights* wf,
                                  const NetImage* imgs, void* const* ws, int n, unsigned int* err,
                                  cudaStream_t s) {
-  if (w->elem == 1) return forward<__nv_bfloat16>(w, wf, imgs, ws, n, err, s);
-  return forward<__half>(w, wf, imgs, ws, n, err, s);
+  if (w->elem == 2) return forward<__half, true>(w, wf, imgs, ws, n, err, s);
+  if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, imgs, ws, n, err, s);
+  return forward<__half, false>(w, wf, imgs, ws, n, err, s);
 }
 
 void net_tc_set_ctas_per_sm(int v) { g_conv_ctas_per_sm = v < 1 ? 1 : (v > 4 ? 4 : v); }

@@ -232,13 +232,17 @@ struct AdapterImg {
 template <typename TA>
 cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
                                cudaStream_t s);
+// amax (nullable): per image, where the maximum of the stored outputs is
+// accumulated (FP8 path)
 template <typename T>
 cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, T* const* outs,
-                                  int n, cudaStream_t s);
+                                  float* const* amax, int n, cudaStream_t s);
 const AdapterParamSet& net_f32_adapter_params(const NetF32Weights* w);
 
-// tensor-core (tcgen05) network, 16-bit operands (elem 0 = FP16, 1 = BF16),
-// FP32 accumulation in TMEM
+// tensor-core (tcgen05) network: elem 0 = FP16 and 1 = BF16 operands
+// (kind::f16), 2 = FP8 E4M3 operands (kind::f8f6f4) with per-tensor activation
+// and per-output-channel weight scales; FP32 accumulation in TMEM, FP16
+// activations between layers in the FP8 case
 struct NetTcWeights;
 NetTcWeights* net_tc_create(const float* host_params, const NetLayout& L, int elem,
                             cudaError_t* err);

@@ -395,8 +395,8 @@ nsl_status nsl_server_create(const void* blob, size_t blob_bytes, const nsl_serv
   nsl_default_server_opts(&o);
   if (opts) o = *opts;
   if (o.streams < 1 || o.streams > 4 || o.max_batch < 1 || o.max_batch > kMaxGroup ||
-      (o.precision != NSL_PREC_F16 && o.precision != NSL_PREC_BF16))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_server_create: streams 1..4, max_batch 1..%d, precision F16/BF16",
+      (o.precision != NSL_PREC_F16 && o.precision != NSL_PREC_BF16 && o.precision != NSL_PREC_FP8))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_server_create: streams 1..4, max_batch 1..%d, precision F16/BF16/FP8",
                 kMaxGroup);
   if (!o.scratch_bytes_per_stream) o.scratch_bytes_per_stream = o.hbm_budget_bytes / 8;
   if (o.scratch_bytes_per_stream * o.streams >= o.hbm_budget_bytes)

