@@ -352,8 +352,9 @@ def bench_animated(nsl, I, dev, args, with_oracle):
     """Animated form: 300 frames of a 256^3 FP16 plume advected along a seeded
     curl-noise velocity (generated on the GPU before timing), camera on a
     seeded spline, light turning 1 degree per frame; 1024x1024 billboard, step
-    4 voxels.  Every frame stages its own grid, marches the guide, runs the
-    network and shades, timed with CUDA events per frame."""
+    4 voxels, FP8 network (and FP16 beside it).  Every frame stages its own
+    grid, marches the guide, runs the network and shades, timed with CUDA
+    events per frame."""
     import torch
     t0 = time.perf_counter()
     seq = I.animated_sequence(256, 300, seed=3, width=1024, height=1024, step=4.0, device=dev)
@@ -369,7 +370,7 @@ def bench_animated(nsl, I, dev, args, with_oracle):
     out = {"workload": "256^3 f16 plume, 300 frames (curl-noise advection, seed 3), perspective 1024x1024 "
                        "on a spline, light turning 1 deg/frame, step 4 voxels",
            "generation_s": gen_s, "frames": 300}
-    for name, prec in (("f16", nsl.NSL_PREC_F16), ("bf16", nsl.NSL_PREC_BF16)):
+    for name, prec in (("fp8", nsl.NSL_PREC_FP8), ("f16", nsl.NSL_PREC_F16)):
         def frame(t, evs=None):
             if evs:
                 evs[0].record(stream)
