@@ -445,6 +445,28 @@ cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>*
   adapters_pass2_group<TA><<<blocks, 128, 0, s>>>(G, prm.p2);
   return cudaGetLastError();
 }
+template <typename TA>
+cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
+                                       cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  AdapterGroupArgs<TA> G{};
+  G.nimg = n;
+  int tiles = 0;
+  for (int k = 0; k < n; ++k) {
+    G.img[k] = imgs[k];
+    G.tile_start[k] = tiles;
+    tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
+  }
+  G.tile_start[n] = tiles;
+  adapters_reduce_group<TA><<<n, 1024, 0, s>>>(G, prm.sca);
+  return cudaGetLastError();
+}
+template cudaError_t adapters_reduce_only_group<__half>(const AdapterParamSet&, const AdapterImg<__half>*,
+                                                        int, cudaStream_t);
+template cudaError_t adapters_reduce_only_group<__nv_bfloat16>(const AdapterParamSet&,
+                                                               const AdapterImg<__nv_bfloat16>*, int,
+                                                               cudaStream_t);
+
 template cudaError_t adapters_run_group<__nv_bfloat16>(const AdapterParamSet&,
                                                        const AdapterImg<__nv_bfloat16>*, int,
                                                        cudaStream_t);

@@ -1,0 +1,604 @@
+// The four NAFBlock channel adapters (Sec. 4.3, Fig. 3) with their 1x1
+// convolutions on the tensor cores (tcgen05 kind::f16, FP16 operands, FP32
+// accumulation in TMEM); used by the tensor-core network paths.
+//
+// Pass 1, per 16x8 tile (persistent CTAs of 256 threads): the 18x10 halo of F
+// is normalised (LayerNorm without its affine, which is folded into pw1) into
+// FP16 A planes (rows = halo pixels, padded to two M = 128 tiles); in two
+// rounds of two adapters, one MMA per M tile applies their pw1 (N = 2 x 32,
+// K = 16), the accumulators go to shared memory (zero outside the image: the
+// depthwise convolution pads its input with zeros), and the SIMT cores run the
+// depthwise 3x3 and the simple gate, each thread one 8-pixel column for two
+// gated channels, writing x1 and the tile's per-channel sums.
+// Pass 2, per 128 pixels: four chained MMAs with block-diagonal weights (the
+// four adapters side by side): pw2 on att * x1 (K = 64, N = 64), ffn1 on
+// LN2(y) (N = 128), ffn2 on the gate (N = 64), the heads on z (N = 16, eight
+// used); between them each thread handles its pixel's row.
+// The SCA reduction between the passes is the deterministic SIMT one.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "nsl_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace nsl {
+
+namespace {
+
+constexpr int C = kC0;                  // 16 channels per adapter
+constexpr int kTW = 16, kTH = 8;        // pass-1 tile: same tiling as the SIMT pass 1
+constexpr int kHW = kTW + 2, kHH = kTH + 2;
+constexpr int kHalo = kHW * kHH;        // 180
+constexpr int kRows = 256;              // A rows: halo pixels padded to 2 x 128
+constexpr int kChS = 184;               // floats per channel of the pw1 buffer (the two
+                                        // half-warps of a warp, two channels apart, land 16 banks apart)
+
+// pass-1 shared memory (bytes); pw1 runs in two rounds of two adapters (N = 64)
+constexpr int kP1Threads = 256;
+constexpr int kP1A = 0;                                   // 2 planes x 256 rows x 16 B
+constexpr int kP1B = kP1A + 2 * kRows * 16;               // pw1 B operand, 128 x 32 B
+constexpr int kP1Pw = kP1B + 128 * 32;                    // pw1 output of one round [64][kChS] f32
+constexpr int kP1Dw = kP1Pw + 64 * kChS * 4;              // pw1 bias [128] + dw weights [128][9] + dw bias [128]
+constexpr int kP1In = kP1Dw + (128 * 9 + 128 + 128) * 4;  // inside flags [192]
+constexpr int kP1Bar = kP1In + 192;
+constexpr int kP1Smem = kP1Bar + 16;
+
+// pass-2 shared memory (bytes)
+constexpr int kP2W2 = 0;                  // 64 x 64 block-diagonal
+constexpr int kP2F1 = kP2W2 + 64 * 64 * 2;
+constexpr int kP2F2 = kP2F1 + 128 * 64 * 2;
+constexpr int kP2Hd = kP2F2 + 64 * 64 * 2;
+constexpr int kP2A = kP2Hd + 16 * 64 * 2;  // 8 planes x 128 rows x 16 B
+constexpr int kP2Par = kP2A + 8 * 128 * 16;
+constexpr int kP2ParN = 64 + 64 + 128 + 64 + 64 + 16;   // b2, beta, fb1, fb2, gamma, hb
+constexpr int kP2Att = kP2Par + kP2ParN * 4;
+constexpr int kP2Bar = kP2Att + 64 * 4;
+constexpr int kP2Smem = kP2Bar + 16;
+
+struct AdapterTcDev {
+  const uint8_t* b1;   // pass-1 B operand (4096 B)
+  const float* p1f;    // [pw1 bias 128][dw weights 128 x 9][dw bias 128]
+  const uint8_t* w2;   // 8192 B
+  const uint8_t* f1;   // 16384 B
+  const uint8_t* f2;   // 8192 B
+  const uint8_t* hd;   // 2048 B
+  const float* p2f;    // kP2ParN floats
+};
+
+template <typename T> __device__ __forceinline__ float tof(T v);
+template <> __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T fromf(float v);
+template <> __device__ __forceinline__ __half fromf<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 fromf<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// n (a multiple of 8) channels of a 16-bit NHWC row into floats
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T* p, float* v) {
+#pragma unroll
+  for (int q = 0; q < N / 8; ++q) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(p) + q);
+    const T* h = reinterpret_cast<const T*>(&t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[8 * q + k] = tof<T>(h[k]);
+  }
+}
+
+// 8 floats -> one 16-byte row of an FP16 A plane
+__device__ __forceinline__ uint4 pack8h(const float* v) {
+  __align__(16) __half2 h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) h[k] = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+  return *reinterpret_cast<const uint4*>(h);
+}
+
+// (x - mean) / sqrt(var + 1e-6) over 16 channels
+__device__ __forceinline__ void norm16(const float* x, float* y) {
+  float mu = 0.f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) mu += x[c];
+  mu *= (1.f / C);
+  float var = 0.f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float d = x[c] - mu;
+    var = fmaf(d, d, var);
+  }
+  var *= (1.f / C);
+  const float inv = 1.f / sqrtf(var + 1e-6f);
+#pragma unroll
+  for (int c = 0; c < C; ++c) y[c] = (x[c] - mu) * inv;
+}
+
+template <typename TA>
+struct AdGroup {
+  AdapterImg<TA> img[kMaxGroup];
+  int tile_start[kMaxGroup + 1];
+  int px_start[kMaxGroup + 1];
+  int nimg;
+};
+
+__device__ __forceinline__ int find_group(const int* start, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void copy_to_smem(uint8_t* dst, const void* src, int bytes) {
+  for (int i = threadIdx.x * 16; i < bytes; i += blockDim.x * 16)
+    *reinterpret_cast<uint4*>(dst + i) = __ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(src) + i));
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_constant__ AdGroup<TA> G,
+                                                             const AdapterTcDev W, unsigned int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* A = smem + kP1A;
+  float* pw = reinterpret_cast<float*>(smem + kP1Pw);
+  const float* b1s = reinterpret_cast<const float*>(smem + kP1Dw);
+  const float* dww = b1s + 128;
+  const float* dwb = dww + 128 * 9;
+  uint8_t* inside = smem + kP1In;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP1Bar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP1Bar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  copy_to_smem(smem + kP1B, W.b1, 128 * 32);
+  copy_to_smem(smem + kP1Dw, W.p1f, (128 + 128 * 9 + 128) * 4);
+  // A rows 180..255 stay zero (finite operands for the unused accumulator rows)
+  for (int r = kHalo + tid; r < kRows; r += kP1Threads) {
+    *reinterpret_cast<uint4*>(A + r * 16) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(A + kRows * 16 + r * 16) = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, 128);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  constexpr uint32_t idesc = idesc_f16kind(0u, 128, 64);
+  const int total = G.tile_start[G.nimg];
+  uint32_t phase = 0;
+  bool ok = true;
+  // TMEM rows: warp w reads lanes 32 (w % 4) .. +31; warps 0-3 take M tile 0
+  // (halo rows 0..127), warps 4-7 M tile 1 (rows 128..255)
+  const int mt = warp >> 2, row = mt * 128 + (tid & 127);
+
+#pragma unroll 1
+  for (int t = blockIdx.x; ok && t < total; t += gridDim.x) {
+    const int k = find_group(G.tile_start, G.nimg, t);
+    const AdapterImg<TA>& im = G.img[k];
+    const int lt = t - G.tile_start[k];
+    const int ntx = (im.W + kTW - 1) / kTW;
+    const int x0 = (lt % ntx) * kTW, y0 = (lt / ntx) * kTH;
+    __syncthreads();  // the previous tile's readers of A and inside are done
+    for (int hp = tid; hp < kHalo; hp += kP1Threads) {
+      const int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
+      const bool in = y >= 0 && y < im.H && x >= 0 && x < im.W;
+      float v[C], n[C];
+      if (in) {
+        load_row<TA, C>(im.F + ((size_t)y * im.W + x) * C, v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = 0.f;
+      }
+      norm16(v, n);
+      *reinterpret_cast<uint4*>(A + hp * 16) = pack8h(n);
+      *reinterpret_cast<uint4*>(A + kRows * 16 + hp * 16) = pack8h(n + 8);
+      inside[hp] = in ? 1 : 0;
+    }
+    // two rounds: adapters (0, 1), then (2, 3)
+#pragma unroll 1
+    for (int rd = 0; rd < 2; ++rd) {
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();  // A is staged; the previous round's readers of pw are done
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t ab = smem_u32(A), bb = smem_u32(smem + kP1B) + (uint32_t)(rd * 64 * 16);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+          mma_f16kind(tmem + (uint32_t)(i * 64), smem_desc(ab + (uint32_t)(i * 128 * 16), kRows * 16, 128),
+                      smem_desc(bb, 128 * 16, 128), idesc, 0u);
+        mma_commit(bar);
+      }
+      ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+      if (!ok) {
+        record_error(err, 0x100u);
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      // accumulators -> pw (+ bias; zero outside the image): channel c of the
+      // round is pw1 output 64 rd + c
+      {
+        const bool inrow = row < kHalo;
+        const bool keep = inrow && inside[inrow ? row : 0];
+#pragma unroll 1
+        for (int c = 0; c < 64; c += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * 64 + c), v);
+          if (inrow) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              pw[(c + j) * kChS + row] = keep ? v[j] + b1s[rd * 64 + c + j] : 0.f;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      // depthwise 3x3 + simple gate: thread = (channel group g in 0..15, column
+      // x); group g covers adapter a = 2 rd + g / 8 and gated channels
+      // (g % 8) * 2, +1 of it, with their partners +16
+      {
+        const int g = tid >> 4, x = tid & 15, al = g >> 3, a = 2 * rd + al, j0 = (g & 7) * 2;
+        const int px = x0 + x;
+        float gv[2][kTH];
+        float sums[2];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int cl0 = al * 32 + j0 + jj, cl1 = cl0 + 16;     // channel within the round
+          const int cg0 = rd * 64 + cl0, cg1 = cg0 + 16;          // global pw1 channel
+          float d0[kTH], d1[kTH];
+#pragma unroll
+          for (int y = 0; y < kTH; ++y) {
+            d0[y] = dwb[cg0];
+            d1[y] = dwb[cg1];
+          }
+          const float* q0 = pw + cl0 * kChS + x;
+          const float* q1 = pw + cl1 * kChS + x;
+#pragma unroll
+          for (int r = 0; r < kHH; ++r) {
+            const float u0 = q0[r * kHW], u1 = q0[r * kHW + 1], u2 = q0[r * kHW + 2];
+            const float v0 = q1[r * kHW], v1 = q1[r * kHW + 1], v2 = q1[r * kHW + 2];
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const int y = r - ky;
+              if (y >= 0 && y < kTH) {
+                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 0], u0, d0[y]);
+                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 1], u1, d0[y]);
+                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 2], u2, d0[y]);
+                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 0], v0, d1[y]);
+                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 1], v1, d1[y]);
+                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 2], v2, d1[y]);
+              }
+            }
+          }
+          float sm = 0.f;
+#pragma unroll
+          for (int y = 0; y < kTH; ++y) {
+            const bool valid = px < im.W && y0 + y < im.H;
+            gv[jj][y] = d0[y] * d1[y];
+            sm += valid ? gv[jj][y] : 0.f;
+          }
+          sums[jj] = sm;
+        }
+#pragma unroll
+        for (int y = 0; y < kTH; ++y) {
+          if (px < im.W && y0 + y < im.H) {
+            __align__(4) TA o[2] = {fromf<TA>(gv[0][y]), fromf<TA>(gv[1][y])};
+            *reinterpret_cast<uint32_t*>(im.x1 + ((size_t)(y0 + y) * im.W + px) * (4 * C) + a * C + j0) =
+                *reinterpret_cast<const uint32_t*>(o);
+          }
+        }
+        // per-channel tile sums over the 16 columns of the group (a half-warp), fixed tree
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          float sm = sums[jj];
+#pragma unroll
+          for (int off = 8; off > 0; off >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, off);
+          if (x == 0) im.partial[(size_t)lt * (4 * C) + a * C + j0 + jj] = sm;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// one 16-channel row slice of an FP16 A plane pair at row `row`
+__device__ __forceinline__ void put16(uint8_t* A, int plane, int row, const float* v) {
+  *reinterpret_cast<uint4*>(A + plane * 2048 + row * 16) = pack8h(v);
+  *reinterpret_cast<uint4*>(A + (plane + 1) * 2048 + row * 16) = pack8h(v + 8);
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ AdGroup<TA> G,
+                                                      const AdapterTcDev W, unsigned int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* A = smem + kP2A;
+  const float* par = reinterpret_cast<const float*>(smem + kP2Par);
+  const float* b2 = par;
+  const float* beta = b2 + 64;
+  const float* fb1 = beta + 64;
+  const float* fb2 = fb1 + 128;
+  const float* gamma = fb2 + 64;
+  const float* hb = gamma + 64;
+  float* att = reinterpret_cast<float*>(smem + kP2Att);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP2Bar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP2Bar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  copy_to_smem(smem + kP2W2, W.w2, 64 * 64 * 2);
+  copy_to_smem(smem + kP2F1, W.f1, 128 * 64 * 2);
+  copy_to_smem(smem + kP2F2, W.f2, 64 * 64 * 2);
+  copy_to_smem(smem + kP2Hd, W.hd, 16 * 64 * 2);
+  copy_to_smem(smem + kP2Par, W.p2f, kP2ParN * 4);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, 128);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t ab = smem_u32(A);
+  const int total = G.px_start[G.nimg];
+  constexpr int plane_of[8] = {4, 5, 0, 1, 2, 3, 6, 7};   // head column -> output plane
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // one GEMM stage: D[0, n) = A(K = 64) x B(n rows), then wait
+  auto stage = [&](const uint8_t* b, int n, uint32_t idesc) -> bool {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t bb = smem_u32(b);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_f16kind(tmem, smem_desc(ab + (uint32_t)(kk * 2 * 2048), 2048, 128),
+                    smem_desc(bb + (uint32_t)(kk * n * 32), (uint32_t)(n * 16), 128), idesc,
+                    kk > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    const bool done = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+    tc_fence_after();
+    return done;
+  };
+
+#pragma unroll 1
+  for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
+    const int k = find_group(G.px_start, G.nimg, blk);
+    const AdapterImg<TA>& im = G.img[k];
+    const int npix = im.H * im.W;
+    const int p = (blk - G.px_start[k]) * 128 + tid;
+    const bool valid = p < npix;
+    __syncthreads();  // the previous block is done with att and A
+    if (tid < 64) att[tid] = im.att[tid];
+    __syncthreads();
+    float f[C], y[4 * C];
+    // stage 1: A = att * x1
+    {
+      float xv[4 * C];
+      if (valid) {
+        load_row<TA, C>(im.F + (size_t)p * C, f);
+        load_row<TA, 4 * C>(im.x1 + (size_t)p * (4 * C), xv);
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) f[c] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4 * C; ++c) xv[c] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4 * C; ++c) xv[c] *= att[c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) put16(A, 2 * a, tid, xv + a * C);
+    }
+    if (!(ok = stage(smem + kP2W2, 64, idesc_f16kind(0u, 128, 64)))) break;
+    // stage 2: y = F + beta (pw2 + b2); A = LN2(y) (affine folded into ffn1)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float d[16], n[16];
+      tmem_ld16(lane_base + (uint32_t)(a * 16), d);
+#pragma unroll
+      for (int c = 0; c < C; ++c) y[a * C + c] = fmaf(beta[a * C + c], d[c] + b2[a * C + c], f[c]);
+      norm16(y + a * C, n);
+      put16(A, 2 * a, tid, n);
+    }
+    if (!(ok = stage(smem + kP2F1, 128, idesc_f16kind(0u, 128, 128)))) break;
+    // stage 3: gate of ffn1 (channels o and o + 16 of each adapter)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float u[16], v[16], gt[16];
+      tmem_ld16(lane_base + (uint32_t)(a * 32), u);
+      tmem_ld16(lane_base + (uint32_t)(a * 32 + 16), v);
+#pragma unroll
+      for (int c = 0; c < C; ++c) gt[c] = (u[c] + fb1[a * 32 + c]) * (v[c] + fb1[a * 32 + 16 + c]);
+      put16(A, 2 * a, tid, gt);
+    }
+    if (!(ok = stage(smem + kP2F2, 64, idesc_f16kind(0u, 128, 64)))) break;
+    // stage 4: z = y + gamma (ffn2 + fb2); heads
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float d[16], z[16];
+      tmem_ld16(lane_base + (uint32_t)(a * 16), d);
+#pragma unroll
+      for (int c = 0; c < C; ++c) z[c] = fmaf(gamma[a * C + c], d[c] + fb2[a * C + c], y[a * C + c]);
+      put16(A, 2 * a, tid, z);
+    }
+    if (!(ok = stage(smem + kP2Hd, 16, idesc_f16kind(0u, 128, 16)))) break;
+    {
+      float d[16];
+      tmem_ld16(lane_base, d);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) im.out[(size_t)plane_of[j] * npix + p] = d[j] + hb[j];
+      }
+    }
+  }
+  if (!ok) record_error(err, 0x200u);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+// Pack a [N][K] row-major float matrix (K a multiple of 16) as the FP16
+// K-major B operand: per 16-wide K slice, N rows x 32 bytes, the two 8-wide K
+// core matrices N*16 bytes apart, rows grouped by 8 (128 bytes).
+void pack_b(const std::vector<float>& w, int N, int K, std::vector<uint8_t>& out) {
+  out.assign((size_t)N * K * 2, 0);
+  for (int kk = 0; kk < K / 16; ++kk)
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < 16; ++k) {
+        const __half h = __float2half_rn(w[(size_t)n * K + kk * 16 + k]);
+        std::memcpy(out.data() + (size_t)kk * N * 32 + (k / 8) * N * 16 + (n / 8) * 128 + (n % 8) * 16 +
+                        (k % 8) * 2,
+                    &h, 2);
+      }
+}
+
+}  // namespace
+
+struct AdapterTcWeights {
+  AdapterTcDev dev{};
+  std::vector<void*> allocs;
+  int p1_grid = 0, p2_grid = 0;
+};
+
+AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* err) {
+  *err = cudaSuccess;
+  AdapterTcWeights* w = new AdapterTcWeights();
+  auto up = [&](const void* src, size_t bytes) -> void* {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { *err = e; return nullptr; }
+    w->allocs.push_back(p);
+    if ((e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice)) != cudaSuccess) *err = e;
+    return p;
+  };
+  const AdapterP1& p1 = prm.p1;
+  const AdapterP2& p2 = prm.p2;
+  std::vector<float> m;
+  std::vector<uint8_t> pk;
+  // pw1 of the four adapters: row 32a + o, K = the 16 normalised channels
+  m.assign(128 * 16, 0.f);
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o)
+      for (int c = 0; c < 16; ++c) m[(size_t)(a * 32 + o) * 16 + c] = p1.w1[a][o][c];
+  pack_b(m, 128, 16, pk);
+  w->dev.b1 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  std::vector<float> f1s;
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o) f1s.push_back(p1.b1[a][o]);
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o)
+      for (int k = 0; k < 9; ++k) f1s.push_back(p1.dww[a][o][k]);
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o) f1s.push_back(p1.dwb[a][o]);
+  w->dev.p1f = static_cast<const float*>(up(f1s.data(), f1s.size() * 4));
+  // block-diagonal pass-2 weights: input channel a*16 + ci feeds only adapter a
+  m.assign(64 * 64, 0.f);
+  for (int a = 0; a < 4; ++a)
+    for (int co = 0; co < 16; ++co)
+      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 16 + co) * 64 + a * 16 + ci] = p2.w2[a][co][ci];
+  pack_b(m, 64, 64, pk);
+  w->dev.w2 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  m.assign(128 * 64, 0.f);
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o)
+      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 32 + o) * 64 + a * 16 + ci] = p2.f1[a][o][ci];
+  pack_b(m, 128, 64, pk);
+  w->dev.f1 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  m.assign(64 * 64, 0.f);
+  for (int a = 0; a < 4; ++a)
+    for (int co = 0; co < 16; ++co)
+      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 16 + co) * 64 + a * 16 + ci] = p2.f2[a][co][ci];
+  pack_b(m, 64, 64, pk);
+  w->dev.f2 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  m.assign(16 * 64, 0.f);
+  for (int a = 0; a < 4; ++a)
+    for (int j = 0; j < 2; ++j)
+      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 2 + j) * 64 + a * 16 + ci] = p2.hw[a][j][ci];
+  pack_b(m, 16, 64, pk);
+  w->dev.hd = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  std::vector<float> f2s;
+  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.b2[a][c]);
+  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.beta[a][c]);
+  for (int a = 0; a < 4; ++a) for (int o = 0; o < 32; ++o) f2s.push_back(p2.fb1[a][o]);
+  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.fb2[a][c]);
+  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.gamma[a][c]);
+  for (int a = 0; a < 4; ++a) for (int j = 0; j < 2; ++j) f2s.push_back(p2.hb[a][j]);
+  while (f2s.size() < (size_t)kP2ParN) f2s.push_back(0.f);
+  w->dev.p2f = static_cast<const float*>(up(f2s.data(), f2s.size() * 4));
+  if (*err != cudaSuccess) {
+    adapters_tc_destroy(w);
+    return nullptr;
+  }
+  return w;
+}
+
+void adapters_tc_destroy(AdapterTcWeights* w) {
+  if (!w) return;
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+}
+
+template <typename TA>
+cudaError_t adapters_tc_run_group(const AdapterTcWeights* w, const AdapterParamSet& prm,
+                                  const AdapterImg<TA>* imgs, int n, unsigned int* err,
+                                  cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  static bool init = false;
+  static int occ1 = 0, occ2 = 0;
+  if (!init) {
+    // the largest shared-memory carveout, so that several CTAs fit per SM
+    cudaError_t e = cudaFuncSetAttribute(adapters_p1_tc<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP1Smem);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2Smem)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(adapters_p1_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+      return e;
+    occ1 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p1_tc<TA>), kP1Threads, kP1Smem, 128);
+    occ2 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p2_tc<TA>), 128, kP2Smem, 128);
+    init = true;
+  }
+  AdGroup<TA> G{};
+  G.nimg = n;
+  int tiles = 0, blocks = 0;
+  for (int k = 0; k < n; ++k) {
+    G.img[k] = imgs[k];
+    G.tile_start[k] = tiles;
+    G.px_start[k] = blocks;
+    tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
+    blocks += (imgs[k].W * imgs[k].H + 127) / 128;
+  }
+  G.tile_start[n] = tiles;
+  G.px_start[n] = blocks;
+  const int g1 = tiles < kNumSMs * occ1 ? tiles : kNumSMs * occ1;
+  adapters_p1_tc<TA><<<g1, kP1Threads, kP1Smem, s>>>(G, w->dev, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = adapters_reduce_only_group<TA>(prm, imgs, n, s)) != cudaSuccess) return e;
+  const int g2 = blocks < kNumSMs * occ2 ? blocks : kNumSMs * occ2;
+  adapters_p2_tc<TA><<<g2, 128, kP2Smem, s>>>(G, w->dev, err);
+  return cudaGetLastError();
+}
+
+template cudaError_t adapters_tc_run_group<__half>(const AdapterTcWeights*, const AdapterParamSet&,
+                                                   const AdapterImg<__half>*, int, unsigned int*,
+                                                   cudaStream_t);
+template cudaError_t adapters_tc_run_group<__nv_bfloat16>(const AdapterTcWeights*, const AdapterParamSet&,
+                                                          const AdapterImg<__nv_bfloat16>*, int,
+                                                          unsigned int*, cudaStream_t);
+
+}  // namespace nsl

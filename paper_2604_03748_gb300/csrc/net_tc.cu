@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "nsl_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace nsl {
 
@@ -38,141 +39,10 @@ constexpr int kPatchW = 8, kPatchH = 16;                     // M tile = 128 pix
 constexpr int kHaloW = kPatchW + 2, kHaloH = kPatchH + 2;    // 10 x 18
 constexpr int kHaloPix = kHaloW * kHaloH;                    // 180
 constexpr int kPlane = kHaloPix * 16;                        // bytes per 8-channel plane
-constexpr long long kWaitCycles = 4000000000LL;              // ~2 s at 2 GHz
 #ifndef NSL_CONV_CTAS_PER_SM
 #define NSL_CONV_CTAS_PER_SM 2
 #endif
 constexpr int kConvCtasPerSM = NSL_CONV_CTAS_PER_SM;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: false after ~2 s without the phase completing.  The outcome is
-// made warp-uniform, since the TMEM loads that follow are warp-collective.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  bool done = mbar_try_wait(b, parity);
-  if (!done) {
-    const long long t0 = clock64();
-    while (!(done = mbar_try_wait(b, parity))) {
-      if (clock64() - t0 > kWaitCycles) break;
-    }
-  }
-  return __all_sync(0xffffffffu, done);
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(b))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle (canonical K-major core-matrix
-// layout): start address, leading-dimension (K) byte offset, stride-dimension
-// (M/N) byte offset, all in 16-byte units; bit 46 = descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: D f32, A and B of format `fmt` (0 FP16,
-// 1 BF16; both operands always the same type), both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_f16kind(uint32_t fmt, int M, int N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16kind(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-// kind::f8f6f4 with both operands FP8 E4M3 (format code 0 in the same
-// instruction-descriptor fields), FP32 accumulation; K = 32 per instruction.
-__device__ __forceinline__ void mma_f8kind(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                        uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* b) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(b))
-      : "memory");
-}
-
-// 32 lanes x 16 columns of 32-bit accumulators: thread t of the warp gets row
-// (32*(warp%4) + t), columns [col, col+16).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%"
-      "14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // 16-bit operand types of kind::f16: BF16 (format code 1) and FP16 (code 0).
 template <typename T> struct Half;
@@ -285,9 +155,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void record_error(unsigned int* err, unsigned int code) {
-  if (err) atomicOr_system(err, code);
-}
 
 // One image of a (grouped) layer launch.  A launch covers up to kMaxGroup
 // images of any sizes that share the layer's weights; tiles are numbered
@@ -810,6 +677,31 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
 // host side
 // ---------------------------------------------------------------------------
 
+}  // namespace
+
+// CTAs of a kernel that fit on one SM at once, from its shared memory,
+// registers, threads and TMEM columns.  (The runtime's occupancy query reports
+// one CTA per SM for every kernel that allocates tensor memory, whatever its
+// resources, so it cannot size these grids.)
+int tc_ctas_per_sm(const void* kernel, int threads, int dyn_smem, int tmem_cols) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 1;
+  const int by_smem = 233472 / (dyn_smem + (int)fa.sharedSizeBytes + 1024);
+  const int warps = (threads + 31) / 32;
+  const int regs_per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = regs_per_warp > 0 ? 65536 / (regs_per_warp * warps) : 32;
+  const int by_threads = 2048 / threads;
+  const int by_tmem = tmem_cols > 0 ? 512 / tmem_cols : 32;
+  int n = by_smem;
+  if (by_regs < n) n = by_regs;
+  if (by_threads < n) n = by_threads;
+  if (by_tmem < n) n = by_tmem;
+  if (n > 32) n = 32;
+  return n < 1 ? 1 : n;
+}
+
+namespace {
+
 // Kernel launch configuration: persistent grid of (CTAs per SM) x SMs, where
 // the CTAs per SM are limited so that their TMEM allocations fit in 512 columns.
 struct Launch {
@@ -829,12 +721,12 @@ static cudaError_t configure(K kernel, int smem_needed, int tmem_cols, Launch* L
   if (smem > 232448) smem = 232448;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem);
+  // prefer the largest shared-memory carveout, so that several CTAs fit per SM
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
   L->smem = smem;
-  L->per_sm = occ < tmem_fit ? occ : tmem_fit;
+  L->per_sm = tc_ctas_per_sm(reinterpret_cast<const void*>(kernel), 128, smem, tmem_cols);
   return cudaSuccess;
 }
 
@@ -968,6 +860,7 @@ struct NetTcWeights {
   uint8_t* up_w[3] = {};
   float* up_b[3] = {};
   float* up_s[3] = {};
+  AdapterTcWeights* ad = nullptr;   // tensor-core adapters
   std::vector<void*> allocs;
 };
 
@@ -1027,6 +920,12 @@ NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, int elem, cudaE
   if (elem == 2) fill_weights_q8(w, hp, L, err);
   else if (elem == 1) fill_weights<__nv_bfloat16>(w, hp, L, err);
   else fill_weights<__half>(w, hp, L, err);
+  if (*err == cudaSuccess) {
+    AdapterParamSet* prm = new AdapterParamSet();
+    adapter_params_from(hp + L.adapter[0], &prm->p1, &prm->sca, &prm->p2);
+    w->ad = adapters_tc_create(*prm, err);
+    delete prm;
+  }
   if (*err != cudaSuccess) { net_tc_destroy(w); return nullptr; }
   return w;
 }
@@ -1034,6 +933,7 @@ NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, int elem, cudaE
 void net_tc_destroy(NetTcWeights* w) {
   if (!w) return;
   for (void* p : w->allocs) cudaFree(p);
+  adapters_tc_destroy(w->ad);
   delete w;
 }
 
@@ -1209,7 +1109,7 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
   AdapterImg<T> ai[kMaxGroup];
   for (int k = 0; k < n; ++k)
     ai[k] = AdapterImg<T>{B[k].fa, B[k].x1, B[k].partial, B[k].att, imgs[k].out, imgs[k].H, imgs[k].W};
-  TRY(adapters_run_group<T>(net_f32_adapter_params(wf), ai, n, s));
+  TRY(adapters_tc_run_group<T>(w->ad, net_f32_adapter_params(wf), ai, n, err, s));
 #undef SET
 #undef TRY
   return cudaSuccess;

@@ -232,6 +232,19 @@ struct AdapterImg {
 template <typename TA>
 cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
                                cudaStream_t s);
+// the SCA reduction alone (per image: partial tile sums -> att), one launch
+template <typename TA>
+cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
+                                       cudaStream_t s);
+// tensor-core adapters (adapters_tc.cu): pw1 / pw2 / ffn1 / ffn2 / heads on
+// tcgen05 with FP16 operands; same tiling and partial layout as the SIMT ones
+struct AdapterTcWeights;
+AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* err);
+void adapters_tc_destroy(AdapterTcWeights* w);
+template <typename TA>
+cudaError_t adapters_tc_run_group(const AdapterTcWeights* w, const AdapterParamSet& prm,
+                                  const AdapterImg<TA>* imgs, int n, unsigned int* err,
+                                  cudaStream_t s);
 // amax (nullable): per image, where the maximum of the stored outputs is
 // accumulated (FP8 path)
 template <typename T>
@@ -258,6 +271,9 @@ cudaError_t net_tc_forward_group(const NetTcWeights* wt, const NetF32Weights* wf
                                  unsigned int* err_flag, cudaStream_t s);
 // runtime tunable: CTAs per SM of the tensor-core convolutions (1..4)
 void net_tc_set_ctas_per_sm(int v);
+
+// CTAs of a tensor-memory kernel that fit on one SM (net_tc.cu)
+int tc_ctas_per_sm(const void* kernel, int threads, int dyn_smem, int tmem_cols);
 
 // ---- batched frames (batch.cu), used by the server ----
 void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes);
