@@ -249,7 +249,21 @@ __device__ __forceinline__ void adapters_reduce_body(const float* __restrict__ p
   __shared__ float mean[4 * C];
   const int ch = threadIdx.x % (4 * C), lane = threadIdx.x / (4 * C);  // 64 channels x 16 lanes
   float s = 0.f, comp = 0.f;
-  for (int t = lane; t < ntiles; t += 16) {
+  // eight loads in flight ahead of the compensated sums (same order of addition)
+  int t = lane;
+  for (; t + 7 * 16 < ntiles; t += 8 * 16) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = partial[(size_t)(t + u * 16) * (4 * C) + ch];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float y = v[u] - comp;
+      const float w = s + y;
+      comp = (w - s) - y;
+      s = w;
+    }
+  }
+  for (; t < ntiles; t += 16) {
     const float y = partial[(size_t)t * (4 * C) + ch] - comp;
     const float u = s + y;
     comp = (u - s) - y;

@@ -369,6 +369,25 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     return done;
   };
 
+  // this thread's pixel of a block: raw x1 (64 channels) and F (16 channels);
+  // the next block's are loaded while the current block's GEMMs run
+  uint4 rx[8], rf[2];
+  auto fetch = [&](int blk) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) rx[q] = make_uint4(0, 0, 0, 0);
+    rf[0] = rf[1] = make_uint4(0, 0, 0, 0);
+    if (blk >= total) return;
+    const int kk = find_group(G.px_start, G.nimg, blk);
+    const AdapterImg<TA>& m = G.img[kk];
+    const int pp = (blk - G.px_start[kk]) * 128 + tid;
+    if (pp >= m.H * m.W) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) rx[q] = __ldg(reinterpret_cast<const uint4*>(m.x1 + (size_t)pp * (4 * C)) + q);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) rf[q] = __ldg(reinterpret_cast<const uint4*>(m.F + (size_t)pp * C) + q);
+  };
+  fetch(blockIdx.x);
+
 #pragma unroll 1
   for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
     const int k = find_group(G.px_start, G.nimg, blk);
@@ -383,20 +402,22 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     // stage 1: A = att * x1
     {
       float xv[4 * C];
-      if (valid) {
-        load_row<TA, C>(im.F + (size_t)p * C, f);
-        load_row<TA, 4 * C>(im.x1 + (size_t)p * (4 * C), xv);
-      } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) f[c] = 0.f;
+      for (int q = 0; q < 8; ++q) {
+        const TA* h = reinterpret_cast<const TA*>(&rx[q]);
 #pragma unroll
-        for (int c = 0; c < 4 * C; ++c) xv[c] = 0.f;
+        for (int e = 0; e < 8; ++e) xv[8 * q + e] = tof<TA>(h[e]) * att[8 * q + e];
       }
 #pragma unroll
-      for (int c = 0; c < 4 * C; ++c) xv[c] *= att[c];
+      for (int q = 0; q < 2; ++q) {
+        const TA* h = reinterpret_cast<const TA*>(&rf[q]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[8 * q + e] = tof<TA>(h[e]);
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a) put16(A, 2 * a, tid, xv + a * C);
     }
+    fetch(blk + (int)gridDim.x);
     if (!(ok = stage(smem + kP2W2, 64, idesc_f16kind(0u, 128, 64)))) break;
     // stage 2: y = F + beta (pw2 + b2); A = LN2(y) (affine folded into ffn1)
 #pragma unroll

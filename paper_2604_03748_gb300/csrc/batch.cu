@@ -69,7 +69,7 @@ struct nsl_batch {
   // tuning
   int seg_len = kMarchSegLen;
   int seg_blocks_per_sm = 0;       // 0 = occupancy maximum
-  int conv_ctas = 2;
+  int conv_ctas = 4;
   // captured graph
   cudaGraphExec_t exec = nullptr;
   bool capturing = false;
@@ -529,7 +529,7 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   const int conv_ctas[] = {1, 2, 4};
   const int occ = march_segment_blocks_max();
   std::vector<int> march_bps = {0};
-  for (int v : {4, 6}) if (v < occ) march_bps.push_back(v);
+  for (int v : {4, 5}) if (v < occ) march_bps.push_back(v);
   cudaEvent_t e0, e1;
   NSL_CUDA_TRY(cudaEventCreate(&e0));
   NSL_CUDA_TRY(cudaEventCreate(&e1));

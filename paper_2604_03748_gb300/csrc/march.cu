@@ -205,6 +205,59 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
     return;
   }
 #endif
+#if NSL_SHADOW_FLAT
+  // the two rays back to back in one sequence of Kt + Kb samples, two per
+  // iteration so that two gathers are in flight (each ray's samples and sums
+  // in the same order as below): the sequence length is nearly the same for
+  // every lane of a warp, where max(Kt, Kb) is not
+  (void)K;
+  const int Kall = Kt + (ab ? Kb : 0);
+  int j = at ? 1 : Kt + 1;
+  while (j <= Kall) {
+    const int j2 = j + 1;
+    const bool hasB = j2 <= Kall;
+    const bool tA = j <= Kt, tB = j2 <= Kt;
+    const float khA = __fmul_rn((float)(tA ? j : j - Kt), h);
+    const float khB = __fmul_rn((float)(tB ? j2 : j2 - Kt), h);
+    const float dAx = __fmul_rn(khA, u[0]), dAy = __fmul_rn(khA, u[1]), dAz = __fmul_rn(khA, u[2]);
+    const float dBx = __fmul_rn(khB, u[0]), dBy = __fmul_rn(khB, u[1]), dBz = __fmul_rn(khB, u[2]);
+    const Fetch fA = fetch(g, tA ? __fadd_rn(px, dAx) : __fsub_rn(px, dAx),
+                           tA ? __fadd_rn(py, dAy) : __fsub_rn(py, dAy),
+                           tA ? __fadd_rn(pz, dAz) : __fsub_rn(pz, dAz));
+    const Fetch fB = fetch(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
+                           tB ? __fadd_rn(py, dBy) : __fsub_rn(py, dBy),
+                           tB ? __fadd_rn(pz, dBz) : __fsub_rn(pz, dBz));
+    const float vA = interp(fA), vB = interp(fB);
+    int jn = j + 2;
+    if (tA) {
+      taut = fmaf(vA, h, taut);
+      if (kCount) ++nsamp;
+      if (taut > tau_lim) {
+        jn = Kt + 1;               // top ray done; sample B (if bottom) is taken next
+      } else if (hasB) {
+        if (tB) {
+          taut = fmaf(vB, h, taut);
+          if (kCount) ++nsamp;
+          if (taut > tau_lim) jn = Kt + 1;
+        } else {
+          taub = fmaf(vB, h, taub);
+          if (kCount) ++nsamp;
+          if (taub > tau_lim) break;
+        }
+      }
+    } else {
+      taub = fmaf(vA, h, taub);
+      if (kCount) ++nsamp;
+      if (taub > tau_lim) break;
+      if (hasB) {
+        taub = fmaf(vB, h, taub);
+        if (kCount) ++nsamp;
+        if (taub > tau_lim) break;
+      }
+    }
+    j = jn;
+  }
+#else
   for (int k = 1; k <= K && (at || ab); ++k) {
     const float kh = __fmul_rn((float)k, h);
     const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
@@ -219,6 +272,7 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
       if (k >= Kb || taub > tau_lim) ab = false;
     }
   }
+#endif
   Tt = expf(-taut);
   Tb = expf(-taub);
 }

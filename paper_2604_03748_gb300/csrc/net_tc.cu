@@ -40,7 +40,10 @@ constexpr int kHaloW = kPatchW + 2, kHaloH = kPatchH + 2;    // 10 x 18
 constexpr int kHaloPix = kHaloW * kHaloH;                    // 180
 constexpr int kPlane = kHaloPix * 16;                        // bytes per 8-channel plane
 #ifndef NSL_CONV_CTAS_PER_SM
-#define NSL_CONV_CTAS_PER_SM 2
+#define NSL_CONV_CTAS_PER_SM 4
+#endif
+#ifndef NSL_CONV_MIN_TILES
+#define NSL_CONV_MIN_TILES 1
 #endif
 constexpr int kConvCtasPerSM = NSL_CONV_CTAS_PER_SM;
 
@@ -1008,11 +1011,13 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   a.bias = w->conv_b[l];
   a.wscale = w->conv_s[l];
   a.err = err;
-  // enough CTAs to cover every SM, each pipelining >= 4 tiles when there are
-  // that many; per-SM residency is capped by the tunable CTAs-per-SM
+  // enough CTAs to cover every SM, each pipelining >= NSL_CONV_MIN_TILES tiles
+  // when there are that many; per-SM residency is capped by the tunable
+  // CTAs-per-SM
   const int per_sm = L.per_sm < g_conv_ctas_per_sm ? L.per_sm : g_conv_ctas_per_sm;
   int grid = kNumSMs * per_sm / (COUT / NT);
-  if (grid > (ntiles + 3) / 4) grid = (ntiles + 3) / 4;
+  if (grid > (ntiles + NSL_CONV_MIN_TILES - 1) / NSL_CONV_MIN_TILES)
+    grid = (ntiles + NSL_CONV_MIN_TILES - 1) / NSL_CONV_MIN_TILES;
   if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;

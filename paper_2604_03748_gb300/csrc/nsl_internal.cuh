@@ -62,11 +62,14 @@ struct MarchPlume {
   float* seg_L;       // [segment][pixel] partial guide radiance
 };
 
+#ifndef NSL_SHADOW_FLAT
+#define NSL_SHADOW_FLAT 1   // top and bottom shadow rays as one two-sample-per-step sequence
+#endif
 #ifndef NSL_MARCH_PIPELINE
 #define NSL_MARCH_PIPELINE 0
 #endif
 #ifndef NSL_MARCH_MIN_BLOCKS
-#define NSL_MARCH_MIN_BLOCKS 8
+#define NSL_MARCH_MIN_BLOCKS 6
 #endif
 #ifndef NSL_MARCH_SEG
 #define NSL_MARCH_SEG 8
