@@ -529,7 +529,7 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   const int conv_ctas[] = {1, 2, 4};
   const int occ = march_segment_blocks_max();
   std::vector<int> march_bps = {0};
-  for (int v : {4, 5}) if (v < occ) march_bps.push_back(v);
+  for (int v : {5, 6}) if (v < occ) march_bps.push_back(v);
   cudaEvent_t e0, e1;
   NSL_CUDA_TRY(cudaEventCreate(&e0));
   NSL_CUDA_TRY(cudaEventCreate(&e1));

@@ -127,6 +127,25 @@ __device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float 
   return f;
 }
 
+// fetch() without the index clamps, for points within rounding of the closed
+// box (every shadow sample k <= K is): floor(p - 0.5) then lies in [-1, n-1]
+// on every axis, inside the padded array.
+__device__ __forceinline__ Fetch fetch_in(const Grid& g, float px, float py, float pz) {
+  Fetch f;
+  f.in = px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz;
+  float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
+  float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+  f.tx = __fsub_rn(qx, flx);
+  f.ty = __fsub_rn(qy, fly);
+  f.tz = __fsub_rn(qz, flz);
+  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+  const float4* q = reinterpret_cast<const float4*>(g.v) +
+                    ((unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1));
+  f.a = __ldg(q);
+  f.b = __ldg(q + pl);
+  return f;
+}
+
 __device__ __forceinline__ float interp(const Fetch& f) {
   const float c00 = fmaf(f.tx, f.a.y - f.a.x, f.a.x);
   const float c10 = fmaf(f.tx, f.a.w - f.a.z, f.a.z);
@@ -206,6 +225,11 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
   }
 #endif
 #if NSL_SHADOW_FLAT
+#if NSL_SHADOW_NOCLAMP
+#define SHADOW_FETCH fetch_in
+#else
+#define SHADOW_FETCH fetch
+#endif
   // the two rays back to back in one sequence of Kt + Kb samples, two per
   // iteration so that two gathers are in flight (each ray's samples and sums
   // in the same order as below): the sequence length is nearly the same for
@@ -214,17 +238,17 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
   const int Kall = Kt + (ab ? Kb : 0);
   int j = at ? 1 : Kt + 1;
   while (j <= Kall) {
-    const int j2 = j + 1;
-    const bool hasB = j2 <= Kall;
+    const bool hasB = j + 1 <= Kall;
+    const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice, never past the ray's end
     const bool tA = j <= Kt, tB = j2 <= Kt;
     const float khA = __fmul_rn((float)(tA ? j : j - Kt), h);
     const float khB = __fmul_rn((float)(tB ? j2 : j2 - Kt), h);
     const float dAx = __fmul_rn(khA, u[0]), dAy = __fmul_rn(khA, u[1]), dAz = __fmul_rn(khA, u[2]);
     const float dBx = __fmul_rn(khB, u[0]), dBy = __fmul_rn(khB, u[1]), dBz = __fmul_rn(khB, u[2]);
-    const Fetch fA = fetch(g, tA ? __fadd_rn(px, dAx) : __fsub_rn(px, dAx),
+    const Fetch fA = SHADOW_FETCH(g, tA ? __fadd_rn(px, dAx) : __fsub_rn(px, dAx),
                            tA ? __fadd_rn(py, dAy) : __fsub_rn(py, dAy),
                            tA ? __fadd_rn(pz, dAz) : __fsub_rn(pz, dAz));
-    const Fetch fB = fetch(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
+    const Fetch fB = SHADOW_FETCH(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
                            tB ? __fadd_rn(py, dBy) : __fsub_rn(py, dBy),
                            tB ? __fadd_rn(pz, dBz) : __fsub_rn(pz, dBz));
     const float vA = interp(fA), vB = interp(fB);

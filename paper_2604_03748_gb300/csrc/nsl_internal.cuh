@@ -65,11 +65,14 @@ struct MarchPlume {
 #ifndef NSL_SHADOW_FLAT
 #define NSL_SHADOW_FLAT 1   // top and bottom shadow rays as one two-sample-per-step sequence
 #endif
+#ifndef NSL_SHADOW_NOCLAMP
+#define NSL_SHADOW_NOCLAMP 1   // shadow samples k <= K are inside the padded grid by construction
+#endif
 #ifndef NSL_MARCH_PIPELINE
 #define NSL_MARCH_PIPELINE 0
 #endif
 #ifndef NSL_MARCH_MIN_BLOCKS
-#define NSL_MARCH_MIN_BLOCKS 6
+#define NSL_MARCH_MIN_BLOCKS 7
 #endif
 #ifndef NSL_MARCH_SEG
 #define NSL_MARCH_SEG 8

@@ -198,7 +198,7 @@ def test_batch_autotune_and_cache(lib, tmp_path):
     ms = b.autotune(items, 3, cache_path=cache)
     assert ms > 0
     seg_len, mb, cc = b.get_tuning()
-    assert seg_len in (4, 8, 16) and mb in (0, 4, 5) and cc in (1, 2, 4)
+    assert seg_len in (4, 8, 16) and mb in (0, 5, 6) and cc in (1, 2, 4)
     lines = open(cache).read().splitlines()
     assert len(lines) == 1
     # the cached entry is applied without timing: plant a marker time and tuning
