@@ -40,6 +40,14 @@ struct Grid {
   float fx, fy, fz;  // box extents
 };
 
+// 32-byte load of an octo cell: the 2x2 x/y neighbourhood of slice z (a) and
+// of slice z+1 (b), in one 256-bit vector access
+__device__ __forceinline__ void ldg_octo(const float* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 // Extinction at p: 0 outside the closed box [0,n]; trilinear interpolation of
 // the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.
 __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, float pz) {
@@ -80,6 +88,16 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
     c10 = fmaf(tx, a1.y - a1.x, a1.x);
     c01 = fmaf(tx, b0.y - b0.x, b0.x);
     c11 = fmaf(tx, b1.y - b1.x, b1.x);
+  } else if constexpr (kMarchLayout == kLayoutOcto) {
+    // padded octo cells: cell (ix+1, iy+1, iz+1) of an (nx+1) x (ny+1) x (nz+1)
+    // array holds the 8 corners, every index of a point inside the box in range
+    const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+    float4 a, b;
+    ldg_octo(g.v + 8 * (size_t)((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1)), a, b);
+    c00 = fmaf(tx, a.y - a.x, a.x);
+    c10 = fmaf(tx, a.w - a.z, a.z);
+    c01 = fmaf(tx, b.y - b.x, b.x);
+    c11 = fmaf(tx, b.w - b.z, b.z);
   } else {
     // padded quads: cell (ix+1, iy+1, iz+1) of a (nx+1) x (ny+1) x (nz+2) array,
     // every index of a point inside the box is in range
@@ -120,10 +138,14 @@ __device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float 
   const int ix = min(max((int)flx, -1), g.nx - 1), iy = min(max((int)fly, -1), g.ny - 1);
   const int iz = min(max((int)flz, -1), g.nz - 1);
   const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  const float4* q = reinterpret_cast<const float4*>(g.v) +
-                    ((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1));
-  f.a = __ldg(q);
-  f.b = __ldg(q + pl);
+  const unsigned cell = (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1);
+  if constexpr (kMarchLayout == kLayoutOcto) {
+    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
+    f.a = __ldg(q);
+    f.b = __ldg(q + pl);
+  }
   return f;
 }
 
@@ -139,10 +161,14 @@ __device__ __forceinline__ Fetch fetch_in(const Grid& g, float px, float py, flo
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
   const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  const float4* q = reinterpret_cast<const float4*>(g.v) +
-                    ((unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1));
-  f.a = __ldg(q);
-  f.b = __ldg(q + pl);
+  const unsigned cell = (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1);
+  if constexpr (kMarchLayout == kLayoutOcto) {
+    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
+    f.a = __ldg(q);
+    f.b = __ldg(q + pl);
+  }
   return f;
 }
 
@@ -748,6 +774,37 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
+// Staged cell c of the padded quad / octo layouts: the x/y 2x2 neighbourhood
+// whose low corner is voxel (a-1, b-1) of slice c_z - 1 (quad), or those of
+// slices c_z - 1 and c_z (octo), every index clamped into the grid.
+template <typename T>
+__device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                               int nx, int ny, int nz, float scale,
+                                               float* __restrict__ out, size_t c) {
+  auto val = [&](size_t idx) {
+    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+  };
+  const int px = nx + 1, py = ny + 1;
+  const int a = (int)(c % px);
+  const size_t r = c / px;
+  const int b = (int)(r % py);
+  const int cz = (int)(r / py);
+  const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
+  const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+  const int k0 = min(max(cz - 1, 0), nz - 1);
+  const size_t b0 = ((size_t)k0 * ny + j0) * nx, b1 = ((size_t)k0 * ny + j1) * nx;
+  const float4 lo = make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1));
+  if constexpr (kMarchLayout == kLayoutOcto) {
+    const int k1 = min(cz, nz - 1);
+    const size_t e0 = ((size_t)k1 * ny + j0) * nx, e1 = ((size_t)k1 * ny + j1) * nx;
+    __stcs(reinterpret_cast<float4*>(out) + 2 * c, lo);
+    __stcs(reinterpret_cast<float4*>(out) + 2 * c + 1,
+           make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1)));
+  } else {
+    __stcs(reinterpret_cast<float4*>(out) + c, lo);
+  }
+}
+
 // One thread per staged cell, writing the layout kMarchLayout of sigma' =
 // scale * rho * [mask == 0] with out-of-grid neighbours clamped to the edge.
 // The quad layout is padded: cell (a, b, c) of an (nx+1) x (ny+1) x (nz+2) array
@@ -761,21 +818,11 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
   auto val = [&](size_t idx) {
     return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
   };
-  if constexpr (kMarchLayout == kLayoutQuad) {
-    const int px = nx + 1, py = ny + 1, pz = nz + 2;
-    const size_t n = (size_t)px * py * pz;
+  if constexpr (kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto) {
+    const size_t n = staged_cells(nx, ny, nz);
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-         c += (size_t)gridDim.x * blockDim.x) {
-      const int a = (int)(c % px);
-      const size_t r = c / px;
-      const int b = (int)(r % py);
-      const int k = min(max((int)(r / py) - 1, 0), nz - 1);
-      const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
-      const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
-      const size_t b0 = ((size_t)k * ny + j0) * nx, b1 = ((size_t)k * ny + j1) * nx;
-      __stcs(reinterpret_cast<float4*>(out) + c,
-             make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1)));
-    }
+         c += (size_t)gridDim.x * blockDim.x)
+      stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, c);
     return;
   }
   const size_t n = (size_t)nx * ny * nz;
@@ -797,7 +844,7 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
 
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s) {
-  const size_t n = staged_floats(nx, ny, nz) / 4;
+  const size_t n = staged_cells(nx, ny, nz);
   int blocks = (int)((n + 255) / 256);
   if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
   if (blocks < 1) blocks = 1;
@@ -860,21 +907,8 @@ template <typename T>
 __device__ __forceinline__ void stage_cells(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
                                             int nx, int ny, int nz, float scale, float* __restrict__ out,
                                             size_t c0, size_t c1) {
-  auto val = [&](size_t idx) {
-    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
-  };
-  const int px = nx + 1, py = ny + 1;
-  for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const int a = (int)(c % px);
-    const size_t r = c / px;
-    const int b = (int)(r % py);
-    const int k = min(max((int)(r / py) - 1, 0), nz - 1);
-    const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
-    const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
-    const size_t b0 = ((size_t)k * ny + j0) * nx, b1 = ((size_t)k * ny + j1) * nx;
-    __stcs(reinterpret_cast<float4*>(out) + c,
-           make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1)));
-  }
+  for (size_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+    stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, c);
 }
 
 constexpr int kStageChunk = 2048;  // staged cells per block
@@ -884,7 +918,7 @@ __global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __res
                                                           int n) {
   const int k = find_start(block_starts, n, blockIdx.x);
   const StageItem& it = items[k];
-  const size_t cells = (size_t)(it.nx + 1) * (it.ny + 1) * (it.nz + 2);
+  const size_t cells = staged_cells(it.nx, it.ny, it.nz);
   const size_t c0 = (size_t)(blockIdx.x - __ldg(block_starts + k)) * kStageChunk;
   const size_t c1 = c0 + kStageChunk < cells ? c0 + kStageChunk : cells;
   if (it.dtype == NSL_F16)
@@ -896,13 +930,14 @@ __global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __res
 }
 
 int stage_batch_blocks(const StageItem& it) {
-  const size_t cells = (size_t)(it.nx + 1) * (it.ny + 1) * (it.nz + 2);
+  const size_t cells = staged_cells(it.nx, it.ny, it.nz);
   return (int)((cells + kStageChunk - 1) / kStageChunk);
 }
 
 cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_starts_dev, int n,
                                int total_blocks, cudaStream_t s) {
-  static_assert(kMarchLayout == kLayoutQuad, "batched staging writes the padded quad layout");
+  static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto,
+                "batched staging writes a padded layout");
   if (total_blocks == 0) return cudaSuccess;
   stage_batch_kernel<<<total_blocks, 256, 0, s>>>(items_dev, block_starts_dev, n);
   return cudaGetLastError();

@@ -87,13 +87,19 @@ constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
 // Staged grid layout (see march.cu): 0 linear, 1 x-pairs, 2 x/y quads.
-constexpr int kLayoutLinear = 0, kLayoutXPair = 1, kLayoutQuad = 2;
+constexpr int kLayoutLinear = 0, kLayoutXPair = 1, kLayoutQuad = 2, kLayoutOcto = 3;
 #ifndef NSL_MARCH_LAYOUT
 #define NSL_MARCH_LAYOUT 2
 #endif
 constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
+// cells of the padded staged layouts: quad (nx+1)(ny+1)(nz+2) of 4 floats,
+// octo (nx+1)(ny+1)(nz+1) of 8 floats
+__host__ __device__ inline size_t staged_cells(int nx, int ny, int nz) {
+  return (size_t)(nx + 1) * (ny + 1) * (nz + (kMarchLayout == kLayoutOcto ? 1 : 2));
+}
 inline size_t staged_floats(int nx, int ny, int nz) {
-  if (kMarchLayout == kLayoutQuad) return (size_t)(nx + 1) * (ny + 1) * (nz + 2) * 4;  // padded
+  if (kMarchLayout == kLayoutQuad) return staged_cells(nx, ny, nz) * 4;
+  if (kMarchLayout == kLayoutOcto) return staged_cells(nx, ny, nz) * 8;
   return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : 2);
 }
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
