@@ -132,6 +132,22 @@ def cpu_oracle_frame(pf, rows, blob_params, c0=16, keep=False):
     return t, rows * pf.camera.width
 
 
+def max_over_ranks(local_ms, dev, ws):
+    """The slowest rank's time (every rank gets it); a no-op for one process."""
+    if ws <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix(frames_all_ranks, pixels_per_frame, max_ms):
+    """Whole-job throughput: the frames every rank completed over the slowest rank's time."""
+    return frames_all_ranks * pixels_per_frame / (max_ms / 1e3) / 1e6
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle as it stands, on host cores."""
     ws, rank, _ = dist_env()
@@ -267,12 +283,9 @@ def main():
     net_ms = [e[2].elapsed_time(e[3]) for e in events]
     shade_ms = [e[3].elapsed_time(e[4]) for e in events]
     total_ms = float(sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev, ws)
     frames = args.steps * ws
-    value = frames * H * W / (total_ms / 1e3) / 1e6
+    value = whole_job_mpix(frames, H * W, total_ms)
 
     # end to end through the host entry point: H2D of the grid + mask, D2H of
     # guide, lightmaps and rgba, every step
