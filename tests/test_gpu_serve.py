@@ -79,10 +79,11 @@ def _server(lib, **kw):
     return lib.Server(blob, lib.server_opts(**kw))
 
 
-def test_serving_alone_equals_mix(lib):
+@pytest.mark.parametrize("precision", [3, 1, 2], ids=["f16", "bf16", "fp8"])
+def test_serving_alone_equals_mix(lib, precision):
     import torch
     plumes = _plumes()
-    srv = _server(lib, hbm_budget_bytes=2 << 30, streams=2, max_batch=8)
+    srv = _server(lib, hbm_budget_bytes=2 << 30, streams=2, max_batch=8, precision=precision)
     ids = [srv.add_plume(p["vol"], p["mask"], 2.0, p["w"], p["h"]) for p in plumes]
     # alone: one request at a time
     alone = {}
@@ -123,7 +124,7 @@ def test_serving_alone_equals_mix(lib):
                 guide=torch.empty((3, p["h"], p["w"]), device="cuda"),
                 lightmaps=torch.empty((8, p["h"], p["w"]), device="cuda"),
                 rgba=torch.empty((4, p["h"], p["w"]), device="cuda"))
-    b.render([item], lib.NSL_PREC_F16)
+    b.render([item], precision)
     torch.cuda.synchronize()
     assert np.array_equal(item["lightmaps"].cpu().numpy(), alone[(ids[0], 2)][0])
     # a request without output buffers writes the plume's resident state
