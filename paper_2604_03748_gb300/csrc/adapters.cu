@@ -221,8 +221,8 @@ __global__ void __launch_bounds__(128) adapters_pass1_group(const __grid_constan
   adapters_pass1_tile<TA>(im.F, P, im.x1, im.partial, im.H, im.W, t % tx, t / tx, t);
 }
 
-// Deterministic reduction of the tile sums: 16 lanes per channel each sum a
-// fixed stride of tiles (Kahan), then a fixed tree; att = W_sca mean + b_sca.
+// Deterministic reduction of the tile sums (fixed order: strided lane sums,
+// then a fixed binary tree); att = W_sca mean + b_sca.
 __device__ __forceinline__ void adapters_reduce_body(const float* __restrict__ partial, int ntiles,
                                                      float inv_count, const AdapterSCA& S,
                                                      float* __restrict__ att);
@@ -245,39 +245,46 @@ __global__ void __launch_bounds__(1024) adapters_reduce_group(const __grid_const
 __device__ __forceinline__ void adapters_reduce_body(const float* __restrict__ partial, int ntiles,
                                                      float inv_count, const AdapterSCA& S,
                                                      float* __restrict__ att) {
-  __shared__ float part[16][4 * C];
+  // 1024 threads = 64 tile lanes x 16 channel quads: lane l sums tiles l, l + 64,
+  // ... of quad q (float4 loads, 16 consecutive threads read one 256-byte tile
+  // row), eight loads in flight; then a fixed binary tree over the 64 lanes.
+  __shared__ float4 part[64][16];
   __shared__ float mean[4 * C];
-  const int ch = threadIdx.x % (4 * C), lane = threadIdx.x / (4 * C);  // 64 channels x 16 lanes
-  float s = 0.f, comp = 0.f;
-  // eight loads in flight ahead of the compensated sums (same order of addition)
-  int t = lane;
-  for (; t + 7 * 16 < ntiles; t += 8 * 16) {
-    float v[8];
+  const int q = threadIdx.x & 15, l = threadIdx.x >> 4;
+  const float4* P = reinterpret_cast<const float4*>(partial);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  int t = l;
+  for (; t + 7 * 64 < ntiles; t += 8 * 64) {
+    float4 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = partial[(size_t)(t + u * 16) * (4 * C) + ch];
+    for (int u = 0; u < 8; ++u) v[u] = P[(size_t)(t + u * 64) * 16 + q];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float y = v[u] - comp;
-      const float w = s + y;
-      comp = (w - s) - y;
-      s = w;
+      s.x += v[u].x; s.y += v[u].y; s.z += v[u].z; s.w += v[u].w;
     }
   }
-  for (; t < ntiles; t += 16) {
-    const float y = partial[(size_t)t * (4 * C) + ch] - comp;
-    const float u = s + y;
-    comp = (u - s) - y;
-    s = u;
+  for (; t < ntiles; t += 64) {
+    const float4 v = P[(size_t)t * 16 + q];
+    s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
   }
-  part[lane][ch] = s;
+  part[l][q] = s;
   __syncthreads();
-  if (lane == 0) {
-    float a8[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a8[k] = part[2 * k][ch] + part[2 * k + 1][ch];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a8[k] = a8[2 * k] + a8[2 * k + 1];
-    mean[ch] = ((a8[0] + a8[1]) + (a8[2] + a8[3])) * inv_count;
+  for (int half = 32; half > 0; half >>= 1) {
+    if (l < half) {
+      const float4 o = part[l + half][q];
+      float4 m = part[l][q];
+      m.x += o.x; m.y += o.y; m.z += o.z; m.w += o.w;
+      part[l][q] = m;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 16) {
+    const float4 m = part[0][threadIdx.x];
+    mean[4 * threadIdx.x + 0] = m.x * inv_count;
+    mean[4 * threadIdx.x + 1] = m.y * inv_count;
+    mean[4 * threadIdx.x + 2] = m.z * inv_count;
+    mean[4 * threadIdx.x + 3] = m.w * inv_count;
   }
   __syncthreads();
   if (threadIdx.x < 4 * C) {
