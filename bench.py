@@ -429,53 +429,55 @@ def bench_serving(nsl, I, dev, args):
     2 batch streams, batches of up to 64, BF16 network), all admitted by one
     warm-up request each, then seeded Poisson arrivals at 2000 req/s (and at
     lower rates) for a fixed time, each request a new camera and light for a
-    uniformly drawn plume.  Latency = submit -> lightmaps ready."""
+    uniformly drawn plume.  Latency = submit -> lightmaps ready.  Two step
+    conventions (the workload states none): 2 voxels for every grid, and n/64
+    voxels (the ratio of the 128^3 and 256^3 workloads)."""
     import torch
     spec = I.serving_plumes_spec(256, seed=5)
     blob = I.pack_blob(I.make_params(16, 0), 16)
-    srv = nsl.Server(blob, nsl.server_opts(hbm_budget_bytes=40 << 30, streams=2, max_batch=64,
-                                           precision=nsl.NSL_PREC_BF16))
     t0 = time.perf_counter()
-    ids = []
-    for p in spec:
-        host = I.blob_fbm_volume_fast(p.n, p.seed, device=dev).cpu().numpy()
-        ids.append(srv.add_plume(host, None, p.step, p.width, p.height))
-    setup_s = time.perf_counter() - t0
-    for pid, p in zip(ids, spec):                     # warm-up: admit every plume once
-        srv.submit(pid, p.camera, p.light)
-    srv.drain()
-    warm = srv.stats()
-    out = {"workload": "256 resident plumes, grids U{32,48,64,96,128,192,256}^3 f32, billboards "
-                       "U{64,128,256,512,1024}^2, perspective fov 40, step 2 voxels, seed 5; Poisson "
-                       "arrivals, plume uniform, new camera and light per request",
-           "budget_bytes": 40 << 30, "streams": 2, "max_batch": 64, "precision": "bf16",
-           "resident_after_warmup": {"plumes": warm["resident_plumes"], "bytes": warm["resident_bytes"]},
-           "setup_s": setup_s, "frame_budgets_ms": [11.1, 16.7], "runs": []}
+    hosts = [I.blob_fbm_volume_fast(p.n, p.seed, device=dev).cpu().numpy() for p in spec]
+    gen_s = time.perf_counter() - t0
     mean_px = float(np.mean([p.width * p.height for p in spec]))
-    for rate in (2000.0, 1000.0, 500.0):
-        reqs = I.poisson_requests(len(spec), rate, args.serve_seconds, seed=5)
-        cams = [(I.perspective_camera(spec[k].n, cs, spec[k].width, spec[k].height), I.random_light(ls))
-                for _, k, cs, ls in reqs]
-        srv.reset_stats()
-        clocks = ClockSampler(torch.cuda.current_device())
-        clocks.start()
-        start = time.perf_counter()
-        for (t, k, _, _), (cam, light) in zip(reqs, cams):
-            while time.perf_counter() - start < t:
-                pass
-            srv.submit(ids[k], cam, light)
-        submit_s = time.perf_counter() - start
-        srv.drain(600000.0)
-        st = srv.stats()
-        clk = clocks.stop()
-        run = {"rate_req_s": rate, "requests": len(reqs), "offered_mpix_s": rate * mean_px / 1e6,
-               "submit_s": submit_s, "value": st["pixels_completed"] / max(st["busy_s"], 1e-9) / 1e6,
-               "unit": "Mpix/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-               "completed": st["completed"], "failed": st["failed"], "batches": st["batches"],
-               "mean_batch": st["mean_batch"], "evictions": st["evictions"],
-               "clocks": clk}
-        out["runs"].append(run)
-    srv.close()
+    out = {"workload": "256 resident plumes, grids U{32,48,64,96,128,192,256}^3 f32, billboards "
+                       "U{64,128,256,512,1024}^2, perspective fov 40, seed 5; Poisson arrivals, plume "
+                       "uniform, new camera and light per request",
+           "budget_bytes": 40 << 30, "streams": 2, "max_batch": 64, "precision": "bf16",
+           "generation_s": gen_s, "frame_budgets_ms": [11.1, 16.7], "steps": {}}
+    for step_name, step_of in (("2 voxels", lambda n: 2.0), ("n/64 voxels", lambda n: n / 64.0)):
+        srv = nsl.Server(blob, nsl.server_opts(hbm_budget_bytes=40 << 30, streams=2, max_batch=64,
+                                               precision=nsl.NSL_PREC_BF16))
+        ids = [srv.add_plume(h, None, step_of(p.n), p.width, p.height) for h, p in zip(hosts, spec)]
+        for pid, p in zip(ids, spec):                 # warm-up: admit every plume once
+            srv.submit(pid, p.camera, p.light)
+        srv.drain()
+        warm = srv.stats()
+        res = {"resident_after_warmup": {"plumes": warm["resident_plumes"], "bytes": warm["resident_bytes"]},
+               "runs": []}
+        for rate in (2000.0, 1000.0, 500.0):
+            reqs = I.poisson_requests(len(spec), rate, args.serve_seconds, seed=5)
+            cams = [(I.perspective_camera(spec[k].n, cs, spec[k].width, spec[k].height), I.random_light(ls))
+                    for _, k, cs, ls in reqs]
+            srv.reset_stats()
+            clocks = ClockSampler(torch.cuda.current_device())
+            clocks.start()
+            start = time.perf_counter()
+            for (t, k, _, _), (cam, light) in zip(reqs, cams):
+                while time.perf_counter() - start < t:
+                    pass
+                srv.submit(ids[k], cam, light)
+            submit_s = time.perf_counter() - start
+            srv.drain(600000.0)
+            st = srv.stats()
+            clk = clocks.stop()
+            res["runs"].append({
+                "rate_req_s": rate, "requests": len(reqs), "offered_mpix_s": rate * mean_px / 1e6,
+                "submit_s": submit_s, "value": st["pixels_completed"] / max(st["busy_s"], 1e-9) / 1e6,
+                "unit": "Mpix/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "completed": st["completed"], "failed": st["failed"], "batches": st["batches"],
+                "mean_batch": st["mean_batch"], "evictions": st["evictions"], "clocks": clk})
+        srv.close()
+        out["steps"][step_name] = res
     return out
 
 
