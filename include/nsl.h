@@ -198,6 +198,20 @@ NSL_API nsl_status nsl_render_frame_host(nsl_ctx* ctx, const void* density_host,
                                  const nsl_march_opts* opts, int precision, float* guide_host,
                                  float* lightmaps_host, float* rgba_host, void* stream);
 
+/* nsl_render_frame_host without the final synchronisation: every copy and
+ * kernel is enqueued on `stream` and the call returns.  With page-locked host
+ * buffers the copies run asynchronously, so frames of two contexts on two
+ * streams overlap one frame's copies with the other's kernels.  The caller
+ * must not change the inputs nor read the outputs until the stream has
+ * completed, and must not issue the next frame of the same context on another
+ * stream before that (the context's device buffers are reused). */
+NSL_API nsl_status nsl_render_frame_host_async(nsl_ctx* ctx, const void* density_host,
+                                       const uint8_t* mask_host, const nsl_camera* cam,
+                                       const nsl_light* lights, int n_lights, float step_voxels,
+                                       const nsl_march_opts* opts, int precision,
+                                       float* guide_host, float* lightmaps_host, float* rgba_host,
+                                       void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched frames: many plumes of different grid and billboard sizes per call.
  * Every stage runs as one launch over all plumes (staging, the guide march,

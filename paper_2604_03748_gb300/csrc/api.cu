@@ -520,11 +520,15 @@ static cudaError_t ensure(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
-nsl_status nsl_render_frame_host(nsl_ctx* c, const void* density_host, const uint8_t* mask_host,
-                                 const nsl_camera* cam, const nsl_light* lights, int n_lights,
-                                 float step, const nsl_march_opts* opts, int precision,
-                                 float* guide_host, float* lm_host, float* rgba_host,
-                                 void* stream) {
+}  // extern "C"
+
+// The host-buffer frame: uploads, the three stages, downloads, all on
+// `stream`; `wait` synchronises the stream before returning.
+static nsl_status render_frame_host(nsl_ctx* c, const void* density_host, const uint8_t* mask_host,
+                                    const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                                    float step, const nsl_march_opts* opts, int precision,
+                                    float* guide_host, float* lm_host, float* rgba_host,
+                                    void* stream, bool wait) {
   if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_render_frame_host: ctx is NULL");
   if (!density_host) return fail(NSL_ERR_INVALID_ARG, "nsl_render_frame_host: NULL density");
   nsl_status st = check_camera(c, cam, "nsl_render_frame_host");
@@ -556,8 +560,28 @@ nsl_status nsl_render_frame_host(nsl_ctx* c, const void* density_host, const uin
     NSL_CUDA_TRY(cudaMemcpyAsync(lm_host, c->h_lm, 8 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (rgba_host)
     NSL_CUDA_TRY(cudaMemcpyAsync(rgba_host, c->h_rgba, 4 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
-  NSL_CUDA_TRY(cudaStreamSynchronize(s));
+  if (wait) NSL_CUDA_TRY(cudaStreamSynchronize(s));
   return NSL_OK;
+}
+
+extern "C" {
+
+nsl_status nsl_render_frame_host(nsl_ctx* c, const void* density_host, const uint8_t* mask_host,
+                                 const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                                 float step, const nsl_march_opts* opts, int precision,
+                                 float* guide_host, float* lm_host, float* rgba_host,
+                                 void* stream) {
+  return render_frame_host(c, density_host, mask_host, cam, lights, n_lights, step, opts, precision,
+                           guide_host, lm_host, rgba_host, stream, true);
+}
+
+nsl_status nsl_render_frame_host_async(nsl_ctx* c, const void* density_host, const uint8_t* mask_host,
+                                       const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                                       float step, const nsl_march_opts* opts, int precision,
+                                       float* guide_host, float* lm_host, float* rgba_host,
+                                       void* stream) {
+  return render_frame_host(c, density_host, mask_host, cam, lights, n_lights, step, opts, precision,
+                           guide_host, lm_host, rgba_host, stream, false);
 }
 
 }  // extern "C"

@@ -22,7 +22,7 @@ NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
 EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_grid",
            "nsl_guiding_map", "nsl_guiding_map_noalloc", "nsl_guide_sample_count",
            "nsl_predict_lightmaps", "nsl_shade", "nsl_render_frame_host", "nsl_last_error",
-           "nsl_status_str", "nsl_batch_create", "nsl_batch_destroy", "nsl_batch_render",
+           "nsl_status_str", "nsl_render_frame_host_async", "nsl_batch_create", "nsl_batch_destroy", "nsl_batch_render",
            "nsl_batch_capture_graph", "nsl_batch_update_graph", "nsl_batch_launch_graph",
            "nsl_batch_set_tuning", "nsl_batch_get_tuning", "nsl_batch_autotune",
            "nsl_default_server_opts", "nsl_server_create", "nsl_server_destroy",
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
     lib.nsl_render_frame_host.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light),
                                           i, f, C.POINTER(nsl_march_opts), i, vp, vp, vp, vp]
+    lib.nsl_render_frame_host_async.argtypes = lib.nsl_render_frame_host.argtypes
+    lib.nsl_render_frame_host_async.restype = C.c_int
     lib.nsl_batch_create.argtypes = [vp, C.c_size_t, i, C.POINTER(vp)]
     lib.nsl_batch_destroy.argtypes = [vp]
     lib.nsl_batch_destroy.restype = None
@@ -297,6 +299,20 @@ def nsl_render_frame_host(ctx, density_np, mask_np, cam, light_list, step, preci
                                        C.byref(opts) if opts is not None else None, int(precision),
                                        hp(guide_np), hp(lightmaps_np), hp(rgba_np), _stream(stream)),
           "nsl_render_frame_host")
+
+
+def nsl_render_frame_host_async(ctx, density_np, mask_np, cam, light_list, step, precision,
+                                guide_np=None, lightmaps_np=None, rgba_np=None, opts=None, stream=None):
+    """nsl_render_frame_host without the final synchronisation (page-locked
+    host buffers make the copies asynchronous); synchronise `stream` before
+    touching the buffers."""
+    def hp(a):
+        return None if a is None else C.c_void_p(a.ctypes.data)
+    check(load().nsl_render_frame_host_async(ctx, hp(density_np), hp(mask_np), C.byref(camera(cam)),
+                                             lights(light_list), len(light_list), float(step),
+                                             C.byref(opts) if opts is not None else None, int(precision),
+                                             hp(guide_np), hp(lightmaps_np), hp(rgba_np), _stream(stream)),
+          "nsl_render_frame_host_async")
 
 
 class Context:

@@ -278,3 +278,39 @@ def test_render_frame_host_matches_device_calls(lib, orc):
     ref_rgba = orc.shade(lm.astype(np.float64), pf.camera, [pf.light])
     assert max(PT.range_err(rgba.astype(np.float64), ref_rgba)) <= PT.TOL_SHADE
     ctx.close()
+
+
+def test_render_frame_host_async_two_contexts(lib):
+    """Frames alternating between two contexts on two streams through the
+    asynchronous host entry point equal the synchronous call, frame by frame
+    (different cameras per frame, page-locked host buffers)."""
+    import torch
+    from paper_2604_03748_gb300 import nsl
+    pf = I.config_plain_64()
+    H, W = pf.camera.height, pf.camera.width
+    cams = [I.orbit_ortho_camera(64, 40 + k, W, H) for k in range(6)]
+    dens = torch.from_numpy(pf.density).pin_memory()
+    ref = []
+    ctx0 = PT.make_ctx(pf)
+    for cam in cams:
+        lm = np.zeros((8, H, W), np.float32)
+        rgba = np.zeros((4, H, W), np.float32)
+        nsl.nsl_render_frame_host(ctx0.ctx, pf.density, None, cam, [pf.light], pf.step, nsl.NSL_PREC_F16,
+                                  None, lm, rgba)
+        ref.append((lm, rgba))
+    ctxs = [ctx0, PT.make_ctx(pf)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [(torch.zeros((8, H, W)).pin_memory(), torch.zeros((4, H, W)).pin_memory()) for _ in cams]
+    for i, cam in enumerate(cams):
+        if i >= 2:
+            streams[i % 2].synchronize()
+        nsl.nsl_render_frame_host_async(ctxs[i % 2].ctx, dens.numpy(), None, cam, [pf.light], pf.step,
+                                        nsl.NSL_PREC_F16, None, outs[i][0].numpy(), outs[i][1].numpy(),
+                                        stream=streams[i % 2])
+    for s in streams:
+        s.synchronize()
+    for (lm, rgba), (glm, grgba) in zip(ref, outs):
+        assert np.array_equal(glm.numpy(), lm)
+        assert np.array_equal(grgba.numpy(), rgba)
+    for c in ctxs:
+        c.close()
