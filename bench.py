@@ -192,8 +192,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="nsl", choices=["nsl", "reference"])
     ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -335,7 +335,7 @@ def main():
         for i in range(4):
             dev_frame(i)
         torch.cuda.synchronize()
-        nf = 2 * max(1, args.steps)
+        nf = 2 * max(1, min(args.steps, 200))
         t0 = time.perf_counter()
         for i in range(nf):
             if i >= 2:
@@ -388,10 +388,18 @@ def main():
                                         and not args.no_cpu_baseline)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+        # whole 512x512 frames until about 10 s of CPU work (at least one)
         t, px, ref = cpu_oracle_frame(pf, 512, flat, keep=True)
+        nfr = 1
+        while t < 10.0 and nfr < 20:
+            t2, px2 = cpu_oracle_frame(pf, 512, flat)
+            t += t2
+            px += px2
+            nfr += 1
         line["cpu_baseline"] = {"value": px / t / 1e6, "unit": "Mpix/s", "cores": os.cpu_count(),
                                 "kind": "oracle",
-                                "sample": "one whole 512x512 frame: FP64 guide march, FP64 network, shade"}
+                                "sample": f"{nfr} whole 512x512 frames ({t:.1f} s): FP64 guide march, "
+                                          "FP64 network, shade"}
         # error of this run's last frame against that oracle frame, per channel,
         # relative to the oracle's range (guide: march; lightmaps: end to end,
         # i.e. the network's precision on top of the march)
@@ -574,9 +582,10 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
             flush.zero_()
             b.launch_graph(stream)
         torch.cuda.synchronize()
+        nsteps = min(args.steps, 30)                  # a batch is ~16 ms of work
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        for k in range(args.steps):
+              for _ in range(nsteps)]
+        for k in range(nsteps):
             flush.zero_()
             ev[k][0].record(stream)
             b.launch_graph(stream)
