@@ -10,10 +10,13 @@
 // depthwise convolution pads its input with zeros), and the SIMT cores run the
 // depthwise 3x3 and the simple gate, each thread one 8-pixel column for two
 // gated channels, writing x1 and the tile's per-channel sums.
-// Pass 2, per 128 pixels: four chained MMAs with block-diagonal weights (the
+// Pass 2, per 128 pixels: three chained MMAs with block-diagonal weights (the
 // four adapters side by side): pw2 on att * x1 (K = 64, N = 64), ffn1 on
-// LN2(y) (N = 128), ffn2 on the gate (N = 64), the heads on z (N = 16, eight
-// used); between them each thread handles its pixel's row.
+// LN2(y) (N = 128), and on the gate g the heads folded through ffn2 (N = 16,
+// eight used): z = y + gamma (W_f2 g + b_f2) only feeds the heads, so
+// W_h z + b_h = W_h y + (W_h diag(gamma) W_f2) g + (W_h (gamma b_f2) + b_h),
+// the first term on the SIMT cores.  Between the MMAs each thread handles its
+// pixel's row.
 // The SCA reduction between the passes is the deterministic SIMT one.
 #include <cmath>
 #include <cstring>
@@ -47,11 +50,10 @@ constexpr int kP1Smem = kP1Bar + 16;
 // pass-2 shared memory (bytes)
 constexpr int kP2W2 = 0;                  // 64 x 64 block-diagonal
 constexpr int kP2F1 = kP2W2 + 64 * 64 * 2;
-constexpr int kP2F2 = kP2F1 + 128 * 64 * 2;
-constexpr int kP2Hd = kP2F2 + 64 * 64 * 2;
+constexpr int kP2Hd = kP2F1 + 128 * 64 * 2;  // folded head on the gate, 16 x 64
 constexpr int kP2A = kP2Hd + 16 * 64 * 2;  // 8 planes x 128 rows x 16 B
 constexpr int kP2Par = kP2A + 8 * 128 * 16;
-constexpr int kP2ParN = 64 + 64 + 128 + 64 + 64 + 16;   // b2, beta, fb1, fb2, gamma, hb
+constexpr int kP2ParN = 64 + 64 + 128 + 16 + 128;   // b2, beta, fb1, head constant, head on y
 constexpr int kP2Att = kP2Par + kP2ParN * 4;
 constexpr int kP2Bar = kP2Att + 64 * 4;
 constexpr int kP2Smem = kP2Bar + 16;
@@ -61,8 +63,7 @@ struct AdapterTcDev {
   const float* p1f;    // [pw1 bias 128][dw weights 128 x 9][dw bias 128]
   const uint8_t* w2;   // 8192 B
   const uint8_t* f1;   // 16384 B
-  const uint8_t* f2;   // 8192 B
-  const uint8_t* hd;   // 2048 B
+  const uint8_t* hd;   // 2048 B: the heads folded through ffn2 and gamma
   const float* p2f;    // kP2ParN floats
 };
 
@@ -319,9 +320,8 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
   const float* b2 = par;
   const float* beta = b2 + 64;
   const float* fb1 = beta + 64;
-  const float* fb2 = fb1 + 128;
-  const float* gamma = fb2 + 64;
-  const float* hb = gamma + 64;
+  const float* hc = fb1 + 128;     // folded head constant [8]
+  const float* hy = hc + 16;       // head weights on y [8][16] (head j reads adapter j / 2)
   float* att = reinterpret_cast<float*>(smem + kP2Att);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP2Bar);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP2Bar + 8);
@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
 
   copy_to_smem(smem + kP2W2, W.w2, 64 * 64 * 2);
   copy_to_smem(smem + kP2F1, W.f1, 128 * 64 * 2);
-  copy_to_smem(smem + kP2F2, W.f2, 64 * 64 * 2);
   copy_to_smem(smem + kP2Hd, W.hd, 16 * 64 * 2);
   copy_to_smem(smem + kP2Par, W.p2f, kP2ParN * 4);
   if (tid == 0) {
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     __syncthreads();  // the previous block is done with att and A
     if (tid < 64) att[tid] = im.att[tid];
     __syncthreads();
-    float f[C], y[4 * C];
+    float f[C], hs[8];
     // stage 1: A = att * x1
     {
       float xv[4 * C];
@@ -419,18 +418,26 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     }
     fetch(blk + (int)gridDim.x);
     if (!(ok = stage(smem + kP2W2, 64, idesc_f16kind(0u, 128, 64)))) break;
-    // stage 2: y = F + beta (pw2 + b2); A = LN2(y) (affine folded into ffn1)
+    // stage 2: y = F + beta (pw2 + b2); the heads' part on y; A = LN2(y)
+    // (affine folded into ffn1)
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      float d[16], n[16];
+      float d[16], y[16], n[16];
       tmem_ld16(lane_base + (uint32_t)(a * 16), d);
 #pragma unroll
-      for (int c = 0; c < C; ++c) y[a * C + c] = fmaf(beta[a * C + c], d[c] + b2[a * C + c], f[c]);
-      norm16(y + a * C, n);
+      for (int c = 0; c < C; ++c) y[c] = fmaf(beta[a * C + c], d[c] + b2[a * C + c], f[c]);
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        float h = hc[2 * a + jj];
+#pragma unroll
+        for (int c = 0; c < C; ++c) h = fmaf(hy[(2 * a + jj) * C + c], y[c], h);
+        hs[2 * a + jj] = h;
+      }
+      norm16(y, n);
       put16(A, 2 * a, tid, n);
     }
     if (!(ok = stage(smem + kP2F1, 128, idesc_f16kind(0u, 128, 128)))) break;
-    // stage 3: gate of ffn1 (channels o and o + 16 of each adapter)
+    // the gate of ffn1 (channels o and o + 16 of each adapter)
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       float u[16], v[16], gt[16];
@@ -440,23 +447,14 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
       for (int c = 0; c < C; ++c) gt[c] = (u[c] + fb1[a * 32 + c]) * (v[c] + fb1[a * 32 + 16 + c]);
       put16(A, 2 * a, tid, gt);
     }
-    if (!(ok = stage(smem + kP2F2, 64, idesc_f16kind(0u, 128, 64)))) break;
-    // stage 4: z = y + gamma (ffn2 + fb2); heads
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float d[16], z[16];
-      tmem_ld16(lane_base + (uint32_t)(a * 16), d);
-#pragma unroll
-      for (int c = 0; c < C; ++c) z[c] = fmaf(gamma[a * C + c], d[c] + fb2[a * C + c], y[a * C + c]);
-      put16(A, 2 * a, tid, z);
-    }
+    // stage 3: the folded heads on the gate, plus the part on y
     if (!(ok = stage(smem + kP2Hd, 16, idesc_f16kind(0u, 128, 16)))) break;
     {
       float d[16];
       tmem_ld16(lane_base, d);
       if (valid) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) im.out[(size_t)plane_of[j] * npix + p] = d[j] + hb[j];
+        for (int j = 0; j < 8; ++j) im.out[(size_t)plane_of[j] * npix + p] = d[j] + hs[j];
       }
     }
   }
@@ -537,25 +535,30 @@ AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* er
       for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 32 + o) * 64 + a * 16 + ci] = p2.f1[a][o][ci];
   pack_b(m, 128, 64, pk);
   w->dev.f1 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
-  m.assign(64 * 64, 0.f);
-  for (int a = 0; a < 4; ++a)
-    for (int co = 0; co < 16; ++co)
-      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 16 + co) * 64 + a * 16 + ci] = p2.f2[a][co][ci];
-  pack_b(m, 64, 64, pk);
-  w->dev.f2 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  // heads folded through ffn2 and gamma: row 2a + j, input channel a*16 + ci,
+  // W' = W_h diag(gamma) W_f2 (double accumulation); constant W_h (gamma b_f2) + b_h
   m.assign(16 * 64, 0.f);
+  std::vector<float> hcst(16, 0.f), hyv(128, 0.f);
   for (int a = 0; a < 4; ++a)
-    for (int j = 0; j < 2; ++j)
-      for (int ci = 0; ci < 16; ++ci) m[(size_t)(a * 2 + j) * 64 + a * 16 + ci] = p2.hw[a][j][ci];
+    for (int j = 0; j < 2; ++j) {
+      double cst = p2.hb[a][j];
+      for (int co = 0; co < 16; ++co) cst += (double)p2.hw[a][j][co] * p2.gamma[a][co] * p2.fb2[a][co];
+      hcst[2 * a + j] = (float)cst;
+      for (int ci = 0; ci < 16; ++ci) {
+        double v = 0.0;
+        for (int co = 0; co < 16; ++co) v += (double)p2.hw[a][j][co] * p2.gamma[a][co] * p2.f2[a][co][ci];
+        m[(size_t)(2 * a + j) * 64 + a * 16 + ci] = (float)v;
+        hyv[(2 * a + j) * 16 + ci] = p2.hw[a][j][ci];
+      }
+    }
   pack_b(m, 16, 64, pk);
   w->dev.hd = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
   std::vector<float> f2s;
   for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.b2[a][c]);
   for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.beta[a][c]);
   for (int a = 0; a < 4; ++a) for (int o = 0; o < 32; ++o) f2s.push_back(p2.fb1[a][o]);
-  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.fb2[a][c]);
-  for (int a = 0; a < 4; ++a) for (int c = 0; c < 16; ++c) f2s.push_back(p2.gamma[a][c]);
-  for (int a = 0; a < 4; ++a) for (int j = 0; j < 2; ++j) f2s.push_back(p2.hb[a][j]);
+  for (int k = 0; k < 16; ++k) f2s.push_back(hcst[k]);
+  for (int k = 0; k < 128; ++k) f2s.push_back(hyv[k]);
   while (f2s.size() < (size_t)kP2ParN) f2s.push_back(0.f);
   w->dev.p2f = static_cast<const float*>(up(f2s.data(), f2s.size() * 4));
   if (*err != cudaSuccess) {
