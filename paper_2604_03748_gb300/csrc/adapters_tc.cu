@@ -34,15 +34,15 @@ constexpr int kTW = 16, kTH = 8;        // pass-1 tile: same tiling as the SIMT 
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kHalo = kHW * kHH;        // 180
 constexpr int kRows = 256;              // A rows: halo pixels padded to 2 x 128
-constexpr int kChS = 184;               // floats per channel of the pw1 buffer (the two
-                                        // half-warps of a warp, two channels apart, land 16 banks apart)
+constexpr int kChS = 184;               // words per gate pair of the pw1 buffer (the two half-
+                                        // warps of a warp, two pairs apart, land 16 banks apart)
 
 // pass-1 shared memory (bytes); pw1 runs in two rounds of two adapters (N = 64)
 constexpr int kP1Threads = 256;
 constexpr int kP1A = 0;                                   // 2 planes x 256 rows x 16 B
 constexpr int kP1B = kP1A + 2 * kRows * 16;               // pw1 B operand, 128 x 32 B
-constexpr int kP1Pw = kP1B + 128 * 32;                    // pw1 output of one round [64][kChS] f32
-constexpr int kP1Dw = kP1Pw + 64 * kChS * 4;              // pw1 bias [128] + dw weights [128][9] + dw bias [128]
+constexpr int kP1Pw = kP1B + 128 * 32;                    // pw1 output of one round: [32 gate pairs][kChS] half2
+constexpr int kP1Dw = kP1Pw + 32 * kChS * 4;              // pw1 bias [128] + dw weights [128][9] + dw bias [128]
 constexpr int kP1In = kP1Dw + (128 * 9 + 128 + 128) * 4;  // inside flags [192]
 constexpr int kP1Bar = kP1In + 192;
 constexpr int kP1Smem = kP1Bar + 16;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
                                                              const AdapterTcDev W, unsigned int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* A = smem + kP1A;
-  float* pw = reinterpret_cast<float*>(smem + kP1Pw);
+  __half2* pw = reinterpret_cast<__half2*>(smem + kP1Pw);   // gate pairs (o, o + 16) of a round
   const float* b1s = reinterpret_cast<const float*>(smem + kP1Dw);
   const float* dww = b1s + 128;
   const float* dwb = dww + 128 * 9;
@@ -217,19 +217,24 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
       }
       phase ^= 1u;
       tc_fence_after();
-      // accumulators -> pw (+ bias; zero outside the image): channel c of the
-      // round is pw1 output 64 rd + c
+      // accumulators -> pw (+ bias; zero outside the image): round channel
+      // al * 32 + o is pw1 output 64 rd + al * 32 + o; outputs o and o + 16 of
+      // adapter 2 rd + al (the gate's two halves) share one half2 word
       {
         const bool inrow = row < kHalo;
         const bool keep = inrow && inside[inrow ? row : 0];
 #pragma unroll 1
-        for (int c = 0; c < 64; c += 16) {
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * 64 + c), v);
+        for (int al = 0; al < 2; ++al) {
+          float v0[16], v1[16];
+          const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * 64 + al * 32);
+          tmem_ld16(t0, v0);
+          tmem_ld16(t0 + 16, v1);
           if (inrow) {
+            const float* bb = b1s + rd * 64 + al * 32;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              pw[(c + j) * kChS + row] = keep ? v[j] + b1s[rd * 64 + c + j] : 0.f;
+            for (int o = 0; o < 16; ++o)
+              pw[(al * 16 + o) * kChS + row] =
+                  keep ? __floats2half2_rn(v0[o] + bb[o], v1[o] + bb[16 + o]) : __floats2half2_rn(0.f, 0.f);
           }
         }
       }
@@ -245,20 +250,20 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
         float sums[2];
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
-          const int cl0 = al * 32 + j0 + jj, cl1 = cl0 + 16;     // channel within the round
-          const int cg0 = rd * 64 + cl0, cg1 = cg0 + 16;          // global pw1 channel
+          const int o = j0 + jj;                             // gated channel of the adapter
+          const int cg0 = rd * 64 + al * 32 + o, cg1 = cg0 + 16;  // global pw1 channels of the pair
           float d0[kTH], d1[kTH];
 #pragma unroll
           for (int y = 0; y < kTH; ++y) {
             d0[y] = dwb[cg0];
             d1[y] = dwb[cg1];
           }
-          const float* q0 = pw + cl0 * kChS + x;
-          const float* q1 = pw + cl1 * kChS + x;
+          const __half2* q = pw + (al * 16 + o) * kChS + x;
 #pragma unroll
           for (int r = 0; r < kHH; ++r) {
-            const float u0 = q0[r * kHW], u1 = q0[r * kHW + 1], u2 = q0[r * kHW + 2];
-            const float v0 = q1[r * kHW], v1 = q1[r * kHW + 1], v2 = q1[r * kHW + 2];
+            const __half2 w0 = q[r * kHW], w1 = q[r * kHW + 1], w2 = q[r * kHW + 2];
+            const float u0 = __low2float(w0), u1 = __low2float(w1), u2 = __low2float(w2);
+            const float v0 = __high2float(w0), v1 = __high2float(w1), v2 = __high2float(w2);
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
               const int y = r - ky;

@@ -344,8 +344,12 @@ __device__ __forceinline__ void conv_epilogue(const ConvImg<T>& a, const float* 
 
 // N tile of a 3x3 layer: all output channels up to 64, and 32 when Cin = 128
 // so that weights + two halo buffers fit in 227 KB of shared memory.
+#ifndef NSL_CONV_NT_MAX
+#define NSL_CONV_NT_MAX 64
+#endif
 __host__ __device__ constexpr int conv_nt(int cin, int cout) {
-  return cin >= 128 ? 32 : (cout > 64 ? 64 : cout);
+  return cin >= 128 ? (NSL_CONV_NT_MAX < 32 ? NSL_CONV_NT_MAX : 32)
+                    : (cout > NSL_CONV_NT_MAX ? NSL_CONV_NT_MAX : cout);
 }
 
 template <int CIN, int COUT, int NT, bool Q8 = false>
