@@ -377,6 +377,36 @@ def main():
         "clocks": clk,
         "host_wall_s": t_host,
     }
+    # the paper's own sampling distance, h = 10 voxels, on the same workload
+    step10 = None
+    if args.e2e_steps > 0:
+        ctx10 = nsl.Context(pf.density.shape, nsl.NSL_F32, blob, W, H)
+        g10 = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+        lm10 = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+        rgba10 = torch.empty((4, H, W), dtype=torch.float32, device=dev)
+
+        def frame10():
+            nsl.nsl_stage_grid(ctx10.ctx, dens, mask, stream=stream)
+            nsl.nsl_guiding_map(ctx10.ctx, None, None, pf.camera, 10.0, g10, opts=opts, stream=stream)
+            nsl.nsl_predict_lightmaps(ctx10.ctx, g10, W, H, prec, lm10, stream=stream)
+            nsl.nsl_shade(ctx10.ctx, lm10, W, H, pf.camera, [pf.light], rgba10, stream=stream)
+        for _ in range(3):
+            frame10()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(5, min(args.steps, 100))):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            frame10()
+            b_.record(stream)
+            ts.append((a_, b_))
+        torch.cuda.synchronize()
+        ms10 = float(np.mean([a_.elapsed_time(b_) for a_, b_ in ts]))
+        step10 = {"value": H * W / (ms10 / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms10,
+                  "samples": ctx10.guide_sample_count(pf.camera, 10.0, opts)}
+        ctx10.close()
+    line["step_10_voxels"] = step10
     ctx.close()
     forms = [f for f in args.forms.split(",") if f and f != "none"]
     if "animated" in forms:
@@ -406,6 +436,22 @@ def main():
         line["err_vs_oracle"] = {
             "guide": range_errs(guide.cpu().numpy(), ref[0]),
             "lightmaps": range_errs(lm.cpu().numpy(), ref[1]),
+        }
+        # reported only: the fine-step (0.25 voxel) six-light reference on the
+        # middle row against the coarse guide's transmittance and the lightmaps
+        # of the untrained network (the physical target of a trained one)
+        import oracle
+        t0 = time.perf_counter()
+        o7 = oracle.reference_lightmaps(pf.density, pf.mask, pf.camera, hf=0.25, rows=(H // 2, H // 2 + 1))
+        r = H // 2
+        g_np, lm_np = guide.cpu().numpy(), lm.cpu().numpy()
+        rng7 = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+        line["vs_fine_reference"] = {
+            "row": r, "oracle_s": time.perf_counter() - t0,
+            "guide_T": rng7(g_np[1, r], o7[6, r]),
+            "lightmaps_six_planes": [rng7(lm_np[c, r], o7[c, r]) for c in range(6)],
+            "lightmaps_T": rng7(lm_np[6, r], o7[6, r]),
+            "note": "untrained network: reported, not a pass criterion",
         }
     if rank == 0:
         print(json.dumps(line), flush=True)

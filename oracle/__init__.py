@@ -81,6 +81,9 @@ def _load():
     lib.nslo_reference_lightmaps.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                              C.c_double, C.POINTER(_Camera), C.c_double,
                                              C.c_double, C.c_void_p]
+    lib.nslo_reference_lightmaps_rows.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                                  C.c_double, C.POINTER(_Camera), C.c_double, C.c_double,
+                                                  C.c_int, C.c_int, C.c_void_p]
     lib.nslo_net_forward.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                      C.c_double, C.c_void_p]
     lib.nslo_net_forward_q8.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
@@ -181,15 +184,18 @@ def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
     return out, samples, flags
 
 
-def reference_lightmaps(density, mask, camera, hf=0.25, sigma_scale=1.0, phase_g=0.0):
-    """Fine-step six-light single-scattering reference: [7,H,W] = +X,-X,+Y,-Y,+Z,-Z,T."""
+def reference_lightmaps(density, mask, camera, hf=0.25, sigma_scale=1.0, phase_g=0.0, rows=None):
+    """Fine-step six-light single-scattering reference: [7,H,W] = +X,-X,+Y,-Y,+Z,-Z,T.
+    rows=(r0, r1) restricts it to image rows [r0, r1) (others stay 0)."""
     lib = _load()
     d, nx, ny, nz = _grid(density)
     m = _mask(mask)
     out = np.zeros((7, camera.height, camera.width), np.float64)
     cam = _cam(camera)
-    rc = lib.nslo_reference_lightmaps(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale),
-                                      C.byref(cam), float(hf), float(phase_g), _ptr(out))
+    r0, r1 = (0, camera.height) if rows is None else rows
+    rc = lib.nslo_reference_lightmaps_rows(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale),
+                                           C.byref(cam), float(hf), float(phase_g), int(r0), int(r1),
+                                           _ptr(out))
     if rc != 0:
         raise ValueError(f"nslo_reference_lightmaps failed ({rc})")
     return out

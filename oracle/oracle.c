@@ -360,12 +360,21 @@ static double light_tau(const field* F, const float p[3], const double s[3], dou
 int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, int ny, int nz,
                              double sigma_scale, const nslo_camera* cam, double hf,
                              double g, double* out) {
+  return nslo_reference_lightmaps_rows(density, mask, nx, ny, nz, sigma_scale, cam, hf, g, 0,
+                                       cam ? cam->height : 0, out);
+}
+
+int nslo_reference_lightmaps_rows(const float* density, const uint8_t* mask, int nx, int ny, int nz,
+                                  double sigma_scale, const nslo_camera* cam, double hf, double g,
+                                  int row0, int row1, double* out) {
   if (!density || !cam || !out || !(hf > 0.0)) return 1;
+  if (row0 < 0 || row1 > cam->height || row0 > row1) return 1;
   field F = {density, mask, nx, ny, nz, sigma_scale, {(float)nx, (float)ny, (float)nz}};
   cam_frame fr;
   cam_setup(cam, &fr);
   const int W = cam->width, H = cam->height;
   const size_t plane = (size_t)W * H;
+  (void)H;
   /* toward-light directions in the camera frame: +X right, -X, +Y up, -Y,
    * +Z back (behind the smoke, along the view direction), -Z front */
   double dirs[6][3];
@@ -375,7 +384,7 @@ int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, 
     dirs[4][k] = fr.f[k]; dirs[5][k] = -(double)fr.f[k];
   }
 #pragma omp parallel for schedule(dynamic, 2)
-  for (int j = 0; j < H; ++j) {
+  for (int j = row0; j < row1; ++j) {
     for (int i = 0; i < W; ++i) {
       size_t pix = (size_t)j * W + i;
       float o[3], d[3], tin, tout;

@@ -63,6 +63,11 @@ int nslo_reference_lightmaps(const float* density, const uint8_t* mask, int nx, 
                              int nz, double sigma_scale, const nslo_camera* cam,
                              double hf, double phase_g, double* out);
 
+/* Same for image rows [row0, row1) only; other rows untouched. */
+int nslo_reference_lightmaps_rows(const float* density, const uint8_t* mask, int nx, int ny,
+                                  int nz, double sigma_scale, const nslo_camera* cam, double hf,
+                                  double phase_g, int row0, int row1, double* out);
+
 /* Lightmap network forward (UNet + 4 NAFBlock adapters), all FP64.
  * guide: [3][H][W]; params: float64 values in the blob order; out: [8][H][W]. */
 int nslo_net_forward(const double* guide, int H, int W, const double* params,

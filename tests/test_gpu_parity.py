@@ -314,3 +314,17 @@ def test_render_frame_host_async_two_contexts(lib):
         assert np.array_equal(grgba.numpy(), rgba)
     for c in ctxs:
         c.close()
+
+
+def test_guide_parity_paper_step_10(lib, orc):
+    """The paper's own sampling distance (h = 10 voxels) on the 512^2 obstacle
+    workload, every pixel."""
+    import dataclasses
+    pf = dataclasses.replace(I.config_obstacle_128(), step=10.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf)
+    o, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= PT.MAX_EXCUSED_FRAC * g[0].size
+    ctx.close()
