@@ -525,7 +525,7 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
       std::fclose(f);
     }
   }
-  const int seg_lens[] = {4, 8, 16};
+  const int seg_lens[] = {4, 6, 8};
   const int conv_ctas[] = {1, 2, 4};
   const int occ = march_segment_blocks_max();
   std::vector<int> march_bps = {0};

@@ -75,7 +75,7 @@ struct MarchPlume {
 #define NSL_MARCH_MIN_BLOCKS 7
 #endif
 #ifndef NSL_MARCH_SEG
-#define NSL_MARCH_SEG 8
+#define NSL_MARCH_SEG 6
 #endif
 constexpr int kMarchSegLen = NSL_MARCH_SEG;  // view steps per segment of the segmented march
 #ifndef NSL_MARCH_TX

@@ -87,7 +87,7 @@ struct nsl_server {
   nsl_server_opts o{};
   int device = 0;
   size_t seg_cap = 0, net_cap = 0, slot_scratch = 0;
-  int seg_len = 8;
+  int seg_len = kMarchSegLen;
   cudaMemPool_t pool = nullptr;
   std::vector<PlumeRec> plumes;
   std::unordered_map<uint64_t, Req> reqs;
