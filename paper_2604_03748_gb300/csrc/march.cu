@@ -172,6 +172,27 @@ __device__ __forceinline__ Fetch fetch_in(const Grid& g, float px, float py, flo
   return f;
 }
 
+// Cell fetch at q = p - 0.5 of a point strictly inside the closed box (no box
+// test, no clamps): floor(q) lies in [-1, n-1] on every axis.
+__device__ __forceinline__ Fetch fetch_q(const Grid& g, float qx, float qy, float qz) {
+  Fetch f;
+  f.in = true;
+  const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+  f.tx = __fsub_rn(qx, flx);
+  f.ty = __fsub_rn(qy, fly);
+  f.tz = __fsub_rn(qz, flz);
+  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+  const unsigned cell = (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1);
+  if constexpr (kMarchLayout == kLayoutOcto) {
+    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
+    f.a = __ldg(q);
+    f.b = __ldg(q + pl);
+  }
+  return f;
+}
+
 __device__ __forceinline__ float interp(const Fetch& f) {
   const float c00 = fmaf(f.tx, f.a.y - f.a.x, f.a.x);
   const float c10 = fmaf(f.tx, f.a.w - f.a.z, f.a.z);
@@ -250,7 +271,77 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
     return;
   }
 #endif
-#if NSL_SHADOW_FLAT
+#if NSL_SHADOW_V2
+  // Samples 1..K-1 of a ray lie strictly inside the closed box: K h <= t_exit
+  // (up to one rounding), so (K-1) h falls short of every face crossing by h,
+  // far more than the rounding of p + k h s for any step above 1e-3 voxel.
+  // They need no box test, and their cell coordinates may be taken from
+  // q = (p - 0.5) + k h s (the trilinear value is continuous in q).  The last
+  // sample of each ray can lie on or just past the exit face: it is taken at
+  // the exact position p + k h s, with the box test, after the others.
+  (void)K;
+  const int Mt = Kt > 0 ? Kt - 1 : 0, Mb = Kb > 0 ? Kb - 1 : 0;
+  const int Mall = Mt + Mb;
+  const float qx0 = __fsub_rn(px, 0.5f), qy0 = __fsub_rn(py, 0.5f), qz0 = __fsub_rn(pz, 0.5f);
+  int j = 1;
+  while (j <= Mall) {
+    const bool hasB = j + 1 <= Mall;
+    const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice
+    const bool tA = j <= Mt, tB = j2 <= Mt;
+    // signed step count: negative along the bottom ray (direction -u)
+    const float khA = __fmul_rn((float)(tA ? j : Mt - j), h);
+    const float khB = __fmul_rn((float)(tB ? j2 : Mt - j2), h);
+    const Fetch fA = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khA, u[0])), __fadd_rn(qy0, __fmul_rn(khA, u[1])),
+                             __fadd_rn(qz0, __fmul_rn(khA, u[2])));
+    const Fetch fB = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khB, u[0])), __fadd_rn(qy0, __fmul_rn(khB, u[1])),
+                             __fadd_rn(qz0, __fmul_rn(khB, u[2])));
+    const float vA = interp(fA), vB = interp(fB);
+    int jn = j + 2;
+    if (tA) {
+      taut = fmaf(vA, h, taut);
+      if (kCount) ++nsamp;
+      if (taut > tau_lim) {
+        at = false;
+        jn = Mt + 1;               // top ray done; sample B (if bottom) is taken next
+      } else if (hasB) {
+        if (tB) {
+          taut = fmaf(vB, h, taut);
+          if (kCount) ++nsamp;
+          if (taut > tau_lim) { at = false; jn = Mt + 1; }
+        } else {
+          taub = fmaf(vB, h, taub);
+          if (kCount) ++nsamp;
+          if (taub > tau_lim) { ab = false; break; }
+        }
+      }
+    } else {
+      taub = fmaf(vA, h, taub);
+      if (kCount) ++nsamp;
+      if (taub > tau_lim) { ab = false; break; }
+      if (hasB) {
+        taub = fmaf(vB, h, taub);
+        if (kCount) ++nsamp;
+        if (taub > tau_lim) { ab = false; break; }
+      }
+    }
+    j = jn;
+  }
+  if (at || ab) {
+    const float kt = __fmul_rn((float)Kt, h), kb = __fmul_rn((float)Kb, h);
+    const Fetch ft = fetch(g, __fadd_rn(px, __fmul_rn(kt, u[0])), __fadd_rn(py, __fmul_rn(kt, u[1])),
+                           __fadd_rn(pz, __fmul_rn(kt, u[2])));
+    const Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kb, u[0])), __fsub_rn(py, __fmul_rn(kb, u[1])),
+                           __fsub_rn(pz, __fmul_rn(kb, u[2])));
+    if (at) {
+      taut = fmaf(interp(ft), h, taut);
+      if (kCount) ++nsamp;
+    }
+    if (ab) {
+      taub = fmaf(interp(fb), h, taub);
+      if (kCount) ++nsamp;
+    }
+  }
+#elif NSL_SHADOW_FLAT
 #if NSL_SHADOW_NOCLAMP
 #define SHADOW_FETCH fetch_in
 #else

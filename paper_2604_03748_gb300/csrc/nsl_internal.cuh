@@ -62,6 +62,9 @@ struct MarchPlume {
   float* seg_L;       // [segment][pixel] partial guide radiance
 };
 
+#ifndef NSL_SHADOW_V2
+#define NSL_SHADOW_V2 1   // box test only on the last sample of each shadow ray
+#endif
 #ifndef NSL_SHADOW_FLAT
 #define NSL_SHADOW_FLAT 1   // top and bottom shadow rays as one two-sample-per-step sequence
 #endif
