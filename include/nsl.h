@@ -61,7 +61,10 @@ enum { NSL_CAM_ORTHO = 0, NSL_CAM_PERSP = 1 };
 typedef struct nsl_ctx nsl_ctx; /* opaque, library-owned */
 
 typedef struct {
-  int nx, ny, nz;     /* grid size in voxels, each in [1, 4096] */
+  int nx, ny, nz;     /* grid size in voxels, each in [1, 4096], with
+                         (nx+1)(ny+1)(nz+2) < 2^32 (the staged cells the
+                         march addresses with 32-bit indices); other sizes
+                         are rejected with NSL_ERR_INVALID_ARG */
   int dtype;          /* NSL_F32 or NSL_F16 */
   float sigma_scale;  /* extinction = sigma_scale * density (albedo 1) */
 } nsl_grid_desc;

@@ -159,8 +159,7 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   if (!out) return fail(NSL_ERR_INVALID_ARG, "nsl_create: out is NULL");
   *out = nullptr;
   if (!grid || !blob) return fail(NSL_ERR_INVALID_ARG, "nsl_create: NULL grid or blob");
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 4096 || grid->ny > 4096 ||
-      grid->nz > 4096)
+  if (!grid_dims_ok(grid->nx, grid->ny, grid->nz))
     return fail(NSL_ERR_INVALID_ARG, "nsl_create: grid dims out of range");
   if (grid->dtype != NSL_F32 && grid->dtype != NSL_F16)
     return fail(NSL_ERR_INVALID_ARG, "nsl_create: bad density dtype %d", grid->dtype);

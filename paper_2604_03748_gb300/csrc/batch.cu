@@ -106,8 +106,7 @@ nsl_status validate_plume(const nsl_plume& pl, int k, bool prestaged) {
   char fn[64];
   std::snprintf(fn, sizeof fn, "nsl_batch: plume %d", k);
   const nsl_grid_desc& g = pl.grid;
-  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.nx > 4096 || g.ny > 4096 || g.nz > 4096 ||
-      (g.dtype != NSL_F32 && g.dtype != NSL_F16) || !(g.sigma_scale >= 0.f))
+  if (!grid_dims_ok(g.nx, g.ny, g.nz) || (g.dtype != NSL_F32 && g.dtype != NSL_F16) || !(g.sigma_scale >= 0.f))
     return fail(NSL_ERR_INVALID_ARG, "%s: bad grid", fn);
   if ((!pl.density_dev && !prestaged) || !pl.guide_dev || !pl.lightmaps_dev)
     return fail(NSL_ERR_INVALID_ARG, "%s: NULL buffer", fn);

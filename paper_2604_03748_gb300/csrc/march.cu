@@ -291,10 +291,15 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
     // signed step count: negative along the bottom ray (direction -u)
     const float khA = __fmul_rn((float)(tA ? j : Mt - j), h);
     const float khB = __fmul_rn((float)(tB ? j2 : Mt - j2), h);
+#if NSL_SHADOW_QFMA
+    const Fetch fA = fetch_q(g, fmaf(khA, u[0], qx0), fmaf(khA, u[1], qy0), fmaf(khA, u[2], qz0));
+    const Fetch fB = fetch_q(g, fmaf(khB, u[0], qx0), fmaf(khB, u[1], qy0), fmaf(khB, u[2], qz0));
+#else
     const Fetch fA = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khA, u[0])), __fadd_rn(qy0, __fmul_rn(khA, u[1])),
                              __fadd_rn(qz0, __fmul_rn(khA, u[2])));
     const Fetch fB = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khB, u[0])), __fadd_rn(qy0, __fmul_rn(khB, u[1])),
                              __fadd_rn(qz0, __fmul_rn(khB, u[2])));
+#endif
     const float vA = interp(fA), vB = interp(fB);
     int jn = j + 2;
     if (tA) {
@@ -875,9 +880,10 @@ __device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const 
   auto val = [&](size_t idx) {
     return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
   };
-  const int px = nx + 1, py = ny + 1;
-  const int a = (int)(c % px);
-  const size_t r = c / px;
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u;
+  const unsigned c32 = (unsigned)c;   // staged cells < 2^32 (grids up to 1024^3)
+  const int a = (int)(c32 % px);
+  const unsigned r = c32 / px;
   const int b = (int)(r % py);
   const int cz = (int)(r / py);
   const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
@@ -888,11 +894,11 @@ __device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const 
   if constexpr (kMarchLayout == kLayoutOcto) {
     const int k1 = min(cz, nz - 1);
     const size_t e0 = ((size_t)k1 * ny + j0) * nx, e1 = ((size_t)k1 * ny + j1) * nx;
-    __stcs(reinterpret_cast<float4*>(out) + 2 * c, lo);
-    __stcs(reinterpret_cast<float4*>(out) + 2 * c + 1,
-           make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1)));
+    reinterpret_cast<float4*>(out)[2 * c] = lo;
+    reinterpret_cast<float4*>(out)[2 * c + 1] =
+        make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1));
   } else {
-    __stcs(reinterpret_cast<float4*>(out) + c, lo);
+    reinterpret_cast<float4*>(out)[c] = lo;
   }
 }
 

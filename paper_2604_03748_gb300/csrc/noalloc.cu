@@ -59,8 +59,7 @@ extern "C" nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const v
                                               float* guide, void* stream) {
   if (!grid || !density || !cam || !guide)
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: NULL argument");
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 4096 || grid->ny > 4096 ||
-      grid->nz > 4096 || (grid->dtype != NSL_F32 && grid->dtype != NSL_F16) ||
+  if (!grid_dims_ok(grid->nx, grid->ny, grid->nz) || (grid->dtype != NSL_F32 && grid->dtype != NSL_F16) ||
       !(grid->sigma_scale >= 0.f) || !std::isfinite(grid->sigma_scale))
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: bad grid description");
   const size_t need = staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float);

@@ -65,6 +65,9 @@ struct MarchPlume {
 #ifndef NSL_SHADOW_V2
 #define NSL_SHADOW_V2 1   // box test only on the last sample of each shadow ray
 #endif
+#ifndef NSL_SHADOW_QFMA
+#define NSL_SHADOW_QFMA 1   // in-ray cell coordinates by one fused multiply-add per axis
+#endif
 #ifndef NSL_SHADOW_FLAT
 #define NSL_SHADOW_FLAT 1   // top and bottom shadow rays as one two-sample-per-step sequence
 #endif
@@ -99,6 +102,12 @@ constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
 // octo (nx+1)(ny+1)(nz+1) of 8 floats
 __host__ __device__ inline size_t staged_cells(int nx, int ny, int nz) {
   return (size_t)(nx + 1) * (ny + 1) * (nz + (kMarchLayout == kLayoutOcto ? 1 : 2));
+}
+// Grid sizes the march accepts: every axis in [1, 4096] and fewer than 2^32
+// staged cells (the march addresses staged cells with 32-bit indices).
+inline bool grid_dims_ok(int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return false;
+  return staged_cells(nx, ny, nz) < ((size_t)1 << 32);
 }
 inline size_t staged_floats(int nx, int ny, int nz) {
   if (kMarchLayout == kLayoutQuad) return staged_cells(nx, ny, nz) * 4;

@@ -358,8 +358,7 @@ void worker_main(nsl_server* S) {
 }
 
 nsl_status check_grid(const nsl_grid_desc* g) {
-  if (!g || g->nx < 1 || g->ny < 1 || g->nz < 1 || g->nx > 4096 || g->ny > 4096 || g->nz > 4096 ||
-      (g->dtype != NSL_F32 && g->dtype != NSL_F16) || !(g->sigma_scale >= 0.f))
+  if (!g || !grid_dims_ok(g->nx, g->ny, g->nz) || (g->dtype != NSL_F32 && g->dtype != NSL_F16) || !(g->sigma_scale >= 0.f))
     return fail(NSL_ERR_INVALID_ARG, "nsl_server_add_plume: bad grid description");
   return NSL_OK;
 }

@@ -52,3 +52,14 @@ def test_create_rejects_bad_blob_without_touching_the_gpu():
     with pytest.raises(nsl.NslError) as ei:
         nsl.nsl_create(8, 8, 8, nsl.NSL_F32, 1.0, blob8, 64, 64)
     assert ei.value.status == nsl.NSL_ERR_UNSUPPORTED
+
+
+def test_create_rejects_grids_past_32_bit_cell_indices_without_touching_the_gpu():
+    """Grid dimensions are checked before any CUDA call: each axis in
+    [1, 4096] and (nx+1)(ny+1)(nz+2) staged cells below 2^32."""
+    from paper_2604_03748_gb300 import inputs as I, nsl
+    blob = I.pack_blob(I.make_params(16), 16)
+    for dims in ((0, 8, 8), (8, 4097, 8), (2048, 2048, 1024), (4096, 4096, 300)):
+        with pytest.raises(nsl.NslError) as ei:
+            nsl.nsl_create(*dims, nsl.NSL_F32, 1.0, blob, 64, 64)
+        assert ei.value.status == nsl.NSL_ERR_INVALID_ARG, dims
