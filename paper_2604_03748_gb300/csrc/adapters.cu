@@ -237,6 +237,8 @@ __global__ void __launch_bounds__(1024) adapters_reduce(const float* __restrict_
 template <typename TA>
 __global__ void __launch_bounds__(1024) adapters_reduce_group(const __grid_constant__ AdapterGroupArgs<TA> G,
                                                               const __grid_constant__ AdapterSCA S) {
+  pdl_wait();      // the partial sums come from pass 1
+  pdl_trigger();
   const AdapterImg<TA>& im = G.img[blockIdx.x];
   adapters_reduce_body(im.partial, G.tile_start[blockIdx.x + 1] - G.tile_start[blockIdx.x],
                        1.f / ((float)im.H * (float)im.W), S, im.att);
@@ -479,8 +481,7 @@ cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const Adapter
     tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
   }
   G.tile_start[n] = tiles;
-  adapters_reduce_group<TA><<<n, 1024, 0, s>>>(G, prm.sca);
-  return cudaGetLastError();
+  return launch_pdl(adapters_reduce_group<TA>, dim3(n), dim3(1024), 0, s, G, prm.sca);
 }
 template cudaError_t adapters_reduce_only_group<__half>(const AdapterParamSet&, const AdapterImg<__half>*,
                                                         int, cudaStream_t);

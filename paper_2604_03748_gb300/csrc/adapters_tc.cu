@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  pdl_wait();      // F comes from the last convolution
+  pdl_trigger();
   constexpr uint32_t idesc = idesc_f16kind(0u, 128, 64);
   const int total = G.tile_start[G.nimg];
   uint32_t phase = 0;
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
   }
   tc_fence_before();
   __syncthreads();
+  pdl_trigger_end();
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
@@ -390,6 +393,8 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
 #pragma unroll
     for (int q = 0; q < 2; ++q) rf[q] = __ldg(reinterpret_cast<const uint4*>(m.F + (size_t)pp * C) + q);
   };
+  pdl_wait();      // x1 and the attention weights come from pass 1 and the reduction
+  pdl_trigger();
   fetch(blockIdx.x);
 
 #pragma unroll 1
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
   if (!ok) record_error(err, 0x200u);
   tc_fence_before();
   __syncthreads();
+  pdl_trigger_end();
   if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
@@ -614,13 +620,11 @@ cudaError_t adapters_tc_run_group(const AdapterTcWeights* w, const AdapterParamS
   G.tile_start[n] = tiles;
   G.px_start[n] = blocks;
   const int g1 = tiles < kNumSMs * occ1 ? tiles : kNumSMs * occ1;
-  adapters_p1_tc<TA><<<g1, kP1Threads, kP1Smem, s>>>(G, w->dev, err);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(adapters_p1_tc<TA>, dim3(g1), dim3(kP1Threads), (size_t)kP1Smem, s, G, w->dev, err);
   if (e != cudaSuccess) return e;
   if ((e = adapters_reduce_only_group<TA>(prm, imgs, n, s)) != cudaSuccess) return e;
   const int g2 = blocks < kNumSMs * occ2 ? blocks : kNumSMs * occ2;
-  adapters_p2_tc<TA><<<g2, 128, kP2Smem, s>>>(G, w->dev, err);
-  return cudaGetLastError();
+  return launch_pdl(adapters_p2_tc<TA>, dim3(g2), dim3(128), (size_t)kP2Smem, s, G, w->dev, err);
 }
 
 template cudaError_t adapters_tc_run_group<__half>(const AdapterTcWeights*, const AdapterParamSet&,

@@ -90,6 +90,8 @@ struct ConvGroupArgs {
 
 template <typename TOut>
 __global__ void __launch_bounds__(128) first_conv_group_kernel(const __grid_constant__ ConvGroupArgs G) {
+  pdl_wait();      // the guide comes from the march
+  pdl_trigger();
   int lo = 0, hi = G.nimg - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -377,8 +379,7 @@ cudaError_t simt_first_conv_group(const NetF32Weights* w, const NetImage* imgs, 
     tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
   }
   G.tile_start[n] = tiles;
-  first_conv_group_kernel<T><<<tiles, 128, 0, s>>>(G);
-  return cudaGetLastError();
+  return launch_pdl(first_conv_group_kernel<T>, dim3(tiles), dim3(128), 0, s, G);
 }
 template cudaError_t simt_first_conv_group<__nv_bfloat16>(const NetF32Weights*, const NetImage*,
                                                           __nv_bfloat16* const*, float* const*, int,

@@ -410,6 +410,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       *reinterpret_cast<uint4*>(halo + (e / (kPlane / 16)) * Cfg::HBYTES + kPlane + (e % (kPlane / 16)) * 16) =
           make_uint4(0, 0, 0, 0);
   }
+  pdl_wait();      // the input tiles come from the previous layer
+  pdl_trigger();
   // prefetch the first S-1 halos while the weights arrive
   auto issue = [&](int k) {
     if (k < nmine) {
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   cp_async_wait<0>();
   tc_fence_before();
   __syncthreads();
+  pdl_trigger_end();
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
@@ -511,9 +514,23 @@ struct TcConvTArgs {
   unsigned int* err;
 };
 
-template <int CIN, int COUT, bool Q8 = false>
+// CTAs that share one input tile of transposed convolution l (0: 128 -> 64
+// channels, 1: 64 -> 32, 2: 32 -> 16), each taking N / split of the
+// [sub-position][co] columns: the low-resolution layers have few tiles.
+#ifndef NSL_UP_SPLIT0
+#define NSL_UP_SPLIT0 4
+#endif
+#ifndef NSL_UP_SPLIT1
+#define NSL_UP_SPLIT1 2
+#endif
+#ifndef NSL_UP_SPLIT2
+#define NSL_UP_SPLIT2 1
+#endif
+constexpr int kUpSplit[3] = {NSL_UP_SPLIT0, NSL_UP_SPLIT1, NSL_UP_SPLIT2};
+
+template <int CIN, int COUT, bool Q8 = false, int NS = 1>
 struct ConvTCfg {
-  static constexpr int N = 4 * COUT;
+  static constexpr int N = 4 * COUT / NS;     // columns of one CTA
   static constexpr int G = Q8 ? CIN / 16 : CIN / 8;     // 16-byte planes (CIN >= 32)
   static constexpr int APLANE = 128 * 16;
   static constexpr int WBYTES = (G / 2) * N * 32;
@@ -523,9 +540,10 @@ struct ConvTCfg {
   static constexpr int SMEM = WBYTES + 2 * ABYTES + 64;
 };
 
-template <typename T, int CIN, int COUT, bool Q8>
+template <typename T, int CIN, int COUT, bool Q8, int NS>
 __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
-  using Cfg = ConvTCfg<CIN, COUT, Q8>;
+  using Cfg = ConvTCfg<CIN, COUT, Q8, NS>;
+  static_assert((4 * COUT) % NS == 0 && Cfg::N % 16 == 0, "column split");
   static_assert(!Q8 || CIN >= 32, "FP8 transposed convolution needs K >= 32");
   constexpr int N = Cfg::N;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -549,11 +567,15 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   const uint32_t tmem = *slot;
   if (tid == 0) {
     mbar_expect_tx(&bars[0], Cfg::WBYTES);
+    // this CTA's column block: the weights are packed block-major
+    const uint8_t* wsrc = a.wpack + (size_t)blockIdx.y * Cfg::WBYTES;
     for (int off = 0; off < Cfg::WBYTES; off += 32768) {
       const int n = Cfg::WBYTES - off < 32768 ? Cfg::WBYTES - off : 32768;
-      bulk_g2s(wsm + off, a.wpack + off, (uint32_t)n, &bars[0]);
+      bulk_g2s(wsm + off, wsrc + off, (uint32_t)n, &bars[0]);
     }
   }
+  pdl_wait();
+  pdl_trigger();
   bool ok = mbar_wait(&bars[0], 0);
   if (!ok) record_error(a.err, 4u);
 
@@ -576,7 +598,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
     for (int c = 0; c < N; c += 16) {
       float v[16];
       tmem_ld16(tacc + c, v);
-      const int k = c / COUT, co = c % COUT;
+      const int n = (int)blockIdx.y * N + c, k = n / COUT, co = n % COUT;
       const int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
       __align__(16) typename Half<T>::T2 h[8];
 #pragma unroll
@@ -677,6 +699,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   }
   tc_fence_before();
   __syncthreads();
+  pdl_trigger_end();
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
@@ -760,22 +783,25 @@ static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uin
 
 // Pack a transposed-conv weight [cin][cout][2][2] into B tiles with rows
 // n = (2a+b)*cout + co and K = cin.
+// The columns are cut into ns blocks of N / ns (one per CTA of a tile), each
+// block stored whole: [block][K step][N/ns rows x 32 bytes].
 template <typename T>
-static void pack_convT(const float* w, int cin, int cout, std::vector<uint8_t>& out) {
-  const int N = 4 * cout;
-  const size_t slice = (size_t)N * 32;
-  out.assign((size_t)(cin / 16) * slice, 0);
-  for (int j = 0; j < cin / 16; ++j) {
-    uint8_t* s = out.data() + j * slice;
-    for (int n = 0; n < N; ++n)
-      for (int k = 0; k < 16; ++k) {
-        const int kpos = n / cout, co = n % cout, ci = j * 16 + k;
-        const float v = w[((size_t)ci * cout + co) * 4 + kpos];
-        T b = Half<T>::from(v);
-        const size_t off = (size_t)(k / 8) * N * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
-        std::memcpy(s + off, &b, 2);
-      }
-  }
+static void pack_convT(const float* w, int cin, int cout, int ns, std::vector<uint8_t>& out) {
+  const int N = 4 * cout, Nb = N / ns, KS = cin / 16;
+  const size_t slice = (size_t)Nb * 32;
+  out.assign((size_t)ns * KS * slice, 0);
+  for (int sb = 0; sb < ns; ++sb)
+    for (int j = 0; j < KS; ++j) {
+      uint8_t* s = out.data() + ((size_t)sb * KS + j) * slice;
+      for (int r = 0; r < Nb; ++r)
+        for (int k = 0; k < 16; ++k) {
+          const int n = sb * Nb + r, kpos = n / cout, co = n % cout, ci = j * 16 + k;
+          const float v = w[((size_t)ci * cout + co) * 4 + kpos];
+          T b = Half<T>::from(v);
+          const size_t off = (size_t)(k / 8) * Nb * 16 + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+          std::memcpy(s + off, &b, 2);
+        }
+    }
 }
 
 // Nearest-even E4M3 code of a float with saturation to the largest finite
@@ -833,11 +859,11 @@ static void pack_conv_q8(const float* w, int cin, int cout, int NT, std::vector<
 // FP8 packing of a transposed-conv weight [cin][cout][2][2]: rows
 // n = (2a+b)*cout + co, K = cin in steps of 32; scale per output channel over
 // ci and the four kernel positions.
-static void pack_convT_q8(const float* w, int cin, int cout, std::vector<uint8_t>& out,
+static void pack_convT_q8(const float* w, int cin, int cout, int ns, std::vector<uint8_t>& out,
                           std::vector<float>& scale) {
-  const int N = 4 * cout;
-  const size_t slice = (size_t)N * 32;
-  out.assign((size_t)(cin / 32) * slice, 0);
+  const int N = 4 * cout, Nb = N / ns, KS = cin / 32;
+  const size_t slice = (size_t)Nb * 32;
+  out.assign((size_t)ns * KS * slice, 0);
   scale.resize(cout);
   for (int co = 0; co < cout; ++co) {
     float amax = 0.f;
@@ -845,15 +871,16 @@ static void pack_convT_q8(const float* w, int cin, int cout, std::vector<uint8_t
       for (int k = 0; k < 4; ++k) amax = std::fmax(amax, std::fabs(w[((size_t)ci * cout + co) * 4 + k]));
     scale[co] = amax > 0.f ? amax / 448.0f : 1.0f;
   }
-  for (int j = 0; j < cin / 32; ++j) {
-    uint8_t* s = out.data() + j * slice;
-    for (int n = 0; n < N; ++n)
-      for (int k = 0; k < 32; ++k) {
-        const int kpos = n / cout, co = n % cout, ci = j * 32 + k;
-        const float v = w[((size_t)ci * cout + co) * 4 + kpos] / scale[co];
-        s[(size_t)(k / 16) * N * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 16)] = e4m3_code(v);
-      }
-  }
+  for (int sb = 0; sb < ns; ++sb)
+    for (int j = 0; j < KS; ++j) {
+      uint8_t* s = out.data() + ((size_t)sb * KS + j) * slice;
+      for (int r = 0; r < Nb; ++r)
+        for (int k = 0; k < 32; ++k) {
+          const int n = sb * Nb + r, kpos = n / cout, co = n % cout, ci = j * 32 + k;
+          const float v = w[((size_t)ci * cout + co) * 4 + kpos] / scale[co];
+          s[(size_t)(k / 16) * Nb * 16 + (r / 8) * 128 + (r % 8) * 16 + (k % 16)] = e4m3_code(v);
+        }
+    }
 }
 
 }  // namespace
@@ -894,7 +921,7 @@ static void fill_weights(NetTcWeights* w, const float* hp, const NetLayout& L, c
     w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
   }
   for (int l = 0; l < 3; ++l) {
-    pack_convT<T>(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk);
+    pack_convT<T>(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], kUpSplit[l], pk);
     w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
     w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
   }
@@ -913,7 +940,7 @@ static void fill_weights_q8(NetTcWeights* w, const float* hp, const NetLayout& L
     w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
   }
   for (int l = 0; l < 3; ++l) {
-    pack_convT_q8(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], pk, sc);
+    pack_convT_q8(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], kUpSplit[l], pk, sc);
     w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
     w->up_s[l] = dev_copy(w, sc.data(), sc.size(), err);
     w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
@@ -1025,18 +1052,19 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8><<<dim3(grid, COUT / NT), 128, L.smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8>, dim3(grid, COUT / NT), dim3(128),
+                    (size_t)L.smem, s, a);
 }
 
-template <typename T, int CIN, int COUT, bool Q8>
-cudaError_t run_convT(const NetTcWeights* w, int l, int n, const T* const* ins, T* const* outs,
+template <typename T, int CIN, int COUT, bool Q8, int LAYER>
+cudaError_t run_convT(const NetTcWeights* w, int n, const T* const* ins, T* const* outs,
                       const int* H, const int* W, AmaxSlots am, unsigned int* err, cudaStream_t s) {
-  using Cfg = ConvTCfg<CIN, COUT, Q8>;
+  constexpr int NS = kUpSplit[LAYER];
+  using Cfg = ConvTCfg<CIN, COUT, Q8, NS>;
   static Launch L;
   static bool init = false;
   if (!init) {
-    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT, Q8>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
+    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT, Q8, NS>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
     if (e != cudaSuccess) return e;
     init = true;
   }
@@ -1051,14 +1079,13 @@ cudaError_t run_convT(const NetTcWeights* w, int l, int n, const T* const* ins, 
     ntiles += tx * ty;
   }
   a.total_tiles = ntiles;
-  a.wpack = w->up_w[l];
-  a.bias = w->up_b[l];
-  a.wscale = w->up_s[l];
+  a.wpack = w->up_w[LAYER];
+  a.bias = w->up_b[LAYER];
+  a.wscale = w->up_s[LAYER];
   a.err = err;
-  int grid = kNumSMs * L.per_sm;
+  int grid = (kNumSMs * L.per_sm + NS - 1) / NS;
   if (grid > ntiles) grid = ntiles;
-  convT_tc_kernel<T, CIN, COUT, Q8><<<grid, 128, L.smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(convT_tc_kernel<T, CIN, COUT, Q8, NS>, dim3(grid, NS), dim3(128), (size_t)L.smem, s, a);
 }
 
 template <typename T, bool Q8>
@@ -1106,13 +1133,13 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
   SET(l2a, nullptr, s3); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], slots(4, -1, 5), err, s)));
   SET(s3, nullptr, l3a); TRY((run_conv<T, 64, 128, TC_POOL, Q8>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], slots(5, -1, 6), err, s)));
   SET(l3a, nullptr, l3b); TRY((run_conv<T, 128, 128, TC_PLAIN, Q8>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], slots(6, -1, 7), err, s)));
-  SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64, Q8>(w, 0, n, in, out, Hs[3], Ws[3], slots(7, -1, 14), err, s)));
+  SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64, Q8, 0>(w, n, in, out, Hs[3], Ws[3], slots(7, -1, 14), err, s)));
   SET(l2a, B[k].s3, l2b); TRY((run_conv<T, 128, 64, TC_CONCAT, Q8>(w, 8, n, in, sk, out, Hs[2], Ws[2], slots(14, 5, 8), err, s)));
   SET(l2b, nullptr, l2a); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], slots(8, -1, 9), err, s)));
-  SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32, Q8>(w, 1, n, in, out, Hs[2], Ws[2], slots(9, -1, 15), err, s)));
+  SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32, Q8, 1>(w, n, in, out, Hs[2], Ws[2], slots(9, -1, 15), err, s)));
   SET(l1a, B[k].s2, l1b); TRY((run_conv<T, 64, 32, TC_CONCAT, Q8>(w, 10, n, in, sk, out, Hs[1], Ws[1], slots(15, 3, 10), err, s)));
   SET(l1b, nullptr, l1a); TRY((run_conv<T, 32, 32, TC_PLAIN, Q8>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], slots(10, -1, 11), err, s)));
-  SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16, Q8>(w, 2, n, in, out, Hs[1], Ws[1], slots(11, -1, 16), err, s)));
+  SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16, Q8, 2>(w, n, in, out, Hs[1], Ws[1], slots(11, -1, 16), err, s)));
   SET(fa, B[k].s1, fb);  TRY((run_conv<T, 32, 16, TC_CONCAT, Q8>(w, 12, n, in, sk, out, Hs[0], Ws[0], slots(16, 1, 12), err, s)));
   SET(fb, nullptr, fa);  TRY((run_conv<T, 16, 16, TC_PLAIN, Q8>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], slots(12, -1, 13), err, s)));
   AdapterImg<T> ai[kMaxGroup];

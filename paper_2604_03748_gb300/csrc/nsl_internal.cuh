@@ -8,6 +8,42 @@
 
 #include "../../include/nsl.h"
 
+#ifndef NSL_PDL
+#define NSL_PDL 1   // network kernels use programmatic dependent launch
+#endif
+
+namespace nsl {
+// Programmatic dependent launch (griddepcontrol).  A kernel started by
+// launch_pdl may begin while its predecessor in the stream is finishing: it
+// does its set-up (barriers, tensor memory, weights), then calls pdl_wait()
+// before its first access to memory the predecessor writes or reads, and
+// pdl_trigger() so that its own successor may start early.  Both are no-ops
+// in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#ifndef NSL_PDL_TRIGGER
+#define NSL_PDL_TRIGGER 2   // 1: successor released once a kernel passed its wait, 2: at its end
+#endif
+__device__ __forceinline__ void pdl_trigger() { if (NSL_PDL_TRIGGER == 1) pdl_launch(); }
+__device__ __forceinline__ void pdl_trigger_end() { if (NSL_PDL_TRIGGER == 2) pdl_launch(); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = NSL_PDL;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+}  // namespace nsl
+
 namespace nsl {
 
 constexpr int kNumSMs = 152;
