@@ -721,7 +721,12 @@ cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int tot
 
 // pass 1 and pass 3: one thread per pixel, warps over 8x4 tiles
 template <int kPass>
-__global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPlume P, int ntiles) {
+__global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPlume P, int ntiles,
+                                                                        int* __restrict__ counter) {
+  pdl_wait();      // the staged grid (pass 1) or the segment partials (pass 3)
+  pdl_trigger();
+  // pass 1 clears the work queue of pass 2 (pass 2 starts after pass 1 ends)
+  if (kPass == 1 && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * (kMarchThreads / 32) + (threadIdx.x >> 5);
   if (tile >= ntiles) return;
@@ -735,6 +740,8 @@ __global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPl
 // pass 2: warps take (tile, segment) items from a queue, segment-major
 __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
 march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ counter) {
+  pdl_wait();      // the view pass's segment starts and the cleared queue
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   while (true) {
     int item = 0;
@@ -760,10 +767,9 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
   if (ntiles == 0) return cudaSuccess;
   const int warps_per_block = kMarchThreads / 32;
   const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
-  march_pixel_pass_kernel<1><<<blocks, kMarchThreads, 0, s>>>(p, ntiles);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(march_pixel_pass_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles,
+                             tile_counter);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
   static int grid = 0;
   if (!grid) {
     int occ = 0;
@@ -772,10 +778,10 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
       occ = 1;
     grid = occ * kNumSMs;
   }
-  march_segment_kernel<<<grid, kMarchThreads, 0, s>>>(p, ntiles, ntiles * max_segments, tile_counter);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  march_pixel_pass_kernel<3><<<blocks, kMarchThreads, 0, s>>>(p, ntiles);
-  return cudaGetLastError();
+  if ((e = launch_pdl(march_segment_kernel, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
+                      ntiles * max_segments, tile_counter)) != cudaSuccess)
+    return e;
+  return launch_pdl(march_pixel_pass_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles, tile_counter);
 }
 
 // ---------------------------------------------------------------------------
@@ -794,7 +800,10 @@ __device__ __forceinline__ int find_start(const int* __restrict__ starts, int n,
 template <int kPass>
 __global__ void __launch_bounds__(kMarchThreads) march_pass_batch_kernel(
     const MarchPlume* __restrict__ table, const int* __restrict__ tile_starts, int nplumes,
-    int total_tiles) {
+    int total_tiles, int* __restrict__ counter) {
+  pdl_wait();
+  pdl_trigger();
+  if (kPass == 1 && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int lane = threadIdx.x & 31;
   const int gt = blockIdx.x * (kMarchThreads / 32) + (threadIdx.x >> 5);
   if (gt >= total_tiles) return;
@@ -813,6 +822,8 @@ __global__ void __launch_bounds__(kMarchThreads) march_pass_batch_kernel(
 __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks) march_segment_batch_kernel(
     const MarchPlume* __restrict__ table, const int* __restrict__ item_starts,
     const int* __restrict__ tile_counts, int nplumes, int nitems, int* __restrict__ counter) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   while (true) {
     int item = 0;
@@ -836,17 +847,14 @@ cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int*
   if (total_tiles == 0) return cudaSuccess;
   const int wpb = kMarchThreads / 32;
   const int blocks = (total_tiles + wpb - 1) / wpb;
-  march_pass_batch_kernel<1><<<blocks, kMarchThreads, 0, s>>>(table_dev, tile_starts_dev, nplumes,
-                                                             total_tiles);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(march_pass_batch_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0, s, table_dev,
+                             tile_starts_dev, nplumes, total_tiles, counter);
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(counter, 0, sizeof(int), s)) != cudaSuccess) return e;
-  march_segment_batch_kernel<<<seg_blocks, kMarchThreads, 0, s>>>(
-      table_dev, item_starts_dev, tile_counts_dev, nplumes, total_items, counter);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  march_pass_batch_kernel<3><<<blocks, kMarchThreads, 0, s>>>(table_dev, tile_starts_dev, nplumes,
-                                                             total_tiles);
-  return cudaGetLastError();
+  if ((e = launch_pdl(march_segment_batch_kernel, dim3(seg_blocks), dim3(kMarchThreads), 0, s, table_dev,
+                      item_starts_dev, tile_counts_dev, nplumes, total_items, counter)) != cudaSuccess)
+    return e;
+  return launch_pdl(march_pass_batch_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, table_dev,
+                    tile_starts_dev, nplumes, total_tiles, counter);
 }
 
 int march_segment_blocks_max() {
@@ -912,6 +920,8 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
                                                     const uint8_t* __restrict__ mask, int nx,
                                                     int ny, int nz, float scale,
                                                     float* __restrict__ out) {
+  pdl_wait();      // the previous frame's march may still read the staged grid
+  pdl_trigger();
   auto val = [&](size_t idx) {
     return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
   };
@@ -946,18 +956,18 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
   if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
   if (blocks < 1) blocks = 1;
   if (dtype == NSL_F16)
-    stage_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(density), mask, nx, ny,
-                                                 nz, scale, staged);
-  else
-    stage_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(density), mask, nx, ny,
-                                                nz, scale, staged);
-  return cudaGetLastError();
+    return launch_pdl(stage_kernel<__half>, dim3(blocks), dim3(256), 0, s,
+                      static_cast<const __half*>(density), mask, nx, ny, nz, scale, staged);
+  return launch_pdl(stage_kernel<float>, dim3(blocks), dim3(256), 0, s, static_cast<const float*>(density),
+                    mask, nx, ny, nz, scale, staged);
 }
 
 // ---------------------------------------------------------------------------
 // six-way shading (Sec. 3): rgb_c = sum_q M[c][q] L_q + E, A = clamp(1 - T, 0, 1)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) shade_kernel(ShadeArgs a) {
+  pdl_wait();      // the lightmaps come from the network
+  pdl_trigger();
   const size_t P = (size_t)a.W * a.H;
   const size_t P4 = P / 4;
   const float4* lm = reinterpret_cast<const float4*>(a.lm);
@@ -993,8 +1003,7 @@ cudaError_t launch_shade(const ShadeArgs& a, cudaStream_t s) {
   if (P4 == 0) return cudaSuccess;
   int blocks = (int)((P4 + 255) / 256);
   if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
-  shade_kernel<<<blocks, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(shade_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,6 +1022,8 @@ constexpr int kStageChunk = 2048;  // staged cells per block
 __global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __restrict__ items,
                                                           const int* __restrict__ block_starts,
                                                           int n) {
+  pdl_wait();
+  pdl_trigger();
   const int k = find_start(block_starts, n, blockIdx.x);
   const StageItem& it = items[k];
   const size_t cells = staged_cells(it.nx, it.ny, it.nz);
@@ -1036,13 +1047,14 @@ cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_star
   static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto,
                 "batched staging writes a padded layout");
   if (total_blocks == 0) return cudaSuccess;
-  stage_batch_kernel<<<total_blocks, 256, 0, s>>>(items_dev, block_starts_dev, n);
-  return cudaGetLastError();
+  return launch_pdl(stage_batch_kernel, dim3(total_blocks), dim3(256), 0, s, items_dev, block_starts_dev, n);
 }
 
 __global__ void __launch_bounds__(256) shade_batch_kernel(const ShadeArgs* __restrict__ items,
                                                           const int* __restrict__ block_starts,
                                                           int n) {
+  pdl_wait();
+  pdl_trigger();
   const int k = find_start(block_starts, n, blockIdx.x);
   const ShadeArgs& a = items[k];
   const size_t P4 = (size_t)a.W * a.H / 4;
@@ -1075,8 +1087,7 @@ __global__ void __launch_bounds__(256) shade_batch_kernel(const ShadeArgs* __res
 cudaError_t launch_shade_batch(const ShadeArgs* items_dev, const int* block_starts_dev, int n,
                                int total_blocks, cudaStream_t s) {
   if (total_blocks == 0) return cudaSuccess;
-  shade_batch_kernel<<<total_blocks, 256, 0, s>>>(items_dev, block_starts_dev, n);
-  return cudaGetLastError();
+  return launch_pdl(shade_batch_kernel, dim3(total_blocks), dim3(256), 0, s, items_dev, block_starts_dev, n);
 }
 
 }  // namespace nsl
