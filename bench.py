@@ -36,6 +36,8 @@ METRIC = "Mpix/s guide+lightmaps"
 # sample position 7 (3 mul, 3 add, 1 mul for k*h), trilinear 30 (3 sub, 3 floor,
 # 3 sub, 7 lerps x (1 sub + 1 FMA)), optical-depth accumulation 2.
 FLOP_PER_SAMPLE = 39
+GATHER_BYTES = 32                 # 8 FP32 voxels per trilinear density sample
+L1_PEAK_GBS = 152 * 128 * 2.07    # L1 data path: 128 B per clock per SM at 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -366,7 +368,14 @@ def main():
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "work": {"density_samples": samples, "flop_per_sample": FLOP_PER_SAMPLE},
-                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     # the march's closer limit: the trilinear gathers through L1 (8 FP32
+                     # voxels = 32 B per density sample) against the L1 data path
+                     "gather": {"bytes_per_sample": GATHER_BYTES,
+                                "achieved": samples * GATHER_BYTES / march_avg_s / 1e9,
+                                "peak": L1_PEAK_GBS, "unit": "GB/s",
+                                "frac": samples * GATHER_BYTES / march_avg_s / 1e9 / L1_PEAK_GBS,
+                                "peak_kind": "derived: 152 SMs x 128 B/clk x 2.07 GHz"}},
         "e2e": {"value": e2e_val, "unit": "Mpix/s",
                 "h2d_bytes_per_step": int(pf.density.nbytes + pf.mask.nbytes),
                 "d2h_bytes_per_step": int((3 + 8 + 4) * H * W * 4)},

@@ -16,6 +16,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                         E4M3 codes; the quantised network against a PyTorch
                         float64 assembly using those casts)
   shade                 pinned (axis lights select one plane; linearity)
+  pack_lightmaps        pinned (Fig. 2 channel layout on exact binary fractions,
+                        ties to even, clamping; binary16 against numpy's cast)
+  guide light sets      pinned (constant-cube closed form for front only and
+                        front/left/right)
   paper-level quality   parity unpinned (no trained weights, no dataset)
 """
 from __future__ import annotations
@@ -55,7 +59,8 @@ class _Camera(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
                 ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
-                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("margin", C.c_float)]
+                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("margin", C.c_float),
+                ("light_set", C.c_int)]
 
 
 class _Light(C.Structure):
@@ -154,7 +159,7 @@ def _mask(mask):
 
 
 DEFAULT_OPTS = dict(tau_depth=0.01, t_min=1e-4, jitter=1, seed=0, frame=0, phase_g=0.0,
-                    surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5)
+                    surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5, light_set=0)
 
 
 def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
@@ -174,6 +179,7 @@ def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
     op.seed = int(o["seed"]) & 0xFFFFFFFF; op.frame = int(o["frame"]) & 0xFFFFFFFF
     op.phase_g = o["phase_g"]; op.surrogate_I[:] = list(o["surrogate_I"])
     op.segment_exact = int(o["segment_exact"]); op.margin = o["margin"]
+    op.light_set = int(o["light_set"])
     cam = _cam(camera)
     r0, r1 = (0, H) if rows is None else rows
     rc = lib.nslo_guide_rows(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(cam),
@@ -270,6 +276,38 @@ def shade(lightmaps, camera, lights):
     if rc != 0:
         raise ValueError(f"nslo_shade failed ({rc})")
     return out
+
+
+TEX_RGBA8, TEX_RGBA16F, TEX_RGBA32F = 0, 1, 2
+
+
+def pack_lightmaps(lightmaps, fmt):
+    """The two RGBA textures of the six-way layout (Sec. 3, Fig. 2) from the
+    eight planes [+X, -X, +Y, -Y, +Z, -Z, T, E] (camera frame: X right, Y up,
+    Z away from the viewer).  Texture 1 = (right +X, top +Y, back +Z,
+    transparency T); texture 2 = (left -X, bottom -Y, front -Z, emissive E);
+    each [H][W][4].  RGBA8: the UNORM code of the value clamped to [0, 1] (NaN
+    to 0), the float32 product v * 255 rounded to the nearest integer, ties to
+    even.  RGBA16F: nearest binary16, ties to even.  RGBA32F: the values."""
+    lm = np.asarray(lightmaps, np.float32)
+    assert lm.ndim == 3 and lm.shape[0] == 8
+    planes1 = (0, 2, 4, 6)
+    planes2 = (1, 3, 5, 7)
+
+    def one(idx):
+        t = np.empty(lm.shape[1:] + (4,), np.float32)
+        for c, q in enumerate(idx):
+            t[..., c] = lm[q]
+        if fmt == TEX_RGBA8:
+            v = np.where(np.isnan(t), np.float32(0), t)
+            v = np.minimum(np.maximum(v, np.float32(0)), np.float32(1))
+            return np.rint(v * np.float32(255)).astype(np.uint8)
+        if fmt == TEX_RGBA16F:
+            return t.astype(np.float16)
+        if fmt == TEX_RGBA32F:
+            return t
+        raise ValueError(fmt)
+    return one(planes1), one(planes2)
 
 
 def sample_sigma(density, mask, p, sigma_scale=1.0):

@@ -282,10 +282,14 @@ int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, i
         float span = (tout - tin) / h;
         int N = (int)floorf(span + u);
         /* surrogate lights (Eq. approx): front = toward the camera (-d), top =
-         * camera up (+u), bottom = -u; HG cosines against the view ray. */
-        float s_top[3] = {fr.u[0], fr.u[1], fr.u[2]};
-        float s_bot[3] = {-fr.u[0], -fr.u[1], -fr.u[2]};
-        double cu = (double)d[0] * fr.u[0] + (double)d[1] * fr.u[1] + (double)d[2] * fr.u[2];
+         * camera up (+u), bottom = -u; HG cosines against the view ray.  The
+         * ablation sets of Sec. 5 replace the side pair by right (+r) / left
+         * (-r), or drop it (front only). */
+        const int side_on = op->light_set != 1;
+        const float* sd = op->light_set == 2 ? fr.r : fr.u;
+        float s_top[3] = {sd[0], sd[1], sd[2]};
+        float s_bot[3] = {-sd[0], -sd[1], -sd[2]};
+        double cu = (double)d[0] * sd[0] + (double)d[1] * sd[1] + (double)d[2] * sd[2];
         double P_f = nslo_hg_phase(g, -1.0);
         double P_t = nslo_hg_phase(g, cu);
         double P_b = nslo_hg_phase(g, -cu);
@@ -308,12 +312,12 @@ int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, i
           /* sigma_n = 0 gives A_n = 0, so A_n L_n vanishes whatever L_n is: the
            * shadow rays of such a sample are not marched (and not counted) */
           double Tt = 1.0, Tb = 1.0;
-          if (sg > 0.0) {
+          if (sg > 0.0 && side_on) {
             Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
             Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
           }
-          double Ln = P_f * op->surrogate_I[0] * T + P_t * op->surrogate_I[1] * Tt +
-                      P_b * op->surrogate_I[2] * Tb;
+          double Ln = P_f * op->surrogate_I[0] * T;
+          if (side_on) Ln += P_t * op->surrogate_I[1] * Tt + P_b * op->surrogate_I[2] * Tb;
           L += A * Ln;
           tau += sg * (double)h;
           T = exp(-tau);

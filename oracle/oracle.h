@@ -34,6 +34,9 @@ typedef struct {
   float surrogate_I[3];   /* intensities of the front, top, bottom lights */
   int segment_exact;      /* 0: A_n = T_{n-1} sigma_n h; 1: T_{n-1}(1-exp(-sigma_n h)) */
   float margin;           /* relative margin for threshold-decision flags */
+  int light_set;          /* surrogate lights (Sec. 5, ablation on the guiding
+                             light directions): 0 front/top/bottom, 1 front
+                             only, 2 front/left/right */
 } nslo_march_opts;
 
 typedef struct {

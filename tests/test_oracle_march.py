@@ -81,6 +81,32 @@ def test_constant_cube_closed_form(orc, jitter, segment_exact):
         assert np.all(g[2, j] == h)         # first sample already exceeds tau_depth
 
 
+@pytest.mark.parametrize("jitter", [0, 1])
+def test_light_sets_constant_cube_closed_form(orc, jitter):
+    """The guiding-light ablation of Sec. 5: front only drops the side pair;
+    front/left/right marches the side pair along the camera's right axis.
+    Looking down -z with up +y, right is +x and pixel column i sits at
+    x = 2i + 1, so the right / left shadow rays hold (n - x) // h and x // h
+    samples (the top / bottom pair's closed form with columns for rows)."""
+    n, h, sig = 32, 4.0, 0.05
+    W = H = 16
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = axis_camera(n, W, H)
+    s32 = float(np.float32(sig))
+    M = n // int(h)
+    g1, s1, _ = orc.guide(vol, None, cam, h, jitter=jitter, t_min=0.0, light_set=1, seed=5)
+    L1, T1 = cube_closed_form(s32, h, M, 0, 0, Pt=0.0, Pb=0.0)
+    np.testing.assert_allclose(g1[0], L1, rtol=1e-12)
+    np.testing.assert_allclose(g1[1], T1, rtol=1e-12)
+    assert np.all(s1 == M)                      # view samples only: no shadow rays
+    g2, _, _ = orc.guide(vol, None, cam, h, jitter=jitter, t_min=0.0, light_set=2, seed=5)
+    for i in range(W):
+        x = 2 * i + 1
+        L, T = cube_closed_form(s32, h, M, int((n - x) // h), int(x // h))
+        np.testing.assert_allclose(g2[0, :, i], L, rtol=1e-12)
+        np.testing.assert_allclose(g2[1, :, i], T, rtol=1e-12)
+
+
 def test_constant_cube_with_early_termination(orc):
     n, h, sig = 32, 4.0, 0.9
     vol = np.full((n, n, n), sig, np.float32)
