@@ -90,10 +90,17 @@ typedef struct {
   float phase_g;         /* Henyey-Greenstein g of the surrogate lights (0 = isotropic) */
   float surrogate_I[3];  /* intensities of the front, top, bottom surrogate lights */
   int segment_exact;     /* 0: A_n = T_{n-1} sigma_n h;  1: A_n = T_{n-1}(1 - e^{-sigma_n h}) */
+  int light_set;         /* surrogate lights (Sec. 5, ablation on the guiding light
+                            directions): NSL_LIGHTS_FTB front/top/bottom (default),
+                            NSL_LIGHTS_F front only (no shadow rays),
+                            NSL_LIGHTS_FLR front/left/right (side pair along the
+                            camera's right axis; surrogate_I[1] right, [2] left) */
 } nsl_march_opts;
 
+enum { NSL_LIGHTS_FTB = 0, NSL_LIGHTS_F = 1, NSL_LIGHTS_FLR = 2 };
+
 /* Default options: tau_depth 0.01, t_min 1e-4, jitter 1, seed 0, frame 0,
- * g 0, intensities 1, segment_exact 0. */
+ * g 0, intensities 1, segment_exact 0, light_set NSL_LIGHTS_FTB. */
 NSL_API void nsl_default_march_opts(nsl_march_opts* out);
 
 /* Create a context.  Sec. 4.3 (one network for all scenes, Sec. 5).
@@ -180,6 +187,29 @@ NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, f
  *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
                                  int precision, float* lightmaps_dev, void* stream);
+
+/* Texture formats of nsl_pack_lightmaps. */
+enum { NSL_TEX_RGBA8 = 0, NSL_TEX_RGBA16F = 1, NSL_TEX_RGBA32F = 2 };
+
+/* Pack the eight lightmap planes into the two RGBA textures of the six-way
+ * layout (Sec. 3, Fig. 2), the form a game engine samples:
+ *   tex1 = (R right +X, G top +Y, B back +Z, A transparency T)
+ *   tex2 = (R left -X,  G bottom -Y, B front -Z, A emissive E)
+ * each an interleaved [H][W][4] image, row 0 at the top, in the format:
+ *   NSL_TEX_RGBA8    unsigned normalised bytes: the value clamped to [0, 1]
+ *                    (NaN to 0), times 255 in float32, rounded to the nearest
+ *                    integer, ties to even (4 bytes per texel)
+ *   NSL_TEX_RGBA16F  binary16, round to nearest even (8 bytes per texel)
+ *   NSL_TEX_RGBA32F  the float32 values (16 bytes per texel)
+ *                    (in both float formats a NaN stays a NaN; its payload
+ *                    is not specified)
+ *   lightmaps_dev  [8][H][W] float32 planes as written by nsl_predict_lightmaps
+ *   tex1_dev, tex2_dev  caller-owned device buffers of H*W texels each
+ * All three buffers must be 16-byte aligned; width and height multiples of 8
+ * in [8, 8192].  Asynchronous on the stream; no context is needed.  Returns
+ * NSL_ERR_INVALID_ARG for bad arguments, NSL_ERR_CUDA for a launch failure. */
+NSL_API nsl_status nsl_pack_lightmaps(const float* lightmaps_dev, int width, int height, int format,
+                                      void* tex1_dev, void* tex2_dev, void* stream);
 
 /* Six-way shading, Sec. 3 (directional interpolation, summed over lights):
  *   rgb = sum_l I_l * sum_{p in X,Y,Z} |w_p| L_p^{sign w_p} + E,  A = clamp(1 - T, 0, 1)

@@ -137,6 +137,7 @@ void nsl_default_march_opts(nsl_march_opts* o) {
   o->phase_g = 0.f;
   o->surrogate_I[0] = o->surrogate_I[1] = o->surrogate_I[2] = 1.f;
   o->segment_exact = 0;
+  o->light_set = NSL_LIGHTS_FTB;
 }
 
 const char* nsl_last_error(void) { return g_err; }
@@ -300,6 +301,8 @@ nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, fl
     return fail(NSL_ERR_INVALID_ARG, "%s: t_min must be in [0, 1)", fn);
   if (!(o.phase_g > -1.f && o.phase_g < 1.f))
     return fail(NSL_ERR_INVALID_ARG, "%s: phase_g must be in (-1, 1)", fn);
+  if (o.light_set < NSL_LIGHTS_FTB || o.light_set > NSL_LIGHTS_FLR)
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad light_set %d", fn, o.light_set);
   *p = MarchPlume{};
   p->nx = grid.nx; p->ny = grid.ny; p->nz = grid.nz;
   cam_frame_from(cam, &p->cam);
@@ -312,6 +315,7 @@ nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, fl
   p->g = o.phase_g;
   for (int k = 0; k < 3; ++k) p->I[k] = o.surrogate_I[k];
   p->segment_exact = o.segment_exact ? 1 : 0;
+  p->light_set = o.light_set;
   p->tiles_x = (cam.width + kMarchTX - 1) / kMarchTX;
   p->tile_start = 0;
   return NSL_OK;

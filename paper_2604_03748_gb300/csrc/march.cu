@@ -487,10 +487,12 @@ __device__ __forceinline__ Ray ray_setup(const MarchPlume& P, const Grid& g, int
     }
     r.N = (int)floorf(__fadd_rn(__fdiv_rn(__fsub_rn(tf, tn), P.h), r.u));
   }
-  // surrogate lights: front (toward the camera), top (+up), bottom (-up)
+  // surrogate lights: front (toward the camera), top (+up), bottom (-up); the
+  // front/left/right set takes the side pair along +-right
   float Pf = 0.07957747154594767f, Pt = Pf, Pb = Pf;
   if (P.g != 0.f) {
-    const float cu = r.d[0] * c.u[0] + r.d[1] * c.u[1] + r.d[2] * c.u[2];
+    const float* sd = P.light_set == NSL_LIGHTS_FLR ? c.r : c.u;
+    const float cu = r.d[0] * sd[0] + r.d[1] * sd[1] + r.d[2] * sd[2];
     Pf = hg_phase(P.g, -1.f);
     Pt = hg_phase(P.g, cu);
     Pb = hg_phase(P.g, -cu);
@@ -526,9 +528,15 @@ __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, co
                                           unsigned long long& nsamp) {
   const float h = P.h;
   const float A = P.segment_exact ? T * (1.f - expf(-s * h)) : T * s * h;
-  float Tt, Tb;
-  shadow_pair<kCount>(g, px, py, pz, P.cam.u, h, P.tau_lim, Tt, Tb, nsamp);
-  const float Ln = fmaf(r.wf, T, fmaf(r.wt, Tt, r.wb * Tb));
+  float Ln;
+  if (P.light_set == NSL_LIGHTS_F) {
+    Ln = r.wf * T;                 // front only: no shadow rays
+  } else {
+    float Tt, Tb;
+    shadow_pair<kCount>(g, px, py, pz, P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u, h, P.tau_lim,
+                        Tt, Tb, nsamp);
+    Ln = fmaf(r.wf, T, fmaf(r.wt, Tt, r.wb * Tb));
+  }
   kahan_add(L, Lc, A * Ln);
   kahan_add(tau, tc, s * h);
   T = expf(-tau);

@@ -97,8 +97,9 @@ extern "C" nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const v
   nsl_march_opts o;
   nsl_default_march_opts(&o);
   if (opts) o = *opts;
-  if (!(o.t_min >= 0.f && o.t_min < 1.f) || !(o.phase_g > -1.f && o.phase_g < 1.f))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: t_min or phase_g out of range");
+  if (!(o.t_min >= 0.f && o.t_min < 1.f) || !(o.phase_g > -1.f && o.phase_g < 1.f) ||
+      o.light_set < NSL_LIGHTS_FTB || o.light_set > NSL_LIGHTS_FLR)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: t_min, phase_g or light_set out of range");
 
   unsigned char* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);
@@ -123,6 +124,7 @@ extern "C" nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const v
   p.g = o.phase_g;
   for (int k = 0; k < 3; ++k) p.I[k] = o.surrogate_I[k];
   p.segment_exact = o.segment_exact ? 1 : 0;
+  p.light_set = o.light_set;
   p.guide = guide;
   p.tiles_x = (cam->width + kMarchTX - 1) / kMarchTX;
   p.tile_start = 0;

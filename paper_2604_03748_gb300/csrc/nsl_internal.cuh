@@ -86,6 +86,7 @@ struct MarchPlume {
   float g;            // HG parameter of the surrogate lights
   float I[3];         // front, top, bottom intensities
   int segment_exact;
+  int light_set;      // NSL_LIGHTS_FTB / _F / _FLR
   float* guide;       // [3][H][W]
   int tiles_x;        // tiles per row
   int tile_start;     // first tile index of this plume in a batch

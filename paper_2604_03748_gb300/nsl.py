@@ -17,6 +17,8 @@ NSL_OK, NSL_ERR_INVALID_ARG, NSL_ERR_OOM, NSL_ERR_CUDA, NSL_ERR_UNSUPPORTED, NSL
 NSL_F32, NSL_F16 = 0, 1
 NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8, NSL_PREC_F16 = 0, 1, 2, 3
 NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
+NSL_LIGHTS_FTB, NSL_LIGHTS_F, NSL_LIGHTS_FLR = 0, 1, 2
+NSL_TEX_RGBA8, NSL_TEX_RGBA16F, NSL_TEX_RGBA32F = 0, 1, 2
 
 # every symbol include/nsl.h declares
 EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_grid",
@@ -28,7 +30,7 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_default_server_opts", "nsl_server_create", "nsl_server_destroy",
            "nsl_server_add_plume", "nsl_server_remove_plume", "nsl_server_submit", "nsl_server_wait",
            "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
-           "nsl_server_reset_stats"]
+           "nsl_server_reset_stats", "nsl_pack_lightmaps"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -49,7 +51,7 @@ class nsl_light(C.Structure):
 class nsl_march_opts(C.Structure):
     _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
                 ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
-                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int)]
+                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("light_set", C.c_int)]
 
 
 class nsl_plume(C.Structure):
@@ -108,6 +110,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                            C.POINTER(C.c_ulonglong), vp]
     lib.nsl_predict_lightmaps.argtypes = [vp, vp, i, i, i, vp, vp]
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
+    lib.nsl_pack_lightmaps.argtypes = [vp, i, i, i, vp, vp, vp]
+    lib.nsl_pack_lightmaps.restype = C.c_int
     lib.nsl_render_frame_host.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light),
                                           i, f, C.POINTER(nsl_march_opts), i, vp, vp, vp, vp]
     lib.nsl_render_frame_host_async.argtypes = lib.nsl_render_frame_host.argtypes
@@ -287,6 +291,22 @@ def nsl_shade(ctx, lightmaps, width, height, cam, light_list, rgba, stream=None)
     check(load().nsl_shade(ctx, _dptr(lightmaps, F32), int(width), int(height), C.byref(camera(cam)),
                            lights(light_list), len(light_list), _dptr(rgba, F32), _stream(stream)),
           "nsl_shade")
+
+
+_TEX_DTYPES = {NSL_TEX_RGBA8: ("uint8",), NSL_TEX_RGBA16F: ("float16",), NSL_TEX_RGBA32F: ("float32",)}
+
+
+def nsl_pack_lightmaps(lightmaps, width, height, fmt, tex1, tex2, stream=None):
+    """Two RGBA textures of the six-way layout; tex1/tex2 are [H][W][4] CUDA
+    tensors of uint8, float16 or float32 for NSL_TEX_RGBA8 / 16F / 32F."""
+    if fmt not in _TEX_DTYPES:
+        raise ValueError(f"bad texture format {fmt}")
+    for t in (tex1, tex2):
+        if tuple(t.shape) != (int(height), int(width), 4):
+            raise ValueError("textures must be [H][W][4]")
+    check(load().nsl_pack_lightmaps(_dptr(lightmaps, F32), int(width), int(height), int(fmt),
+                                    _dptr(tex1, _TEX_DTYPES[fmt]), _dptr(tex2, _TEX_DTYPES[fmt]),
+                                    _stream(stream)), "nsl_pack_lightmaps")
 
 
 def nsl_render_frame_host(ctx, density_np, mask_np, cam, light_list, step, precision,

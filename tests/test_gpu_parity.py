@@ -58,7 +58,9 @@ def test_guide_parity_obstacle_128_full_size(lib, orc):
 
 @pytest.mark.parametrize("opts", [dict(jitter=0, t_min=0.0), dict(segment_exact=1),
                                   dict(phase_g=0.5, surrogate_I=(1.0, 0.5, 2.0)),
-                                  dict(seed=123, frame=77, tau_depth=0.2)])
+                                  dict(seed=123, frame=77, tau_depth=0.2),
+                                  dict(light_set=1), dict(light_set=2),
+                                  dict(light_set=2, phase_g=0.4, surrogate_I=(1.0, 0.6, 1.7))])
 def test_guide_options(lib, orc, opts):
     pf = I.small_case(24, 24, 16, seed=13, kind=I.PERSP, step=2.0)
     ctx = PT.make_ctx(pf)
