@@ -224,201 +224,144 @@ __device__ __forceinline__ int shadow_steps(const Grid& g, float px, float py, f
 }
 
 // Transmittances toward the top (+u) and bottom (-u) surrogate lights from p:
-// both rays are marched in one loop (two independent load chains), each at step
-// h to the box exit, T = exp(-h sum_k sigma(p +- k h u)), and each stops once its
-// optical depth exceeds tau_lim (transmittance below t_min).
-template <bool kCount>
+// each ray is marched at step h to the box exit, T = exp(-h sum_k sigma(p +- k h u)),
+// and stops once its optical depth exceeds tau_lim (transmittance below t_min).
+// The two rays run back to back as one sequence of K_t + K_b samples, two per
+// loop step (two gathers in flight): that length is nearly the same on every
+// lane of a warp (the box's extent along u), where max(K_t, K_b) is not.  Each
+// ray's samples and sums keep their order.
+//
+// kExactLast = true (single-plume kernels): samples 1..K-1 of a ray lie strictly
+// inside the closed box (K h <= t_exit up to one rounding, so (K-1) h falls
+// short of every face crossing by h, far more than the rounding of p + k h s for
+// any step above 1e-3 voxel); they need no box test and their cell coordinates
+// come from q = fma(k h, s, p - 0.5) (the trilinear value is continuous in q).
+// The last sample of each ray, which can lie on or just past the exit face, is
+// taken after the others at its exact position with the box test.
+// kExactLast = false (grouped kernels): every sample at its exact position with
+// the box test, the rays' last samples inside the two-per-step sequence; in the
+// grouped march the separate last-sample step cost more latency than the box
+// tests it saved (measured: 16.4 against 17.5 ms per 64-plume batch).
+template <bool kCount, bool kExactLast>
 __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, float pz,
-                                            const float u[3], float h, float tau_lim, float& Tt,
+                                            const float u_in[3], float h, float tau_lim, float& Tt,
                                             float& Tb, unsigned long long& nsamp) {
+  // the direction in registers: u_in may point into a plume table in global memory
+  const float u[3] = {u_in[0], u_in[1], u_in[2]};
   const int Kt = shadow_steps(g, px, py, pz, u[0], u[1], u[2], h);
   const int Kb = shadow_steps(g, px, py, pz, -u[0], -u[1], -u[2], h);
   float taut = 0.f, taub = 0.f;
   bool at = Kt > 0, ab = Kb > 0;
-  const int K = max(Kt, Kb);
-#if NSL_MARCH_PIPELINE
-  if (kMarchLayout == kLayoutQuad && K > 0) {
-    // loads of step k+1 are issued before step k is consumed
-    float kh = h;
-    Fetch ft = fetch(g, __fadd_rn(px, __fmul_rn(kh, u[0])), __fadd_rn(py, __fmul_rn(kh, u[1])),
-                     __fadd_rn(pz, __fmul_rn(kh, u[2])));
-    Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kh, u[0])), __fsub_rn(py, __fmul_rn(kh, u[1])),
-                     __fsub_rn(pz, __fmul_rn(kh, u[2])));
-    for (int k = 1; k <= K; ++k) {
-      Fetch nt = ft, nb = fb;
-      if (k < K) {
-        kh = __fmul_rn((float)(k + 1), h);
-        const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
-        if (at && k < Kt) nt = fetch(g, __fadd_rn(px, dx), __fadd_rn(py, dy), __fadd_rn(pz, dz));
-        if (ab && k < Kb) nb = fetch(g, __fsub_rn(px, dx), __fsub_rn(py, dy), __fsub_rn(pz, dz));
-      }
-      if (at) {
-        taut = fmaf(interp(ft), h, taut);
+  if constexpr (kExactLast) {
+    const int Mt = Kt > 0 ? Kt - 1 : 0, Mb = Kb > 0 ? Kb - 1 : 0;
+    const int Mall = Mt + Mb;
+    const float qx0 = __fsub_rn(px, 0.5f), qy0 = __fsub_rn(py, 0.5f), qz0 = __fsub_rn(pz, 0.5f);
+    int j = 1;
+    while (j <= Mall) {
+      const bool hasB = j + 1 <= Mall;
+      const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice
+      const bool tA = j <= Mt, tB = j2 <= Mt;
+      // signed step count: negative along the bottom ray (direction -u)
+      const float khA = __fmul_rn((float)(tA ? j : Mt - j), h);
+      const float khB = __fmul_rn((float)(tB ? j2 : Mt - j2), h);
+      const Fetch fA = fetch_q(g, fmaf(khA, u[0], qx0), fmaf(khA, u[1], qy0), fmaf(khA, u[2], qz0));
+      const Fetch fB = fetch_q(g, fmaf(khB, u[0], qx0), fmaf(khB, u[1], qy0), fmaf(khB, u[2], qz0));
+      const float vA = interp(fA), vB = interp(fB);
+      int jn = j + 2;
+      if (tA) {
+        taut = fmaf(vA, h, taut);
         if (kCount) ++nsamp;
-        if (k >= Kt || taut > tau_lim) at = false;
-      }
-      if (ab) {
-        taub = fmaf(interp(fb), h, taub);
+        if (taut > tau_lim) {
+          at = false;
+          jn = Mt + 1;             // top ray done; sample B (if bottom) is taken next
+        } else if (hasB) {
+          if (tB) {
+            taut = fmaf(vB, h, taut);
+            if (kCount) ++nsamp;
+            if (taut > tau_lim) { at = false; jn = Mt + 1; }
+          } else {
+            taub = fmaf(vB, h, taub);
+            if (kCount) ++nsamp;
+            if (taub > tau_lim) { ab = false; break; }
+          }
+        }
+      } else {
+        taub = fmaf(vA, h, taub);
         if (kCount) ++nsamp;
-        if (k >= Kb || taub > tau_lim) ab = false;
-      }
-      if (!(at || ab)) break;
-      ft = nt;
-      fb = nb;
-    }
-    Tt = expf(-taut);
-    Tb = expf(-taub);
-    return;
-  }
-#endif
-#if NSL_SHADOW_V2
-  // Samples 1..K-1 of a ray lie strictly inside the closed box: K h <= t_exit
-  // (up to one rounding), so (K-1) h falls short of every face crossing by h,
-  // far more than the rounding of p + k h s for any step above 1e-3 voxel.
-  // They need no box test, and their cell coordinates may be taken from
-  // q = (p - 0.5) + k h s (the trilinear value is continuous in q).  The last
-  // sample of each ray can lie on or just past the exit face: it is taken at
-  // the exact position p + k h s, with the box test, after the others.
-  (void)K;
-  const int Mt = Kt > 0 ? Kt - 1 : 0, Mb = Kb > 0 ? Kb - 1 : 0;
-  const int Mall = Mt + Mb;
-  const float qx0 = __fsub_rn(px, 0.5f), qy0 = __fsub_rn(py, 0.5f), qz0 = __fsub_rn(pz, 0.5f);
-  int j = 1;
-  while (j <= Mall) {
-    const bool hasB = j + 1 <= Mall;
-    const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice
-    const bool tA = j <= Mt, tB = j2 <= Mt;
-    // signed step count: negative along the bottom ray (direction -u)
-    const float khA = __fmul_rn((float)(tA ? j : Mt - j), h);
-    const float khB = __fmul_rn((float)(tB ? j2 : Mt - j2), h);
-#if NSL_SHADOW_QFMA
-    const Fetch fA = fetch_q(g, fmaf(khA, u[0], qx0), fmaf(khA, u[1], qy0), fmaf(khA, u[2], qz0));
-    const Fetch fB = fetch_q(g, fmaf(khB, u[0], qx0), fmaf(khB, u[1], qy0), fmaf(khB, u[2], qz0));
-#else
-    const Fetch fA = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khA, u[0])), __fadd_rn(qy0, __fmul_rn(khA, u[1])),
-                             __fadd_rn(qz0, __fmul_rn(khA, u[2])));
-    const Fetch fB = fetch_q(g, __fadd_rn(qx0, __fmul_rn(khB, u[0])), __fadd_rn(qy0, __fmul_rn(khB, u[1])),
-                             __fadd_rn(qz0, __fmul_rn(khB, u[2])));
-#endif
-    const float vA = interp(fA), vB = interp(fB);
-    int jn = j + 2;
-    if (tA) {
-      taut = fmaf(vA, h, taut);
-      if (kCount) ++nsamp;
-      if (taut > tau_lim) {
-        at = false;
-        jn = Mt + 1;               // top ray done; sample B (if bottom) is taken next
-      } else if (hasB) {
-        if (tB) {
-          taut = fmaf(vB, h, taut);
-          if (kCount) ++nsamp;
-          if (taut > tau_lim) { at = false; jn = Mt + 1; }
-        } else {
+        if (taub > tau_lim) { ab = false; break; }
+        if (hasB) {
           taub = fmaf(vB, h, taub);
           if (kCount) ++nsamp;
           if (taub > tau_lim) { ab = false; break; }
         }
       }
-    } else {
-      taub = fmaf(vA, h, taub);
-      if (kCount) ++nsamp;
-      if (taub > tau_lim) { ab = false; break; }
-      if (hasB) {
-        taub = fmaf(vB, h, taub);
+      j = jn;
+    }
+    if (at || ab) {
+      const float kt = __fmul_rn((float)Kt, h), kb = __fmul_rn((float)Kb, h);
+      const Fetch ft = fetch(g, __fadd_rn(px, __fmul_rn(kt, u[0])), __fadd_rn(py, __fmul_rn(kt, u[1])),
+                             __fadd_rn(pz, __fmul_rn(kt, u[2])));
+      const Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kb, u[0])), __fsub_rn(py, __fmul_rn(kb, u[1])),
+                             __fsub_rn(pz, __fmul_rn(kb, u[2])));
+      if (at) {
+        taut = fmaf(interp(ft), h, taut);
         if (kCount) ++nsamp;
-        if (taub > tau_lim) { ab = false; break; }
+      }
+      if (ab) {
+        taub = fmaf(interp(fb), h, taub);
+        if (kCount) ++nsamp;
       }
     }
-    j = jn;
-  }
-  if (at || ab) {
-    const float kt = __fmul_rn((float)Kt, h), kb = __fmul_rn((float)Kb, h);
-    const Fetch ft = fetch(g, __fadd_rn(px, __fmul_rn(kt, u[0])), __fadd_rn(py, __fmul_rn(kt, u[1])),
-                           __fadd_rn(pz, __fmul_rn(kt, u[2])));
-    const Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kb, u[0])), __fsub_rn(py, __fmul_rn(kb, u[1])),
-                           __fsub_rn(pz, __fmul_rn(kb, u[2])));
-    if (at) {
-      taut = fmaf(interp(ft), h, taut);
-      if (kCount) ++nsamp;
-    }
-    if (ab) {
-      taub = fmaf(interp(fb), h, taub);
-      if (kCount) ++nsamp;
-    }
-  }
-#elif NSL_SHADOW_FLAT
-#if NSL_SHADOW_NOCLAMP
-#define SHADOW_FETCH fetch_in
-#else
-#define SHADOW_FETCH fetch
-#endif
-  // the two rays back to back in one sequence of Kt + Kb samples, two per
-  // iteration so that two gathers are in flight (each ray's samples and sums
-  // in the same order as below): the sequence length is nearly the same for
-  // every lane of a warp, where max(Kt, Kb) is not
-  (void)K;
-  const int Kall = Kt + (ab ? Kb : 0);
-  int j = at ? 1 : Kt + 1;
-  while (j <= Kall) {
-    const bool hasB = j + 1 <= Kall;
-    const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice, never past the ray's end
-    const bool tA = j <= Kt, tB = j2 <= Kt;
-    const float khA = __fmul_rn((float)(tA ? j : j - Kt), h);
-    const float khB = __fmul_rn((float)(tB ? j2 : j2 - Kt), h);
-    const float dAx = __fmul_rn(khA, u[0]), dAy = __fmul_rn(khA, u[1]), dAz = __fmul_rn(khA, u[2]);
-    const float dBx = __fmul_rn(khB, u[0]), dBy = __fmul_rn(khB, u[1]), dBz = __fmul_rn(khB, u[2]);
-    const Fetch fA = SHADOW_FETCH(g, tA ? __fadd_rn(px, dAx) : __fsub_rn(px, dAx),
-                           tA ? __fadd_rn(py, dAy) : __fsub_rn(py, dAy),
-                           tA ? __fadd_rn(pz, dAz) : __fsub_rn(pz, dAz));
-    const Fetch fB = SHADOW_FETCH(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
-                           tB ? __fadd_rn(py, dBy) : __fsub_rn(py, dBy),
-                           tB ? __fadd_rn(pz, dBz) : __fsub_rn(pz, dBz));
-    const float vA = interp(fA), vB = interp(fB);
-    int jn = j + 2;
-    if (tA) {
-      taut = fmaf(vA, h, taut);
-      if (kCount) ++nsamp;
-      if (taut > tau_lim) {
-        jn = Kt + 1;               // top ray done; sample B (if bottom) is taken next
-      } else if (hasB) {
-        if (tB) {
-          taut = fmaf(vB, h, taut);
-          if (kCount) ++nsamp;
-          if (taut > tau_lim) jn = Kt + 1;
-        } else {
+  } else {
+    // every sample k <= K lies within rounding of the closed box, so
+    // floor(p - 0.5) is within [-1, n-1] on every axis: fetch_in needs no clamps
+    const int Kall = Kt + (ab ? Kb : 0);
+    int j = at ? 1 : Kt + 1;
+    while (j <= Kall) {
+      const bool hasB = j + 1 <= Kall;
+      const int j2 = hasB ? j + 1 : j;  // a lone last sample is fetched twice, never past the ray's end
+      const bool tA = j <= Kt, tB = j2 <= Kt;
+      const float khA = __fmul_rn((float)(tA ? j : j - Kt), h);
+      const float khB = __fmul_rn((float)(tB ? j2 : j2 - Kt), h);
+      const float dAx = __fmul_rn(khA, u[0]), dAy = __fmul_rn(khA, u[1]), dAz = __fmul_rn(khA, u[2]);
+      const float dBx = __fmul_rn(khB, u[0]), dBy = __fmul_rn(khB, u[1]), dBz = __fmul_rn(khB, u[2]);
+      const Fetch fA = fetch_in(g, tA ? __fadd_rn(px, dAx) : __fsub_rn(px, dAx),
+                                tA ? __fadd_rn(py, dAy) : __fsub_rn(py, dAy),
+                                tA ? __fadd_rn(pz, dAz) : __fsub_rn(pz, dAz));
+      const Fetch fB = fetch_in(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
+                                tB ? __fadd_rn(py, dBy) : __fsub_rn(py, dBy),
+                                tB ? __fadd_rn(pz, dBz) : __fsub_rn(pz, dBz));
+      const float vA = interp(fA), vB = interp(fB);
+      int jn = j + 2;
+      if (tA) {
+        taut = fmaf(vA, h, taut);
+        if (kCount) ++nsamp;
+        if (taut > tau_lim) {
+          jn = Kt + 1;               // top ray done; sample B (if bottom) is taken next
+        } else if (hasB) {
+          if (tB) {
+            taut = fmaf(vB, h, taut);
+            if (kCount) ++nsamp;
+            if (taut > tau_lim) jn = Kt + 1;
+          } else {
+            taub = fmaf(vB, h, taub);
+            if (kCount) ++nsamp;
+            if (taub > tau_lim) break;
+          }
+        }
+      } else {
+        taub = fmaf(vA, h, taub);
+        if (kCount) ++nsamp;
+        if (taub > tau_lim) break;
+        if (hasB) {
           taub = fmaf(vB, h, taub);
           if (kCount) ++nsamp;
           if (taub > tau_lim) break;
         }
       }
-    } else {
-      taub = fmaf(vA, h, taub);
-      if (kCount) ++nsamp;
-      if (taub > tau_lim) break;
-      if (hasB) {
-        taub = fmaf(vB, h, taub);
-        if (kCount) ++nsamp;
-        if (taub > tau_lim) break;
-      }
-    }
-    j = jn;
-  }
-#else
-  for (int k = 1; k <= K && (at || ab); ++k) {
-    const float kh = __fmul_rn((float)k, h);
-    const float dx = __fmul_rn(kh, u[0]), dy = __fmul_rn(kh, u[1]), dz = __fmul_rn(kh, u[2]);
-    if (at) {
-      taut = fmaf(sigma_at(g, __fadd_rn(px, dx), __fadd_rn(py, dy), __fadd_rn(pz, dz)), h, taut);
-      if (kCount) ++nsamp;
-      if (k >= Kt || taut > tau_lim) at = false;
-    }
-    if (ab) {
-      taub = fmaf(sigma_at(g, __fsub_rn(px, dx), __fsub_rn(py, dy), __fsub_rn(pz, dz)), h, taub);
-      if (kCount) ++nsamp;
-      if (k >= Kb || taub > tau_lim) ab = false;
+      j = jn;
     }
   }
-#endif
   Tt = expf(-taut);
   Tb = expf(-taub);
 }
@@ -521,7 +464,7 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
 
 // One view step n with sigma = s > 0: A_n, the three surrogate lights, L_n;
 // accumulates A_n L_n into (L, Lc) and the optical depth into (tau, tc).
-template <bool kCount>
+template <bool kCount, bool kExactLast>
 __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, const Ray& r,
                                           float px, float py, float pz, float s, float& T,
                                           float& tau, float& tc, float& L, float& Lc,
@@ -533,7 +476,7 @@ __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, co
     Ln = r.wf * T;                 // front only: no shadow rays
   } else {
     float Tt, Tb;
-    shadow_pair<kCount>(g, px, py, pz, P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u, h, P.tau_lim,
+    shadow_pair<kCount, kExactLast>(g, px, py, pz, P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u, h, P.tau_lim,
                         Tt, Tb, nsamp);
     Ln = fmaf(r.wf, T, fmaf(r.wt, Tt, r.wb * Tb));
   }
@@ -544,7 +487,7 @@ __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, co
 
 // Single-pass march of one pixel (Alg. 1): used by the sample-count variant and
 // the allocation-free entry point.
-template <bool kCount>
+template <bool kCount, bool kExactLast>
 __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   unsigned long long nsamp = 0;
   const CamFrame& c = P.cam;
@@ -562,7 +505,7 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
     if (kCount) ++nsamp;
     if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, P.h);
     if (s > 0.f) {
-      view_step<kCount>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+      view_step<kCount, kExactLast>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
       if (T < P.t_min) break;
     }
   }
@@ -615,6 +558,7 @@ __device__ __forceinline__ void march_view_pixel(const MarchPlume& P, int i, int
   P.seg_nef[pix] = nef;
 }
 
+template <bool kExactLast>
 __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j, int seg) {
   const CamFrame& c = P.cam;
   const size_t plane = (size_t)c.W * c.H;
@@ -635,7 +579,7 @@ __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j,
     float px, py, pz;
     view_point(r, n, P.h, px, py, pz);
     const float s = sigma_at(g, px, py, pz);
-    if (s > 0.f) view_step<false>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+    if (s > 0.f) view_step<false, kExactLast>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
   }
   P.seg_L[k] = L;
 }
@@ -680,7 +624,7 @@ march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplume
     const int tx = tile % P->tiles_x, ty = tile / P->tiles_x;
     const int i = tx * kMarchTX + (lane % kMarchTX);
     const int j = ty * kMarchTY + (lane / kMarchTX);
-    if (i < P->cam.W && j < P->cam.H) march_pixel<kCount>(*P, i, j);
+    if (i < P->cam.W && j < P->cam.H) march_pixel<kCount, !kBatch>(*P, i, j);
   }
 }
 
@@ -759,7 +703,7 @@ march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ cou
     const int seg = item / ntiles, tile = item % ntiles;
     const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
     const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
-    if (i < P.cam.W && j < P.cam.H) march_segment(P, i, j, seg);
+    if (i < P.cam.W && j < P.cam.H) march_segment<true>(P, i, j, seg);
   }
 }
 
@@ -844,7 +788,7 @@ __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks) march_segment_
     const int seg = local / nt, tile = local % nt;
     const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
     const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
-    if (i < P.cam.W && j < P.cam.H) march_segment(P, i, j, seg);
+    if (i < P.cam.W && j < P.cam.H) march_segment<false>(P, i, j, seg);
   }
 }
 
@@ -914,7 +858,11 @@ __device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const 
     reinterpret_cast<float4*>(out)[2 * c + 1] =
         make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1));
   } else {
+#if NSL_STAGE_CS
+    __stcs(reinterpret_cast<float4*>(out) + c, lo);
+#else
     reinterpret_cast<float4*>(out)[c] = lo;
+#endif
   }
 }
 

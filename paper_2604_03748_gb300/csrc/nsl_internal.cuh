@@ -99,20 +99,8 @@ struct MarchPlume {
   float* seg_L;       // [segment][pixel] partial guide radiance
 };
 
-#ifndef NSL_SHADOW_V2
-#define NSL_SHADOW_V2 1   // box test only on the last sample of each shadow ray
-#endif
-#ifndef NSL_SHADOW_QFMA
-#define NSL_SHADOW_QFMA 1   // in-ray cell coordinates by one fused multiply-add per axis
-#endif
-#ifndef NSL_SHADOW_FLAT
-#define NSL_SHADOW_FLAT 1   // top and bottom shadow rays as one two-sample-per-step sequence
-#endif
-#ifndef NSL_SHADOW_NOCLAMP
-#define NSL_SHADOW_NOCLAMP 1   // shadow samples k <= K are inside the padded grid by construction
-#endif
-#ifndef NSL_MARCH_PIPELINE
-#define NSL_MARCH_PIPELINE 0
+#ifndef NSL_STAGE_CS
+#define NSL_STAGE_CS 0   // staging stores marked evict-first
 #endif
 #ifndef NSL_MARCH_MIN_BLOCKS
 #define NSL_MARCH_MIN_BLOCKS 7

@@ -66,11 +66,12 @@ def _device_plumes(frames, with_rgba=True):
     return items
 
 
-def _single(lib, pf, precision):
-    """The single-plume entry points on one frame: guide, lightmaps, rgba."""
+def _single(lib, pf, precision, guide=None):
+    """The single-plume entry points on one frame: guide, lightmaps, rgba (the
+    network and shading on `guide` when given)."""
     import torch
     ctx = PT.make_ctx(pf, c0=C0)
-    g = PT.gpu_guide(ctx, pf)
+    g = PT.gpu_guide(ctx, pf) if guide is None else guide
     dev = torch.device("cuda:0")
     H, W = pf.camera.height, pf.camera.width
     gd = torch.from_numpy(g.astype(np.float32)).to(dev)
@@ -98,8 +99,14 @@ def test_batch_equals_single_plume_path(lib, precision):
     b.render(items, precision)
     guides, lms, rgbas = _host(items, "guide"), _host(items, "lightmaps"), _host(items, "rgba")
     for k, pf in enumerate(frames):
-        g1, lm1, rgba1 = _single(lib, pf, precision)
-        assert np.array_equal(guides[k], g1), k
+        # the grouped march takes every shadow sample at its exact position,
+        # the single-plume march the in-ray ones from p - 0.5 + k h u: the
+        # guides agree to rounding
+        g1, _, _ = _single(lib, pf, precision)
+        for c in range(3):
+            assert np.abs(guides[k][c] - g1[c]).max() <= 1e-6 * max(np.abs(g1[c]).max(), 1e-30), (k, c)
+        # the same network and shading kernels: bitwise on the batch's guide
+        _, lm1, rgba1 = _single(lib, pf, precision, guide=guides[k])
         assert np.array_equal(lms[k], lm1), k
         assert np.allclose(rgbas[k], rgba1, rtol=1e-6, atol=1e-7), k
     # a second render of the same batch is bitwise identical (deterministic)
