@@ -20,6 +20,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                         ties to even, clamping; binary16 against numpy's cast)
   guide light sets      pinned (constant-cube closed form for front only and
                         front/left/right)
+  shadow_map            pinned (single voxel and slab closed forms, axis and
+                        oblique lights)
+  shade_shadowed        pinned (occluder slab: shadowed pixels keep only E,
+                        lit ones equal shade(); no maps equals shade())
   paper-level quality   parity unpinned (no trained weights, no dataset)
 """
 from __future__ import annotations
@@ -104,6 +108,11 @@ def _load():
     lib.nslo_q8_weights.restype = None
     lib.nslo_shade.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(_Camera), C.POINTER(_Light),
                                C.c_int, C.c_void_p]
+    lib.nslo_shadow_map.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float * 3),
+                                    C.c_int, C.c_void_p]
+    lib.nslo_shade_shadowed.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(_Camera),
+                                        C.POINTER(_Light), C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_void_p), C.c_int, C.c_float, C.c_void_p]
     lib.nslo_sample_sigma.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
                                       C.POINTER(C.c_float * 3)]
     lib.nslo_sample_sigma.restype = C.c_double
@@ -275,6 +284,47 @@ def shade(lightmaps, camera, lights):
     rc = lib.nslo_shade(_ptr(lm), H, W, C.byref(cam), arr, len(lights), _ptr(out))
     if rc != 0:
         raise ValueError(f"nslo_shade failed ({rc})")
+    return out
+
+
+def shadow_map(mask, light_dir, R):
+    """Obstacle shadow map (Sec. 4.5) of the uint8 mask [nz][ny][nx] for a light
+    toward light_dir: float32 [R][R] of first-hit parameters (+inf = none)."""
+    lib = _load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    nz, ny, nx = m.shape
+    out = np.zeros((R, R), np.float32)
+    d = (C.c_float * 3)(*[float(v) for v in light_dir])
+    if lib.nslo_shadow_map(_ptr(m), nx, ny, nz, C.byref(d), int(R), _ptr(out)) != 0:
+        raise ValueError("nslo_shadow_map failed")
+    return out
+
+
+def shade_shadowed(lightmaps, guide, camera, lights, grid_shape, maps, bias):
+    """shade() with each light's term times the visibility of the pixel's smoke
+    shell against that light's shadow map (maps[l] None = no obstacle shadow).
+    guide: float32 [3][H][W]; grid_shape: (nz, ny, nx)."""
+    lib = _load()
+    lm = np.ascontiguousarray(lightmaps, dtype=np.float64)
+    g = np.ascontiguousarray(guide, dtype=np.float32)
+    _, H, W = lm.shape
+    arr = (_Light * max(1, len(lights)))()
+    for i, li in enumerate(lights):
+        arr[i].dir[:] = [float(v) for v in li.dir]
+        arr[i].intensity[:] = [float(v) for v in li.intensity]
+    R = 1
+    keep = [None if mp is None else np.ascontiguousarray(mp, dtype=np.float32) for mp in maps]
+    for mp in keep:
+        if mp is not None:
+            R = mp.shape[0]
+    ptrs = (C.c_void_p * max(1, len(keep)))(*[None if mp is None else mp.ctypes.data for mp in keep])
+    nz, ny, nx = grid_shape
+    out = np.zeros((4, H, W), np.float64)
+    cam = _cam(camera)
+    rc = lib.nslo_shade_shadowed(_ptr(lm), _ptr(g), H, W, C.byref(cam), arr, len(lights), nx, ny, nz,
+                                 ptrs, int(R), float(bias), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_shade_shadowed failed ({rc})")
     return out
 
 

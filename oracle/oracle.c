@@ -1015,3 +1015,189 @@ int nslo_shade(const double* lm, int H, int W, const nslo_camera* cam, const nsl
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Obstacle shadowing (Sec. 4.5): the smoke shell depth D of the guide moved   */
+/* into the light's frame and compared with a shadow map of the obstacle.     */
+/* ------------------------------------------------------------------------- */
+
+/* Light frame of a directional light, built in binary64 and rounded once to
+ * binary32: w = -dir/|dir| (the propagation direction), e1 = normalize(w x a)
+ * with a = +Y, or +Z when |w_y| > 0.9, e2 = e1 x w.  The map is the square of
+ * side S = |(nx, ny, nz)| centred on the grid centre c, in the plane through c
+ * spanned by (e1, e2). */
+typedef struct {
+  float w[3], e1[3], e2[3], c[3], S;
+} light_frame;
+
+static int light_setup(const float dir[3], int nx, int ny, int nz, light_frame* L) {
+  double v[3] = {dir[0], dir[1], dir[2]};
+  double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  if (!(nv > 0.0)) return 1;
+  double w[3] = {-v[0] / nv, -v[1] / nv, -v[2] / nv};
+  double a[3] = {0.0, 1.0, 0.0};
+  if (fabs(w[1]) > 0.9) { a[1] = 0.0; a[2] = 1.0; }
+  double e1[3] = {w[1] * a[2] - w[2] * a[1], w[2] * a[0] - w[0] * a[2], w[0] * a[1] - w[1] * a[0]};
+  double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int k = 0; k < 3; ++k) e1[k] /= l1;
+  double e2[3] = {e1[1] * w[2] - e1[2] * w[1], e1[2] * w[0] - e1[0] * w[2], e1[0] * w[1] - e1[1] * w[0]};
+  for (int k = 0; k < 3; ++k) {
+    L->w[k] = (float)w[k];
+    L->e1[k] = (float)e1[k];
+    L->e2[k] = (float)e2[k];
+  }
+  L->c[0] = (float)nx * 0.5f;
+  L->c[1] = (float)ny * 0.5f;
+  L->c[2] = (float)nz * 0.5f;
+  L->S = (float)sqrt((double)nx * nx + (double)ny * ny + (double)nz * nz);
+  return 0;
+}
+
+/* Slab test of the unit voxel with low corner (i, j, k) against the line
+ * o + t w (t unbounded); returns 1 and the entry parameter on a hit (touching
+ * counts). */
+static int voxel_entry(const float o[3], const float w[3], int i, int j, int k, float* t_enter) {
+  const float lo[3] = {(float)i, (float)j, (float)k};
+  float tn = -INFINITY, tf = INFINITY;
+  for (int q = 0; q < 3; ++q) {
+    const float hi = lo[q] + 1.0f;
+    if (w[q] != 0.0f) {
+      float ta = (lo[q] - o[q]) / w[q];
+      float tb = (hi - o[q]) / w[q];
+      float nr = ta < tb ? ta : tb;
+      float fr = ta < tb ? tb : ta;
+      if (nr > tn) tn = nr;
+      if (fr < tf) tf = fr;
+    } else if (o[q] < lo[q] || o[q] > hi) {
+      return 0;
+    }
+  }
+  if (!(tn <= tf)) return 0;
+  *t_enter = tn;
+  return 1;
+}
+
+/* Shadow map of the obstacle mask for one directional light: texel (i, j)
+ * (column i, row j of an R x R map) holds the entry parameter t of the first
+ * occupied voxel along the line o + t w through
+ *   o = c + a e1 + b e2,  a = ((i + 0.5)/R - 0.5) S,  b = ((j + 0.5)/R - 0.5) S,
+ * i.e. the minimum over all occupied voxels the line meets (brute force), or
+ * +infinity.  t is signed distance from the map plane along w. */
+int nslo_shadow_map(const uint8_t* mask, int nx, int ny, int nz, const float dir[3], int R,
+                    float* out) {
+  if (!mask || !dir || !out || R < 1) return 1;
+  light_frame L;
+  if (light_setup(dir, nx, ny, nz, &L)) return 1;
+  const size_t nvox = (size_t)nx * ny * nz;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int j = 0; j < R; ++j) {
+    for (int i = 0; i < R; ++i) {
+      float ua = ((float)i + 0.5f) / (float)R;
+      float ub = ((float)j + 0.5f) / (float)R;
+      float a = (ua - 0.5f) * L.S;
+      float b = (ub - 0.5f) * L.S;
+      float o[3];
+      for (int k = 0; k < 3; ++k) {
+        float t1 = a * L.e1[k];
+        float t2 = b * L.e2[k];
+        o[k] = (L.c[k] + t1) + t2;
+      }
+      float best = INFINITY;
+      for (size_t v = 0; v < nvox; ++v) {
+        if (!mask[v]) continue;
+        const int vi = (int)(v % nx), vj = (int)((v / nx) % ny), vk = (int)(v / ((size_t)nx * ny));
+        float te;
+        if (voxel_entry(o, L.w, vi, vj, vk, &te) && te < best) best = te;
+      }
+      out[(size_t)j * R + i] = best;
+    }
+  }
+  return 0;
+}
+
+/* Visibility of pixel p's smoke shell from light l: the shell point is
+ * x = o + (t_in + D) d on the pixel's ray (t_in its box entry, D the guide's
+ * depth channel; the jitter offset below one step is ignored); in the light's
+ * frame, relative to c, it has map coordinates (a, b) = (x - c).(e1, e2) and
+ * depth z = (x - c).w, all in binary32 in this order.  It is shadowed when its
+ * texel (floor((a/S + 1/2) R), likewise for b) lies on the map and
+ * z > t_hit + bias.  D = 0 (no shell) and rays missing the box are lit. */
+static int shell_shadowed(const cam_frame* fr, const float nbox[3], const light_frame* L,
+                          const float* map, int R, float bias, int i, int j, float D) {
+  if (!(D > 0.0f) || !map) return 0;
+  float o[3], d[3], tin, tout;
+  pixel_ray(fr, i, j, o, d);
+  if (!clip_box(o, d, nbox, &tin, &tout)) return 0;
+  const float t = tin + D;
+  float rel[3];
+  for (int k = 0; k < 3; ++k) {
+    float st = t * d[k];
+    float x = o[k] + st;
+    rel[k] = x - L->c[k];
+  }
+  float pa0 = rel[0] * L->e1[0], pa1 = rel[1] * L->e1[1], pa2 = rel[2] * L->e1[2];
+  float pb0 = rel[0] * L->e2[0], pb1 = rel[1] * L->e2[1], pb2 = rel[2] * L->e2[2];
+  float pz0 = rel[0] * L->w[0], pz1 = rel[1] * L->w[1], pz2 = rel[2] * L->w[2];
+  float a = (pa0 + pa1) + pa2;
+  float b = (pb0 + pb1) + pb2;
+  float z = (pz0 + pz1) + pz2;
+  float fa = (a / L->S + 0.5f) * (float)R;
+  float fb = (b / L->S + 0.5f) * (float)R;
+  float ffa = floorf(fa), ffb = floorf(fb);
+  if (!(ffa >= 0.0f && ffa < (float)R && ffb >= 0.0f && ffb < (float)R)) return 0;
+  const float th = map[(size_t)(int)ffb * R + (int)ffa];
+  const float lim = th + bias;
+  return z > lim;
+}
+
+/* Six-way shading with obstacle shadows: nslo_shade with each light's term
+ * multiplied by its visibility (0 or 1); maps[l] may be NULL (no obstacle
+ * shadow for light l).  guide is the float32 [3][H][W] guide (D = plane 2). */
+int nslo_shade_shadowed(const double* lm, const float* guide, int H, int W, const nslo_camera* cam,
+                        const nslo_light* lights, int n_lights, int nx, int ny, int nz,
+                        const float* const* maps, int R, float bias, double* rgba) {
+  if (!lm || !guide || !cam || !rgba || n_lights < 0 || n_lights > 64 || (n_lights > 0 && !lights))
+    return 1;
+  cam_frame fr;
+  cam_setup(cam, &fr);
+  const float nbox[3] = {(float)nx, (float)ny, (float)nz};
+  const size_t P = (size_t)H * W;
+  double wts[64][6];
+  light_frame LF[64];
+  for (int l = 0; l < n_lights; ++l) {
+    double v[3] = {lights[l].dir[0], lights[l].dir[1], lights[l].dir[2]};
+    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(nv > 0.0)) return 1;
+    for (int k = 0; k < 3; ++k) v[k] /= nv;
+    double w[3];
+    w[0] = v[0] * fr.r[0] + v[1] * fr.r[1] + v[2] * fr.r[2];
+    w[1] = v[0] * fr.u[0] + v[1] * fr.u[1] + v[2] * fr.u[2];
+    w[2] = v[0] * fr.f[0] + v[1] * fr.f[1] + v[2] * fr.f[2];
+    for (int p = 0; p < 3; ++p) {
+      wts[l][2 * p] = w[p] >= 0.0 ? w[p] : 0.0;
+      wts[l][2 * p + 1] = w[p] < 0.0 ? -w[p] : 0.0;
+    }
+    if (light_setup(lights[l].dir, nx, ny, nz, &LF[l])) return 1;
+  }
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      const size_t p = (size_t)j * W + i;
+      const float D = guide[2 * P + p];
+      double vis[64];
+      for (int l = 0; l < n_lights; ++l)
+        vis[l] = shell_shadowed(&fr, nbox, &LF[l], maps ? maps[l] : NULL, R, bias, i, j, D) ? 0.0 : 1.0;
+      const double E = lm[7 * P + p];
+      for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int l = 0; l < n_lights; ++l) {
+          double s = 0.0;
+          for (int q = 0; q < 6; ++q) s += wts[l][q] * lm[q * P + p];
+          acc += vis[l] * lights[l].intensity[c] * s;
+        }
+        rgba[c * P + p] = acc + E;
+      }
+      double a = 1.0 - lm[6 * P + p];
+      rgba[3 * P + p] = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    }
+  return 0;
+}

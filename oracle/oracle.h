@@ -115,4 +115,16 @@ int64_t nslo_nafblock_params(int C);
 #ifdef __cplusplus
 }
 #endif
+
+/* Obstacle shadowing (Sec. 4.5).  Shadow map of the obstacle mask for one
+ * directional light (dir toward the light): R x R float32, texel (i, j) = the
+ * entry parameter of the first occupied voxel along its light ray, +inf for
+ * none.  Returns 0 on success. */
+int nslo_shadow_map(const uint8_t* mask, int nx, int ny, int nz, const float dir[3], int R,
+                    float* out);
+/* nslo_shade with each light's term times the visibility of the pixel's smoke
+ * shell (guide depth D) against that light's shadow map (maps[l] may be NULL). */
+int nslo_shade_shadowed(const double* lm, const float* guide, int H, int W, const nslo_camera* cam,
+                        const nslo_light* lights, int n_lights, int nx, int ny, int nz,
+                        const float* const* maps, int R, float bias, double* rgba);
 #endif
