@@ -188,6 +188,49 @@ NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, f
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
                                  int precision, float* lightmaps_dev, void* stream);
 
+/* Obstacle shadowing, Sec. 4.5 (a depth-based screen-space approximation).
+ * Shadow map of the obstacle for one directional light: the obstacle mask is
+ * rendered from the light as the depth of the first occupied voxel along each
+ * light ray.  The light's frame is built in binary64 and rounded once: w =
+ * -dir/|dir| (propagation), e1 = normalize(w x a) with a = +Y (+Z when
+ * |w_y| > 0.9), e2 = e1 x w.  The map is the square of side S = |(nx, ny, nz)|
+ * centred on the grid centre c in the plane through c spanned by (e1, e2):
+ * texel (i, j) (column i, row j) holds the entry parameter t of the first
+ * occupied voxel along c + a e1 + b e2 + t w, a = ((i + 0.5)/R - 0.5) S,
+ * b = ((j + 0.5)/R - 0.5) S (signed distance from the map plane along w), or
+ * +infinity when the line meets no occupied voxel.
+ *   mask_dev        [nz][ny][nx] uint8, non-zero = obstacle (device)
+ *   light_dir       world-space vector toward the light (host, 3 floats)
+ *   resolution      R in [1, 8192]
+ *   shadow_map_dev  output [R][R] float32 (device, 16-byte aligned)
+ * Asynchronous on the stream; no context is needed.  NSL_ERR_INVALID_ARG for
+ * bad arguments, NSL_ERR_CUDA for a launch failure. */
+NSL_API nsl_status nsl_obstacle_shadow_map(const uint8_t* mask_dev, int nx, int ny, int nz,
+                                           const float light_dir[3], int resolution, float* shadow_map_dev,
+                                           void* stream);
+
+/* Six-way shading with obstacle shadows (Sec. 4.5): nsl_shade with each light's
+ * term multiplied by the visibility of the pixel's smoke shell.  The shell point
+ * is x = o + (t_in + D) d on the pixel's camera ray (t_in its entry into the
+ * context's grid box, D the guide's depth channel; the jitter offset below one
+ * step is ignored).  In light l's frame it has map coordinates a = (x - c).e1,
+ * b = (x - c).e2 and depth z = (x - c).w; it is shadowed when its texel
+ * (floor((a/S + 1/2) R), floor((b/S + 1/2) R)) lies on the map and
+ * z > t_hit + bias.  Pixels with D = 0 (no shell), rays that miss the box and
+ * lights whose map pointer is NULL are lit.  These decisions are taken in
+ * binary32 with one rounding per operation in a fixed order.
+ *   guide_dev        [3][H][W] float32 guide of the same frame (D in plane 2)
+ *   lights           n_lights in [0, 16]
+ *   shadow_maps_dev  host array of n_lights device pointers to [R][R] maps from
+ *                    nsl_obstacle_shadow_map (entries may be NULL), or NULL
+ *   resolution       R of the maps;  bias  depth bias in voxels
+ *   rgba_dev         output [4][H][W] float32
+ * Buffers 16-byte aligned.  Asynchronous on the stream. */
+NSL_API nsl_status nsl_shade_shadowed(nsl_ctx* ctx, const float* lightmaps_dev, const float* guide_dev,
+                                      int width, int height, const nsl_camera* cam, const nsl_light* lights,
+                                      int n_lights, const float* const* shadow_maps_dev, int resolution,
+                                      float bias, float* rgba_dev, void* stream);
+
 /* Texture formats of nsl_pack_lightmaps. */
 enum { NSL_TEX_RGBA8 = 0, NSL_TEX_RGBA16F = 1, NSL_TEX_RGBA32F = 2 };
 

@@ -492,6 +492,70 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
   return NSL_OK;
 }
 
+nsl_status nsl_obstacle_shadow_map(const uint8_t* mask_dev, int nx, int ny, int nz, const float light_dir[3],
+                                   int resolution, float* shadow_map_dev, void* stream) {
+  const char* fn = "nsl_obstacle_shadow_map";
+  if (!mask_dev || !light_dir || !shadow_map_dev) return fail(NSL_ERR_INVALID_ARG, "%s: NULL argument", fn);
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail(NSL_ERR_INVALID_ARG, "%s: grid dims out of range", fn);
+  if (resolution < 1 || resolution > 8192)
+    return fail(NSL_ERR_INVALID_ARG, "%s: resolution must be in [1, 8192]", fn);
+  if (!aligned16(shadow_map_dev)) return fail(NSL_ERR_INVALID_ARG, "%s: map must be 16-byte aligned", fn);
+  LightFrame L;
+  if (!light_frame_from(light_dir, nx, ny, nz, &L))
+    return fail(NSL_ERR_INVALID_ARG, "%s: zero or non-finite light direction", fn);
+  cudaError_t e = launch_shadow_map(mask_dev, nx, ny, nz, L, resolution, shadow_map_dev,
+                                    static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return NSL_OK;
+}
+
+nsl_status nsl_shade_shadowed(nsl_ctx* c, const float* lm, const float* guide, int width, int height,
+                              const nsl_camera* cam, const nsl_light* lights, int n_lights,
+                              const float* const* shadow_maps_dev, int resolution, float bias, float* rgba,
+                              void* stream) {
+  const char* fn = "nsl_shade_shadowed";
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+  if (!lm || !guide || !rgba) return fail(NSL_ERR_INVALID_ARG, "%s: NULL buffer", fn);
+  if (!aligned16(lm) || !aligned16(guide) || !aligned16(rgba))
+    return fail(NSL_ERR_INVALID_ARG, "%s: buffers must be 16-byte aligned", fn);
+  if (!cam) return fail(NSL_ERR_INVALID_ARG, "%s: camera is NULL", fn);
+  if (width < 8 || height < 8 || width % 8 || height % 8 || width > 8192 || height > 8192)
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad size %dx%d", fn, width, height);
+  if (n_lights < 0 || n_lights > kMaxShadowLights || (n_lights > 0 && !lights))
+    return fail(NSL_ERR_INVALID_ARG, "%s: n_lights must be in [0, %d]", fn, kMaxShadowLights);
+  if (resolution < 1 || resolution > 8192)
+    return fail(NSL_ERR_INVALID_ARG, "%s: resolution must be in [1, 8192]", fn);
+  if (!std::isfinite(bias)) return fail(NSL_ERR_INVALID_ARG, "%s: bias must be finite", fn);
+  nsl_camera cc = *cam;
+  cc.width = width;
+  cc.height = height;
+  nsl_status st = check_camera_basic(&cc, fn);
+  if (st != NSL_OK) return st;
+  ShadowShadeArgs a{};
+  a.lm = lm;
+  a.guide = guide;
+  a.rgba = rgba;
+  a.W = width;
+  a.H = height;
+  a.R = resolution;
+  a.n_lights = n_lights;
+  a.bias = bias;
+  a.fx = (float)c->grid.nx;
+  a.fy = (float)c->grid.ny;
+  a.fz = (float)c->grid.nz;
+  cam_frame_from(cc, &a.cam);
+  for (int l = 0; l < n_lights; ++l) {
+    if ((st = shade_matrix(cc, lights + l, 1, a.light[l].M, fn)) != NSL_OK) return st;
+    if (!light_frame_from(lights[l].dir, c->grid.nx, c->grid.ny, c->grid.nz, &a.light[l].F))
+      return fail(NSL_ERR_INVALID_ARG, "%s: light %d has a zero direction", fn, l);
+    a.light[l].map = shadow_maps_dev ? shadow_maps_dev[l] : nullptr;
+  }
+  cudaError_t e = launch_shade_shadowed(a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, fn);
+  return NSL_OK;
+}
+
 nsl_status nsl_shade(nsl_ctx* c, const float* lm, int width, int height, const nsl_camera* cam,
                      const nsl_light* lights, int n_lights, float* rgba, void* stream) {
   if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_shade: ctx is NULL");

@@ -70,6 +70,30 @@ struct CamFrame {
 };
 void cam_frame_from(const nsl_camera& c, CamFrame* out);
 
+// Obstacle shadowing (Sec. 4.5): a directional light's frame and map square.
+struct LightFrame {
+  float w[3], e1[3], e2[3], c[3], S;
+};
+bool light_frame_from(const float dir[3], int nx, int ny, int nz, LightFrame* L);
+constexpr int kMaxShadowLights = 16;
+struct ShadowLight {
+  float M[3][6];       // this light's six-way weights times its intensity
+  LightFrame F;
+  const float* map;    // [R][R] first-hit depths, or null (no obstacle shadow)
+};
+struct ShadowShadeArgs {
+  const float* lm;     // [8][H][W]
+  const float* guide;  // [3][H][W], depth D in plane 2
+  float* rgba;         // [4][H][W]
+  int W, H, R, n_lights;
+  float bias, fx, fy, fz;
+  CamFrame cam;
+  ShadowLight light[kMaxShadowLights];
+};
+cudaError_t launch_shadow_map(const uint8_t* mask, int nx, int ny, int nz, const LightFrame& L, int R,
+                              float* out, cudaStream_t s);
+cudaError_t launch_shade_shadowed(const ShadowShadeArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // guide march
 // ---------------------------------------------------------------------------

@@ -30,7 +30,8 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_default_server_opts", "nsl_server_create", "nsl_server_destroy",
            "nsl_server_add_plume", "nsl_server_remove_plume", "nsl_server_submit", "nsl_server_wait",
            "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
-           "nsl_server_reset_stats", "nsl_pack_lightmaps"]
+           "nsl_server_reset_stats", "nsl_pack_lightmaps", "nsl_obstacle_shadow_map",
+           "nsl_shade_shadowed"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -112,6 +113,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
     lib.nsl_pack_lightmaps.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.nsl_pack_lightmaps.restype = C.c_int
+    lib.nsl_obstacle_shadow_map.argtypes = [vp, i, i, i, C.POINTER(C.c_float * 3), i, vp, vp]
+    lib.nsl_obstacle_shadow_map.restype = C.c_int
+    lib.nsl_shade_shadowed.argtypes = [vp, vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i,
+                                       C.POINTER(vp), i, f, vp, vp]
+    lib.nsl_shade_shadowed.restype = C.c_int
     lib.nsl_render_frame_host.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), C.POINTER(nsl_light),
                                           i, f, C.POINTER(nsl_march_opts), i, vp, vp, vp, vp]
     lib.nsl_render_frame_host_async.argtypes = lib.nsl_render_frame_host.argtypes
@@ -307,6 +313,30 @@ def nsl_pack_lightmaps(lightmaps, width, height, fmt, tex1, tex2, stream=None):
     check(load().nsl_pack_lightmaps(_dptr(lightmaps, F32), int(width), int(height), int(fmt),
                                     _dptr(tex1, _TEX_DTYPES[fmt]), _dptr(tex2, _TEX_DTYPES[fmt]),
                                     _stream(stream)), "nsl_pack_lightmaps")
+
+
+def nsl_obstacle_shadow_map(mask, light_dir, resolution, out, stream=None):
+    """Shadow map of a [nz][ny][nx] uint8 CUDA mask for a light toward light_dir
+    into out, a [R][R] float32 CUDA tensor."""
+    nz, ny, nx = mask.shape
+    if tuple(out.shape) != (int(resolution), int(resolution)):
+        raise ValueError("out must be [R][R]")
+    d = (C.c_float * 3)(*[float(v) for v in light_dir])
+    check(load().nsl_obstacle_shadow_map(_dptr(mask, ("uint8",)), nx, ny, nz, C.byref(d), int(resolution),
+                                         _dptr(out, F32), _stream(stream)), "nsl_obstacle_shadow_map")
+
+
+def nsl_shade_shadowed(ctx, lightmaps, guide, width, height, cam, light_list, maps, resolution, bias, rgba,
+                       stream=None):
+    """Six-way shading with obstacle shadows; maps: one [R][R] CUDA tensor (or
+    None) per light."""
+    if len(maps) != len(light_list):
+        raise ValueError("one map (or None) per light")
+    ptrs = (C.c_void_p * max(1, len(maps)))(*[None if m is None else _dptr(m, F32).value for m in maps])
+    check(load().nsl_shade_shadowed(ctx, _dptr(lightmaps, F32), _dptr(guide, F32), int(width), int(height),
+                                    C.byref(camera(cam)), lights(light_list), len(light_list), ptrs,
+                                    int(resolution), float(bias), _dptr(rgba, F32), _stream(stream)),
+          "nsl_shade_shadowed")
 
 
 def nsl_render_frame_host(ctx, density_np, mask_np, cam, light_list, step, precision,
