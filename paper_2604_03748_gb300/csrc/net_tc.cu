@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_fp8.h>
 #include "nsl_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -78,48 +79,25 @@ __device__ __forceinline__ uint4 ldg128(const void* p) {
   return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-// E4M3 code of a finite float, rounded to nearest with ties to even and
-// saturated at 448, from the format's definition (exponent bias 7, 3 fraction
-// bits, subnormal quantum 2^-9, S.1111.111 = NaN is never produced).  Written
-// out with integer operations so that ties, which power-of-two scaling of
-// FP16 values makes common, are broken exactly as the definition says.
-__device__ __forceinline__ uint32_t e4m3_rne(float v) {
-  const uint32_t bits = __float_as_uint(v);
-  const uint32_t sign = (bits >> 24) & 0x80u;
-  const uint32_t a = bits & 0x7fffffffu;
-  const int e = (int)(a >> 23) - 127;          // unbiased exponent of a normal float
-  if (e < -6) {
-    // E4M3 subnormal range: integer multiple of 2^-9, rounded to nearest even
-    const int m = __float2int_rn(__uint_as_float(a) * 512.0f);  // exact scaling
-    return sign | (uint32_t)m;                 // m = 8 is the code of 2^-6
-  }
-  uint32_t r = (a >> 20) & 7u;                 // top three fraction bits
-  const uint32_t rem = a & 0xfffffu, half = 0x80000u;
-  int E = e;
-  if (rem > half || (rem == half && (r & 1u))) {
-    if (++r == 8u) { r = 0u; ++E; }
-  }
-  if (E > 8 || (E == 8 && r == 7u)) return sign | 0x7eu;  // saturate at 448
-  return sign | ((uint32_t)(E + 7) << 3) | r;
-}
-
 // FP8 path: 16 FP16 activations (two 16-byte words, channel order) times the
-// tensor's inverse scale (a power of two), each rounded to nearest-even E4M3
-// with saturation; byte c of the result is channel c.
+// tensor's inverse scale (a power of two, so the product is exact), each
+// converted to E4M3 by the hardware's paired conversion (round to nearest
+// even, saturating at the largest finite magnitude 448); byte c of the result
+// is channel c.
 __device__ __forceinline__ uint4 q8_pack16(uint4 lo, uint4 hi, float inv) {
-  const __half* h0 = reinterpret_cast<const __half*>(&lo);
-  const __half* h1 = reinterpret_cast<const __half*>(&hi);
+  const __half2* h0 = reinterpret_cast<const __half2*>(&lo);
+  const __half2* h1 = reinterpret_cast<const __half2*>(&hi);
   uint32_t w[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    uint32_t acc = 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = 4 * q + c;
-      const float v = __fmul_rn(__half2float(i < 8 ? h0[i] : h1[i - 8]), inv);
-      acc |= e4m3_rne(v) << (8 * c);
-    }
-    w[q] = acc;
+    const __half2 pa = q < 2 ? h0[2 * q] : h1[2 * q - 4];
+    const __half2 pb = q < 2 ? h0[2 * q + 1] : h1[2 * q - 3];
+    const float2 fa = __half22float2(pa), fb = __half22float2(pb);
+    const uint32_t c01 = __nv_cvt_float2_to_fp8x2(make_float2(__fmul_rn(fa.x, inv), __fmul_rn(fa.y, inv)),
+                                                  __NV_SATFINITE, __NV_E4M3);
+    const uint32_t c23 = __nv_cvt_float2_to_fp8x2(make_float2(__fmul_rn(fb.x, inv), __fmul_rn(fb.y, inv)),
+                                                  __NV_SATFINITE, __NV_E4M3);
+    w[q] = (c01 & 0xffffu) | (c23 << 16);
   }
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
