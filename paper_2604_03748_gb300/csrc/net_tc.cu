@@ -277,7 +277,7 @@ __device__ __forceinline__ void load_halo_q8(const ConvImg<__half>& a, int tile,
 }
 
 template <typename T, int NT, bool Q8>
-__device__ __forceinline__ void conv_epilogue(const ConvImg<T>& a, const float* __restrict__ bias,
+__device__ __forceinline__ float conv_epilogue(const ConvImg<T>& a, const float* __restrict__ bias,
                                               const float* __restrict__ wscale, int tile,
                                               uint32_t tacc, int n0, int cout) {
   const int warp = threadIdx.x >> 5;
@@ -314,11 +314,11 @@ __device__ __forceinline__ void conv_epilogue(const ConvImg<T>& a, const float* 
       reinterpret_cast<uint4*>(dst + c)[1] = reinterpret_cast<const uint4*>(h)[1];
     }
   }
-  if constexpr (Q8) {
-    // the stored (FP16-rounded) maximum: rounding is monotonic
-    amax_publish(a.amax_out, valid ? __half2float(__float2half_rn(mx)) : 0.f);
-  }
+  // FP8 path: this thread's largest stored (FP16-rounded) value, rounding
+  // being monotonic; the kernel publishes the running maximum
+  return Q8 && valid ? __half2float(__float2half_rn(mx)) : 0.f;
 }
+
 
 // N tile of a 3x3 layer: all output channels up to 64, and 32 when Cin = 128
 // so that weights + two halo buffers fit in 227 KB of shared memory.
@@ -409,6 +409,20 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
   // E4M3 has format code 0 in the f8f6f4 descriptor, like FP16 in the f16 one
   constexpr uint32_t idesc = idesc_f16kind(Q8 ? 0u : Half<T>::kFmt, 128, NT);
   uint32_t phase[2] = {0u, 0u};
+  // FP8 path: running maximum of this CTA's outputs, published (one atomic per
+  // warp) when its tiles move on to another image and once at the end, rather
+  // than after every tile: per-tile atomics put thousands of updates per
+  // layer on one word
+  int run_im = -1;
+  float run_mx = 0.f;
+  auto amax_track = [&](int im, float v) {
+    if (im != run_im) {
+      if (run_im >= 0) amax_publish(a.img[run_im].amax_out, run_mx);
+      run_im = im;
+      run_mx = 0.f;
+    }
+    run_mx = fmaxf(run_mx, v);
+  };
 #pragma unroll 1
   for (int k = 0; ok && k < nmine; ++k) {
     const int buf = k % S, acc = k & 1;
@@ -444,8 +458,9 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
       phase[pacc] ^= 1u;
       tc_fence_after();
       const int t = blockIdx.x + (k - 1) * gridDim.x, im = image_of(a, t);
-      conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
-                               tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      const float emx = conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
+                                                 tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      if constexpr (Q8) amax_track(im, emx);
     }
     // the buffer of tile k-1 is free again (its MMAs completed): refill it
     issue(k + S - 1);
@@ -457,9 +472,13 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
     } else {
       tc_fence_after();
       const int t = blockIdx.x + (nmine - 1) * gridDim.x, im = image_of(a, t);
-      conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
-                               tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      const float emx = conv_epilogue<T, NT, Q8>(a.img[im], a.bias, a.wscale, t - a.img[im].tile_start,
+                                                 tmem + (uint32_t)(pacc * NT), nt * NT, COUT);
+      if constexpr (Q8) amax_track(im, emx);
     }
+  }
+  if constexpr (Q8) {
+    if (run_im >= 0) amax_publish(a.img[run_im].amax_out, run_mx);
   }
   cp_async_wait<0>();
   tc_fence_before();
@@ -560,6 +579,8 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   constexpr uint32_t idesc = idesc_f16kind(Q8 ? 0u : Half<T>::kFmt, 128, N);
   uint32_t phase[2] = {0u, 0u};
   int buf = 0, prev = -1, prevbuf = 0;
+  int run_im = -1;
+  float run_mx = 0.f;
 
   auto epilogue = [&](int gtile, int b) {
     const int imi = image_of(a, gtile);
@@ -599,7 +620,15 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
         reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(h)[1];
       }
     }
-    if constexpr (Q8) amax_publish(im.amax_out, valid ? __half2float(__float2half_rn(mx)) : 0.f);
+    if constexpr (Q8) {
+      // running maximum as in the 3x3 layers
+      if (imi != run_im) {
+        if (run_im >= 0) amax_publish(a.img[run_im].amax_out, run_mx);
+        run_im = imi;
+        run_mx = 0.f;
+      }
+      run_mx = fmaxf(run_mx, valid ? __half2float(__float2half_rn(mx)) : 0.f);
+    }
   };
 
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -674,6 +703,9 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
       tc_fence_after();
       epilogue(prev, prevbuf);
     }
+  }
+  if constexpr (Q8) {
+    if (run_im >= 0) amax_publish(a.img[run_im].amax_out, run_mx);
   }
   tc_fence_before();
   __syncthreads();
