@@ -20,6 +20,8 @@ Parity status per function (pins live in tests/test_oracle_*.py):
                         ties to even, clamping; binary16 against numpy's cast)
   guide light sets      pinned (constant-cube closed form for front only and
                         front/left/right)
+  guide shadow volume   pinned (constant-cube closed form of the interpolated
+                        voxel-centre transmittances)
   shadow_map            pinned (single voxel and slab closed forms, axis and
                         oblique lights)
   shade_shadowed        pinned (occluder slab: shadowed pixels keep only E,
@@ -64,7 +66,7 @@ class _Opts(C.Structure):
     _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
                 ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
                 ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("margin", C.c_float),
-                ("light_set", C.c_int)]
+                ("light_set", C.c_int), ("shadow_volume", C.c_int)]
 
 
 class _Light(C.Structure):
@@ -168,7 +170,8 @@ def _mask(mask):
 
 
 DEFAULT_OPTS = dict(tau_depth=0.01, t_min=1e-4, jitter=1, seed=0, frame=0, phase_g=0.0,
-                    surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5, light_set=0)
+                    surrogate_I=(1.0, 1.0, 1.0), segment_exact=0, margin=1e-5, light_set=0,
+                    shadow_volume=0)
 
 
 def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
@@ -189,6 +192,7 @@ def guide(density, mask, camera, step, sigma_scale=1.0, rows=None, **opts):
     op.phase_g = o["phase_g"]; op.surrogate_I[:] = list(o["surrogate_I"])
     op.segment_exact = int(o["segment_exact"]); op.margin = o["margin"]
     op.light_set = int(o["light_set"])
+    op.shadow_volume = int(o["shadow_volume"])
     cam = _cam(camera)
     r0, r1 = (0, H) if rows is None else rows
     rc = lib.nslo_guide_rows(_ptr(d), _ptr(m), nx, ny, nz, float(sigma_scale), C.byref(cam),

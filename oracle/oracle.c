@@ -245,6 +245,34 @@ static double shadow_T(const field* F, const float p[3], const float s[3], float
   return T;
 }
 
+/* Trilinear value of a cell-centred volume v [nz][ny][nx] at p (inside the
+ * box): q = p - 0.5 with clamp-to-edge indices, as for the density. */
+static double vol_at(const double* v, int nx, int ny, int nz, const float p[3]) {
+  double q[3] = {(double)p[0] - 0.5, (double)p[1] - 0.5, (double)p[2] - 0.5};
+  int i0[3];
+  double t[3];
+  for (int k = 0; k < 3; ++k) {
+    double fl = floor(q[k]);
+    i0[k] = (int)fl;
+    t[k] = q[k] - fl;
+  }
+  int lim[3] = {nx - 1, ny - 1, nz - 1};
+  int ia[3], ib[3];
+  for (int k = 0; k < 3; ++k) {
+    ia[k] = clampi(i0[k], 0, lim[k]);
+    ib[k] = clampi(i0[k] + 1, 0, lim[k]);
+  }
+  double acc = 0.0;
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+        size_t idx = ((size_t)(dz ? ib[2] : ia[2]) * ny + (dy ? ib[1] : ia[1])) * nx + (dx ? ib[0] : ia[0]);
+        acc += w * v[idx];
+      }
+  return acc;
+}
+
 int nslo_guide(const float* density, const uint8_t* mask, int nx, int ny, int nz,
                double sigma_scale, const nslo_camera* cam, float h,
                const nslo_march_opts* op, double* guide, int64_t* samples, uint8_t* flags) {
@@ -267,6 +295,30 @@ int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, i
   const size_t plane = (size_t)W * H;
   const double t_min = op->t_min, margin = op->margin;
   const double g = op->phase_g;
+
+  /* shadow_volume: the top/bottom (or right/left) transmittances marched once
+   * from every voxel centre, as from a view sample */
+  double* volT = NULL;
+  double* volB = NULL;
+  if (op->shadow_volume && op->light_set != 1) {
+    const size_t nv = (size_t)nx * ny * nz;
+    volT = (double*)malloc(nv * sizeof(double));
+    volB = (double*)malloc(nv * sizeof(double));
+    if (!volT || !volB) { free(volT); free(volB); return 1; }
+    const float* sd = op->light_set == 2 ? fr.r : fr.u;
+    const float st[3] = {sd[0], sd[1], sd[2]}, sb[3] = {-sd[0], -sd[1], -sd[2]};
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const float p[3] = {(float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f};
+          int64_t ns_unused = 0;
+          int nf_unused = 0;
+          const size_t idx = ((size_t)k * ny + j) * nx + i;
+          volT[idx] = shadow_T(&F, p, st, h, t_min, margin, &ns_unused, &nf_unused);
+          volB[idx] = shadow_T(&F, p, sb, h, t_min, margin, &ns_unused, &nf_unused);
+        }
+  }
 
 #pragma omp parallel for schedule(dynamic, 4)
   for (int j = row0; j < row1; ++j) {
@@ -313,8 +365,13 @@ int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, i
            * shadow rays of such a sample are not marched (and not counted) */
           double Tt = 1.0, Tb = 1.0;
           if (sg > 0.0 && side_on) {
-            Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
-            Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
+            if (volT) {
+              Tt = vol_at(volT, nx, ny, nz, p);
+              Tb = vol_at(volB, nx, ny, nz, p);
+            } else {
+              Tt = shadow_T(&F, p, s_top, h, t_min, margin, &ns, &near_term);
+              Tb = shadow_T(&F, p, s_bot, h, t_min, margin, &ns, &near_term);
+            }
           }
           double Ln = P_f * op->surrogate_I[0] * T;
           if (side_on) Ln += P_t * op->surrogate_I[1] * Tt + P_b * op->surrogate_I[2] * Tb;
@@ -334,6 +391,8 @@ int nslo_guide_rows(const float* density, const uint8_t* mask, int nx, int ny, i
       if (flags) flags[pix] = (uint8_t)(near_term | (near_depth << 1));
     }
   }
+  free(volT);
+  free(volB);
   return 0;
 }
 

@@ -37,6 +37,10 @@ typedef struct {
   int light_set;          /* surrogate lights (Sec. 5, ablation on the guiding
                              light directions): 0 front/top/bottom, 1 front
                              only, 2 front/left/right */
+  int shadow_volume;      /* 0: side-light shadows marched from every view
+                             sample; 1: one shadow march per voxel centre into
+                             two transmittance volumes, read trilinearly at the
+                             view samples (an approximation) */
 } nslo_march_opts;
 
 typedef struct {

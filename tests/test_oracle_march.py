@@ -107,6 +107,33 @@ def test_light_sets_constant_cube_closed_form(orc, jitter):
         np.testing.assert_allclose(g2[1, :, i], T, rtol=1e-12)
 
 
+@pytest.mark.parametrize("jitter", [0, 1])
+def test_shadow_volume_constant_cube_closed_form(orc, jitter):
+    """Transmittance-volume mode: every voxel centre y_c holds exp(-sigma h K)
+    with K = floor((n - y_c) / h) toward the top and floor(y_c / h) toward the
+    bottom; a view sample at height y reads the linear interpolation between the
+    voxel centres y - 1/2 +- 1/2 (the box is constant along x and z).  Pixel row
+    j sits at y = 31 - 2j, so it blends the centres 30.5 - 2j and 31.5 - 2j
+    half and half."""
+    n, h, sig = 32, 4.0, 0.05
+    W = H = 16
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = axis_camera(n, W, H)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=jitter, t_min=0.0, shadow_volume=1, seed=9)
+    s32 = float(np.float32(sig))
+    q = math.exp(-s32 * h)
+    M = n // int(h)
+    for j in range(H):
+        yc = (30.5 - 2 * j, 31.5 - 2 * j)
+        Tt = 0.5 * sum(q ** int((n - y) // h) for y in yc)
+        Tb = 0.5 * sum(q ** int(y // h) for y in yc)
+        front = sum(q ** (2 * (m - 1)) for m in range(1, M + 1))
+        geo = sum(q ** (m - 1) for m in range(1, M + 1))
+        L = s32 * h * (front + (Tt + Tb) * geo) / FOUR_PI
+        np.testing.assert_allclose(g[0, j], L, rtol=1e-12)
+        np.testing.assert_allclose(g[1, j], math.exp(-s32 * n), rtol=1e-12)
+
+
 def test_constant_cube_with_early_termination(orc):
     n, h, sig = 32, 4.0, 0.9
     vol = np.full((n, n, n), sig, np.float32)
