@@ -95,12 +95,19 @@ typedef struct {
                             NSL_LIGHTS_F front only (no shadow rays),
                             NSL_LIGHTS_FLR front/left/right (side pair along the
                             camera's right axis; surrogate_I[1] right, [2] left) */
+  int shadow_volume;     /* 0: the side lights' shadow rays are marched from every
+                            view sample (Alg. 1); 1: they are marched once from
+                            every voxel centre into two transmittance volumes that
+                            the view march reads trilinearly (an approximation of
+                            Alg. 1, cheaper when view samples outnumber voxels;
+                            single-plume entry points only) */
 } nsl_march_opts;
 
 enum { NSL_LIGHTS_FTB = 0, NSL_LIGHTS_F = 1, NSL_LIGHTS_FLR = 2 };
 
 /* Default options: tau_depth 0.01, t_min 1e-4, jitter 1, seed 0, frame 0,
- * g 0, intensities 1, segment_exact 0, light_set NSL_LIGHTS_FTB. */
+ * g 0, intensities 1, segment_exact 0, light_set NSL_LIGHTS_FTB,
+ * shadow_volume 0. */
 NSL_API void nsl_default_march_opts(nsl_march_opts* out);
 
 /* Create a context.  Sec. 4.3 (one network for all scenes, Sec. 5).

@@ -102,6 +102,8 @@ struct nsl_ctx {
   std::vector<float> params;
   NetLayout layout{};
   float* staged = nullptr;          // staged extinction grid
+  float* tvol = nullptr;            // transmittance volumes: raw top, raw bottom, staged top, staged bottom
+  size_t tvol_bytes = 0;
   bool staged_valid = false;        // a staging has been queued
   unsigned long long* counter = nullptr;  // sample-count scratch
   int* tile_counter = nullptr;            // march tile queue (scratch)
@@ -138,6 +140,7 @@ void nsl_default_march_opts(nsl_march_opts* o) {
   o->surrogate_I[0] = o->surrogate_I[1] = o->surrogate_I[2] = 1.f;
   o->segment_exact = 0;
   o->light_set = NSL_LIGHTS_FTB;
+  o->shadow_volume = 0;
 }
 
 const char* nsl_last_error(void) { return g_err; }
@@ -227,6 +230,7 @@ void nsl_destroy(nsl_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   cudaFree(c->staged);
+  cudaFree(c->tvol);
   cudaFree(c->counter);
   cudaFree(c->tile_counter);
   cudaFree(c->seg_scratch);
@@ -303,6 +307,8 @@ nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, fl
     return fail(NSL_ERR_INVALID_ARG, "%s: phase_g must be in (-1, 1)", fn);
   if (o.light_set < NSL_LIGHTS_FTB || o.light_set > NSL_LIGHTS_FLR)
     return fail(NSL_ERR_INVALID_ARG, "%s: bad light_set %d", fn, o.light_set);
+  if (o.shadow_volume != 0 && o.shadow_volume != 1)
+    return fail(NSL_ERR_INVALID_ARG, "%s: shadow_volume must be 0 or 1", fn);
   *p = MarchPlume{};
   p->nx = grid.nx; p->ny = grid.ny; p->nz = grid.nz;
   cam_frame_from(cam, &p->cam);
@@ -316,6 +322,7 @@ nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, fl
   for (int k = 0; k < 3; ++k) p->I[k] = o.surrogate_I[k];
   p->segment_exact = o.segment_exact ? 1 : 0;
   p->light_set = o.light_set;
+  p->shadow_volume = o.shadow_volume && o.light_set != NSL_LIGHTS_F ? 1 : 0;
   p->tiles_x = (cam.width + kMarchTX - 1) / kMarchTX;
   p->tile_start = 0;
   return NSL_OK;
@@ -405,6 +412,34 @@ nsl_status nsl_guiding_map(nsl_ctx* c, const void* density, const uint8_t* mask,
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map: density is NULL and no grid is staged");
   }
   p.guide = guide;
+  if (p.shadow_volume) {
+    // one shadow march per voxel centre into the two transmittance volumes,
+    // staged like the density for the view march's trilinear reads
+    const size_t nv = grid_voxels(c->grid), raw = (nv * sizeof(float) + 255) / 256 * 256;
+    const size_t stg = (staged_floats(c->grid.nx, c->grid.ny, c->grid.nz) * sizeof(float) + 255) / 256 * 256;
+    if (2 * raw + 2 * stg > c->tvol_bytes) {
+      NSL_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+      cudaFree(c->tvol);
+      c->tvol = nullptr;
+      c->tvol_bytes = 0;
+      NSL_CUDA_TRY(cudaMalloc(&c->tvol, 2 * raw + 2 * stg));
+      c->tvol_bytes = 2 * raw + 2 * stg;
+    }
+    char* tb = reinterpret_cast<char*>(c->tvol);
+    float* rawT = reinterpret_cast<float*>(tb);
+    float* rawB = reinterpret_cast<float*>(tb + raw);
+    float* stT = reinterpret_cast<float*>(tb + 2 * raw);
+    float* stB = reinterpret_cast<float*>(tb + 2 * raw + stg);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_transmittance_volume(p, rawT, rawB, s);
+    if (e == cudaSuccess)
+      e = launch_stage_volume(rawT, NSL_F32, nullptr, c->grid.nx, c->grid.ny, c->grid.nz, 1.f, stT, s);
+    if (e == cudaSuccess)
+      e = launch_stage_volume(rawB, NSL_F32, nullptr, c->grid.nx, c->grid.ny, c->grid.nz, 1.f, stB, s);
+    if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map: transmittance volumes");
+    p.volT = stT;
+    p.volB = stB;
+  }
   // segmented-march scratch, grown on demand: per pixel the step count, per
   // (segment, pixel) the optical depth, its compensation and the partial radiance
   const int maxseg = march_max_segments(c->grid.nx, c->grid.ny, c->grid.nz, step, kMarchSegLen);
@@ -439,6 +474,7 @@ nsl_status nsl_guide_sample_count(nsl_ctx* c, const nsl_camera* cam, float step,
   nsl_status st = march_setup(c, cam, step, opts, "nsl_guide_sample_count", &p);
   if (st != NSL_OK) return st;
   if (!c->staged_valid) return fail(NSL_ERR_INVALID_ARG, "nsl_guide_sample_count: no grid staged");
+  p.shadow_volume = 0;   // counts the density evaluations of Alg. 1's own shadow marches
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!c->counter) NSL_CUDA_TRY(cudaMalloc(&c->counter, sizeof(unsigned long long)));
   NSL_CUDA_TRY(cudaMemsetAsync(c->counter, 0, sizeof(unsigned long long), s));

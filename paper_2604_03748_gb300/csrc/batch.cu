@@ -174,6 +174,8 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     MarchPlume& m = T.march[k];
     st = fill_march_plume(p.grid, p.camera, p.step_voxels, opts, "nsl_batch", &m);
     if (st != NSL_OK) return st;
+    if (m.shadow_volume)
+      return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: shadow_volume is for the single-plume entry points");
     const size_t P = (size_t)p.camera.width * p.camera.height;
     const bool pre = prestaged && prestaged[k];
     float* staged_k = pre ? const_cast<float*>(prestaged[k])

@@ -464,7 +464,7 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
 
 // One view step n with sigma = s > 0: A_n, the three surrogate lights, L_n;
 // accumulates A_n L_n into (L, Lc) and the optical depth into (tau, tc).
-template <bool kCount, bool kExactLast>
+template <bool kCount, bool kExactLast, bool kVolume = false>
 __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, const Ray& r,
                                           float px, float py, float pz, float s, float& T,
                                           float& tau, float& tc, float& L, float& Lc,
@@ -476,8 +476,16 @@ __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, co
     Ln = r.wf * T;                 // front only: no shadow rays
   } else {
     float Tt, Tb;
-    shadow_pair<kCount, kExactLast>(g, px, py, pz, P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u, h, P.tau_lim,
-                        Tt, Tb, nsamp);
+    if constexpr (kVolume) {
+      // the shadow_volume option: the side lights' transmittances interpolated
+      // from the voxel-centre volumes
+      const Grid gT{P.volT, P.nx, P.ny, P.nz, g.fx, g.fy, g.fz}, gB{P.volB, P.nx, P.ny, P.nz, g.fx, g.fy, g.fz};
+      Tt = interp(fetch(gT, px, py, pz));
+      Tb = interp(fetch(gB, px, py, pz));
+    } else {
+      shadow_pair<kCount, kExactLast>(g, px, py, pz, P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u, h,
+                                      P.tau_lim, Tt, Tb, nsamp);
+    }
     Ln = fmaf(r.wf, T, fmaf(r.wt, Tt, r.wb * Tb));
   }
   kahan_add(L, Lc, A * Ln);
@@ -558,7 +566,7 @@ __device__ __forceinline__ void march_view_pixel(const MarchPlume& P, int i, int
   P.seg_nef[pix] = nef;
 }
 
-template <bool kExactLast>
+template <bool kExactLast, bool kVolume = false>
 __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j, int seg) {
   const CamFrame& c = P.cam;
   const size_t plane = (size_t)c.W * c.H;
@@ -579,7 +587,7 @@ __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j,
     float px, py, pz;
     view_point(r, n, P.h, px, py, pz);
     const float s = sigma_at(g, px, py, pz);
-    if (s > 0.f) view_step<false, kExactLast>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+    if (s > 0.f) view_step<false, kExactLast, kVolume>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
   }
   P.seg_L[k] = L;
 }
@@ -690,6 +698,8 @@ __global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPl
 }
 
 // pass 2: warps take (tile, segment) items from a queue, segment-major
+// (kVolume: the side lights' transmittances from the shadow_volume volumes)
+template <bool kVolume>
 __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
 march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ counter) {
   pdl_wait();      // the view pass's segment starts and the cleared queue
@@ -703,7 +713,7 @@ march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ cou
     const int seg = item / ntiles, tile = item % ntiles;
     const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
     const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
-    if (i < P.cam.W && j < P.cam.H) march_segment<true>(P, i, j, seg);
+    if (i < P.cam.W && j < P.cam.H) march_segment<true, kVolume>(P, i, j, seg);
   }
 }
 
@@ -725,14 +735,16 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
   static int grid = 0;
   if (!grid) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_kernel, kMarchThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_kernel<false>, kMarchThreads, 0) !=
             cudaSuccess || occ < 1)
       occ = 1;
     grid = occ * kNumSMs;
   }
-  if ((e = launch_pdl(march_segment_kernel, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
-                      ntiles * max_segments, tile_counter)) != cudaSuccess)
-    return e;
+  e = p.shadow_volume ? launch_pdl(march_segment_kernel<true>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
+                                   ntiles * max_segments, tile_counter)
+                      : launch_pdl(march_segment_kernel<false>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
+                                   ntiles * max_segments, tile_counter);
+  if (e != cudaSuccess) return e;
   return launch_pdl(march_pixel_pass_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles, tile_counter);
 }
 
@@ -916,6 +928,33 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
                       static_cast<const __half*>(density), mask, nx, ny, nz, scale, staged);
   return launch_pdl(stage_kernel<float>, dim3(blocks), dim3(256), 0, s, static_cast<const float*>(density),
                     mask, nx, ny, nz, scale, staged);
+}
+
+// Transmittance volumes of the shadow_volume option: one thread per voxel
+// centre marches the side lights' two shadow rays exactly as from a view sample
+// (consecutive threads along x, so a warp's rays run side by side).
+__global__ void __launch_bounds__(256) transmittance_volume_kernel(MarchPlume P, float* __restrict__ outT,
+                                                                   float* __restrict__ outB) {
+  pdl_wait();      // the staged grid
+  pdl_trigger();
+  const Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const float* sd = P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u;
+  const size_t n = (size_t)P.nx * P.ny * P.nz;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(v % P.nx), j = (int)((v / P.nx) % P.ny), k = (int)(v / ((size_t)P.nx * P.ny));
+    float Tt, Tb;
+    unsigned long long ns = 0;
+    shadow_pair<false, true>(g, (float)i + 0.5f, (float)j + 0.5f, (float)k + 0.5f, sd, P.h, P.tau_lim, Tt, Tb, ns);
+    outT[v] = Tt;
+    outB[v] = Tb;
+  }
+}
+
+cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s) {
+  const size_t n = (size_t)p.nx * p.ny * p.nz;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  return launch_pdl(transmittance_volume_kernel, dim3(blocks), dim3(256), 0, s, p, outT, outB);
 }
 
 // ---------------------------------------------------------------------------

@@ -100,6 +100,8 @@ extern "C" nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const v
   if (!(o.t_min >= 0.f && o.t_min < 1.f) || !(o.phase_g > -1.f && o.phase_g < 1.f) ||
       o.light_set < NSL_LIGHTS_FTB || o.light_set > NSL_LIGHTS_FLR)
     return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: t_min, phase_g or light_set out of range");
+  if (o.shadow_volume)
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_guiding_map_noalloc: shadow_volume needs a context");
 
   unsigned char* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);

@@ -111,6 +111,9 @@ struct MarchPlume {
   float I[3];         // front, top, bottom intensities
   int segment_exact;
   int light_set;      // NSL_LIGHTS_FTB / _F / _FLR
+  int shadow_volume;  // side-light transmittances read from volT / volB
+  const float* volT;  // staged transmittance volumes (top / bottom), padded quad layout
+  const float* volB;
   float* guide;       // [3][H][W]
   int tiles_x;        // tiles per row
   int tile_start;     // first tile index of this plume in a batch
@@ -163,6 +166,7 @@ inline size_t staged_floats(int nx, int ny, int nz) {
   if (kMarchLayout == kLayoutOcto) return staged_cells(nx, ny, nz) * 8;
   return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : 2);
 }
+cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s);
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s);
 int march_tiles(int W, int H);

@@ -52,7 +52,8 @@ class nsl_light(C.Structure):
 class nsl_march_opts(C.Structure):
     _fields_ = [("tau_depth", C.c_float), ("t_min", C.c_float), ("jitter", C.c_int),
                 ("seed", C.c_uint32), ("frame", C.c_uint32), ("phase_g", C.c_float),
-                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("light_set", C.c_int)]
+                ("surrogate_I", C.c_float * 3), ("segment_exact", C.c_int), ("light_set", C.c_int),
+                ("shadow_volume", C.c_int)]
 
 
 class nsl_plume(C.Structure):

@@ -60,7 +60,8 @@ def test_guide_parity_obstacle_128_full_size(lib, orc):
                                   dict(phase_g=0.5, surrogate_I=(1.0, 0.5, 2.0)),
                                   dict(seed=123, frame=77, tau_depth=0.2),
                                   dict(light_set=1), dict(light_set=2),
-                                  dict(light_set=2, phase_g=0.4, surrogate_I=(1.0, 0.6, 1.7))])
+                                  dict(light_set=2, phase_g=0.4, surrogate_I=(1.0, 0.6, 1.7)),
+                                  dict(shadow_volume=1, t_min=0.0), dict(shadow_volume=1, light_set=2, t_min=0.0)])
 def test_guide_options(lib, orc, opts):
     pf = I.small_case(24, 24, 16, seed=13, kind=I.PERSP, step=2.0)
     ctx = PT.make_ctx(pf)
@@ -330,3 +331,31 @@ def test_guide_parity_paper_step_10(lib, orc):
     assert max(errs) <= PT.TOL_GUIDE, errs
     assert bad <= PT.MAX_EXCUSED_FRAC * g[0].size
     ctx.close()
+
+
+def test_guide_shadow_volume_with_early_termination(lib, orc):
+    """Transmittance-volume mode with shadow rays stopped at t_min: a voxel
+    ray whose stopping decision sits at the threshold moves that voxel's
+    transmittance by at most about t_min, so the guide is held to 1e-4 of its
+    range here (1e-5 with t_min = 0 above)."""
+    pf = I.small_case(24, 32, 24, seed=11, kind=I.PERSP, step=2.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf, shadow_volume=1)
+    o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step, shadow_volume=1)
+    errs, bad = PT.compare_guide(g, o, f, tol=1e-4)
+    assert max(errs) <= 1e-4, errs
+    ctx.close()
+
+
+def test_shadow_volume_rejected_where_unsupported(lib):
+    """The option needs a context: the grouped and allocation-free paths refuse it."""
+    import torch
+    pf = I.small_case(16, 16, 16, seed=3, kind=I.ORTHO, step=2.0, with_mask=False)
+    b = lib.Batch(I.pack_blob(I.make_params(16, 0), 16), 1)
+    item = dict(density=torch.from_numpy(pf.density).cuda(), mask=None, camera=pf.camera, step=pf.step,
+                light=pf.light, guide=torch.empty((3, 16, 16), device="cuda"),
+                lightmaps=torch.empty((8, 16, 16), device="cuda"), rgba=torch.empty((4, 16, 16), device="cuda"))
+    with pytest.raises(lib.NslError) as ei:
+        b.render([item], lib.NSL_PREC_F16, opts=lib.march_opts(shadow_volume=1))
+    assert ei.value.status == lib.NSL_ERR_UNSUPPORTED
+    b.close()
