@@ -25,15 +25,13 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
   return (word >> 22u) ^ word;
 }
 
-// Staged grid layouts (all hold sigma' = scale * rho * [mask == 0], float32):
-//   kLayoutLinear  one float per voxel; a sample reads 8 corners
-//   kLayoutXPair   float2 per voxel (rho(i), rho(i+1)) along x; a sample reads
-//                  4 x 8 bytes
-//   kLayoutQuad    float4 per voxel, the x/y 2x2 neighbourhood of its slice; a
-//                  sample reads 2 x 16 bytes
-// The +1 neighbours are clamped to the grid edge, so on the low edge (index -1)
-// the corner pair holds voxels (0, 1) while both corners should be voxel 0: a
-// zero interpolation weight reproduces that exactly.
+// Staged grid layouts (both hold sigma' = scale * rho * [mask == 0], float32,
+// padded by one cell on the low sides with every neighbour index clamped to the
+// grid, so a sample inside the box needs no clamping):
+//   kLayoutQuad    float4 per cell, the x/y 2x2 neighbourhood of its slice; a
+//                  sample reads 2 x 16 bytes (the default)
+//   kLayoutOcto    2 x float4 per cell, the 2x2x2 neighbourhood; a sample reads
+//                  one 32-byte vector (twice the memory)
 struct Grid {
   const float* __restrict__ v;
   int nx, ny, nz;
@@ -57,38 +55,7 @@ __device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, flo
   float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
   float c00, c10, c01, c11;
-  if constexpr (kMarchLayout == kLayoutLinear) {
-    const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
-    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    const int x0 = max(ix, 0), x1 = min(ix + 1, g.nx - 1);
-    const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
-    const float* r00 = g.v + (z0 * plane + (unsigned)(y0 * g.nx));
-    const float* r01 = g.v + (z0 * plane + (unsigned)(y1 * g.nx));
-    const float* r10 = g.v + (z1 * plane + (unsigned)(y0 * g.nx));
-    const float* r11 = g.v + (z1 * plane + (unsigned)(y1 * g.nx));
-    const float v000 = __ldg(r00 + x0), v100 = __ldg(r00 + x1);
-    const float v010 = __ldg(r01 + x0), v110 = __ldg(r01 + x1);
-    const float v001 = __ldg(r10 + x0), v101 = __ldg(r10 + x1);
-    const float v011 = __ldg(r11 + x0), v111 = __ldg(r11 + x1);
-    c00 = fmaf(tx, v100 - v000, v000);
-    c10 = fmaf(tx, v110 - v010, v010);
-    c01 = fmaf(tx, v101 - v001, v001);
-    c11 = fmaf(tx, v111 - v011, v011);
-  } else if constexpr (kMarchLayout == kLayoutXPair) {
-    const int z0 = max(iz, 0), z1 = min(iz + 1, g.nz - 1);
-    const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
-    if (ix < 0) { ix = 0; tx = 0.f; }
-    const int y0 = max(iy, 0), y1 = min(iy + 1, g.ny - 1);
-    const float2* q = reinterpret_cast<const float2*>(g.v);
-    const float2 a0 = __ldg(q + (z0 * plane + (unsigned)(y0 * g.nx + ix)));
-    const float2 a1 = __ldg(q + (z0 * plane + (unsigned)(y1 * g.nx + ix)));
-    const float2 b0 = __ldg(q + (z1 * plane + (unsigned)(y0 * g.nx + ix)));
-    const float2 b1 = __ldg(q + (z1 * plane + (unsigned)(y1 * g.nx + ix)));
-    c00 = fmaf(tx, a0.y - a0.x, a0.x);
-    c10 = fmaf(tx, a1.y - a1.x, a1.x);
-    c01 = fmaf(tx, b0.y - b0.x, b0.x);
-    c11 = fmaf(tx, b1.y - b1.x, b1.x);
-  } else if constexpr (kMarchLayout == kLayoutOcto) {
+  if constexpr (kMarchLayout == kLayoutOcto) {
     // padded octo cells: cell (ix+1, iy+1, iz+1) of an (nx+1) x (ny+1) x (nz+1)
     // array holds the 8 corners, every index of a point inside the box in range
     const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
@@ -890,31 +857,9 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
                                                     float* __restrict__ out) {
   pdl_wait();      // the previous frame's march may still read the staged grid
   pdl_trigger();
-  auto val = [&](size_t idx) {
-    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
-  };
-  if constexpr (kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto) {
-    const size_t n = staged_cells(nx, ny, nz);
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-         c += (size_t)gridDim.x * blockDim.x)
-      stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, c);
-    return;
-  }
-  const size_t n = (size_t)nx * ny * nz;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
-       c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx);
-    const size_t r = c / nx;
-    const int j = (int)(r % ny);
-    const size_t k = r / ny;
-    const int i1 = min(i + 1, nx - 1), j1 = min(j + 1, ny - 1);
-    const size_t b0 = (k * ny + j) * nx;
-    (void)j1;
-    if constexpr (kMarchLayout == kLayoutLinear)
-      __stcs(out + c, val(b0 + i));
-    else if constexpr (kMarchLayout == kLayoutXPair)
-      __stcs(reinterpret_cast<float2*>(out) + c, make_float2(val(b0 + i), val(b0 + i1)));
-  }
+  const size_t n = staged_cells(nx, ny, nz);
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, c);
 }
 
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
@@ -1039,8 +984,6 @@ int stage_batch_blocks(const StageItem& it) {
 
 cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_starts_dev, int n,
                                int total_blocks, cudaStream_t s) {
-  static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto,
-                "batched staging writes a padded layout");
   if (total_blocks == 0) return cudaSuccess;
   return launch_pdl(stage_batch_kernel, dim3(total_blocks), dim3(256), 0, s, items_dev, block_starts_dev, n);
 }

@@ -144,12 +144,13 @@ constexpr int kMarchTY = 32 / kMarchTX;
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
-// Staged grid layout (see march.cu): 0 linear, 1 x-pairs, 2 x/y quads.
-constexpr int kLayoutLinear = 0, kLayoutXPair = 1, kLayoutQuad = 2, kLayoutOcto = 3;
+// Staged grid layout (see march.cu): 2 x/y quads (default), 3 octo cells.
+constexpr int kLayoutQuad = 2, kLayoutOcto = 3;
 #ifndef NSL_MARCH_LAYOUT
 #define NSL_MARCH_LAYOUT 2
 #endif
 constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
+static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto, "staged layout: 2 (quad) or 3 (octo)");
 // cells of the padded staged layouts: quad (nx+1)(ny+1)(nz+2) of 4 floats,
 // octo (nx+1)(ny+1)(nz+1) of 8 floats
 __host__ __device__ inline size_t staged_cells(int nx, int ny, int nz) {
@@ -162,9 +163,7 @@ inline bool grid_dims_ok(int nx, int ny, int nz) {
   return staged_cells(nx, ny, nz) < ((size_t)1 << 32);
 }
 inline size_t staged_floats(int nx, int ny, int nz) {
-  if (kMarchLayout == kLayoutQuad) return staged_cells(nx, ny, nz) * 4;
-  if (kMarchLayout == kLayoutOcto) return staged_cells(nx, ny, nz) * 8;
-  return (size_t)nx * ny * nz * (kMarchLayout == kLayoutLinear ? 1 : 2);
+  return staged_cells(nx, ny, nz) * (kMarchLayout == kLayoutOcto ? 8 : 4);
 }
 cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s);
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
