@@ -140,6 +140,24 @@ def test_batch_against_oracle(lib, orc):
     b.close()
 
 
+@pytest.mark.parametrize("opts", [dict(light_set=1), dict(light_set=2, phase_g=0.3),
+                                  dict(segment_exact=1, jitter=0)])
+def test_batch_march_options_against_oracle(lib, orc, opts):
+    """The march options reach the grouped march: light sets of the Sec. 5
+    ablation, HG phase, segment-exact A_n, no jitter."""
+    frames = _frames()[:3]
+    b = lib.Batch(I.pack_blob(I.make_params(C0, seed=0), C0), max_plumes=3)
+    items = _device_plumes(frames)
+    b.render(items, 3, opts=lib.march_opts(**opts))
+    guides = _host(items, "guide")
+    for k, pf in enumerate(frames):
+        o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step, **opts)
+        errs, bad = PT.compare_guide(guides[k], o, f)
+        assert max(errs) <= PT.TOL_GUIDE, (k, errs)
+        assert bad <= max(1, PT.MAX_EXCUSED_FRAC * o[0].size)
+    b.close()
+
+
 def test_batch_graph_replay_and_update(lib):
     import torch
     frames = _frames()
