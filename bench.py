@@ -627,9 +627,10 @@ def launches_per_step(precision):
     """Kernels of one single-plume step: staging 1, guide march 3 (view pass,
     segment pass, finish pass), network, shading 1.  Tensor-core network: SIMT
     first convolution 1 + 13 tensor-core convolutions + 3 transposed
-    convolutions + adapters 3 = 20; FP32 network: 14 convolutions + 3
-    transposed convolutions + adapters 3 = 20."""
-    return 1 + 3 + 20 + 1
+    convolutions + adapters 4 (pass 1, the two-launch channel-attention
+    reduction, pass 2) = 21; FP32 network: 14 convolutions + 3 transposed
+    convolutions + adapters 3 = 20."""
+    return 1 + 3 + (20 if precision == "f32" else 21) + 1
 
 
 def bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
@@ -684,7 +685,7 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
         out[name] = {"value": pixels / (ms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
                      "tuning": {"seg_len": tuning[0], "march_blocks_per_sm": tuning[1],
                                 "conv_ctas_per_sm": tuning[2], "autotune_ms": tune_ms},
-                     "launches_per_step": 1 + 3 + 20 + 1}
+                     "launches_per_step": 1 + 3 + 21 + 1}
     b.close()
 
     # the plain single-plume path with the FP32 network on the same plumes
