@@ -198,28 +198,8 @@ template <typename TA>
 struct AdapterGroupArgs {
   AdapterImg<TA> img[kMaxGroup];
   int tile_start[kMaxGroup + 1];
-  int px_start[kMaxGroup + 1];
   int nimg;
 };
-
-__device__ __forceinline__ int group_of(const int* start, int n, int t) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (start[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename TA>
-__global__ void __launch_bounds__(128) adapters_pass1_group(const __grid_constant__ AdapterGroupArgs<TA> G,
-                                                            const __grid_constant__ AdapterP1 P) {
-  const int k = group_of(G.tile_start, G.nimg, blockIdx.x);
-  const AdapterImg<TA>& im = G.img[k];
-  const int t = blockIdx.x - G.tile_start[k];
-  const int tx = (im.W + kTW - 1) / kTW;
-  adapters_pass1_tile<TA>(im.F, P, im.x1, im.partial, im.H, im.W, t % tx, t / tx, t);
-}
 
 // Deterministic reduction of the tile sums (fixed order: strided lane sums,
 // then a fixed binary tree); att = W_sca mean + b_sca.
@@ -232,16 +212,6 @@ __global__ void __launch_bounds__(1024) adapters_reduce(const float* __restrict_
                                                         const __grid_constant__ AdapterSCA S,
                                                         float* __restrict__ att) {
   adapters_reduce_body(partial, ntiles, inv_count, S, att);
-}
-
-template <typename TA>
-__global__ void __launch_bounds__(1024) adapters_reduce_group(const __grid_constant__ AdapterGroupArgs<TA> G,
-                                                              const __grid_constant__ AdapterSCA S) {
-  pdl_wait();      // the partial sums come from pass 1
-  pdl_trigger();
-  const AdapterImg<TA>& im = G.img[blockIdx.x];
-  adapters_reduce_body(im.partial, G.tile_start[blockIdx.x + 1] - G.tile_start[blockIdx.x],
-                       1.f / ((float)im.H * (float)im.W), S, im.att);
 }
 
 // Sum of the pass-1 tile sums of tiles [t0, t1) in a fixed order: 1024 threads
@@ -382,21 +352,6 @@ __global__ void __launch_bounds__(128) adapters_pass2(const TA* __restrict__ F,
   adapters_pass2_pixel<TA>(F, x1, at, P, out, npix, p);
 }
 
-// grouped: each image's pixels start a fresh 128-pixel block (px_start counts blocks)
-template <typename TA>
-__global__ void __launch_bounds__(128) adapters_pass2_group(const __grid_constant__ AdapterGroupArgs<TA> G,
-                                                            const __grid_constant__ AdapterP2 P) {
-  __shared__ float at[4 * C];
-  const int k = group_of(G.px_start, G.nimg, blockIdx.x);
-  const AdapterImg<TA>& im = G.img[k];
-  if (threadIdx.x < 4 * C) at[threadIdx.x] = im.att[threadIdx.x];
-  __syncthreads();
-  const int npix = im.H * im.W;
-  const int p = (blockIdx.x - G.px_start[k]) * 128 + threadIdx.x;
-  if (p >= npix) return;
-  adapters_pass2_pixel<TA>(im.F, im.x1, at, P, im.out, npix, p);
-}
-
 template <typename TA>
 __device__ __forceinline__ void adapters_pass2_pixel(const TA* __restrict__ F,
                                                      const TA* __restrict__ x1, const float* at,
@@ -508,30 +463,6 @@ cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float*
 }
 
 template <typename TA>
-cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
-                               cudaStream_t s) {
-  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
-  AdapterGroupArgs<TA> G{};
-  G.nimg = n;
-  int tiles = 0, blocks = 0;
-  for (int k = 0; k < n; ++k) {
-    G.img[k] = imgs[k];
-    G.tile_start[k] = tiles;
-    G.px_start[k] = blocks;
-    tiles += ((imgs[k].W + kTW - 1) / kTW) * ((imgs[k].H + kTH - 1) / kTH);
-    blocks += (imgs[k].W * imgs[k].H + 127) / 128;
-  }
-  G.tile_start[n] = tiles;
-  G.px_start[n] = blocks;
-  adapters_pass1_group<TA><<<tiles, 128, 0, s>>>(G, prm.p1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  adapters_reduce_group<TA><<<n, 1024, 0, s>>>(G, prm.sca);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  adapters_pass2_group<TA><<<blocks, 128, 0, s>>>(G, prm.p2);
-  return cudaGetLastError();
-}
-template <typename TA>
 cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
                                        cudaStream_t s) {
   if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
@@ -554,18 +485,8 @@ template cudaError_t adapters_reduce_only_group<__nv_bfloat16>(const AdapterPara
                                                                const AdapterImg<__nv_bfloat16>*, int,
                                                                cudaStream_t);
 
-template cudaError_t adapters_run_group<__nv_bfloat16>(const AdapterParamSet&,
-                                                       const AdapterImg<__nv_bfloat16>*, int,
-                                                       cudaStream_t);
-template cudaError_t adapters_run_group<__half>(const AdapterParamSet&, const AdapterImg<__half>*,
-                                                int, cudaStream_t);
 
 template cudaError_t adapters_run<float>(const AdapterParamSet&, const float*, float*, float*,
                                          float*, float*, int, int, cudaStream_t);
-template cudaError_t adapters_run<__nv_bfloat16>(const AdapterParamSet&, const __nv_bfloat16*,
-                                                 __nv_bfloat16*, float*, float*, float*, int, int,
-                                                 cudaStream_t);
-template cudaError_t adapters_run<__half>(const AdapterParamSet&, const __half*, __half*, float*,
-                                          float*, float*, int, int, cudaStream_t);
 
 }  // namespace nsl

@@ -837,11 +837,7 @@ __device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const 
     reinterpret_cast<float4*>(out)[2 * c + 1] =
         make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1));
   } else {
-#if NSL_STAGE_CS
-    __stcs(reinterpret_cast<float4*>(out) + c, lo);
-#else
     reinterpret_cast<float4*>(out)[c] = lo;
-#endif
   }
 }
 

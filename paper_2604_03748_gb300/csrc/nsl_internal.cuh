@@ -126,9 +126,6 @@ struct MarchPlume {
   float* seg_L;       // [segment][pixel] partial guide radiance
 };
 
-#ifndef NSL_STAGE_CS
-#define NSL_STAGE_CS 0   // staging stores marked evict-first
-#endif
 #ifndef NSL_MARCH_MIN_BLOCKS
 #define NSL_MARCH_MIN_BLOCKS 7
 #endif
@@ -295,7 +292,7 @@ size_t adapter_partial_floats(int max_w, int max_h);
 template <typename TA>
 cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float* partial,
                          float* att, float* out, int H, int W, cudaStream_t s);
-// the same for a group of images (one launch per pass)
+// one image of a grouped adapter launch (tensor-core passes and the reduction)
 template <typename TA>
 struct AdapterImg {
   const TA* F;
@@ -305,10 +302,7 @@ struct AdapterImg {
   float* out;       // [8][H][W]
   int H, W;
 };
-template <typename TA>
-cudaError_t adapters_run_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
-                               cudaStream_t s);
-// the SCA reduction alone (per image: partial tile sums -> att), one launch
+// the SCA reduction alone (per image: partial tile sums -> att), two launches
 template <typename TA>
 cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
                                        cudaStream_t s);
