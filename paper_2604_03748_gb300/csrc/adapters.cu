@@ -305,20 +305,25 @@ __global__ void __launch_bounds__(1024) adapters_reduce_chunks(const __grid_cons
 }
 
 template <typename TA>
-__global__ void __launch_bounds__(64) adapters_reduce_finish(const __grid_constant__ AdapterGroupArgs<TA> G,
-                                                             const __grid_constant__ AdapterSCA S) {
+__global__ void __launch_bounds__(16 * kReduceSplit) adapters_reduce_finish(
+    const __grid_constant__ AdapterGroupArgs<TA> G, const __grid_constant__ AdapterSCA S) {
   pdl_wait();      // the chunk sums
   pdl_trigger();
   const int img = blockIdx.x;
   const AdapterImg<TA>& im = G.img[img];
   const int ntiles = G.tile_start[img + 1] - G.tile_start[img];
   const int chunk = reduce_chunk(ntiles), nslots = (ntiles + chunk - 1) / chunk;
+  __shared__ float4 slot[kReduceSplit][16];
   __shared__ float mean[4 * C];
+  // every chunk sum loaded at once (thread = slot x quad), then added in slot order
+  const float4* P = reinterpret_cast<const float4*>(im.partial);
+  const int q = threadIdx.x & 15, k = threadIdx.x >> 4;
+  if (k < nslots) slot[k][q] = P[(size_t)k * chunk * 16 + q];
+  __syncthreads();
   if (threadIdx.x < 16) {
-    const float4* P = reinterpret_cast<const float4*>(im.partial);
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 0; k < nslots; ++k) {
-      const float4 v = P[(size_t)k * chunk * 16 + threadIdx.x];
+    for (int k2 = 0; k2 < nslots; ++k2) {
+      const float4 v = slot[k2][threadIdx.x];
       s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
     }
     const float inv_count = 1.f / ((float)im.H * (float)im.W);
@@ -477,7 +482,7 @@ cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const Adapter
   G.tile_start[n] = tiles;
   cudaError_t e = launch_pdl(adapters_reduce_chunks<TA>, dim3(kReduceSplit, n), dim3(1024), 0, s, G);
   if (e != cudaSuccess) return e;
-  return launch_pdl(adapters_reduce_finish<TA>, dim3(n), dim3(64), 0, s, G, prm.sca);
+  return launch_pdl(adapters_reduce_finish<TA>, dim3(n), dim3(16 * kReduceSplit), 0, s, G, prm.sca);
 }
 template cudaError_t adapters_reduce_only_group<__half>(const AdapterParamSet&, const AdapterImg<__half>*,
                                                         int, cudaStream_t);
