@@ -195,6 +195,16 @@ NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, f
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
                                  int precision, float* lightmaps_dev, void* stream);
 
+/* Diagnostic of the failure detection (no paper counterpart).  Every wait of
+ * the tensor-core kernels on an mbarrier is bounded (about 2 s); when one runs
+ * out, the kernel records a code in the context's error word, releases its
+ * tensor memory and returns, and the next nsl_predict_lightmaps returns
+ * NSL_ERR_TIMEOUT.  This call launches, on the stream, one warp whose bounded
+ * wait can never complete (nothing arrives at its mbarrier): after about 2 s
+ * it records code 0x8000 and returns, so the caller can check that the timeout
+ * is reported and that the context keeps working.  No GPU fault is involved. */
+NSL_API nsl_status nsl_selftest_wait_timeout(nsl_ctx* ctx, void* stream);
+
 /* Obstacle shadowing, Sec. 4.5 (a depth-based screen-space approximation).
  * Shadow map of the obstacle for one directional light: the obstacle mask is
  * rendered from the light as the depth of the first occupied voxel along each

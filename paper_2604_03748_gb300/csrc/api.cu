@@ -528,6 +528,14 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
   return NSL_OK;
 }
 
+nsl_status nsl_selftest_wait_timeout(nsl_ctx* c, void* stream) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_selftest_wait_timeout: ctx is NULL");
+  if (!c->err_dev) return fail(NSL_ERR_UNSUPPORTED, "nsl_selftest_wait_timeout: no error word");
+  cudaError_t e = launch_wait_timeout_probe(c->err_dev, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "nsl_selftest_wait_timeout");
+  return NSL_OK;
+}
+
 nsl_status nsl_obstacle_shadow_map(const uint8_t* mask_dev, int nx, int ny, int nz, const float light_dir[3],
                                    int resolution, float* shadow_map_dev, void* stream) {
   const char* fn = "nsl_obstacle_shadow_map";

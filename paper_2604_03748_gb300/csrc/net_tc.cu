@@ -713,11 +713,30 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
+// Failure-detection probe: one warp waits, with the same bounded wait as every
+// tensor-core kernel, on an mbarrier that nothing arrives at; the wait gives up
+// after its limit (about 2 s), records code 0x8000 in the error word and the
+// kernel returns normally.
+__global__ void __launch_bounds__(32) wait_timeout_probe(unsigned int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (!mbar_wait(&bar, 0) && threadIdx.x == 0) record_error(err, 0x8000u);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
 }  // namespace
+
+cudaError_t launch_wait_timeout_probe(unsigned int* err, cudaStream_t s) {
+  wait_timeout_probe<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
+}
 
 // CTAs of a kernel that fit on one SM at once, from its shared memory,
 // registers, threads and TMEM columns.  (The runtime's occupancy query reports

@@ -343,6 +343,7 @@ cudaError_t net_tc_forward_group(const NetTcWeights* wt, const NetF32Weights* wf
 void net_tc_set_ctas_per_sm(int v);
 
 // CTAs of a tensor-memory kernel that fit on one SM (net_tc.cu)
+cudaError_t launch_wait_timeout_probe(unsigned int* err, cudaStream_t s);
 int tc_ctas_per_sm(const void* kernel, int threads, int dyn_smem, int tmem_cols);
 
 // ---- batched frames (batch.cu), used by the server ----

@@ -31,7 +31,7 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_server_add_plume", "nsl_server_remove_plume", "nsl_server_submit", "nsl_server_wait",
            "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
            "nsl_server_reset_stats", "nsl_pack_lightmaps", "nsl_obstacle_shadow_map",
-           "nsl_shade_shadowed"]
+           "nsl_shade_shadowed", "nsl_selftest_wait_timeout"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
     lib.nsl_pack_lightmaps.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.nsl_pack_lightmaps.restype = C.c_int
+    lib.nsl_selftest_wait_timeout.argtypes = [vp, vp]
+    lib.nsl_selftest_wait_timeout.restype = C.c_int
     lib.nsl_obstacle_shadow_map.argtypes = [vp, i, i, i, C.POINTER(C.c_float * 3), i, vp, vp]
     lib.nsl_obstacle_shadow_map.restype = C.c_int
     lib.nsl_shade_shadowed.argtypes = [vp, vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i,
