@@ -283,9 +283,14 @@ nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, 
   if (!density) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: density is NULL");
   if (!aligned16(density) || (mask && !aligned16(mask)))
     return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: buffers must be 16-byte aligned");
-  cudaError_t e = launch_stage_volume(density, c->grid.dtype, mask, c->grid.nx, c->grid.ny,
-                                      c->grid.nz, c->grid.sigma_scale, c->staged,
-                                      static_cast<cudaStream_t>(stream));
+  // an FP16 grid stays FP16 (half the march's gather bytes); sigma_scale is
+  // applied after the trilinear blend
+  cudaError_t e = c->grid.dtype == NSL_F16
+                      ? launch_stage_volume_half(static_cast<const __half*>(density), mask, c->grid.nx, c->grid.ny,
+                                                 c->grid.nz, reinterpret_cast<__half*>(c->staged),
+                                                 static_cast<cudaStream_t>(stream))
+                      : launch_stage_volume(density, c->grid.dtype, mask, c->grid.nx, c->grid.ny, c->grid.nz,
+                                            c->grid.sigma_scale, c->staged, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_stage_grid");
   c->staged_valid = true;
   return NSL_OK;
@@ -391,6 +396,8 @@ static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
   st = fill_march_plume(c->grid, *cam, step, opts, fn, p);
   if (st != NSL_OK) return st;
   p->vol = c->staged;
+  p->staged_half = c->grid.dtype == NSL_F16;
+  p->scl = c->grid.sigma_scale;
   return NSL_OK;
 }
 

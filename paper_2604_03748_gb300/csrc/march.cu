@@ -37,6 +37,16 @@ struct Grid {
   int nx, ny, nz;
   float fx, fy, fz;  // box extents
 };
+// FP16 quads of the masked density rho (single-plume contexts with an FP16
+// grid): values exact, sigma = scl * (trilinear value); half the bytes
+struct GridH {
+  const __half* __restrict__ v;
+  int nx, ny, nz;
+  float fx, fy, fz;
+  float scl;          // sigma_scale
+};
+__device__ __forceinline__ float scaled(const Grid&, float v) { return v; }
+__device__ __forceinline__ float scaled(const GridH& g, float v) { return __fmul_rn(g.scl, v); }
 
 // 32-byte load of an octo cell: the 2x2 x/y neighbourhood of slice z (a) and
 // of slice z+1 (b), in one 256-bit vector access
@@ -46,41 +56,49 @@ __device__ __forceinline__ void ldg_octo(const float* p, float4& a, float4& b) {
       : "l"(p));
 }
 
+// The two x/y quads of padded cell `cell` (slice z in a, z+1 in b).
+__device__ __forceinline__ void load_cell(const Grid& g, unsigned cell, unsigned pl, float4& a, float4& b) {
+  if constexpr (kMarchLayout == kLayoutOcto) {
+    ldg_octo(g.v + 8 * (size_t)cell, a, b);
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
+    a = __ldg(q);
+    b = __ldg(q + pl);
+  }
+}
+__device__ __forceinline__ float4 half4_to_float4(uint2 u) {
+  const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ void load_cell(const GridH& g, unsigned cell, unsigned pl, float4& a, float4& b) {
+  static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
+  const uint2* q = reinterpret_cast<const uint2*>(g.v) + cell;
+  a = half4_to_float4(__ldg(q));
+  b = half4_to_float4(__ldg(q + pl));
+}
+
 // Extinction at p: 0 outside the closed box [0,n]; trilinear interpolation of
 // the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.
-__device__ __forceinline__ float sigma_at(const Grid& g, float px, float py, float pz) {
+template <class G>
+__device__ __forceinline__ float sigma_at(const G& g, float px, float py, float pz) {
   if (!(px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz)) return 0.f;
   float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
   float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
   float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  float c00, c10, c01, c11;
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    // padded octo cells: cell (ix+1, iy+1, iz+1) of an (nx+1) x (ny+1) x (nz+1)
-    // array holds the 8 corners, every index of a point inside the box in range
-    const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-    float4 a, b;
-    ldg_octo(g.v + 8 * (size_t)((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1)), a, b);
-    c00 = fmaf(tx, a.y - a.x, a.x);
-    c10 = fmaf(tx, a.w - a.z, a.z);
-    c01 = fmaf(tx, b.y - b.x, b.x);
-    c11 = fmaf(tx, b.w - b.z, b.z);
-  } else {
-    // padded quads: cell (ix+1, iy+1, iz+1) of a (nx+1) x (ny+1) x (nz+2) array,
-    // every index of a point inside the box is in range
-    const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-    const float4* q = reinterpret_cast<const float4*>(g.v) +
-                      ((unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1));
-    const float4 a = __ldg(q);
-    const float4 b = __ldg(q + pl);
-    c00 = fmaf(tx, a.y - a.x, a.x);
-    c10 = fmaf(tx, a.w - a.z, a.z);
-    c01 = fmaf(tx, b.y - b.x, b.x);
-    c11 = fmaf(tx, b.w - b.z, b.z);
-  }
+  // padded cells: cell (ix+1, iy+1, iz+1) holds the corners, every index of a
+  // point inside the box is in range
+  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+  float4 a, b;
+  load_cell(g, (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1), pl, a, b);
+  const float c00 = fmaf(tx, a.y - a.x, a.x);
+  const float c10 = fmaf(tx, a.w - a.z, a.z);
+  const float c01 = fmaf(tx, b.y - b.x, b.x);
+  const float c11 = fmaf(tx, b.w - b.z, b.z);
   const float c0 = fmaf(ty, c10 - c00, c00);
   const float c1 = fmaf(ty, c11 - c01, c01);
-  return fmaf(tz, c1 - c0, c0);
+  return scaled(g, fmaf(tz, c1 - c0, c0));
 }
 
 // Two-stage form of sigma_at for software pipelining (quad layout): fetch()
@@ -93,7 +111,8 @@ struct Fetch {
   bool in;
 };
 
-__device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float pz) {
+template <class G>
+__device__ __forceinline__ Fetch fetch(const G& g, float px, float py, float pz) {
   Fetch f;
   f.in = px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz;
   float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
@@ -105,21 +124,15 @@ __device__ __forceinline__ Fetch fetch(const Grid& g, float px, float py, float 
   const int ix = min(max((int)flx, -1), g.nx - 1), iy = min(max((int)fly, -1), g.ny - 1);
   const int iz = min(max((int)flz, -1), g.nz - 1);
   const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  const unsigned cell = (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1);
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
-    f.a = __ldg(q);
-    f.b = __ldg(q + pl);
-  }
+  load_cell(g, (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1), pl, f.a, f.b);
   return f;
 }
 
 // fetch() without the index clamps, for points within rounding of the closed
 // box (every shadow sample k <= K is): floor(p - 0.5) then lies in [-1, n-1]
 // on every axis, inside the padded array.
-__device__ __forceinline__ Fetch fetch_in(const Grid& g, float px, float py, float pz) {
+template <class G>
+__device__ __forceinline__ Fetch fetch_in(const G& g, float px, float py, float pz) {
   Fetch f;
   f.in = px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz;
   float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
@@ -128,20 +141,15 @@ __device__ __forceinline__ Fetch fetch_in(const Grid& g, float px, float py, flo
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
   const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  const unsigned cell = (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1);
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
-    f.a = __ldg(q);
-    f.b = __ldg(q + pl);
-  }
+  load_cell(g, (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1), pl,
+            f.a, f.b);
   return f;
 }
 
 // Cell fetch at q = p - 0.5 of a point strictly inside the closed box (no box
 // test, no clamps): floor(q) lies in [-1, n-1] on every axis.
-__device__ __forceinline__ Fetch fetch_q(const Grid& g, float qx, float qy, float qz) {
+template <class G>
+__device__ __forceinline__ Fetch fetch_q(const G& g, float qx, float qy, float qz) {
   Fetch f;
   f.in = true;
   const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
@@ -149,14 +157,8 @@ __device__ __forceinline__ Fetch fetch_q(const Grid& g, float qx, float qy, floa
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
   const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  const unsigned cell = (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1);
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    ldg_octo(g.v + 8 * (size_t)cell, f.a, f.b);
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
-    f.a = __ldg(q);
-    f.b = __ldg(q + pl);
-  }
+  load_cell(g, (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1), pl,
+            f.a, f.b);
   return f;
 }
 
@@ -178,7 +180,8 @@ __device__ __forceinline__ float hg_phase(float g, float c) {
 
 // Number of shadow steps K = floor(t_exit / h) from p along the unit direction
 // s to the exit of the closed box.
-__device__ __forceinline__ int shadow_steps(const Grid& g, float px, float py, float pz, float sx,
+template <class G>
+__device__ __forceinline__ int shadow_steps(const G& g, float px, float py, float pz, float sx,
                                             float sy, float sz, float h) {
   float te = INFINITY;
   if (sx > 0.f) te = fminf(te, __fdiv_rn(__fsub_rn(g.fx, px), sx));
@@ -209,8 +212,8 @@ __device__ __forceinline__ int shadow_steps(const Grid& g, float px, float py, f
 // the box test, the rays' last samples inside the two-per-step sequence; in the
 // grouped march the separate last-sample step cost more latency than the box
 // tests it saved (measured: 16.4 against 17.5 ms per 64-plume batch).
-template <bool kCount, bool kExactLast>
-__device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, float pz,
+template <bool kCount, bool kExactLast, class G>
+__device__ __forceinline__ void shadow_pair(const G& g, float px, float py, float pz,
                                             const float u_in[3], float h, float tau_lim, float& Tt,
                                             float& Tb, unsigned long long& nsamp) {
   // the direction in registers: u_in may point into a plume table in global memory
@@ -233,7 +236,7 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
       const float khB = __fmul_rn((float)(tB ? j2 : Mt - j2), h);
       const Fetch fA = fetch_q(g, fmaf(khA, u[0], qx0), fmaf(khA, u[1], qy0), fmaf(khA, u[2], qz0));
       const Fetch fB = fetch_q(g, fmaf(khB, u[0], qx0), fmaf(khB, u[1], qy0), fmaf(khB, u[2], qz0));
-      const float vA = interp(fA), vB = interp(fB);
+      const float vA = scaled(g, interp(fA)), vB = scaled(g, interp(fB));
       int jn = j + 2;
       if (tA) {
         taut = fmaf(vA, h, taut);
@@ -271,11 +274,11 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
       const Fetch fb = fetch(g, __fsub_rn(px, __fmul_rn(kb, u[0])), __fsub_rn(py, __fmul_rn(kb, u[1])),
                              __fsub_rn(pz, __fmul_rn(kb, u[2])));
       if (at) {
-        taut = fmaf(interp(ft), h, taut);
+        taut = fmaf(scaled(g, interp(ft)), h, taut);
         if (kCount) ++nsamp;
       }
       if (ab) {
-        taub = fmaf(interp(fb), h, taub);
+        taub = fmaf(scaled(g, interp(fb)), h, taub);
         if (kCount) ++nsamp;
       }
     }
@@ -298,7 +301,7 @@ __device__ __forceinline__ void shadow_pair(const Grid& g, float px, float py, f
       const Fetch fB = fetch_in(g, tB ? __fadd_rn(px, dBx) : __fsub_rn(px, dBx),
                                 tB ? __fadd_rn(py, dBy) : __fsub_rn(py, dBy),
                                 tB ? __fadd_rn(pz, dBz) : __fsub_rn(pz, dBz));
-      const float vA = interp(fA), vB = interp(fB);
+      const float vA = scaled(g, interp(fA)), vB = scaled(g, interp(fB));
       int jn = j + 2;
       if (tA) {
         taut = fmaf(vA, h, taut);
@@ -343,7 +346,8 @@ struct Ray {
   float wf, wt, wb;
 };
 
-__device__ __forceinline__ Ray ray_setup(const MarchPlume& P, const Grid& g, int i, int j) {
+template <class G>
+__device__ __forceinline__ Ray ray_setup(const MarchPlume& P, const G& g, int i, int j) {
   const CamFrame& c = P.cam;
   Ray r;
   // ray through the pixel centre
@@ -431,8 +435,8 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
 
 // One view step n with sigma = s > 0: A_n, the three surrogate lights, L_n;
 // accumulates A_n L_n into (L, Lc) and the optical depth into (tau, tc).
-template <bool kCount, bool kExactLast, bool kVolume = false>
-__device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, const Ray& r,
+template <bool kCount, bool kExactLast, bool kVolume = false, class G = Grid>
+__device__ __forceinline__ void view_step(const MarchPlume& P, const G& g, const Ray& r,
                                           float px, float py, float pz, float s, float& T,
                                           float& tau, float& tc, float& L, float& Lc,
                                           unsigned long long& nsamp) {
@@ -460,13 +464,26 @@ __device__ __forceinline__ void view_step(const MarchPlume& P, const Grid& g, co
   T = expf(-tau);
 }
 
+// The staged density of a plume as the sampling functions see it.
+template <class G>
+__device__ __forceinline__ G plume_grid(const MarchPlume& P);
+template <>
+__device__ __forceinline__ Grid plume_grid<Grid>(const MarchPlume& P) {
+  return Grid{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+}
+template <>
+__device__ __forceinline__ GridH plume_grid<GridH>(const MarchPlume& P) {
+  return GridH{reinterpret_cast<const __half*>(P.vol), P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz,
+               P.scl};
+}
+
 // Single-pass march of one pixel (Alg. 1): used by the sample-count variant and
 // the allocation-free entry point.
-template <bool kCount, bool kExactLast>
+template <bool kCount, bool kExactLast, class G = Grid>
 __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
   unsigned long long nsamp = 0;
   const CamFrame& c = P.cam;
-  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const G g = plume_grid<G>(P);
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
   const Ray r = ray_setup(P, g, i, j);
@@ -480,7 +497,7 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
     if (kCount) ++nsamp;
     if (D == 0.f && s > P.tau_depth) D = __fmul_rn((float)n, P.h);
     if (s > 0.f) {
-      view_step<kCount, kExactLast>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+      view_step<kCount, kExactLast, false, G>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
       if (T < P.t_min) break;
     }
   }
@@ -502,9 +519,10 @@ __device__ __forceinline__ void march_pixel(const MarchPlume& P, int i, int j) {
 // from the recorded state, which reproduces the single-pass T_{n-1} bit for
 // bit; pass 3 adds the segment partials of each pixel in order.
 // ---------------------------------------------------------------------------
+template <class G = Grid>
 __device__ __forceinline__ void march_view_pixel(const MarchPlume& P, int i, int j) {
   const CamFrame& c = P.cam;
-  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const G g = plume_grid<G>(P);
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
   const Ray r = ray_setup(P, g, i, j);
@@ -533,7 +551,7 @@ __device__ __forceinline__ void march_view_pixel(const MarchPlume& P, int i, int
   P.seg_nef[pix] = nef;
 }
 
-template <bool kExactLast, bool kVolume = false>
+template <bool kExactLast, bool kVolume = false, class G = Grid>
 __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j, int seg) {
   const CamFrame& c = P.cam;
   const size_t plane = (size_t)c.W * c.H;
@@ -543,7 +561,7 @@ __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j,
   const int first = seg * S + 1;
   if (first > nef) return;
   const int last = min(first + S - 1, nef);
-  Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const G g = plume_grid<G>(P);
   const Ray r = ray_setup(P, g, i, j);
   const size_t k = (size_t)seg * plane + pix;
   float tau = P.seg_tau[k], tc = P.seg_comp[k];
@@ -554,7 +572,7 @@ __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j,
     float px, py, pz;
     view_point(r, n, P.h, px, py, pz);
     const float s = sigma_at(g, px, py, pz);
-    if (s > 0.f) view_step<false, kExactLast, kVolume>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
+    if (s > 0.f) view_step<false, kExactLast, kVolume, G>(P, g, r, px, py, pz, s, T, tau, tc, L, Lc, nsamp);
   }
   P.seg_L[k] = L;
 }
@@ -581,7 +599,7 @@ __device__ __forceinline__ int find_plume(const MarchPlume* __restrict__ t, int 
 // Persistent march: every warp repeatedly takes the next 8x4-pixel tile from a
 // global counter (dynamic balancing of very uneven per-pixel costs).  The
 // counter lives in library scratch and is zeroed before each launch.
-template <bool kBatch, bool kCount>
+template <bool kBatch, bool kCount, class G = Grid>
 __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
 march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplumes, int total_tiles,
              int* __restrict__ tile_counter) {
@@ -599,7 +617,7 @@ march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplume
     const int tx = tile % P->tiles_x, ty = tile / P->tiles_x;
     const int i = tx * kMarchTX + (lane % kMarchTX);
     const int j = ty * kMarchTY + (lane / kMarchTX);
-    if (i < P->cam.W && j < P->cam.H) march_pixel<kCount, !kBatch>(*P, i, j);
+    if (i < P->cam.W && j < P->cam.H) march_pixel<kCount, !kBatch, G>(*P, i, j);
   }
 }
 
@@ -627,10 +645,16 @@ cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
   if (e != cudaSuccess) return e;
   if (count) {
     int grid = march_grid<false, true>();
-    march_kernel<false, true><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+    if (p.staged_half)
+      march_kernel<false, true, GridH><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+    else
+      march_kernel<false, true><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
   } else {
     int grid = march_grid<false, false>();
-    march_kernel<false, false><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+    if (p.staged_half)
+      march_kernel<false, false, GridH><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+    else
+      march_kernel<false, false><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
   }
   return cudaGetLastError();
 }
@@ -647,7 +671,7 @@ cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int tot
 }
 
 // pass 1 and pass 3: one thread per pixel, warps over 8x4 tiles
-template <int kPass>
+template <int kPass, class G = Grid>
 __global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPlume P, int ntiles,
                                                                         int* __restrict__ counter) {
   pdl_wait();      // the staged grid (pass 1) or the segment partials (pass 3)
@@ -660,13 +684,13 @@ __global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPl
   const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
   const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
   if (i >= P.cam.W || j >= P.cam.H) return;
-  if (kPass == 1) march_view_pixel(P, i, j);
+  if (kPass == 1) march_view_pixel<G>(P, i, j);
   else march_finish_pixel(P, i, j);
 }
 
 // pass 2: warps take (tile, segment) items from a queue, segment-major
 // (kVolume: the side lights' transmittances from the shadow_volume volumes)
-template <bool kVolume>
+template <bool kVolume, class G = Grid>
 __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks)
 march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ counter) {
   pdl_wait();      // the view pass's segment starts and the cleared queue
@@ -680,7 +704,7 @@ march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ cou
     const int seg = item / ntiles, tile = item % ntiles;
     const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
     const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
-    if (i < P.cam.W && j < P.cam.H) march_segment<true, kVolume>(P, i, j, seg);
+    if (i < P.cam.W && j < P.cam.H) march_segment<true, kVolume, G>(P, i, j, seg);
   }
 }
 
@@ -696,8 +720,10 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
   if (ntiles == 0) return cudaSuccess;
   const int warps_per_block = kMarchThreads / 32;
   const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
-  cudaError_t e = launch_pdl(march_pixel_pass_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles,
-                             tile_counter);
+  cudaError_t e = p.staged_half ? launch_pdl(march_pixel_pass_kernel<1, GridH>, dim3(blocks),
+                                              dim3(kMarchThreads), 0, s, p, ntiles, tile_counter)
+                                 : launch_pdl(march_pixel_pass_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0,
+                                              s, p, ntiles, tile_counter);
   if (e != cudaSuccess) return e;
   static int grid = 0;
   if (!grid) {
@@ -707,10 +733,17 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
       occ = 1;
     grid = occ * kNumSMs;
   }
-  e = p.shadow_volume ? launch_pdl(march_segment_kernel<true>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
-                                   ntiles * max_segments, tile_counter)
-                      : launch_pdl(march_segment_kernel<false>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
-                                   ntiles * max_segments, tile_counter);
+  const int nitems = ntiles * max_segments;
+  if (p.staged_half)
+    e = p.shadow_volume ? launch_pdl(march_segment_kernel<true, GridH>, dim3(grid), dim3(kMarchThreads), 0, s, p,
+                                     ntiles, nitems, tile_counter)
+                        : launch_pdl(march_segment_kernel<false, GridH>, dim3(grid), dim3(kMarchThreads), 0, s, p,
+                                     ntiles, nitems, tile_counter);
+  else
+    e = p.shadow_volume ? launch_pdl(march_segment_kernel<true>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
+                                     nitems, tile_counter)
+                        : launch_pdl(march_segment_kernel<false>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
+                                     nitems, tile_counter);
   if (e != cudaSuccess) return e;
   return launch_pdl(march_pixel_pass_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles, tile_counter);
 }
@@ -913,14 +946,64 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
                     mask, nx, ny, nz, scale, staged);
 }
 
+// FP16 staging of the quad layout (single-plume contexts with an FP16 grid):
+// the raw values rho, masked to 0, four cells per thread as in stage_unit;
+// the march multiplies by sigma_scale after the trilinear blend.
+__global__ void __launch_bounds__(256) stage_half_kernel(const __half* __restrict__ rho,
+                                                         const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                         uint2* __restrict__ out) {
+  pdl_wait();      // the previous frame's march may still read the staged grid
+  pdl_trigger();
+  const size_t n = stage_units(nx, ny, nz);
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpr = (px + 3u) / 4u;
+  const __half zero = __float2half_rn(0.f);
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
+    auto val = [&](size_t idx) { return (mask && __ldg(mask + idx)) ? zero : rho[idx]; };
+    const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
+    const unsigned r = u32 / gpr;
+    const int a0 = (int)(4u * (u32 % gpr));
+    const int b = (int)(r % py), cz = (int)(r / py);
+    const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+    const int k0 = min(max(cz - 1, 0), nz - 1);
+    const size_t b0 = ((size_t)k0 * ny + j0) * nx, b1 = ((size_t)k0 * ny + j1) * nx;
+    __half w0[5], w1[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const int x = min(max(a0 - 1 + t, 0), nx - 1);
+      w0[t] = val(b0 + x);
+      w1[t] = val(b1 + x);
+    }
+    uint2* dst = out + ((size_t)r * px + (unsigned)a0);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (a0 + t < (int)px) {
+        const __half2 lo = __halves2half2(w0[t], w0[t + 1]), hi = __halves2half2(w1[t], w1[t + 1]);
+        dst[t] = make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+      }
+    }
+  }
+}
+
+cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
+                                     __half* staged, cudaStream_t s) {
+  static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
+  const size_t n = stage_units(nx, ny, nz);
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
+  if (blocks < 1) blocks = 1;
+  return launch_pdl(stage_half_kernel, dim3(blocks), dim3(256), 0, s, density, mask, nx, ny, nz,
+                    reinterpret_cast<uint2*>(staged));
+}
+
 // Transmittance volumes of the shadow_volume option: one thread per voxel
 // centre marches the side lights' two shadow rays exactly as from a view sample
 // (consecutive threads along x, so a warp's rays run side by side).
+template <class G>
 __global__ void __launch_bounds__(256) transmittance_volume_kernel(MarchPlume P, float* __restrict__ outT,
                                                                    float* __restrict__ outB) {
   pdl_wait();      // the staged grid
   pdl_trigger();
-  const Grid g{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+  const G g = plume_grid<G>(P);
   const float* sd = P.light_set == NSL_LIGHTS_FLR ? P.cam.r : P.cam.u;
   const size_t n = (size_t)P.nx * P.ny * P.nz;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
@@ -937,7 +1020,9 @@ cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float*
   const size_t n = (size_t)p.nx * p.ny * p.nz;
   int blocks = (int)((n + 255) / 256);
   if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
-  return launch_pdl(transmittance_volume_kernel, dim3(blocks), dim3(256), 0, s, p, outT, outB);
+  if (p.staged_half)
+    return launch_pdl(transmittance_volume_kernel<GridH>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
+  return launch_pdl(transmittance_volume_kernel<Grid>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
 }
 
 // ---------------------------------------------------------------------------

@@ -98,7 +98,10 @@ cudaError_t launch_shade_shadowed(const ShadowShadeArgs& a, cudaStream_t s);
 // guide march
 // ---------------------------------------------------------------------------
 struct MarchPlume {
-  const float* vol;   // staged extinction sigma' = scale*rho*[mask==0], [nz][ny][nx] fp32
+  const float* vol;   // staged extinction sigma' = scale*rho*[mask==0], padded quad layout, fp32
+                      // (staged_half: FP16 quads of rho*[mask==0], sigma = scl * value)
+  int staged_half;
+  float scl;
   int nx, ny, nz;
   CamFrame cam;
   float h;            // step in voxels
@@ -165,6 +168,8 @@ inline size_t staged_floats(int nx, int ny, int nz) {
 cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s);
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s);
+cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
+                                     __half* staged, cudaStream_t s);
 int march_tiles(int W, int H);
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
                          bool count = false);

@@ -120,6 +120,25 @@ def test_guide_fp16_density(lib, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(jitter=0, t_min=0.0), dict(segment_exact=1), dict(light_set=1),
+                                  dict(light_set=2), dict(shadow_volume=1, t_min=0.0),
+                                  dict(shadow_volume=1, light_set=2)])
+def test_guide_fp16_density_options(lib, orc, opts):
+    # an FP16 grid is staged as FP16 (sigma_scale applied after the blend):
+    # masked, a ragged 27^3 grid and 40x24 image, every light set and the
+    # shadow volumes
+    pf = I.small_case(27, 40, 24, seed=15, kind=I.PERSP, step=1.75)
+    pf.density = pf.density.astype(np.float16)
+    assert pf.mask is not None and pf.mask.any()
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf, **opts)
+    o, _, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step, **opts)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= max(1, PT.MAX_EXCUSED_FRAC * g[0].size)
+    ctx.close()
+
+
 def test_guide_deterministic(lib):
     pf = I.config_plain_64()
     ctx = PT.make_ctx(pf)
