@@ -127,8 +127,11 @@ NSL_API nsl_status nsl_create(const nsl_grid_desc* grid, const void* weights_blo
 NSL_API void nsl_destroy(nsl_ctx* ctx);
 
 /* Stage a density grid into the context (Sec. 4.2: sigma_s in a 3D texture):
- * sigma' = sigma_scale * density * [mask == 0], widened to float32, kept in a
- * context-owned device buffer until the next staging.  A later
+ * sigma' = sigma_scale * density * [mask == 0], kept in a context-owned device
+ * buffer until the next staging.  A float32 grid is staged as float32 sigma';
+ * a float16 grid is staged as float16 density * [mask == 0] (its values
+ * exactly) and the march applies sigma_scale after the trilinear blend, which
+ * differs from blending sigma' by rounding only.  A later
  * nsl_guiding_map with density_dev == NULL marches this resident grid.
  *   density_dev   [nz][ny][nx] float32 or float16 (grid.dtype)
  *   mask_dev      [nz][ny][nx] uint8 obstacle mask (non-zero = obstacle) or NULL */
@@ -155,8 +158,9 @@ NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const 
  * cudaMalloc at all: a render thread whose frame budget cannot absorb the device
  * synchronisation an allocation may cause, an engine whose own allocator owns
  * every byte of device memory, or code that has no context to keep between
- * frames.  It computes exactly what nsl_guiding_map computes, with the same
- * kernels; the staged grid and the tile counter live in one static device
+ * frames.  It computes exactly what nsl_guiding_map computes for a float32
+ * grid, with the same kernels (a float16 grid is staged here as float32 sigma',
+ * so its guide can differ from nsl_guiding_map's by rounding); the staged grid and the tile counter live in one static device
  * array of 40 MiB + 256 bytes inside libnsl, which every GPU that loads the
  * library holds until the process exits.
  *   grid          shape, storage and sigma_scale of density_dev
