@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--forms", default="animated,batched,serving",
                     help="comma list of further workloads measured after the primary line's "
                          "('animated', 'batched', 'serving', or 'none')")
+    ap.add_argument("--anim-frames", type=int, default=300,
+                    help="frames of the animated form (300; fewer keep a profiler capture small)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of each Poisson arrival run of the serving form")
     args = ap.parse_args()
@@ -504,7 +506,7 @@ def main():
 
 
 def bench_animated(nsl, I, dev, args, with_oracle):
-    """Animated form: 300 frames of a 256^3 FP16 plume advected along a seeded
+    """Animated form: 300 frames (--anim-frames) of a 256^3 FP16 plume advected along a seeded
     curl-noise velocity (generated on the GPU before timing), camera on a
     seeded spline, light turning 1 degree per frame; 1024x1024 billboard, step
     4 voxels, FP8 network (and FP16 beside it).  Every frame stages its own
@@ -512,7 +514,9 @@ def bench_animated(nsl, I, dev, args, with_oracle):
     events per frame."""
     import torch
     t0 = time.perf_counter()
-    seq = I.animated_sequence(256, 300, seed=3, width=1024, height=1024, step=4.0, device=dev)
+    nf = max(4, args.anim_frames)
+    mid = nf // 2
+    seq = I.animated_sequence(256, nf, seed=3, width=1024, height=1024, step=4.0, device=dev)
     gen_s = time.perf_counter() - t0
     W = H = 1024
     blob = I.pack_blob(I.make_params(16, 0), 16)
@@ -522,9 +526,9 @@ def bench_animated(nsl, I, dev, args, with_oracle):
     lm = torch.empty((8, H, W), dtype=torch.float32, device=dev)
     rgba = torch.empty((4, H, W), dtype=torch.float32, device=dev)
     opts = nsl.march_opts()
-    out = {"workload": "256^3 f16 plume, 300 frames (curl-noise advection, seed 3), perspective 1024x1024 "
+    out = {"workload": f"256^3 f16 plume, {nf} frames (curl-noise advection, seed 3), perspective 1024x1024 "
                        "on a spline, light turning 1 deg/frame, step 4 voxels",
-           "generation_s": gen_s, "frames": 300}
+           "generation_s": gen_s, "frames": nf}
     for name, prec in (("fp8", nsl.NSL_PREC_FP8), ("f16", nsl.NSL_PREC_F16)):
         def frame(t, evs=None):
             if evs:
@@ -538,27 +542,27 @@ def bench_animated(nsl, I, dev, args, with_oracle):
         for t in range(3):
             frame(t)
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(300)]
-        for t in range(300):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nf)]
+        for t in range(nf):
             frame(t, evs[t])
         torch.cuda.synchronize()
         ms = np.array([a.elapsed_time(b) for a, b in evs])
-        out[name] = {"value": 300 * W * H / (ms.sum() / 1e3) / 1e6, "unit": "Mpix/s",
+        out[name] = {"value": nf * W * H / (ms.sum() / 1e3) / 1e6, "unit": "Mpix/s",
                      "ms_per_frame": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)),
                      "p99_ms": float(np.percentile(ms, 99)), "max_ms": float(ms.max())}
     if with_oracle:
-        # FP64 oracle guide on a 64-row band of frame 150 against this run's guide
+        # FP64 oracle guide on a 64-row band of the middle frame against this run's guide
         import oracle
-        frame(150)
+        frame(mid)
         torch.cuda.synchronize()
         g = guide.cpu().numpy()
-        host = seq.frames[150].cpu().numpy()
+        host = seq.frames[mid].cpu().numpy()
         t1 = time.perf_counter()
-        o, _, _ = oracle.guide(host, None, seq.cameras[150], seq.step, rows=(480, 544))
+        o, _, _ = oracle.guide(host, None, seq.cameras[mid], seq.step, rows=(480, 544))
         dt = time.perf_counter() - t1
-        out["err_vs_oracle"] = {"guide_band_frame150": range_errs(g[:, 480:544], o[:, 480:544])}
+        out["err_vs_oracle"] = {f"guide_band_frame{mid}": range_errs(g[:, 480:544], o[:, 480:544])}
         out["cpu_baseline"] = {"value": 64 * W / dt / 1e6, "unit": "Mpix/s (guide only)", "cores": os.cpu_count(),
-                               "kind": "oracle", "sample": "FP64 guide march of rows 480..543 of frame 150"}
+                               "kind": "oracle", "sample": f"FP64 guide march of rows 480..543 of frame {mid}"}
     ctx.close()
     del seq
     torch.cuda.empty_cache()
