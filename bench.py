@@ -39,6 +39,11 @@ FLOP_PER_SAMPLE = 39
 GATHER_BYTES = 32                 # 8 FP32 voxels per trilinear density sample
 L1_PEAK_GBS = 152 * 128 * 2.07    # L1 data path: 128 B per clock per SM at 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (read + write) of the three march passes of one frame of this
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum with
+# --cache-control none on the current march kernels (the staged grid is in L2
+# when the view pass starts; the writes are the segment scratch and the guide).
+MARCH_DRAM_BYTES = 2_117_888 + 17_257_472
 
 
 def peaks():
@@ -368,7 +373,7 @@ def main():
                      "net": float(np.mean(net_ms)), "shade": float(np.mean(shade_ms))},
         "roofline": {"kernel": "guide march (view pass + segment pass + finish pass)", "bound": "alu",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MARCH_DRAM_BYTES,
                      "work": {"density_samples": samples, "flop_per_sample": FLOP_PER_SAMPLE},
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      # the march's closer limit: the trilinear gathers through L1 (8 FP32
