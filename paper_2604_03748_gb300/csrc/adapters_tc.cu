@@ -590,23 +590,34 @@ cudaError_t adapters_tc_run_group(const AdapterTcWeights* w, const AdapterParamS
                                   const AdapterImg<TA>* imgs, int n, unsigned int* err,
                                   cudaStream_t s) {
   if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
-  static bool init = false;
-  static int occ1 = 0, occ2 = 0;
-  if (!init) {
+  // kernel attributes and residency, set up once per process (a function-local
+  // static is initialised thread-safely, so concurrent first calls wait for it)
+  struct Setup {
+    cudaError_t err;
+    int occ1, occ2;
+  };
+  static const Setup setup = [] {
+    Setup r{cudaSuccess, 0, 0};
     // the largest shared-memory carveout, so that several CTAs fit per SM
     cudaError_t e = cudaFuncSetAttribute(adapters_p1_tc<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP1Smem);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2Smem)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(adapters_p1_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
-      return e;
-    occ1 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p1_tc<TA>), kP1Threads, kP1Smem, 128);
-    occ2 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p2_tc<TA>), 128, kP2Smem, 128);
-    init = true;
-  }
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2Smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adapters_p1_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adapters_p2_tc<TA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) {
+      r.err = e;
+      return r;
+    }
+    r.occ1 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p1_tc<TA>), kP1Threads, kP1Smem, 128);
+    r.occ2 = tc_ctas_per_sm(reinterpret_cast<const void*>(adapters_p2_tc<TA>), 128, kP2Smem, 128);
+    return r;
+  }();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int occ1 = setup.occ1, occ2 = setup.occ2;
   AdGroup<TA> G{};
   G.nimg = n;
   int tiles = 0, blocks = 0;

@@ -621,16 +621,19 @@ march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplume
   }
 }
 
+// Resident blocks of a march kernel over the whole GPU, computed once per
+// process (function-local statics are initialised thread-safely).
+template <class K>
+static int resident_blocks(K kernel) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kMarchThreads, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  return occ * kNumSMs;
+}
+
 template <bool kBatch, bool kCount>
 static int march_grid() {
-  static int blocks = 0;
-  if (!blocks) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_kernel<kBatch, kCount>,
-                                                      kMarchThreads, 0) != cudaSuccess || occ < 1)
-      occ = 1;
-    blocks = occ * kNumSMs;
-  }
+  static const int blocks = resident_blocks(march_kernel<kBatch, kCount>);
   return blocks;
 }
 
@@ -725,14 +728,7 @@ cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* t
                                  : launch_pdl(march_pixel_pass_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0,
                                               s, p, ntiles, tile_counter);
   if (e != cudaSuccess) return e;
-  static int grid = 0;
-  if (!grid) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_kernel<false>, kMarchThreads, 0) !=
-            cudaSuccess || occ < 1)
-      occ = 1;
-    grid = occ * kNumSMs;
-  }
+  static const int grid = resident_blocks(march_segment_kernel<false>);
   const int nitems = ntiles * max_segments;
   if (p.staged_half)
     e = p.shadow_volume ? launch_pdl(march_segment_kernel<true, GridH>, dim3(grid), dim3(kMarchThreads), 0, s, p,
@@ -822,13 +818,7 @@ cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int*
 }
 
 int march_segment_blocks_max() {
-  static int occ = 0;
-  if (!occ) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, march_segment_batch_kernel,
-                                                      kMarchThreads, 0) != cudaSuccess ||
-        occ < 1)
-      occ = 1;
-  }
+  static const int occ = resident_blocks(march_segment_batch_kernel) / kNumSMs;
   return occ;
 }
 

@@ -789,6 +789,21 @@ static cudaError_t configure(K kernel, int smem_needed, int tmem_cols, Launch* L
   return cudaSuccess;
 }
 
+// A kernel's launch configuration, computed once per process: held in a
+// function-local static, whose initialisation is thread-safe (concurrent
+// first calls wait for it).  A failed configuration is returned again on
+// every call.
+struct LaunchOnce {
+  cudaError_t err = cudaSuccess;
+  Launch L;
+};
+template <typename K>
+static LaunchOnce configure_once(K kernel, int smem_needed, int tmem_cols) {
+  LaunchOnce o;
+  o.err = configure(kernel, smem_needed, tmem_cols, &o.L);
+  return o;
+}
+
 // Pack a 3x3 conv weight [cout][cin][3][3] (float) into the B-operand tiles.
 template <typename T>
 static void pack_conv(const float* w, int cin, int cout, int NT, std::vector<uint8_t>& out) {
@@ -1047,14 +1062,10 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   constexpr int NT = conv_nt(CIN, COUT);
   using Cfg = ConvCfg<CIN, COUT, NT, Q8>;
   static_assert(Cfg::SMEM <= 232448, "shared memory budget");
-  static Launch L;
-  static bool init = false;
-  if (!init) {
-    cudaError_t e =
-        configure(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static const LaunchOnce once =
+      configure_once(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8>, Cfg::SMEM, Cfg::TMEM_COLS);
+  if (once.err != cudaSuccess) return once.err;
+  const Launch& L = once.L;
   TcConvArgs<T> a{};
   a.nimg = n;
   int ntiles = 0;
@@ -1090,13 +1101,9 @@ cudaError_t run_convT(const NetTcWeights* w, int n, const T* const* ins, T* cons
                       const int* H, const int* W, AmaxSlots am, unsigned int* err, cudaStream_t s) {
   constexpr int NS = kUpSplit[LAYER];
   using Cfg = ConvTCfg<CIN, COUT, Q8, NS>;
-  static Launch L;
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = configure(convT_tc_kernel<T, CIN, COUT, Q8, NS>, Cfg::SMEM, Cfg::TMEM_COLS, &L);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static const LaunchOnce once = configure_once(convT_tc_kernel<T, CIN, COUT, Q8, NS>, Cfg::SMEM, Cfg::TMEM_COLS);
+  if (once.err != cudaSuccess) return once.err;
+  const Launch& L = once.L;
   TcConvTArgs<T> a{};
   a.nimg = n;
   int ntiles = 0;
