@@ -165,11 +165,11 @@ def run_reference(args):
     oracle.build()
     pf = I.config_obstacle_128()
     flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
-    # size the per-step band so the whole run stays within ~2.5 minutes: one
-    # probe band measures the per-pixel cost on this host
+    # size the per-step band so the whole run stays within --ref-seconds (150 s
+    # by default): one probe band measures the per-pixel cost on this host
     probe_t, probe_px = cpu_oracle_frame(pf, 16, flat)
     per_px = probe_t / probe_px
-    budget = 150.0 / max(1, args.steps + args.warmup)
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
     rows = int(max(8, min(pf.camera.height, budget / per_px / pf.camera.width)) // 8 * 8)
     for _ in range(args.warmup):
         cpu_oracle_frame(pf, 8, flat)
@@ -208,6 +208,8 @@ def main():
     ap.add_argument("--forms", default="animated,batched,serving",
                     help="comma list of further workloads measured after the primary line's "
                          "('animated', 'batched', 'serving', or 'none')")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="CPU time the reference arm (the FP64 oracle) spends on its timed and warm-up steps")
     ap.add_argument("--anim-frames", type=int, default=300,
                     help="frames of the animated form (300; fewer keep a profiler capture small)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
