@@ -283,6 +283,21 @@ def test_jitter_unbiased_sample_count():
     assert abs(N.mean() - chord / h) < 1e-4
 
 
+def test_jittered_view_sample_count_is_unbiased(orc):
+    """Through the oracle: with the front light only (no shadow samples) each
+    pixel's count is its number of view samples N = floor(chord/h + u); over the
+    per-pixel hashed jitter u it takes only the two neighbouring integers and
+    averages chord/h, and without jitter it is floor(chord/h)."""
+    n, h = 32, 3.0
+    vol = np.full((n, n, n), 0.01, np.float32)
+    cam = axis_camera(n, 64, 64)
+    _, s, _ = orc.guide(vol, None, cam, h, jitter=1, t_min=0.0, light_set=1, seed=5, frame=9)
+    assert set(np.unique(s)) == {10, 11}
+    assert abs(s.mean() - n / h) < 0.03          # 4 standard errors over 4096 pixels
+    _, s0, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0, light_set=1)
+    assert np.all(s0 == 10)
+
+
 def test_vertical_flip_symmetry(orc):
     """Flipping the grid about the horizontal mid-plane flips the guide rows; top
     and bottom lights swap roles, their sum is invariant."""
