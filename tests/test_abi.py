@@ -63,3 +63,33 @@ def test_create_rejects_grids_past_32_bit_cell_indices_without_touching_the_gpu(
         with pytest.raises(nsl.NslError) as ei:
             nsl.nsl_create(*dims, nsl.NSL_F32, 1.0, blob, 64, 64)
         assert ei.value.status == nsl.NSL_ERR_INVALID_ARG, dims
+
+
+def test_default_options_without_gpu():
+    """Documented defaults: t_min 1e-4 (early termination), tau_depth 0.01,
+    jitter on, unit surrogate intensities, HG g = 0, front/top/bottom lights;
+    the server's 40 GiB budget, 2 streams, batches of up to 64, FP16 network."""
+    from paper_2604_03748_gb300 import nsl
+    o = nsl.march_opts()
+    assert o.t_min == pytest.approx(1e-4) and o.tau_depth == pytest.approx(0.01)
+    assert o.jitter == 1 and o.seed == 0 and o.frame == 0 and o.phase_g == 0.0
+    assert list(o.surrogate_I) == [1.0, 1.0, 1.0]
+    assert o.segment_exact == 0 and o.light_set == nsl.NSL_LIGHTS_FTB and o.shadow_volume == 0
+    s = nsl.server_opts()
+    assert s.hbm_budget_bytes == 40 << 30 and s.streams == 2 and s.max_batch == 64
+    assert s.precision == nsl.NSL_PREC_F16 and s.scratch_bytes_per_stream == 0
+    assert s.march.t_min == pytest.approx(1e-4) and s.march.jitter == 1
+
+
+def test_null_handles_rejected_without_gpu():
+    """Host-side argument checks return an error status and set the last-error
+    message before any CUDA call."""
+    import ctypes as C
+    from paper_2604_03748_gb300 import nsl
+    lib = nsl.load()
+    st = lib.nsl_server_create(None, 0, None, None)
+    assert st == nsl.NSL_ERR_INVALID_ARG and b"NULL" in lib.nsl_last_error()
+    out = C.c_void_p()
+    bad = nsl.server_opts(streams=0)
+    st = lib.nsl_server_create(None, 0, C.byref(bad), C.byref(out))
+    assert st == nsl.NSL_ERR_INVALID_ARG and not out.value
