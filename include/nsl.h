@@ -313,7 +313,10 @@ NSL_API nsl_status nsl_render_frame_host_async(nsl_ctx* ctx, const void* density
  * Batched frames: many plumes of different grid and billboard sizes per call.
  * Every stage runs as one launch over all plumes (staging, the guide march,
  * each network layer, shading), so the launch count does not grow with the
- * number of plumes.  Same arithmetic as the single-plume calls.
+ * number of plumes.  The method is that of the single-plume calls. The
+ * guide agrees with theirs to rounding, because the grouped march takes every
+ * shadow sample at its exact position and stages float16 grids as float32.
+ * The network and the shading are bit-identical given the same guide.
  * ------------------------------------------------------------------------- */
 typedef struct {
   const void* density_dev;   /* [nz][ny][nx], grid.dtype */
