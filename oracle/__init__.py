@@ -7,8 +7,8 @@ it; inputs arrive as plain numpy arrays and dataclass-like objects.
 
 Parity status per function (pins live in tests/test_oracle_*.py):
   guide                 pinned (closed forms: empty, constant cube, linear field,
-                        homogeneous sphere chords, symmetry, mask, HG
-                        normalisation)
+                        homogeneous sphere chords, perspective camera
+                        chords, symmetry, mask, HG normalisation)
   reference_lightmaps   pinned (slab closed form, midpoint order)
   net_forward           pinned (PyTorch float64 conv/convT/pool/LayerNorm,
                         NAFBlock identity at beta=gamma=0)

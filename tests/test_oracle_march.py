@@ -226,6 +226,48 @@ def test_linear_field_optical_depth_series(orc):
     np.testing.assert_allclose(-np.log(g[1]), tau, rtol=1e-9)
 
 
+def test_perspective_camera_chords(orc):
+    """The perspective camera model (fov_y, aspect W/H, pixel centres, the frame
+    r = f x up, u = r x f): on a constant cube without jitter a pixel's view
+    samples sit at t_in + n h for n = 1..floor(chord/h), so -ln T is sigma h
+    floor(chord/h) with the chord of that pixel's ray through the box, which the
+    test computes from the camera definition in float64."""
+    n, h, sig = 32, 0.5, 0.01
+    W, H, fov = 40, 24, 40.0
+    vol = np.full((n, n, n), sig, np.float32)
+    eye, tgt = np.array([16.0, 16.0, 80.0]), np.array([16.0, 16.0, 16.0])
+    cam = I.Camera(I.PERSP, tuple(eye), tuple(tgt), (0.0, 1.0, 0.0), fov, 1.0, W, H)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0)
+    f = (tgt - eye) / np.linalg.norm(tgt - eye)
+    r = np.cross(f, [0.0, 1.0, 0.0])
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    k = 2.0 * math.tan(math.radians(fov) / 2.0)
+    s32 = float(np.float32(sig))
+    checked = missed = 0
+    for j in range(H):
+        for i in range(W):
+            sx, sy = (i + 0.5) / W - 0.5, 0.5 - (j + 0.5) / H
+            d = f + k * (sx * (W / H) * r + sy * u)
+            d /= np.linalg.norm(d)
+            with np.errstate(divide="ignore"):
+                ta, tb = (0.0 - eye) / d, (n - eye) / d
+            t_in = max(np.minimum(ta, tb).max(), 0.0)
+            t_out = np.maximum(ta, tb).min()
+            chord = max(t_out - t_in, 0.0)
+            if chord == 0.0:
+                assert g[1, j, i] == 1.0 and g[0, j, i] == 0.0
+                missed += 1
+                continue
+            q = chord / h
+            if min(q - math.floor(q), math.ceil(q) - q) < 1e-3:
+                continue          # a sample on the exit face: float rounding decides
+            tau = s32 * h * math.floor(q)
+            assert abs(-math.log(g[1, j, i]) - tau) <= 1e-9 * tau, (i, j)
+            checked += 1
+    assert checked > 0.5 * W * H and missed > 0
+
+
 def test_homogeneous_sphere_chord(orc):
     """A homogeneous sphere seen along -z through the voxel-centre columns: the
     column's trilinear profile is piecewise linear with breakpoints on the
