@@ -107,6 +107,25 @@ def test_light_sets_constant_cube_closed_form(orc, jitter):
         np.testing.assert_allclose(g2[1, :, i], T, rtol=1e-12)
 
 
+def test_side_lights_follow_the_camera_up_axis(orc):
+    """The top / bottom surrogate lights are the camera's +u / -u, not world Y:
+    looking down -z with up = +x, the frame is r = -y, u = +x, so image row j
+    sits at x = n - 1 - 2j and the top / bottom shadow rays hold (n - x) // h
+    and x // h samples, whatever the pixel's y."""
+    n, h, sig = 32, 4.0, 0.05
+    W = H = 16
+    vol = np.full((n, n, n), sig, np.float32)
+    cam = I.Camera(I.ORTHO, (n / 2, n / 2, n + 18.0), (n / 2, n / 2, 0.0), (1.0, 0.0, 0.0), 40.0, float(n), W, H)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=0, t_min=0.0)
+    s32 = float(np.float32(sig))
+    M = n // int(h)
+    for j in range(H):
+        x = n - 1 - 2 * j
+        L, T = cube_closed_form(s32, h, M, int((n - x) // h), int(x // h))
+        np.testing.assert_allclose(g[0, j], L, rtol=1e-12)
+        np.testing.assert_allclose(g[1, j], T, rtol=1e-12)
+
+
 @pytest.mark.parametrize("jitter", [0, 1])
 def test_shadow_volume_constant_cube_closed_form(orc, jitter):
     """Transmittance-volume mode: every voxel centre y_c holds exp(-sigma h K)
