@@ -229,6 +229,14 @@ def _dptr(t, dtypes=None):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(t, count, what):
+    """The C ABI takes plain pointers and cannot see a buffer's size: refuse a
+    tensor with fewer than `count` elements before the call (a kernel would
+    read or write past its end)."""
+    if t is not None and t.numel() < count:
+        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: buffer holds {t.numel()} elements, needs {count}")
+
+
 F32 = ("float32",)
 GRID_TYPES = ("float32", "float16")
 U8 = ("uint8",)
@@ -272,6 +280,7 @@ def nsl_guide_sample_count(ctx, cam, step, opts=None, stream=None) -> int:
 
 
 def nsl_guiding_map(ctx, density, mask, cam, step, guide, light=None, opts=None, stream=None):
+    _need(guide, 3 * int(cam.width) * int(cam.height), "nsl_guiding_map: guide")
     lib = load()
     li = lights([light])[0] if light is not None else None
     check(lib.nsl_guiding_map(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), C.byref(camera(cam)),
@@ -284,6 +293,9 @@ def nsl_guiding_map_noalloc(grid_shape, dtype, sigma_scale, density, mask, cam, 
                             opts=None, stream=None):
     """Guide march whose scratch is the library's static device array (no allocation)."""
     nz, ny, nx = grid_shape
+    _need(density, nx * ny * nz, "nsl_guiding_map_noalloc: density")
+    _need(mask, nx * ny * nz, "nsl_guiding_map_noalloc: mask")
+    _need(guide, 3 * int(cam.width) * int(cam.height), "nsl_guiding_map_noalloc: guide")
     g = nsl_grid_desc(nx, ny, nz, dtype, sigma_scale)
     check(load().nsl_guiding_map_noalloc(C.byref(g), _dptr(density, GRID_TYPES), _dptr(mask, U8),
                                          C.byref(camera(cam)), float(step),
@@ -292,11 +304,15 @@ def nsl_guiding_map_noalloc(grid_shape, dtype, sigma_scale, density, mask, cam, 
 
 
 def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, stream=None):
+    _need(guide, 3 * int(width) * int(height), "nsl_predict_lightmaps: guide")
+    _need(lightmaps, 8 * int(width) * int(height), "nsl_predict_lightmaps: lightmaps")
     check(load().nsl_predict_lightmaps(ctx, _dptr(guide, F32), int(width), int(height), int(precision),
                                        _dptr(lightmaps, F32), _stream(stream)), "nsl_predict_lightmaps")
 
 
 def nsl_shade(ctx, lightmaps, width, height, cam, light_list, rgba, stream=None):
+    _need(lightmaps, 8 * int(width) * int(height), "nsl_shade: lightmaps")
+    _need(rgba, 4 * int(width) * int(height), "nsl_shade: rgba")
     check(load().nsl_shade(ctx, _dptr(lightmaps, F32), int(width), int(height), C.byref(camera(cam)),
                            lights(light_list), len(light_list), _dptr(rgba, F32), _stream(stream)),
           "nsl_shade")
@@ -313,6 +329,7 @@ def nsl_pack_lightmaps(lightmaps, width, height, fmt, tex1, tex2, stream=None):
     for t in (tex1, tex2):
         if tuple(t.shape) != (int(height), int(width), 4):
             raise ValueError("textures must be [H][W][4]")
+    _need(lightmaps, 8 * int(width) * int(height), "nsl_pack_lightmaps: lightmaps")
     check(load().nsl_pack_lightmaps(_dptr(lightmaps, F32), int(width), int(height), int(fmt),
                                     _dptr(tex1, _TEX_DTYPES[fmt]), _dptr(tex2, _TEX_DTYPES[fmt]),
                                     _stream(stream)), "nsl_pack_lightmaps")
@@ -335,6 +352,12 @@ def nsl_shade_shadowed(ctx, lightmaps, guide, width, height, cam, light_list, ma
     None) per light."""
     if len(maps) != len(light_list):
         raise ValueError("one map (or None) per light")
+    hw = int(width) * int(height)
+    _need(lightmaps, 8 * hw, "nsl_shade_shadowed: lightmaps")
+    _need(guide, 3 * hw, "nsl_shade_shadowed: guide")
+    _need(rgba, 4 * hw, "nsl_shade_shadowed: rgba")
+    for m in maps:
+        _need(m, int(resolution) * int(resolution), "nsl_shade_shadowed: shadow map")
     ptrs = (C.c_void_p * max(1, len(maps)))(*[None if m is None else _dptr(m, F32).value for m in maps])
     check(load().nsl_shade_shadowed(ctx, _dptr(lightmaps, F32), _dptr(guide, F32), int(width), int(height),
                                     C.byref(camera(cam)), lights(light_list), len(light_list), ptrs,
@@ -374,6 +397,7 @@ class Context:
     def __init__(self, grid_shape, dtype, blob, max_width, max_height, sigma_scale=1.0):
         nz, ny, nx = grid_shape
         self.ctx = nsl_create(nx, ny, nz, dtype, sigma_scale, blob, max_width, max_height)
+        self.voxels = nx * ny * nz
 
     def close(self):
         if self.ctx:
@@ -387,12 +411,16 @@ class Context:
             pass
 
     def stage_grid(self, density, mask, stream=None):
+        _need(density, self.voxels, "nsl_stage_grid: density")
+        _need(mask, self.voxels, "nsl_stage_grid: mask")
         nsl_stage_grid(self.ctx, density, mask, stream=stream)
 
     def guide_sample_count(self, cam, step, opts=None, stream=None):
         return nsl_guide_sample_count(self.ctx, cam, step, opts=opts, stream=stream)
 
     def guiding_map(self, density, mask, cam, step, guide, opts=None, stream=None):
+        _need(density, self.voxels, "nsl_guiding_map: density")
+        _need(mask, self.voxels, "nsl_guiding_map: mask")
         nsl_guiding_map(self.ctx, density, mask, cam, step, guide, opts=opts, stream=stream)
 
     def predict_lightmaps(self, guide, width, height, precision, lightmaps, stream=None):
@@ -414,6 +442,11 @@ def plume_array(items):
         p = arr[k]
         d = it["density"]
         nz, ny, nx = d.shape
+        hw = int(it["camera"].width) * int(it["camera"].height)
+        _need(it.get("mask"), nx * ny * nz, f"plume {k}: mask")
+        _need(it["guide"], 3 * hw, f"plume {k}: guide")
+        _need(it["lightmaps"], 8 * hw, f"plume {k}: lightmaps")
+        _need(it.get("rgba"), 4 * hw, f"plume {k}: rgba")
         p.density_dev = _dptr(d, GRID_TYPES)
         p.mask_dev = _dptr(it.get("mask"), U8)
         p.grid = nsl_grid_desc(nx, ny, nz, NSL_F16 if str(d.dtype).endswith("float16") else NSL_F32,
@@ -546,6 +579,9 @@ class Server:
         self._keep.pop(pid, None)
 
     def submit(self, pid, cam, light, lightmaps=None, rgba=None) -> int:
+        hw = int(cam.width) * int(cam.height)
+        _need(lightmaps, 8 * hw, "nsl_server_submit: lightmaps")
+        _need(rgba, 4 * hw, "nsl_server_submit: rgba")
         rid = C.c_uint64()
         c = camera(cam)
         lt = lights([light])

@@ -93,3 +93,33 @@ def test_null_handles_rejected_without_gpu():
     bad = nsl.server_opts(streams=0)
     st = lib.nsl_server_create(None, 0, C.byref(bad), C.byref(out))
     assert st == nsl.NSL_ERR_INVALID_ARG and not out.value
+
+
+def test_binding_refuses_undersized_buffers_without_gpu():
+    """The C ABI takes plain pointers; the binding checks each buffer's element
+    count against the sizes of the call before anything reaches the library
+    (CPU tensors here: the size check comes before the device check)."""
+    import torch
+    from paper_2604_03748_gb300 import inputs as I, nsl
+    H, W = 16, 24
+    small = torch.empty(3 * H * W - 1)
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.nsl_predict_lightmaps(None, small, W, H, nsl.NSL_PREC_F32, torch.empty(8 * H * W))
+    assert ei.value.status == nsl.NSL_ERR_INVALID_ARG and "guide" in str(ei.value)
+    with pytest.raises(nsl.NslError):
+        nsl.nsl_predict_lightmaps(None, torch.empty(3 * H * W), W, H, nsl.NSL_PREC_F32, torch.empty(8 * H * W - 8))
+    with pytest.raises(nsl.NslError):
+        nsl.nsl_shade(None, torch.empty(8 * H * W), W, H, I.perspective_camera(16, 1, W, H), [],
+                      torch.empty((3, H, W)))
+    cam = I.perspective_camera(16, 1, W, H)
+    with pytest.raises(nsl.NslError):
+        nsl.nsl_guiding_map(None, torch.empty(16 ** 3), None, cam, 2.0, torch.empty((3, H, W - 8)))
+    item = dict(density=torch.empty((16, 16, 16)), mask=None, camera=cam, step=2.0,
+                light=I.random_light(1), guide=torch.empty((3, H, W)), lightmaps=torch.empty((8, H, W - 1)),
+                rgba=None)
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.plume_array([item])
+    assert "lightmaps" in str(ei.value)
+    # buffers of the right size get as far as the device check
+    with pytest.raises(ValueError):
+        nsl.nsl_predict_lightmaps(None, torch.empty(3 * H * W), W, H, nsl.NSL_PREC_F32, torch.empty(8 * H * W))
