@@ -4,9 +4,10 @@
 // non-zero density shoots two shadow rays toward the top and bottom surrogate
 // lights (camera up / down) to the box exit; the front light's transmittance
 // is the view ray's own T_{n-1} (a front-light march from p_n toward the camera
-// visits exactly the earlier samples).  The staged grid (<= 64 MiB for the
-// grids used here) stays resident in the 126 MB L2 after its first touch, so
-// the kernel is bound by L1/L2 gather throughput and FP32 issue, not by HBM.
+// visits exactly the earlier samples).  A staged grid that fits the 129 MB L2
+// (34.6 MB at 128^3) stays resident after its first touch, so the kernel is
+// bound by L1/L2 gather throughput and FP32 issue, not by HBM; a larger one
+// (256^3: 136 MB as FP16 quads) is partly re-read from DRAM.
 //
 // Geometry that decides integers (sample counts, positions) is evaluated with
 // one IEEE rounding per operation in a fixed order (__fadd_rn & co. are never
@@ -27,7 +28,8 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
 
 // Staged grid layouts (both hold sigma' = scale * rho * [mask == 0], float32,
 // padded by one cell on the low sides with every neighbour index clamped to the
-// grid, so a sample inside the box needs no clamping):
+// grid, so a sample inside the box needs no clamping; GridH below is the quad
+// layout in FP16 holding rho * [mask == 0], scaled after the blend):
 //   kLayoutQuad    float4 per cell, the x/y 2x2 neighbourhood of its slice; a
 //                  sample reads 2 x 16 bytes (the default)
 //   kLayoutOcto    2 x float4 per cell, the 2x2x2 neighbourhood; a sample reads
