@@ -405,6 +405,22 @@ def test_depth_channel(orc):
     assert np.all(g[2] == 11 * h)
 
 
+def test_depth_channel_with_jitter_is_literal(orc):
+    """With jitter, D stays the literal n h of Alg. 1 (measured from the jittered
+    x_0): a multiple of h, at the first sample above tau, whose position
+    t_in + (n - u) h lies within one step of the slab edge."""
+    n, h = 32, 2.0
+    vol = np.zeros((n, n, n), np.float32)
+    vol[:10] = 0.5
+    cam = axis_camera(n, 16, 16)
+    g, _, _ = orc.guide(vol, None, cam, h, jitter=1, t_min=0.0, seed=3, frame=1)
+    m = g[2] / h
+    assert np.all(m == np.round(m)) and np.all(m >= 1)
+    # the first sample above tau sits at z = 32 - (m - u) h, just past the ramp's
+    # tau crossing at z = 10.5 - 0.02 = 10.48 (voxel centres 9.5 -> 10.5, 0.5 -> 0)
+    assert set(np.unique(m)) <= {11.0, 12.0}
+
+
 def test_sample_counts_and_flags_small(orc):
     pf = I.config_plain_64()
     g, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
