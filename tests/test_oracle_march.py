@@ -230,6 +230,22 @@ def test_trilinear_exact_on_linear_field(orc):
     assert orc.sample_sigma(vol32, None, (0.0, 0.0, 0.0)) == pytest.approx(float(vol32[0, 0, 0]), abs=1e-12)
 
 
+def test_mask_applied_per_voxel_before_interpolation(orc):
+    """R12: an obstacle voxel is zeroed before the trilinear blend, so the field
+    is 0 at its centre, the full value at the neighbouring centres and the
+    linear blend in between; sigma_scale multiplies the result."""
+    n, c = 8, 0.4
+    vol = np.full((n, n, n), c, np.float32)
+    mask = np.zeros((n, n, n), np.uint8)
+    mask[4, 3, 5] = 1                                   # (z, y, x)
+    cf = float(np.float32(c))
+    assert orc.sample_sigma(vol, mask, (5.5, 3.5, 4.5)) == 0.0
+    assert orc.sample_sigma(vol, mask, (6.5, 3.5, 4.5)) == pytest.approx(cf, abs=1e-15)
+    assert orc.sample_sigma(vol, mask, (6.0, 3.5, 4.5)) == pytest.approx(0.5 * cf, abs=1e-15)
+    assert orc.sample_sigma(vol, mask, (5.75, 3.75, 4.5)) == pytest.approx((1 - 0.75 * 0.75) * cf, abs=1e-15)
+    assert orc.sample_sigma(vol, mask, (6.0, 3.5, 4.5), sigma_scale=3.0) == pytest.approx(1.5 * cf, abs=1e-15)
+
+
 def test_linear_field_optical_depth_series(orc):
     """Density linear in z, camera along -z without jitter: the view samples sit
     at z = n - m h, so -ln T is an arithmetic series of the clamped linear field."""
