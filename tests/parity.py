@@ -14,7 +14,7 @@ TOL_NET_F16 = 2e-2        # FP16-operand tensor-core network, of the output rang
 # 7.6% on the 512^2 obstacle-scene guide, so the BF16 path is held to 1e-1; the
 # 2e-2 bound applies to FP16 operands (emulated 0.6% / 0.95%).
 TOL_NET_BF16 = 1e-1
-TOL_NET_FP8 = 6e-2        # FP8 network, of the output range (spec bound, see below)
+TOL_NET_FP8 = 6e-2        # FP8 network, of the output range (the FP8 precision bound, see below)
 # FP8 E4M3 (3 fraction bits) on these random weights: the oracle's exact
 # emulation of the FP8 path is itself 15-53% of the range away from FP64, so
 # the GPU FP8 network is compared with the emulation, and its distance to FP64
@@ -28,7 +28,7 @@ TOL_NET_FP8 = 6e-2        # FP8 network, of the output range (spec bound, 
 # the median and the 99th percentile of |gpu - emulation| / range, and a
 # sanity bound on the maximum.
 TOL_NET_FP8_EMU_MEDIAN = 2e-3  # measured 1e-5 .. 6e-5
-TOL_NET_FP8_EMU_P99 = 6e-2   # the spec FP8 figure, on the 99th percentile
+TOL_NET_FP8_EMU_P99 = 6e-2   # the FP8 bound, on the 99th percentile
 TOL_NET_FP8_EMU_MAX = 0.5
 TOL_SHADE = 1e-5
 MAX_EXCUSED_FRAC = 1e-3   # threshold-flip pixels allowed to differ
