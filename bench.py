@@ -155,6 +155,24 @@ def whole_job_mpix(frames_all_ranks, pixels_per_frame, max_ms):
     return frames_all_ranks * pixels_per_frame / (max_ms / 1e3) / 1e6
 
 
+def single_core_oracle(rows=8):
+    """The oracle on one host core: the same band measurement in a child process
+    with OpenMP held to one thread.  Returns (Mpix/s, None) or (None, reason)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import numpy as np; import bench, oracle; "
+            "from paper_2604_03748_gb300 import inputs as I; oracle.build(); pf = I.config_obstacle_128(); "
+            "flat = I.flat_params(I.make_params(16, 0)).astype(np.float64); "
+            "print(json.dumps(bench.cpu_oracle_frame(pf, %d, flat)))" % (ROOT, rows))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    except subprocess.TimeoutExpired:
+        return None, "timed out"
+    if r.returncode != 0:
+        return None, (r.stderr.strip().splitlines() or ["failed"])[-1][:200]
+    t, px = json.loads(r.stdout.strip().splitlines()[-1])
+    return px / t / 1e6, None
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle as it stands, on host cores."""
     ws, rank, _ = dist_env()
@@ -180,6 +198,7 @@ def run_reference(args):
         total_px += px
     value = total_px / total_t / 1e6
     cores = os.cpu_count()
+    one, why = single_core_oracle()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
@@ -189,7 +208,10 @@ def run_reference(args):
                                         "sample_rows_per_step": rows},
         "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                          "sample": f"{rows}x512 pixel band of the 512x512 frame per step: guide march, "
-                                   f"network on the band, shade"},
+                                   f"network on the band, shade",
+                         "single_core": {"value": one, "unit": "Mpix/s", "cores": 1,
+                                         "sample": "8x512 pixel band, OMP_NUM_THREADS=1",
+                                         **({"unavailable": why} if why else {})}},
         "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -30,6 +30,8 @@ def test_reference_arm_json_line():
     assert d["config"]["workload"] == "plume128_sphere20_persp512_h2"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    one = cb["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and "unavailable" not in one
     assert d["e2e"] == {"value": d["value"], "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
