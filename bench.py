@@ -139,6 +139,19 @@ def cpu_oracle_frame(pf, rows, blob_params, c0=16, keep=False):
     return t, rows * pf.camera.width
 
 
+REPLICA_TIMEOUT_S = 600.0   # a replica that dies ends the others' next collective with an error
+
+
+def init_replicas(backend, timeout_s=REPLICA_TIMEOUT_S):
+    """Process group of the independent replicas (one per GPU).  Its only
+    collectives are the barriers around the timed region and the max-over-ranks
+    reduction; the finite timeout turns a replica that died or never arrives
+    into an error on the others instead of a hang."""
+    import datetime
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s))
+
+
 def max_over_ranks(local_ms, dev, ws):
     """The slowest rank's time (every rank gets it); a no-op for one process."""
     if ws <= 1:
@@ -245,7 +258,7 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        init_replicas("nccl")
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())

@@ -53,3 +53,36 @@ def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(3.5, None, 1) == 3.5
     assert bench.whole_job_mpix(20, 512 * 512, 1000.0) == pytest.approx(20 * 512 * 512 / 1e6)
+
+
+def _failing_rank_main(rank, ws, port, out):
+    import time
+    import torch
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["RANK"] = str(rank)                 # as torchrun sets them
+    os.environ["WORLD_SIZE"] = str(ws)
+    bench.init_replicas("gloo", timeout_s=10.0)
+    if rank == 1:
+        os._exit(0)                      # a replica that dies between steps, before the reduction
+    t0 = time.perf_counter()
+    try:
+        bench.max_over_ranks(5.0, torch.device("cpu"), ws)
+        out["raised"] = False
+    except Exception as e:               # the survivor learns of it as an error, not a hang
+        out["raised"] = True
+        out["what"] = type(e).__name__
+    out["seconds"] = time.perf_counter() - t0
+
+
+def test_dead_replica_is_an_error_not_a_hang():
+    ws = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_failing_rank_main, args=(ws, _free_port(), out), nprocs=ws, join=True,
+                       start_method="spawn")
+    assert out["raised"] is True, dict(out)
+    assert out["seconds"] < 60.0
