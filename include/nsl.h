@@ -158,21 +158,30 @@ NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const 
  * cudaMalloc at all: a render thread whose frame budget cannot absorb the device
  * synchronisation an allocation may cause, an engine whose own allocator owns
  * every byte of device memory, or code that has no context to keep between
- * frames.  It computes exactly what nsl_guiding_map computes for a float32
- * grid, with the same kernels (a float16 grid is staged here as float32 sigma',
- * so its guide can differ from nsl_guiding_map's by rounding); the staged grid and the tile counter live in one static device
- * array of 40 MiB + 256 bytes inside libnsl, which every GPU that loads the
- * library holds until the process exits.
+ * frames.  It stages the grid with the kernel nsl_guiding_map uses (float32
+ * quads of sigma' for a float32 grid, float16 quads for a float16 one) and then
+ * runs the single-pass march kernel (the one nsl_guide_sample_count runs) rather
+ * than nsl_guiding_map's three-pass segmented march, which would need per-pixel
+ * segment scratch.  The two marches make the same samples and decisions; their
+ * guides differ only by the rounding of the in-scattering sum's grouping (well
+ * inside 1e-5 of the range), not bitwise.  The staged grid and the tile counter
+ * live in one static device array of 40 MiB + 256 bytes inside libnsl, which
+ * every GPU that loads the library holds until the process exits.
  *   grid          shape, storage and sigma_scale of density_dev
  *   density_dev, mask_dev, cam, step_voxels, opts, guide_dev, stream
- *                 as for nsl_guiding_map (no light argument)
- * Limits: the staged grid takes 16 bytes per cell of (nx+1)(ny+1)(nz+2) cells
- * and must fit in 40 MiB (136^3 fits; 137^3 does not); larger grids return
- * NSL_ERR_INVALID_ARG with a message, and nothing is queued.  No cudaMalloc, cudaFree or other allocating
- * call is made.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it: make that
- * first call before any stream capture.  All calls share the one array and it
- * keeps the last call's contents (every call restages the grid and zeroes the
+ *                 as for nsl_guiding_map (no light argument); opts->shadow_volume
+ *                 is refused with NSL_ERR_UNSUPPORTED (its volumes need a context)
+ * Limits: the staged grid takes (nx+1)(ny+1)(nz+2) cells of 16 bytes (float32
+ * grid) or 8 bytes (float16 grid) and must fit in 40 MiB: a float32 136^3 grid
+ * fits and 137^3 does not; a float16 172^3 grid fits and 173^3 does not.  Larger
+ * grids return NSL_ERR_INVALID_ARG with a message, and nothing is queued.  No
+ * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and keeps it for the life of the process: make that first
+ * call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library is loaded, since the kept address
+ * belongs to the device's primary context.  All calls share the one array and
+ * it keeps the last call's contents (every call restages the grid and zeroes the
  * counter first); calls that overlap on the GPU (different streams, or devices
  * sharing nothing but this rule) race on it, so serialise them. */
 NSL_API nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const void* density_dev,

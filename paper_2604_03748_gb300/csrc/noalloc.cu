@@ -1,8 +1,11 @@
 // nsl_guiding_map_noalloc: the guide march for callers that must not allocate
 // device memory.  Its scratch (the staged grid and the march tile counter)
 // lives in one file-scope __device__ array instead of context-owned cudaMalloc
-// buffers; the kernels are the same staging and march kernels nsl_guiding_map
-// launches.
+// buffers.  Staging is the kernel nsl_guiding_map uses (FP32 quads for a float32
+// grid, FP16 quads for a float16 one); the march is the single-pass march kernel
+// (the one nsl_guide_sample_count runs), which needs no per-segment scratch.  It
+// equals nsl_guiding_map's three-pass segmented march up to the grouping of the
+// in-scattering sum.
 #include <cmath>
 #include <mutex>
 
@@ -10,10 +13,10 @@
 
 namespace nsl {
 
-// Scratch bytes: 40 MiB for the staged grid (16 bytes per cell of the padded
-// x/y-quad layout, (nx+1)(ny+1)(nz+2) cells: 128^3 takes 34.6 MB) plus 256 bytes
-// for the tile counter.  Every GPU that loads the library holds this array until
-// exit.
+// Scratch bytes: 40 MiB for the staged grid ((nx+1)(ny+1)(nz+2) cells of the
+// padded x/y-quad layout, 16 bytes per cell for a float32 grid and 8 for a
+// float16 one: a float32 128^3 grid takes 34.6 MB) plus 256 bytes for the tile
+// counter.  Every GPU that loads the library holds this array until exit.
 constexpr size_t kNoAllocGridBytes = size_t(40) << 20;
 constexpr size_t kNoAllocBytes = kNoAllocGridBytes + 256;
 
@@ -25,7 +28,8 @@ std::mutex g_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
 
 // Device address of the scratch array on the current device (host code must not
-// pass the array's host-side name to a kernel).  Looked up once per device.
+// pass the array's host-side name to a kernel).  Looked up once per device, in
+// that device's primary context, and kept for the life of the process.
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -41,12 +45,6 @@ cudaError_t scratch_address(unsigned char** out) {
   *out = g_scratch_addr[dev];
   return cudaSuccess;
 }
-
-uint32_t pcg_host(uint32_t v) {
-  uint32_t state = v * 747796405u + 2891336453u;
-  uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
-  return (word >> 22u) ^ word;
-}
 }  // namespace
 
 }  // namespace nsl
@@ -57,79 +55,47 @@ extern "C" nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const v
                                               const uint8_t* mask, const nsl_camera* cam,
                                               float step, const nsl_march_opts* opts,
                                               float* guide, void* stream) {
+  static const char* fn = "nsl_guiding_map_noalloc";
   if (!grid || !density || !cam || !guide)
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: NULL argument");
+    return fail(NSL_ERR_INVALID_ARG, "%s: NULL argument", fn);
   if (!grid_dims_ok(grid->nx, grid->ny, grid->nz) || (grid->dtype != NSL_F32 && grid->dtype != NSL_F16) ||
       !(grid->sigma_scale >= 0.f) || !std::isfinite(grid->sigma_scale))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: bad grid description");
-  const size_t need = staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float);
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad grid description", fn);
+  const bool half = grid->dtype == NSL_F16;
+  const size_t need = staged_cells(grid->nx, grid->ny, grid->nz) * (half ? 4 * sizeof(__half) : 4 * sizeof(float));
   if (need > kNoAllocGridBytes)
     return fail(NSL_ERR_INVALID_ARG,
-                "nsl_guiding_map_noalloc: a %dx%dx%d grid needs %zu bytes of scratch; the "
-                "built-in scratch holds %zu (use nsl_guiding_map with a context instead)",
-                grid->nx, grid->ny, grid->nz, need, kNoAllocGridBytes);
+                "%s: a %dx%dx%d %s grid needs %zu bytes of scratch; the built-in scratch holds %zu "
+                "(use nsl_guiding_map with a context instead)",
+                fn, grid->nx, grid->ny, grid->nz, half ? "float16" : "float32", need, kNoAllocGridBytes);
   const uintptr_t align_bits = reinterpret_cast<uintptr_t>(density) |
                                reinterpret_cast<uintptr_t>(guide) |
                                reinterpret_cast<uintptr_t>(mask);
   if (align_bits & 15u)
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: buffers must be 16-byte aligned");
-  if (cam->kind != NSL_CAM_ORTHO && cam->kind != NSL_CAM_PERSP)
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: bad camera kind");
-  if (cam->width < 8 || cam->height < 8 || cam->width % 8 || cam->height % 8 ||
-      cam->width > 8192 || cam->height > 8192)
-    return fail(NSL_ERR_INVALID_ARG,
-                "nsl_guiding_map_noalloc: width/height must be multiples of 8 in [8, 8192]");
-  if (cam->kind == NSL_CAM_PERSP && !(cam->fov_y_deg > 0.f && cam->fov_y_deg < 179.f))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: fov_y_deg out of (0, 179)");
-  if (cam->kind == NSL_CAM_ORTHO && !(cam->ortho_height > 0.f))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: ortho_height must be > 0");
-  {
-    const double fx = (double)cam->target[0] - cam->eye[0], fy = (double)cam->target[1] - cam->eye[1],
-                 fz = (double)cam->target[2] - cam->eye[2];
-    const double fl = std::sqrt(fx * fx + fy * fy + fz * fz);
-    const double rx = fy * cam->up[2] - fz * cam->up[1], ry = fz * cam->up[0] - fx * cam->up[2],
-                 rz = fx * cam->up[1] - fy * cam->up[0];
-    if (!(fl > 0.0) || !(std::sqrt(rx * rx + ry * ry + rz * rz) > 1e-9 * fl))
-      return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: degenerate camera basis");
-  }
-  if (!(step > 0.f) || !std::isfinite(step))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: step must be > 0");
-  nsl_march_opts o;
-  nsl_default_march_opts(&o);
-  if (opts) o = *opts;
-  if (!(o.t_min >= 0.f && o.t_min < 1.f) || !(o.phase_g > -1.f && o.phase_g < 1.f) ||
-      o.light_set < NSL_LIGHTS_FTB || o.light_set > NSL_LIGHTS_FLR)
-    return fail(NSL_ERR_INVALID_ARG, "nsl_guiding_map_noalloc: t_min, phase_g or light_set out of range");
-  if (o.shadow_volume)
-    return fail(NSL_ERR_UNSUPPORTED, "nsl_guiding_map_noalloc: shadow_volume needs a context");
+    return fail(NSL_ERR_INVALID_ARG, "%s: buffers must be 16-byte aligned", fn);
+  nsl_status st = check_camera_basic(cam, fn);
+  if (st != NSL_OK) return st;
+  MarchPlume p;
+  st = fill_march_plume(*grid, *cam, step, opts, fn, &p);
+  if (st != NSL_OK) return st;
+  if (p.shadow_volume)
+    return fail(NSL_ERR_UNSUPPORTED, "%s: shadow_volume needs a context", fn);
 
   unsigned char* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map_noalloc: scratch address");
-  float* staged = reinterpret_cast<float*>(scratch);
   int* tile_counter = reinterpret_cast<int*>(scratch + kNoAllocGridBytes);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  e = launch_stage_volume(density, grid->dtype, mask, grid->nx, grid->ny, grid->nz,
-                          grid->sigma_scale, staged, s);
+  e = half ? launch_stage_volume_half(static_cast<const __half*>(density), mask, grid->nx, grid->ny, grid->nz,
+                                      reinterpret_cast<__half*>(scratch), s)
+           : launch_stage_volume(density, grid->dtype, mask, grid->nx, grid->ny, grid->nz, grid->sigma_scale,
+                                 reinterpret_cast<float*>(scratch), s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map_noalloc: staging");
-  MarchPlume p{};
-  p.vol = staged;
-  p.nx = grid->nx; p.ny = grid->ny; p.nz = grid->nz;
-  cam_frame_from(*cam, &p.cam);
-  p.h = step;
-  p.tau_depth = o.tau_depth;
-  p.t_min = o.t_min;
-  p.tau_lim = o.t_min > 0.f ? (float)(-std::log((double)o.t_min)) : INFINITY;
-  p.jitter = o.jitter ? 1 : 0;
-  p.key = pcg_host(o.frame + pcg_host(o.seed));
-  p.g = o.phase_g;
-  for (int k = 0; k < 3; ++k) p.I[k] = o.surrogate_I[k];
-  p.segment_exact = o.segment_exact ? 1 : 0;
-  p.light_set = o.light_set;
+  p.vol = reinterpret_cast<const float*>(scratch);
+  p.staged_half = half ? 1 : 0;
+  p.scl = grid->sigma_scale;
   p.guide = guide;
-  p.tiles_x = (cam->width + kMarchTX - 1) / kMarchTX;
-  p.tile_start = 0;
   // launch_march zeroes the tile counter with cudaMemsetAsync before the march
   e = launch_march(p, tile_counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map_noalloc: march");

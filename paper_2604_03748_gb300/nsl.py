@@ -240,6 +240,36 @@ def _need(t, count, what):
 F32 = ("float32",)
 GRID_TYPES = ("float32", "float16")
 U8 = ("uint8",)
+_GRID_DTYPE_NAME = {NSL_F32: "float32", NSL_F16: "float16"}
+# grid (voxel count, dtype) of every live context, keyed by its handle: the C
+# ABI's density pointer carries neither, and a float16 buffer read as float32
+# would be read past its end
+_ctx_grid: dict = {}
+
+
+def _check_grid(t, dtype, voxels, what):
+    """Refuse a density buffer (torch tensor or numpy array) whose element type
+    is not the grid's `dtype` or that holds fewer than `voxels` elements."""
+    if t is None:
+        return
+    want = _GRID_DTYPE_NAME.get(int(dtype))
+    if want is None:
+        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: bad grid dtype {dtype}")
+    got = str(t.dtype).replace("torch.", "")
+    if got != want:
+        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: density is {got} but the grid is {want}")
+    _need(t, voxels, what)
+
+
+def _ctx_check_grid(ctx, density, mask, what):
+    info = _ctx_grid.get(getattr(ctx, "value", ctx))
+    if info is None:
+        return
+    voxels, dtype = info
+    _check_grid(density, dtype, voxels, f"{what}: density")
+    if mask is not None and str(mask.dtype).replace("torch.", "") != "uint8":
+        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: mask must be uint8, got {mask.dtype}")
+    _need(mask, voxels, f"{what}: mask")
 
 
 def _stream(stream):
@@ -259,14 +289,17 @@ def nsl_create(nx, ny, nz, dtype, sigma_scale, blob: bytes, max_width, max_heigh
     out = C.c_void_p()
     buf = C.create_string_buffer(blob, len(blob))
     check(lib.nsl_create(C.byref(g), buf, len(blob), max_width, max_height, C.byref(out)), "nsl_create")
+    _ctx_grid[out.value] = (int(nx) * int(ny) * int(nz), int(dtype))
     return out
 
 
 def nsl_destroy(ctx):
+    _ctx_grid.pop(getattr(ctx, "value", ctx), None)
     load().nsl_destroy(ctx)
 
 
 def nsl_stage_grid(ctx, density, mask, stream=None):
+    _ctx_check_grid(ctx, density, mask, "nsl_stage_grid")
     check(load().nsl_stage_grid(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), _stream(stream)),
           "nsl_stage_grid")
 
@@ -281,6 +314,7 @@ def nsl_guide_sample_count(ctx, cam, step, opts=None, stream=None) -> int:
 
 def nsl_guiding_map(ctx, density, mask, cam, step, guide, light=None, opts=None, stream=None):
     _need(guide, 3 * int(cam.width) * int(cam.height), "nsl_guiding_map: guide")
+    _ctx_check_grid(ctx, density, mask, "nsl_guiding_map")
     lib = load()
     li = lights([light])[0] if light is not None else None
     check(lib.nsl_guiding_map(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), C.byref(camera(cam)),
@@ -293,7 +327,7 @@ def nsl_guiding_map_noalloc(grid_shape, dtype, sigma_scale, density, mask, cam, 
                             opts=None, stream=None):
     """Guide march whose scratch is the library's static device array (no allocation)."""
     nz, ny, nx = grid_shape
-    _need(density, nx * ny * nz, "nsl_guiding_map_noalloc: density")
+    _check_grid(density, dtype, nx * ny * nz, "nsl_guiding_map_noalloc: density")
     _need(mask, nx * ny * nz, "nsl_guiding_map_noalloc: mask")
     _need(guide, 3 * int(cam.width) * int(cam.height), "nsl_guiding_map_noalloc: guide")
     g = nsl_grid_desc(nx, ny, nz, dtype, sigma_scale)
@@ -368,6 +402,8 @@ def nsl_shade_shadowed(ctx, lightmaps, guide, width, height, cam, light_list, ma
 def nsl_render_frame_host(ctx, density_np, mask_np, cam, light_list, step, precision,
                           guide_np=None, lightmaps_np=None, rgba_np=None, opts=None, stream=None):
     """Whole frame from host numpy buffers (copies in and out inside the call)."""
+    _ctx_check_grid(ctx, density_np, mask_np, "nsl_render_frame_host")
+
     def hp(a):
         return None if a is None else C.c_void_p(a.ctypes.data)
     check(load().nsl_render_frame_host(ctx, hp(density_np), hp(mask_np), C.byref(camera(cam)),
@@ -382,6 +418,8 @@ def nsl_render_frame_host_async(ctx, density_np, mask_np, cam, light_list, step,
     """nsl_render_frame_host without the final synchronisation (page-locked
     host buffers make the copies asynchronous); synchronise `stream` before
     touching the buffers."""
+    _ctx_check_grid(ctx, density_np, mask_np, "nsl_render_frame_host_async")
+
     def hp(a):
         return None if a is None else C.c_void_p(a.ctypes.data)
     check(load().nsl_render_frame_host_async(ctx, hp(density_np), hp(mask_np), C.byref(camera(cam)),

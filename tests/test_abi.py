@@ -123,3 +123,53 @@ def test_binding_refuses_undersized_buffers_without_gpu():
     # buffers of the right size get as far as the device check
     with pytest.raises(ValueError):
         nsl.nsl_predict_lightmaps(None, torch.empty(3 * H * W), W, H, nsl.NSL_PREC_F32, torch.empty(8 * H * W))
+
+
+def test_binding_refuses_a_density_of_the_wrong_type_without_gpu():
+    """A float16 density passed for a float32 grid would be read past its end by
+    the staging kernel: the binding refuses it before the call, for the
+    allocation-free entry point and for a context's grid (CPU tensors here)."""
+    import ctypes as C
+    import torch
+    from paper_2604_03748_gb300 import inputs as I, nsl
+    cam = I.perspective_camera(16, 1, 16, 16)
+    g = torch.empty((3, 16, 16))
+    half = torch.empty((16, 16, 16), dtype=torch.float16)
+    with pytest.raises(nsl.NslError) as ei:
+        nsl.nsl_guiding_map_noalloc(half.shape, nsl.NSL_F32, 1.0, half, None, cam, 2.0, g)
+    assert ei.value.status == nsl.NSL_ERR_INVALID_ARG and "float16" in str(ei.value)
+    with pytest.raises(nsl.NslError):
+        nsl.nsl_guiding_map_noalloc(half.shape, nsl.NSL_F16, 1.0, half.float(), None, cam, 2.0, g)
+    fake = C.c_void_p(0x10000)   # a handle the binding knows, never passed to the library
+    nsl._ctx_grid[fake.value] = (16 ** 3, nsl.NSL_F32)
+    try:
+        for fn in (lambda: nsl.nsl_stage_grid(fake, half, None),
+                   lambda: nsl.nsl_guiding_map(fake, half, None, cam, 2.0, g),
+                   lambda: nsl.nsl_render_frame_host(fake, half.numpy(), None, cam, [], 2.0, nsl.NSL_PREC_F32)):
+            with pytest.raises(nsl.NslError) as ei:
+                fn()
+            assert "float16" in str(ei.value)
+        with pytest.raises(nsl.NslError):   # right type, too few voxels
+            nsl.nsl_stage_grid(fake, torch.empty(16 ** 3 - 1), None)
+    finally:
+        nsl._ctx_grid.pop(fake.value, None)
+
+
+def test_noalloc_size_limit_without_gpu():
+    """The allocation-free entry point's scratch holds a float32 136^3 grid and
+    a float16 172^3 one; one voxel more per axis is refused by the size check,
+    which runs before any CUDA call (the pointers below are never read)."""
+    import ctypes as C
+    from paper_2604_03748_gb300 import inputs as I, nsl
+    lib = nsl.load()
+    cam = nsl.camera(I.perspective_camera(16, 1, 16, 16))
+    fake = C.c_void_p(0x10000)
+    for n, dt in ((137, nsl.NSL_F32), (173, nsl.NSL_F16)):
+        g = nsl.nsl_grid_desc(n, n, n, dt, 1.0)
+        st = lib.nsl_guiding_map_noalloc(C.byref(g), fake, None, C.byref(cam), 2.0, None, fake, None)
+        assert st == nsl.NSL_ERR_INVALID_ARG, n
+        assert b"scratch" in lib.nsl_last_error()
+    # the limits themselves: 16 or 8 bytes per cell of (n+1)^2 (n+2) cells
+    lim = 40 << 20
+    assert 137 * 137 * 138 * 16 <= lim < 138 * 138 * 139 * 16
+    assert 173 * 173 * 174 * 8 <= lim < 174 * 174 * 175 * 8

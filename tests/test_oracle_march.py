@@ -231,7 +231,8 @@ def test_trilinear_exact_on_linear_field(orc):
 
 
 def test_mask_applied_per_voxel_before_interpolation(orc):
-    """R12: an obstacle voxel is zeroed before the trilinear blend, so the field
+    """The obstacle mask zeroes a voxel before the trilinear blend (the texture
+    holds the masked extinction; Sec. 4.2 samples it trilinearly), so the field
     is 0 at its centre, the full value at the neighbouring centres and the
     linear blend in between; sigma_scale multiplies the result."""
     n, c = 8, 0.4
