@@ -100,6 +100,12 @@ def _load():
                                      C.c_double, C.c_void_p]
     lib.nslo_net_forward_q8.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
                                         C.c_double, C.c_void_p]
+    lib.nslo_net_forward_prec.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int,
+                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.nslo_net_trace_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.nslo_net_trace_size.restype = C.c_int64
+    lib.nslo_round_bf16.argtypes = [C.c_double]
+    lib.nslo_round_bf16.restype = C.c_double
     lib.nslo_round_f16.argtypes = [C.c_double]
     lib.nslo_round_f16.restype = C.c_double
     lib.nslo_e4m3_rn.argtypes = [C.c_double]
@@ -232,6 +238,49 @@ def net_forward_q8(guide_planes, params_flat, c0, depth_scale):
     if rc != 0:
         raise ValueError(f"nslo_net_forward_q8 failed ({rc})")
     return out
+
+
+PREC_F64, PREC_F16, PREC_BF16, PREC_FP8, PREC_BF16X3 = 0, 1, 2, 3, 4
+# the network's 17 convolutions in order (nslo_net_forward_prec)
+NET_LAYERS = ("enc1a", "enc1b", "enc2a", "enc2b", "enc3a", "enc3b", "enc4a", "enc4b", "up3", "dec3a",
+              "dec3b", "up2", "dec2a", "dec2b", "up1", "dec1a", "dec1b")
+
+
+def net_forward_prec(guide_planes, params_flat, c0, depth_scale, prec, trace=False):
+    """The network with convolution l in precision form prec[l] (a sequence of
+    17 codes, or one code for every layer); see nslo_net_forward_prec.
+    Returns out [8,H,W], and with trace=True also the 17 stored layer outputs
+    as a list of [C,H_l,W_l] arrays."""
+    lib = _load()
+    g = np.ascontiguousarray(guide_planes, np.float64)
+    p = np.ascontiguousarray(params_flat, np.float64)
+    H, W = g.shape[1:]
+    codes = [int(prec)] * 17 if np.isscalar(prec) else [int(v) for v in prec]
+    if len(codes) != 17:
+        raise ValueError("prec needs 17 layer codes")
+    pr = np.asarray(codes, np.int32)
+    out = np.zeros((8, H, W), np.float64)
+    sizes = [int(lib.nslo_net_trace_size(int(c0), H, W, l)) for l in range(17)]
+    tr = np.zeros(sum(sizes), np.float64) if trace else None
+    rc = lib.nslo_net_forward_prec(_ptr(g), H, W, _ptr(p), p.size, int(c0), float(depth_scale), _ptr(pr),
+                                   _ptr(out), _ptr(tr) if trace else None)
+    if rc != 0:
+        raise ValueError(f"nslo_net_forward_prec failed ({rc})")
+    if not trace:
+        return out
+    mult = (1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 4, 2, 2, 2, 1, 1, 1)
+    lvl = (0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0)
+    layers, off = [], 0
+    for l in range(17):
+        shp = (mult[l] * int(c0), H >> lvl[l], W >> lvl[l])
+        layers.append(tr[off:off + sizes[l]].reshape(shp))
+        off += sizes[l]
+    return out, layers
+
+
+def round_bf16(x):
+    lib = _load()
+    return np.vectorize(lambda v: lib.nslo_round_bf16(float(v)), otypes=[np.float64])(x)
 
 
 def round_f16(x):

@@ -1028,6 +1028,206 @@ done:
 }
 
 /* ------------------------------------------------------------------------- */
+/* Per-layer precision forms of the network (no counterpart in the paper)    */
+/* ------------------------------------------------------------------------- */
+
+/* bfloat16 rounding (round to nearest, ties to even) of a finite double:
+ * 8 significand bits (7 stored), the binary32 exponent range (normal down to
+ * 2^-126, subnormal quantum 2^-133); magnitudes that round above the largest
+ * finite value (2 - 2^-7) 2^127 become infinite. */
+double nslo_round_bf16(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  const double a = fabs(x);
+  int e;
+  frexp(a, &e);            /* a in [2^(e-1), 2^e) */
+  int E = e - 1;
+  if (E < -126) E = -126;
+  const double q = ldexp(1.0, E - 7);
+  double r = rint(a / q) * q;
+  if (r > ldexp(2.0 - ldexp(1.0, -7), 127)) r = INFINITY;
+  return copysign(r, x);
+}
+
+/* Value an activation is stored as after a layer of form `prec`: binary16 for
+ * the FP16 form and for the FP8 form (whose activations stay binary16 between
+ * layers), bfloat16 for the BF16 form, binary32 for the split-BF16 form, the
+ * value itself for FP64. */
+static double store_as(int prec, double v) {
+  switch (prec) {
+    case NSLO_PREC_F16:
+    case NSLO_PREC_FP8: return nslo_round_f16(v);
+    case NSLO_PREC_BF16: return nslo_round_bf16(v);
+    case NSLO_PREC_BF16X3: return (double)(float)v;
+    default: return v;
+  }
+}
+
+/* Operand of a multiplication in a 16-bit form. */
+static double operand_as(int prec, double v) {
+  return prec == NSLO_PREC_F16 ? nslo_round_f16(v) : (prec == NSLO_PREC_BF16 ? nslo_round_bf16(v) : v);
+}
+
+/* One 3x3 (k = 3) or 2x2 stride-2 transposed (k = 2) convolution in form
+ * `prec`, weights and bias from the cursor, ReLU after the 3x3 ones:
+ *   F64          exact weights and inputs;
+ *   F16, BF16    weights and inputs rounded to the 16-bit type, the exact sum
+ *                of products plus the bias;
+ *   BF16X3       every weight and input split into a bfloat16 high part and
+ *                the bfloat16 rounding of the remainder, hi*hi + hi*lo +
+ *                lo*hi summed exactly (the lo*lo term dropped) plus the bias;
+ *   FP8          the scheme of conv3_q8 / convT_q8.
+ * The result is stored as store_as(prec). */
+static int conv_prec(cursor* cur, int prec, int k, const double* x, int cin, int H, int W, int cout,
+                     double* out) {
+  if (prec == NSLO_PREC_FP8)
+    return k == 3 ? conv3_q8(cur, x, cin, H, W, cout, out) : convT_q8(cur, x, cin, H, W, cout, out);
+  const int64_t nw = (int64_t)cout * cin * (k == 3 ? 9 : 4);
+  const double* w = take(cur, nw);
+  const double* b = take(cur, cout);
+  if (!w || !b) return 3;
+  const size_t P = (size_t)H * W, Pout = k == 3 ? P : 4 * P, nx = (size_t)cin * P;
+  double* xh = malloc(sizeof(double) * nx);
+  double* xl = malloc(sizeof(double) * nx);
+  double* wh = malloc(sizeof(double) * nw);
+  double* wl = malloc(sizeof(double) * nw);
+  double* t = malloc(sizeof(double) * cout * Pout);
+  if (!xh || !xl || !wh || !wl || !t) { free(xh); free(xl); free(wh); free(wl); free(t); return 2; }
+  const int split = prec == NSLO_PREC_BF16X3;
+  for (size_t i = 0; i < nx; ++i) {
+    xh[i] = split ? nslo_round_bf16(x[i]) : operand_as(prec, x[i]);
+    xl[i] = split ? nslo_round_bf16(x[i] - xh[i]) : 0.0;
+  }
+  for (int64_t i = 0; i < nw; ++i) {
+    wh[i] = split ? nslo_round_bf16(w[i]) : operand_as(prec, w[i]);
+    wl[i] = split ? nslo_round_bf16(w[i] - wh[i]) : 0.0;
+  }
+  if (k == 3) nslo_conv2d(xh, cin, H, W, wh, b, cout, 3, out);
+  else nslo_conv_transpose2x2(xh, cin, H, W, wh, b, cout, out);
+  if (split) {
+    if (k == 3) nslo_conv2d(xh, cin, H, W, wl, NULL, cout, 3, t);
+    else nslo_conv_transpose2x2(xh, cin, H, W, wl, NULL, cout, t);
+    for (size_t i = 0; i < (size_t)cout * Pout; ++i) out[i] += t[i];
+    if (k == 3) nslo_conv2d(xl, cin, H, W, wh, NULL, cout, 3, t);
+    else nslo_conv_transpose2x2(xl, cin, H, W, wh, NULL, cout, t);
+    for (size_t i = 0; i < (size_t)cout * Pout; ++i) out[i] += t[i];
+  }
+  for (size_t i = 0; i < (size_t)cout * Pout; ++i) {
+    const double v = (k == 3 && out[i] < 0.0) ? 0.0 : out[i];
+    out[i] = store_as(prec, v);
+  }
+  free(xh); free(xl); free(wh); free(wl); free(t);
+  return 0;
+}
+
+/* Element count of stored tensor l (0..16, network order) of an H x W image. */
+int64_t nslo_net_trace_size(int c0, int H, int W, int l) {
+  static const int cmul[17] = {1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 4, 2, 2, 2, 1, 1, 1};
+  static const int lvl[17] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 2, 1, 1, 1, 0, 0, 0};
+  if (l < 0 || l > 16) return 0;
+  return (int64_t)cmul[l] * c0 * (H >> lvl[l]) * (W >> lvl[l]);
+}
+
+/* The Sec. 4.3 generator with each of its 17 convolutions in its own
+ * precision form: prec[l] for l in network order (0 enc1a, 1 enc1b, 2 enc2a,
+ * 3 enc2b, 4 enc3a, 5 enc3b, 6 enc4a, 7 enc4b, 8 up3, 9 dec3a, 10 dec3b,
+ * 11 up2, 12 dec2a, 13 dec2b, 14 up1, 15 dec1a, 16 dec1b).  The first
+ * convolution (three guide channels) keeps exact weights and inputs whatever
+ * its form; its form sets only how its output is stored.  Max-pooling and the
+ * skip concatenation act on stored values.  The adapters run in binary64 on the
+ * stored feature map F.  trace (nullable): the 17 stored outputs one after
+ * another, each planar [C][H_l][W_l] (sizes from nslo_net_trace_size). */
+int nslo_net_forward_prec(const double* guide, int H, int W, const double* params, int64_t n_params,
+                          int c0, double depth_scale, const int* prec, double* out, double* trace) {
+  if (H % 8 || W % 8 || H <= 0 || W <= 0) return 1;
+  for (int l = 0; l < 17; ++l)
+    if (prec[l] < NSLO_PREC_F64 || prec[l] > NSLO_PREC_BF16X3) return 5;
+  cursor cur = {params, n_params};
+  const int c1 = c0, c2 = 2 * c0, c3 = 4 * c0, c4 = 8 * c0;
+  size_t P0 = (size_t)H * W, P1 = P0 / 4, P2 = P0 / 16, P3 = P0 / 64;
+  int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  double* x0 = malloc(sizeof(double) * 3 * P0);
+  double* a0 = malloc(sizeof(double) * c1 * P0);
+  double* s1 = malloc(sizeof(double) * c1 * P0);
+  double* p1 = malloc(sizeof(double) * c1 * P1);
+  double* a1 = malloc(sizeof(double) * c2 * P1);
+  double* s2 = malloc(sizeof(double) * c2 * P1);
+  double* p2 = malloc(sizeof(double) * c2 * P2);
+  double* a2 = malloc(sizeof(double) * c3 * P2);
+  double* s3 = malloc(sizeof(double) * c3 * P2);
+  double* p3 = malloc(sizeof(double) * c3 * P3);
+  double* a3 = malloc(sizeof(double) * c4 * P3);
+  double* bt = malloc(sizeof(double) * c4 * P3);
+  double* cat = malloc(sizeof(double) * 2 * c1 * P0 + sizeof(double) * c4 * P2);
+  double* d = malloc(sizeof(double) * c1 * P0 * 2 + sizeof(double) * c4 * P2);
+  double* F = malloc(sizeof(double) * c1 * P0);
+  double* z = malloc(sizeof(double) * c1 * P0);
+  double* tr = trace;
+  int rc = 0;
+  if (!x0 || !a0 || !s1 || !p1 || !a1 || !s2 || !p2 || !a2 || !s3 || !p3 || !a3 || !bt || !cat ||
+      !d || !F || !z) { rc = 2; goto done; }
+#define TRACE(buf, n)                                   \
+  do {                                                  \
+    if (tr) { memcpy(tr, (buf), sizeof(double) * (n)); tr += (n); } \
+  } while (0)
+
+  memcpy(x0, guide, sizeof(double) * 2 * P0);
+  for (size_t p = 0; p < P0; ++p) x0[2 * P0 + p] = guide[2 * P0 + p] * depth_scale;
+
+  /* first convolution: exact, then stored in its form */
+  if ((rc = conv3_relu(&cur, x0, 3, H, W, c1, a0))) goto done;
+  for (size_t i = 0; i < (size_t)c1 * P0; ++i) a0[i] = store_as(prec[0], a0[i]);
+  TRACE(a0, (size_t)c1 * P0);
+  /* encoder */
+  if ((rc = conv_prec(&cur, prec[1], 3, a0, c1, H, W, c1, s1))) goto done;
+  TRACE(s1, (size_t)c1 * P0);
+  nslo_maxpool2(s1, c1, H, W, p1);
+  if ((rc = conv_prec(&cur, prec[2], 3, p1, c1, H1, W1, c2, a1))) goto done;
+  TRACE(a1, (size_t)c2 * P1);
+  if ((rc = conv_prec(&cur, prec[3], 3, a1, c2, H1, W1, c2, s2))) goto done;
+  TRACE(s2, (size_t)c2 * P1);
+  nslo_maxpool2(s2, c2, H1, W1, p2);
+  if ((rc = conv_prec(&cur, prec[4], 3, p2, c2, H2, W2, c3, a2))) goto done;
+  TRACE(a2, (size_t)c3 * P2);
+  if ((rc = conv_prec(&cur, prec[5], 3, a2, c3, H2, W2, c3, s3))) goto done;
+  TRACE(s3, (size_t)c3 * P2);
+  nslo_maxpool2(s3, c3, H2, W2, p3);
+  if ((rc = conv_prec(&cur, prec[6], 3, p3, c3, H3, W3, c4, a3))) goto done;
+  TRACE(a3, (size_t)c4 * P3);
+  if ((rc = conv_prec(&cur, prec[7], 3, a3, c4, H3, W3, c4, bt))) goto done;
+  TRACE(bt, (size_t)c4 * P3);
+  /* decoder: upsampled first, skip second */
+  if ((rc = conv_prec(&cur, prec[8], 2, bt, c4, H3, W3, c3, cat))) goto done;
+  TRACE(cat, (size_t)c3 * P2);
+  memcpy(cat + (size_t)c3 * P2, s3, sizeof(double) * c3 * P2);
+  if ((rc = conv_prec(&cur, prec[9], 3, cat, 2 * c3, H2, W2, c3, d))) goto done;
+  TRACE(d, (size_t)c3 * P2);
+  if ((rc = conv_prec(&cur, prec[10], 3, d, c3, H2, W2, c3, a2))) goto done;
+  TRACE(a2, (size_t)c3 * P2);
+  if ((rc = conv_prec(&cur, prec[11], 2, a2, c3, H2, W2, c2, cat))) goto done;
+  TRACE(cat, (size_t)c2 * P1);
+  memcpy(cat + (size_t)c2 * P1, s2, sizeof(double) * c2 * P1);
+  if ((rc = conv_prec(&cur, prec[12], 3, cat, 2 * c2, H1, W1, c2, d))) goto done;
+  TRACE(d, (size_t)c2 * P1);
+  if ((rc = conv_prec(&cur, prec[13], 3, d, c2, H1, W1, c2, a1))) goto done;
+  TRACE(a1, (size_t)c2 * P1);
+  if ((rc = conv_prec(&cur, prec[14], 2, a1, c2, H1, W1, c1, cat))) goto done;
+  TRACE(cat, (size_t)c1 * P0);
+  memcpy(cat + (size_t)c1 * P0, s1, sizeof(double) * c1 * P0);
+  if ((rc = conv_prec(&cur, prec[15], 3, cat, 2 * c1, H, W, c1, d))) goto done;
+  TRACE(d, (size_t)c1 * P0);
+  if ((rc = conv_prec(&cur, prec[16], 3, d, c1, H, W, c1, F))) goto done;
+  TRACE(F, (size_t)c1 * P0);
+#undef TRACE
+  /* channel adapters, binary64, on the stored feature map */
+  if ((rc = adapters_forward(&cur, F, c1, H, W, z, out))) goto done;
+  if (cur.left != 0) rc = 4;
+done:
+  free(x0); free(a0); free(s1); free(p1); free(a1); free(s2); free(p2); free(a2); free(s3);
+  free(p3); free(a3); free(bt); free(cat); free(d); free(F); free(z);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Six-way shading (Sec. 3, directional interpolation)                        */
 /* ------------------------------------------------------------------------- */
 

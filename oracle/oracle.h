@@ -94,6 +94,24 @@ void nslo_q8_tensor(const double* x, size_t n, double* codes, float* deq);
 void nslo_q8_weights(const double* w, int cout, int count, int64_t so, int64_t sj, double* codes,
                      float* s);
 
+/* Per-layer precision forms of the network's 17 convolutions. */
+enum {
+  NSLO_PREC_F64 = 0,    /* exact */
+  NSLO_PREC_F16 = 1,    /* binary16 weights and activations, exact sums */
+  NSLO_PREC_BF16 = 2,   /* bfloat16 weights and activations, exact sums */
+  NSLO_PREC_FP8 = 3,    /* the FP8 E4M3 scheme of nslo_net_forward_q8 */
+  NSLO_PREC_BF16X3 = 4  /* bfloat16 hi/lo splits of weights and binary32
+                           activations, hi*hi + hi*lo + lo*hi */
+};
+/* The network with convolution l (network order, 0 = enc1a .. 16 = dec1b) in
+ * form prec[l]; the adapters in binary64 on the stored feature map.  trace
+ * (nullable) receives the 17 stored layer outputs, planar, one after another. */
+int nslo_net_forward_prec(const double* guide, int H, int W, const double* params,
+                          int64_t n_params, int c0, double depth_scale, const int* prec,
+                          double* out, double* trace);
+int64_t nslo_net_trace_size(int c0, int H, int W, int l);
+double nslo_round_bf16(double x);
+
 /* Six-way shading: rgba [4][H][W]. */
 int nslo_shade(const double* lightmaps, int H, int W, const nslo_camera* cam,
                const nslo_light* lights, int n_lights, double* rgba);
