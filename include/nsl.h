@@ -189,6 +189,24 @@ NSL_API nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const void
                                            float step_voxels, const nsl_march_opts* opts,
                                            float* guide_dev, void* stream);
 
+/* Roofline denominators measured on the current device (the paper has no
+ * counterpart; used by the benchmark).  Runs three short kernels on `stream`,
+ * each timed with CUDA events after a warm-up launch, and synchronises it;
+ * allocates and frees about 65 MB of scratch.
+ *   sms             multiprocessors of the device
+ *   fp32_tflops     FP32 FMA rate (eight independent fmaf chains per thread)
+ *   l1_gbps         L1 data path: warps reading 512 contiguous bytes (16 per
+ *                   lane) from a 16 KB region held in L1
+ *   l2_gather_gbps  16-byte loads at hashed positions of a 64 MiB buffer
+ *                   resident in L2 (a warp's lanes touch unrelated lines) */
+typedef struct {
+  int sms;
+  double fp32_tflops;
+  double l1_gbps;
+  double l2_gather_gbps;
+} nsl_peaks;
+NSL_API nsl_status nsl_measure_peaks(nsl_peaks* out, void* stream);
+
 /* Number of density evaluations the guide march of nsl_guiding_map makes for
  * this camera, step and options on the staged grid: view samples plus the
  * shadow samples of every view sample with non-zero density (Alg. 1).  Runs a
@@ -207,6 +225,30 @@ NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, f
  *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
                                  int precision, float* lightmaps_dev, void* stream);
+
+/* Diagnostic form of nsl_predict_lightmaps (the paper has no counterpart): the
+ * same network run, which also copies every convolution's stored output into
+ * trace_dev, so that each layer can be compared with an emulation of its
+ * arithmetic on the same input.  Tensor-core precisions only (NSL_PREC_BF16,
+ * NSL_PREC_F16, NSL_PREC_FP8; NSL_PREC_F32 returns NSL_ERR_UNSUPPORTED).
+ *   trace_dev     caller-owned device buffer, 16-byte aligned, of at least
+ *                 nsl_lightmap_trace_bytes(width, height) bytes; it receives
+ *                 the 17 stored tensors in network order (enc1a, enc1b,
+ *                 enc2a, enc2b, enc3a, enc3b, enc4a, enc4b, up3, dec3a, dec3b,
+ *                 up2, dec2a, dec2b, up1, dec1a, dec1b), back to back, each
+ *                 NHWC [H/2^l][W/2^l][C] with l its level (0 at full size) and
+ *                 C its channels, in the activation type: bfloat16 for
+ *                 NSL_PREC_BF16, binary16 for NSL_PREC_F16 and NSL_PREC_FP8
+ *                 (whose activations are binary16 between layers)
+ *   other arguments as for nsl_predict_lightmaps
+ * A smaller or unaligned trace buffer returns NSL_ERR_INVALID_ARG before any
+ * work is queued.  The copies are ordered on `stream` after each layer. */
+NSL_API nsl_status nsl_predict_lightmaps_trace(nsl_ctx* ctx, const float* guide_dev, int width,
+                                               int height, int precision, float* lightmaps_dev,
+                                               void* trace_dev, size_t trace_bytes, void* stream);
+/* Bytes of the trace of a width x height image: 144 activation values per
+ * pixel, two bytes each; 0 for a non-positive size. */
+NSL_API size_t nsl_lightmap_trace_bytes(int width, int height);
 
 /* Diagnostic of the failure detection (no paper counterpart).  Every wait of
  * the tensor-core kernels on an mbarrier is bounded (about 2 s); when one runs

@@ -104,6 +104,11 @@ def _load():
                                           C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.nslo_net_trace_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
     lib.nslo_net_trace_size.restype = C.c_int64
+    lib.nslo_conv_layer_prec.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                         C.c_void_p, C.c_int, C.c_void_p]
+    lib.nslo_store_as.argtypes = [C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+    lib.nslo_store_as.restype = None
+    lib.nslo_net_adapters.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p]
     lib.nslo_round_bf16.argtypes = [C.c_double]
     lib.nslo_round_bf16.restype = C.c_double
     lib.nslo_round_f16.argtypes = [C.c_double]
@@ -276,6 +281,45 @@ def net_forward_prec(guide_planes, params_flat, c0, depth_scale, prec, trace=Fal
         layers.append(tr[off:off + sizes[l]].reshape(shp))
         off += sizes[l]
     return out, layers
+
+
+def conv_layer_prec(prec, x, w, b, transposed=False):
+    """One convolution of the network in precision form `prec` (see
+    nslo_conv_layer_prec): x [cin,H,W]; w [cout,cin,3,3] (3x3 + ReLU) or, with
+    transposed=True, [cin,cout,2,2] (2x2 stride 2)."""
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    cin, H, W = x.shape
+    cout = w.shape[1] if transposed else w.shape[0]
+    out = np.zeros((cout, 2 * H, 2 * W) if transposed else (cout, H, W), np.float64)
+    rc = lib.nslo_conv_layer_prec(int(prec), 2 if transposed else 3, _ptr(x), cin, H, W, _ptr(w), _ptr(b),
+                                  cout, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_conv_layer_prec failed ({rc})")
+    return out
+
+
+def store_as(prec, x):
+    """The values x are stored as after a layer of form `prec`."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(x)
+    _load().nslo_store_as(int(prec), _ptr(x), x.size, _ptr(out))
+    return out
+
+
+def net_adapters(F, adapter_params, c0):
+    """The four adapters and their heads on a feature map F [c0,H,W]: [8,H,W]."""
+    lib = _load()
+    F = np.ascontiguousarray(F, np.float64)
+    p = np.ascontiguousarray(adapter_params, np.float64)
+    _, H, W = F.shape
+    out = np.zeros((8, H, W), np.float64)
+    rc = lib.nslo_net_adapters(_ptr(F), int(c0), H, W, _ptr(p), p.size, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"nslo_net_adapters failed ({rc})")
+    return out
 
 
 def round_bf16(x):

@@ -1119,6 +1119,42 @@ static int conv_prec(cursor* cur, int prec, int k, const double* x, int cin, int
   return 0;
 }
 
+/* One convolution of the network in form `prec` with explicit parameters
+ * (conv_prec): k = 3 is a 3x3 convolution followed by ReLU, w [cout][cin][3][3],
+ * out [cout][H][W]; k = 2 a 2x2 stride-2 transposed convolution, w
+ * [cin][cout][2][2], out [cout][2H][2W]. */
+int nslo_conv_layer_prec(int prec, int k, const double* x, int cin, int H, int W, const double* w,
+                         const double* b, int cout, double* out) {
+  if ((k != 2 && k != 3) || prec < NSLO_PREC_F64 || prec > NSLO_PREC_BF16X3) return 1;
+  const int64_t nw = (int64_t)cout * cin * (k == 3 ? 9 : 4);
+  double* pb = malloc(sizeof(double) * (size_t)(nw + cout));
+  if (!pb) return 2;
+  memcpy(pb, w, sizeof(double) * (size_t)nw);
+  memcpy(pb + nw, b, sizeof(double) * (size_t)cout);
+  cursor cur = {pb, nw + cout};
+  const int rc = conv_prec(&cur, prec, k, x, cin, H, W, cout, out);
+  free(pb);
+  return rc;
+}
+
+/* out[i] = the value x[i] is stored as after a layer of form prec. */
+void nslo_store_as(int prec, const double* x, size_t n, double* out) {
+  for (size_t i = 0; i < n; ++i) out[i] = store_as(prec, x[i]);
+}
+
+/* The four channel adapters and their heads on a feature map F [c0][H][W],
+ * binary64 (adapters_forward); params: the adapters' part of the blob. */
+int nslo_net_adapters(const double* F, int c0, int H, int W, const double* params, int64_t n_params,
+                      double* out) {
+  cursor cur = {params, n_params};
+  double* z = malloc(sizeof(double) * (size_t)c0 * H * W);
+  if (!z) return 2;
+  int rc = adapters_forward(&cur, F, c0, H, W, z, out);
+  if (!rc && cur.left != 0) rc = 4;
+  free(z);
+  return rc;
+}
+
 /* Element count of stored tensor l (0..16, network order) of an H x W image. */
 int64_t nslo_net_trace_size(int c0, int H, int W, int l) {
   static const int cmul[17] = {1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 4, 2, 2, 2, 1, 1, 1};

@@ -110,6 +110,14 @@ int nslo_net_forward_prec(const double* guide, int H, int W, const double* param
                           int64_t n_params, int c0, double depth_scale, const int* prec,
                           double* out, double* trace);
 int64_t nslo_net_trace_size(int c0, int H, int W, int l);
+/* One convolution in form prec with explicit weights (k = 3: 3x3 + ReLU; k = 2:
+ * 2x2 stride-2 transposed), and the storage rounding of a form. */
+int nslo_conv_layer_prec(int prec, int k, const double* x, int cin, int H, int W, const double* w,
+                         const double* b, int cout, double* out);
+void nslo_store_as(int prec, const double* x, size_t n, double* out);
+/* The adapters and heads alone on a feature map F [c0][H][W]. */
+int nslo_net_adapters(const double* F, int c0, int H, int W, const double* params, int64_t n_params,
+                      double* out);
 double nslo_round_bf16(double x);
 
 /* Six-way shading: rgba [4][H][W]. */

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
 #pragma unroll
         for (int y = 0; y < kTH; ++y) {
           if (px < im.W && y0 + y < im.H) {
-            __align__(4) TA o[2] = {fromf<TA>(gv[0][y]), fromf<TA>(gv[1][y])};
+            __align__(4) __half o[2] = {__float2half_rn(gv[0][y]), __float2half_rn(gv[1][y])};
             *reinterpret_cast<uint32_t*>(im.x1 + ((size_t)(y0 + y) * im.W + px) * (4 * C) + a * C + j0) =
                 *reinterpret_cast<const uint32_t*>(o);
           }
@@ -413,9 +413,9 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
       float xv[4 * C];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const TA* h = reinterpret_cast<const TA*>(&rx[q]);
+        const __half* h = reinterpret_cast<const __half*>(&rx[q]);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) xv[8 * q + e] = tof<TA>(h[e]) * att[8 * q + e];
+        for (int e = 0; e < 8; ++e) xv[8 * q + e] = __half2float(h[e]) * att[8 * q + e];
       }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -630,11 +630,11 @@ cudaError_t adapters_tc_run_group(const AdapterTcWeights* w, const AdapterParamS
   }
   G.tile_start[n] = tiles;
   G.px_start[n] = blocks;
-  const int g1 = tiles < kNumSMs * occ1 ? tiles : kNumSMs * occ1;
+  const int g1 = tiles < num_sms() * occ1 ? tiles : num_sms() * occ1;
   cudaError_t e = launch_pdl(adapters_p1_tc<TA>, dim3(g1), dim3(kP1Threads), (size_t)kP1Smem, s, G, w->dev, err);
   if (e != cudaSuccess) return e;
   if ((e = adapters_reduce_only_group<TA>(prm, imgs, n, s)) != cudaSuccess) return e;
-  const int g2 = blocks < kNumSMs * occ2 ? blocks : kNumSMs * occ2;
+  const int g2 = blocks < num_sms() * occ2 ? blocks : num_sms() * occ2;
   return launch_pdl(adapters_p2_tc<TA>, dim3(g2), dim3(128), (size_t)kP2Smem, s, G, w->dev, err);
 }
 

@@ -14,6 +14,18 @@ namespace nsl {
 
 static thread_local char g_err[512] = "";
 
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static int cached[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+  int v = __atomic_load_n(&cached[dev], __ATOMIC_ACQUIRE);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+  __atomic_store_n(&cached[dev], v, __ATOMIC_RELEASE);
+  return v;
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -492,14 +504,14 @@ nsl_status nsl_guide_sample_count(nsl_ctx* c, const nsl_camera* cam, float step,
   return NSL_OK;
 }
 
-nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int height,
-                                 int precision, float* lm, void* stream) {
-  if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: ctx is NULL");
-  if (!guide || !lm) return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: NULL buffer");
+static nsl_status predict(nsl_ctx* c, const float* guide, int width, int height, int precision,
+                          float* lm, uint8_t* trace, void* stream, const char* fn) {
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+  if (!guide || !lm) return fail(NSL_ERR_INVALID_ARG, "%s: NULL buffer", fn);
   if (!aligned16(guide) || !aligned16(lm))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: buffers must be 16-byte aligned");
+    return fail(NSL_ERR_INVALID_ARG, "%s: buffers must be 16-byte aligned", fn);
   if (width < 8 || height < 8 || width % 8 || height % 8 || width > c->max_w || height > c->max_h)
-    return fail(NSL_ERR_INVALID_ARG, "nsl_predict_lightmaps: bad size %dx%d", width, height);
+    return fail(NSL_ERR_INVALID_ARG, "%s: bad size %dx%d", fn, width, height);
   NetImage img{guide, lm, height, width,
                (float)(1.0 / std::sqrt((double)c->grid.nx * c->grid.nx +
                                        (double)c->grid.ny * c->grid.ny +
@@ -510,11 +522,12 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
   if (c->err_host && *reinterpret_cast<volatile unsigned int*>(c->err_host) != 0) {
     unsigned int code = *c->err_host;
     *c->err_host = 0;
-    return fail(NSL_ERR_TIMEOUT, "nsl_predict_lightmaps: an earlier tensor-core launch timed out "
-                "waiting on an mbarrier (code 0x%x)", code);
+    return fail(NSL_ERR_TIMEOUT, "%s: an earlier tensor-core launch timed out "
+                "waiting on an mbarrier (code 0x%x)", fn, code);
   }
   switch (precision) {
     case NSL_PREC_F32:
+      if (trace) return fail(NSL_ERR_UNSUPPORTED, "%s: no trace of the FP32 network", fn);
       e = net_f32_forward(c->wf32, img, c->ws, c->ws_bytes, s);
       break;
     case NSL_PREC_BF16:
@@ -525,14 +538,34 @@ nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int 
         c->wtc[elem] = net_tc_create(c->params.data(), c->layout, elem, &e);
         if (!c->wtc[elem]) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");
       }
-      e = net_tc_forward(c->wtc[elem], c->wf32, img, c->ws, c->ws_bytes, c->err_dev, s);
+      e = net_tc_forward(c->wtc[elem], c->wf32, img, c->ws, c->ws_bytes, c->err_dev, s, trace);
       break;
     }
     default:
-      return fail(NSL_ERR_UNSUPPORTED, "nsl_predict_lightmaps: precision %d not built", precision);
+      return fail(NSL_ERR_UNSUPPORTED, "%s: precision %d not built", fn, precision);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "nsl_predict_lightmaps");
+  if (e != cudaSuccess) return cuda_fail(e, fn);
   return NSL_OK;
+}
+
+nsl_status nsl_predict_lightmaps(nsl_ctx* c, const float* guide, int width, int height,
+                                 int precision, float* lm, void* stream) {
+  return predict(c, guide, width, height, precision, lm, nullptr, stream, "nsl_predict_lightmaps");
+}
+
+size_t nsl_lightmap_trace_bytes(int width, int height) {
+  return width > 0 && height > 0 ? net_tc_trace_bytes(width, height) : 0;
+}
+
+nsl_status nsl_predict_lightmaps_trace(nsl_ctx* c, const float* guide, int width, int height,
+                                       int precision, float* lm, void* trace, size_t trace_bytes,
+                                       void* stream) {
+  static const char* fn = "nsl_predict_lightmaps_trace";
+  if (!trace || !aligned16(trace)) return fail(NSL_ERR_INVALID_ARG, "%s: trace buffer NULL or unaligned", fn);
+  if (width > 0 && height > 0 && trace_bytes < net_tc_trace_bytes(width, height))
+    return fail(NSL_ERR_INVALID_ARG, "%s: trace buffer of %zu bytes, needs %zu", fn, trace_bytes,
+                net_tc_trace_bytes(width, height));
+  return predict(c, guide, width, height, precision, lm, static_cast<uint8_t*>(trace), stream, fn);
 }
 
 nsl_status nsl_selftest_wait_timeout(nsl_ctx* c, void* stream) {

@@ -257,7 +257,7 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
   if (b->seg_blocks_per_sm > 0 && b->seg_blocks_per_sm < per_sm) per_sm = b->seg_blocks_per_sm;
   e = launch_march_segmented_batch(b->dev->march, b->dev->tile_starts, b->dev->item_starts,
                                    b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
-                                   per_sm * kNumSMs, b->counter, s);
+                                   per_sm * num_sms(), b->counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: march");
   const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
   if (!b->wtc[elem]) {

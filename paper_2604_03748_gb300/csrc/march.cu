@@ -630,7 +630,7 @@ static int resident_blocks(K kernel) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kMarchThreads, 0) != cudaSuccess || occ < 1)
     occ = 1;
-  return occ * kNumSMs;
+  return occ * num_sms();
 }
 
 template <bool kBatch, bool kCount>
@@ -820,7 +820,7 @@ cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int*
 }
 
 int march_segment_blocks_max() {
-  static const int occ = resident_blocks(march_segment_batch_kernel) / kNumSMs;
+  static const int occ = resident_blocks(march_segment_batch_kernel) / num_sms();
   return occ;
 }
 
@@ -929,7 +929,7 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
                                 int ny, int nz, float scale, float* staged, cudaStream_t s) {
   const size_t n = stage_units(nx, ny, nz);
   int blocks = (int)((n + 255) / 256);
-  if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
   if (blocks < 1) blocks = 1;
   if (dtype == NSL_F16)
     return launch_pdl(stage_kernel<__half>, dim3(blocks), dim3(256), 0, s,
@@ -981,7 +981,7 @@ cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask,
   static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
   const size_t n = stage_units(nx, ny, nz);
   int blocks = (int)((n + 255) / 256);
-  if (blocks > kNumSMs * 16) blocks = kNumSMs * 16;
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
   if (blocks < 1) blocks = 1;
   return launch_pdl(stage_half_kernel, dim3(blocks), dim3(256), 0, s, density, mask, nx, ny, nz,
                     reinterpret_cast<uint2*>(staged));
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(256) transmittance_volume_kernel(MarchPlume P,
 cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s) {
   const size_t n = (size_t)p.nx * p.ny * p.nz;
   int blocks = (int)((n + 255) / 256);
-  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   if (p.staged_half)
     return launch_pdl(transmittance_volume_kernel<GridH>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
   return launch_pdl(transmittance_volume_kernel<Grid>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
@@ -1057,7 +1057,7 @@ cudaError_t launch_shade(const ShadeArgs& a, cudaStream_t s) {
   size_t P4 = (size_t)a.W * a.H / 4;
   if (P4 == 0) return cudaSuccess;
   int blocks = (int)((P4 + 255) / 256);
-  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   return launch_pdl(shade_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
 

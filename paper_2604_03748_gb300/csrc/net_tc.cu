@@ -1086,10 +1086,10 @@ cudaError_t run_conv(const NetTcWeights* w, int l, int n, const T* const* ins, c
   // when there are that many; per-SM residency is capped by the tunable
   // CTAs-per-SM
   const int per_sm = L.per_sm < g_conv_ctas_per_sm ? L.per_sm : g_conv_ctas_per_sm;
-  int grid = kNumSMs * per_sm / (COUT / NT);
+  int grid = num_sms() * per_sm / (COUT / NT);
   if (grid > (ntiles + NSL_CONV_MIN_TILES - 1) / NSL_CONV_MIN_TILES)
     grid = (ntiles + NSL_CONV_MIN_TILES - 1) / NSL_CONV_MIN_TILES;
-  if (grid < kNumSMs / (COUT / NT)) grid = kNumSMs / (COUT / NT);
+  if (grid < num_sms() / (COUT / NT)) grid = num_sms() / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
   return launch_pdl(conv3x3_tc_kernel<T, CIN, COUT, NT, MODE, Q8>, dim3(grid, COUT / NT), dim3(128),
@@ -1119,15 +1119,15 @@ cudaError_t run_convT(const NetTcWeights* w, int n, const T* const* ins, T* cons
   a.bias = w->up_b[LAYER];
   a.wscale = w->up_s[LAYER];
   a.err = err;
-  int grid = (kNumSMs * L.per_sm + NS - 1) / NS;
+  int grid = (num_sms() * L.per_sm + NS - 1) / NS;
   if (grid > ntiles) grid = ntiles;
   return launch_pdl(convT_tc_kernel<T, CIN, COUT, Q8, NS>, dim3(grid, NS), dim3(128), (size_t)L.smem, s, a);
 }
 
 template <typename T, bool Q8>
 cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs,
-                    void* const* ws, int n, unsigned int* err, cudaStream_t s) {
-  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+                    void* const* ws, int n, unsigned int* err, cudaStream_t s, uint8_t* trace) {
+  if (n < 1 || n > kMaxGroup || (trace && n != 1)) return cudaErrorInvalidValue;
   TcBuffers<T> B[kMaxGroup];
   int Hs[4][kMaxGroup], Ws[4][kMaxGroup];
   for (int k = 0; k < n; ++k) {
@@ -1156,32 +1156,63 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
     m.out = io;
     return m;
   };
+  // diagnostic trace (one image): after each layer, a copy of its stored
+  // output (NHWC, the activation type) appended to `trace`
+  const size_t P0 = (size_t)imgs[0].H * imgs[0].W;
+  size_t toff = 0;
+  auto trace_copy = [&](const T* buf, int ch, int lv) -> cudaError_t {
+    if (!trace) return cudaSuccess;
+    const size_t bytes = (P0 >> (2 * lv)) * (size_t)ch * sizeof(T);
+    cudaError_t ce = cudaMemcpyAsync(trace + toff, buf, bytes, cudaMemcpyDeviceToDevice, s);
+    toff += bytes;
+    return ce;
+  };
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
 #define SET(IN, SKIP, OUT) for (int k = 0; k < n; ++k) { in[k] = B[k].IN; sk[k] = SKIP; out[k] = B[k].OUT; }
+#define TRACE(BUF, CH, LV) TRY(trace_copy(B[0].BUF, CH, LV))
   for (int k = 0; k < n; ++k) out[k] = B[k].fa;
   float* first_amax[kMaxGroup];
   for (int k = 0; k < n; ++k) first_amax[k] = Q8 ? amax + (size_t)k * kAmaxSlots : nullptr;
   TRY(simt_first_conv_group<T>(wf, imgs, out, Q8 ? first_amax : nullptr, n, s));
+  TRACE(fa, 16, 0);
   SET(fa, nullptr, s1);  TRY((run_conv<T, 16, 16, TC_PLAIN, Q8>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], slots(0, -1, 1), err, s)));
+  TRACE(s1, 16, 0);
   SET(s1, nullptr, l1a); TRY((run_conv<T, 16, 32, TC_POOL, Q8>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], slots(1, -1, 2), err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, nullptr, s2); TRY((run_conv<T, 32, 32, TC_PLAIN, Q8>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], slots(2, -1, 3), err, s)));
+  TRACE(s2, 32, 1);
   SET(s2, nullptr, l2a); TRY((run_conv<T, 32, 64, TC_POOL, Q8>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], slots(3, -1, 4), err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, nullptr, s3); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], slots(4, -1, 5), err, s)));
+  TRACE(s3, 64, 2);
   SET(s3, nullptr, l3a); TRY((run_conv<T, 64, 128, TC_POOL, Q8>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], slots(5, -1, 6), err, s)));
+  TRACE(l3a, 128, 3);
   SET(l3a, nullptr, l3b); TRY((run_conv<T, 128, 128, TC_PLAIN, Q8>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], slots(6, -1, 7), err, s)));
+  TRACE(l3b, 128, 3);
   SET(l3b, nullptr, l2a); TRY((run_convT<T, 128, 64, Q8, 0>(w, n, in, out, Hs[3], Ws[3], slots(7, -1, 14), err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, B[k].s3, l2b); TRY((run_conv<T, 128, 64, TC_CONCAT, Q8>(w, 8, n, in, sk, out, Hs[2], Ws[2], slots(14, 5, 8), err, s)));
+  TRACE(l2b, 64, 2);
   SET(l2b, nullptr, l2a); TRY((run_conv<T, 64, 64, TC_PLAIN, Q8>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], slots(8, -1, 9), err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, nullptr, l1a); TRY((run_convT<T, 64, 32, Q8, 1>(w, n, in, out, Hs[2], Ws[2], slots(9, -1, 15), err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, B[k].s2, l1b); TRY((run_conv<T, 64, 32, TC_CONCAT, Q8>(w, 10, n, in, sk, out, Hs[1], Ws[1], slots(15, 3, 10), err, s)));
+  TRACE(l1b, 32, 1);
   SET(l1b, nullptr, l1a); TRY((run_conv<T, 32, 32, TC_PLAIN, Q8>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], slots(10, -1, 11), err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, nullptr, fa); TRY((run_convT<T, 32, 16, Q8, 2>(w, n, in, out, Hs[1], Ws[1], slots(11, -1, 16), err, s)));
+  TRACE(fa, 16, 0);
   SET(fa, B[k].s1, fb);  TRY((run_conv<T, 32, 16, TC_CONCAT, Q8>(w, 12, n, in, sk, out, Hs[0], Ws[0], slots(16, 1, 12), err, s)));
+  TRACE(fb, 16, 0);
   SET(fb, nullptr, fa);  TRY((run_conv<T, 16, 16, TC_PLAIN, Q8>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], slots(12, -1, 13), err, s)));
+  TRACE(fa, 16, 0);
   AdapterImg<T> ai[kMaxGroup];
   for (int k = 0; k < n; ++k)
-    ai[k] = AdapterImg<T>{B[k].fa, B[k].x1, B[k].partial, B[k].att, imgs[k].out, imgs[k].H, imgs[k].W};
+    ai[k] = AdapterImg<T>{B[k].fa, reinterpret_cast<__half*>(B[k].x1), B[k].partial, B[k].att, imgs[k].out,
+                          imgs[k].H, imgs[k].W};
   TRY(adapters_tc_run_group<T>(w->ad, net_f32_adapter_params(wf), ai, n, err, s));
+#undef TRACE
 #undef SET
 #undef TRY
   return cudaSuccess;
@@ -1194,18 +1225,27 @@ size_t net_tc_workspace_bytes(int max_w, int max_h) {
 }
 
 cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
-                           void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s) {
+                           void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s,
+                           uint8_t* trace) {
   if (net_tc_workspace_bytes(img.W, img.H) > ws_bytes) return cudaErrorInvalidValue;
   void* ws[1] = {workspace};
-  return net_tc_forward_group(w, wf, &img, ws, 1, err, s);
+  if (w->elem == 2) return forward<__half, true>(w, wf, &img, ws, 1, err, s, trace);
+  if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, &img, ws, 1, err, s, trace);
+  return forward<__half, false>(w, wf, &img, ws, 1, err, s, trace);
+}
+
+size_t net_tc_trace_bytes(int width, int height) {
+  // 144 activation values per pixel of the full-resolution image (the 17
+  // stored tensors), two bytes each
+  return (size_t)width * height * 144 * 2;
 }
 
 cudaError_t net_tc_forward_group(const NetTcWeights* w, const NetF32Weights* wf,
                                  const NetImage* imgs, void* const* ws, int n, unsigned int* err,
                                  cudaStream_t s) {
-  if (w->elem == 2) return forward<__half, true>(w, wf, imgs, ws, n, err, s);
-  if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, imgs, ws, n, err, s);
-  return forward<__half, false>(w, wf, imgs, ws, n, err, s);
+  if (w->elem == 2) return forward<__half, true>(w, wf, imgs, ws, n, err, s, nullptr);
+  if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, imgs, ws, n, err, s, nullptr);
+  return forward<__half, false>(w, wf, imgs, ws, n, err, s, nullptr);
 }
 
 void net_tc_set_ctas_per_sm(int v) { g_conv_ctas_per_sm = v < 1 ? 1 : (v > 4 ? 4 : v); }

@@ -46,7 +46,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 namespace nsl {
 
-constexpr int kNumSMs = 152;
+// Streaming multiprocessors of the current device
+// (cudaDevAttrMultiProcessorCount; 152 on GB300), looked up once per device.
+int num_sms();
 constexpr int kMaxGroup = 64;   // images per grouped network launch / plumes per batch launch
 
 // Error recording (thread-local message, see nsl_last_error).
@@ -301,7 +303,8 @@ cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float*
 template <typename TA>
 struct AdapterImg {
   const TA* F;
-  TA* x1;
+  __half* x1;       // the gated depthwise output: binary16 whatever F's type
+                    // (it is LayerNorm-scaled, well inside the binary16 range)
   float* partial;   // per-tile channel sums of this image
   float* att;       // 64 attention values of this image
   float* out;       // [8][H][W]
@@ -336,9 +339,12 @@ NetTcWeights* net_tc_create(const float* host_params, const NetLayout& L, int el
                             cudaError_t* err);
 void net_tc_destroy(NetTcWeights* w);
 size_t net_tc_workspace_bytes(int max_w, int max_h);
+// trace (nullable): after each of the 17 convolutions a copy of its stored
+// output (NHWC, 16-bit activation type) is appended; net_tc_trace_bytes bytes
 cudaError_t net_tc_forward(const NetTcWeights* wt, const NetF32Weights* wf, const NetImage& img,
                            void* workspace, size_t ws_bytes, unsigned int* err_flag,
-                           cudaStream_t s);
+                           cudaStream_t s, uint8_t* trace = nullptr);
+size_t net_tc_trace_bytes(int width, int height);
 // grouped forward: n <= kMaxGroup images, image k uses workspace ws[k] of at
 // least net_tc_workspace_bytes(W_k, H_k) bytes; every layer is one launch.
 cudaError_t net_tc_forward_group(const NetTcWeights* wt, const NetF32Weights* wf,

@@ -59,7 +59,7 @@ extern "C" nsl_status nsl_pack_lightmaps(const float* lightmaps_dev, int width, 
     return fail(NSL_ERR_INVALID_ARG, "%s: buffers must be 16-byte aligned", fn);
   const size_t P = (size_t)width * height;
   int blocks = (int)((P + 255) / 256);
-  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (format == NSL_TEX_RGBA8)

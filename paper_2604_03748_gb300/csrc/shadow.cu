@@ -37,10 +37,19 @@ __device__ __forceinline__ bool voxel_entry(const float o[3], const float w[3], 
   return true;
 }
 
-// One thread per texel: the line through the texel centre along w is clipped
-// to the grid box and walked voxel by voxel (each boundary crossing recomputed
-// from o, no accumulated steps); the first occupied voxel that the exact slab
-// test confirms gives the depth, +infinity when there is none.
+// One thread per texel: the depth is the smallest slab-test entry parameter
+// over every occupied voxel the line through the texel centre (along w) meets,
+// the same minimum a brute force over all occupied voxels takes.  The line is
+// walked voxel by voxel (each boundary crossing recomputed from o, no
+// accumulated steps), and at every visited voxel the 27 voxels of its 3x3x3
+// neighbourhood are tested: a voxel that the binary32 slab test reports as met
+// lies within rounding of the line, so it shares at least a corner with a
+// voxel the walk visits.  The walk is clipped to the box grown by half a voxel
+// (a line grazing the box still visits the voxels beside it) and may visit the
+// layer of voxels just outside the grid, whose neighbours inside are tested.
+// It stops once the entry parameter of the visited voxel exceeds the best
+// depth by 4: any voxel met later is entered at least 2*sqrt(3) after the
+// entry of a visited voxel it touches.  +infinity when no occupied voxel is met.
 __global__ void __launch_bounds__(256) shadow_map_kernel(const uint8_t* __restrict__ mask, int nx, int ny,
                                                          int nz, LightFrame L, int R, float* __restrict__ out) {
   pdl_wait();
@@ -55,26 +64,27 @@ __global__ void __launch_bounds__(256) shadow_map_kernel(const uint8_t* __restri
 #pragma unroll
     for (int k = 0; k < 3; ++k) o[k] = __fadd_rn(__fadd_rn(L.c[k], __fmul_rn(a, L.e1[k])), __fmul_rn(b, L.e2[k]));
     float best = INFINITY;
-    // clip the line to the box [0, n]
+    // clip the line to the box [-1/2, n + 1/2]
     float t0 = -INFINITY, t1 = INFINITY;
     bool hit = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+      const float lo = -0.5f, hi = __fadd_rn((float)n3[k], 0.5f);
       if (L.w[k] != 0.f) {
-        const float ta = __fdiv_rn(__fsub_rn(0.f, o[k]), L.w[k]);
-        const float tb = __fdiv_rn(__fsub_rn((float)n3[k], o[k]), L.w[k]);
+        const float ta = __fdiv_rn(__fsub_rn(lo, o[k]), L.w[k]);
+        const float tb = __fdiv_rn(__fsub_rn(hi, o[k]), L.w[k]);
         t0 = fmaxf(t0, fminf(ta, tb));
         t1 = fminf(t1, fmaxf(ta, tb));
-      } else if (o[k] < 0.f || o[k] > (float)n3[k]) {
+      } else if (o[k] < lo || o[k] > hi) {
         hit = false;
       }
     }
     if (hit && t0 <= t1) {
-      // voxel, step and next boundary parameter per axis, in scalars (no
-      // dynamically indexed arrays)
+      // voxel index in [-1, n], step and next boundary parameter per axis, in
+      // scalars (no dynamically indexed arrays)
       auto start = [&](int k, int& v, int& st, float& tm) {
         const float pk = __fadd_rn(o[k], __fmul_rn(t0, L.w[k]));
-        v = min(max((int)floorf(pk), 0), n3[k] - 1);
+        v = min(max((int)floorf(pk), -1), n3[k]);
         st = L.w[k] > 0.f ? 1 : (L.w[k] < 0.f ? -1 : 0);
         tm = st == 0 ? INFINITY : __fdiv_rn(__fsub_rn((float)(v + (st > 0 ? 1 : 0)), o[k]), L.w[k]);
       };
@@ -83,26 +93,41 @@ __global__ void __launch_bounds__(256) shadow_map_kernel(const uint8_t* __restri
       start(0, vx, sx, tx);
       start(1, vy, sy, ty);
       start(2, vz, sz, tz);
-      for (int guard = nx + ny + nz + 3; guard > 0; --guard) {
-        float te;
-        if (__ldg(mask + ((size_t)vz * ny + vy) * nx + vx) && voxel_entry(o, L.w, vx, vy, vz, &te)) {
-          best = te;
-          break;
+      float tcur = t0;
+      for (int guard = nx + ny + nz + 9; guard > 0; --guard) {
+        if (tcur > __fadd_rn(best, 4.f)) break;
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int kz = vz + dz;
+          if (kz < 0 || kz >= nz) continue;
+          for (int dy = -1; dy <= 1; ++dy) {
+            const int ky = vy + dy;
+            if (ky < 0 || ky >= ny) continue;
+            const uint8_t* row = mask + ((size_t)kz * ny + ky) * nx;
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int kx = vx + dx;
+              float te;
+              if (kx >= 0 && kx < nx && __ldg(row + kx) && voxel_entry(o, L.w, kx, ky, kz, &te) && te < best)
+                best = te;
+            }
+          }
         }
         if (tx <= ty && tx <= tz) {
           if (!(tx <= t1)) break;
+          tcur = tx;
           vx += sx;
-          if (vx < 0 || vx >= nx) break;
+          if (vx < -1 || vx > nx) break;
           tx = __fdiv_rn(__fsub_rn((float)(vx + (sx > 0 ? 1 : 0)), o[0]), L.w[0]);
         } else if (ty <= tz) {
           if (!(ty <= t1)) break;
+          tcur = ty;
           vy += sy;
-          if (vy < 0 || vy >= ny) break;
+          if (vy < -1 || vy > ny) break;
           ty = __fdiv_rn(__fsub_rn((float)(vy + (sy > 0 ? 1 : 0)), o[1]), L.w[1]);
         } else {
           if (!(tz <= t1)) break;
+          tcur = tz;
           vz += sz;
-          if (vz < 0 || vz >= nz) break;
+          if (vz < -1 || vz > nz) break;
           tz = __fdiv_rn(__fsub_rn((float)(vz + (sz > 0 ? 1 : 0)), o[2]), L.w[2]);
         }
       }
@@ -239,14 +264,14 @@ bool light_frame_from(const float dir[3], int nx, int ny, int nz, LightFrame* L)
 cudaError_t launch_shadow_map(const uint8_t* mask, int nx, int ny, int nz, const LightFrame& L, int R,
                               float* out, cudaStream_t s) {
   int blocks = (R * R + 255) / 256;
-  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   return launch_pdl(shadow_map_kernel, dim3(blocks), dim3(256), 0, s, mask, nx, ny, nz, L, R, out);
 }
 
 cudaError_t launch_shade_shadowed(const ShadowShadeArgs& a, cudaStream_t s) {
   const size_t P = (size_t)a.W * a.H;
   int blocks = (int)((P + 255) / 256);
-  if (blocks > kNumSMs * 8) blocks = kNumSMs * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   return launch_pdl(shade_shadowed_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
 

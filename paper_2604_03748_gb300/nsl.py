@@ -31,7 +31,8 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_server_add_plume", "nsl_server_remove_plume", "nsl_server_submit", "nsl_server_wait",
            "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
            "nsl_server_reset_stats", "nsl_pack_lightmaps", "nsl_obstacle_shadow_map",
-           "nsl_shade_shadowed", "nsl_selftest_wait_timeout"]
+           "nsl_shade_shadowed", "nsl_selftest_wait_timeout", "nsl_predict_lightmaps_trace",
+           "nsl_lightmap_trace_bytes", "nsl_measure_peaks"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -80,6 +81,11 @@ class nsl_server_stats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class nsl_peaks(C.Structure):
+    _fields_ = [("sms", C.c_int), ("fp32_tflops", C.c_double), ("l1_gbps", C.c_double),
+                ("l2_gather_gbps", C.c_double)]
+
+
 class NslError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} [status {status}]")
@@ -111,6 +117,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_guide_sample_count.argtypes = [vp, C.POINTER(nsl_camera), f, C.POINTER(nsl_march_opts),
                                            C.POINTER(C.c_ulonglong), vp]
     lib.nsl_predict_lightmaps.argtypes = [vp, vp, i, i, i, vp, vp]
+    lib.nsl_predict_lightmaps_trace.argtypes = [vp, vp, i, i, i, vp, vp, C.c_size_t, vp]
+    lib.nsl_predict_lightmaps_trace.restype = C.c_int
+    lib.nsl_measure_peaks.argtypes = [C.POINTER(nsl_peaks), vp]
+    lib.nsl_measure_peaks.restype = C.c_int
+    lib.nsl_lightmap_trace_bytes.argtypes = [i, i]
+    lib.nsl_lightmap_trace_bytes.restype = C.c_size_t
     lib.nsl_shade.argtypes = [vp, vp, i, i, C.POINTER(nsl_camera), C.POINTER(nsl_light), i, vp, vp]
     lib.nsl_pack_lightmaps.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.nsl_pack_lightmaps.restype = C.c_int
@@ -233,8 +245,11 @@ def _need(t, count, what):
     """The C ABI takes plain pointers and cannot see a buffer's size: refuse a
     tensor with fewer than `count` elements before the call (a kernel would
     read or write past its end)."""
-    if t is not None and t.numel() < count:
-        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: buffer holds {t.numel()} elements, needs {count}")
+    if t is None:
+        return
+    n = t.numel() if hasattr(t, "numel") else int(t.size)   # torch tensor or numpy array
+    if n < count:
+        raise NslError(NSL_ERR_INVALID_ARG, f"{what}: buffer holds {n} elements, needs {count}")
 
 
 F32 = ("float32",)
@@ -342,6 +357,50 @@ def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, strea
     _need(lightmaps, 8 * int(width) * int(height), "nsl_predict_lightmaps: lightmaps")
     check(load().nsl_predict_lightmaps(ctx, _dptr(guide, F32), int(width), int(height), int(precision),
                                        _dptr(lightmaps, F32), _stream(stream)), "nsl_predict_lightmaps")
+
+
+# channels and level of the 17 stored tensors of the network, in order
+TRACE_LAYERS = (("enc1a", 16, 0), ("enc1b", 16, 0), ("enc2a", 32, 1), ("enc2b", 32, 1), ("enc3a", 64, 2),
+                ("enc3b", 64, 2), ("enc4a", 128, 3), ("enc4b", 128, 3), ("up3", 64, 2), ("dec3a", 64, 2),
+                ("dec3b", 64, 2), ("up2", 32, 1), ("dec2a", 32, 1), ("dec2b", 32, 1), ("up1", 16, 0),
+                ("dec1a", 16, 0), ("dec1b", 16, 0))
+
+
+def nsl_predict_lightmaps_trace(ctx, guide, width, height, precision, lightmaps, trace, stream=None):
+    """nsl_predict_lightmaps that also copies every layer's stored output into
+    `trace`, a CUDA uint8 tensor of at least nsl_lightmap_trace_bytes bytes."""
+    _need(guide, 3 * int(width) * int(height), "nsl_predict_lightmaps_trace: guide")
+    _need(lightmaps, 8 * int(width) * int(height), "nsl_predict_lightmaps_trace: lightmaps")
+    need = int(load().nsl_lightmap_trace_bytes(int(width), int(height)))
+    _need(trace, need, "nsl_predict_lightmaps_trace: trace")
+    check(load().nsl_predict_lightmaps_trace(ctx, _dptr(guide, F32), int(width), int(height), int(precision),
+                                             _dptr(lightmaps, F32), _dptr(trace, U8), trace.numel(),
+                                             _stream(stream)), "nsl_predict_lightmaps_trace")
+
+
+def split_trace(trace_u8, width, height, dtype_name):
+    """The 17 NHWC tensors of a trace (a flat uint8 tensor) as [C, H_l, W_l]
+    float64 numpy arrays; dtype_name is 'bfloat16' or 'float16'."""
+    import numpy as np
+    import torch
+    tdt = getattr(torch, dtype_name)
+    out, off = [], 0
+    for _, ch, lv in TRACE_LAYERS:
+        h, w = int(height) >> lv, int(width) >> lv
+        n = h * w * ch * 2
+        t = trace_u8[off:off + n].view(tdt).reshape(h, w, ch).permute(2, 0, 1)
+        out.append(t.to(torch.float64).cpu().numpy())
+        off += n
+    return out
+
+
+def nsl_measure_peaks(stream=None) -> dict:
+    """Measured FP32 FMA rate, L1 data-path rate and L2 random-gather rate of
+    the current device (see include/nsl.h)."""
+    p = nsl_peaks()
+    check(load().nsl_measure_peaks(C.byref(p), _stream(stream)), "nsl_measure_peaks")
+    return {"sms": p.sms, "fp32_tflops": p.fp32_tflops, "l1_gbps": p.l1_gbps,
+            "l2_gather_gbps": p.l2_gather_gbps}
 
 
 def nsl_shade(ctx, lightmaps, width, height, cam, light_list, rgba, stream=None):
@@ -463,6 +522,9 @@ class Context:
 
     def predict_lightmaps(self, guide, width, height, precision, lightmaps, stream=None):
         nsl_predict_lightmaps(self.ctx, guide, width, height, precision, lightmaps, stream=stream)
+
+    def predict_lightmaps_trace(self, guide, width, height, precision, lightmaps, trace, stream=None):
+        nsl_predict_lightmaps_trace(self.ctx, guide, width, height, precision, lightmaps, trace, stream=stream)
 
     def shade(self, lightmaps, width, height, cam, light_list, rgba, stream=None):
         nsl_shade(self.ctx, lightmaps, width, height, cam, light_list, rgba, stream=stream)

@@ -130,6 +130,7 @@ def test_binding_refuses_a_density_of_the_wrong_type_without_gpu():
     the staging kernel: the binding refuses it before the call, for the
     allocation-free entry point and for a context's grid (CPU tensors here)."""
     import ctypes as C
+    import numpy as np
     import torch
     from paper_2604_03748_gb300 import inputs as I, nsl
     cam = I.perspective_camera(16, 1, 16, 16)
@@ -151,6 +152,9 @@ def test_binding_refuses_a_density_of_the_wrong_type_without_gpu():
             assert "float16" in str(ei.value)
         with pytest.raises(nsl.NslError):   # right type, too few voxels
             nsl.nsl_stage_grid(fake, torch.empty(16 ** 3 - 1), None)
+        with pytest.raises(nsl.NslError):   # a numpy host buffer, too few voxels
+            nsl.nsl_render_frame_host(fake, np.empty(16 ** 3 - 1, np.float32), None, cam, [], 2.0,
+                                      nsl.NSL_PREC_F32)
     finally:
         nsl._ctx_grid.pop(fake.value, None)
 

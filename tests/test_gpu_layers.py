@@ -1,0 +1,142 @@
+"""Layer-by-layer parity of the tensor-core networks (FP16, BF16, FP8) with the
+oracle's emulation of each layer's arithmetic, through the C ABI's trace entry
+point (nsl_predict_lightmaps_trace).
+
+Every convolution l is emulated by the oracle on the GPU's own stored inputs
+(the trace of the layers before it), so a difference can only come from the
+order of the tensor core's FP32 accumulation, never from earlier layers: each
+stored value must equal the emulation's or be its neighbour in the storage
+type (one unit in the last place), and only a small share of values may be
+neighbours.  The adapters (binary16 operands on the tensor cores) are held to
+the oracle's binary64 adapters on the GPU's feature map.  The whole network is
+then compared with the oracle's emulation of the same form and with FP64."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2604_03748_gb300 import inputs as I
+import parity as PT
+
+pytestmark = pytest.mark.gpu
+
+# (name, nsl precision, trace storage type, oracle form, significand bits of the storage)
+FORMS = [("f16", 3, "float16", 1, 11), ("bf16", 1, "bfloat16", 2, 8), ("fp8", 2, "float16", 3, 11)]
+# share of a layer's stored values allowed to be the emulation's neighbour
+# rather than the emulation's value itself (measured on the 512^2 workload:
+# at most 4.8e-3 for FP16, 3.0e-4 for BF16, 1.3e-4 for FP8)
+MAX_NEIGHBOUR_SHARE = {"f16": 0.01, "bf16": 0.002, "fp8": 0.002}
+TOL_ADAPTERS = 1e-2       # adapters with binary16 operands vs binary64, of the range
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_03748_gb300 import build, nsl
+    build.build()
+    nsl.load()
+    return nsl
+
+
+def _gpu_trace(nsl, pf, guide, prec, dtype):
+    import torch
+    dev = torch.device("cuda:0")
+    ctx = PT.make_ctx(pf)
+    _, H, W = guide.shape
+    g = torch.from_numpy(np.ascontiguousarray(guide, dtype=np.float32)).to(dev)
+    out = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+    tr = torch.empty(int(nsl.load().nsl_lightmap_trace_bytes(W, H)), dtype=torch.uint8, device=dev)
+    ctx.predict_lightmaps_trace(g, W, H, prec, out, tr)
+    plain = torch.empty_like(out)
+    ctx.predict_lightmaps(g, W, H, prec, plain)
+    torch.cuda.synchronize()
+    layers = nsl.split_trace(tr, W, H, dtype)
+    ctx.close()
+    lm = out.cpu().numpy().astype(np.float64)
+    assert np.array_equal(lm, plain.cpu().numpy().astype(np.float64))   # the trace changes nothing
+    return lm, layers
+
+
+def _layer_inputs(orc, L):
+    pool = orc.maxpool2
+    return {1: L[0], 2: pool(L[1]), 3: L[2], 4: pool(L[3]), 5: L[4], 6: pool(L[5]), 7: L[6], 8: L[7],
+            9: np.concatenate([L[8], L[5]]), 10: L[9], 11: L[10], 12: np.concatenate([L[11], L[3]]),
+            13: L[12], 14: L[13], 15: np.concatenate([L[14], L[1]]), 16: L[15]}
+
+
+def _neighbour_check(name, got, emu, bits, what):
+    """Every value equals the emulation's or is one storage ulp away; returns
+    the share of neighbours."""
+    d = np.abs(got - emu)
+    mag = np.maximum(np.abs(got), np.abs(emu))
+    floor = 1e-5 * max(np.abs(emu).max(), 1e-30)    # values that cancel to about zero
+    ok = d <= 2.0 ** (1 - bits) * mag + floor
+    assert ok.all(), f"{what}: {int((~ok).sum())} values beyond one ulp, worst {float((d - 2.0 ** (1 - bits) * mag).max())}"
+    return float((d > 0).mean())
+
+
+def _check_layers(orc, name, code, bits, guide, ds, L):
+    P = {k: v.astype(np.float64) for k, v in I.make_params(16, 0)}
+    x0 = guide.astype(np.float32).astype(np.float64).copy()
+    x0[2] *= ds
+    shares = []
+    a0 = orc.store_as(code, orc.conv_layer_prec(0, x0, P["enc1a.w"], P["enc1a.b"]))
+    shares.append(_neighbour_check(name, L[0], a0, bits, "enc1a"))
+    ins = _layer_inputs(orc, L)
+    for l in range(1, 17):
+        ln = orc.NET_LAYERS[l]
+        emu = orc.conv_layer_prec(code, ins[l], P[ln + ".w"], P[ln + ".b"], transposed=ln.startswith("up"))
+        shares.append(_neighbour_check(name, L[l], emu, bits, ln))
+    assert max(shares) <= MAX_NEIGHBOUR_SHARE[name], dict(zip(orc.NET_LAYERS, shares))
+    return shares
+
+
+def _guide(H, W, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0, 0.2, (H, W)), rng.uniform(0, 1, (H, W)), rng.uniform(0, 60, (H, W))])
+
+
+@pytest.mark.parametrize("form", FORMS, ids=[f[0] for f in FORMS])
+@pytest.mark.parametrize("H,W", [(64, 96), (24, 136)])
+def test_each_layer_matches_its_emulation(lib, orc, form, H, W):
+    name, prec, dtype, code, bits = form
+    n = 64
+    pf = I.PlumeFrame(np.zeros((n, n, n), np.float32), None, I.perspective_camera(n, 1, W, H),
+                      I.random_light(1), 2.0)
+    guide = _guide(H, W, H * 7 + W)
+    lm, L = _gpu_trace(lib, pf, guide, prec, dtype)
+    ds = 1.0 / math.sqrt(3 * n * n)
+    _check_layers(orc, name, code, bits, guide, ds, L)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    n_ad = 4 * (orc.nafblock_params(16) + 2 * 16 + 2)
+    ad = orc.net_adapters(L[16], flat[-n_ad:], 16)
+    assert max(PT.range_err(lm, ad)) <= TOL_ADAPTERS
+
+
+@pytest.mark.parametrize("form", FORMS, ids=[f[0] for f in FORMS])
+def test_layers_on_the_512_workload(lib, orc, form):
+    """The 512^2 obstacle scene on the oracle's guide: every layer against its
+    emulation, the adapters against binary64, and the whole network against the
+    oracle's emulation of the form (reported with the FP64 distance)."""
+    name, prec, dtype, code, bits = form
+    pf = I.config_obstacle_128()
+    o, _, _ = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+    guide = o.astype(np.float32).astype(np.float64)
+    lm, L = _gpu_trace(lib, pf, guide, prec, dtype)
+    ds = 1.0 / math.sqrt(3 * 128 * 128)
+    shares = _check_layers(orc, name, code, bits, guide, ds, L)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    n_ad = 4 * (orc.nafblock_params(16) + 2 * 16 + 2)
+    ad_err = max(PT.range_err(lm, orc.net_adapters(L[16], flat[-n_ad:], 16)))
+    assert ad_err <= TOL_ADAPTERS
+    emu = orc.net_forward_prec(guide, flat, 16, ds, code)
+    full = orc.net_forward(guide, flat, 16, ds)
+    e_emu, e64 = max(PT.range_err(lm, emu)), max(PT.range_err(lm, full))
+    # the whole network: the one-ulp accumulation differences above are spread
+    # by the later layers as much as their own rounding is, so the form's
+    # distance to FP64 is the bound here (FP8: reported only)
+    if name == "f16":
+        assert e64 <= PT.TOL_NET_F16
+    elif name == "bf16":
+        assert e64 <= PT.TOL_NET_BF16
+    print(f"\n{name}: neighbour shares per layer {np.round(shares, 5).tolist()}; adapters {ad_err:.2e}; "
+          f"network vs emulation {e_emu:.3e}, vs FP64 {e64:.3e}")

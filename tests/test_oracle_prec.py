@@ -174,3 +174,29 @@ def test_prec_mixed_layers_change_only_their_own_rounding(orc):
             np.testing.assert_array_equal(got[j], ref[j])
         np.testing.assert_array_equal(got[l], bf16_bits(got[l]))
         assert np.abs(got[l] - ref[l]).max() <= 2.0 ** -8 * np.abs(ref[l]).max()
+
+
+def test_layer_and_adapter_pieces_recompose_the_network(orc):
+    """Running each convolution alone (nslo_conv_layer_prec) on the previous
+    stored outputs, and the adapters alone on the stored feature map, gives the
+    whole network's trace and output again."""
+    c0, H, W = 8, 16, 24
+    params, flat, guide = _case(c0, H, W, 35)
+    P = {k: v.astype(np.float64) for k, v in params}
+    ds = 1 / 40.0
+    for code in (orc.PREC_BF16, orc.PREC_FP8, orc.PREC_F16):
+        out, L = orc.net_forward_prec(guide, flat, c0, ds, code, trace=True)
+        x0 = guide.copy()
+        x0[2] *= ds
+        a0 = orc.store_as(code, orc.conv_layer_prec(orc.PREC_F64, x0, P["enc1a.w"], P["enc1a.b"]))
+        np.testing.assert_array_equal(a0, L[0])
+        pool = orc.maxpool2
+        ins = {1: L[0], 2: pool(L[1]), 3: L[2], 4: pool(L[3]), 5: L[4], 6: pool(L[5]), 7: L[6], 8: L[7],
+               9: np.concatenate([L[8], L[5]]), 10: L[9], 11: L[10], 12: np.concatenate([L[11], L[3]]),
+               13: L[12], 14: L[13], 15: np.concatenate([L[14], L[1]]), 16: L[15]}
+        for l in range(1, 17):
+            name = orc.NET_LAYERS[l]
+            got = orc.conv_layer_prec(code, ins[l], P[name + ".w"], P[name + ".b"], transposed=name.startswith("up"))
+            np.testing.assert_array_equal(got, L[l])
+        n_ad = 4 * (orc.nafblock_params(c0) + 2 * c0 + 2)
+        np.testing.assert_array_equal(orc.net_adapters(L[16], flat[-n_ad:], c0), out)
