@@ -189,6 +189,50 @@ NSL_API nsl_status nsl_guiding_map_noalloc(const nsl_grid_desc* grid, const void
                                            float step_voxels, const nsl_march_opts* opts,
                                            float* guide_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Training slice (Sec. 4.4, the MSE term only): Adam on the mean squared
+ * error between the network's eight output planes and target planes, each
+ * plane's term with its own weight (the paper trains on values encoded to
+ * sRGB, which raises dark lightmap values; weights that equalise the planes'
+ * ranges play that part here on linear values) (for
+ * example nsl_reference_lightmaps with a zero emissive plane), for batches of
+ * `batch` guides of width x height.  Forward and backward run in FP32 on the
+ * SIMT cores with every activation kept (about 1.3 KB per pixel of the
+ * batch); the trained weights leave as a weight blob for nsl_create.  The
+ * paper's VGG and FlowNet loss terms need pretrained networks and are not
+ * built.
+ * ------------------------------------------------------------------------- */
+typedef struct nsl_trainer nsl_trainer;
+typedef struct {
+  int batch;            /* images per step, 1..64 */
+  int width, height;    /* image size, multiples of 8, at most 512^2 pixels */
+  float lr, beta1, beta2, eps;   /* Adam */
+  float plane_weight[8];         /* weight of each output plane's squared error */
+} nsl_train_opts;
+/* Defaults: batch 4, 64 x 64, lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8, every
+ * plane weight 1 (the loss is then the plain mean squared error). */
+NSL_API void nsl_default_train_opts(nsl_train_opts* o);
+/* Starts from the weights of `weights_blob` (C0 = 16). */
+NSL_API nsl_status nsl_trainer_create(const void* weights_blob, size_t blob_bytes, const nsl_train_opts* opts,
+                                      nsl_trainer** out);
+/* One step on device batches guides_dev [batch][3][H][W] (the guide, depth
+ * channel in voxels, scaled by depth_scale as nsl_predict_lightmaps scales it:
+ * 1 / |grid diagonal|) and targets_dev [batch][8][H][W]: forward, loss,
+ * backward, and with update != 0 one Adam update.  Synchronises `stream` and
+ * writes the loss (the mean over every plane and pixel of the batch of the
+ * plane-weighted squared error) to *loss_out (nullable). */
+NSL_API nsl_status nsl_trainer_step(nsl_trainer* t, const float* guides_dev, const float* targets_dev,
+                                    float depth_scale, int update, float* loss_out, void* stream);
+/* Learning rate of the following steps (a schedule is the caller's). */
+NSL_API nsl_status nsl_trainer_set_lr(nsl_trainer* t, float lr);
+/* The last step's gradient of the loss, in weight-blob order, into grad_dev
+ * (count >= the number of parameters). */
+NSL_API nsl_status nsl_trainer_gradients(nsl_trainer* t, float* grad_dev, size_t count, void* stream);
+/* The current weights as a weight blob (host memory); *needed receives its
+ * size, and blob_host = NULL only queries it. */
+NSL_API nsl_status nsl_trainer_get_blob(nsl_trainer* t, void* blob_host, size_t bytes, size_t* needed);
+NSL_API void nsl_trainer_destroy(nsl_trainer* t);
+
 /* Roofline denominators measured on the current device (the paper has no
  * counterpart; used by the benchmark).  Runs three short kernels on `stream`,
  * each timed with CUDA events after a warm-up launch, and synchronises it;
@@ -215,6 +259,26 @@ NSL_API nsl_status nsl_measure_peaks(nsl_peaks* out, void* stream);
 NSL_API nsl_status nsl_guide_sample_count(nsl_ctx* ctx, const nsl_camera* cam, float step_voxels,
                                           const nsl_march_opts* opts,
                                           unsigned long long* samples_out, void* stream);
+
+/* Fine-step six-light reference lightmaps: single scattering of Sec. 3 (Eq. RE
+ * with Eq. scatter) under six directional lights along the camera axes, the
+ * physical quantity the lightmap network approximates and is trained toward
+ * (Sec. 4.4; training data, not part of the per-frame path).  Per pixel, the
+ * view ray's chord is split into ceil(chord / hf) equal steps sampled at their
+ * midpoints; at every sample the transmittance toward each light is the
+ * midpoint sum of its own ray to the box exit in steps of at most hf.
+ *   density_dev, mask_dev  as for nsl_guiding_map (NULL density: the grid
+ *                 staged last)
+ *   cam           camera; cam->width x cam->height <= the context maximum
+ *   hf            step in voxels, at least 1/64
+ *   phase_g       Henyey-Greenstein parameter in (-1, 1) (0: isotropic)
+ *   out_dev       output [7][H][W] float32: light from +X (right), -X, +Y (up),
+ *                 -Y, +Z (back), -Z (front) in the camera frame, then the
+ *                 view transmittance T
+ * The cost grows as (extent / hf)^2 per pixel: meant for small images. */
+NSL_API nsl_status nsl_reference_lightmaps(nsl_ctx* ctx, const void* density_dev, const uint8_t* mask_dev,
+                                           const nsl_camera* cam, float hf, float phase_g, float* out_dev,
+                                           void* stream);
 
 /* Lightmap network, Sec. 4.3 / Fig. 3.
  *   guide_dev      [3][H][W] float32 guide
@@ -420,9 +484,17 @@ NSL_API nsl_status nsl_batch_set_tuning(nsl_batch* b, int seg_len, int march_blo
                                         int conv_ctas_per_sm);
 NSL_API nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blocks_per_sm,
                                         int* conv_ctas_per_sm);
+/* Pixel tile of one warp of the batched march: tile_width x (32 / tile_width)
+ * pixels, tile_width 2, 4, 8 (the default) or 16.  Every pixel's march is the
+ * same whatever the tile, so results are bitwise unchanged; a change drops a
+ * captured graph. */
+NSL_API nsl_status nsl_batch_set_march_tile(nsl_batch* b, int tile_width);
+NSL_API nsl_status nsl_batch_get_march_tile(const nsl_batch* b, int* tile_width);
 
-/* Autotuner: renders the batch under each candidate setting of the tuning
- * knobs, times it with CUDA events (median of 3) and keeps the fastest.  With
+/* Autotuner: renders the batch under each candidate setting of the march's
+ * knobs (tile width 8, 4 or 16 x segment length 4, 6 or 8 x march CTAs per
+ * SM), then of the convolutions' CTAs per SM (1, 2, 4), times each with CUDA
+ * events (median of 3) and keeps the fastest.  With
  * a cache path (JSON lines), a result stored for the same batch signature
  * (sizes, steps, precision) is applied without timing and new results are
  * appended.  Synchronises `stream`; *best_ms (may be NULL) gets the time. */
@@ -457,6 +529,10 @@ typedef struct {
   int max_batch;                   /* requests per batch, 1..64 */
   int precision;                   /* NSL_PREC_F16, NSL_PREC_BF16 or NSL_PREC_FP8 */
   nsl_march_opts march;            /* march options of every frame */
+  size_t max_batch_pixels;         /* billboard pixels a batch may hold (0: no cap); the
+                                      oldest runnable request is always taken, later ones
+                                      only while the batch stays under the cap, so a few
+                                      large frames do not hold many small ones back */
 } nsl_server_opts;
 
 typedef struct {
@@ -472,7 +548,8 @@ typedef struct {
   double busy_s;                   /* first submit -> last completion */
 } nsl_server_stats;
 
-/* Defaults: 40 GiB budget, 2 streams, batches of up to 64, FP16 network. */
+/* Defaults: 40 GiB budget, 2 streams, batches of up to 64 requests and
+ * 1 Mi billboard pixels, FP16 network. */
 NSL_API void nsl_default_server_opts(nsl_server_opts* o);
 NSL_API nsl_status nsl_server_create(const void* weights_blob, size_t blob_bytes,
                                      const nsl_server_opts* opts, nsl_server** out);

@@ -340,6 +340,7 @@ nsl_status fill_march_plume(const nsl_grid_desc& grid, const nsl_camera& cam, fl
   p->segment_exact = o.segment_exact ? 1 : 0;
   p->light_set = o.light_set;
   p->shadow_volume = o.shadow_volume && o.light_set != NSL_LIGHTS_F ? 1 : 0;
+  p->tx_log2 = kMarchTXLog2;
   p->tiles_x = (cam.width + kMarchTX - 1) / kMarchTX;
   p->tile_start = 0;
   return NSL_OK;
@@ -482,6 +483,28 @@ nsl_status nsl_guiding_map(nsl_ctx* c, const void* density, const uint8_t* mask,
   p.seg_L = p.seg_comp + (size_t)maxseg * P;
   cudaError_t e = launch_march_segmented(p, maxseg, c->tile_counter, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_guiding_map: march");
+  return NSL_OK;
+}
+
+nsl_status nsl_reference_lightmaps(nsl_ctx* c, const void* density, const uint8_t* mask, const nsl_camera* cam,
+                                   float hf, float phase_g, float* out, void* stream) {
+  static const char* fn = "nsl_reference_lightmaps";
+  if (!c) return fail(NSL_ERR_INVALID_ARG, "%s: ctx is NULL", fn);
+  if (!(hf >= 1.f / 64.f) || !std::isfinite(hf))
+    return fail(NSL_ERR_INVALID_ARG, "%s: hf must be a finite step of at least 1/64 voxel", fn);
+  if (!(phase_g > -1.f && phase_g < 1.f)) return fail(NSL_ERR_INVALID_ARG, "%s: phase_g must be in (-1, 1)", fn);
+  MarchPlume p;
+  nsl_status st = march_setup(c, cam, 1.f, nullptr, fn, &p);
+  if (st != NSL_OK) return st;
+  if (!out || !aligned16(out)) return fail(NSL_ERR_INVALID_ARG, "%s: out NULL or not 16-byte aligned", fn);
+  if (density) {
+    st = nsl_stage_grid(c, density, mask, stream);
+    if (st != NSL_OK) return st;
+  } else if (!c->staged_valid) {
+    return fail(NSL_ERR_INVALID_ARG, "%s: density is NULL and no grid is staged", fn);
+  }
+  cudaError_t e = launch_reference_lightmaps(p, (double)hf, phase_g, out, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, fn);
   return NSL_OK;
 }
 

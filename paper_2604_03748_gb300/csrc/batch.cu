@@ -70,6 +70,7 @@ struct nsl_batch {
   int seg_len = kMarchSegLen;
   int seg_blocks_per_sm = 0;       // 0 = occupancy maximum
   int conv_ctas = 4;
+  int tile_log2 = kMarchTXLog2;    // march tile: 2^tile_log2 x 2^(5 - tile_log2) pixels
   // captured graph
   cudaGraphExec_t exec = nullptr;
   bool capturing = false;
@@ -152,7 +153,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     if (st != NSL_OK) return st;
     const nsl_grid_desc& g = pl[k].grid;
     off_staged[k] = staged;
-    if (!(prestaged && prestaged[k])) staged += align256(staged_floats(g.nx, g.ny, g.nz) * sizeof(float));
+    if (!(prestaged && prestaged[k])) staged += align256(staged_grid_bytes(g));
     maxseg[k] = march_max_segments(g.nx, g.ny, g.nz, pl[k].step_voxels, b->seg_len);
     size_t sb, nb;
     batch_plume_scratch(pl[k], b->seg_len, &sb, &nb);
@@ -176,11 +177,15 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     if (st != NSL_OK) return st;
     if (m.shadow_volume)
       return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: shadow_volume is for the single-plume entry points");
+    m.tx_log2 = b->tile_log2;
+    m.tiles_x = (p.camera.width + (1 << b->tile_log2) - 1) >> b->tile_log2;
     const size_t P = (size_t)p.camera.width * p.camera.height;
     const bool pre = prestaged && prestaged[k];
     float* staged_k = pre ? const_cast<float*>(prestaged[k])
                           : reinterpret_cast<float*>(static_cast<char*>(b->staged) + off_staged[k]);
     m.vol = staged_k;
+    m.staged_half = p.grid.dtype == NSL_F16 ? 1 : 0;   // float16 grids stay float16 quads
+    m.scl = p.grid.sigma_scale;
     m.guide = p.guide_dev;
     m.seg_len = b->seg_len;
     char* sb = static_cast<char*>(b->seg) + off_seg[k];
@@ -188,7 +193,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     m.seg_tau = reinterpret_cast<float*>(sb + align256(P * sizeof(int)));
     m.seg_comp = m.seg_tau + (size_t)maxseg[k] * P;
     m.seg_L = m.seg_comp + (size_t)maxseg[k] * P;
-    const int nt = march_tiles(p.camera.width, p.camera.height);
+    const int nt = march_tiles(p.camera.width, p.camera.height, b->tile_log2);
     T.tile_starts[k] = tiles;
     T.item_starts[k] = items;
     T.tile_counts[k] = nt;
@@ -196,7 +201,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     items += nt * maxseg[k];
     StageItem& si = T.stage[k];
     si = StageItem{p.density_dev, p.mask_dev, staged_k, p.grid.nx, p.grid.ny, p.grid.nz,
-                   p.grid.dtype, p.grid.sigma_scale};
+                   p.grid.dtype, p.grid.sigma_scale, p.grid.dtype == NSL_F16 ? 1 : 0};
     T.stage_starts[k] = sblocks;
     if (!pre) sblocks += stage_batch_blocks(si);
     if (p.rgba_dev) {
@@ -472,6 +477,24 @@ nsl_status nsl_batch_set_tuning(nsl_batch* b, int seg_len, int march_blocks_per_
   return NSL_OK;
 }
 
+nsl_status nsl_batch_set_march_tile(nsl_batch* b, int tile_width) {
+  if (!b) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_set_march_tile: NULL batch");
+  const int lg = tile_width == 2 ? 1 : tile_width == 4 ? 2 : tile_width == 8 ? 3 : tile_width == 16 ? 4 : -1;
+  if (lg < 0) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_set_march_tile: width must be 2, 4, 8 or 16");
+  if (lg != b->tile_log2) {
+    cudaDeviceSynchronize();
+    drop_graph(b);   // a captured graph holds the old tile counts
+  }
+  b->tile_log2 = lg;
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_get_march_tile(const nsl_batch* b, int* tile_width) {
+  if (!b || !tile_width) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_get_march_tile: NULL argument");
+  *tile_width = 1 << b->tile_log2;
+  return NSL_OK;
+}
+
 nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blocks_per_sm,
                                 int* conv_ctas_per_sm) {
   if (!b || !seg_len || !march_blocks_per_sm || !conv_ctas_per_sm)
@@ -482,10 +505,11 @@ nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blo
   return NSL_OK;
 }
 
-// Autotuner: time each candidate (segment length x march blocks per SM x conv
-// CTAs per SM) on this batch with CUDA events (median of 3 after one warm-up)
-// and keep the fastest; with a cache path, a result recorded for the same batch
-// signature is reused and new results are appended.
+// Autotuner: time each candidate of the march (tile shape x segment length x
+// march blocks per SM), then of the convolutions' CTAs per SM, on this batch
+// with CUDA events (median of 3 after one warm-up) and keep the fastest; with a
+// cache path, a result recorded for the same batch signature is reused and new
+// results are appended.
 nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
                               const nsl_march_opts* opts, int precision, const char* cache_path,
                               void* stream, float* best_ms) {
@@ -513,14 +537,16 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
       char line[256];
       while (std::fgets(line, sizeof line, f)) {
         char k2[32];
-        int a, c, d;
+        int a, c, d, tw;
         float ms;
         if (std::sscanf(line, " {\"key\": \"%31[0-9a-f]\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
-                              "\"conv_ctas_per_sm\": %d, \"ms\": %f}", k2, &a, &c, &d, &ms) == 5 &&
+                              "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"ms\": %f}", k2, &a, &c, &d,
+                        &tw, &ms) == 6 &&
             std::strcmp(k2, key) == 0) {
           std::fclose(f);
           if (best_ms) *best_ms = ms;
-          return nsl_batch_set_tuning(b, a, c, d);
+          nsl_status st = nsl_batch_set_march_tile(b, tw);
+          return st == NSL_OK ? nsl_batch_set_tuning(b, a, c, d) : st;
         }
       }
       std::fclose(f);
@@ -528,6 +554,7 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   }
   const int seg_lens[] = {4, 6, 8};
   const int conv_ctas[] = {1, 2, 4};
+  const int tiles[] = {8, 4, 16};
   const int occ = march_segment_blocks_max();
   std::vector<int> march_bps = {0};
   for (int v : {5, 6}) if (v < occ) march_bps.push_back(v);
@@ -535,24 +562,43 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   NSL_CUDA_TRY(cudaEventCreate(&e0));
   NSL_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bs = b->seg_len, bm = b->seg_blocks_per_sm, bc = b->conv_ctas;
+  int bs = b->seg_len, bm = b->seg_blocks_per_sm, bc = b->conv_ctas, bt = 1 << b->tile_log2;
   nsl_status st = NSL_OK;
-  for (int sl : seg_lens)
-    for (int mb : march_bps)
-      for (int cc : conv_ctas) {
-        nsl_batch_set_tuning(b, sl, mb, cc);
-        float t[3];
-        for (int r = 0; r < 4 && st == NSL_OK; ++r) {
-          cudaEventRecord(e0, s);
-          st = render(b, plumes, n, opts, precision, s);
-          cudaEventRecord(e1, s);
-          cudaEventSynchronize(e1);
-          if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
-        }
+  // median of three timed renders after one warm-up
+  auto time_it = [&](float* med) {
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int r = 0; r < 4 && st == NSL_OK; ++r) {
+      cudaEventRecord(e0, s);
+      st = render(b, plumes, n, opts, precision, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      if (r > 0) cudaEventElapsedTime(&t[r - 1], e0, e1);
+    }
+    const float a = t[0], c = t[1], d = t[2];
+    *med = a > c ? (c > d ? c : (a > d ? d : a)) : (a > d ? a : (c > d ? d : c));
+  };
+  // the march's knobs (tile shape, segment length, CTAs per SM) with the
+  // network's at their current value, then the network's CTAs per SM: the two
+  // stages do not interact
+  for (int tw : tiles)
+    for (int sl : seg_lens)
+      for (int mb : march_bps) {
+        nsl_batch_set_march_tile(b, tw);
+        nsl_batch_set_tuning(b, sl, mb, bc);
+        float med;
+        time_it(&med);
         if (st != NSL_OK) break;
-        float a = t[0], c = t[1], d = t[2], med = a > c ? (c > d ? c : (a > d ? d : a)) : (a > d ? a : (c > d ? d : c));
-        if (med < best) { best = med; bs = sl; bm = mb; bc = cc; }
+        if (med < best) { best = med; bs = sl; bm = mb; bt = tw; }
       }
+  nsl_batch_set_march_tile(b, bt);
+  for (int cc : conv_ctas) {
+    if (st != NSL_OK) break;
+    nsl_batch_set_tuning(b, bs, bm, cc);
+    float med;
+    time_it(&med);
+    if (st != NSL_OK) break;
+    if (med < best) { best = med; bc = cc; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NSL_OK) return st;
@@ -561,7 +607,8 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
       std::fprintf(f, "{\"key\": \"%s\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
-                      "\"conv_ctas_per_sm\": %d, \"ms\": %.4f}\n", key, bs, bm, bc, best);
+                      "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"ms\": %.4f}\n", key, bs, bm, bc, bt,
+                   best);
       std::fclose(f);
     }
   }

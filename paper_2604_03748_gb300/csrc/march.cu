@@ -15,6 +15,7 @@
 // binary32 evaluation of the same sequence.
 #include <cmath>
 
+#include "grid_sample.cuh"
 #include "nsl_internal.cuh"
 
 namespace nsl {
@@ -24,83 +25,6 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
   uint32_t state = v * 747796405u + 2891336453u;
   uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
   return (word >> 22u) ^ word;
-}
-
-// Staged grid layouts (both hold sigma' = scale * rho * [mask == 0], float32,
-// padded by one cell on the low sides with every neighbour index clamped to the
-// grid, so a sample inside the box needs no clamping; GridH below is the quad
-// layout in FP16 holding rho * [mask == 0], scaled after the blend):
-//   kLayoutQuad    float4 per cell, the x/y 2x2 neighbourhood of its slice; a
-//                  sample reads 2 x 16 bytes (the default)
-//   kLayoutOcto    2 x float4 per cell, the 2x2x2 neighbourhood; a sample reads
-//                  one 32-byte vector (twice the memory)
-struct Grid {
-  const float* __restrict__ v;
-  int nx, ny, nz;
-  float fx, fy, fz;  // box extents
-};
-// FP16 quads of the masked density rho (single-plume contexts with an FP16
-// grid): values exact, sigma = scl * (trilinear value); half the bytes
-struct GridH {
-  const __half* __restrict__ v;
-  int nx, ny, nz;
-  float fx, fy, fz;
-  float scl;          // sigma_scale
-};
-__device__ __forceinline__ float scaled(const Grid&, float v) { return v; }
-__device__ __forceinline__ float scaled(const GridH& g, float v) { return __fmul_rn(g.scl, v); }
-
-// 32-byte load of an octo cell: the 2x2 x/y neighbourhood of slice z (a) and
-// of slice z+1 (b), in one 256-bit vector access
-__device__ __forceinline__ void ldg_octo(const float* p, float4& a, float4& b) {
-  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-      : "l"(p));
-}
-
-// The two x/y quads of padded cell `cell` (slice z in a, z+1 in b).
-__device__ __forceinline__ void load_cell(const Grid& g, unsigned cell, unsigned pl, float4& a, float4& b) {
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    ldg_octo(g.v + 8 * (size_t)cell, a, b);
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
-    a = __ldg(q);
-    b = __ldg(q + pl);
-  }
-}
-__device__ __forceinline__ float4 half4_to_float4(uint2 u) {
-  const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-  const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-  return make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-__device__ __forceinline__ void load_cell(const GridH& g, unsigned cell, unsigned pl, float4& a, float4& b) {
-  static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
-  const uint2* q = reinterpret_cast<const uint2*>(g.v) + cell;
-  a = half4_to_float4(__ldg(q));
-  b = half4_to_float4(__ldg(q + pl));
-}
-
-// Extinction at p: 0 outside the closed box [0,n]; trilinear interpolation of
-// the staged voxels at q = p - 0.5 with clamp-to-edge indices inside it.
-template <class G>
-__device__ __forceinline__ float sigma_at(const G& g, float px, float py, float pz) {
-  if (!(px >= 0.f && px <= g.fx && py >= 0.f && py <= g.fy && pz >= 0.f && pz <= g.fz)) return 0.f;
-  float qx = __fsub_rn(px, 0.5f), qy = __fsub_rn(py, 0.5f), qz = __fsub_rn(pz, 0.5f);
-  float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
-  float tx = __fsub_rn(qx, flx), ty = __fsub_rn(qy, fly), tz = __fsub_rn(qz, flz);
-  int ix = (int)flx, iy = (int)fly, iz = (int)flz;
-  // padded cells: cell (ix+1, iy+1, iz+1) holds the corners, every index of a
-  // point inside the box is in range
-  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  float4 a, b;
-  load_cell(g, (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1), pl, a, b);
-  const float c00 = fmaf(tx, a.y - a.x, a.x);
-  const float c10 = fmaf(tx, a.w - a.z, a.z);
-  const float c01 = fmaf(tx, b.y - b.x, b.x);
-  const float c11 = fmaf(tx, b.w - b.z, b.z);
-  const float c0 = fmaf(ty, c10 - c00, c00);
-  const float c1 = fmaf(ty, c11 - c01, c01);
-  return scaled(g, fmaf(tz, c1 - c0, c0));
 }
 
 // Two-stage form of sigma_at for software pipelining (quad layout): fetch()
@@ -617,8 +541,8 @@ march_kernel(MarchPlume single, const MarchPlume* __restrict__ table, int nplume
       tile -= P->tile_start;
     }
     const int tx = tile % P->tiles_x, ty = tile / P->tiles_x;
-    const int i = tx * kMarchTX + (lane % kMarchTX);
-    const int j = ty * kMarchTY + (lane / kMarchTX);
+    const int i = (tx << P->tx_log2) + (lane & ((1 << P->tx_log2) - 1));
+    const int j = (ty << (5 - P->tx_log2)) + (lane >> P->tx_log2);
     if (i < P->cam.W && j < P->cam.H) march_pixel<kCount, !kBatch, G>(*P, i, j);
   }
 }
@@ -639,12 +563,13 @@ static int march_grid() {
   return blocks;
 }
 
-int march_tiles(int W, int H) {
-  return ((W + kMarchTX - 1) / kMarchTX) * ((H + kMarchTY - 1) / kMarchTY);
+int march_tiles(int W, int H, int tx_log2) {
+  const int tx = 1 << tx_log2, ty = 32 / tx;
+  return ((W + tx - 1) / tx) * ((H + ty - 1) / ty);
 }
 
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s, bool count) {
-  const int ntiles = march_tiles(p.cam.W, p.cam.H);
+  const int ntiles = march_tiles(p.cam.W, p.cam.H, p.tx_log2);
   if (ntiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -686,8 +611,8 @@ __global__ void __launch_bounds__(kMarchThreads) march_pixel_pass_kernel(MarchPl
   const int lane = threadIdx.x & 31;
   const int tile = blockIdx.x * (kMarchThreads / 32) + (threadIdx.x >> 5);
   if (tile >= ntiles) return;
-  const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
-  const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+  const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+  const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
   if (i >= P.cam.W || j >= P.cam.H) return;
   if (kPass == 1) march_view_pixel<G>(P, i, j);
   else march_finish_pixel(P, i, j);
@@ -707,8 +632,8 @@ march_segment_kernel(MarchPlume P, int ntiles, int nitems, int* __restrict__ cou
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= nitems) break;
     const int seg = item / ntiles, tile = item % ntiles;
-    const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
-    const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+    const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+    const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
     if (i < P.cam.W && j < P.cam.H) march_segment<true, kVolume, G>(P, i, j, seg);
   }
 }
@@ -721,7 +646,7 @@ int march_max_segments(int nx, int ny, int nz, float h, int seg_len) {
 
 cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
                                    cudaStream_t s) {
-  const int ntiles = march_tiles(p.cam.W, p.cam.H);
+  const int ntiles = march_tiles(p.cam.W, p.cam.H, p.tx_log2);
   if (ntiles == 0) return cudaSuccess;
   const int warps_per_block = kMarchThreads / 32;
   const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
@@ -772,11 +697,15 @@ __global__ void __launch_bounds__(kMarchThreads) march_pass_batch_kernel(
   const int k = find_start(tile_starts, nplumes, gt);
   const MarchPlume& P = table[k];
   const int tile = gt - __ldg(tile_starts + k);
-  const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
-  const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
+  const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+  const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
   if (i >= P.cam.W || j >= P.cam.H) return;
-  if (kPass == 1) march_view_pixel(P, i, j);
-  else march_finish_pixel(P, i, j);
+  if (kPass == 1) {
+    if (P.staged_half) march_view_pixel<GridH>(P, i, j);
+    else march_view_pixel(P, i, j);
+  } else {
+    march_finish_pixel(P, i, j);
+  }
 }
 
 // pass 2 over (plume, segment, tile) items: item_starts[p] = first item of plume
@@ -796,9 +725,12 @@ __global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks) march_segment_
     const MarchPlume& P = table[k];
     const int local = item - __ldg(item_starts + k), nt = __ldg(tile_counts + k);
     const int seg = local / nt, tile = local % nt;
-    const int i = (tile % P.tiles_x) * kMarchTX + lane % kMarchTX;
-    const int j = (tile / P.tiles_x) * kMarchTY + lane / kMarchTX;
-    if (i < P.cam.W && j < P.cam.H) march_segment<false>(P, i, j, seg);
+    const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+    const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
+    if (i < P.cam.W && j < P.cam.H) {
+      if (P.staged_half) march_segment<false, false, GridH>(P, i, j, seg);   // warp-uniform branch
+      else march_segment<false>(P, i, j, seg);
+    }
   }
 }
 
@@ -941,39 +873,43 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
 // FP16 staging of the quad layout (single-plume contexts with an FP16 grid):
 // the raw values rho, masked to 0, four cells per thread as in stage_unit;
 // the march multiplies by sigma_scale after the trilinear blend.
+__device__ __forceinline__ void stage_half_unit(const __half* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                                int nx, int ny, int nz, uint2* __restrict__ out, size_t u) {
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpr = (px + 3u) / 4u;
+  const __half zero = __float2half_rn(0.f);
+  auto val = [&](size_t idx) { return (mask && __ldg(mask + idx)) ? zero : rho[idx]; };
+  const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
+  const unsigned r = u32 / gpr;
+  const int a0 = (int)(4u * (u32 % gpr));
+  const int b = (int)(r % py), cz = (int)(r / py);
+  const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+  const int k0 = min(max(cz - 1, 0), nz - 1);
+  const size_t b0 = ((size_t)k0 * ny + j0) * nx, b1 = ((size_t)k0 * ny + j1) * nx;
+  __half w0[5], w1[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int x = min(max(a0 - 1 + t, 0), nx - 1);
+    w0[t] = val(b0 + x);
+    w1[t] = val(b1 + x);
+  }
+  uint2* dst = out + ((size_t)r * px + (unsigned)a0);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (a0 + t < (int)px) {
+      const __half2 lo = __halves2half2(w0[t], w0[t + 1]), hi = __halves2half2(w1[t], w1[t + 1]);
+      dst[t] = make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) stage_half_kernel(const __half* __restrict__ rho,
                                                          const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                                                          uint2* __restrict__ out) {
   pdl_wait();      // the previous frame's march may still read the staged grid
   pdl_trigger();
   const size_t n = stage_units(nx, ny, nz);
-  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpr = (px + 3u) / 4u;
-  const __half zero = __float2half_rn(0.f);
-  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x) {
-    auto val = [&](size_t idx) { return (mask && __ldg(mask + idx)) ? zero : rho[idx]; };
-    const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
-    const unsigned r = u32 / gpr;
-    const int a0 = (int)(4u * (u32 % gpr));
-    const int b = (int)(r % py), cz = (int)(r / py);
-    const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
-    const int k0 = min(max(cz - 1, 0), nz - 1);
-    const size_t b0 = ((size_t)k0 * ny + j0) * nx, b1 = ((size_t)k0 * ny + j1) * nx;
-    __half w0[5], w1[5];
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      const int x = min(max(a0 - 1 + t, 0), nx - 1);
-      w0[t] = val(b0 + x);
-      w1[t] = val(b1 + x);
-    }
-    uint2* dst = out + ((size_t)r * px + (unsigned)a0);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (a0 + t < (int)px) {
-        const __half2 lo = __halves2half2(w0[t], w0[t + 1]), hi = __halves2half2(w1[t], w1[t + 1]);
-        dst[t] = make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
-      }
-    }
-  }
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x)
+    stage_half_unit(rho, mask, nx, ny, nz, out, u);
 }
 
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
@@ -1085,7 +1021,11 @@ __global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __res
   const size_t units = stage_units(it.nx, it.ny, it.nz);
   const size_t u0 = (size_t)(blockIdx.x - __ldg(block_starts + k)) * kStageChunk;
   const size_t u1 = u0 + kStageChunk < units ? u0 + kStageChunk : units;
-  if (it.dtype == NSL_F16)
+  if (it.dtype == NSL_F16 && it.half_out) {
+    for (size_t u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+      stage_half_unit(static_cast<const __half*>(it.density), it.mask, it.nx, it.ny, it.nz,
+                      reinterpret_cast<uint2*>(it.out), u);
+  } else if (it.dtype == NSL_F16)
     stage_units_range<__half>(static_cast<const __half*>(it.density), it.mask, it.nx, it.ny, it.nz,
                               it.scale, it.out, u0, u1);
   else

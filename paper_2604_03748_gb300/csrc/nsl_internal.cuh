@@ -121,6 +121,7 @@ struct MarchPlume {
   const float* volB;
   float* guide;       // [3][H][W]
   int tiles_x;        // tiles per row
+  int tx_log2;        // march tile: 2^tx_log2 x 2^(5 - tx_log2) pixels per warp (3: 8 x 4)
   int tile_start;     // first tile index of this plume in a batch
   unsigned long long* counter;  // density-evaluation counter (counting variant only)
   // segmented march scratch ([segment][pixel]) and the segment length S
@@ -141,8 +142,10 @@ constexpr int kMarchSegLen = NSL_MARCH_SEG;  // view steps per segment of the se
 #ifndef NSL_MARCH_TX
 #define NSL_MARCH_TX 8
 #endif
-constexpr int kMarchTX = NSL_MARCH_TX;  // march tile: TX x (32/TX) pixels, one warp
+constexpr int kMarchTX = NSL_MARCH_TX;  // default march tile: TX x (32/TX) pixels, one warp
 constexpr int kMarchTY = 32 / kMarchTX;
+constexpr int kMarchTXLog2 = kMarchTX == 16 ? 4 : (kMarchTX == 8 ? 3 : (kMarchTX == 4 ? 2 : 1));
+static_assert((1 << kMarchTXLog2) == kMarchTX, "march tile width: 2, 4, 8 or 16");
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
@@ -172,12 +175,14 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
                                 int ny, int nz, float scale, float* staged, cudaStream_t s);
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
                                      __half* staged, cudaStream_t s);
-int march_tiles(int W, int H);
+int march_tiles(int W, int H, int tx_log2 = kMarchTXLog2);
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
                          bool count = false);
 int march_max_segments(int nx, int ny, int nz, float h, int seg_len);
 cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
                                    cudaStream_t s);
+// fine-step six-light reference lightmaps [7][H][W] of the staged grid (reference.cu)
+cudaError_t launch_reference_lightmaps(const MarchPlume& p, double hf, float g, float* out, cudaStream_t s);
 // batched forms (device tables; see march.cu)
 struct StageItem {
   const void* density;
@@ -185,7 +190,15 @@ struct StageItem {
   float* out;            // padded quad staging of this plume
   int nx, ny, nz, dtype;
   float scale;
+  int half_out;          // a float16 grid staged as float16 quads of rho * [mask == 0]
+                         // (sigma_scale applied by the march after the blend)
 };
+// Bytes of the staged grid of one plume: float16 quads for a float16 grid,
+// float32 quads otherwise.
+inline size_t staged_grid_bytes(const nsl_grid_desc& g) {
+  return g.dtype == NSL_F16 ? staged_cells(g.nx, g.ny, g.nz) * 4 * sizeof(__half)
+                            : staged_floats(g.nx, g.ny, g.nz) * sizeof(float);
+}
 int stage_batch_blocks(const StageItem& it);
 cudaError_t launch_stage_batch(const StageItem* items_dev, const int* block_starts_dev, int n,
                                int total_blocks, cudaStream_t s);

@@ -190,9 +190,14 @@ bool admit(nsl_server* S, int idx, Slot& sl) {
   if (cudaMemcpyAsync(sl.up_dens, p.dens_host, p.dens_bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
       (p.mask_host && cudaMemcpyAsync(sl.up_mask, p.mask_host, p.mask_bytes, cudaMemcpyHostToDevice,
                                       sl.stream) != cudaSuccess) ||
-      launch_stage_volume(sl.up_dens, p.grid.dtype, p.mask_host ? static_cast<const uint8_t*>(sl.up_mask) : nullptr,
-                          p.grid.nx, p.grid.ny, p.grid.nz, p.grid.sigma_scale, static_cast<float*>(staged),
-                          sl.stream) != cudaSuccess) {
+      (p.grid.dtype == NSL_F16
+           ? launch_stage_volume_half(static_cast<const __half*>(sl.up_dens),
+                                      p.mask_host ? static_cast<const uint8_t*>(sl.up_mask) : nullptr, p.grid.nx,
+                                      p.grid.ny, p.grid.nz, static_cast<__half*>(staged), sl.stream)
+           : launch_stage_volume(sl.up_dens, p.grid.dtype,
+                                 p.mask_host ? static_cast<const uint8_t*>(sl.up_mask) : nullptr, p.grid.nx,
+                                 p.grid.ny, p.grid.nz, p.grid.sigma_scale, static_cast<float*>(staged),
+                                 sl.stream)) != cudaSuccess) {
     cudaGetLastError();
     cudaFreeAsync(staged, sl.stream);
     cudaFreeAsync(state, sl.stream);
@@ -220,7 +225,7 @@ void fail_request(nsl_server* S, uint64_t id, nsl_status st, const std::string& 
 bool launch_batch(nsl_server* S, Slot& sl) {
   std::vector<uint64_t> pick;
   std::vector<int> picked;
-  size_t seg = 0, net = 0;
+  size_t seg = 0, net = 0, pix = 0;
   for (uint64_t id : S->queue) {
     if ((int)pick.size() >= S->o.max_batch) break;
     Req& r = S->reqs[id];
@@ -229,7 +234,9 @@ bool launch_batch(nsl_server* S, Slot& sl) {
     size_t sb, nb;
     const nsl_plume q = plume_of(p, r);
     batch_plume_scratch(q, S->seg_len, &sb, &nb);
-    if (seg + sb > S->seg_cap || net + nb > S->net_cap) {
+    const size_t rpix = (size_t)r.cam.width * r.cam.height;
+    if (seg + sb > S->seg_cap || net + nb > S->net_cap ||
+        (!pick.empty() && S->o.max_batch_pixels && pix + rpix > S->o.max_batch_pixels)) {
       p.busy = true;  // keep later requests of this plume behind this one
       picked.push_back(-1 - r.plume);
       continue;
@@ -244,6 +251,7 @@ bool launch_batch(nsl_server* S, Slot& sl) {
     pick.push_back(id);
     seg += sb;
     net += nb;
+    pix += rpix;
   }
   // plumes only held back for ordering become free again
   for (int v : picked)
@@ -382,6 +390,7 @@ void nsl_default_server_opts(nsl_server_opts* o) {
   o->scratch_bytes_per_stream = 0;
   o->streams = 2;
   o->max_batch = 64;
+  o->max_batch_pixels = size_t(1) << 20;
   o->precision = NSL_PREC_F16;
   nsl_default_march_opts(&o->march);
 }
@@ -488,7 +497,7 @@ nsl_status nsl_server_add_plume(nsl_server* S, const nsl_grid_desc* grid, const 
   p.step = step;
   p.max_w = max_w;
   p.max_h = max_h;
-  p.staged_bytes = align256(staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float));
+  p.staged_bytes = align256(staged_grid_bytes(*grid));
   p.state_bytes = align256((size_t)kStatePlanes * max_w * max_h * sizeof(float));
   // the plume alone (with its upload buffers) next to the slots' scratch, and
   // a frame at its largest billboard inside one slot's scratch

@@ -32,7 +32,10 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_server_drain", "nsl_server_plume_state", "nsl_server_get_stats",
            "nsl_server_reset_stats", "nsl_pack_lightmaps", "nsl_obstacle_shadow_map",
            "nsl_shade_shadowed", "nsl_selftest_wait_timeout", "nsl_predict_lightmaps_trace",
-           "nsl_lightmap_trace_bytes", "nsl_measure_peaks"]
+           "nsl_lightmap_trace_bytes", "nsl_measure_peaks", "nsl_reference_lightmaps",
+           "nsl_default_train_opts", "nsl_trainer_create", "nsl_trainer_step", "nsl_trainer_gradients",
+           "nsl_trainer_get_blob", "nsl_trainer_destroy", "nsl_trainer_set_lr", "nsl_batch_set_march_tile",
+           "nsl_batch_get_march_tile"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -66,7 +69,7 @@ class nsl_plume(C.Structure):
 class nsl_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("scratch_bytes_per_stream", C.c_size_t),
                 ("streams", C.c_int), ("max_batch", C.c_int), ("precision", C.c_int),
-                ("march", nsl_march_opts)]
+                ("march", nsl_march_opts), ("max_batch_pixels", C.c_size_t)]
 
 
 class nsl_server_stats(C.Structure):
@@ -84,6 +87,11 @@ class nsl_server_stats(C.Structure):
 class nsl_peaks(C.Structure):
     _fields_ = [("sms", C.c_int), ("fp32_tflops", C.c_double), ("l1_gbps", C.c_double),
                 ("l2_gather_gbps", C.c_double)]
+
+
+class nsl_train_opts(C.Structure):
+    _fields_ = [("batch", C.c_int), ("width", C.c_int), ("height", C.c_int), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("plane_weight", C.c_float * 8)]
 
 
 class NslError(RuntimeError):
@@ -119,6 +127,20 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_predict_lightmaps.argtypes = [vp, vp, i, i, i, vp, vp]
     lib.nsl_predict_lightmaps_trace.argtypes = [vp, vp, i, i, i, vp, vp, C.c_size_t, vp]
     lib.nsl_predict_lightmaps_trace.restype = C.c_int
+    lib.nsl_reference_lightmaps.argtypes = [vp, vp, vp, C.POINTER(nsl_camera), f, f, vp, vp]
+    lib.nsl_reference_lightmaps.restype = C.c_int
+    lib.nsl_default_train_opts.argtypes = [C.POINTER(nsl_train_opts)]
+    lib.nsl_default_train_opts.restype = None
+    lib.nsl_trainer_create.argtypes = [vp, C.c_size_t, C.POINTER(nsl_train_opts), C.POINTER(vp)]
+    lib.nsl_trainer_step.argtypes = [vp, vp, vp, f, i, C.POINTER(C.c_float), vp]
+    lib.nsl_trainer_gradients.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.nsl_trainer_get_blob.argtypes = [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]
+    lib.nsl_trainer_set_lr.argtypes = [vp, f]
+    for name in ("nsl_trainer_create", "nsl_trainer_step", "nsl_trainer_gradients", "nsl_trainer_get_blob",
+                 "nsl_trainer_set_lr"):
+        getattr(lib, name).restype = C.c_int
+    lib.nsl_trainer_destroy.argtypes = [vp]
+    lib.nsl_trainer_destroy.restype = None
     lib.nsl_measure_peaks.argtypes = [C.POINTER(nsl_peaks), vp]
     lib.nsl_measure_peaks.restype = C.c_int
     lib.nsl_lightmap_trace_bytes.argtypes = [i, i]
@@ -146,11 +168,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_batch_launch_graph.argtypes = [vp, vp]
     lib.nsl_batch_set_tuning.argtypes = [vp, i, i, i]
     lib.nsl_batch_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.nsl_batch_set_march_tile.argtypes = [vp, i]
+    lib.nsl_batch_get_march_tile.argtypes = [vp, C.POINTER(C.c_int)]
     lib.nsl_batch_autotune.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts), i,
                                        C.c_char_p, vp, C.POINTER(C.c_float)]
     for name in ("nsl_batch_create", "nsl_batch_render", "nsl_batch_capture_graph",
                  "nsl_batch_update_graph", "nsl_batch_launch_graph", "nsl_batch_set_tuning",
-                 "nsl_batch_get_tuning", "nsl_batch_autotune"):
+                 "nsl_batch_get_tuning", "nsl_batch_autotune", "nsl_batch_set_march_tile",
+                 "nsl_batch_get_march_tile"):
         getattr(lib, name).restype = C.c_int
     lib.nsl_default_server_opts.argtypes = [C.POINTER(nsl_server_opts)]
     lib.nsl_default_server_opts.restype = None
@@ -350,6 +375,15 @@ def nsl_guiding_map_noalloc(grid_shape, dtype, sigma_scale, density, mask, cam, 
                                          C.byref(camera(cam)), float(step),
                                          C.byref(opts) if opts is not None else None,
                                          _dptr(guide, F32), _stream(stream)), "nsl_guiding_map_noalloc")
+
+
+def nsl_reference_lightmaps(ctx, density, mask, cam, hf, out, phase_g=0.0, stream=None):
+    """Fine-step six-light reference lightmaps [7][H][W] of the grid (see include/nsl.h)."""
+    _need(out, 7 * int(cam.width) * int(cam.height), "nsl_reference_lightmaps: out")
+    _ctx_check_grid(ctx, density, mask, "nsl_reference_lightmaps")
+    check(load().nsl_reference_lightmaps(ctx, _dptr(density, GRID_TYPES), _dptr(mask, U8), C.byref(camera(cam)),
+                                         float(hf), float(phase_g), _dptr(out, F32), _stream(stream)),
+          "nsl_reference_lightmaps")
 
 
 def nsl_predict_lightmaps(ctx, guide, width, height, precision, lightmaps, stream=None):
@@ -608,6 +642,14 @@ class Batch:
         check(load().nsl_batch_get_tuning(self.b, C.byref(a), C.byref(b), C.byref(c)), "nsl_batch_get_tuning")
         return a.value, b.value, c.value
 
+    def set_march_tile(self, width):
+        check(load().nsl_batch_set_march_tile(self.b, int(width)), "nsl_batch_set_march_tile")
+
+    def get_march_tile(self):
+        w = C.c_int()
+        check(load().nsl_batch_get_march_tile(self.b, C.byref(w)), "nsl_batch_get_march_tile")
+        return int(w.value)
+
     def autotune(self, plumes, precision, cache_path=None, opts=None, stream=None):
         arr = plume_array(plumes)
         ms = C.c_float(0)
@@ -710,3 +752,66 @@ class Server:
 
     def reset_stats(self):
         check(load().nsl_server_reset_stats(self.s), "nsl_server_reset_stats")
+
+
+# --------------------------------------------------------------------------
+# training slice
+# --------------------------------------------------------------------------
+
+def train_opts(**kw) -> nsl_train_opts:
+    o = nsl_train_opts()
+    load().nsl_default_train_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "plane_weight":
+            o.plane_weight[:] = [float(x) for x in v]
+        else:
+            setattr(o, k, type(getattr(o, k))(v))
+    return o
+
+
+class Trainer:
+    """Owns an nsl_trainer (Adam on the MSE of the eight output planes)."""
+
+    def __init__(self, blob: bytes, opts: nsl_train_opts | None = None):
+        self.o = opts if opts is not None else train_opts()
+        out = C.c_void_p()
+        buf = C.create_string_buffer(blob, len(blob))
+        check(load().nsl_trainer_create(buf, len(blob), C.byref(self.o), C.byref(out)), "nsl_trainer_create")
+        self.t = out
+        self.n_params = (len(blob) - 20) // 4
+
+    def close(self):
+        if self.t:
+            load().nsl_trainer_destroy(self.t)
+            self.t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, guides, targets, depth_scale, update=True, stream=None) -> float:
+        """guides [B,3,H,W], targets [B,8,H,W]: float32 CUDA tensors."""
+        B, H, W = int(self.o.batch), int(self.o.height), int(self.o.width)
+        _need(guides, B * 3 * H * W, "nsl_trainer_step: guides")
+        _need(targets, B * 8 * H * W, "nsl_trainer_step: targets")
+        loss = C.c_float()
+        check(load().nsl_trainer_step(self.t, _dptr(guides, F32), _dptr(targets, F32), float(depth_scale),
+                                      1 if update else 0, C.byref(loss), _stream(stream)), "nsl_trainer_step")
+        return float(loss.value)
+
+    def set_lr(self, lr):
+        check(load().nsl_trainer_set_lr(self.t, float(lr)), "nsl_trainer_set_lr")
+
+    def gradients(self, out, stream=None):
+        _need(out, self.n_params, "nsl_trainer_gradients: out")
+        check(load().nsl_trainer_gradients(self.t, _dptr(out, F32), out.numel(), _stream(stream)),
+              "nsl_trainer_gradients")
+
+    def blob(self) -> bytes:
+        need = C.c_size_t()
+        check(load().nsl_trainer_get_blob(self.t, None, 0, C.byref(need)), "nsl_trainer_get_blob")
+        buf = C.create_string_buffer(need.value)
+        check(load().nsl_trainer_get_blob(self.t, buf, need.value, C.byref(need)), "nsl_trainer_get_blob")
+        return buf.raw

@@ -9,6 +9,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = ["nsl_grid_desc", "nsl_camera", "nsl_light", "nsl_march_opts", "nsl_plume", "nsl_server_opts", "nsl_peaks",
+           "nsl_train_opts",
            "nsl_server_stats"]
 
 

@@ -229,11 +229,22 @@ def test_batch_autotune_and_cache(lib, tmp_path):
     # the cached entry is applied without timing: plant a marker time and tuning
     import json
     rec = json.loads(lines[0])
-    rec.update(seg_len=8, march_blocks_per_sm=4, conv_ctas_per_sm=1, ms=123.5)
+    assert rec["march_tile_width"] in (4, 8, 16)
+    rec.update(seg_len=8, march_blocks_per_sm=4, conv_ctas_per_sm=1, march_tile_width=16, ms=123.5)
     with open(cache, "w") as f:
         f.write(json.dumps(rec) + "\n")
     ms2 = b.autotune(items, 3, cache_path=cache)
-    assert abs(ms2 - 123.5) < 1e-3 and b.get_tuning() == (8, 4, 1)
+    assert abs(ms2 - 123.5) < 1e-3 and b.get_tuning() == (8, 4, 1) and b.get_march_tile() == 16
+    # every pixel marches the same whatever the warp's tile: bitwise equal guides
+    b.render(items, 3)
+    g16 = _host(items, "guide")
+    b.set_march_tile(4)
+    b.render(items, 3)
+    for a, c in zip(g16, _host(items, "guide")):
+        assert np.array_equal(a, c)
+    with pytest.raises(lib.NslError):
+        b.set_march_tile(6)
+    b.set_march_tile(8)
     # another segment length groups the per-segment in-scattering partial sums
     # differently: the guide moves by rounding only, the lightmaps by what
     # the network makes of that; the same tuning again is bitwise identical
