@@ -1011,11 +1011,28 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         ms = float(np.mean([a.elapsed_time(c) for a, c in ev]))
+        # the march form the tuner did not pick, timed the same way
+        form = b.get_march_form()
+        b.set_march_form(1 - form)
+        b.capture_graph(items, prec, stream)
+        for _ in range(3):
+            b.launch_graph(stream)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        for k in range(nsteps):
+            flush.zero_()
+            ev2[k][0].record(stream)
+            b.launch_graph(stream)
+            ev2[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms_other = float(np.mean([a.elapsed_time(c) for a, c in ev2]))
+        b.set_march_form(form)
+        b.capture_graph(items, prec, stream)
         out[name] = {"value": pixels / (ms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
+                     "ms_per_step_other_march_form": ms_other,
                      "tuning": {"seg_len": tuning[0], "march_blocks_per_sm": tuning[1],
                                 "conv_ctas_per_sm": tuning[2], "march_tile_width": b.get_march_tile(),
-                                "autotune_ms": tune_ms},
-                     "launches_per_step": 1 + 3 + 21 + 1}
+                                "persistent_march": b.get_march_form(), "autotune_ms": tune_ms},
+                     "launches_per_step": 1 + (1 if b.get_march_form() else 3) + 21 + 1}
     b.close()
 
     # the plain single-plume path with the FP32 network on the same plumes

@@ -490,10 +490,22 @@ NSL_API nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* m
  * captured graph. */
 NSL_API nsl_status nsl_batch_set_march_tile(nsl_batch* b, int tile_width);
 NSL_API nsl_status nsl_batch_get_march_tile(const nsl_batch* b, int* tile_width);
+/* Launch form of the batched march: persistent = 1 (the default) runs the view
+ * pass, the segment pass and the finish pass in one cooperative launch of
+ * resident CTAs separated by grid-wide barriers (each wait bounded at about
+ * 2 s; a barrier that gives up records an error that the next render reports
+ * as NSL_ERR_TIMEOUT); persistent = 0 runs them as three launches.  Results
+ * are bitwise the same.  A cooperative launch needs every one of its CTAs
+ * resident at once, so batches rendered concurrently on several streams (as a
+ * server's slots are) use the three-launch form.  A change drops a captured
+ * graph. */
+NSL_API nsl_status nsl_batch_set_march_form(nsl_batch* b, int persistent);
+NSL_API nsl_status nsl_batch_get_march_form(const nsl_batch* b, int* persistent);
 
 /* Autotuner: renders the batch under each candidate setting of the march's
- * knobs (tile width 8, 4 or 16 x segment length 4, 6 or 8 x march CTAs per
- * SM), then of the convolutions' CTAs per SM (1, 2, 4), times each with CUDA
+ * knobs (launch form persistent or three passes x tile width 8 or 4 x segment
+ * length 4, 6 or 8 x march CTAs per SM), then of the convolutions' CTAs per SM
+ * (1, 2, 4), times each with CUDA
  * events (median of 3) and keeps the fastest.  With
  * a cache path (JSON lines), a result stored for the same batch signature
  * (sizes, steps, precision) is applied without timing and new results are

@@ -71,6 +71,7 @@ struct nsl_batch {
   int seg_blocks_per_sm = 0;       // 0 = occupancy maximum
   int conv_ctas = 4;
   int tile_log2 = kMarchTXLog2;    // march tile: 2^tile_log2 x 2^(5 - tile_log2) pixels
+  int persistent_march = 1;        // 1: the march as one cooperative launch, 0: three passes
   // captured graph
   cudaGraphExec_t exec = nullptr;
   bool capturing = false;
@@ -236,7 +237,10 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
   if (*reinterpret_cast<volatile unsigned int*>(b->err_host) != 0) {
     const unsigned code = *b->err_host;
     *b->err_host = 0;
-    return fail(NSL_ERR_TIMEOUT, "nsl_batch: an earlier tensor-core launch timed out (code 0x%x)", code);
+    // a barrier that gave up may have left its words behind: start them afresh
+    NSL_CUDA_TRY(cudaStreamSynchronize(s));
+    NSL_CUDA_TRY(cudaMemset(b->counter, 0, 256));
+    return fail(NSL_ERR_TIMEOUT, "nsl_batch: an earlier launch timed out waiting (code 0x%x)", code);
   }
   // host slot: the graph's own while capturing, else the next ring slot once
   // the copy that last read it has run
@@ -260,9 +264,14 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
   if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: staging");
   int per_sm = march_segment_blocks_max();
   if (b->seg_blocks_per_sm > 0 && b->seg_blocks_per_sm < per_sm) per_sm = b->seg_blocks_per_sm;
-  e = launch_march_segmented_batch(b->dev->march, b->dev->tile_starts, b->dev->item_starts,
-                                   b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
-                                   per_sm * num_sms(), b->counter, s);
+  if (b->persistent_march)
+    e = launch_march_persistent_batch(b->dev->march, b->dev->tile_starts, b->dev->item_starts, b->dev->tile_counts,
+                                      n, T.tile_starts[n], T.item_starts[n], per_sm * num_sms(),
+                                      reinterpret_cast<unsigned*>(b->counter), b->err_dev, s);
+  else
+    e = launch_march_segmented_batch(b->dev->march, b->dev->tile_starts, b->dev->item_starts,
+                                     b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
+                                     per_sm * num_sms(), b->counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: march");
   const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
   if (!b->wtc[elem]) {
@@ -346,6 +355,7 @@ nsl_status nsl_batch_create(const void* blob, size_t blob_bytes, int max_plumes,
   }
   if ((e = cudaMalloc(reinterpret_cast<void**>(&b->dev), sizeof(Tables))) != cudaSuccess ||
       (e = cudaMalloc(reinterpret_cast<void**>(&b->counter), 256)) != cudaSuccess ||
+      (e = cudaMemset(b->counter, 0, 256)) != cudaSuccess ||
       (e = cudaHostAlloc(reinterpret_cast<void**>(&b->err_host), sizeof(unsigned int), cudaHostAllocMapped)) != cudaSuccess) {
     nsl_batch_destroy(b);
     return cuda_fail(e, "nsl_batch_create: allocation");
@@ -489,6 +499,23 @@ nsl_status nsl_batch_set_march_tile(nsl_batch* b, int tile_width) {
   return NSL_OK;
 }
 
+nsl_status nsl_batch_set_march_form(nsl_batch* b, int persistent) {
+  if (!b || (persistent != 0 && persistent != 1))
+    return fail(NSL_ERR_INVALID_ARG, "nsl_batch_set_march_form: NULL batch or form not 0 / 1");
+  if (persistent != b->persistent_march) {
+    cudaDeviceSynchronize();
+    drop_graph(b);
+  }
+  b->persistent_march = persistent;
+  return NSL_OK;
+}
+
+nsl_status nsl_batch_get_march_form(const nsl_batch* b, int* persistent) {
+  if (!b || !persistent) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_get_march_form: NULL argument");
+  *persistent = b->persistent_march;
+  return NSL_OK;
+}
+
 nsl_status nsl_batch_get_march_tile(const nsl_batch* b, int* tile_width) {
   if (!b || !tile_width) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_get_march_tile: NULL argument");
   *tile_width = 1 << b->tile_log2;
@@ -505,8 +532,9 @@ nsl_status nsl_batch_get_tuning(const nsl_batch* b, int* seg_len, int* march_blo
   return NSL_OK;
 }
 
-// Autotuner: time each candidate of the march (tile shape x segment length x
-// march blocks per SM), then of the convolutions' CTAs per SM, on this batch
+// Autotuner: time each candidate of the march (one persistent launch or three
+// passes x tile shape x segment length x march blocks per SM), then of the
+// convolutions' CTAs per SM, on this batch
 // with CUDA events (median of 3 after one warm-up) and keep the fastest; with a
 // cache path, a result recorded for the same batch signature is reused and new
 // results are appended.
@@ -537,15 +565,16 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
       char line[256];
       while (std::fgets(line, sizeof line, f)) {
         char k2[32];
-        int a, c, d, tw;
+        int a, c, d, tw, pf;
         float ms;
         if (std::sscanf(line, " {\"key\": \"%31[0-9a-f]\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
-                              "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"ms\": %f}", k2, &a, &c, &d,
-                        &tw, &ms) == 6 &&
+                              "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"persistent_march\": %d, "
+                              "\"ms\": %f}", k2, &a, &c, &d, &tw, &pf, &ms) == 7 &&
             std::strcmp(k2, key) == 0) {
           std::fclose(f);
           if (best_ms) *best_ms = ms;
           nsl_status st = nsl_batch_set_march_tile(b, tw);
+          if (st == NSL_OK) st = nsl_batch_set_march_form(b, pf);
           return st == NSL_OK ? nsl_batch_set_tuning(b, a, c, d) : st;
         }
       }
@@ -554,7 +583,8 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   }
   const int seg_lens[] = {4, 6, 8};
   const int conv_ctas[] = {1, 2, 4};
-  const int tiles[] = {8, 4, 16};
+  const int tiles[] = {8, 4};
+  const int forms[] = {1, 0};
   const int occ = march_segment_blocks_max();
   std::vector<int> march_bps = {0};
   for (int v : {5, 6}) if (v < occ) march_bps.push_back(v);
@@ -562,7 +592,8 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   NSL_CUDA_TRY(cudaEventCreate(&e0));
   NSL_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bs = b->seg_len, bm = b->seg_blocks_per_sm, bc = b->conv_ctas, bt = 1 << b->tile_log2;
+  int bs = b->seg_len, bm = b->seg_blocks_per_sm, bc = b->conv_ctas, bt = 1 << b->tile_log2,
+      bf = b->persistent_march;
   nsl_status st = NSL_OK;
   // median of three timed renders after one warm-up
   auto time_it = [&](float* med) {
@@ -580,16 +611,19 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   // the march's knobs (tile shape, segment length, CTAs per SM) with the
   // network's at their current value, then the network's CTAs per SM: the two
   // stages do not interact
-  for (int tw : tiles)
-    for (int sl : seg_lens)
-      for (int mb : march_bps) {
-        nsl_batch_set_march_tile(b, tw);
-        nsl_batch_set_tuning(b, sl, mb, bc);
-        float med;
-        time_it(&med);
-        if (st != NSL_OK) break;
-        if (med < best) { best = med; bs = sl; bm = mb; bt = tw; }
-      }
+  for (int pf : forms)
+    for (int tw : tiles)
+      for (int sl : seg_lens)
+        for (int mb : march_bps) {
+          nsl_batch_set_march_form(b, pf);
+          nsl_batch_set_march_tile(b, tw);
+          nsl_batch_set_tuning(b, sl, mb, bc);
+          float med;
+          time_it(&med);
+          if (st != NSL_OK) break;
+          if (med < best) { best = med; bs = sl; bm = mb; bt = tw; bf = pf; }
+        }
+  nsl_batch_set_march_form(b, bf);
   nsl_batch_set_march_tile(b, bt);
   for (int cc : conv_ctas) {
     if (st != NSL_OK) break;
@@ -607,8 +641,8 @@ nsl_status nsl_batch_autotune(nsl_batch* b, const nsl_plume* plumes, int n,
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
       std::fprintf(f, "{\"key\": \"%s\", \"seg_len\": %d, \"march_blocks_per_sm\": %d, "
-                      "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"ms\": %.4f}\n", key, bs, bm, bc, bt,
-                   best);
+                      "\"conv_ctas_per_sm\": %d, \"march_tile_width\": %d, \"persistent_march\": %d, "
+                      "\"ms\": %.4f}\n", key, bs, bm, bc, bt, bf, best);
       std::fclose(f);
     }
   }

@@ -483,14 +483,14 @@ __device__ __forceinline__ void march_segment(const MarchPlume& P, int i, int j,
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
   const int S = P.seg_len;
-  const int nef = P.seg_nef[pix];
+  const int nef = __ldcg(P.seg_nef + pix);
   const int first = seg * S + 1;
   if (first > nef) return;
   const int last = min(first + S - 1, nef);
   const G g = plume_grid<G>(P);
   const Ray r = ray_setup(P, g, i, j);
   const size_t k = (size_t)seg * plane + pix;
-  float tau = P.seg_tau[k], tc = P.seg_comp[k];
+  float tau = __ldcg(P.seg_tau + k), tc = __ldcg(P.seg_comp + k);
   float T = expf(-tau);
   float L = 0.f, Lc = 0.f;
   unsigned long long nsamp = 0;
@@ -507,9 +507,9 @@ __device__ __forceinline__ void march_finish_pixel(const MarchPlume& P, int i, i
   const CamFrame& c = P.cam;
   const size_t plane = (size_t)c.W * c.H;
   const size_t pix = (size_t)j * c.W + i;
-  const int nseg = (P.seg_nef[pix] + P.seg_len - 1) / P.seg_len;
+  const int nseg = (__ldcg(P.seg_nef + pix) + P.seg_len - 1) / P.seg_len;
   float L = 0.f, Lc = 0.f;
-  for (int s = 0; s < nseg; ++s) kahan_add(L, Lc, P.seg_L[(size_t)s * plane + pix]);
+  for (int s = 0; s < nseg; ++s) kahan_add(L, Lc, __ldcg(P.seg_L + (size_t)s * plane + pix));
   P.guide[pix] = L;
 }
 
@@ -749,6 +749,128 @@ cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int*
     return e;
   return launch_pdl(march_pass_batch_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, table_dev,
                     tile_starts_dev, nplumes, total_tiles, counter);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): the last CTA
+// to arrive resets the arrival count and advances the generation; the others
+// wait for the generation to move, for at most ~2 s of clock64, after which
+// they record code 0x200 in the error word and return false (no hang).  The
+// fences order each phase's stores before the arrival and the next phase's
+// loads after it; the scratch written by another CTA is read through L2.
+__device__ __forceinline__ bool grid_barrier(unsigned* __restrict__ count, unsigned* gen, unsigned* err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(count, 1u) + 1u == gridDim.x) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (atomicAdd(gen, 0u) == g) {
+        if (clock64() - t0 > 4000000000LL) {
+          ok = 0;
+          if (err) atomicOr_system(err, 0x200u);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// The segment pass of the persistent batched march, kept out of line so that
+// its shadow loop gets the register budget of the separate segment kernel.
+__device__ __noinline__ void persistent_segment_phase(const MarchPlume* __restrict__ table,
+                                                      const int* __restrict__ item_starts,
+                                                      const int* __restrict__ tile_counts, int nplumes, int nitems,
+                                                      unsigned* __restrict__ queue) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= (unsigned)nitems) break;
+    const int k = find_start(item_starts, nplumes, (int)item);
+    const MarchPlume& P = table[k];
+    const int local = (int)item - __ldg(item_starts + k), nt = __ldg(tile_counts + k);
+    const int seg = local / nt, tile = local % nt;
+    const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+    const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
+    if (i < P.cam.W && j < P.cam.H) {
+      if (P.staged_half) march_segment<false, false, GridH>(P, i, j, seg);
+      else march_segment<false>(P, i, j, seg);
+    }
+  }
+}
+
+// The batched march in one persistent launch: the view pass over every
+// plume's tiles (grid-stride), a grid-wide barrier, the segment pass from the
+// work queue, a barrier, the finish pass.  sync[0] is the work queue, sync[1]
+// and sync[2] the barrier's arrival count and generation.
+__global__ void __launch_bounds__(kMarchThreads, kMarchMinBlocks) march_persistent_batch_kernel(
+    const MarchPlume* __restrict__ table, const int* __restrict__ tile_starts, const int* __restrict__ item_starts,
+    const int* __restrict__ tile_counts, int nplumes, int total_tiles, int nitems, unsigned* __restrict__ sync,
+    unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = kMarchThreads / 32, w0 = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sync[0] = 0u;
+  for (int gt = w0; gt < total_tiles; gt += nw) {
+    const int k = find_start(tile_starts, nplumes, gt);
+    const MarchPlume& P = table[k];
+    const int tile = gt - __ldg(tile_starts + k);
+    const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+    const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
+    if (i < P.cam.W && j < P.cam.H) {
+      if (P.staged_half) march_view_pixel<GridH>(P, i, j);
+      else march_view_pixel(P, i, j);
+    }
+  }
+  if (!grid_barrier(sync + 1, sync + 2, err)) return;
+  persistent_segment_phase(table, item_starts, tile_counts, nplumes, nitems, sync);
+  if (!grid_barrier(sync + 1, sync + 2, err)) return;
+  for (int gt = w0; gt < total_tiles; gt += nw) {
+    const int k = find_start(tile_starts, nplumes, gt);
+    const MarchPlume& P = table[k];
+    const int tile = gt - __ldg(tile_starts + k);
+    const int i = ((tile % P.tiles_x) << P.tx_log2) + (lane & ((1 << P.tx_log2) - 1));
+    const int j = ((tile / P.tiles_x) << (5 - P.tx_log2)) + (lane >> P.tx_log2);
+    if (i < P.cam.W && j < P.cam.H) march_finish_pixel(P, i, j);
+  }
+}
+
+// CTAs of the persistent batched march resident at once on the whole GPU.
+int march_persistent_blocks_max() {
+  static const int blocks = resident_blocks(march_persistent_batch_kernel);
+  return blocks;
+}
+
+cudaError_t launch_march_persistent_batch(const MarchPlume* table_dev, const int* tile_starts_dev,
+                                          const int* item_starts_dev, const int* tile_counts_dev, int nplumes,
+                                          int total_tiles, int total_items, int blocks, unsigned* sync,
+                                          unsigned* err, cudaStream_t s) {
+  if (total_tiles == 0) return cudaSuccess;
+  const int most = march_persistent_blocks_max();
+  if (blocks < 1 || blocks > most) blocks = most;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kMarchThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, march_persistent_batch_kernel, table_dev, tile_starts_dev, item_starts_dev,
+                            tile_counts_dev, nplumes, total_tiles, total_items, sync, err);
 }
 
 int march_segment_blocks_max() {

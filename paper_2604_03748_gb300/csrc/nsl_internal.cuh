@@ -207,6 +207,15 @@ cudaError_t launch_march_segmented_batch(const MarchPlume* table_dev, const int*
                                          int nplumes, int total_tiles, int total_items,
                                          int seg_blocks, int* counter, cudaStream_t s);
 int march_segment_blocks_max();
+// the batched march as one cooperative persistent launch (view pass, barrier,
+// segment pass, barrier, finish pass); sync: three zero-initialised words
+// (work queue, barrier arrivals, barrier generation); blocks <= 0 or above
+// march_persistent_blocks_max(): every resident CTA
+int march_persistent_blocks_max();
+cudaError_t launch_march_persistent_batch(const MarchPlume* table_dev, const int* tile_starts_dev,
+                                          const int* item_starts_dev, const int* tile_counts_dev, int nplumes,
+                                          int total_tiles, int total_items, int blocks, unsigned* sync,
+                                          unsigned* err, cudaStream_t s);
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
                                int* tile_counter, cudaStream_t s);
 

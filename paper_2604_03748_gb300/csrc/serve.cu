@@ -432,6 +432,9 @@ nsl_status nsl_server_create(const void* blob, size_t blob_bytes, const nsl_serv
   S->slots.resize(o.streams);
   for (Slot& sl : S->slots) {
     nsl_status st = nsl_batch_create(blob, blob_bytes, o.max_batch, &sl.batch);
+    // slots run concurrently: the march in three ordinary passes, since a
+    // cooperative launch occupies every SM until all its CTAs fit at once
+    if (st == NSL_OK) st = nsl_batch_set_march_form(sl.batch, 0);
     if (st == NSL_OK && ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
                          (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess))
       st = cuda_fail(e, "nsl_server_create: stream");

@@ -35,7 +35,7 @@ EXPORTS = ["nsl_default_march_opts", "nsl_create", "nsl_destroy", "nsl_stage_gri
            "nsl_lightmap_trace_bytes", "nsl_measure_peaks", "nsl_reference_lightmaps",
            "nsl_default_train_opts", "nsl_trainer_create", "nsl_trainer_step", "nsl_trainer_gradients",
            "nsl_trainer_get_blob", "nsl_trainer_destroy", "nsl_trainer_set_lr", "nsl_batch_set_march_tile",
-           "nsl_batch_get_march_tile"]
+           "nsl_batch_get_march_tile", "nsl_batch_set_march_form", "nsl_batch_get_march_form"]
 
 
 class nsl_grid_desc(C.Structure):
@@ -170,12 +170,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.nsl_batch_get_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.nsl_batch_set_march_tile.argtypes = [vp, i]
     lib.nsl_batch_get_march_tile.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.nsl_batch_set_march_form.argtypes = [vp, i]
+    lib.nsl_batch_get_march_form.argtypes = [vp, C.POINTER(C.c_int)]
     lib.nsl_batch_autotune.argtypes = [vp, C.POINTER(nsl_plume), i, C.POINTER(nsl_march_opts), i,
                                        C.c_char_p, vp, C.POINTER(C.c_float)]
     for name in ("nsl_batch_create", "nsl_batch_render", "nsl_batch_capture_graph",
                  "nsl_batch_update_graph", "nsl_batch_launch_graph", "nsl_batch_set_tuning",
                  "nsl_batch_get_tuning", "nsl_batch_autotune", "nsl_batch_set_march_tile",
-                 "nsl_batch_get_march_tile"):
+                 "nsl_batch_get_march_tile", "nsl_batch_set_march_form", "nsl_batch_get_march_form"):
         getattr(lib, name).restype = C.c_int
     lib.nsl_default_server_opts.argtypes = [C.POINTER(nsl_server_opts)]
     lib.nsl_default_server_opts.restype = None
@@ -649,6 +651,14 @@ class Batch:
         w = C.c_int()
         check(load().nsl_batch_get_march_tile(self.b, C.byref(w)), "nsl_batch_get_march_tile")
         return int(w.value)
+
+    def set_march_form(self, persistent):
+        check(load().nsl_batch_set_march_form(self.b, int(persistent)), "nsl_batch_set_march_form")
+
+    def get_march_form(self):
+        v = C.c_int()
+        check(load().nsl_batch_get_march_form(self.b, C.byref(v)), "nsl_batch_get_march_form")
+        return int(v.value)
 
     def autotune(self, plumes, precision, cache_path=None, opts=None, stream=None):
         arr = plume_array(plumes)

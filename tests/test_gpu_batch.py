@@ -229,12 +229,14 @@ def test_batch_autotune_and_cache(lib, tmp_path):
     # the cached entry is applied without timing: plant a marker time and tuning
     import json
     rec = json.loads(lines[0])
-    assert rec["march_tile_width"] in (4, 8, 16)
-    rec.update(seg_len=8, march_blocks_per_sm=4, conv_ctas_per_sm=1, march_tile_width=16, ms=123.5)
+    assert rec["march_tile_width"] in (4, 8) and rec["persistent_march"] in (0, 1)
+    rec.update(seg_len=8, march_blocks_per_sm=4, conv_ctas_per_sm=1, march_tile_width=16, persistent_march=0,
+               ms=123.5)
     with open(cache, "w") as f:
         f.write(json.dumps(rec) + "\n")
     ms2 = b.autotune(items, 3, cache_path=cache)
     assert abs(ms2 - 123.5) < 1e-3 and b.get_tuning() == (8, 4, 1) and b.get_march_tile() == 16
+    assert b.get_march_form() == 0
     # every pixel marches the same whatever the warp's tile: bitwise equal guides
     b.render(items, 3)
     g16 = _host(items, "guide")
@@ -284,4 +286,36 @@ def test_batch_errors(lib):
         b.render(bad, 3)
     b.render(items, 3)                              # still usable
     torch.cuda.synchronize()
+    b.close()
+
+
+def test_persistent_march_equals_three_passes(lib):
+    """The batched march as one cooperative launch with grid-wide barriers gives
+    bitwise the guides (and so the lightmaps) of its three-launch form, with
+    float16 and float32 grids, and inside a captured graph."""
+    import torch
+    frames = _frames()
+    b = lib.Batch(I.pack_blob(I.make_params(C0, seed=0), C0), max_plumes=len(frames))
+    items = _device_plumes(frames)
+    b.set_march_form(0)
+    b.render(items, 3)
+    ref = _host(items, "guide"), _host(items, "lightmaps")
+    b.set_march_form(1)
+    assert b.get_march_form() == 1
+    for _ in range(2):                       # twice: the barrier words are reused
+        b.render(items, 3)
+        got = _host(items, "guide"), _host(items, "lightmaps")
+        for r, g in zip(ref, got):
+            assert all(np.array_equal(a, c) for a, c in zip(r, g))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.capture_graph(items, 3, stream)
+        for it in items:
+            it["guide"].zero_()
+        b.launch_graph(stream)
+    stream.synchronize()
+    for a, c in zip(ref[0], _host(items, "guide")):
+        assert np.array_equal(a, c)
+    with pytest.raises(lib.NslError):
+        b.set_march_form(2)
     b.close()
