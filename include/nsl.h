@@ -545,6 +545,9 @@ typedef struct {
                                       oldest runnable request is always taken, later ones
                                       only while the batch stays under the cap, so a few
                                       large frames do not hold many small ones back */
+  size_t small_first_pixels;       /* requests of at most this many pixels are taken
+                                      into a forming batch before larger ones (0: plain
+                                      arrival order); a plume's requests keep their order */
 } nsl_server_opts;
 
 typedef struct {
@@ -561,7 +564,8 @@ typedef struct {
 } nsl_server_stats;
 
 /* Defaults: 40 GiB budget, 2 streams, batches of up to 64 requests and
- * 1 Mi billboard pixels, FP16 network. */
+ * 1 Mi billboard pixels, requests of up to 256 x 256 pixels first, FP16
+ * network. */
 NSL_API void nsl_default_server_opts(nsl_server_opts* o);
 NSL_API nsl_status nsl_server_create(const void* weights_blob, size_t blob_bytes,
                                      const nsl_server_opts* opts, nsl_server** out);

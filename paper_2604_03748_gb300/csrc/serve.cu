@@ -225,37 +225,58 @@ void fail_request(nsl_server* S, uint64_t id, nsl_status st, const std::string& 
 bool launch_batch(nsl_server* S, Slot& sl) {
   std::vector<uint64_t> pick;
   std::vector<int> picked;
+  std::vector<char> taken(S->queue.size(), 0);
   size_t seg = 0, net = 0, pix = 0;
-  for (uint64_t id : S->queue) {
-    if ((int)pick.size() >= S->o.max_batch) break;
-    Req& r = S->reqs[id];
-    PlumeRec& p = S->plumes[r.plume];
-    if (p.busy) continue;  // running elsewhere, or already in this batch: keeps per-plume order
-    size_t sb, nb;
-    const nsl_plume q = plume_of(p, r);
-    batch_plume_scratch(q, S->seg_len, &sb, &nb);
-    const size_t rpix = (size_t)r.cam.width * r.cam.height;
-    if (seg + sb > S->seg_cap || net + nb > S->net_cap ||
-        (!pick.empty() && S->o.max_batch_pixels && pix + rpix > S->o.max_batch_pixels)) {
-      p.busy = true;  // keep later requests of this plume behind this one
-      picked.push_back(-1 - r.plume);
-      continue;
-    }
-    if (!p.resident && !admit(S, r.plume, sl)) {
+  // two scans of the queue in arrival order: the first takes only small
+  // requests (at most small_first_pixels), the second the rest; a plume
+  // whose oldest queued request is passed over in a scan takes no later one
+  // in that scan, which keeps every plume's requests in arrival order
+  const int scans = S->o.small_first_pixels ? 2 : 1;
+  for (int scan = 0; scan < scans; ++scan) {
+    const bool small_only = scans == 2 && scan == 0;
+    size_t qi = 0;
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it, ++qi) {
+      if ((int)pick.size() >= S->o.max_batch) break;
+      if (taken[qi]) continue;
+      const uint64_t id = *it;
+      Req& r = S->reqs[id];
+      PlumeRec& p = S->plumes[r.plume];
+      if (p.busy) continue;  // running elsewhere, already in this batch or held back: keeps per-plume order
+      const size_t rpix = (size_t)r.cam.width * r.cam.height;
+      if (small_only && rpix > S->o.small_first_pixels) {
+        p.busy = true;       // its later requests wait for this one
+        picked.push_back(-1 - r.plume);
+        continue;
+      }
+      size_t sb, nb;
+      const nsl_plume q = plume_of(p, r);
+      batch_plume_scratch(q, S->seg_len, &sb, &nb);
+      if (seg + sb > S->seg_cap || net + nb > S->net_cap ||
+          (!pick.empty() && S->o.max_batch_pixels && pix + rpix > S->o.max_batch_pixels)) {
+        p.busy = true;  // keep later requests of this plume behind this one
+        picked.push_back(-1 - r.plume);
+        continue;
+      }
+      if (!p.resident && !admit(S, r.plume, sl)) {
+        p.busy = true;
+        picked.push_back(-1 - r.plume);
+        continue;
+      }
       p.busy = true;
-      picked.push_back(-1 - r.plume);
-      continue;
+      picked.push_back(r.plume);
+      pick.push_back(id);
+      taken[qi] = 1;
+      seg += sb;
+      net += nb;
+      pix += rpix;
     }
-    p.busy = true;
-    picked.push_back(r.plume);
-    pick.push_back(id);
-    seg += sb;
-    net += nb;
-    pix += rpix;
+    // plumes only held back during this scan become free again
+    for (int& v : picked)
+      if (v < 0) {
+        S->plumes[-1 - v].busy = false;
+        v = INT32_MAX;
+      }
   }
-  // plumes only held back for ordering become free again
-  for (int v : picked)
-    if (v < 0) S->plumes[-1 - v].busy = false;
   if (pick.empty()) return false;
 
   std::vector<nsl_plume> pl;
@@ -391,6 +412,7 @@ void nsl_default_server_opts(nsl_server_opts* o) {
   o->streams = 2;
   o->max_batch = 64;
   o->max_batch_pixels = size_t(1) << 20;
+  o->small_first_pixels = size_t(256) * 256;
   o->precision = NSL_PREC_F16;
   nsl_default_march_opts(&o->march);
 }

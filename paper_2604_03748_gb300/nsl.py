@@ -69,7 +69,7 @@ class nsl_plume(C.Structure):
 class nsl_server_opts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("scratch_bytes_per_stream", C.c_size_t),
                 ("streams", C.c_int), ("max_batch", C.c_int), ("precision", C.c_int),
-                ("march", nsl_march_opts), ("max_batch_pixels", C.c_size_t)]
+                ("march", nsl_march_opts), ("max_batch_pixels", C.c_size_t), ("small_first_pixels", C.c_size_t)]
 
 
 class nsl_server_stats(C.Structure):

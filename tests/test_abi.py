@@ -68,8 +68,8 @@ def test_create_rejects_grids_past_32_bit_cell_indices_without_touching_the_gpu(
 def test_default_options_without_gpu():
     """Documented defaults: t_min 1e-4 (early termination), tau_depth 0.01,
     jitter on, unit surrogate intensities, HG g = 0, front/top/bottom lights;
-    the server's 40 GiB budget, 2 streams, batches of up to 64 requests and 1 Mi pixels,
-    FP16 network."""
+    the server's 40 GiB budget, 2 streams, batches of up to 64 requests and 1 Mi pixels
+    with requests of up to 256^2 pixels first, FP16 network."""
     from paper_2604_03748_gb300 import nsl
     o = nsl.march_opts()
     assert o.t_min == pytest.approx(1e-4) and o.tau_depth == pytest.approx(0.01)
@@ -78,7 +78,7 @@ def test_default_options_without_gpu():
     assert o.segment_exact == 0 and o.light_set == nsl.NSL_LIGHTS_FTB and o.shadow_volume == 0
     s = nsl.server_opts()
     assert s.hbm_budget_bytes == 40 << 30 and s.streams == 2 and s.max_batch == 64
-    assert s.max_batch_pixels == 1 << 20
+    assert s.max_batch_pixels == 1 << 20 and s.small_first_pixels == 256 * 256
     assert s.precision == nsl.NSL_PREC_F16 and s.scratch_bytes_per_stream == 0
     assert s.march.t_min == pytest.approx(1e-4) and s.march.jitter == 1
 
