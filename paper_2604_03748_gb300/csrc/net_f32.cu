@@ -74,11 +74,36 @@ __device__ __forceinline__ float load_in(const ConvArgs& a, int y, int x, int c)
 
 template <int CIN, int MODE, typename TOut>
 __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, int bx, int by,
-                                                 int cg);
+                                                 int cg, int ks = 0, int nks = 1, float* partial = nullptr);
 
+// blockIdx.z = output-channel group x input-channel split: with nks > 1 each
+// block sums CIN / nks input channels and writes its raw partial sums, which
+// conv_split_finish adds in split order (a fixed order: deterministic)
 template <int CIN, int MODE, typename TOut>
-__global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout) {
-  conv3x3_f32_tile<CIN, MODE, TOut>(a, cout, blockIdx.x, blockIdx.y, blockIdx.z);
+__global__ void __launch_bounds__(128) conv3x3_f32_kernel(ConvArgs a, int cout, int nks, float* partial) {
+  conv3x3_f32_tile<CIN, MODE, TOut>(a, cout, blockIdx.x, blockIdx.y, blockIdx.z / nks, blockIdx.z % nks, nks,
+                                    partial);
+}
+
+// out = ReLU(bias + sum over the nks partial sums, in split order), float4 of
+// channels per thread; partial [nks][H*W][cout]
+__global__ void __launch_bounds__(256) conv_split_finish(const float* __restrict__ partial, int nks,
+                                                         const float* __restrict__ bias, float* __restrict__ out,
+                                                         int P, int cout) {
+  const int n4 = P * cout / 4;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += gridDim.x * blockDim.x) {
+    float4 acc = reinterpret_cast<const float4*>(partial)[e];
+    for (int k = 1; k < nks; ++k) {
+      const float4 v = reinterpret_cast<const float4*>(partial)[(size_t)k * n4 + e];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    const int c = (4 * e) % cout;
+    acc.x = fmaxf(acc.x + __ldg(bias + c), 0.f);
+    acc.y = fmaxf(acc.y + __ldg(bias + c + 1), 0.f);
+    acc.z = fmaxf(acc.z + __ldg(bias + c + 2), 0.f);
+    acc.w = fmaxf(acc.w + __ldg(bias + c + 3), 0.f);
+    reinterpret_cast<float4*>(out)[e] = acc;
+  }
 }
 
 // grouped first layer: 16x16 tiles numbered image after image
@@ -104,7 +129,7 @@ __global__ void __launch_bounds__(128) first_conv_group_kernel(const __grid_cons
 
 template <int CIN, int MODE, typename TOut>
 __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, int bx, int by,
-                                                 int cg) {
+                                                 int cg, int ks, int nks, float* partial) {
   constexpr int CT = CIN < 16 ? CIN : 16;  // input-channel chunk
   __shared__ float halo[CT * kHaloStride];
   __shared__ __align__(16) float ws[CT * 9 * 16];
@@ -115,7 +140,8 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
 #pragma unroll
   for (int o = 0; o < 16; ++o) { acc0[o] = 0.f; acc1[o] = 0.f; }
 
-  for (int c0 = 0; c0 < CIN; c0 += CT) {
+  const int cbeg = CIN / nks * ks, cend = CIN / nks * (ks + 1);
+  for (int c0 = cbeg; c0 < cend; c0 += CT) {
     __syncthreads();
     for (int e = tid; e < CT * kHaloPix; e += 128) {
       int c = e % CT, hp = e / CT;
@@ -170,6 +196,19 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
     }
   }
   if (x >= a.W) return;
+  if (nks > 1) {   // raw partial sums of this split
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int y = y0 + ty + r;
+      if (y >= a.H) continue;
+      float* dst = partial + ((size_t)ks * a.H * a.W + (size_t)y * a.W + x) * cout + cg * 16;
+      const float* acc = r ? acc1 : acc0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    return;
+  }
   const float* bias = a.b + cg * 16;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -325,7 +364,13 @@ void net_f32_destroy(NetF32Weights* w) {
 // workspace carve-up (floats), P = max pixels
 struct F32Buffers {
   float *fa, *fb, *s1, *l1a, *l1b, *s2, *l2a, *l2b, *s3, *l3a, *l3b, *x1, *partial, *att;
+  float* split;         // input-channel split partial sums of the low-resolution layers
+  size_t split_floats;
 };
+
+// floats of the split partial sums (64 B per pixel of the largest image plus
+// 4 MiB): conv() splits a layer only as far as nks * pixels * cout fits
+static size_t split_capacity(size_t P) { return P * 16 + ((size_t)1 << 20); }
 
 static size_t carve(size_t P, F32Buffers* b, char* base) {
   size_t off = 0;
@@ -341,6 +386,8 @@ static size_t carve(size_t P, F32Buffers* b, char* base) {
   b->x1 = take(P * 64);
   b->partial = take(adapter_partial_floats((int)P, 1) + (P / 128 + 1024) * 64);
   b->att = take(64);
+  b->split_floats = split_capacity(P);
+  b->split = take(b->split_floats);
   return off;
 }
 
@@ -349,10 +396,27 @@ size_t net_f32_workspace_bytes(int max_w, int max_h) {
   return carve((size_t)max_w * max_h, &b, nullptr);
 }
 
+// A layer whose tiles and output-channel groups give fewer than two blocks per
+// SM splits its input channels over up to CIN / 16 blocks (powers of two),
+// then conv_split_finish adds the partial sums: the low-resolution layers of a
+// small image otherwise run a handful of blocks through long channel loops.
 template <int CIN, int MODE, typename TOut = float>
-static cudaError_t conv(const ConvArgs& a, int cout, cudaStream_t s) {
-  dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH, cout / 16);
-  conv3x3_f32_kernel<CIN, MODE, TOut><<<grid, 128, 0, s>>>(a, cout);
+static cudaError_t conv(const ConvArgs& a, int cout, cudaStream_t s, float* split = nullptr,
+                        size_t split_floats = 0) {
+  const int tiles = ((a.W + kTW - 1) / kTW) * ((a.H + kTH - 1) / kTH);
+  const size_t P = (size_t)a.W * a.H;
+  int nks = 1;
+  if (sizeof(TOut) == 4 && CIN >= 32 && split)
+    while (tiles * (cout / 16) * nks < 2 * num_sms() && 2 * nks <= CIN / 16 &&
+           (size_t)(2 * nks) * P * cout <= split_floats)
+      nks *= 2;
+  dim3 grid((a.W + kTW - 1) / kTW, (a.H + kTH - 1) / kTH, cout / 16 * nks);
+  conv3x3_f32_kernel<CIN, MODE, TOut><<<grid, 128, 0, s>>>(a, cout, nks, split);
+  if (nks > 1) {
+    int blocks = (int)((P * cout / 4 + 255) / 256);
+    if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+    conv_split_finish<<<blocks, 256, 0, s>>>(split, nks, a.b, static_cast<float*>(a.out), (int)P, cout);
+  }
   return cudaGetLastError();
 }
 
@@ -424,20 +488,20 @@ cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* w
   TRY((conv<3, IN_GUIDE>(A(img.guide, nullptr, 0, B.fa, H, W), 16, s)));
   TRY((conv<16, IN_PLAIN>(A(B.fa, nullptr, 1, B.s1, H, W), 16, s)));
   TRY((conv<16, IN_POOL>(A(B.s1, nullptr, 2, B.l1a, H1, W1), 32, s)));
-  TRY((conv<32, IN_PLAIN>(A(B.l1a, nullptr, 3, B.s2, H1, W1), 32, s)));
-  TRY((conv<32, IN_POOL>(A(B.s2, nullptr, 4, B.l2a, H2, W2), 64, s)));
-  TRY((conv<64, IN_PLAIN>(A(B.l2a, nullptr, 5, B.s3, H2, W2), 64, s)));
-  TRY((conv<64, IN_POOL>(A(B.s3, nullptr, 6, B.l3a, H3, W3), 128, s)));
-  TRY((conv<128, IN_PLAIN>(A(B.l3a, nullptr, 7, B.l3b, H3, W3), 128, s)));
+  TRY((conv<32, IN_PLAIN>(A(B.l1a, nullptr, 3, B.s2, H1, W1), 32, s, B.split, B.split_floats)));
+  TRY((conv<32, IN_POOL>(A(B.s2, nullptr, 4, B.l2a, H2, W2), 64, s, B.split, B.split_floats)));
+  TRY((conv<64, IN_PLAIN>(A(B.l2a, nullptr, 5, B.s3, H2, W2), 64, s, B.split, B.split_floats)));
+  TRY((conv<64, IN_POOL>(A(B.s3, nullptr, 6, B.l3a, H3, W3), 128, s, B.split, B.split_floats)));
+  TRY((conv<128, IN_PLAIN>(A(B.l3a, nullptr, 7, B.l3b, H3, W3), 128, s, B.split, B.split_floats)));
   // decoder
   TRY(convT<128>(B.l3b, w->up_w[0], w->up_b[0], B.l2a, H3, W3, 64, s));
-  TRY((conv<128, IN_CONCAT>(A(B.l2a, B.s3, 8, B.l2b, H2, W2), 64, s)));
-  TRY((conv<64, IN_PLAIN>(A(B.l2b, nullptr, 9, B.l2a, H2, W2), 64, s)));
+  TRY((conv<128, IN_CONCAT>(A(B.l2a, B.s3, 8, B.l2b, H2, W2), 64, s, B.split, B.split_floats)));
+  TRY((conv<64, IN_PLAIN>(A(B.l2b, nullptr, 9, B.l2a, H2, W2), 64, s, B.split, B.split_floats)));
   TRY(convT<64>(B.l2a, w->up_w[1], w->up_b[1], B.l1a, H2, W2, 32, s));
-  TRY((conv<64, IN_CONCAT>(A(B.l1a, B.s2, 10, B.l1b, H1, W1), 32, s)));
-  TRY((conv<32, IN_PLAIN>(A(B.l1b, nullptr, 11, B.l1a, H1, W1), 32, s)));
+  TRY((conv<64, IN_CONCAT>(A(B.l1a, B.s2, 10, B.l1b, H1, W1), 32, s, B.split, B.split_floats)));
+  TRY((conv<32, IN_PLAIN>(A(B.l1b, nullptr, 11, B.l1a, H1, W1), 32, s, B.split, B.split_floats)));
   TRY(convT<32>(B.l1a, w->up_w[2], w->up_b[2], B.fa, H1, W1, 16, s));
-  TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s)));
+  TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s, B.split, B.split_floats)));
   TRY((conv<16, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), 16, s)));
   // adapters
   TRY(adapters_run<float>(w->adp, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
