@@ -208,32 +208,55 @@ __device__ __forceinline__ void load_halo_async(const ConvImg<T>& a, int tile, u
   }
 }
 
+// Synchronous halo loaders (max-pool mode, FP8 path): each thread takes its
+// elements in batches of kLdBatch and issues every global load of a batch
+// before the first use, so it waits for one round of memory latency per batch
+// rather than per element (a low-resolution layer's CTA stages one tile, and
+// those rounds were most of its time).  Out-of-image elements load from a
+// clamped in-image address and are replaced by zeros afterwards, which keeps
+// the loads free of branches.
+constexpr int kLdBatch = 4;
+
+// 8 channels (16 bytes) of halo pixel (y, x), clamped into the image, at
+// channel group g (POOL: the 2x2 max of the finer level)
+template <typename T, int CIN, int MODE>
+__device__ __forceinline__ uint4 halo8(const ConvImg<T>& a, int y, int x, int g) {
+  if constexpr (MODE == TC_PLAIN) {
+    return ldg128(a.inA + ((size_t)y * a.W + x) * CIN + g * 8);
+  } else if constexpr (MODE == TC_CONCAT) {
+    constexpr int G = CIN / 8, CH = CIN / 2;
+    return g < G / 2 ? ldg128(a.inA + ((size_t)y * a.W + x) * CH + g * 8)
+                     : ldg128(a.inB + ((size_t)y * a.W + x) * CH + (g - G / 2) * 8);
+  } else {
+    const size_t W2 = 2 * (size_t)a.W;
+    const T* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 8;
+    return half8_max<T>(half8_max<T>(ldg128(p), ldg128(p + CIN)),
+                        half8_max<T>(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
+  }
+}
+
 template <typename T, int CIN, int MODE>
 __device__ __forceinline__ void load_halo(const ConvImg<T>& a, int tile, uint8_t* halo) {
-  constexpr int G = CIN / 8;
+  constexpr int G = CIN / 8, NE = kHaloPix * G;
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
-  for (int e = threadIdx.x; e < kHaloPix * G; e += blockDim.x) {
-    const int hp = e / G, g = e % G;
-    const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
-      if constexpr (MODE == TC_PLAIN) {
-        v = ldg128(a.inA + ((size_t)y * a.W + x) * CIN + g * 8);
-      } else if constexpr (MODE == TC_CONCAT) {
-        constexpr int CH = CIN / 2;
-        if (g < G / 2)
-          v = ldg128(a.inA + ((size_t)y * a.W + x) * CH + g * 8);
-        else
-          v = ldg128(a.inB + ((size_t)y * a.W + x) * CH + (g - G / 2) * 8);
-      } else {  // TC_POOL: 2x2 max of the finer level
-        const size_t W2 = 2 * (size_t)a.W;
-        const T* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 8;
-        v = half8_max<T>(half8_max<T>(ldg128(p), ldg128(p + CIN)),
-                         half8_max<T>(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
-      }
+  for (int e0 = threadIdx.x; e0 < NE; e0 += kLdBatch * blockDim.x) {
+    uint4 v[kLdBatch];
+    bool in[kLdBatch];
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = min(e0 + b * (int)blockDim.x, NE - 1);
+      const int hp = e / G, g = e % G;
+      const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+      in[b] = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      v[b] = halo8<T, CIN, MODE>(a, min(max(y, 0), a.H - 1), min(max(x, 0), a.W - 1), g);
     }
-    *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = v;
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = e0 + b * (int)blockDim.x;
+      if (e < NE)
+        *reinterpret_cast<uint4*>(halo + (e % G) * kPlane + (e / G) * 16) = in[b] ? v[b] : make_uint4(0, 0, 0, 0);
+    }
   }
 }
 
@@ -241,38 +264,33 @@ __device__ __forceinline__ void load_halo(const ConvImg<T>& a, int tile, uint8_t
 // quantising the FP16 activations with the input tensor's scale on the way.
 template <int CIN, int MODE>
 __device__ __forceinline__ void load_halo_q8(const ConvImg<__half>& a, int tile, uint8_t* halo) {
-  constexpr int GR = CIN / 16;
+  constexpr int GR = CIN / 16, NE = kHaloPix * GR;
   const float am = a.amax_b ? fmaxf(__ldg(a.amax_a), __ldg(a.amax_b)) : __ldg(a.amax_a);
   const float inv = q8_inv(am);
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
-  for (int e = threadIdx.x; e < kHaloPix * GR; e += blockDim.x) {
-    const int hp = e / GR, g = e % GR;
-    const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
-      uint4 lo, hi;
-      if constexpr (MODE == TC_PLAIN) {
-        const __half* p = a.inA + ((size_t)y * a.W + x) * CIN + g * 16;
-        lo = ldg128(p);
-        hi = ldg128(p + 8);
-      } else if constexpr (MODE == TC_CONCAT) {
-        constexpr int CH = CIN / 2;
-        const __half* p = g < GR / 2 ? a.inA + ((size_t)y * a.W + x) * CH + g * 16
-                                     : a.inB + ((size_t)y * a.W + x) * CH + (g - GR / 2) * 16;
-        lo = ldg128(p);
-        hi = ldg128(p + 8);
-      } else {  // TC_POOL
-        const size_t W2 = 2 * (size_t)a.W;
-        const __half* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + g * 16;
-        lo = half8_max<__half>(half8_max<__half>(ldg128(p), ldg128(p + CIN)),
-                               half8_max<__half>(ldg128(p + W2 * CIN), ldg128(p + W2 * CIN + CIN)));
-        hi = half8_max<__half>(half8_max<__half>(ldg128(p + 8), ldg128(p + CIN + 8)),
-                               half8_max<__half>(ldg128(p + W2 * CIN + 8), ldg128(p + W2 * CIN + CIN + 8)));
-      }
-      v = q8_pack16(lo, hi, inv);
+  for (int e0 = threadIdx.x; e0 < NE; e0 += kLdBatch * blockDim.x) {
+    uint4 lo[kLdBatch], hi[kLdBatch];
+    bool in[kLdBatch];
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = min(e0 + b * (int)blockDim.x, NE - 1);
+      const int hp = e / GR, g = e % GR;
+      const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+      in[b] = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const int yc = min(max(y, 0), a.H - 1), xc = min(max(x, 0), a.W - 1);
+      // channels 16g .. 16g+15 are the 8-channel groups 2g and 2g+1 (a
+      // concatenation's halves hold whole 16-channel groups)
+      lo[b] = halo8<__half, CIN, MODE>(a, yc, xc, 2 * g);
+      hi[b] = halo8<__half, CIN, MODE>(a, yc, xc, 2 * g + 1);
     }
-    *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = v;
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = e0 + b * (int)blockDim.x;
+      if (e < NE)
+        *reinterpret_cast<uint4*>(halo + (e % GR) * kPlane + (e / GR) * 16) =
+            in[b] ? q8_pack16(lo[b], hi[b], inv) : make_uint4(0, 0, 0, 0);
+    }
   }
 }
 
@@ -639,21 +657,42 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
       const int lt = tile - im.tile_start;
       const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
       uint8_t* dstb = abuf + buf * Cfg::ABYTES;
-      float inv = 1.f;
-      if constexpr (Q8) inv = q8_inv(__ldg(im.amax_in));
-      for (int e = tid; e < 128 * Cfg::G; e += blockDim.x) {
-        const int m = e / Cfg::G, g = e % Cfg::G;
-        const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (y < im.H && x < im.W) {
-          if constexpr (Q8) {
-            const T* p = im.in + ((size_t)y * im.W + x) * CIN + g * 16;
-            v = q8_pack16(ldg128(p), ldg128(p + 8), inv);
-          } else {
-            v = ldg128(im.in + ((size_t)y * im.W + x) * CIN + g * 8);
+      constexpr int NE = 128 * Cfg::G;
+      if constexpr (Q8) {
+        // loads in batches issued before their first use (see load_halo)
+        const float inv = q8_inv(__ldg(im.amax_in));
+        for (int e0 = tid; e0 < NE; e0 += kLdBatch * blockDim.x) {
+          uint4 lo[kLdBatch], hi[kLdBatch];
+          bool in[kLdBatch];
+#pragma unroll
+          for (int b = 0; b < kLdBatch; ++b) {
+            const int e = min(e0 + b * (int)blockDim.x, NE - 1);
+            const int m = e / Cfg::G, g = e % Cfg::G;
+            const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+            in[b] = y < im.H && x < im.W;
+            const T* p = im.in + ((size_t)min(y, im.H - 1) * im.W + min(x, im.W - 1)) * CIN + g * 16;
+            lo[b] = ldg128(p);
+            hi[b] = ldg128(p + 8);
+          }
+#pragma unroll
+          for (int b = 0; b < kLdBatch; ++b) {
+            const int e = e0 + b * (int)blockDim.x;
+            if (e < NE)
+              *reinterpret_cast<uint4*>(dstb + (e % Cfg::G) * Cfg::APLANE + (e / Cfg::G) * 16) =
+                  in[b] ? q8_pack16(lo[b], hi[b], inv) : make_uint4(0, 0, 0, 0);
           }
         }
-        *reinterpret_cast<uint4*>(dstb + g * Cfg::APLANE + m * 16) = v;
+      } else {
+        // asynchronous 16-byte copies, zeros outside the image
+        for (int e = tid; e < NE; e += blockDim.x) {
+          const int m = e / Cfg::G, g = e % Cfg::G;
+          const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+          const bool in = y < im.H && x < im.W;
+          cp_async16(dstb + g * Cfg::APLANE + m * 16,
+                     im.in + ((size_t)(in ? y : 0) * im.W + (in ? x : 0)) * CIN + g * 8, in ? 16u : 0u);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
       }
     }
     fence_proxy_async();
