@@ -112,6 +112,16 @@ __device__ __forceinline__ void norm16(const float* x, float* y) {
   for (int c = 0; c < C; ++c) y[c] = (x[c] - mu) * inv;
 }
 
+// x1 (the gated depthwise output of the four adapters, 64 channels) is stored
+// as eight planes of 16-byte chunks: plane q holds channels 8q .. 8q+7 of every
+// pixel.  Pass 2's thread-per-pixel loads of one chunk are then 512
+// contiguous bytes per warp, and pass 1's column-per-thread stores of a
+// channel pair span 256 bytes per half-warp (NHWC rows of 128 bytes spread
+// both over 16-32 lines per warp instruction).
+__device__ __forceinline__ size_t x1_index(int npix, int pix, int ch) {
+  return ((size_t)(ch >> 3) * npix + pix) * 8 + (ch & 7);
+}
+
 template <typename TA>
 struct AdGroup {
   AdapterImg<TA> img[kMaxGroup];
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
         for (int y = 0; y < kTH; ++y) {
           if (px < im.W && y0 + y < im.H) {
             __align__(4) __half o[2] = {__float2half_rn(gv[0][y]), __float2half_rn(gv[1][y])};
-            *reinterpret_cast<uint32_t*>(im.x1 + ((size_t)(y0 + y) * im.W + px) * (4 * C) + a * C + j0) =
+            *reinterpret_cast<uint32_t*>(im.x1 + x1_index(im.H * im.W, (y0 + y) * im.W + px, a * C + j0)) =
                 *reinterpret_cast<const uint32_t*>(o);
           }
         }
@@ -389,7 +399,8 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     const int pp = (blk - G.px_start[kk]) * 128 + tid;
     if (pp >= m.H * m.W) return;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) rx[q] = __ldg(reinterpret_cast<const uint4*>(m.x1 + (size_t)pp * (4 * C)) + q);
+    for (int q = 0; q < 8; ++q)
+      rx[q] = __ldg(reinterpret_cast<const uint4*>(m.x1 + x1_index(m.H * m.W, pp, 8 * q)));
 #pragma unroll
     for (int q = 0; q < 2; ++q) rf[q] = __ldg(reinterpret_cast<const uint4*>(m.F + (size_t)pp * C) + q);
   };

@@ -326,7 +326,8 @@ template <typename TA>
 struct AdapterImg {
   const TA* F;
   __half* x1;       // the gated depthwise output: binary16 whatever F's type
-                    // (it is LayerNorm-scaled, well inside the binary16 range)
+                    // (it is LayerNorm-scaled, well inside the binary16 range),
+                    // eight planes of 8 channels x H x W (16 bytes per pixel)
   float* partial;   // per-tile channel sums of this image
   float* att;       // 64 attention values of this image
   float* out;       // [8][H][W]
