@@ -72,6 +72,25 @@ __device__ __forceinline__ float load_in(const ConvArgs& a, int y, int x, int c)
   }
 }
 
+// Four consecutive channels c .. c+3 (c a multiple of 4) at conv-input pixel
+// (y, x), already inside the image (not for IN_GUIDE).
+template <int MODE, int CIN>
+__device__ __forceinline__ float4 load_in4(const ConvArgs& a, int y, int x, int c) {
+  auto ld4 = [](const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); };
+  if constexpr (MODE == IN_PLAIN) {
+    return ld4(a.inA + ((size_t)y * a.W + x) * CIN + c);
+  } else if constexpr (MODE == IN_POOL) {
+    const int W2 = 2 * a.W;
+    const float* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + c;
+    const float4 u0 = ld4(p), u1 = ld4(p + CIN), u2 = ld4(p + (size_t)W2 * CIN), u3 = ld4(p + (size_t)W2 * CIN + CIN);
+    return make_float4(fmaxf(fmaxf(fmaxf(u0.x, u1.x), u2.x), u3.x), fmaxf(fmaxf(fmaxf(u0.y, u1.y), u2.y), u3.y),
+                       fmaxf(fmaxf(fmaxf(u0.z, u1.z), u2.z), u3.z), fmaxf(fmaxf(fmaxf(u0.w, u1.w), u2.w), u3.w));
+  } else {  // IN_CONCAT: a group of four lies within one operand
+    constexpr int CH = CIN / 2;
+    return c < CH ? ld4(a.inA + ((size_t)y * a.W + x) * CH + c) : ld4(a.inB + ((size_t)y * a.W + x) * CH + (c - CH));
+  }
+}
+
 template <int CIN, int MODE, typename TOut>
 __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, int bx, int by,
                                                  int cg, int ks = 0, int nks = 1, float* partial = nullptr);
@@ -143,15 +162,65 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
   const int cbeg = CIN / nks * ks, cend = CIN / nks * (ks + 1);
   for (int c0 = cbeg; c0 < cend; c0 += CT) {
     __syncthreads();
-    for (int e = tid; e < CT * kHaloPix; e += 128) {
-      int c = e % CT, hp = e / CT;
-      int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
-      float v = 0.f;
-      if (y >= 0 && y < a.H && x >= 0 && x < a.W) v = load_in<MODE, CIN>(a, y, x, c0 + c);
-      halo[c * kHaloStride + hp] = v;
+    // Halo and weights of this channel chunk.  Each thread issues its loads in
+    // batches before their first use (one round of memory latency per batch
+    // instead of per element); out-of-image elements load from a clamped
+    // in-image address and are replaced by zeros.
+    if constexpr (CT % 4 == 0 && MODE != IN_GUIDE) {
+      constexpr int NQ = CT / 4, NE = NQ * kHaloPix, NB = MODE == IN_POOL ? 4 : 8;
+      for (int e0 = tid; e0 < NE; e0 += NB * 128) {
+        float4 v[NB];
+        bool in[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int e = min(e0 + b * 128, NE - 1);
+          const int q = e % NQ, hp = e / NQ;
+          const int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
+          in[b] = y >= 0 && y < a.H && x >= 0 && x < a.W;
+          v[b] = load_in4<MODE, CIN>(a, min(max(y, 0), a.H - 1), min(max(x, 0), a.W - 1), c0 + 4 * q);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int e = e0 + b * 128;
+          if (e < NE) {
+            const int q = e % NQ, hp = e / NQ;
+            float* h = halo + 4 * q * kHaloStride + hp;
+            h[0] = in[b] ? v[b].x : 0.f;
+            h[kHaloStride] = in[b] ? v[b].y : 0.f;
+            h[2 * kHaloStride] = in[b] ? v[b].z : 0.f;
+            h[3 * kHaloStride] = in[b] ? v[b].w : 0.f;
+          }
+        }
+      }
+    } else {
+      constexpr int NE = CT * kHaloPix, NB = 8;
+      for (int e0 = tid; e0 < NE; e0 += NB * 128) {
+        float v[NB];
+        bool in[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int e = min(e0 + b * 128, NE - 1);
+          const int c = e % CT, hp = e / CT;
+          const int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
+          in[b] = y >= 0 && y < a.H && x >= 0 && x < a.W;
+          v[b] = load_in<MODE, CIN>(a, min(max(y, 0), a.H - 1), min(max(x, 0), a.W - 1), c0 + c);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const int e = e0 + b * 128;
+          if (e < NE) halo[(e % CT) * kHaloStride + e / CT] = in[b] ? v[b] : 0.f;
+        }
+      }
     }
-    const float* wsrc = a.w + ((size_t)cg * CIN + c0) * 9 * 16;
-    for (int e = tid; e < CT * 9 * 16; e += 128) ws[e] = __ldg(wsrc + e);
+    {
+      constexpr int NW4 = CT * 9 * 4;  // float4 groups of this chunk's weights
+      const float4* wsrc = reinterpret_cast<const float4*>(a.w + ((size_t)cg * CIN + c0) * 9 * 16);
+#pragma unroll
+      for (int k = 0; k < (NW4 + 127) / 128; ++k) {
+        const int e = tid + k * 128;
+        if (e < NW4) reinterpret_cast<float4*>(ws)[e] = __ldg(wsrc + e);
+      }
+    }
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < CT; ++c) {
