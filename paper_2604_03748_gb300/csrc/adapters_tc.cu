@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
 
 #pragma unroll 1
   for (int t = blockIdx.x; ok && t < total; t += gridDim.x) {
+    if (t + (int)gridDim.x >= total) pdl_trigger_last();
     const int k = find_group(G.tile_start, G.nimg, t);
     const AdapterImg<TA>& im = G.img[k];
     const int lt = t - G.tile_start[k];
@@ -410,6 +411,7 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
 
 #pragma unroll 1
   for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
+    if (blk + (int)gridDim.x >= total) pdl_trigger_last();
     const int k = find_group(G.px_start, G.nimg, blk);
     const AdapterImg<TA>& im = G.img[k];
     const int npix = im.H * im.W;

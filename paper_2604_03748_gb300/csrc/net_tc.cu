@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcConvArgs<T> a) {
 #pragma unroll 1
   for (int k = 0; ok && k < nmine; ++k) {
     const int buf = k % S, acc = k & 1;
+    if (k == nmine - 1) pdl_trigger_last();
     cp_async_wait<S - 2>();  // this thread's copies of tile k have landed
     fence_proxy_async();
     tc_fence_before();
@@ -650,6 +651,7 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   };
 
   for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    if (tile + (int)gridDim.x >= ntiles) pdl_trigger_last();
     // stage the 128 input pixels of the patch: plane g holds channels 8g..8g+7
     {
       const int imi = image_of(a, tile);

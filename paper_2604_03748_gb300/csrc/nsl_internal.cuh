@@ -22,10 +22,12 @@ namespace nsl {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 #ifndef NSL_PDL_TRIGGER
-#define NSL_PDL_TRIGGER 2   // 1: successor released once a kernel passed its wait, 2: at its end
+#define NSL_PDL_TRIGGER 2   // 1: successor released once a kernel passed its wait, 2: at its end,
+                            // 3: when each persistent CTA starts its last work item
 #endif
 __device__ __forceinline__ void pdl_trigger() { if (NSL_PDL_TRIGGER == 1) pdl_launch(); }
 __device__ __forceinline__ void pdl_trigger_end() { if (NSL_PDL_TRIGGER == 2) pdl_launch(); }
+__device__ __forceinline__ void pdl_trigger_last() { if (NSL_PDL_TRIGGER == 3) pdl_launch(); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
