@@ -118,8 +118,11 @@ NSL_API void nsl_default_march_opts(nsl_march_opts* out);
  *                 checksum.  Copied; the caller keeps ownership.
  *   max_width, max_height  largest billboard any later call may use; the
  *                 network workspace is allocated for it (device memory).
+ * C0 (the UNet base width, Sec. 4.3: widths C0, 2 C0, 4 C0, 8 C0, adapters of
+ * C0 channels) is 16 or 32; a C0 = 32 context runs the FP32 network only (the
+ * tensor-core precisions of nsl_predict_lightmaps return NSL_ERR_UNSUPPORTED).
  * Returns NSL_ERR_INVALID_ARG for a malformed blob or sizes, NSL_ERR_OOM when
- * device memory runs out, NSL_ERR_UNSUPPORTED for C0 other than 16. */
+ * device memory runs out, NSL_ERR_UNSUPPORTED for C0 other than 16 or 32. */
 NSL_API nsl_status nsl_create(const nsl_grid_desc* grid, const void* weights_blob, size_t blob_bytes,
                       int max_width, int max_height, nsl_ctx** out);
 
@@ -284,7 +287,8 @@ NSL_API nsl_status nsl_reference_lightmaps(nsl_ctx* ctx, const void* density_dev
  *   guide_dev      [3][H][W] float32 guide
  *   width, height  multiples of 8, within the context maximum
  *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16, NSL_PREC_F16 or
- *                  NSL_PREC_FP8 (tensor cores, FP32 accumulation)
+ *                  NSL_PREC_FP8 (tensor cores, FP32 accumulation; C0 = 16
+ *                  contexts only, NSL_ERR_UNSUPPORTED at C0 = 32)
  *   lightmaps_dev  output [8][H][W] float32 planes
  *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
@@ -448,7 +452,8 @@ typedef struct {
 typedef struct nsl_batch nsl_batch;
 
 /* Create a batch context for up to max_plumes (<= 64) plumes per call with
- * the network weights of an NSLW blob (see nsl_create).  Device buffers are
+ * the network weights of an NSLW blob (see nsl_create; C0 = 16 only, other
+ * widths return NSL_ERR_UNSUPPORTED).  Device buffers are
  * sized by the first call and grow when a later call needs more. */
 NSL_API nsl_status nsl_batch_create(const void* weights_blob, size_t blob_bytes, int max_plumes,
                                     nsl_batch** out);

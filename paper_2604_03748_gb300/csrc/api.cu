@@ -97,10 +97,11 @@ bool build_net_layout(int c0, NetLayout* L) {
   up(2, c[1], c[0]); conv(12, c[1], c[0]); conv(13, c[0], c[0]);
   for (int a = 0; a < 4; ++a) {
     L->adapter[a] = off;
-    off += kAdapterParams;
+    off += adapter_param_count(c0);
   }
   L->total = off;
-  return c0 == kC0;
+  L->c0 = c0;
+  return c0 == kC0 || c0 == kWideC0;
 }
 
 }  // namespace nsl
@@ -196,7 +197,7 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
     return fail(NSL_ERR_INVALID_ARG, "nsl_create: blob size mismatch");
   NetLayout L{};
   if (!build_net_layout((int)c0, &L))
-    return fail(NSL_ERR_UNSUPPORTED, "nsl_create: base width C0=%u (only 16 is built)", c0);
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_create: base width C0=%u (16 and 32 are built)", c0);
   if (L.total != nf) return fail(NSL_ERR_INVALID_ARG, "nsl_create: parameter count %u", nf);
   uint32_t chk = 0, stored;
   for (uint32_t i = 0; i < nf; ++i) {
@@ -222,8 +223,8 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: tile counter"); }
   c->wf32 = net_f32_create(c->params.data(), L, &e);
   if (!c->wf32) { nsl_destroy(c); return cuda_fail(e, "nsl_create: FP32 weights"); }
-  c->ws_bytes = net_f32_workspace_bytes(max_width, max_height);
-  {
+  c->ws_bytes = net_f32_workspace_bytes(max_width, max_height, L.c0);
+  if (L.c0 == kC0) {
     size_t tcb = net_tc_workspace_bytes(max_width, max_height);
     if (tcb > c->ws_bytes) c->ws_bytes = tcb;
   }
@@ -556,6 +557,9 @@ static nsl_status predict(nsl_ctx* c, const float* guide, int width, int height,
     case NSL_PREC_BF16:
     case NSL_PREC_F16:
     case NSL_PREC_FP8: {
+      if (c->layout.c0 != kC0)
+        return fail(NSL_ERR_UNSUPPORTED, "%s: the tensor-core networks are built for C0=16 (this blob: C0=%d)",
+                    fn, c->layout.c0);
       const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
       if (!c->wtc[elem]) {
         c->wtc[elem] = net_tc_create(c->params.data(), c->layout, elem, &e);

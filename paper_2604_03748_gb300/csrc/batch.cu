@@ -327,7 +327,8 @@ nsl_status nsl_batch_create(const void* blob, size_t blob_bytes, int max_plumes,
   if (ver != 1 || (size_t)nf * 4 + 20 != blob_bytes)
     return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: blob version or size mismatch");
   NetLayout L{};
-  if (!build_net_layout((int)c0, &L)) return fail(NSL_ERR_UNSUPPORTED, "nsl_batch_create: C0=%u", c0);
+  if (!build_net_layout((int)c0, &L) || L.c0 != kC0)
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch_create: C0=%u (batches run C0=16)", c0);
   if (L.total != nf) return fail(NSL_ERR_INVALID_ARG, "nsl_batch_create: parameter count");
   uint32_t chk = 0, stored;
   for (uint32_t i = 0; i < nf; ++i) {

@@ -373,7 +373,9 @@ struct NetF32Weights {
   float* conv_b[14];
   float* up_w[3];      // packed [cout/16][cin][4][16]
   float* up_b[3];
-  AdapterParamSet adp; // folded adapter parameters
+  AdapterParamSet adp; // folded adapter parameters (base width kC0)
+  AdapterWideWeights* wide = nullptr;  // the adapters at base width kWideC0
+  int c0 = kC0;
   int conv_cin[14], conv_cout[14], up_cin[3], up_cout[3];
   std::vector<void*> allocs;
 };
@@ -415,7 +417,12 @@ NetF32Weights* net_f32_create(const float* hp, const NetLayout& L, cudaError_t* 
     w->up_w[l] = upload(w, pk, err);
     w->up_b[l] = upload(w, std::vector<float>(hp + L.up_b[l], hp + L.up_b[l] + cout), err);
   }
-  adapter_params_from(hp + L.adapter[0], &w->adp.p1, &w->adp.sca, &w->adp.p2);
+  w->c0 = L.c0;
+  if (L.c0 == kC0) {
+    adapter_params_from(hp + L.adapter[0], &w->adp.p1, &w->adp.sca, &w->adp.p2);
+  } else if (*err == cudaSuccess) {
+    w->wide = adapters_wide_create(hp + L.adapter[0], err);
+  }
   if (*err != cudaSuccess) { net_f32_destroy(w); return nullptr; }
   return w;
 }
@@ -427,6 +434,7 @@ const AdapterParamSet& net_f32_adapter_params(const NetF32Weights* w) { return w
 void net_f32_destroy(NetF32Weights* w) {
   if (!w) return;
   for (void* p : w->allocs) cudaFree(p);
+  adapters_wide_destroy(w->wide);
   delete w;
 }
 
@@ -437,32 +445,35 @@ struct F32Buffers {
   size_t split_floats;
 };
 
-// floats of the split partial sums (64 B per pixel of the largest image plus
-// 4 MiB): conv() splits a layer only as far as nks * pixels * cout fits
-static size_t split_capacity(size_t P) { return P * 16 + ((size_t)1 << 20); }
+// floats of the split partial sums (4 C0 bytes per pixel of the largest image
+// plus 4 MiB): conv() splits a layer only as far as nks * pixels * cout fits
+static size_t split_capacity(size_t P, int c0) { return P * c0 + ((size_t)1 << 20); }
 
-static size_t carve(size_t P, F32Buffers* b, char* base) {
+// P = max pixels (a multiple of 64: both sides are multiples of 8), c0 = base width
+static size_t carve(size_t P, int c0, F32Buffers* b, char* base) {
   size_t off = 0;
   auto take = [&](size_t nfloats) {
     float* p = base ? reinterpret_cast<float*>(base + off) : nullptr;
     off += ((nfloats * sizeof(float) + 255) / 256) * 256;
     return p;
   };
-  b->fa = take(P * 16); b->fb = take(P * 16); b->s1 = take(P * 16);
-  b->l1a = take(P / 4 * 32); b->l1b = take(P / 4 * 32); b->s2 = take(P / 4 * 32);
-  b->l2a = take(P / 16 * 64); b->l2b = take(P / 16 * 64); b->s3 = take(P / 16 * 64);
-  b->l3a = take(P / 64 * 128); b->l3b = take(P / 64 * 128);
-  b->x1 = take(P * 64);
-  b->partial = take(adapter_partial_floats((int)P, 1) + (P / 128 + 1024) * 64);
-  b->att = take(64);
-  b->split_floats = split_capacity(P);
+  const size_t c = (size_t)c0;
+  b->fa = take(P * c); b->fb = take(P * c); b->s1 = take(P * c);
+  b->l1a = take(P / 4 * 2 * c); b->l1b = take(P / 4 * 2 * c); b->s2 = take(P / 4 * 2 * c);
+  b->l2a = take(P / 16 * 4 * c); b->l2b = take(P / 16 * 4 * c); b->s3 = take(P / 16 * 4 * c);
+  b->l3a = take(P / 64 * 8 * c); b->l3b = take(P / 64 * 8 * c);
+  b->x1 = take(P * 4 * c);
+  b->partial = take(c0 == kC0 ? adapter_partial_floats((int)P, 1) + (P / 128 + 1024) * 64
+                              : adapter_wide_partial_floats((int)P, 1));
+  b->att = take(8 * c);
+  b->split_floats = split_capacity(P, c0);
   b->split = take(b->split_floats);
   return off;
 }
 
-size_t net_f32_workspace_bytes(int max_w, int max_h) {
+size_t net_f32_workspace_bytes(int max_w, int max_h, int c0) {
   F32Buffers b;
-  return carve((size_t)max_w * max_h, &b, nullptr);
+  return carve((size_t)max_w * max_h, c0, &b, nullptr);
 }
 
 // A layer whose tiles and output-channel groups give fewer than two blocks per
@@ -539,43 +550,58 @@ static cudaError_t convT(const float* in, const float* w, const float* b, float*
   return cudaGetLastError();
 }
 
-cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* workspace,
-                            size_t ws_bytes, cudaStream_t s) {
+// The UNet of base width C0 (Fig. 3): encoder, decoder, then the adapters.
+template <int C0>
+static cudaError_t forward_f32(const NetF32Weights* w, const NetImage& img, const F32Buffers& B,
+                               cudaStream_t s) {
+  constexpr int C1 = 2 * C0, C2 = 4 * C0, C3 = 8 * C0;
   const int H = img.H, W = img.W;
-  const size_t P = (size_t)H * W;
-  F32Buffers B;
-  if (carve(P, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
-  carve(P, &B, static_cast<char*>(workspace));
   cudaError_t e;
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
   auto A = [&](const float* inA, const float* inB, int l, float* out, int h, int ww) {
     ConvArgs a{inA, inB, w->conv_w[l], w->conv_b[l], out, h, ww, img.depth_scale};
     return a;
   };
+  float* const sp = B.split;
+  const size_t sf = B.split_floats;
   const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
   // encoder
-  TRY((conv<3, IN_GUIDE>(A(img.guide, nullptr, 0, B.fa, H, W), 16, s)));
-  TRY((conv<16, IN_PLAIN>(A(B.fa, nullptr, 1, B.s1, H, W), 16, s)));
-  TRY((conv<16, IN_POOL>(A(B.s1, nullptr, 2, B.l1a, H1, W1), 32, s)));
-  TRY((conv<32, IN_PLAIN>(A(B.l1a, nullptr, 3, B.s2, H1, W1), 32, s, B.split, B.split_floats)));
-  TRY((conv<32, IN_POOL>(A(B.s2, nullptr, 4, B.l2a, H2, W2), 64, s, B.split, B.split_floats)));
-  TRY((conv<64, IN_PLAIN>(A(B.l2a, nullptr, 5, B.s3, H2, W2), 64, s, B.split, B.split_floats)));
-  TRY((conv<64, IN_POOL>(A(B.s3, nullptr, 6, B.l3a, H3, W3), 128, s, B.split, B.split_floats)));
-  TRY((conv<128, IN_PLAIN>(A(B.l3a, nullptr, 7, B.l3b, H3, W3), 128, s, B.split, B.split_floats)));
+  TRY((conv<3, IN_GUIDE>(A(img.guide, nullptr, 0, B.fa, H, W), C0, s)));
+  TRY((conv<C0, IN_PLAIN>(A(B.fa, nullptr, 1, B.s1, H, W), C0, s, sp, sf)));
+  TRY((conv<C0, IN_POOL>(A(B.s1, nullptr, 2, B.l1a, H1, W1), C1, s, sp, sf)));
+  TRY((conv<C1, IN_PLAIN>(A(B.l1a, nullptr, 3, B.s2, H1, W1), C1, s, sp, sf)));
+  TRY((conv<C1, IN_POOL>(A(B.s2, nullptr, 4, B.l2a, H2, W2), C2, s, sp, sf)));
+  TRY((conv<C2, IN_PLAIN>(A(B.l2a, nullptr, 5, B.s3, H2, W2), C2, s, sp, sf)));
+  TRY((conv<C2, IN_POOL>(A(B.s3, nullptr, 6, B.l3a, H3, W3), C3, s, sp, sf)));
+  TRY((conv<C3, IN_PLAIN>(A(B.l3a, nullptr, 7, B.l3b, H3, W3), C3, s, sp, sf)));
   // decoder
-  TRY(convT<128>(B.l3b, w->up_w[0], w->up_b[0], B.l2a, H3, W3, 64, s));
-  TRY((conv<128, IN_CONCAT>(A(B.l2a, B.s3, 8, B.l2b, H2, W2), 64, s, B.split, B.split_floats)));
-  TRY((conv<64, IN_PLAIN>(A(B.l2b, nullptr, 9, B.l2a, H2, W2), 64, s, B.split, B.split_floats)));
-  TRY(convT<64>(B.l2a, w->up_w[1], w->up_b[1], B.l1a, H2, W2, 32, s));
-  TRY((conv<64, IN_CONCAT>(A(B.l1a, B.s2, 10, B.l1b, H1, W1), 32, s, B.split, B.split_floats)));
-  TRY((conv<32, IN_PLAIN>(A(B.l1b, nullptr, 11, B.l1a, H1, W1), 32, s, B.split, B.split_floats)));
-  TRY(convT<32>(B.l1a, w->up_w[2], w->up_b[2], B.fa, H1, W1, 16, s));
-  TRY((conv<32, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), 16, s, B.split, B.split_floats)));
-  TRY((conv<16, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), 16, s)));
+  TRY(convT<C3>(B.l3b, w->up_w[0], w->up_b[0], B.l2a, H3, W3, C2, s));
+  TRY((conv<2 * C2, IN_CONCAT>(A(B.l2a, B.s3, 8, B.l2b, H2, W2), C2, s, sp, sf)));
+  TRY((conv<C2, IN_PLAIN>(A(B.l2b, nullptr, 9, B.l2a, H2, W2), C2, s, sp, sf)));
+  TRY(convT<C2>(B.l2a, w->up_w[1], w->up_b[1], B.l1a, H2, W2, C1, s));
+  TRY((conv<2 * C1, IN_CONCAT>(A(B.l1a, B.s2, 10, B.l1b, H1, W1), C1, s, sp, sf)));
+  TRY((conv<C1, IN_PLAIN>(A(B.l1b, nullptr, 11, B.l1a, H1, W1), C1, s, sp, sf)));
+  TRY(convT<C1>(B.l1a, w->up_w[2], w->up_b[2], B.fa, H1, W1, C0, s));
+  TRY((conv<2 * C0, IN_CONCAT>(A(B.fa, B.s1, 12, B.fb, H, W), C0, s, sp, sf)));
+  TRY((conv<C0, IN_PLAIN>(A(B.fb, nullptr, 13, B.fa, H, W), C0, s, sp, sf)));
   // adapters
-  TRY(adapters_run<float>(w->adp, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  if constexpr (C0 == kC0) {
+    TRY(adapters_run<float>(w->adp, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  } else {
+    TRY(adapters_wide_run(w->wide, B.fa, B.x1, B.partial, B.att, img.out, H, W, s));
+  }
 #undef TRY
   return cudaSuccess;
+}
+
+cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* workspace,
+                            size_t ws_bytes, cudaStream_t s) {
+  const size_t P = (size_t)img.H * img.W;
+  F32Buffers B;
+  if (carve(P, w->c0, &B, nullptr) > ws_bytes) return cudaErrorInvalidValue;
+  carve(P, w->c0, &B, static_cast<char*>(workspace));
+  if (w->c0 == kWideC0) return forward_f32<kWideC0>(w, img, B, s);
+  return forward_f32<kC0>(w, img, B, s);
 }
 
 }  // namespace nsl

@@ -244,10 +244,15 @@ cudaError_t launch_shade_batch(const ShadeArgs* items_dev, const int* block_star
 // ---------------------------------------------------------------------------
 // network
 // ---------------------------------------------------------------------------
-constexpr int kC0 = 16;
-constexpr int kAdapterParams = 2 * kC0 + (2 * kC0 * kC0 + 2 * kC0) + (18 * kC0 + 2 * kC0) +
-                               (kC0 * kC0 + kC0) + (kC0 * kC0 + kC0) + kC0 + 2 * kC0 +
-                               (2 * kC0 * kC0 + 2 * kC0) + (kC0 * kC0 + kC0) + kC0 + 2 * kC0 + 2;
+constexpr int kC0 = 16;        // base width of every network path
+constexpr int kWideC0 = 32;    // the second base width, built in the FP32 path only
+// floats of one adapter's parameters (LN1, pw1, dw, SCA, pw2, beta, LN2, ffn1,
+// ffn2, gamma, head) at adapter width c
+__host__ __device__ constexpr int adapter_param_count(int c) {
+  return 2 * c + (2 * c * c + 2 * c) + (18 * c + 2 * c) + (c * c + c) + (c * c + c) + c + 2 * c +
+         (2 * c * c + 2 * c) + (c * c + c) + c + 2 * c + 2;
+}
+constexpr int kAdapterParams = adapter_param_count(kC0);
 
 // offsets (in floats) of every parameter tensor inside the flat NSLW payload
 struct NetLayout {
@@ -257,7 +262,10 @@ struct NetLayout {
   int up_cin[3], up_cout[3];
   size_t adapter[4];               // start of each adapter's parameters (incl. head)
   size_t total;
+  int c0;                          // base width
 };
+// Offsets of a blob of base width c0; false unless c0 is kC0 or kWideC0 (only
+// the FP32 path runs kWideC0: callers of the other paths check c0 == kC0).
 bool build_net_layout(int c0, NetLayout* L);
 
 // device-side parameter sets of one adapter (offsets into a packed float array)
@@ -277,7 +285,7 @@ struct NetImage {     // one image of a (possibly batched) network call
 struct NetF32Weights;  // opaque
 NetF32Weights* net_f32_create(const float* host_params, const NetLayout& L, cudaError_t* err);
 void net_f32_destroy(NetF32Weights* w);
-size_t net_f32_workspace_bytes(int max_w, int max_h);
+size_t net_f32_workspace_bytes(int max_w, int max_h, int c0 = kC0);
 cudaError_t net_f32_forward(const NetF32Weights* w, const NetImage& img, void* workspace,
                             size_t ws_bytes, cudaStream_t s);
 const float* net_f32_conv_w(const NetF32Weights* w, int l);  // SIMT-packed conv weights
@@ -323,6 +331,14 @@ size_t adapter_partial_floats(int max_w, int max_h);
 template <typename TA>
 cudaError_t adapters_run(const AdapterParamSet& prm, const TA* F, TA* x1, float* partial,
                          float* att, float* out, int H, int W, cudaStream_t s);
+// FP32 adapters at base width kWideC0 (weights in device memory, staged in
+// shared memory per CTA); F, x1 [4][H][W][C], partial (adapter_wide_partial_floats)
+struct AdapterWideWeights;
+AdapterWideWeights* adapters_wide_create(const float* adapters_blob, cudaError_t* err);
+void adapters_wide_destroy(AdapterWideWeights* w);
+size_t adapter_wide_partial_floats(int max_w, int max_h);
+cudaError_t adapters_wide_run(const AdapterWideWeights* w, const float* F, float* x1, float* partial,
+                              float* mean, float* out, int H, int W, cudaStream_t s);
 // one image of a grouped adapter launch (tensor-core passes and the reduction)
 template <typename TA>
 struct AdapterImg {

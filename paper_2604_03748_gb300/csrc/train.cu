@@ -833,7 +833,8 @@ nsl_status nsl_trainer_create(const void* blob, size_t blob_bytes, const nsl_tra
   if (ver != 1 || (size_t)nf * 4 + 20 != blob_bytes)
     return fail(NSL_ERR_INVALID_ARG, "%s: blob version or size mismatch", fn);
   NetLayout L{};
-  if (!build_net_layout((int)c0, &L)) return fail(NSL_ERR_UNSUPPORTED, "%s: C0=%u (only 16 is built)", fn, c0);
+  if (!build_net_layout((int)c0, &L) || L.c0 != kC0)
+    return fail(NSL_ERR_UNSUPPORTED, "%s: C0=%u (the trainer runs C0=16)", fn, c0);
   if (L.total != nf) return fail(NSL_ERR_INVALID_ARG, "%s: parameter count", fn);
   nsl_trainer* T = new nsl_trainer();
   T->o = o;

@@ -171,7 +171,7 @@ def torch_unet_forward(guide, params, c0, depth_scale):
     return out.numpy()
 
 
-@pytest.mark.parametrize("c0,H,W", [(4, 16, 24), (8, 24, 16)])
+@pytest.mark.parametrize("c0,H,W", [(4, 16, 24), (8, 24, 16), (32, 16, 8)])
 def test_net_forward_matches_torch_assembly(orc, c0, H, W):
     params = I.make_params(c0, seed=0)
     flat = I.flat_params(params).astype(np.float64)
