@@ -162,9 +162,9 @@ def oracle_guide_full(pf):
     return oracle.guide(pf.density, pf.mask, pf.camera, pf.step)
 
 
-def oracle_net(guide, flat, pf):
+def oracle_net(guide, flat, pf, c0=16):
     import oracle
-    return oracle.net_forward(guide, flat, 16, 1.0 / math.sqrt(sum(float(v) ** 2 for v in pf.density.shape)))
+    return oracle.net_forward(guide, flat, c0, 1.0 / math.sqrt(sum(float(v) ** 2 for v in pf.density.shape)))
 
 
 def init_replicas(backend, timeout_s=REPLICA_TIMEOUT_S):
@@ -595,6 +595,38 @@ def main():
                                           "net_ms": nms,
                                           "net_tflops": net_flop_per_pixel(16) * H * W / (nms / 1e3) / 1e12}
             lm_rows[name] = lmr
+        # the same frames with the FP32 network at base width C0 = 32
+        blob32 = I.pack_blob(I.make_params(32, 0), 32)
+        ctx32 = nsl.Context(pf.density.shape, nsl.NSL_F32, blob32, W, H)
+        lm32 = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+
+        def frame32(evs=None):
+            if evs:
+                evs[0].record(stream)
+            nsl.nsl_stage_grid(ctx32.ctx, dens, mask, stream=stream)
+            nsl.nsl_guiding_map(ctx32.ctx, None, None, pf.camera, pf.step, gr, opts=opts, stream=stream)
+            if evs:
+                evs[1].record(stream)
+            nsl.nsl_predict_lightmaps(ctx32.ctx, gr, W, H, nsl.NSL_PREC_F32, lm32, stream=stream)
+            if evs:
+                evs[2].record(stream)
+            nsl.nsl_shade(ctx32.ctx, lm32, W, H, pf.camera, [pf.light], rgba, stream=stream)
+            if evs:
+                evs[3].record(stream)
+        for _ in range(3):
+            frame32()
+        torch.cuda.synchronize()
+        evl = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(max(5, min(args.steps, 20)))]
+        for e in evl:
+            flush.zero_()
+            frame32(e)
+        torch.cuda.synchronize()
+        fms = float(np.mean([e[0].elapsed_time(e[3]) for e in evl]))
+        nms = float(np.mean([e[1].elapsed_time(e[2]) for e in evl]))
+        rows[f"{WORKLOAD}_f32_c0_32"] = {"value": H * W / (fms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": fms,
+                                         "net_ms": nms,
+                                         "net_tflops": net_flop_per_pixel(32) * H * W / (nms / 1e3) / 1e12}
+        ctx32.close()
         # the 64^3 scene, orthographic 128^2, step 4, FP32 network
         pf1 = I.config_plain_64()
         H1, W1 = pf1.camera.height, pf1.camera.width
@@ -680,6 +712,14 @@ def main():
         }
         for name, lmr in lm_rows.items():
             rows[f"{WORKLOAD}_{name}"]["lightmaps_err_vs_oracle"] = max(range_errs(lmr.cpu().numpy(), ref[1]))
+        if f"{WORKLOAD}_f32_c0_32" in rows:
+            # the C0 = 32 network on this frame's guide against the oracle's
+            # network at C0 = 32 on the oracle's guide, every output value
+            flat32 = I.flat_params(I.make_params(32, 0)).astype(np.float64)
+            ref32 = oracle_net(ref[0], flat32, pf, c0=32)
+            l32 = lm32.cpu().numpy()
+            rows[f"{WORKLOAD}_f32_c0_32"]["lightmaps_err_vs_oracle"] = max(range_errs(l32, ref32))
+            rows[f"{WORKLOAD}_f32_c0_32"]["lightmaps_max_abs_vs_oracle"] = float(np.abs(l32 - ref32).max())
         if "plume64_ortho128_h4_f32" in rows:
             o1, _, _ = oracle_guide_full(pf1)
             ref1 = oracle_net(o1, flat, pf1)
