@@ -37,6 +37,15 @@ __device__ __forceinline__ void ldg_octo(const float* p, float4& a, float4& b) {
       : "l"(p));
 }
 
+// Index of padded cell (X, Y, Z) = (ix + 1, iy + 1, iz + 1) in the staged
+// array of an nx x ny x nz grid, in the order kMarchOrder; the cell of the
+// next slice is pl = (nx + 1)(ny + 1) cells further on in both orders.
+__host__ __device__ __forceinline__ unsigned cell_index(int nx, int ny, unsigned X, unsigned Y, unsigned Z) {
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u;
+  if constexpr (kMarchOrder == 1) return (Z * px + X) * py + Y;
+  return (Z * py + Y) * px + X;
+}
+
 // The two x/y quads of padded cell `cell` (slice z in a, z+1 in b).
 __device__ __forceinline__ void load_cell(const Grid& g, unsigned cell, unsigned pl, float4& a, float4& b) {
   if constexpr (kMarchLayout == kLayoutOcto) {
@@ -70,9 +79,9 @@ __device__ __forceinline__ float sigma_at(const G& g, float px, float py, float 
   int ix = (int)flx, iy = (int)fly, iz = (int)flz;
   // padded cells: cell (ix+1, iy+1, iz+1) holds the corners, every index of a
   // point inside the box is in range
-  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
+  const unsigned pl = ((unsigned)g.nx + 1u) * ((unsigned)g.ny + 1u);
   float4 a, b;
-  load_cell(g, (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1), pl, a, b);
+  load_cell(g, cell_index(g.nx, g.ny, (unsigned)(ix + 1), (unsigned)(iy + 1), (unsigned)(iz + 1)), pl, a, b);
   const float c00 = fmaf(tx, a.y - a.x, a.x);
   const float c10 = fmaf(tx, a.w - a.z, a.z);
   const float c01 = fmaf(tx, b.y - b.x, b.x);

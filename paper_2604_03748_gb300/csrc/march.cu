@@ -49,8 +49,8 @@ __device__ __forceinline__ Fetch fetch(const G& g, float px, float py, float pz)
   // clamp into the padded array so that a speculative fetch is always in range
   const int ix = min(max((int)flx, -1), g.nx - 1), iy = min(max((int)fly, -1), g.ny - 1);
   const int iz = min(max((int)flz, -1), g.nz - 1);
-  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  load_cell(g, (unsigned)(iz + 1) * pl + (unsigned)(iy + 1) * rw + (unsigned)(ix + 1), pl, f.a, f.b);
+  const unsigned pl = ((unsigned)g.nx + 1u) * ((unsigned)g.ny + 1u);
+  load_cell(g, cell_index(g.nx, g.ny, (unsigned)(ix + 1), (unsigned)(iy + 1), (unsigned)(iz + 1)), pl, f.a, f.b);
   return f;
 }
 
@@ -66,9 +66,9 @@ __device__ __forceinline__ Fetch fetch_in(const G& g, float px, float py, float 
   f.tx = __fsub_rn(qx, flx);
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
-  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  load_cell(g, (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1), pl,
-            f.a, f.b);
+  const unsigned pl = ((unsigned)g.nx + 1u) * ((unsigned)g.ny + 1u);
+  load_cell(g, cell_index(g.nx, g.ny, (unsigned)((int)flx + 1), (unsigned)((int)fly + 1), (unsigned)((int)flz + 1)),
+            pl, f.a, f.b);
   return f;
 }
 
@@ -82,9 +82,9 @@ __device__ __forceinline__ Fetch fetch_q(const G& g, float qx, float qy, float q
   f.tx = __fsub_rn(qx, flx);
   f.ty = __fsub_rn(qy, fly);
   f.tz = __fsub_rn(qz, flz);
-  const unsigned rw = (unsigned)g.nx + 1u, pl = rw * ((unsigned)g.ny + 1u);
-  load_cell(g, (unsigned)((int)flz + 1) * pl + (unsigned)((int)fly + 1) * rw + (unsigned)((int)flx + 1), pl,
-            f.a, f.b);
+  const unsigned pl = ((unsigned)g.nx + 1u) * ((unsigned)g.ny + 1u);
+  load_cell(g, cell_index(g.nx, g.ny, (unsigned)((int)flx + 1), (unsigned)((int)fly + 1), (unsigned)((int)flz + 1)),
+            pl, f.a, f.b);
   return f;
 }
 
@@ -924,10 +924,40 @@ __device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const 
 // (one thread loads the 5-voxel windows of its two rows once and writes 64
 // contiguous bytes; per cell that is 2.5 loads instead of 8); the octo layout
 // one cell at a time.
+// In the y-fastest order the four cells of a unit run along y (one thread reads
+// the 5-voxel windows of its two x columns), and consecutive units along x, so
+// that a warp's loads of the source rows stay coalesced.
 __host__ __device__ __forceinline__ size_t stage_units(int nx, int ny, int nz) {
   if (kMarchLayout == kLayoutOcto) return staged_cells(nx, ny, nz);
+  if (kMarchOrder == 1) return ((size_t)nx + 1) * (((size_t)ny + 4) / 4) * ((size_t)nz + 2);
   const size_t px = (size_t)nx + 1, rows = ((size_t)ny + 1) * ((size_t)nz + 2);
   return rows * ((px + 3) / 4);
+}
+
+// Four consecutive cells of staging unit u in the y-fastest order: cell
+// (a, b0 + t, cz) holds voxels (a-1, a) x (b0-1+t, b0+t) of slice cz-1, every
+// index clamped into the grid; `put(dst_cell, v00, v10, v01, v11)` stores one.
+template <class V, class Put>
+__device__ __forceinline__ void stage_unit_yfast(int nx, int ny, int nz, size_t u, V val, Put put) {
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpy = (py + 3u) / 4u;
+  const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
+  const int a = (int)(u32 % px);
+  const unsigned rest = u32 / px;
+  const int b0 = (int)(4u * (rest % gpy)), cz = (int)(rest / gpy);
+  const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
+  const int k0 = min(max(cz - 1, 0), nz - 1);
+  decltype(val((size_t)0)) w0[5], w1[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int y = min(max(b0 - 1 + t, 0), ny - 1);
+    const size_t row = ((size_t)k0 * ny + y) * nx;
+    w0[t] = val(row + i0);
+    w1[t] = val(row + i1);
+  }
+  const unsigned c0 = cell_index(nx, ny, (unsigned)a, (unsigned)b0, (unsigned)cz);
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (b0 + t < (int)py) put(c0 + (unsigned)t, w0[t], w1[t], w0[t + 1], w1[t + 1]);
 }
 
 template <typename T>
@@ -935,6 +965,14 @@ __device__ __forceinline__ void stage_unit(const T* __restrict__ rho, const uint
                                            int ny, int nz, float scale, float* __restrict__ out, size_t u) {
   if constexpr (kMarchLayout == kLayoutOcto) {
     stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, u);
+  } else if constexpr (kMarchOrder == 1) {
+    auto val = [&](size_t idx) {
+      return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+    };
+    float4* o4 = reinterpret_cast<float4*>(out);
+    stage_unit_yfast(nx, ny, nz, u, val, [&](unsigned c, float v00, float v10, float v01, float v11) {
+      o4[c] = make_float4(v00, v10, v01, v11);
+    });
   } else {
     auto val = [&](size_t idx) {
       return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
@@ -1000,6 +1038,13 @@ __device__ __forceinline__ void stage_half_unit(const __half* __restrict__ rho, 
   const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpr = (px + 3u) / 4u;
   const __half zero = __float2half_rn(0.f);
   auto val = [&](size_t idx) { return (mask && __ldg(mask + idx)) ? zero : rho[idx]; };
+  if constexpr (kMarchOrder == 1) {
+    stage_unit_yfast(nx, ny, nz, u, val, [&](unsigned c, __half v00, __half v10, __half v01, __half v11) {
+      const __half2 lo = __halves2half2(v00, v10), hi = __halves2half2(v01, v11);
+      out[c] = make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+    });
+    return;
+  }
   const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
   const unsigned r = u32 / gpr;
   const int a0 = (int)(4u * (u32 % gpr));

@@ -146,8 +146,9 @@ constexpr int kMarchSegLen = NSL_MARCH_SEG;  // view steps per segment of the se
 #endif
 constexpr int kMarchTX = NSL_MARCH_TX;  // default march tile: TX x (32/TX) pixels, one warp
 constexpr int kMarchTY = 32 / kMarchTX;
-constexpr int kMarchTXLog2 = kMarchTX == 16 ? 4 : (kMarchTX == 8 ? 3 : (kMarchTX == 4 ? 2 : 1));
-static_assert((1 << kMarchTXLog2) == kMarchTX, "march tile width: 2, 4, 8 or 16");
+constexpr int kMarchTXLog2 =
+    kMarchTX == 16 ? 4 : (kMarchTX == 8 ? 3 : (kMarchTX == 4 ? 2 : (kMarchTX == 2 ? 1 : 0)));
+static_assert((1 << kMarchTXLog2) == kMarchTX, "march tile width: 1, 2, 4, 8 or 16");
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
@@ -157,6 +158,15 @@ constexpr int kLayoutQuad = 2, kLayoutOcto = 3;
 #define NSL_MARCH_LAYOUT 2
 #endif
 constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
+// Order of the staged quad cells in memory: 0 = x fastest, then y, then z;
+// 1 = y fastest, then x, then z.  Slices (z) are outermost in both, so the
+// quad of slice z+1 is one plane (PX * PY cells) further on.
+#ifndef NSL_MARCH_ORDER
+#define NSL_MARCH_ORDER 0
+#endif
+constexpr int kMarchOrder = NSL_MARCH_ORDER;
+static_assert(kMarchOrder == 0 || kMarchOrder == 1, "staged cell order: 0 (x fastest) or 1 (y fastest)");
+static_assert(kMarchOrder == 0 || kMarchLayout == kLayoutQuad, "the y-fastest order is a quad layout");
 static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto, "staged layout: 2 (quad) or 3 (octo)");
 // cells of the padded staged layouts: quad (nx+1)(ny+1)(nz+2) of 4 floats,
 // octo (nx+1)(ny+1)(nz+1) of 8 floats
