@@ -155,9 +155,12 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
   const int tid = threadIdx.x;
   const int x0 = bx * kTW, y0 = by * kTH;
   const int tx = tid % kTW, ty = (tid / kTW) * 2;
-  float acc0[16], acc1[16];
+  // accumulators of output rows ty and ty + 1, as channel pairs: the packed
+  // FP32 FMA updates two output channels per instruction, each lane rounded
+  // once as fmaf
+  float2 p0[8], p1[8];
 #pragma unroll
-  for (int o = 0; o < 16; ++o) { acc0[o] = 0.f; acc1[o] = 0.f; }
+  for (int o = 0; o < 8; ++o) { p0[o] = make_float2(0.f, 0.f); p1[o] = make_float2(0.f, 0.f); }
 
   const int cbeg = CIN / nks * ks, cend = CIN / nks * (ks + 1);
   for (int c0 = cbeg; c0 < cend; c0 += CT) {
@@ -232,20 +235,24 @@ __device__ __forceinline__ void conv3x3_f32_tile(const ConvArgs& a, int cout, in
           float v0 = hc[(ty + ky) * kHW + tx + kx];
           float v1 = hc[(ty + 1 + ky) * kHW + tx + kx];
           const float4* w4 = reinterpret_cast<const float4*>(ws + (c * 9 + ky * 3 + kx) * 16);
+          const float2 vv0 = make_float2(v0, v0), vv1 = make_float2(v1, v1);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            float4 w = w4[q];
-            acc0[4 * q + 0] = fmaf(v0, w.x, acc0[4 * q + 0]);
-            acc0[4 * q + 1] = fmaf(v0, w.y, acc0[4 * q + 1]);
-            acc0[4 * q + 2] = fmaf(v0, w.z, acc0[4 * q + 2]);
-            acc0[4 * q + 3] = fmaf(v0, w.w, acc0[4 * q + 3]);
-            acc1[4 * q + 0] = fmaf(v1, w.x, acc1[4 * q + 0]);
-            acc1[4 * q + 1] = fmaf(v1, w.y, acc1[4 * q + 1]);
-            acc1[4 * q + 2] = fmaf(v1, w.z, acc1[4 * q + 2]);
-            acc1[4 * q + 3] = fmaf(v1, w.w, acc1[4 * q + 3]);
+            const float4 w = w4[q];
+            const float2 wa = make_float2(w.x, w.y), wb = make_float2(w.z, w.w);
+            p0[2 * q] = __ffma2_rn(vv0, wa, p0[2 * q]);
+            p0[2 * q + 1] = __ffma2_rn(vv0, wb, p0[2 * q + 1]);
+            p1[2 * q] = __ffma2_rn(vv1, wa, p1[2 * q]);
+            p1[2 * q + 1] = __ffma2_rn(vv1, wb, p1[2 * q + 1]);
           }
         }
     }
+  }
+  float acc0[16], acc1[16];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    acc0[2 * o] = p0[o].x; acc0[2 * o + 1] = p0[o].y;
+    acc1[2 * o] = p1[o].x; acc1[2 * o + 1] = p1[o].y;
   }
   const int x = x0 + tx;
   if constexpr (sizeof(TOut) == 2) {
