@@ -108,6 +108,10 @@ bool build_net_layout(int c0, NetLayout* L) {
 
 using namespace nsl;
 
+// nsl_render_frame_host uploads the density in this many slabs of z slices,
+// staging each slab while the next one is copied.
+constexpr int kUploadSlabs = 4;
+
 struct nsl_ctx {
   nsl_grid_desc grid{};
   int max_w = 0, max_h = 0;
@@ -134,6 +138,9 @@ struct nsl_ctx {
   float* h_guide = nullptr;
   float* h_lm = nullptr;
   float* h_rgba = nullptr;
+  // copy stream of nsl_render_frame_host and its events (created on first use)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev[kUploadSlabs + 4] = {};
 };
 
 static size_t grid_voxels(const nsl_grid_desc& g) { return (size_t)g.nx * g.ny * g.nz; }
@@ -253,6 +260,9 @@ void nsl_destroy(nsl_ctx* c) {
   net_tc_destroy(c->wtc[2]);
   cudaFree(c->ws);
   if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->h_density);
   cudaFree(c->h_mask);
   cudaFree(c->h_guide);
@@ -722,22 +732,66 @@ static nsl_status render_frame_host(nsl_ctx* c, const void* density_host, const 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int W = cam->width, H = cam->height;
   const size_t px = (size_t)W * H;
-  NSL_CUDA_TRY(cudaMemcpyAsync(c->h_density, density_host, dbytes, cudaMemcpyHostToDevice, s));
-  if (mask_host)
-    NSL_CUDA_TRY(cudaMemcpyAsync(c->h_mask, mask_host, nvox, cudaMemcpyHostToDevice, s));
-  st = nsl_guiding_map(c, c->h_density, mask_host ? c->h_mask : nullptr, cam, nullptr, step, opts,
-                       c->h_guide, stream);
+  // The copies run on the context's copy stream `a`, overlapped with the
+  // kernels on `s`: the density and mask go up in slabs of z slices, each
+  // slab's cell planes staged on `s` as soon as it has arrived; the guide
+  // comes back while the network runs and the lightmaps while shading runs.
+  // `s` finally waits for `a`, so the frame is complete when `s` is.
+  if (!c->aux) {
+    NSL_CUDA_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->ev) NSL_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t a = c->aux;
+  cudaEvent_t* ev = c->ev;
+  // the upload buffers are free once the work queued on s before this frame is done
+  NSL_CUDA_TRY(cudaEventRecord(ev[0], s));
+  NSL_CUDA_TRY(cudaStreamWaitEvent(a, ev[0], 0));
+  const int nz = c->grid.nz, nslab = nz < kUploadSlabs ? nz : kUploadSlabs;
+  const size_t slice = (size_t)c->grid.nx * c->grid.ny, esz = c->grid.dtype == NSL_F16 ? 2 : 4;
+  const uint8_t* mdev = mask_host ? c->h_mask : nullptr;
+  for (int k = 0; k < nslab; ++k) {
+    const int z0 = nz * k / nslab, z1 = nz * (k + 1) / nslab;
+    const size_t off = (size_t)z0 * slice, cnt = (size_t)(z1 - z0) * slice;
+    NSL_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(c->h_density) + off * esz,
+                                 static_cast<const char*>(density_host) + off * esz, cnt * esz,
+                                 cudaMemcpyHostToDevice, a));
+    if (mask_host)
+      NSL_CUDA_TRY(cudaMemcpyAsync(c->h_mask + off, mask_host + off, cnt, cudaMemcpyHostToDevice, a));
+    NSL_CUDA_TRY(cudaEventRecord(ev[1 + k], a));
+    NSL_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + k], 0));
+    // cell plane cz holds slice cz - 1 (clamped): planes z0 + 1 .. z1, and
+    // plane 0 with the first slab, plane nz + 1 with the last
+    const int c0 = k == 0 ? 0 : z0 + 1, c1 = k == nslab - 1 ? nz + 2 : z1 + 1;
+    const cudaError_t e =
+        c->grid.dtype == NSL_F16
+            ? launch_stage_volume_half(static_cast<const __half*>(c->h_density), mdev, c->grid.nx, c->grid.ny, nz,
+                                       reinterpret_cast<__half*>(c->staged), s, c0, c1)
+            : launch_stage_volume(c->h_density, c->grid.dtype, mdev, c->grid.nx, c->grid.ny, nz,
+                                  c->grid.sigma_scale, c->staged, s, c0, c1);
+    if (e != cudaSuccess) return cuda_fail(e, "nsl_render_frame_host: staging");
+  }
+  c->staged_valid = true;
+  cudaEvent_t ev_g = ev[kUploadSlabs + 1], ev_l = ev[kUploadSlabs + 2], ev_a = ev[kUploadSlabs + 3];
+  st = nsl_guiding_map(c, nullptr, nullptr, cam, nullptr, step, opts, c->h_guide, stream);
   if (st != NSL_OK) return st;
+  if (guide_host) {
+    NSL_CUDA_TRY(cudaEventRecord(ev_g, s));
+    NSL_CUDA_TRY(cudaStreamWaitEvent(a, ev_g, 0));
+    NSL_CUDA_TRY(cudaMemcpyAsync(guide_host, c->h_guide, 3 * px * sizeof(float), cudaMemcpyDeviceToHost, a));
+  }
   st = nsl_predict_lightmaps(c, c->h_guide, W, H, precision, c->h_lm, stream);
   if (st != NSL_OK) return st;
+  if (lm_host) {
+    NSL_CUDA_TRY(cudaEventRecord(ev_l, s));
+    NSL_CUDA_TRY(cudaStreamWaitEvent(a, ev_l, 0));
+    NSL_CUDA_TRY(cudaMemcpyAsync(lm_host, c->h_lm, 8 * px * sizeof(float), cudaMemcpyDeviceToHost, a));
+  }
   st = nsl_shade(c, c->h_lm, W, H, cam, lights, n_lights, c->h_rgba, stream);
   if (st != NSL_OK) return st;
-  if (guide_host)
-    NSL_CUDA_TRY(cudaMemcpyAsync(guide_host, c->h_guide, 3 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
-  if (lm_host)
-    NSL_CUDA_TRY(cudaMemcpyAsync(lm_host, c->h_lm, 8 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (rgba_host)
     NSL_CUDA_TRY(cudaMemcpyAsync(rgba_host, c->h_rgba, 4 * px * sizeof(float), cudaMemcpyDeviceToHost, s));
+  NSL_CUDA_TRY(cudaEventRecord(ev_a, a));
+  NSL_CUDA_TRY(cudaStreamWaitEvent(s, ev_a, 0));
   if (wait) NSL_CUDA_TRY(cudaStreamSynchronize(s));
   return NSL_OK;
 }

@@ -934,6 +934,13 @@ __host__ __device__ __forceinline__ size_t stage_units(int nx, int ny, int nz) {
   return rows * ((px + 3) / 4);
 }
 
+// Staging units of one cell plane (quad layouts: the units of plane cz are
+// the contiguous range [cz, cz + 1) x stage_units_per_plane).
+__host__ __device__ __forceinline__ size_t stage_units_per_plane(int nx, int ny) {
+  if (kMarchOrder == 1) return ((size_t)nx + 1) * (((size_t)ny + 4) / 4);
+  return ((size_t)ny + 1) * (((size_t)nx + 4) / 4);
+}
+
 // Four consecutive cells of staging unit u in the y-fastest order: cell
 // (a, b0 + t, cz) holds voxels (a-1, a) x (b0-1+t, b0+t) of slice cz-1, every
 // index clamped into the grid; `put(dst_cell, v00, v10, v01, v11)` stores one.
@@ -1005,29 +1012,49 @@ __device__ __forceinline__ void stage_unit(const T* __restrict__ rho, const uint
 // The quad layout is padded: cell (a, b, c) of an (nx+1) x (ny+1) x (nz+2) array
 // holds the x/y 2x2 neighbourhood whose low corner is voxel (a-1, b-1) of slice
 // c-1, every index clamped into the grid.
+// Staging units [u0, u1) (all of them by default).
 template <typename T>
 __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
                                                     const uint8_t* __restrict__ mask, int nx,
                                                     int ny, int nz, float scale,
-                                                    float* __restrict__ out) {
+                                                    float* __restrict__ out, size_t u0, size_t u1) {
   pdl_wait();      // the previous frame's march may still read the staged grid
   pdl_trigger();
-  const size_t n = stage_units(nx, ny, nz);
-  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x)
+  for (size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < u1; u += (size_t)gridDim.x * blockDim.x)
     stage_unit<T>(rho, mask, nx, ny, nz, scale, out, u);
 }
 
-cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
-                                int ny, int nz, float scale, float* staged, cudaStream_t s) {
+// Unit range of cell planes [c0, c1) (c1 < 0: to the last plane); the octo
+// layout's planes read two slices, so it is always staged whole.
+static void stage_range(int nx, int ny, int nz, int c0, int c1, size_t* u0, size_t* u1) {
   const size_t n = stage_units(nx, ny, nz);
-  int blocks = (int)((n + 255) / 256);
+  if (kMarchLayout == kLayoutOcto || c1 < 0) {
+    *u0 = kMarchLayout == kLayoutOcto ? 0 : (size_t)c0 * stage_units_per_plane(nx, ny);
+    *u1 = n;
+    return;
+  }
+  *u0 = (size_t)c0 * stage_units_per_plane(nx, ny);
+  *u1 = (size_t)c1 * stage_units_per_plane(nx, ny);
+  if (*u1 > n) *u1 = n;
+  if (*u0 > *u1) *u0 = *u1;
+}
+
+static int stage_blocks(size_t units) {
+  int blocks = (int)((units + 255) / 256);
   if (blocks > num_sms() * 16) blocks = num_sms() * 16;
-  if (blocks < 1) blocks = 1;
+  return blocks < 1 ? 1 : blocks;
+}
+
+cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
+                                int ny, int nz, float scale, float* staged, cudaStream_t s, int c0, int c1) {
+  size_t u0, u1;
+  stage_range(nx, ny, nz, c0, c1, &u0, &u1);
+  const int blocks = stage_blocks(u1 - u0);
   if (dtype == NSL_F16)
     return launch_pdl(stage_kernel<__half>, dim3(blocks), dim3(256), 0, s,
-                      static_cast<const __half*>(density), mask, nx, ny, nz, scale, staged);
+                      static_cast<const __half*>(density), mask, nx, ny, nz, scale, staged, u0, u1);
   return launch_pdl(stage_kernel<float>, dim3(blocks), dim3(256), 0, s, static_cast<const float*>(density),
-                    mask, nx, ny, nz, scale, staged);
+                    mask, nx, ny, nz, scale, staged, u0, u1);
 }
 
 // FP16 staging of the quad layout (single-plume contexts with an FP16 grid):
@@ -1071,23 +1098,20 @@ __device__ __forceinline__ void stage_half_unit(const __half* __restrict__ rho, 
 
 __global__ void __launch_bounds__(256) stage_half_kernel(const __half* __restrict__ rho,
                                                          const uint8_t* __restrict__ mask, int nx, int ny, int nz,
-                                                         uint2* __restrict__ out) {
+                                                         uint2* __restrict__ out, size_t u0, size_t u1) {
   pdl_wait();      // the previous frame's march may still read the staged grid
   pdl_trigger();
-  const size_t n = stage_units(nx, ny, nz);
-  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (size_t)gridDim.x * blockDim.x)
+  for (size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < u1; u += (size_t)gridDim.x * blockDim.x)
     stage_half_unit(rho, mask, nx, ny, nz, out, u);
 }
 
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
-                                     __half* staged, cudaStream_t s) {
+                                     __half* staged, cudaStream_t s, int c0, int c1) {
   static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
-  const size_t n = stage_units(nx, ny, nz);
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
-  if (blocks < 1) blocks = 1;
-  return launch_pdl(stage_half_kernel, dim3(blocks), dim3(256), 0, s, density, mask, nx, ny, nz,
-                    reinterpret_cast<uint2*>(staged));
+  size_t u0, u1;
+  stage_range(nx, ny, nz, c0, c1, &u0, &u1);
+  return launch_pdl(stage_half_kernel, dim3(stage_blocks(u1 - u0)), dim3(256), 0, s, density, mask, nx, ny, nz,
+                    reinterpret_cast<uint2*>(staged), u0, u1);
 }
 
 // Transmittance volumes of the shadow_volume option: one thread per voxel

@@ -183,10 +183,15 @@ inline size_t staged_floats(int nx, int ny, int nz) {
   return staged_cells(nx, ny, nz) * (kMarchLayout == kLayoutOcto ? 8 : 4);
 }
 cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s);
+// Staging of the cell planes [c0, c1) of the padded quad layout (c1 < 0: to the
+// last plane, nz + 1).  Cell plane cz reads density slice min(max(cz - 1, 0),
+// nz - 1) only, so the planes of a slab of slices can be staged as soon as that
+// slab has arrived.
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
-                                int ny, int nz, float scale, float* staged, cudaStream_t s);
+                                int ny, int nz, float scale, float* staged, cudaStream_t s, int c0 = 0,
+                                int c1 = -1);
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
-                                     __half* staged, cudaStream_t s);
+                                     __half* staged, cudaStream_t s, int c0 = 0, int c1 = -1);
 int march_tiles(int W, int H, int tx_log2 = kMarchTXLog2);
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
                          bool count = false);

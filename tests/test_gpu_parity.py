@@ -302,6 +302,49 @@ def test_render_frame_host_matches_device_calls(lib, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["obstacle128_f32_mask", "ragged27_f16_mask", "thin3_f32"])
+def test_render_frame_host_slab_upload_bitwise(lib, case):
+    """The host entry point uploads the grid in slabs of z slices and stages
+    each slab while the next one is copied; its guide, lightmaps and rgba equal
+    the device-buffer calls (one staging of the whole grid) bit for bit: a
+    masked 128^3 FP32 grid, a ragged masked FP16 grid, and a grid thinner
+    (3 slices) than the number of slabs."""
+    import dataclasses
+    import torch
+    from paper_2604_03748_gb300 import nsl
+    if case == "obstacle128_f32_mask":
+        pf = I.config_obstacle_128()
+        pf = dataclasses.replace(pf, camera=dataclasses.replace(pf.camera, width=128, height=96))
+    elif case == "ragged27_f16_mask":
+        pf = I.small_case(27, 40, 24, seed=21, kind=I.PERSP, step=1.5)
+        pf = dataclasses.replace(pf, density=pf.density.astype(np.float16))
+    else:
+        pf = I.small_case(20, 24, 16, seed=22, kind=I.ORTHO, step=2.0)
+        pf = dataclasses.replace(pf, density=np.ascontiguousarray(pf.density[:3]),
+                                 mask=np.ascontiguousarray(pf.mask[:3]))
+    H, W = pf.camera.height, pf.camera.width
+    dev = torch.device("cuda:0")
+    ctx = PT.make_ctx(pf)
+    d = torch.from_numpy(pf.density).to(dev)
+    m = torch.from_numpy(pf.mask).to(dev)
+    guide = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    lm = torch.empty((8, H, W), dtype=torch.float32, device=dev)
+    rgba = torch.empty((4, H, W), dtype=torch.float32, device=dev)
+    ctx.guiding_map(d, m, pf.camera, pf.step, guide)
+    ctx.predict_lightmaps(guide, W, H, nsl.NSL_PREC_F16, lm)
+    ctx.shade(lm, W, H, pf.camera, [pf.light], rgba)
+    torch.cuda.synchronize()
+    hg = np.zeros((3, H, W), np.float32)
+    hl = np.zeros((8, H, W), np.float32)
+    hr = np.zeros((4, H, W), np.float32)
+    nsl.nsl_render_frame_host(ctx.ctx, pf.density, pf.mask, pf.camera, [pf.light], pf.step,
+                              nsl.NSL_PREC_F16, hg, hl, hr)
+    assert np.array_equal(hg, guide.cpu().numpy())
+    assert np.array_equal(hl, lm.cpu().numpy())
+    assert np.array_equal(hr, rgba.cpu().numpy())
+    ctx.close()
+
+
 def test_render_frame_host_async_two_contexts(lib):
     """Frames alternating between two contexts on two streams through the
     asynchronous host entry point equal the synchronous call, frame by frame
