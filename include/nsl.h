@@ -406,7 +406,13 @@ NSL_API nsl_status nsl_shade(nsl_ctx* ctx, const float* lightmaps_dev, int width
 /* One whole frame from HOST buffers: copies density (and mask) to the device,
  * runs the guide, the network and the shading, copies guide, lightmaps and
  * rgba back, and synchronises `stream`.  Host pointers may be NULL for outputs
- * that are not wanted.  Uses context-owned device staging buffers.
+ * that are not wanted.  Uses context-owned device staging buffers.  The copies
+ * run on a copy stream owned by the context, overlapped with the kernels on
+ * `stream` (the grid goes up in slabs of z slices, each staged on arrival; the
+ * guide comes back while the network runs, the lightmaps while shading runs);
+ * `stream` waits for that copy stream before the call returns, so the frame is
+ * complete when `stream` is.  The outputs equal those of the device-buffer
+ * calls bit for bit.
  *   density_host  grid.dtype elements; mask_host may be NULL */
 NSL_API nsl_status nsl_render_frame_host(nsl_ctx* ctx, const void* density_host,
                                  const uint8_t* mask_host, const nsl_camera* cam,
@@ -415,7 +421,8 @@ NSL_API nsl_status nsl_render_frame_host(nsl_ctx* ctx, const void* density_host,
                                  float* lightmaps_host, float* rgba_host, void* stream);
 
 /* nsl_render_frame_host without the final synchronisation: every copy and
- * kernel is enqueued on `stream` and the call returns.  With page-locked host
+ * kernel is enqueued (on `stream` and on the context's copy stream, which
+ * `stream` then waits for) and the call returns.  With page-locked host
  * buffers the copies run asynchronously, so frames of two contexts on two
  * streams overlap one frame's copies with the other's kernels.  The caller
  * must not change the inputs nor read the outputs until the stream has
