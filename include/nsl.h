@@ -131,8 +131,12 @@ NSL_API void nsl_destroy(nsl_ctx* ctx);
 
 /* Stage a density grid into the context (Sec. 4.2: sigma_s in a 3D texture):
  * sigma' = sigma_scale * density * [mask == 0], kept in a context-owned device
- * buffer until the next staging.  A float32 grid is staged as float32 sigma';
- * a float16 grid is staged as float16 density * [mask == 0] (its values
+ * buffer until the next staging.  A float32 grid is staged as float32 sigma':
+ * as cells holding the 2x2x2 corner neighbourhood of each trilinear sample when
+ * those take at most 60% of the device's L2 (up to about 135^3 on a GB300), else
+ * as cells holding the 2x2 x/y neighbourhood of one slice (half the bytes); the
+ * two give bitwise equal guides.  A float16 grid is staged as float16 density *
+ * [mask == 0] in the second form (its values
  * exactly) and the march applies sigma_scale after the trilinear blend, which
  * differs from blending sigma' by rounding only.  A later
  * nsl_guiding_map with density_dev == NULL marches this resident grid.
@@ -161,8 +165,8 @@ NSL_API nsl_status nsl_guiding_map(nsl_ctx* ctx, const void* density_dev, const 
  * cudaMalloc at all: a render thread whose frame budget cannot absorb the device
  * synchronisation an allocation may cause, an engine whose own allocator owns
  * every byte of device memory, or code that has no context to keep between
- * frames.  It stages the grid with the kernel nsl_guiding_map uses (float32
- * quads of sigma' for a float32 grid, float16 quads for a float16 one) and then
+ * frames.  It stages the grid as x/y neighbourhood cells (float32 quads of
+ * sigma' for a float32 grid, float16 quads for a float16 one) and then
  * runs the single-pass march kernel (the one nsl_guide_sample_count runs) rather
  * than nsl_guiding_map's three-pass segmented march, which would need per-pixel
  * segment scratch.  The two marches make the same samples and decisions; their

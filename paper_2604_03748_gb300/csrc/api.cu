@@ -1,6 +1,7 @@
 // C ABI of libnsl: argument checking, contexts and orchestration of the
 // kernels of the guide march (Sec. 4.2), the lightmap network (Sec. 4.3) and
 // the six-way shading (Sec. 3).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,6 +25,19 @@ int num_sms() {
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
   __atomic_store_n(&cached[dev], v, __ATOMIC_RELEASE);
   return v;
+}
+
+// A single-plume float32 grid is staged as octo cells (one 32-byte load per
+// trilinear sample instead of two 16-byte ones: 3-4% faster marches measured
+// on the 128^3 workload) when the octo grid takes at most 60% of the L2, so
+// that it stays resident across the march like the quad grid (68.7 MB at 128^3
+// of GB300's 135.5 MB).  Larger grids, float16 grids, batches and serving keep
+// quad cells, which take half the bytes.
+bool octo_fits(int nx, int ny, int nz) {
+  int dev = 0, l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+    return false;
+  return (double)staged_octo_bytes(nx, ny, nz) <= 0.6 * (double)l2;
 }
 
 void set_error(const char* fmt, ...) {
@@ -119,6 +133,7 @@ struct nsl_ctx {
   std::vector<float> params;
   NetLayout layout{};
   float* staged = nullptr;          // staged extinction grid
+  bool octo = false;                // float32 grid staged as octo cells (see octo_fits)
   float* tvol = nullptr;            // transmittance volumes: raw top, raw bottom, staged top, staged bottom
   size_t tvol_bytes = 0;
   bool staged_valid = false;        // a staging has been queued
@@ -224,7 +239,10 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   c->params.resize(nf);
   std::memcpy(c->params.data(), b + 16, (size_t)nf * 4);
   cudaGetDevice(&c->device);
-  cudaError_t e = cudaMalloc(&c->staged, staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float));
+  c->octo = grid->dtype == NSL_F32 && octo_fits(grid->nx, grid->ny, grid->nz);
+  size_t sbytes = staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float);
+  if (c->octo) sbytes = std::max(sbytes, staged_octo_bytes(grid->nx, grid->ny, grid->nz));
+  cudaError_t e = cudaMalloc(&c->staged, sbytes);
   if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: staged grid"); }
   e = cudaMalloc(&c->tile_counter, 256);
   if (e != cudaSuccess) { nsl_destroy(c); return cuda_fail(e, "nsl_create: tile counter"); }
@@ -301,6 +319,18 @@ static uint32_t host_pcg(uint32_t v) {
   return (word >> 22u) ^ word;
 }
 
+// Stages cell planes [c0, c1) (c1 < 0: to the last) of the context's layout.
+static cudaError_t stage_planes(nsl_ctx* c, const void* density, const uint8_t* mask, int c0, int c1,
+                                cudaStream_t s) {
+  const nsl_grid_desc& g = c->grid;
+  if (g.dtype == NSL_F16)
+    return launch_stage_volume_half(static_cast<const __half*>(density), mask, g.nx, g.ny, g.nz,
+                                    reinterpret_cast<__half*>(c->staged), s, c0, c1);
+  if (c->octo)
+    return launch_stage_volume_octo(density, g.dtype, mask, g.nx, g.ny, g.nz, g.sigma_scale, c->staged, s, c0, c1);
+  return launch_stage_volume(density, g.dtype, mask, g.nx, g.ny, g.nz, g.sigma_scale, c->staged, s, c0, c1);
+}
+
 nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, void* stream) {
   if (!c) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: ctx is NULL");
   if (!density) return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: density is NULL");
@@ -308,12 +338,7 @@ nsl_status nsl_stage_grid(nsl_ctx* c, const void* density, const uint8_t* mask, 
     return fail(NSL_ERR_INVALID_ARG, "nsl_stage_grid: buffers must be 16-byte aligned");
   // an FP16 grid stays FP16 (half the march's gather bytes); sigma_scale is
   // applied after the trilinear blend
-  cudaError_t e = c->grid.dtype == NSL_F16
-                      ? launch_stage_volume_half(static_cast<const __half*>(density), mask, c->grid.nx, c->grid.ny,
-                                                 c->grid.nz, reinterpret_cast<__half*>(c->staged),
-                                                 static_cast<cudaStream_t>(stream))
-                      : launch_stage_volume(density, c->grid.dtype, mask, c->grid.nx, c->grid.ny, c->grid.nz,
-                                            c->grid.sigma_scale, c->staged, static_cast<cudaStream_t>(stream));
+  cudaError_t e = stage_planes(c, density, mask, 0, -1, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "nsl_stage_grid");
   c->staged_valid = true;
   return NSL_OK;
@@ -421,6 +446,11 @@ static nsl_status march_setup(nsl_ctx* c, const nsl_camera* cam, float step,
   if (st != NSL_OK) return st;
   p->vol = c->staged;
   p->staged_half = c->grid.dtype == NSL_F16;
+  p->staged_octo = c->octo ? 1 : 0;
+  if (c->octo) {   // 4 x 8 pixel tiles: measured 0.6% faster than 8 x 4 with octo cells
+    p->tx_log2 = 2;
+    p->tiles_x = (cam->width + 3) / 4;
+  }
   p->scl = c->grid.sigma_scale;
   return NSL_OK;
 }
@@ -759,15 +789,12 @@ static nsl_status render_frame_host(nsl_ctx* c, const void* density_host, const 
       NSL_CUDA_TRY(cudaMemcpyAsync(c->h_mask + off, mask_host + off, cnt, cudaMemcpyHostToDevice, a));
     NSL_CUDA_TRY(cudaEventRecord(ev[1 + k], a));
     NSL_CUDA_TRY(cudaStreamWaitEvent(s, ev[1 + k], 0));
-    // cell plane cz holds slice cz - 1 (clamped): planes z0 + 1 .. z1, and
-    // plane 0 with the first slab, plane nz + 1 with the last
-    const int c0 = k == 0 ? 0 : z0 + 1, c1 = k == nslab - 1 ? nz + 2 : z1 + 1;
-    const cudaError_t e =
-        c->grid.dtype == NSL_F16
-            ? launch_stage_volume_half(static_cast<const __half*>(c->h_density), mdev, c->grid.nx, c->grid.ny, nz,
-                                       reinterpret_cast<__half*>(c->staged), s, c0, c1)
-            : launch_stage_volume(c->h_density, c->grid.dtype, mdev, c->grid.nx, c->grid.ny, nz,
-                                  c->grid.sigma_scale, c->staged, s, c0, c1);
+    // a quad cell plane cz holds slice cz - 1 (clamped): planes z0 + 1 .. z1,
+    // plane 0 with the first slab, plane nz + 1 with the last; an octo plane
+    // cz holds slices cz - 1 and cz: planes z0 .. z1 - 1, plane nz with the last
+    const int c0 = k == 0 ? 0 : (c->octo ? z0 : z0 + 1);
+    const int c1 = k == nslab - 1 ? -1 : (c->octo ? z1 : z1 + 1);
+    const cudaError_t e = stage_planes(c, c->h_density, mdev, c0, c1, s);
     if (e != cudaSuccess) return cuda_fail(e, "nsl_render_frame_host: staging");
   }
   c->staged_valid = true;

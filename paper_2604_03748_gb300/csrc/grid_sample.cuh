@@ -1,22 +1,29 @@
-// Sampling of a staged density grid (padded quad layout, FP32 or FP16 quads),
+// Sampling of a staged density grid (padded quad or octo layout, FP32 or FP16),
 // shared by the guide march and the fine-step reference renderer.
 #pragma once
 #include "nsl_internal.cuh"
 
 namespace nsl {
 
-// Staged grid layouts (both hold sigma' = scale * rho * [mask == 0], float32,
-// padded by one cell on the low sides with every neighbour index clamped to the
-// grid, so a sample inside the box needs no clamping; GridH below is the quad
-// layout in FP16 holding rho * [mask == 0], scaled after the blend):
-//   kLayoutQuad    float4 per cell, the x/y 2x2 neighbourhood of its slice; a
-//                  sample reads 2 x 16 bytes (the default)
-//   kLayoutOcto    2 x float4 per cell, the 2x2x2 neighbourhood; a sample reads
-//                  one 32-byte vector (twice the memory)
+// Staged grid layouts.  All are padded by one cell on the low sides with every
+// neighbour index clamped to the grid, so a sample inside the box needs no
+// clamping:
+//   Grid   float4 per cell: the x/y 2x2 neighbourhood of sigma' = scale * rho *
+//          [mask == 0] in its slice; a sample reads 2 x 16 bytes
+//   GridO  2 x float4 per cell: the 2x2x2 neighbourhood of sigma'; a sample
+//          reads one 32-byte vector (twice the memory; single-plume float32
+//          contexts whose octo grid fits their L2 share)
+//   GridH  the quad layout in FP16 holding rho * [mask == 0], scaled after the
+//          blend
 struct Grid {
   const float* __restrict__ v;
   int nx, ny, nz;
   float fx, fy, fz;  // box extents
+};
+struct GridO {
+  const float* __restrict__ v;
+  int nx, ny, nz;
+  float fx, fy, fz;
 };
 // FP16 quads of the masked density rho (single-plume contexts with an FP16
 // grid): values exact, sigma = scl * (trilinear value); half the bytes
@@ -27,6 +34,7 @@ struct GridH {
   float scl;          // sigma_scale
 };
 __device__ __forceinline__ float scaled(const Grid&, float v) { return v; }
+__device__ __forceinline__ float scaled(const GridO&, float v) { return v; }
 __device__ __forceinline__ float scaled(const GridH& g, float v) { return __fmul_rn(g.scl, v); }
 
 // 32-byte load of an octo cell: the 2x2 x/y neighbourhood of slice z (a) and
@@ -48,13 +56,12 @@ __host__ __device__ __forceinline__ unsigned cell_index(int nx, int ny, unsigned
 
 // The two x/y quads of padded cell `cell` (slice z in a, z+1 in b).
 __device__ __forceinline__ void load_cell(const Grid& g, unsigned cell, unsigned pl, float4& a, float4& b) {
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    ldg_octo(g.v + 8 * (size_t)cell, a, b);
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
-    a = __ldg(q);
-    b = __ldg(q + pl);
-  }
+  const float4* q = reinterpret_cast<const float4*>(g.v) + cell;
+  a = __ldg(q);
+  b = __ldg(q + pl);
+}
+__device__ __forceinline__ void load_cell(const GridO& g, unsigned cell, unsigned, float4& a, float4& b) {
+  ldg_octo(g.v + 8 * (size_t)cell, a, b);
 }
 __device__ __forceinline__ float4 half4_to_float4(uint2 u) {
   const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
@@ -62,7 +69,6 @@ __device__ __forceinline__ float4 half4_to_float4(uint2 u) {
   return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 __device__ __forceinline__ void load_cell(const GridH& g, unsigned cell, unsigned pl, float4& a, float4& b) {
-  static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
   const uint2* q = reinterpret_cast<const uint2*>(g.v) + cell;
   a = half4_to_float4(__ldg(q));
   b = half4_to_float4(__ldg(q + pl));

@@ -398,6 +398,10 @@ __device__ __forceinline__ Grid plume_grid<Grid>(const MarchPlume& P) {
   return Grid{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
 }
 template <>
+__device__ __forceinline__ GridO plume_grid<GridO>(const MarchPlume& P) {
+  return GridO{P.vol, P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz};
+}
+template <>
 __device__ __forceinline__ GridH plume_grid<GridH>(const MarchPlume& P) {
   return GridH{reinterpret_cast<const __half*>(P.vol), P.nx, P.ny, P.nz, (float)P.nx, (float)P.ny, (float)P.nz,
                P.scl};
@@ -568,25 +572,26 @@ int march_tiles(int W, int H, int tx_log2) {
   return ((W + tx - 1) / tx) * ((H + ty - 1) / ty);
 }
 
+template <class G>
+static cudaError_t launch_march_g(const MarchPlume& p, int ntiles, int* tile_counter, cudaStream_t s, bool count) {
+  if (count) {
+    static const int grid = resident_blocks(march_kernel<false, true, G>);
+    march_kernel<false, true, G><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+  } else {
+    static const int grid = resident_blocks(march_kernel<false, false, G>);
+    march_kernel<false, false, G><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s, bool count) {
   const int ntiles = march_tiles(p.cam.W, p.cam.H, p.tx_log2);
   if (ntiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(tile_counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (count) {
-    int grid = march_grid<false, true>();
-    if (p.staged_half)
-      march_kernel<false, true, GridH><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
-    else
-      march_kernel<false, true><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
-  } else {
-    int grid = march_grid<false, false>();
-    if (p.staged_half)
-      march_kernel<false, false, GridH><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
-    else
-      march_kernel<false, false><<<grid, kMarchThreads, 0, s>>>(p, nullptr, 1, ntiles, tile_counter);
-  }
-  return cudaGetLastError();
+  if (p.staged_half) return launch_march_g<GridH>(p, ntiles, tile_counter, s, count);
+  if (p.staged_octo) return launch_march_g<GridO>(p, ntiles, tile_counter, s, count);
+  return launch_march_g<Grid>(p, ntiles, tile_counter, s, count);
 }
 
 cudaError_t launch_march_batch(const MarchPlume* table_dev, int nplumes, int total_tiles,
@@ -644,31 +649,35 @@ int march_max_segments(int nx, int ny, int nz, float h, int seg_len) {
   return (int)std::ceil(nmax / seg_len) + 1;
 }
 
+template <class G>
+static cudaError_t launch_march_segmented_g(const MarchPlume& p, int ntiles, int max_segments, int* tile_counter,
+                                           cudaStream_t s) {
+  const int warps_per_block = kMarchThreads / 32;
+  const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
+  cudaError_t e = launch_pdl(march_pixel_pass_kernel<1, G>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles,
+                             tile_counter);
+  if (e != cudaSuccess) return e;
+  const int nitems = ntiles * max_segments;
+  if (p.shadow_volume) {
+    static const int grid = resident_blocks(march_segment_kernel<true, G>);
+    e = launch_pdl(march_segment_kernel<true, G>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles, nitems,
+                   tile_counter);
+  } else {
+    static const int grid = resident_blocks(march_segment_kernel<false, G>);
+    e = launch_pdl(march_segment_kernel<false, G>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles, nitems,
+                   tile_counter);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_pdl(march_pixel_pass_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles, tile_counter);
+}
+
 cudaError_t launch_march_segmented(const MarchPlume& p, int max_segments, int* tile_counter,
                                    cudaStream_t s) {
   const int ntiles = march_tiles(p.cam.W, p.cam.H, p.tx_log2);
   if (ntiles == 0) return cudaSuccess;
-  const int warps_per_block = kMarchThreads / 32;
-  const int blocks = (ntiles + warps_per_block - 1) / warps_per_block;
-  cudaError_t e = p.staged_half ? launch_pdl(march_pixel_pass_kernel<1, GridH>, dim3(blocks),
-                                              dim3(kMarchThreads), 0, s, p, ntiles, tile_counter)
-                                 : launch_pdl(march_pixel_pass_kernel<1>, dim3(blocks), dim3(kMarchThreads), 0,
-                                              s, p, ntiles, tile_counter);
-  if (e != cudaSuccess) return e;
-  static const int grid = resident_blocks(march_segment_kernel<false>);
-  const int nitems = ntiles * max_segments;
-  if (p.staged_half)
-    e = p.shadow_volume ? launch_pdl(march_segment_kernel<true, GridH>, dim3(grid), dim3(kMarchThreads), 0, s, p,
-                                     ntiles, nitems, tile_counter)
-                        : launch_pdl(march_segment_kernel<false, GridH>, dim3(grid), dim3(kMarchThreads), 0, s, p,
-                                     ntiles, nitems, tile_counter);
-  else
-    e = p.shadow_volume ? launch_pdl(march_segment_kernel<true>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
-                                     nitems, tile_counter)
-                        : launch_pdl(march_segment_kernel<false>, dim3(grid), dim3(kMarchThreads), 0, s, p, ntiles,
-                                     nitems, tile_counter);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(march_pixel_pass_kernel<3>, dim3(blocks), dim3(kMarchThreads), 0, s, p, ntiles, tile_counter);
+  if (p.staged_half) return launch_march_segmented_g<GridH>(p, ntiles, max_segments, tile_counter, s);
+  if (p.staged_octo) return launch_march_segmented_g<GridO>(p, ntiles, max_segments, tile_counter, s);
+  return launch_march_segmented_g<Grid>(p, ntiles, max_segments, tile_counter, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,47 +897,13 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 
-// Staged cell c of the padded quad / octo layouts: the x/y 2x2 neighbourhood
-// whose low corner is voxel (a-1, b-1) of slice c_z - 1 (quad), or those of
-// slices c_z - 1 and c_z (octo), every index clamped into the grid.
-template <typename T>
-__device__ __forceinline__ void stage_one_cell(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
-                                               int nx, int ny, int nz, float scale,
-                                               float* __restrict__ out, size_t c) {
-  auto val = [&](size_t idx) {
-    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
-  };
-  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u;
-  const unsigned c32 = (unsigned)c;   // staged cells < 2^32 (grids up to 1024^3)
-  const int a = (int)(c32 % px);
-  const unsigned r = c32 / px;
-  const int b = (int)(r % py);
-  const int cz = (int)(r / py);
-  const int i0 = max(a - 1, 0), i1 = min(a, nx - 1);
-  const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
-  const int k0 = min(max(cz - 1, 0), nz - 1);
-  const size_t b0 = ((size_t)k0 * ny + j0) * nx, b1 = ((size_t)k0 * ny + j1) * nx;
-  const float4 lo = make_float4(val(b0 + i0), val(b0 + i1), val(b1 + i0), val(b1 + i1));
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    const int k1 = min(cz, nz - 1);
-    const size_t e0 = ((size_t)k1 * ny + j0) * nx, e1 = ((size_t)k1 * ny + j1) * nx;
-    reinterpret_cast<float4*>(out)[2 * c] = lo;
-    reinterpret_cast<float4*>(out)[2 * c + 1] =
-        make_float4(val(e0 + i0), val(e0 + i1), val(e1 + i0), val(e1 + i1));
-  } else {
-    reinterpret_cast<float4*>(out)[c] = lo;
-  }
-}
-
 // Staging work units: the quad layout is staged four cells at a time along x
 // (one thread loads the 5-voxel windows of its two rows once and writes 64
-// contiguous bytes; per cell that is 2.5 loads instead of 8); the octo layout
-// one cell at a time.
+// contiguous bytes; per cell that is 2.5 loads instead of 8).
 // In the y-fastest order the four cells of a unit run along y (one thread reads
 // the 5-voxel windows of its two x columns), and consecutive units along x, so
 // that a warp's loads of the source rows stay coalesced.
 __host__ __device__ __forceinline__ size_t stage_units(int nx, int ny, int nz) {
-  if (kMarchLayout == kLayoutOcto) return staged_cells(nx, ny, nz);
   if (kMarchOrder == 1) return ((size_t)nx + 1) * (((size_t)ny + 4) / 4) * ((size_t)nz + 2);
   const size_t px = (size_t)nx + 1, rows = ((size_t)ny + 1) * ((size_t)nz + 2);
   return rows * ((px + 3) / 4);
@@ -970,9 +945,7 @@ __device__ __forceinline__ void stage_unit_yfast(int nx, int ny, int nz, size_t 
 template <typename T>
 __device__ __forceinline__ void stage_unit(const T* __restrict__ rho, const uint8_t* __restrict__ mask, int nx,
                                            int ny, int nz, float scale, float* __restrict__ out, size_t u) {
-  if constexpr (kMarchLayout == kLayoutOcto) {
-    stage_one_cell<T>(rho, mask, nx, ny, nz, scale, out, u);
-  } else if constexpr (kMarchOrder == 1) {
+  if constexpr (kMarchOrder == 1) {
     auto val = [&](size_t idx) {
       return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
     };
@@ -1007,12 +980,11 @@ __device__ __forceinline__ void stage_unit(const T* __restrict__ rho, const uint
   }
 }
 
-// One thread per staged cell, writing the layout kMarchLayout of sigma' =
-// scale * rho * [mask == 0] with out-of-grid neighbours clamped to the edge.
-// The quad layout is padded: cell (a, b, c) of an (nx+1) x (ny+1) x (nz+2) array
-// holds the x/y 2x2 neighbourhood whose low corner is voxel (a-1, b-1) of slice
-// c-1, every index clamped into the grid.
-// Staging units [u0, u1) (all of them by default).
+// Staging of sigma' = scale * rho * [mask == 0] in the quad layout, with
+// out-of-grid neighbours clamped to the edge: cell (a, b, c) of an (nx+1) x
+// (ny+1) x (nz+2) array holds the x/y 2x2 neighbourhood whose low corner is
+// voxel (a-1, b-1) of slice c-1, every index clamped into the grid.  Staging
+// units [u0, u1).
 template <typename T>
 __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
                                                     const uint8_t* __restrict__ mask, int nx,
@@ -1024,17 +996,10 @@ __global__ void __launch_bounds__(256) stage_kernel(const T* __restrict__ rho,
     stage_unit<T>(rho, mask, nx, ny, nz, scale, out, u);
 }
 
-// Unit range of cell planes [c0, c1) (c1 < 0: to the last plane); the octo
-// layout's planes read two slices, so it is always staged whole.
-static void stage_range(int nx, int ny, int nz, int c0, int c1, size_t* u0, size_t* u1) {
-  const size_t n = stage_units(nx, ny, nz);
-  if (kMarchLayout == kLayoutOcto || c1 < 0) {
-    *u0 = kMarchLayout == kLayoutOcto ? 0 : (size_t)c0 * stage_units_per_plane(nx, ny);
-    *u1 = n;
-    return;
-  }
-  *u0 = (size_t)c0 * stage_units_per_plane(nx, ny);
-  *u1 = (size_t)c1 * stage_units_per_plane(nx, ny);
+// Unit range of cell planes [c0, c1) (c1 < 0: to the last plane).
+static void stage_range(size_t n, size_t per_plane, int c0, int c1, size_t* u0, size_t* u1) {
+  *u0 = (size_t)c0 * per_plane;
+  *u1 = c1 < 0 ? n : (size_t)c1 * per_plane;
   if (*u1 > n) *u1 = n;
   if (*u0 > *u1) *u0 = *u1;
 }
@@ -1048,7 +1013,7 @@ static int stage_blocks(size_t units) {
 cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* mask, int nx,
                                 int ny, int nz, float scale, float* staged, cudaStream_t s, int c0, int c1) {
   size_t u0, u1;
-  stage_range(nx, ny, nz, c0, c1, &u0, &u1);
+  stage_range(stage_units(nx, ny, nz), stage_units_per_plane(nx, ny), c0, c1, &u0, &u1);
   const int blocks = stage_blocks(u1 - u0);
   if (dtype == NSL_F16)
     return launch_pdl(stage_kernel<__half>, dim3(blocks), dim3(256), 0, s,
@@ -1107,11 +1072,77 @@ __global__ void __launch_bounds__(256) stage_half_kernel(const __half* __restric
 
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
                                      __half* staged, cudaStream_t s, int c0, int c1) {
-  static_assert(kMarchLayout == kLayoutQuad, "FP16 staging uses the quad layout");
   size_t u0, u1;
-  stage_range(nx, ny, nz, c0, c1, &u0, &u1);
+  stage_range(stage_units(nx, ny, nz), stage_units_per_plane(nx, ny), c0, c1, &u0, &u1);
   return launch_pdl(stage_half_kernel, dim3(stage_blocks(u1 - u0)), dim3(256), 0, s, density, mask, nx, ny, nz,
                     reinterpret_cast<uint2*>(staged), u0, u1);
+}
+
+// Octo staging (single-plume float32 contexts): cell (a, b, cz), cz in [0, nz],
+// holds the x/y 2x2 neighbourhoods of sigma' whose low corner is voxel
+// (a-1, b-1) of slice cz-1 (first float4) and of slice cz (second float4), every
+// index clamped into the grid, so a sample reads its eight corners in one
+// 32-byte load.  A unit is four cells along x: one thread loads the 5-voxel
+// windows of its four rows once.
+__host__ __device__ __forceinline__ size_t stage_octo_units_per_plane(int nx, int ny) {
+  return ((size_t)ny + 1) * (((size_t)nx + 4) / 4);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_octo_unit(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                                int nx, int ny, int nz, float scale, float* __restrict__ out,
+                                                size_t u) {
+  auto val = [&](size_t idx) {
+    return (mask && __ldg(mask + idx)) ? 0.f : __fmul_rn(scale, to_f<T>(rho[idx]));
+  };
+  const unsigned px = (unsigned)nx + 1u, py = (unsigned)ny + 1u, gpr = (px + 3u) / 4u;
+  const unsigned u32 = (unsigned)u;   // staged cells < 2^32 (checked at every entry point)
+  const unsigned r = u32 / gpr;       // row: (plane cz, padded y b)
+  const int a0 = (int)(4u * (u32 % gpr));
+  const int b = (int)(r % py), cz = (int)(r / py);
+  const int j0 = max(b - 1, 0), j1 = min(b, ny - 1);
+  const int k0 = min(max(cz - 1, 0), nz - 1), k1 = min(cz, nz - 1);
+  const size_t rw[4] = {((size_t)k0 * ny + j0) * nx, ((size_t)k0 * ny + j1) * nx, ((size_t)k1 * ny + j0) * nx,
+                        ((size_t)k1 * ny + j1) * nx};
+  float w[4][5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int x = min(max(a0 - 1 + t, 0), nx - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q][t] = val(rw[q] + x);
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (a0 + t < (int)px) {
+      float4* d = reinterpret_cast<float4*>(out) + 2 * (size_t)cell_index(nx, ny, (unsigned)(a0 + t), (unsigned)b,
+                                                                           (unsigned)cz);
+      d[0] = make_float4(w[0][t], w[0][t + 1], w[1][t], w[1][t + 1]);
+      d[1] = make_float4(w[2][t], w[2][t + 1], w[3][t], w[3][t + 1]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) stage_octo_kernel(const T* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                                         int nx, int ny, int nz, float scale, float* __restrict__ out,
+                                                         size_t u0, size_t u1) {
+  pdl_wait();      // the previous frame's march may still read the staged grid
+  pdl_trigger();
+  for (size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < u1; u += (size_t)gridDim.x * blockDim.x)
+    stage_octo_unit<T>(rho, mask, nx, ny, nz, scale, out, u);
+}
+
+cudaError_t launch_stage_volume_octo(const void* density, int dtype, const uint8_t* mask, int nx, int ny, int nz,
+                                     float scale, float* staged, cudaStream_t s, int c0, int c1) {
+  const size_t per = stage_octo_units_per_plane(nx, ny);
+  size_t u0, u1;
+  stage_range(per * ((size_t)nz + 1), per, c0, c1, &u0, &u1);
+  const int blocks = stage_blocks(u1 - u0);
+  if (dtype == NSL_F16)
+    return launch_pdl(stage_octo_kernel<__half>, dim3(blocks), dim3(256), 0, s, static_cast<const __half*>(density),
+                      mask, nx, ny, nz, scale, staged, u0, u1);
+  return launch_pdl(stage_octo_kernel<float>, dim3(blocks), dim3(256), 0, s, static_cast<const float*>(density), mask,
+                    nx, ny, nz, scale, staged, u0, u1);
 }
 
 // Transmittance volumes of the shadow_volume option: one thread per voxel
@@ -1141,6 +1172,8 @@ cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float*
   if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   if (p.staged_half)
     return launch_pdl(transmittance_volume_kernel<GridH>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
+  if (p.staged_octo)
+    return launch_pdl(transmittance_volume_kernel<GridO>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
   return launch_pdl(transmittance_volume_kernel<Grid>, dim3(blocks), dim3(256), 0, s, p, outT, outB);
 }
 
@@ -1199,8 +1232,8 @@ __device__ __forceinline__ void stage_units_range(const T* __restrict__ rho, con
     stage_unit<T>(rho, mask, nx, ny, nz, scale, out, u);
 }
 
-// staging units per block (2048 cells: 512 four-cell units, or 2048 octo cells)
-constexpr int kStageChunk = kMarchLayout == kLayoutOcto ? 2048 : 512;
+// staging units per block (2048 cells: 512 four-cell units)
+constexpr int kStageChunk = 512;
 
 __global__ void __launch_bounds__(256) stage_batch_kernel(const StageItem* __restrict__ items,
                                                           const int* __restrict__ block_starts,

@@ -105,6 +105,7 @@ struct MarchPlume {
   const float* vol;   // staged extinction sigma' = scale*rho*[mask==0], padded quad layout, fp32
                       // (staged_half: FP16 quads of rho*[mask==0], sigma = scl * value)
   int staged_half;
+  int staged_octo;    // vol holds float32 octo cells (single-plume contexts)
   float scl;
   int nx, ny, nz;
   CamFrame cam;
@@ -152,12 +153,6 @@ static_assert((1 << kMarchTXLog2) == kMarchTX, "march tile width: 1, 2, 4, 8 or 
 constexpr int kMarchThreads = 128;   // 4 independent warps per block
 constexpr int kMarchMinBlocks = NSL_MARCH_MIN_BLOCKS;  // register cap for occupancy
 
-// Staged grid layout (see march.cu): 2 x/y quads (default), 3 octo cells.
-constexpr int kLayoutQuad = 2, kLayoutOcto = 3;
-#ifndef NSL_MARCH_LAYOUT
-#define NSL_MARCH_LAYOUT 2
-#endif
-constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
 // Order of the staged quad cells in memory: 0 = x fastest, then y, then z;
 // 1 = y fastest, then x, then z.  Slices (z) are outermost in both, so the
 // quad of slice z+1 is one plane (PX * PY cells) further on.
@@ -166,22 +161,24 @@ constexpr int kMarchLayout = NSL_MARCH_LAYOUT;
 #endif
 constexpr int kMarchOrder = NSL_MARCH_ORDER;
 static_assert(kMarchOrder == 0 || kMarchOrder == 1, "staged cell order: 0 (x fastest) or 1 (y fastest)");
-static_assert(kMarchOrder == 0 || kMarchLayout == kLayoutQuad, "the y-fastest order is a quad layout");
-static_assert(kMarchLayout == kLayoutQuad || kMarchLayout == kLayoutOcto, "staged layout: 2 (quad) or 3 (octo)");
-// cells of the padded staged layouts: quad (nx+1)(ny+1)(nz+2) of 4 floats,
-// octo (nx+1)(ny+1)(nz+1) of 8 floats
+// Staged grid layouts (grid_sample.cuh): quad cells, (nx+1)(ny+1)(nz+2) of 4
+// values (float32 or float16), for every form; octo cells, (nx+1)(ny+1)(nz+1)
+// of 8 float32 values, for single-plume float32 contexts whose octo grid fits
+// the L2 share below (one 32-byte load per sample instead of two 16-byte ones).
 __host__ __device__ inline size_t staged_cells(int nx, int ny, int nz) {
-  return (size_t)(nx + 1) * (ny + 1) * (nz + (kMarchLayout == kLayoutOcto ? 1 : 2));
+  return (size_t)(nx + 1) * (ny + 1) * (nz + 2);
 }
+__host__ __device__ inline size_t staged_cells_octo(int nx, int ny, int nz) {
+  return (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+}
+inline size_t staged_octo_bytes(int nx, int ny, int nz) { return staged_cells_octo(nx, ny, nz) * 8 * sizeof(float); }
 // Grid sizes the march accepts: every axis in [1, 4096] and fewer than 2^32
 // staged cells (the march addresses staged cells with 32-bit indices).
 inline bool grid_dims_ok(int nx, int ny, int nz) {
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return false;
   return staged_cells(nx, ny, nz) < ((size_t)1 << 32);
 }
-inline size_t staged_floats(int nx, int ny, int nz) {
-  return staged_cells(nx, ny, nz) * (kMarchLayout == kLayoutOcto ? 8 : 4);
-}
+inline size_t staged_floats(int nx, int ny, int nz) { return staged_cells(nx, ny, nz) * 4; }
 cudaError_t launch_transmittance_volume(const MarchPlume& p, float* outT, float* outB, cudaStream_t s);
 // Staging of the cell planes [c0, c1) of the padded quad layout (c1 < 0: to the
 // last plane, nz + 1).  Cell plane cz reads density slice min(max(cz - 1, 0),
@@ -192,6 +189,11 @@ cudaError_t launch_stage_volume(const void* density, int dtype, const uint8_t* m
                                 int c1 = -1);
 cudaError_t launch_stage_volume_half(const __half* density, const uint8_t* mask, int nx, int ny, int nz,
                                      __half* staged, cudaStream_t s, int c0 = 0, int c1 = -1);
+// Octo staging (float32 values sigma' as in the quad layout): cell plane cz in
+// [0, nz] holds slices min(max(cz - 1, 0), nz - 1) and min(cz, nz - 1); planes
+// [c0, c1) (c1 < 0: to the last plane, nz).
+cudaError_t launch_stage_volume_octo(const void* density, int dtype, const uint8_t* mask, int nx, int ny, int nz,
+                                     float scale, float* staged, cudaStream_t s, int c0 = 0, int c1 = -1);
 int march_tiles(int W, int H, int tx_log2 = kMarchTXLog2);
 cudaError_t launch_march(const MarchPlume& p, int* tile_counter, cudaStream_t s,
                          bool count = false);

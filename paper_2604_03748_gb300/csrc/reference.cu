@@ -164,6 +164,9 @@ cudaError_t launch_reference_lightmaps(const MarchPlume& p, double hf, float g, 
   if (p.staged_half) {
     const GridH gh{reinterpret_cast<const __half*>(p.vol), p.nx, p.ny, p.nz, a.fx, a.fy, a.fz, p.scl};
     reference_kernel<GridH><<<blocks, 128, 0, s>>>(gh, a);
+  } else if (p.staged_octo) {
+    const GridO go{p.vol, p.nx, p.ny, p.nz, a.fx, a.fy, a.fz};
+    reference_kernel<GridO><<<blocks, 128, 0, s>>>(go, a);
   } else {
     const Grid gf{p.vol, p.nx, p.ny, p.nz, a.fx, a.fy, a.fz};
     reference_kernel<Grid><<<blocks, 128, 0, s>>>(gf, a);

@@ -56,6 +56,31 @@ def test_guide_parity_obstacle_128_full_size(lib, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("opts", [{}, dict(shadow_volume=1, t_min=0.0)])
+def test_guide_quad_staging_large_f32_grid(lib, orc, opts):
+    """A float32 grid whose octo cells would take more than 60% of the L2
+    (144^3: 97.6 MB) is staged as quad cells in a single-plume context; its
+    guide, through the host-buffer entry point too, matches the oracle."""
+    import dataclasses
+    from paper_2604_03748_gb300 import nsl
+    n = 144
+    vol = I.blob_fbm_volume(n, 31)
+    mask, _ = I.sphere_mask(n, 20.0, 31, lo=30.0, hi=float(n - 30))
+    pf = I.PlumeFrame(vol, mask, I.perspective_camera(n, 31, 48, 40), I.random_light(31), 2.0)
+    ctx = PT.make_ctx(pf)
+    g = PT.gpu_guide(ctx, pf, **opts)
+    o, s, f = orc.guide(pf.density, pf.mask, pf.camera, pf.step, **opts)
+    errs, bad = PT.compare_guide(g, o, f)
+    assert max(errs) <= PT.TOL_GUIDE, errs
+    assert bad <= PT.MAX_EXCUSED_FRAC * g[0].size
+    if not opts:
+        hg = np.zeros((3, 40, 48), np.float32)
+        nsl.nsl_render_frame_host(ctx.ctx, pf.density, pf.mask, pf.camera, [pf.light], pf.step,
+                                  nsl.NSL_PREC_F16, hg, None, None)
+        assert np.array_equal(hg.astype(np.float64), g)
+    ctx.close()
+
+
 @pytest.mark.parametrize("opts", [dict(jitter=0, t_min=0.0), dict(segment_exact=1),
                                   dict(phase_g=0.5, surrogate_I=(1.0, 0.5, 2.0)),
                                   dict(seed=123, frame=77, tau_depth=0.2),
