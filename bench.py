@@ -56,9 +56,10 @@ def net_flop_per_pixel(c0=16):
     return f
 # DRAM bytes (read + write) of the three march passes of one frame of this
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum with
-# --cache-control none on the current march kernels (the staged grid is in L2
-# when the view pass starts; the writes are the segment scratch and the guide).
-MARCH_DRAM_BYTES = 2_340_864 + 19_301_376
+# --cache-control none on the current march kernels (octo-staged grid, in L2
+# when the view pass starts; the writes are the segment scratch, the guide and
+# write-backs of staged cells).
+MARCH_DRAM_BYTES = 24_114_688 + 46_593_280
 
 
 def peaks():

@@ -133,9 +133,10 @@ NSL_API void nsl_destroy(nsl_ctx* ctx);
  * sigma' = sigma_scale * density * [mask == 0], kept in a context-owned device
  * buffer until the next staging.  A float32 grid is staged as float32 sigma':
  * as cells holding the 2x2x2 corner neighbourhood of each trilinear sample when
- * those take at most 60% of the device's L2 (up to about 135^3 on a GB300), else
- * as cells holding the 2x2 x/y neighbourhood of one slice (half the bytes); the
- * two give bitwise equal guides.  A float16 grid is staged as float16 density *
+ * those, together with the same cells of the other live contexts on the device,
+ * take at most 60% of its L2 (one grid of up to about 135^3 on a GB300; chosen
+ * at nsl_create), else as cells holding the 2x2 x/y neighbourhood of one slice
+ * (half the bytes); the two give bitwise equal guides.  A float16 grid is staged as float16 density *
  * [mask == 0] in the second form (its values
  * exactly) and the march applies sigma_scale after the trilinear blend, which
  * differs from blending sigma' by rounding only.  A later

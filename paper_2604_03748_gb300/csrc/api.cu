@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -29,15 +30,32 @@ int num_sms() {
 
 // A single-plume float32 grid is staged as octo cells (one 32-byte load per
 // trilinear sample instead of two 16-byte ones: 3-4% faster marches measured
-// on the 128^3 workload) when the octo grid takes at most 60% of the L2, so
-// that it stays resident across the march like the quad grid (68.7 MB at 128^3
-// of GB300's 135.5 MB).  Larger grids, float16 grids, batches and serving keep
-// quad cells, which take half the bytes.
-bool octo_fits(int nx, int ny, int nz) {
-  int dev = 0, l2 = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
-    return false;
-  return (double)staged_octo_bytes(nx, ny, nz) <= 0.6 * (double)l2;
+// on the 128^3 workload) while the octo grids of all live contexts on the
+// device take at most 60% of its L2 (81 MB of GB300's 135.5 MB; 68.7 MB at
+// 128^3), so that a grid stays resident across its march like a quad grid
+// even when several contexts' frames run at once: two 128^3 octo grids in
+// flight together overflowed the L2 and halved the two-stream rate.  Larger
+// grids, further contexts, float16 grids, batches and serving keep quad cells,
+// which take half the bytes.  octo_reserve() books the grid's bytes,
+// octo_release() returns them when the context is destroyed.
+namespace {
+std::mutex g_octo_mu;
+size_t g_octo_bytes[64] = {};
+}  // namespace
+
+bool octo_reserve(int dev, size_t bytes) {
+  int l2 = 0;
+  if (dev < 0 || dev >= 64 || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lk(g_octo_mu);
+  if ((double)(g_octo_bytes[dev] + bytes) > 0.6 * (double)l2) return false;
+  g_octo_bytes[dev] += bytes;
+  return true;
+}
+
+void octo_release(int dev, size_t bytes) {
+  if (dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_octo_mu);
+  g_octo_bytes[dev] = g_octo_bytes[dev] >= bytes ? g_octo_bytes[dev] - bytes : 0;
 }
 
 void set_error(const char* fmt, ...) {
@@ -133,7 +151,7 @@ struct nsl_ctx {
   std::vector<float> params;
   NetLayout layout{};
   float* staged = nullptr;          // staged extinction grid
-  bool octo = false;                // float32 grid staged as octo cells (see octo_fits)
+  bool octo = false;                // float32 grid staged as octo cells (see octo_reserve)
   float* tvol = nullptr;            // transmittance volumes: raw top, raw bottom, staged top, staged bottom
   size_t tvol_bytes = 0;
   bool staged_valid = false;        // a staging has been queued
@@ -239,7 +257,7 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
   c->params.resize(nf);
   std::memcpy(c->params.data(), b + 16, (size_t)nf * 4);
   cudaGetDevice(&c->device);
-  c->octo = grid->dtype == NSL_F32 && octo_fits(grid->nx, grid->ny, grid->nz);
+  c->octo = grid->dtype == NSL_F32 && octo_reserve(c->device, staged_octo_bytes(grid->nx, grid->ny, grid->nz));
   size_t sbytes = staged_floats(grid->nx, grid->ny, grid->nz) * sizeof(float);
   if (c->octo) sbytes = std::max(sbytes, staged_octo_bytes(grid->nx, grid->ny, grid->nz));
   cudaError_t e = cudaMalloc(&c->staged, sbytes);
@@ -267,6 +285,7 @@ nsl_status nsl_create(const nsl_grid_desc* grid, const void* blob, size_t blob_b
 void nsl_destroy(nsl_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  if (c->octo) octo_release(c->device, staged_octo_bytes(c->grid.nx, c->grid.ny, c->grid.nz));
   cudaFree(c->staged);
   cudaFree(c->tvol);
   cudaFree(c->counter);
