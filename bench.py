@@ -809,16 +809,20 @@ def bench_animated(nsl, I, dev, args, with_oracle):
                      "ms_per_frame": float(ms.mean()), "p50_ms": float(np.percentile(ms, 50)),
                      "p99_ms": float(np.percentile(ms, 99)), "max_ms": float(ms.max())}
     if with_oracle:
-        # FP64 oracle guide on a 64-row band of the middle frame against this run's guide
+        # FP64 oracle guide on a 64-row band of the first, middle and last
+        # frames against this run's guides (the middle frame's guide then feeds
+        # the network comparison below)
         import oracle
-        frame(mid)
-        torch.cuda.synchronize()
-        g = guide.cpu().numpy()
-        host = seq.frames[mid].cpu().numpy()
-        t1 = time.perf_counter()
-        o, _, _ = oracle.guide(host, None, seq.cameras[mid], seq.step, rows=(480, 544))
-        dt = time.perf_counter() - t1
-        out["err_vs_oracle"] = {f"guide_band_frame{mid}": range_errs(g[:, 480:544], o[:, 480:544])}
+        out["err_vs_oracle"] = {}
+        for t in (0, nf - 1, mid):
+            frame(t)
+            torch.cuda.synchronize()
+            g = guide.cpu().numpy()
+            host = seq.frames[t].cpu().numpy()
+            t1 = time.perf_counter()
+            o, _, _ = oracle.guide(host, None, seq.cameras[t], seq.step, rows=(480, 544))
+            dt = time.perf_counter() - t1
+            out["err_vs_oracle"][f"guide_band_frame{t}"] = range_errs(g[:, 480:544], o[:, 480:544])
         # the FP8 and FP16 networks on this frame's guide against the oracle's
         # emulation of the FP8 form and the FP64 network on the same guide
         flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)

@@ -54,6 +54,18 @@ def test_reference_float16_grid_and_ragged_box(lib, orc):
     assert max(PT.range_err(got, ref)) <= TOL_REFERENCE
 
 
+def test_reference_quad_staged_large_grid(lib, orc):
+    """A float32 grid too large for octo cells in the L2 share (144^3) is staged
+    as quad cells; the reference renderer reads those the same way."""
+    vol = I.blob_fbm_volume(144, 35)
+    cam = I.perspective_camera(144, 35, 8, 8)
+    pf = I.PlumeFrame(vol, None, cam, I.random_light(35), 2.0)
+    got = _gpu_reference(pf, 1.0)
+    ref = orc.reference_lightmaps(pf.density, pf.mask, pf.camera, hf=1.0)
+    assert ref[:6].max() > 0
+    assert max(PT.range_err(got, ref)) <= TOL_REFERENCE
+
+
 def test_reference_empty_volume(lib):
     pf = I.small_case(16, 16, 16, seed=34, kind=I.ORTHO, step=2.0, with_mask=False)
     pf.density = np.zeros_like(pf.density)
