@@ -566,7 +566,7 @@ def main():
         gr = torch.empty((3, H, W), dtype=torch.float32, device=dev)
         nrep = max(5, min(args.steps, 50))
         for name, pr in (("f32", nsl.NSL_PREC_F32), ("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16),
-                         ("fp8", nsl.NSL_PREC_FP8)):
+                         ("fp8", nsl.NSL_PREC_FP8), ("bf16x3", nsl.NSL_PREC_BF16X3)):
             lmr = torch.empty((8, H, W), dtype=torch.float32, device=dev)
 
             def frame_p(evs=None):
@@ -1038,7 +1038,9 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
                        "perspective fov 40, step 2 voxels, seed 4",
            "pixels_per_step": pixels, "voxels": int(sum(p.n ** 3 for p in spec))}
     b = nsl.Batch(blob, 64)
-    for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16)):
+    # bf16x3: the split-BF16 network (three BF16 tensor-core products per
+    # multiply, binary32 activations), the BF16 form that meets 2e-2 of range
+    for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16), ("bf16x3", nsl.NSL_PREC_BF16X3)):
         tune_ms = b.autotune(items, prec, stream=stream)
         tuning = b.get_tuning()
         b.capture_graph(items, prec, stream)
@@ -1115,19 +1117,20 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
     out["plain_f32_single_plume"] = {"value": pixels / (ms / 1e3) / 1e6, "unit": "Mpix/s", "ms_per_step": ms,
                                      "launches_per_step": 64 * (1 + 3 + 20 + 1)}
     out["speedup_bf16_vs_plain_f32"] = out["bf16"]["value"] / out["plain_f32_single_plume"]["value"]
+    out["speedup_bf16x3_vs_plain_f32"] = out["bf16x3"]["value"] / out["plain_f32_single_plume"]["value"]
     for c in ctxs.values():
         c.close()
 
     if with_oracle:
         # FP64 oracle on 8 plumes of the batch drawn with a seeded generator:
-        # timed (CPU baseline of this form) and compared with the batch's BF16
-        # and F16 output
+        # timed (CPU baseline of this form) and compared with the batch's BF16,
+        # F16 and split-BF16 output
         import oracle
         flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
         order = sorted(np.random.default_rng(4).choice(len(spec), size=8, replace=False).tolist())
         b = nsl.Batch(blob, 64)
         res = {}
-        for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16)):
+        for name, prec in (("bf16", nsl.NSL_PREC_BF16), ("f16", nsl.NSL_PREC_F16), ("bf16x3", nsl.NSL_PREC_BF16X3)):
             b.render(items, prec, stream=stream)
             torch.cuda.synchronize()
             res[name] = [(items[k]["guide"].cpu().numpy(), items[k]["lightmaps"].cpu().numpy()) for k in order]
@@ -1141,7 +1144,7 @@ def _bench_batched(nsl, I, dev, stream, flush, args, with_oracle):
             g, _, _ = oracle.guide(dens, None, p.camera, p.step)
             lm = oracle.net_forward(g, flat, 16, 1.0 / math.sqrt(3.0 * p.n * p.n))
             px += p.camera.width * p.camera.height
-            for name in ("bf16", "f16"):
+            for name in ("bf16", "f16", "bf16x3"):
                 e = errs.setdefault(name, {"guide": [], "lightmaps": []})
                 e["guide"].append(max(range_errs(res[name][j][0], g)))
                 e["lightmaps"].append(max(range_errs(res[name][j][1], lm)))

@@ -55,7 +55,7 @@ typedef enum {
 enum { NSL_F32 = 0, NSL_F16 = 1 };                           /* density storage */
 /* network arithmetic: FP32 SIMT; or tensor cores with FP32 accumulation and
  * BF16, FP8 E4M3 or FP16 operands */
-enum { NSL_PREC_F32 = 0, NSL_PREC_BF16 = 1, NSL_PREC_FP8 = 2, NSL_PREC_F16 = 3 };
+enum { NSL_PREC_F32 = 0, NSL_PREC_BF16 = 1, NSL_PREC_FP8 = 2, NSL_PREC_F16 = 3, NSL_PREC_BF16X3 = 4 };
 enum { NSL_CAM_ORTHO = 0, NSL_CAM_PERSP = 1 };
 
 typedef struct nsl_ctx nsl_ctx; /* opaque, library-owned */
@@ -291,9 +291,19 @@ NSL_API nsl_status nsl_reference_lightmaps(nsl_ctx* ctx, const void* density_dev
 /* Lightmap network, Sec. 4.3 / Fig. 3.
  *   guide_dev      [3][H][W] float32 guide
  *   width, height  multiples of 8, within the context maximum
- *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16, NSL_PREC_F16 or
- *                  NSL_PREC_FP8 (tensor cores, FP32 accumulation; C0 = 16
- *                  contexts only, NSL_ERR_UNSUPPORTED at C0 = 32)
+ *   precision      NSL_PREC_F32 (SIMT FP32), NSL_PREC_BF16, NSL_PREC_F16,
+ *                  NSL_PREC_FP8 or NSL_PREC_BF16X3 (tensor cores, FP32
+ *                  accumulation; C0 = 16 contexts only, NSL_ERR_UNSUPPORTED at
+ *                  C0 = 32).  NSL_PREC_BF16X3 is the split-BF16 form: every
+ *                  convolution after the first takes the bfloat16 high part
+ *                  hi = bf16(x) and low part lo = bf16(x - hi) of both
+ *                  operands and adds hi*hi + hi*lo + lo*hi (three BF16
+ *                  tensor-core products per multiply) on binary32 activations;
+ *                  the adapters run as in the other tensor-core networks.  It is
+ *                  the BF16 form within 2e-2 of the range of the FP64 network
+ *                  (single-BF16 operands are several percent away on seeded
+ *                  weights).  Its first call on a context may grow the context's
+ *                  workspace (binary32 activations), which synchronises `stream`.
  *   lightmaps_dev  output [8][H][W] float32 planes
  *                  [+X right, -X left, +Y top, -Y bottom, +Z back, -Z front, T, E] */
 NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, int width, int height,
@@ -303,7 +313,8 @@ NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, i
  * same network run, which also copies every convolution's stored output into
  * trace_dev, so that each layer can be compared with an emulation of its
  * arithmetic on the same input.  Tensor-core precisions only (NSL_PREC_BF16,
- * NSL_PREC_F16, NSL_PREC_FP8; NSL_PREC_F32 returns NSL_ERR_UNSUPPORTED).
+ * NSL_PREC_F16, NSL_PREC_FP8; NSL_PREC_F32 and NSL_PREC_BF16X3 return
+ * NSL_ERR_UNSUPPORTED).
  *   trace_dev     caller-owned device buffer, 16-byte aligned, of at least
  *                 nsl_lightmap_trace_bytes(width, height) bytes; it receives
  *                 the 17 stored tensors in network order (enc1a, enc1b,
@@ -472,8 +483,10 @@ NSL_API nsl_status nsl_batch_create(const void* weights_blob, size_t blob_bytes,
 NSL_API void nsl_batch_destroy(nsl_batch* b);
 
 /* Guide, lightmaps and (where rgba_dev is set) shading for n plumes, with one
- * set of march options for all; precision NSL_PREC_F16, NSL_PREC_BF16 or
- * NSL_PREC_FP8.
+ * set of march options for all; precision NSL_PREC_F16, NSL_PREC_BF16,
+ * NSL_PREC_FP8 or NSL_PREC_BF16X3 (the split-BF16 form, see
+ * nsl_predict_lightmaps; its per-plume network scratch is about twice that of
+ * the 16-bit forms).
  * Asynchronous on `stream`; the caller owns every buffer of `plumes`. */
 NSL_API nsl_status nsl_batch_render(nsl_batch* b, const nsl_plume* plumes, int n,
                                     const nsl_march_opts* opts, int precision, void* stream);

@@ -489,6 +489,8 @@ template cudaError_t adapters_reduce_only_group<__half>(const AdapterParamSet&, 
 template cudaError_t adapters_reduce_only_group<__nv_bfloat16>(const AdapterParamSet&,
                                                                const AdapterImg<__nv_bfloat16>*, int,
                                                                cudaStream_t);
+template cudaError_t adapters_reduce_only_group<float>(const AdapterParamSet&, const AdapterImg<float>*, int,
+                                                       cudaStream_t);
 
 
 template cudaError_t adapters_run<float>(const AdapterParamSet&, const float*, float*, float*,

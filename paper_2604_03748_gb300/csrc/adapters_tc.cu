@@ -68,21 +68,23 @@ struct AdapterTcDev {
 };
 
 template <typename T> __device__ __forceinline__ float tof(T v);
+template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
 template <> __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename T> __device__ __forceinline__ T fromf(float v);
 template <> __device__ __forceinline__ __half fromf<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 fromf<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// n (a multiple of 8) channels of a 16-bit NHWC row into floats
+// n (a multiple of 8) channels of a 16-bit or binary32 NHWC row into floats
 template <typename T, int N>
 __device__ __forceinline__ void load_row(const T* p, float* v) {
+  constexpr int PER = 16 / (int)sizeof(T);   // values per 16-byte load
 #pragma unroll
-  for (int q = 0; q < N / 8; ++q) {
+  for (int q = 0; q < N / PER; ++q) {
     const uint4 t = __ldg(reinterpret_cast<const uint4*>(p) + q);
     const T* h = reinterpret_cast<const T*>(&t);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[8 * q + k] = tof<T>(h[k]);
+    for (int k = 0; k < PER; ++k) v[PER * q + k] = tof<T>(h[k]);
   }
 }
 
@@ -389,11 +391,13 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
 
   // this thread's pixel of a block: raw x1 (64 channels) and F (16 channels);
   // the next block's are loaded while the current block's GEMMs run
-  uint4 rx[8], rf[2];
+  constexpr int RF = C * (int)sizeof(TA) / 16;   // 16-byte loads of a pixel's F row
+  uint4 rx[8], rf[RF];
   auto fetch = [&](int blk) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) rx[q] = make_uint4(0, 0, 0, 0);
-    rf[0] = rf[1] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int q = 0; q < RF; ++q) rf[q] = make_uint4(0, 0, 0, 0);
     if (blk >= total) return;
     const int kk = find_group(G.px_start, G.nimg, blk);
     const AdapterImg<TA>& m = G.img[kk];
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
     for (int q = 0; q < 8; ++q)
       rx[q] = __ldg(reinterpret_cast<const uint4*>(m.x1 + x1_index(m.H * m.W, pp, 8 * q)));
 #pragma unroll
-    for (int q = 0; q < 2; ++q) rf[q] = __ldg(reinterpret_cast<const uint4*>(m.F + (size_t)pp * C) + q);
+    for (int q = 0; q < RF; ++q) rf[q] = __ldg(reinterpret_cast<const uint4*>(m.F + (size_t)pp * C) + q);
   };
   pdl_wait();      // x1 and the attention weights come from pass 1 and the reduction
   pdl_trigger();
@@ -431,10 +435,10 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
         for (int e = 0; e < 8; ++e) xv[8 * q + e] = __half2float(h[e]) * att[8 * q + e];
       }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < RF; ++q) {
         const TA* h = reinterpret_cast<const TA*>(&rf[q]);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) f[8 * q + e] = tof<TA>(h[e]);
+        for (int e = 0; e < C / RF; ++e) f[(C / RF) * q + e] = tof<TA>(h[e]);
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a) put16(A, 2 * a, tid, xv + a * C);
@@ -657,5 +661,7 @@ template cudaError_t adapters_tc_run_group<__half>(const AdapterTcWeights*, cons
 template cudaError_t adapters_tc_run_group<__nv_bfloat16>(const AdapterTcWeights*, const AdapterParamSet&,
                                                           const AdapterImg<__nv_bfloat16>*, int,
                                                           unsigned int*, cudaStream_t);
+template cudaError_t adapters_tc_run_group<float>(const AdapterTcWeights*, const AdapterParamSet&,
+                                                  const AdapterImg<float>*, int, unsigned int*, cudaStream_t);
 
 }  // namespace nsl

@@ -160,7 +160,8 @@ struct nsl_ctx {
   void* seg_scratch = nullptr;            // segmented-march scratch
   size_t seg_bytes = 0;
   NetF32Weights* wf32 = nullptr;
-  NetTcWeights* wtc[3] = {};        // tensor-core weights: [0] FP16, [1] BF16, [2] FP8 (built on first use)
+  NetTcWeights* wtc[kTcElems] = {}; // tensor-core weights: [0] FP16, [1] BF16, [2] FP8, [3] split BF16
+                                    // (built on first use)
   void* ws = nullptr;               // network workspace (shared by both precisions)
   size_t ws_bytes = 0;
   unsigned int* err_host = nullptr; // device-written error word (mapped host memory)
@@ -292,9 +293,7 @@ void nsl_destroy(nsl_ctx* c) {
   cudaFree(c->tile_counter);
   cudaFree(c->seg_scratch);
   net_f32_destroy(c->wf32);
-  net_tc_destroy(c->wtc[0]);
-  net_tc_destroy(c->wtc[1]);
-  net_tc_destroy(c->wtc[2]);
+  for (NetTcWeights* w : c->wtc) net_tc_destroy(w);
   cudaFree(c->ws);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->aux) cudaStreamDestroy(c->aux);
@@ -615,11 +614,23 @@ static nsl_status predict(nsl_ctx* c, const float* guide, int width, int height,
       break;
     case NSL_PREC_BF16:
     case NSL_PREC_F16:
-    case NSL_PREC_FP8: {
+    case NSL_PREC_FP8:
+    case NSL_PREC_BF16X3: {
       if (c->layout.c0 != kC0)
         return fail(NSL_ERR_UNSUPPORTED, "%s: the tensor-core networks are built for C0=16 (this blob: C0=%d)",
                     fn, c->layout.c0);
-      const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
+      const int elem = tc_elem_of(precision);
+      if (elem == 3 && trace) return fail(NSL_ERR_UNSUPPORTED, "%s: no trace of the split-BF16 network", fn);
+      const size_t need = net_tc_workspace_bytes(c->max_w, c->max_h, elem);
+      if (need > c->ws_bytes) {
+        // the split-BF16 network keeps binary32 activations: grow the workspace once
+        NSL_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+        NSL_CUDA_TRY(cudaMalloc(&c->ws, need));
+        c->ws_bytes = need;
+      }
       if (!c->wtc[elem]) {
         c->wtc[elem] = net_tc_create(c->params.data(), c->layout, elem, &e);
         if (!c->wtc[elem]) return cuda_fail(e, "nsl_predict_lightmaps: tensor-core weights");

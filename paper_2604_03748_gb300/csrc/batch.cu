@@ -54,7 +54,7 @@ struct nsl_batch {
   std::vector<float> params;
   NetLayout layout{};
   NetF32Weights* wf = nullptr;
-  NetTcWeights* wtc[3] = {};         // FP16, BF16, FP8
+  NetTcWeights* wtc[kTcElems] = {};  // FP16, BF16, FP8, split BF16
   // device memory, grown on demand (never while a graph is being captured)
   void* staged = nullptr;  size_t staged_bytes = 0;
   void* seg = nullptr;     size_t seg_bytes = 0;
@@ -126,11 +126,12 @@ nsl_status validate_plume(const nsl_plume& pl, int k, bool prestaged) {
 namespace nsl {
 // Device scratch one plume takes in a batch: segment starts of the march and
 // the network workspace (each rounded up to 256 bytes).
-void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes) {
+void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes, int precision) {
   const size_t P = (size_t)p.camera.width * p.camera.height;
   const int maxseg = march_max_segments(p.grid.nx, p.grid.ny, p.grid.nz, p.step_voxels, seg_len);
   *seg_bytes = align256(P * sizeof(int)) + align256(3 * (size_t)maxseg * P * sizeof(float));
-  *net_bytes = align256(net_tc_workspace_bytes(p.camera.width, p.camera.height));
+  const int elem = tc_elem_of(precision);
+  *net_bytes = align256(net_tc_workspace_bytes(p.camera.width, p.camera.height, elem < 0 ? 0 : elem));
 }
 }  // namespace nsl
 
@@ -144,8 +145,8 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
                    std::vector<void*>* ws, Totals* tot, const float* const* prestaged) {
   if (n < 1 || n > b->max_plumes || n > kMaxGroup)
     return fail(NSL_ERR_INVALID_ARG, "nsl_batch: n must be in [1, %d]", b->max_plumes);
-  if (precision != NSL_PREC_BF16 && precision != NSL_PREC_F16 && precision != NSL_PREC_FP8)
-    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: batched network needs NSL_PREC_BF16, F16 or FP8");
+  if (tc_elem_of(precision) < 0)
+    return fail(NSL_ERR_UNSUPPORTED, "nsl_batch: batched network needs NSL_PREC_BF16, F16, FP8 or BF16X3");
   size_t staged = 0, seg = 0, net = 0;
   std::vector<size_t> off_staged(n), off_seg(n), off_net(n);
   std::vector<int> maxseg(n);
@@ -157,7 +158,7 @@ nsl_status prepare(nsl_batch* b, Tables& T, const nsl_plume* pl, int n, const ns
     if (!(prestaged && prestaged[k])) staged += align256(staged_grid_bytes(g));
     maxseg[k] = march_max_segments(g.nx, g.ny, g.nz, pl[k].step_voxels, b->seg_len);
     size_t sb, nb;
-    batch_plume_scratch(pl[k], b->seg_len, &sb, &nb);
+    batch_plume_scratch(pl[k], b->seg_len, &sb, &nb, precision);
     off_seg[k] = seg;
     seg += sb;
     off_net[k] = net;
@@ -273,7 +274,7 @@ nsl_status render(nsl_batch* b, const nsl_plume* pl, int n, const nsl_march_opts
                                      b->dev->tile_counts, n, T.tile_starts[n], T.item_starts[n],
                                      per_sm * num_sms(), b->counter, s);
   if (e != cudaSuccess) return cuda_fail(e, "nsl_batch: march");
-  const int elem = precision == NSL_PREC_BF16 ? 1 : (precision == NSL_PREC_FP8 ? 2 : 0);
+  const int elem = tc_elem_of(precision);
   if (!b->wtc[elem]) {
     if (b->capturing) return fail(NSL_ERR_INVALID_ARG, "nsl_batch: weights not built before capture");
     b->wtc[elem] = net_tc_create(b->params.data(), b->layout, elem, &e);
@@ -375,9 +376,7 @@ void nsl_batch_destroy(nsl_batch* b) {
   cudaDeviceSynchronize();
   drop_graph(b);
   net_f32_destroy(b->wf);
-  net_tc_destroy(b->wtc[0]);
-  net_tc_destroy(b->wtc[1]);
-  net_tc_destroy(b->wtc[2]);
+  for (NetTcWeights* w : b->wtc) net_tc_destroy(w);
   cudaFree(b->staged);
   cudaFree(b->seg);
   cudaFree(b->net);

@@ -537,6 +537,8 @@ template cudaError_t simt_first_conv_group<__nv_bfloat16>(const NetF32Weights*, 
                                                           cudaStream_t);
 template cudaError_t simt_first_conv_group<__half>(const NetF32Weights*, const NetImage*,
                                                    __half* const*, float* const*, int, cudaStream_t);
+template cudaError_t simt_first_conv_group<float>(const NetF32Weights*, const NetImage*, float* const*,
+                                                  float* const*, int, cudaStream_t);
 template cudaError_t simt_first_conv_half<__nv_bfloat16>(const NetF32Weights*, const NetImage&,
                                                          __nv_bfloat16*, cudaStream_t);
 template cudaError_t simt_first_conv_half<__half>(const NetF32Weights*, const NetImage&, __half*,

@@ -754,6 +754,368 @@ __global__ void __launch_bounds__(128) convT_tc_kernel(TcConvTArgs<T> a) {
   if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Split-BF16 convolutions (NSL_PREC_BF16X3).  Activations are binary32 NHWC
+// between layers; every operand x (activation or weight) is split into a
+// bfloat16 high part hi = bf16(x) and the bfloat16 rounding of the remainder
+// lo = bf16(x - hi) (x - hi is exact in binary32), and each product is taken
+// as hi*hi + hi*lo + lo*hi: three kind::f16 MMAs with BF16 operands into the
+// same FP32 accumulator (the lo*lo term, below 2^-16 of the product, is
+// dropped).  The input channels are taken in chunks of up to 64 (16 planes:
+// 8 of hi parts, 8 of lo parts, 46 KB of halo), so that the 128-channel
+// layers fit in shared memory beside their hi + lo weights; a CTA stages a
+// chunk, runs its MMAs, waits for them, and stages the next chunk into the
+// same buffer.  The weights of all chunks stay in shared memory.
+// ---------------------------------------------------------------------------
+
+// 8 binary32 values -> 16 bytes of hi parts and 16 bytes of lo parts (BF16)
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
+  __align__(16) __nv_bfloat162 h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    const float2 hf = __bfloat1622float2(h[k]);
+    l[k] = __floats2bfloat162_rn(__fsub_rn(v[2 * k], hf.x), __fsub_rn(v[2 * k + 1], hf.y));
+  }
+  hi = *reinterpret_cast<const uint4*>(h);
+  lo = *reinterpret_cast<const uint4*>(l);
+}
+
+__device__ __forceinline__ void ldg8f(const float* p, float* v) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// 8 binary32 channels c .. c+7 of halo pixel (y, x) (clamped into the image by
+// the caller): PLAIN, CONCAT (channels below CIN/2 from inA, the rest from
+// inB) or POOL (the 2x2 maximum of the finer level)
+template <int CIN, int MODE>
+__device__ __forceinline__ void halo8f(const ConvImg<float>& a, int y, int x, int c, float* v) {
+  if constexpr (MODE == TC_PLAIN) {
+    ldg8f(a.inA + ((size_t)y * a.W + x) * CIN + c, v);
+  } else if constexpr (MODE == TC_CONCAT) {
+    constexpr int CH = CIN / 2;
+    if (c < CH) ldg8f(a.inA + ((size_t)y * a.W + x) * CH + c, v);
+    else ldg8f(a.inB + ((size_t)y * a.W + x) * CH + (c - CH), v);
+  } else {
+    const size_t W2 = 2 * (size_t)a.W;
+    const float* p = a.inA + ((size_t)(2 * y) * W2 + 2 * x) * CIN + c;
+    float q[8];
+    ldg8f(p, v);
+    ldg8f(p + CIN, q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fmaxf(v[k], q[k]);
+    ldg8f(p + W2 * CIN, q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fmaxf(v[k], q[k]);
+    ldg8f(p + W2 * CIN + CIN, q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fmaxf(v[k], q[k]);
+  }
+}
+
+// Stage channels [c0, c0 + 8 GC) of the halo of M tile `tile` as GC hi planes
+// followed by GC lo planes (zeros outside the image); loads are issued in
+// batches before their first use.
+template <int CIN, int MODE, int GC>
+__device__ __forceinline__ void load_halo_split(const ConvImg<float>& a, int tile, int c0, uint8_t* halo) {
+  constexpr int NE = kHaloPix * GC;
+  const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
+  for (int e0 = threadIdx.x; e0 < NE; e0 += kLdBatch * blockDim.x) {
+    float v[kLdBatch][8];
+    bool in[kLdBatch];
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = min(e0 + b * (int)blockDim.x, NE - 1);
+      const int hp = e / GC, g = e % GC;
+      const int y = y0 + hp / kHaloW, x = x0 + hp % kHaloW;
+      in[b] = y >= 0 && y < a.H && x >= 0 && x < a.W;
+      halo8f<CIN, MODE>(a, min(max(y, 0), a.H - 1), min(max(x, 0), a.W - 1), c0 + 8 * g, v[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < kLdBatch; ++b) {
+      const int e = e0 + b * (int)blockDim.x;
+      if (e < NE) {
+        uint4 hi = make_uint4(0, 0, 0, 0), lo = hi;
+        if (in[b]) split8(v[b], hi, lo);
+        const int hp = e / GC, g = e % GC;
+        *reinterpret_cast<uint4*>(halo + g * kPlane + hp * 16) = hi;
+        *reinterpret_cast<uint4*>(halo + (GC + g) * kPlane + hp * 16) = lo;
+      }
+    }
+  }
+}
+
+// Shared-memory plan of a split 3x3 layer: N tile NT, chunks of CH input
+// channels (GC hi planes + GC lo planes), hi and lo weights of every chunk.
+template <int CIN, int COUT, int NT>
+struct SplitCfg {
+  static constexpr int CH = CIN < 64 ? CIN : 64;
+  static constexpr int NCH = CIN / CH;
+  static constexpr int GC = CH / 8;
+  static constexpr int KSC = CH / 16;           // K steps per chunk
+  static constexpr int KS = CIN / 16;           // K steps per tap
+  static constexpr int WHALF = 9 * KS * NT * 32;
+  static constexpr int WBYTES = 2 * WHALF;      // hi weights, then lo weights
+  static constexpr int HBYTES = 2 * GC * kPlane;
+  static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+  static constexpr int SMEM = WBYTES + HBYTES + 64;
+};
+__host__ __device__ constexpr int split_nt(int cout) { return cout > 32 ? 32 : cout; }
+
+// Bias, ReLU and the binary32 NHWC store of one split layer's M tile (thread
+// = pixel of the patch, NT accumulator columns from column n0).
+template <int NT>
+__device__ __forceinline__ void split_epilogue(const ConvImg<float>& a, const float* __restrict__ bias, int tile,
+                                               uint32_t tacc, int n0, int cout) {
+  const int warp = threadIdx.x >> 5, m = threadIdx.x;
+  const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
+  const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+  const bool valid = y < a.H && x < a.W;
+  float* dst = a.out + ((size_t)y * a.W + x) * cout + n0;
+#pragma unroll
+  for (int c = 0; c < NT; c += 16) {
+    float v[16];
+    tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + c, v);
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(dst + c)[q] =
+            make_float4(fmaxf(v[4 * q] + __ldg(bias + n0 + c + 4 * q), 0.f),
+                        fmaxf(v[4 * q + 1] + __ldg(bias + n0 + c + 4 * q + 1), 0.f),
+                        fmaxf(v[4 * q + 2] + __ldg(bias + n0 + c + 4 * q + 2), 0.f),
+                        fmaxf(v[4 * q + 3] + __ldg(bias + n0 + c + 4 * q + 3), 0.f));
+    }
+  }
+}
+
+template <int CIN, int COUT, int NT, int MODE>
+__global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a) {
+  using Cfg = SplitCfg<CIN, COUT, NT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* wsm = smem;
+  uint8_t* halo = smem + Cfg::WBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + Cfg::HBYTES);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nt = blockIdx.y;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, Cfg::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], Cfg::WBYTES);
+    const uint8_t* src = a.wpack + (size_t)nt * Cfg::WBYTES;
+    for (int off = 0; off < Cfg::WBYTES; off += 32768) {
+      const int n = Cfg::WBYTES - off < 32768 ? Cfg::WBYTES - off : 32768;
+      bulk_g2s(wsm + off, src + off, (uint32_t)n, &bars[0]);
+    }
+  }
+  pdl_wait();      // the input tiles come from the previous layer
+  pdl_trigger();
+  bool ok = mbar_wait(&bars[0], 0);
+  if (!ok) record_error(a.err, 0x10u);
+  constexpr uint32_t idesc = idesc_f16kind(1u, 128, NT);   // BF16 operands, FP32 accumulation
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (int t = blockIdx.x; ok && t < a.total_tiles; t += gridDim.x) {
+    if (t + (int)gridDim.x >= a.total_tiles) pdl_trigger_last();
+    const int im = image_of(a, t);
+    const int lt = t - a.img[im].tile_start;
+#pragma unroll 1
+    for (int kc = 0; kc < Cfg::NCH; ++kc) {
+      __syncthreads();   // every read of the halo buffer by earlier MMAs has completed
+      load_halo_split<CIN, MODE, Cfg::GC>(a.img[im], lt, kc * Cfg::CH, halo);
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t hb = smem_u32(halo), wb = smem_u32(wsm);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+#pragma unroll
+          for (int j = 0; j < Cfg::KSC; ++j) {
+            const int kk = tap * Cfg::KS + kc * Cfg::KSC + j;
+            const uint64_t ahi = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
+            const uint64_t alo = smem_desc(hb + (uint32_t)((Cfg::GC + 2 * j) * kPlane) + shift, kPlane, kHaloW * 16);
+            const uint64_t bhi = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
+            const uint64_t blo = smem_desc(wb + (uint32_t)(Cfg::WHALF + kk * NT * 32), NT * 16, 128);
+            mma_f16kind(tmem, ahi, bhi, idesc, (kc | tap | j) ? 1u : 0u);
+            mma_f16kind(tmem, ahi, blo, idesc, 1u);
+            mma_f16kind(tmem, alo, bhi, idesc, 1u);
+          }
+        }
+        mma_commit(&bars[1]);
+      }
+      if (!mbar_wait(&bars[1], phase)) {
+        record_error(a.err, 0x20u);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+    }
+    if (!ok) break;
+    split_epilogue<NT>(a.img[im], a.bias, lt, tmem, nt * NT, COUT);
+    tc_fence_before();
+  }
+  tc_fence_before();
+  __syncthreads();
+  pdl_trigger_end();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// Split transposed convolution: M = 128 input pixels, N = 4 COUT / NS columns
+// [sub-position][co] per CTA, K = CIN in chunks of up to 64 channels.
+template <int CIN, int COUT, int NS>
+struct SplitTCfg {
+  static constexpr int N = 4 * COUT / NS;
+  static constexpr int CH = CIN < 64 ? CIN : 64;
+  static constexpr int NCH = CIN / CH;
+  static constexpr int GC = CH / 8;
+  static constexpr int KSC = CH / 16;
+  static constexpr int KS = CIN / 16;
+  static constexpr int APLANE = 128 * 16;
+  static constexpr int WHALF = KS * N * 32;
+  static constexpr int WBYTES = 2 * WHALF;
+  static constexpr int ABYTES = 2 * GC * APLANE;
+  static constexpr int TMEM_COLS = N < 32 ? 32 : N;
+  static constexpr int SMEM = WBYTES + ABYTES + 64;
+};
+
+template <int CIN, int COUT, int NS>
+__global__ void __launch_bounds__(128) convT_split_kernel(TcConvTArgs<float> a) {
+  using Cfg = SplitTCfg<CIN, COUT, NS>;
+  constexpr int N = Cfg::N;
+  static_assert(N % 16 == 0 && COUT % 16 == 0, "column blocks of one sub-position");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* wsm = smem;
+  uint8_t* abuf = smem + Cfg::WBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + Cfg::ABYTES);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(slot, Cfg::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], Cfg::WBYTES);
+    const uint8_t* src = a.wpack + (size_t)blockIdx.y * Cfg::WBYTES;
+    for (int off = 0; off < Cfg::WBYTES; off += 32768) {
+      const int n = Cfg::WBYTES - off < 32768 ? Cfg::WBYTES - off : 32768;
+      bulk_g2s(wsm + off, src + off, (uint32_t)n, &bars[0]);
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  bool ok = mbar_wait(&bars[0], 0);
+  if (!ok) record_error(a.err, 0x40u);
+  constexpr uint32_t idesc = idesc_f16kind(1u, 128, N);
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (int t = blockIdx.x; ok && t < a.total_tiles; t += gridDim.x) {
+    if (t + (int)gridDim.x >= a.total_tiles) pdl_trigger_last();
+    const int imi = image_of(a, t);
+    const ConvTImg<float>& im = a.img[imi];
+    const int lt = t - im.tile_start;
+    const int ty = lt / im.tiles_x, tx = lt % im.tiles_x;
+#pragma unroll 1
+    for (int kc = 0; kc < Cfg::NCH; ++kc) {
+      __syncthreads();   // every read of the A buffer by earlier MMAs has completed
+      constexpr int NE = 128 * Cfg::GC;
+      for (int e0 = tid; e0 < NE; e0 += kLdBatch * blockDim.x) {
+        float v[kLdBatch][8];
+        bool in[kLdBatch];
+#pragma unroll
+        for (int b = 0; b < kLdBatch; ++b) {
+          const int e = min(e0 + b * (int)blockDim.x, NE - 1);
+          const int m = e / Cfg::GC, g = e % Cfg::GC;
+          const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+          in[b] = y < im.H && x < im.W;
+          ldg8f(im.in + ((size_t)min(y, im.H - 1) * im.W + min(x, im.W - 1)) * CIN + kc * Cfg::CH + 8 * g, v[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kLdBatch; ++b) {
+          const int e = e0 + b * (int)blockDim.x;
+          if (e < NE) {
+            uint4 hi = make_uint4(0, 0, 0, 0), lo = hi;
+            if (in[b]) split8(v[b], hi, lo);
+            const int m = e / Cfg::GC, g = e % Cfg::GC;
+            *reinterpret_cast<uint4*>(abuf + g * Cfg::APLANE + m * 16) = hi;
+            *reinterpret_cast<uint4*>(abuf + (Cfg::GC + g) * Cfg::APLANE + m * 16) = lo;
+          }
+        }
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t ab = smem_u32(abuf), wb = smem_u32(wsm);
+#pragma unroll
+        for (int j = 0; j < Cfg::KSC; ++j) {
+          const int kk = kc * Cfg::KSC + j;
+          const uint64_t ahi = smem_desc(ab + (uint32_t)(2 * j * Cfg::APLANE), Cfg::APLANE, 128);
+          const uint64_t alo = smem_desc(ab + (uint32_t)((Cfg::GC + 2 * j) * Cfg::APLANE), Cfg::APLANE, 128);
+          const uint64_t bhi = smem_desc(wb + (uint32_t)(kk * N * 32), N * 16, 128);
+          const uint64_t blo = smem_desc(wb + (uint32_t)(Cfg::WHALF + kk * N * 32), N * 16, 128);
+          mma_f16kind(tmem, ahi, bhi, idesc, (kc | j) ? 1u : 0u);
+          mma_f16kind(tmem, ahi, blo, idesc, 1u);
+          mma_f16kind(tmem, alo, bhi, idesc, 1u);
+        }
+        mma_commit(&bars[1]);
+      }
+      if (!mbar_wait(&bars[1], phase)) {
+        record_error(a.err, 0x80u);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+    }
+    if (!ok) break;
+    // bias and the binary32 store of the four output pixels each input pixel feeds
+    const int m = tid;
+    const int y = ty * kPatchH + m / kPatchW, x = tx * kPatchW + m % kPatchW;
+    const bool valid = y < im.H && x < im.W;
+#pragma unroll 1
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      const int n = (int)blockIdx.y * N + c, k = n / COUT, co = n % COUT;
+      const int oy = 2 * y + (k >> 1), ox = 2 * x + (k & 1);
+      if (valid) {
+        float* dst = im.out + ((size_t)oy * (2 * im.W) + ox) * COUT + co;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          reinterpret_cast<float4*>(dst)[q] =
+              make_float4(v[4 * q] + __ldg(a.bias + co + 4 * q), v[4 * q + 1] + __ldg(a.bias + co + 4 * q + 1),
+                          v[4 * q + 2] + __ldg(a.bias + co + 4 * q + 2), v[4 * q + 3] + __ldg(a.bias + co + 4 * q + 3));
+      }
+    }
+    tc_fence_before();
+  }
+  tc_fence_before();
+  __syncthreads();
+  pdl_trigger_end();
+  if (warp == 0) tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
 // Failure-detection probe: one warp waits, with the same bounded wait as every
 // tensor-core kernel, on an mbarrier that nothing arrives at; the wait gives up
 // after its limit (about 2 s), records code 0x8000 in the error word and the
@@ -971,7 +1333,8 @@ static void pack_convT_q8(const float* w, int cin, int cout, int ns, std::vector
 }  // namespace
 
 struct NetTcWeights {
-  int elem = 0;              // 0 FP16 operands, 1 BF16 operands, 2 FP8 E4M3 operands
+  int elem = 0;              // 0 FP16 operands, 1 BF16 operands, 2 FP8 E4M3 operands,
+                             // 3 split BF16 (hi and lo parts of both operands)
   uint8_t* conv_w[14] = {};  // layer 0 stays on the SIMT path
   float* conv_b[14] = {};
   float* conv_s[14] = {};    // FP8: per-output-channel weight scales
@@ -1032,11 +1395,77 @@ static void fill_weights_q8(NetTcWeights* w, const float* hp, const NetLayout& L
   }
 }
 
+// Split-BF16 weights: the high part bf16(w) and the low part bf16(w - hi) of
+// every weight (w - hi is exact in binary32), each packed as pack_conv /
+// pack_convT pack a 16-bit operand; per N tile (per column block of a
+// transposed convolution) the hi block, then the lo block.
+static void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  *hi = __float2bfloat16_rn(v);
+  *lo = __float2bfloat16_rn(v - __bfloat162float(*hi));
+}
+
+static void pack_conv_split(const float* w, int cin, int cout, int NT, std::vector<uint8_t>& out) {
+  const int KS = cin / 16;
+  const size_t slice = (size_t)NT * 32, half = 9 * (size_t)KS * slice;
+  out.assign((size_t)(cout / NT) * 2 * half, 0);
+  for (int nt = 0; nt < cout / NT; ++nt)
+    for (int tap = 0; tap < 9; ++tap)
+      for (int j = 0; j < KS; ++j) {
+        uint8_t* s = out.data() + (size_t)nt * 2 * half + ((size_t)tap * KS + j) * slice;
+        for (int n = 0; n < NT; ++n)
+          for (int k = 0; k < 16; ++k) {
+            const int co = nt * NT + n, ci = j * 16 + k;
+            __nv_bfloat16 hi, lo;
+            split_bf16(w[((size_t)co * cin + ci) * 9 + tap], &hi, &lo);
+            const size_t off = (size_t)(k / 8) * NT * 16 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+            std::memcpy(s + off, &hi, 2);
+            std::memcpy(s + half + off, &lo, 2);
+          }
+      }
+}
+
+static void pack_convT_split(const float* w, int cin, int cout, int ns, std::vector<uint8_t>& out) {
+  const int N = 4 * cout, Nb = N / ns, KS = cin / 16;
+  const size_t slice = (size_t)Nb * 32, half = (size_t)KS * slice;
+  out.assign((size_t)ns * 2 * half, 0);
+  for (int sb = 0; sb < ns; ++sb)
+    for (int j = 0; j < KS; ++j) {
+      uint8_t* s = out.data() + (size_t)sb * 2 * half + (size_t)j * slice;
+      for (int r = 0; r < Nb; ++r)
+        for (int k = 0; k < 16; ++k) {
+          const int n = sb * Nb + r, kpos = n / cout, co = n % cout, ci = j * 16 + k;
+          __nv_bfloat16 hi, lo;
+          split_bf16(w[((size_t)ci * cout + co) * 4 + kpos], &hi, &lo);
+          const size_t off = (size_t)(k / 8) * Nb * 16 + (r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+          std::memcpy(s + off, &hi, 2);
+          std::memcpy(s + half + off, &lo, 2);
+        }
+    }
+}
+
+static void fill_weights_split(NetTcWeights* w, const float* hp, const NetLayout& L, cudaError_t* err) {
+  std::vector<uint8_t> pk;
+  for (int l = 1; l < 14; ++l) {
+    const int cin = L.conv_cin[l], cout = L.conv_cout[l];
+    const int NT = split_nt(cout);
+    w->conv_nt[l] = NT;
+    pack_conv_split(hp + L.conv_w[l], cin, cout, NT, pk);
+    w->conv_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->conv_b[l] = dev_copy(w, hp + L.conv_b[l], (size_t)cout, err);
+  }
+  for (int l = 0; l < 3; ++l) {
+    pack_convT_split(hp + L.up_w[l], L.up_cin[l], L.up_cout[l], kUpSplit[l], pk);
+    w->up_w[l] = dev_copy(w, pk.data(), pk.size(), err);
+    w->up_b[l] = dev_copy(w, hp + L.up_b[l], (size_t)L.up_cout[l], err);
+  }
+}
+
 NetTcWeights* net_tc_create(const float* hp, const NetLayout& L, int elem, cudaError_t* err) {
   *err = cudaSuccess;
   NetTcWeights* w = new NetTcWeights();
   w->elem = elem;
-  if (elem == 2) fill_weights_q8(w, hp, L, err);
+  if (elem == 3) fill_weights_split(w, hp, L, err);
+  else if (elem == 2) fill_weights_q8(w, hp, L, err);
   else if (elem == 1) fill_weights<__nv_bfloat16>(w, hp, L, err);
   else fill_weights<__half>(w, hp, L, err);
   if (*err == cudaSuccess) {
@@ -1165,6 +1594,115 @@ cudaError_t run_convT(const NetTcWeights* w, int n, const T* const* ins, T* cons
   return launch_pdl(convT_tc_kernel<T, CIN, COUT, Q8, NS>, dim3(grid, NS), dim3(128), (size_t)L.smem, s, a);
 }
 
+template <int CIN, int COUT, int MODE>
+cudaError_t run_conv_split(const NetTcWeights* w, int l, int n, const float* const* ins, const float* const* skips,
+                           float* const* outs, const int* H, const int* W, unsigned int* err, cudaStream_t s) {
+  constexpr int NT = split_nt(COUT);
+  using Cfg = SplitCfg<CIN, COUT, NT>;
+  static_assert(Cfg::SMEM <= 232448, "shared memory budget");
+  static const LaunchOnce once =
+      configure_once(conv3x3_split_kernel<CIN, COUT, NT, MODE>, Cfg::SMEM, Cfg::TMEM_COLS);
+  if (once.err != cudaSuccess) return once.err;
+  const Launch& L = once.L;
+  TcConvArgs<float> a{};
+  a.nimg = n;
+  int ntiles = 0;
+  for (int k = 0; k < n; ++k) {
+    const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
+    a.img[k] = ConvImg<float>{ins[k], skips ? skips[k] : nullptr, outs[k], H[k], W[k], tx, ntiles,
+                              nullptr, nullptr, nullptr};
+    ntiles += tx * ty;
+  }
+  a.total_tiles = ntiles;
+  a.wpack = w->conv_w[l];
+  a.bias = w->conv_b[l];
+  a.err = err;
+  const int per_sm = L.per_sm < g_conv_ctas_per_sm ? L.per_sm : g_conv_ctas_per_sm;
+  int grid = num_sms() * per_sm / (COUT / NT);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  return launch_pdl(conv3x3_split_kernel<CIN, COUT, NT, MODE>, dim3(grid, COUT / NT), dim3(128), (size_t)L.smem, s,
+                    a);
+}
+
+template <int CIN, int COUT, int LAYER>
+cudaError_t run_convT_split(const NetTcWeights* w, int n, const float* const* ins, float* const* outs, const int* H,
+                            const int* W, unsigned int* err, cudaStream_t s) {
+  constexpr int NS = kUpSplit[LAYER];
+  using Cfg = SplitTCfg<CIN, COUT, NS>;
+  static_assert(Cfg::SMEM <= 232448, "shared memory budget");
+  static const LaunchOnce once = configure_once(convT_split_kernel<CIN, COUT, NS>, Cfg::SMEM, Cfg::TMEM_COLS);
+  if (once.err != cudaSuccess) return once.err;
+  const Launch& L = once.L;
+  TcConvTArgs<float> a{};
+  a.nimg = n;
+  int ntiles = 0;
+  for (int k = 0; k < n; ++k) {
+    const int tx = (W[k] + kPatchW - 1) / kPatchW, ty = (H[k] + kPatchH - 1) / kPatchH;
+    a.img[k] = ConvTImg<float>{ins[k], outs[k], H[k], W[k], tx, ntiles, nullptr, nullptr};
+    ntiles += tx * ty;
+  }
+  a.total_tiles = ntiles;
+  a.wpack = w->up_w[LAYER];
+  a.bias = w->up_b[LAYER];
+  a.err = err;
+  int grid = (num_sms() * L.per_sm + NS - 1) / NS;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  return launch_pdl(convT_split_kernel<CIN, COUT, NS>, dim3(grid, NS), dim3(128), (size_t)L.smem, s, a);
+}
+
+// The split-BF16 network: the first convolution on the SIMT cores (binary32
+// output), the 16 tensor-core convolutions in the split form on binary32
+// activations, then the tensor-core adapters (binary16 operands, as in the
+// other tensor-core networks) on the binary32 feature map.
+cudaError_t forward_split(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs, void* const* ws,
+                          int n, unsigned int* err, cudaStream_t s) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  TcBuffers<float> B[kMaxGroup];
+  int Hs[4][kMaxGroup], Ws[4][kMaxGroup];
+  for (int k = 0; k < n; ++k) {
+    const size_t P = (size_t)imgs[k].H * imgs[k].W;
+    carve_tc(P, adapter_partial_floats(imgs[k].W, imgs[k].H), &B[k], static_cast<char*>(ws[k]));
+    for (int lv = 0; lv < 4; ++lv) {
+      Hs[lv][k] = imgs[k].H >> lv;
+      Ws[lv][k] = imgs[k].W >> lv;
+    }
+  }
+  const float* in[kMaxGroup];
+  const float* sk[kMaxGroup];
+  float* out[kMaxGroup];
+  cudaError_t e;
+#define TRY(x) if ((e = (x)) != cudaSuccess) return e
+#define SET(IN, SKIP, OUT) for (int k = 0; k < n; ++k) { in[k] = B[k].IN; sk[k] = SKIP; out[k] = B[k].OUT; }
+  for (int k = 0; k < n; ++k) out[k] = B[k].fa;
+  TRY(simt_first_conv_group<float>(wf, imgs, out, nullptr, n, s));
+  SET(fa, nullptr, s1);  TRY((run_conv_split<16, 16, TC_PLAIN>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  SET(s1, nullptr, l1a); TRY((run_conv_split<16, 32, TC_POOL>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(l1a, nullptr, s2); TRY((run_conv_split<32, 32, TC_PLAIN>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(s2, nullptr, l2a); TRY((run_conv_split<32, 64, TC_POOL>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(l2a, nullptr, s3); TRY((run_conv_split<64, 64, TC_PLAIN>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(s3, nullptr, l3a); TRY((run_conv_split<64, 128, TC_POOL>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  SET(l3a, nullptr, l3b); TRY((run_conv_split<128, 128, TC_PLAIN>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  SET(l3b, nullptr, l2a); TRY((run_convT_split<128, 64, 0>(w, n, in, out, Hs[3], Ws[3], err, s)));
+  SET(l2a, B[k].s3, l2b); TRY((run_conv_split<128, 64, TC_CONCAT>(w, 8, n, in, sk, out, Hs[2], Ws[2], err, s)));
+  SET(l2b, nullptr, l2a); TRY((run_conv_split<64, 64, TC_PLAIN>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  SET(l2a, nullptr, l1a); TRY((run_convT_split<64, 32, 1>(w, n, in, out, Hs[2], Ws[2], err, s)));
+  SET(l1a, B[k].s2, l1b); TRY((run_conv_split<64, 32, TC_CONCAT>(w, 10, n, in, sk, out, Hs[1], Ws[1], err, s)));
+  SET(l1b, nullptr, l1a); TRY((run_conv_split<32, 32, TC_PLAIN>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  SET(l1a, nullptr, fa); TRY((run_convT_split<32, 16, 2>(w, n, in, out, Hs[1], Ws[1], err, s)));
+  SET(fa, B[k].s1, fb);  TRY((run_conv_split<32, 16, TC_CONCAT>(w, 12, n, in, sk, out, Hs[0], Ws[0], err, s)));
+  SET(fb, nullptr, fa);  TRY((run_conv_split<16, 16, TC_PLAIN>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  AdapterImg<float> ai[kMaxGroup];
+  for (int k = 0; k < n; ++k)
+    ai[k] = AdapterImg<float>{B[k].fa, reinterpret_cast<__half*>(B[k].x1), B[k].partial, B[k].att, imgs[k].out,
+                              imgs[k].H, imgs[k].W};
+  TRY(adapters_tc_run_group<float>(w->ad, net_f32_adapter_params(wf), ai, n, err, s));
+#undef SET
+#undef TRY
+  return cudaSuccess;
+}
+
 template <typename T, bool Q8>
 cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs,
                     void* const* ws, int n, unsigned int* err, cudaStream_t s, uint8_t* trace) {
@@ -1260,7 +1798,11 @@ cudaError_t forward(const NetTcWeights* w, const NetF32Weights* wf, const NetIma
 }
 }  // namespace
 
-size_t net_tc_workspace_bytes(int max_w, int max_h) {
+size_t net_tc_workspace_bytes(int max_w, int max_h, int elem) {
+  if (elem == 3) {
+    TcBuffers<float> b;
+    return carve_tc((size_t)max_w * max_h, adapter_partial_floats(max_w, max_h), &b, nullptr);
+  }
   TcBuffers<__half> b;
   return carve_tc((size_t)max_w * max_h, adapter_partial_floats(max_w, max_h), &b, nullptr);
 }
@@ -1268,8 +1810,9 @@ size_t net_tc_workspace_bytes(int max_w, int max_h) {
 cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const NetImage& img,
                            void* workspace, size_t ws_bytes, unsigned int* err, cudaStream_t s,
                            uint8_t* trace) {
-  if (net_tc_workspace_bytes(img.W, img.H) > ws_bytes) return cudaErrorInvalidValue;
+  if (net_tc_workspace_bytes(img.W, img.H, w->elem) > ws_bytes) return cudaErrorInvalidValue;
   void* ws[1] = {workspace};
+  if (w->elem == 3) return trace ? cudaErrorNotSupported : forward_split(w, wf, &img, ws, 1, err, s);
   if (w->elem == 2) return forward<__half, true>(w, wf, &img, ws, 1, err, s, trace);
   if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, &img, ws, 1, err, s, trace);
   return forward<__half, false>(w, wf, &img, ws, 1, err, s, trace);
@@ -1284,6 +1827,7 @@ size_t net_tc_trace_bytes(int width, int height) {
 cudaError_t net_tc_forward_group(const NetTcWeights* w, const NetF32Weights* wf,
                                  const NetImage* imgs, void* const* ws, int n, unsigned int* err,
                                  cudaStream_t s) {
+  if (w->elem == 3) return forward_split(w, wf, imgs, ws, n, err, s);
   if (w->elem == 2) return forward<__half, true>(w, wf, imgs, ws, n, err, s, nullptr);
   if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, imgs, ws, n, err, s, nullptr);
   return forward<__half, false>(w, wf, imgs, ws, n, err, s, nullptr);

@@ -396,7 +396,21 @@ struct NetTcWeights;
 NetTcWeights* net_tc_create(const float* host_params, const NetLayout& L, int elem,
                             cudaError_t* err);
 void net_tc_destroy(NetTcWeights* w);
-size_t net_tc_workspace_bytes(int max_w, int max_h);
+// workspace of a tensor-core network (elem 3, the split-BF16 form, keeps
+// binary32 activations: about twice the bytes)
+size_t net_tc_workspace_bytes(int max_w, int max_h, int elem = 0);
+// tensor-core weight set of a precision: 0 FP16, 1 BF16, 2 FP8, 3 split BF16;
+// -1 for a precision without one
+inline int tc_elem_of(int precision) {
+  switch (precision) {
+    case NSL_PREC_F16: return 0;
+    case NSL_PREC_BF16: return 1;
+    case NSL_PREC_FP8: return 2;
+    case NSL_PREC_BF16X3: return 3;
+    default: return -1;
+  }
+}
+constexpr int kTcElems = 4;
 // trace (nullable): after each of the 17 convolutions a copy of its stored
 // output (NHWC, 16-bit activation type) is appended; net_tc_trace_bytes bytes
 cudaError_t net_tc_forward(const NetTcWeights* wt, const NetF32Weights* wf, const NetImage& img,
@@ -416,7 +430,8 @@ cudaError_t launch_wait_timeout_probe(unsigned int* err, cudaStream_t s);
 int tc_ctas_per_sm(const void* kernel, int threads, int dyn_smem, int tmem_cols);
 
 // ---- batched frames (batch.cu), used by the server ----
-void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes);
+void batch_plume_scratch(const nsl_plume& p, int seg_len, size_t* seg_bytes, size_t* net_bytes,
+                         int precision = NSL_PREC_F16);
 nsl_status batch_render_prestaged(nsl_batch* b, const nsl_plume* plumes, const float* const* staged,
                                   int n, const nsl_march_opts* opts, int precision, cudaStream_t s);
 nsl_status batch_reserve(nsl_batch* b, size_t seg_bytes, size_t net_bytes, cudaStream_t s);

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libnsl.so")
 
 NSL_OK, NSL_ERR_INVALID_ARG, NSL_ERR_OOM, NSL_ERR_CUDA, NSL_ERR_UNSUPPORTED, NSL_ERR_TIMEOUT, NSL_ERR_BUDGET = range(7)
 NSL_F32, NSL_F16 = 0, 1
-NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8, NSL_PREC_F16 = 0, 1, 2, 3
+NSL_PREC_F32, NSL_PREC_BF16, NSL_PREC_FP8, NSL_PREC_F16, NSL_PREC_BF16X3 = 0, 1, 2, 3, 4
 NSL_CAM_ORTHO, NSL_CAM_PERSP = 0, 1
 NSL_LIGHTS_FTB, NSL_LIGHTS_F, NSL_LIGHTS_FLR = 0, 1, 2
 NSL_TEX_RGBA8, NSL_TEX_RGBA16F, NSL_TEX_RGBA32F = 0, 1, 2

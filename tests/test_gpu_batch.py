@@ -91,7 +91,7 @@ def _host(items, key):
     return [it[key].cpu().numpy().astype(np.float64) for it in items]
 
 
-@pytest.mark.parametrize("precision", [3, 1, 2], ids=["f16", "bf16", "fp8"])
+@pytest.mark.parametrize("precision", [3, 1, 2, 4], ids=["f16", "bf16", "fp8", "bf16x3"])
 def test_batch_equals_single_plume_path(lib, precision):
     frames = _frames()
     b = lib.Batch(I.pack_blob(I.make_params(C0, seed=0), C0), max_plumes=8)
