@@ -876,12 +876,17 @@ def bench_serving(nsl, I, dev, args):
            "precision": "bf16",
            "generation_s": gen_s, "frame_budgets_ms": [11.1, 16.7], "steps": {}}
     hosts16 = None
-    for step_name, step_of, f16 in (("2 voxels", lambda n: 2.0, False), ("n/64 voxels", lambda n: n / 64.0, False),
-                                    ("n/64 voxels, f16 grids", lambda n: n / 64.0, True)):
+    # the last configuration serves the split-BF16 network (the BF16 form
+    # within 2e-2 of range of FP64)
+    for step_name, step_of, f16, sprec in (
+            ("2 voxels", lambda n: 2.0, False, nsl.NSL_PREC_BF16),
+            ("n/64 voxels", lambda n: n / 64.0, False, nsl.NSL_PREC_BF16),
+            ("n/64 voxels, f16 grids", lambda n: n / 64.0, True, nsl.NSL_PREC_BF16),
+            ("n/64 voxels, split bf16", lambda n: n / 64.0, False, nsl.NSL_PREC_BF16X3)):
         if f16 and hosts16 is None:
             hosts16 = [h.astype(np.float16) for h in hosts]
         srv = nsl.Server(blob, nsl.server_opts(hbm_budget_bytes=40 << 30, streams=2, max_batch=64,
-                                               precision=nsl.NSL_PREC_BF16))
+                                               precision=sprec))
         ids = [srv.add_plume(h, None, step_of(p.n), p.width, p.height)
                for h, p in zip(hosts16 if f16 else hosts, spec)]
         for pid, p in zip(ids, spec):                 # warm-up: admit every plume once

@@ -569,7 +569,7 @@ typedef struct {
   size_t scratch_bytes_per_stream; /* march + network scratch of one batch slot (0: budget/8) */
   int streams;                     /* batch slots in flight at once, 1..4 */
   int max_batch;                   /* requests per batch, 1..64 */
-  int precision;                   /* NSL_PREC_F16, NSL_PREC_BF16 or NSL_PREC_FP8 */
+  int precision;                   /* NSL_PREC_F16, NSL_PREC_BF16, NSL_PREC_FP8 or NSL_PREC_BF16X3 */
   nsl_march_opts march;            /* march options of every frame */
   size_t max_batch_pixels;         /* billboard pixels a batch may hold (0: no cap); the
                                       oldest runnable request is always taken, later ones

@@ -250,7 +250,7 @@ bool launch_batch(nsl_server* S, Slot& sl) {
       }
       size_t sb, nb;
       const nsl_plume q = plume_of(p, r);
-      batch_plume_scratch(q, S->seg_len, &sb, &nb);
+      batch_plume_scratch(q, S->seg_len, &sb, &nb, S->o.precision);
       if (seg + sb > S->seg_cap || net + nb > S->net_cap ||
           (!pick.empty() && S->o.max_batch_pixels && pix + rpix > S->o.max_batch_pixels)) {
         p.busy = true;  // keep later requests of this plume behind this one
@@ -425,8 +425,8 @@ nsl_status nsl_server_create(const void* blob, size_t blob_bytes, const nsl_serv
   nsl_default_server_opts(&o);
   if (opts) o = *opts;
   if (o.streams < 1 || o.streams > 4 || o.max_batch < 1 || o.max_batch > kMaxGroup ||
-      (o.precision != NSL_PREC_F16 && o.precision != NSL_PREC_BF16 && o.precision != NSL_PREC_FP8))
-    return fail(NSL_ERR_INVALID_ARG, "nsl_server_create: streams 1..4, max_batch 1..%d, precision F16/BF16/FP8",
+      tc_elem_of(o.precision) < 0)
+    return fail(NSL_ERR_INVALID_ARG, "nsl_server_create: streams 1..4, max_batch 1..%d, precision F16/BF16/FP8/BF16X3",
                 kMaxGroup);
   if (!o.scratch_bytes_per_stream) o.scratch_bytes_per_stream = o.hbm_budget_bytes / 8;
   if (o.scratch_bytes_per_stream * o.streams >= o.hbm_budget_bytes)
@@ -537,7 +537,7 @@ nsl_status nsl_server_add_plume(nsl_server* S, const nsl_grid_desc* grid, const 
   q.camera.height = max_h;
   q.step_voxels = step;
   size_t sb, nb;
-  batch_plume_scratch(q, S->seg_len, &sb, &nb);
+  batch_plume_scratch(q, S->seg_len, &sb, &nb, S->o.precision);
   if (sb > S->seg_cap || nb > S->net_cap)
     return fail(NSL_ERR_BUDGET, "nsl_server_add_plume: a %dx%d frame needs %zu + %zu bytes of scratch; a slot "
                 "holds %zu + %zu", max_w, max_h, sb, nb, S->seg_cap, S->net_cap);

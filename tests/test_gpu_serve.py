@@ -79,7 +79,7 @@ def _server(lib, **kw):
     return lib.Server(blob, lib.server_opts(**kw))
 
 
-@pytest.mark.parametrize("precision", [3, 1, 2], ids=["f16", "bf16", "fp8"])
+@pytest.mark.parametrize("precision", [3, 1, 2, 4], ids=["f16", "bf16", "fp8", "bf16x3"])
 def test_serving_alone_equals_mix(lib, precision):
     import torch
     plumes = _plumes()
