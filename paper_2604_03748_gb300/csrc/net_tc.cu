@@ -859,8 +859,11 @@ struct SplitCfg {
   static constexpr int WHALF = 9 * KS * NT * 32;
   static constexpr int WBYTES = 2 * WHALF;      // hi weights, then lo weights
   static constexpr int HBYTES = 2 * GC * kPlane;
+  // layers of one chunk keep two halo buffers: the next tile is staged while
+  // the tensor cores work on this one
+  static constexpr int HBUF = NCH == 1 ? 2 : 1;
   static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
-  static constexpr int SMEM = WBYTES + HBYTES + 64;
+  static constexpr int SMEM = WBYTES + HBUF * HBYTES + 64;
 };
 __host__ __device__ constexpr int split_nt(int cout) { return cout > 32 ? 32 : cout; }
 
@@ -896,7 +899,7 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* wsm = smem;
   uint8_t* halo = smem + Cfg::WBYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + Cfg::HBYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + Cfg::HBUF * Cfg::HBYTES);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = blockIdx.y;
@@ -924,6 +927,64 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
   if (!ok) record_error(a.err, 0x10u);
   constexpr uint32_t idesc = idesc_f16kind(1u, 128, NT);   // BF16 operands, FP32 accumulation
   uint32_t phase = 0;
+  // the MMAs of one chunk on halo buffer hb
+  auto issue_chunk = [&](uint32_t hb, int kc) {
+    const uint32_t wb = smem_u32(wsm);
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+#pragma unroll
+      for (int j = 0; j < Cfg::KSC; ++j) {
+        const int kk = tap * Cfg::KS + kc * Cfg::KSC + j;
+        const uint64_t ahi = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
+        const uint64_t alo = smem_desc(hb + (uint32_t)((Cfg::GC + 2 * j) * kPlane) + shift, kPlane, kHaloW * 16);
+        const uint64_t bhi = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
+        const uint64_t blo = smem_desc(wb + (uint32_t)(Cfg::WHALF + kk * NT * 32), NT * 16, 128);
+        mma_f16kind(tmem, ahi, bhi, idesc, (kc | tap | j) ? 1u : 0u);
+        mma_f16kind(tmem, ahi, blo, idesc, 1u);
+        mma_f16kind(tmem, alo, bhi, idesc, 1u);
+      }
+    }
+    mma_commit(&bars[1]);
+  };
+  if constexpr (Cfg::NCH == 1) {
+    // two halo buffers: stage tile t + grid while the MMAs of tile t run
+    int buf = 0;
+    int t = blockIdx.x;
+    if (ok && t < a.total_tiles) {
+      const int im = image_of(a, t);
+      load_halo_split<CIN, MODE, Cfg::GC>(a.img[im], t - a.img[im].tile_start, 0, halo);
+    }
+#pragma unroll 1
+    for (; ok && t < a.total_tiles; t += gridDim.x) {
+      if (t + (int)gridDim.x >= a.total_tiles) pdl_trigger_last();
+      const int im = image_of(a, t);
+      const int lt = t - a.img[im].tile_start;
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();   // halo[buf] staged; the previous epilogue's TMEM reads are done
+      if (tid == 0) {
+        tc_fence_after();
+        issue_chunk(smem_u32(halo + buf * Cfg::HBYTES), 0);
+      }
+      const int tn = t + (int)gridDim.x;
+      if (tn < a.total_tiles) {   // the other buffer's MMAs completed in the previous iteration
+        const int imn = image_of(a, tn);
+        load_halo_split<CIN, MODE, Cfg::GC>(a.img[imn], tn - a.img[imn].tile_start, 0,
+                                            halo + (buf ^ 1) * Cfg::HBYTES);
+      }
+      if (!mbar_wait(&bars[1], phase)) {
+        record_error(a.err, 0x20u);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      split_epilogue<NT>(a.img[im], a.bias, lt, tmem, nt * NT, COUT);
+      tc_fence_before();
+      buf ^= 1;
+    }
+  } else {
 #pragma unroll 1
   for (int t = blockIdx.x; ok && t < a.total_tiles; t += gridDim.x) {
     if (t + (int)gridDim.x >= a.total_tiles) pdl_trigger_last();
@@ -938,23 +999,7 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t hb = smem_u32(halo), wb = smem_u32(wsm);
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-          const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
-#pragma unroll
-          for (int j = 0; j < Cfg::KSC; ++j) {
-            const int kk = tap * Cfg::KS + kc * Cfg::KSC + j;
-            const uint64_t ahi = smem_desc(hb + (uint32_t)(2 * j * kPlane) + shift, kPlane, kHaloW * 16);
-            const uint64_t alo = smem_desc(hb + (uint32_t)((Cfg::GC + 2 * j) * kPlane) + shift, kPlane, kHaloW * 16);
-            const uint64_t bhi = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
-            const uint64_t blo = smem_desc(wb + (uint32_t)(Cfg::WHALF + kk * NT * 32), NT * 16, 128);
-            mma_f16kind(tmem, ahi, bhi, idesc, (kc | tap | j) ? 1u : 0u);
-            mma_f16kind(tmem, ahi, blo, idesc, 1u);
-            mma_f16kind(tmem, alo, bhi, idesc, 1u);
-          }
-        }
-        mma_commit(&bars[1]);
+        issue_chunk(smem_u32(halo), kc);
       }
       if (!mbar_wait(&bars[1], phase)) {
         record_error(a.err, 0x20u);
@@ -967,6 +1012,7 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
     if (!ok) break;
     split_epilogue<NT>(a.img[im], a.bias, lt, tmem, nt * NT, COUT);
     tc_fence_before();
+  }
   }
   tc_fence_before();
   __syncthreads();
@@ -1617,7 +1663,10 @@ cudaError_t run_conv_split(const NetTcWeights* w, int l, int n, const float* con
   a.wpack = w->conv_w[l];
   a.bias = w->conv_b[l];
   a.err = err;
-  const int per_sm = L.per_sm < g_conv_ctas_per_sm ? L.per_sm : g_conv_ctas_per_sm;
+#ifndef NSL_SPLIT_CTAS
+#define NSL_SPLIT_CTAS 8   // CTAs per SM (4: 0.374 ms, 8: 0.368 ms for the 512^2 network)
+#endif
+  const int per_sm = L.per_sm < NSL_SPLIT_CTAS ? L.per_sm : NSL_SPLIT_CTAS;
   int grid = num_sms() * per_sm / (COUT / NT);
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
