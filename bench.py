@@ -5,7 +5,7 @@ radius-20 sphere obstacle, perspective camera, 512x512 billboard, step 2
 voxels: grid staging -> guide march -> lightmap network -> six-way shading.
 Metric: Mpix/s of completed (guide + lightmaps) frames.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|bf16|f16|fp8|bf16x3]
   python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
 
 N > 1 (torchrun): independent replicas, one frame stream per GPU (the path has
@@ -263,7 +263,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="nsl", choices=["nsl", "reference"])
-    ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8"])
+    ap.add_argument("--precision", default="f16", choices=["f32", "bf16", "f16", "fp8", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--forms", default="animated,batched,serving,training",
@@ -297,7 +297,7 @@ def main():
     nsl.load()
 
     prec = {"f32": nsl.NSL_PREC_F32, "bf16": nsl.NSL_PREC_BF16, "f16": nsl.NSL_PREC_F16,
-            "fp8": nsl.NSL_PREC_FP8}[args.precision]
+            "fp8": nsl.NSL_PREC_FP8, "bf16x3": nsl.NSL_PREC_BF16X3}[args.precision]
     pf = I.config_obstacle_128()
     H, W = pf.camera.height, pf.camera.width
     blob = I.pack_blob(I.make_params(16, 0), 16)
@@ -449,7 +449,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"f32": "f32", "bf16": "f32 march + bf16 net", "f16": "f32 march + f16 net",
-                  "fp8": "f32 march + fp8 net"}[args.precision],
+                  "fp8": "f32 march + fp8 net", "bf16x3": "f32 march + split-bf16 net"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [128, 128, 128], "grid_dtype": "f32", "billboard": [512, 512],
                    "camera": "perspective fov 40", "step_voxels": 2.0, "obstacle": "sphere r=20",
@@ -478,7 +478,7 @@ def main():
                                  "frac": net_flop_per_pixel(16) * H * W / (float(np.mean(net_ms)) / 1e3) / 1e12
                                  / pk["bf16_tflops"],
                                  "peak_kind": f"{pk_kind} cuBLAS bf16 burst (FP16 has the same nominal "
-                                              "tensor rate)" if args.precision in ("bf16", "f16") else
+                                              "tensor rate)" if args.precision in ("bf16", "f16", "bf16x3") else
                                               f"{pk_kind} cuBLAS bf16 burst (reference only: this run's "
                                               f"network is {args.precision})"}},
         "e2e": {"value": e2e_sync, "unit": "Mpix/s",

@@ -817,9 +817,15 @@ __device__ __forceinline__ void halo8f(const ConvImg<float>& a, int y, int x, in
 // Stage channels [c0, c0 + 8 GC) of the halo of M tile `tile` as GC hi planes
 // followed by GC lo planes (zeros outside the image); loads are issued in
 // batches before their first use.
+#ifndef NSL_SPLIT_LDB
+#define NSL_SPLIT_LDB 4
+#endif
+constexpr int kLdBatchSplit = NSL_SPLIT_LDB;   // 8-channel groups loaded per thread before first use
+
 template <int CIN, int MODE, int GC>
 __device__ __forceinline__ void load_halo_split(const ConvImg<float>& a, int tile, int c0, uint8_t* halo) {
   constexpr int NE = kHaloPix * GC;
+  constexpr int kLdBatch = kLdBatchSplit;
   const int ty = tile / a.tiles_x, tx = tile % a.tiles_x;
   const int y0 = ty * kPatchH - 1, x0 = tx * kPatchW - 1;
   for (int e0 = threadIdx.x; e0 < NE; e0 += kLdBatch * blockDim.x) {
