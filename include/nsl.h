@@ -313,7 +313,7 @@ NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, i
  * same network run, which also copies every convolution's stored output into
  * trace_dev, so that each layer can be compared with an emulation of its
  * arithmetic on the same input.  Tensor-core precisions only (NSL_PREC_BF16,
- * NSL_PREC_F16, NSL_PREC_FP8; NSL_PREC_F32 and NSL_PREC_BF16X3 return
+ * NSL_PREC_F16, NSL_PREC_FP8, NSL_PREC_BF16X3; NSL_PREC_F32 returns
  * NSL_ERR_UNSUPPORTED).
  *   trace_dev     caller-owned device buffer, 16-byte aligned, of at least
  *                 nsl_lightmap_trace_bytes(width, height) bytes; it receives
@@ -323,7 +323,8 @@ NSL_API nsl_status nsl_predict_lightmaps(nsl_ctx* ctx, const float* guide_dev, i
  *                 NHWC [H/2^l][W/2^l][C] with l its level (0 at full size) and
  *                 C its channels, in the activation type: bfloat16 for
  *                 NSL_PREC_BF16, binary16 for NSL_PREC_F16 and NSL_PREC_FP8
- *                 (whose activations are binary16 between layers)
+ *                 (whose activations are binary16 between layers), binary32
+ *                 for NSL_PREC_BF16X3
  *   other arguments as for nsl_predict_lightmaps
  * A smaller or unaligned trace buffer returns NSL_ERR_INVALID_ARG before any
  * work is queued.  The copies are ordered on `stream` after each layer. */
@@ -331,7 +332,8 @@ NSL_API nsl_status nsl_predict_lightmaps_trace(nsl_ctx* ctx, const float* guide_
                                                int height, int precision, float* lightmaps_dev,
                                                void* trace_dev, size_t trace_bytes, void* stream);
 /* Bytes of the trace of a width x height image: 144 activation values per
- * pixel, two bytes each; 0 for a non-positive size. */
+ * pixel, four bytes each (the binary32 values of NSL_PREC_BF16X3; the 16-bit
+ * forms fill the first half); 0 for a non-positive size. */
 NSL_API size_t nsl_lightmap_trace_bytes(int width, int height);
 
 /* Diagnostic of the failure detection (no paper counterpart).  Every wait of

@@ -620,7 +620,6 @@ static nsl_status predict(nsl_ctx* c, const float* guide, int width, int height,
         return fail(NSL_ERR_UNSUPPORTED, "%s: the tensor-core networks are built for C0=16 (this blob: C0=%d)",
                     fn, c->layout.c0);
       const int elem = tc_elem_of(precision);
-      if (elem == 3 && trace) return fail(NSL_ERR_UNSUPPORTED, "%s: no trace of the split-BF16 network", fn);
       const size_t need = net_tc_workspace_bytes(c->max_w, c->max_h, elem);
       if (need > c->ws_bytes) {
         // the split-BF16 network keeps binary32 activations: grow the workspace once

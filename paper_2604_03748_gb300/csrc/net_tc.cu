@@ -1712,8 +1712,8 @@ cudaError_t run_convT_split(const NetTcWeights* w, int n, const float* const* in
 // activations, then the tensor-core adapters (binary16 operands, as in the
 // other tensor-core networks) on the binary32 feature map.
 cudaError_t forward_split(const NetTcWeights* w, const NetF32Weights* wf, const NetImage* imgs, void* const* ws,
-                          int n, unsigned int* err, cudaStream_t s) {
-  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+                          int n, unsigned int* err, cudaStream_t s, uint8_t* trace = nullptr) {
+  if (n < 1 || n > kMaxGroup || (trace && n != 1)) return cudaErrorInvalidValue;
   TcBuffers<float> B[kMaxGroup];
   int Hs[4][kMaxGroup], Ws[4][kMaxGroup];
   for (int k = 0; k < n; ++k) {
@@ -1728,31 +1728,60 @@ cudaError_t forward_split(const NetTcWeights* w, const NetF32Weights* wf, const 
   const float* sk[kMaxGroup];
   float* out[kMaxGroup];
   cudaError_t e;
+  // diagnostic trace (one image): after each layer, a copy of its binary32 output
+  const size_t P0 = (size_t)imgs[0].H * imgs[0].W;
+  size_t toff = 0;
+  auto trace_copy = [&](const float* buf, int ch, int lv) -> cudaError_t {
+    if (!trace) return cudaSuccess;
+    const size_t bytes = (P0 >> (2 * lv)) * (size_t)ch * sizeof(float);
+    cudaError_t ce = cudaMemcpyAsync(trace + toff, buf, bytes, cudaMemcpyDeviceToDevice, s);
+    toff += bytes;
+    return ce;
+  };
 #define TRY(x) if ((e = (x)) != cudaSuccess) return e
 #define SET(IN, SKIP, OUT) for (int k = 0; k < n; ++k) { in[k] = B[k].IN; sk[k] = SKIP; out[k] = B[k].OUT; }
+#define TRACE(BUF, CH, LV) TRY(trace_copy(B[0].BUF, CH, LV))
   for (int k = 0; k < n; ++k) out[k] = B[k].fa;
   TRY(simt_first_conv_group<float>(wf, imgs, out, nullptr, n, s));
+  TRACE(fa, 16, 0);
   SET(fa, nullptr, s1);  TRY((run_conv_split<16, 16, TC_PLAIN>(w, 1, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  TRACE(s1, 16, 0);
   SET(s1, nullptr, l1a); TRY((run_conv_split<16, 32, TC_POOL>(w, 2, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, nullptr, s2); TRY((run_conv_split<32, 32, TC_PLAIN>(w, 3, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  TRACE(s2, 32, 1);
   SET(s2, nullptr, l2a); TRY((run_conv_split<32, 64, TC_POOL>(w, 4, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, nullptr, s3); TRY((run_conv_split<64, 64, TC_PLAIN>(w, 5, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  TRACE(s3, 64, 2);
   SET(s3, nullptr, l3a); TRY((run_conv_split<64, 128, TC_POOL>(w, 6, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  TRACE(l3a, 128, 3);
   SET(l3a, nullptr, l3b); TRY((run_conv_split<128, 128, TC_PLAIN>(w, 7, n, in, nullptr, out, Hs[3], Ws[3], err, s)));
+  TRACE(l3b, 128, 3);
   SET(l3b, nullptr, l2a); TRY((run_convT_split<128, 64, 0>(w, n, in, out, Hs[3], Ws[3], err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, B[k].s3, l2b); TRY((run_conv_split<128, 64, TC_CONCAT>(w, 8, n, in, sk, out, Hs[2], Ws[2], err, s)));
+  TRACE(l2b, 64, 2);
   SET(l2b, nullptr, l2a); TRY((run_conv_split<64, 64, TC_PLAIN>(w, 9, n, in, nullptr, out, Hs[2], Ws[2], err, s)));
+  TRACE(l2a, 64, 2);
   SET(l2a, nullptr, l1a); TRY((run_convT_split<64, 32, 1>(w, n, in, out, Hs[2], Ws[2], err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, B[k].s2, l1b); TRY((run_conv_split<64, 32, TC_CONCAT>(w, 10, n, in, sk, out, Hs[1], Ws[1], err, s)));
+  TRACE(l1b, 32, 1);
   SET(l1b, nullptr, l1a); TRY((run_conv_split<32, 32, TC_PLAIN>(w, 11, n, in, nullptr, out, Hs[1], Ws[1], err, s)));
+  TRACE(l1a, 32, 1);
   SET(l1a, nullptr, fa); TRY((run_convT_split<32, 16, 2>(w, n, in, out, Hs[1], Ws[1], err, s)));
+  TRACE(fa, 16, 0);
   SET(fa, B[k].s1, fb);  TRY((run_conv_split<32, 16, TC_CONCAT>(w, 12, n, in, sk, out, Hs[0], Ws[0], err, s)));
+  TRACE(fb, 16, 0);
   SET(fb, nullptr, fa);  TRY((run_conv_split<16, 16, TC_PLAIN>(w, 13, n, in, nullptr, out, Hs[0], Ws[0], err, s)));
+  TRACE(fa, 16, 0);
   AdapterImg<float> ai[kMaxGroup];
   for (int k = 0; k < n; ++k)
     ai[k] = AdapterImg<float>{B[k].fa, reinterpret_cast<__half*>(B[k].x1), B[k].partial, B[k].att, imgs[k].out,
                               imgs[k].H, imgs[k].W};
   TRY(adapters_tc_run_group<float>(w->ad, net_f32_adapter_params(wf), ai, n, err, s));
+#undef TRACE
 #undef SET
 #undef TRY
   return cudaSuccess;
@@ -1867,7 +1896,7 @@ cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const
                            uint8_t* trace) {
   if (net_tc_workspace_bytes(img.W, img.H, w->elem) > ws_bytes) return cudaErrorInvalidValue;
   void* ws[1] = {workspace};
-  if (w->elem == 3) return trace ? cudaErrorNotSupported : forward_split(w, wf, &img, ws, 1, err, s);
+  if (w->elem == 3) return forward_split(w, wf, &img, ws, 1, err, s, trace);
   if (w->elem == 2) return forward<__half, true>(w, wf, &img, ws, 1, err, s, trace);
   if (w->elem == 1) return forward<__nv_bfloat16, false>(w, wf, &img, ws, 1, err, s, trace);
   return forward<__half, false>(w, wf, &img, ws, 1, err, s, trace);
@@ -1875,8 +1904,8 @@ cudaError_t net_tc_forward(const NetTcWeights* w, const NetF32Weights* wf, const
 
 size_t net_tc_trace_bytes(int width, int height) {
   // 144 activation values per pixel of the full-resolution image (the 17
-  // stored tensors), two bytes each
-  return (size_t)width * height * 144 * 2;
+  // stored tensors), up to four bytes each (binary32 in the split-BF16 form)
+  return (size_t)width * height * 144 * 4;
 }
 
 cudaError_t net_tc_forward_group(const NetTcWeights* w, const NetF32Weights* wf,

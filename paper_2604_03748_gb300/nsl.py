@@ -416,14 +416,15 @@ def nsl_predict_lightmaps_trace(ctx, guide, width, height, precision, lightmaps,
 
 def split_trace(trace_u8, width, height, dtype_name):
     """The 17 NHWC tensors of a trace (a flat uint8 tensor) as [C, H_l, W_l]
-    float64 numpy arrays; dtype_name is 'bfloat16' or 'float16'."""
+    float64 numpy arrays; dtype_name is 'bfloat16', 'float16' or 'float32'."""
     import numpy as np
     import torch
     tdt = getattr(torch, dtype_name)
+    esz = torch.empty((), dtype=tdt).element_size()
     out, off = [], 0
     for _, ch, lv in TRACE_LAYERS:
         h, w = int(height) >> lv, int(width) >> lv
-        n = h * w * ch * 2
+        n = h * w * ch * esz
         t = trace_u8[off:off + n].view(tdt).reshape(h, w, ch).permute(2, 0, 1)
         out.append(t.to(torch.float64).cpu().numpy())
         off += n

@@ -112,6 +112,57 @@ def test_each_layer_matches_its_emulation(lib, orc, form, H, W):
     assert max(PT.range_err(lm, ad)) <= TOL_ADAPTERS
 
 
+# The split-BF16 form stores binary32 values; the emulation adds the three
+# products of each multiply exactly and rounds once, the tensor core in FP32
+# in its own order, so each layer is held to the emulation relative to the
+# layer's largest value rather than to one ulp.
+TOL_SPLIT_LAYER = 1e-5
+
+
+def _check_split_layers(orc, guide, ds, L):
+    P = {k: v.astype(np.float64) for k, v in I.make_params(16, 0)}
+    x0 = guide.astype(np.float32).astype(np.float64).copy()
+    x0[2] *= ds
+    errs = []
+    a0 = orc.store_as(orc.PREC_BF16X3, orc.conv_layer_prec(0, x0, P["enc1a.w"], P["enc1a.b"]))
+    errs.append(float(np.abs(L[0] - a0).max() / max(np.abs(a0).max(), 1e-30)))
+    ins = _layer_inputs(orc, L)
+    for l in range(1, 17):
+        ln = orc.NET_LAYERS[l]
+        emu = orc.conv_layer_prec(orc.PREC_BF16X3, ins[l], P[ln + ".w"], P[ln + ".b"],
+                                  transposed=ln.startswith("up"))
+        errs.append(float(np.abs(L[l] - emu).max() / max(np.abs(emu).max(), 1e-30)))
+    assert max(errs) <= TOL_SPLIT_LAYER, dict(zip(orc.NET_LAYERS, errs))
+    return errs
+
+
+@pytest.mark.parametrize("H,W", [(64, 96), (24, 136), (512, 512)])
+def test_split_bf16_each_layer_matches_its_emulation(lib, orc, H, W):
+    """The split-BF16 network (NSL_PREC_BF16X3), layer by layer against the
+    oracle's emulation of the split form on the GPU's own stored inputs, the
+    adapters against binary64, and the whole network against FP64."""
+    n = 64
+    if H == 512:
+        pf = I.config_obstacle_128()
+        o, _, _ = orc.guide(pf.density, pf.mask, pf.camera, pf.step)
+        guide = o.astype(np.float32).astype(np.float64)
+        ds = 1.0 / math.sqrt(3 * 128 * 128)
+    else:
+        pf = I.PlumeFrame(np.zeros((n, n, n), np.float32), None, I.perspective_camera(n, 1, W, H),
+                          I.random_light(1), 2.0)
+        guide = _guide(H, W, H * 7 + W)
+        ds = 1.0 / math.sqrt(3 * n * n)
+    lm, L = _gpu_trace(lib, pf, guide, lib.NSL_PREC_BF16X3, "float32")
+    errs = _check_split_layers(orc, guide, ds, L)
+    flat = I.flat_params(I.make_params(16, 0)).astype(np.float64)
+    n_ad = 4 * (orc.nafblock_params(16) + 2 * 16 + 2)
+    ad_err = max(PT.range_err(lm, orc.net_adapters(L[16], flat[-n_ad:], 16)))
+    assert ad_err <= TOL_ADAPTERS
+    e64 = max(PT.range_err(lm, orc.net_forward(guide, flat, 16, ds)))
+    assert e64 <= 2e-2
+    print(f"\nbf16x3 {H}x{W}: layer errors {np.array(errs).max():.2e}; adapters {ad_err:.2e}; vs FP64 {e64:.3e}")
+
+
 @pytest.mark.parametrize("form", FORMS, ids=[f[0] for f in FORMS])
 def test_layers_on_the_512_workload(lib, orc, form):
     """The 512^2 obstacle scene on the oracle's guide: every layer against its

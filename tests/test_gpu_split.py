@@ -67,18 +67,3 @@ def test_split_bf16_on_oracle_guide_512(lib, orc):
     again = PT.gpu_net(ctx, guide, nsl.NSL_PREC_BF16X3)
     assert np.array_equal(got, again)               # deterministic
     ctx.close()
-
-
-def test_split_bf16_trace_refused(lib):
-    from paper_2604_03748_gb300 import nsl
-    vol = np.zeros((16, 16, 16), np.float32)
-    pf = I.PlumeFrame(vol, None, I.orbit_ortho_camera(16, 1, 16, 16), I.random_light(1), 2.0)
-    ctx = PT.make_ctx(pf)
-    import torch
-    g = torch.zeros((3, 16, 16), dtype=torch.float32, device="cuda")
-    lm = torch.empty((8, 16, 16), dtype=torch.float32, device="cuda")
-    tr = torch.empty(int(nsl.load().nsl_lightmap_trace_bytes(16, 16)), dtype=torch.uint8, device="cuda")
-    with pytest.raises(nsl.NslError) as ei:
-        nsl.nsl_predict_lightmaps_trace(ctx.ctx, g, 16, 16, nsl.NSL_PREC_BF16X3, lm, tr)
-    assert ei.value.status == nsl.NSL_ERR_UNSUPPORTED
-    ctx.close()
