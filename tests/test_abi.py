@@ -83,6 +83,22 @@ def test_default_options_without_gpu():
     assert s.march.t_min == pytest.approx(1e-4) and s.march.jitter == 1
 
 
+def test_precision_codes_and_trace_size_without_gpu():
+    """The precision codes of include/nsl.h, and the trace size: 144 stored
+    activation values per pixel (the 17 network tensors) at four bytes, enough
+    for the binary32 trace of the split-BF16 form."""
+    import re
+    from paper_2604_03748_gb300 import nsl
+    hdr = open(os.path.join(ROOT, "include", "nsl.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"(NSL_PREC_\w+) = (\d+)", hdr))
+    assert codes == {"NSL_PREC_F32": nsl.NSL_PREC_F32, "NSL_PREC_BF16": nsl.NSL_PREC_BF16,
+                     "NSL_PREC_FP8": nsl.NSL_PREC_FP8, "NSL_PREC_F16": nsl.NSL_PREC_F16,
+                     "NSL_PREC_BF16X3": nsl.NSL_PREC_BF16X3}
+    lib = nsl.load()
+    assert lib.nsl_lightmap_trace_bytes(512, 256) == 512 * 256 * 144 * 4
+    assert lib.nsl_lightmap_trace_bytes(0, 8) == 0
+
+
 def test_null_handles_rejected_without_gpu():
     """Host-side argument checks return an error status and set the last-error
     message before any CUDA call."""
