@@ -868,7 +868,9 @@ struct SplitCfg {
   // layers of one chunk keep two halo buffers: the next tile is staged while
   // the tensor cores work on this one
   static constexpr int HBUF = NCH == 1 ? 2 : 1;
-  static constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+  // single-chunk layers keep two accumulators: the MMAs of tile t run during
+  // the epilogue of tile t - 1 and the staging of tile t + 1
+  static constexpr int TMEM_COLS = (NCH == 1 ? 2 * NT : NT) < 32 ? 32 : (NCH == 1 ? 2 * NT : NT);
   static constexpr int SMEM = WBYTES + HBUF * HBYTES + 64;
 };
 __host__ __device__ constexpr int split_nt(int cout) { return cout > 32 ? 32 : cout; }
@@ -906,12 +908,13 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
   uint8_t* wsm = smem;
   uint8_t* halo = smem + Cfg::WBYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::WBYTES + Cfg::HBUF * Cfg::HBYTES);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nt = blockIdx.y;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(slot, Cfg::TMEM_COLS);
@@ -933,8 +936,9 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
   if (!ok) record_error(a.err, 0x10u);
   constexpr uint32_t idesc = idesc_f16kind(1u, 128, NT);   // BF16 operands, FP32 accumulation
   uint32_t phase = 0;
-  // the MMAs of one chunk on halo buffer hb
-  auto issue_chunk = [&](uint32_t hb, int kc) {
+  // the MMAs of one chunk on halo buffer hb into the accumulator at column
+  // acc, completion signalled on bars[bar]
+  auto issue_chunk = [&](uint32_t hb, int kc, uint32_t acc = 0, int bar = 1) {
     const uint32_t wb = smem_u32(wsm);
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
@@ -946,49 +950,67 @@ __global__ void __launch_bounds__(128) conv3x3_split_kernel(TcConvArgs<float> a)
         const uint64_t alo = smem_desc(hb + (uint32_t)((Cfg::GC + 2 * j) * kPlane) + shift, kPlane, kHaloW * 16);
         const uint64_t bhi = smem_desc(wb + (uint32_t)(kk * NT * 32), NT * 16, 128);
         const uint64_t blo = smem_desc(wb + (uint32_t)(Cfg::WHALF + kk * NT * 32), NT * 16, 128);
-        mma_f16kind(tmem, ahi, bhi, idesc, (kc | tap | j) ? 1u : 0u);
-        mma_f16kind(tmem, ahi, blo, idesc, 1u);
-        mma_f16kind(tmem, alo, bhi, idesc, 1u);
+        mma_f16kind(tmem + acc, ahi, bhi, idesc, (kc | tap | j) ? 1u : 0u);
+        mma_f16kind(tmem + acc, ahi, blo, idesc, 1u);
+        mma_f16kind(tmem + acc, alo, bhi, idesc, 1u);
       }
     }
-    mma_commit(&bars[1]);
+    mma_commit(&bars[bar]);
   };
   if constexpr (Cfg::NCH == 1) {
-    // two halo buffers: stage tile t + grid while the MMAs of tile t run
-    int buf = 0;
+    // two halo buffers and two accumulators: while the MMAs of tile t run,
+    // the CTA writes out tile t - 1 and stages tile t + grid
+    uint32_t ph = 0u;   // bit b: the phase of accumulator b's barrier
+    int k = 0, prev = -1;
     int t = blockIdx.x;
     if (ok && t < a.total_tiles) {
       const int im = image_of(a, t);
       load_halo_split<CIN, MODE, Cfg::GC>(a.img[im], t - a.img[im].tile_start, 0, halo);
     }
 #pragma unroll 1
-    for (; ok && t < a.total_tiles; t += gridDim.x) {
+    for (; ok && t < a.total_tiles; t += gridDim.x, ++k) {
       if (t + (int)gridDim.x >= a.total_tiles) pdl_trigger_last();
-      const int im = image_of(a, t);
-      const int lt = t - a.img[im].tile_start;
+      const int buf = k & 1;
       fence_proxy_async();
       tc_fence_before();
-      __syncthreads();   // halo[buf] staged; the previous epilogue's TMEM reads are done
+      __syncthreads();   // halo[buf] staged; the epilogue of the tile before last read its accumulator
       if (tid == 0) {
         tc_fence_after();
-        issue_chunk(smem_u32(halo + buf * Cfg::HBYTES), 0);
+        issue_chunk(smem_u32(halo + buf * Cfg::HBYTES), 0, (uint32_t)(buf * NT), 1 + buf);
+      }
+      if (prev >= 0) {
+        // tile t - grid: its MMAs completed, so its accumulator can be read and
+        // its halo buffer refilled
+        if (!mbar_wait(&bars[1 + (buf ^ 1)], (ph >> (buf ^ 1)) & 1u)) {
+          record_error(a.err, 0x20u);
+          ok = false;
+          break;
+        }
+        ph ^= 1u << (buf ^ 1);
+        tc_fence_after();
+        const int imp = image_of(a, prev);
+        split_epilogue<NT>(a.img[imp], a.bias, prev - a.img[imp].tile_start, tmem + (uint32_t)((buf ^ 1) * NT),
+                           nt * NT, COUT);
+        tc_fence_before();
       }
       const int tn = t + (int)gridDim.x;
-      if (tn < a.total_tiles) {   // the other buffer's MMAs completed in the previous iteration
+      if (tn < a.total_tiles) {
         const int imn = image_of(a, tn);
         load_halo_split<CIN, MODE, Cfg::GC>(a.img[imn], tn - a.img[imn].tile_start, 0,
                                             halo + (buf ^ 1) * Cfg::HBYTES);
       }
-      if (!mbar_wait(&bars[1], phase)) {
+      prev = t;
+    }
+    if (ok && prev >= 0) {
+      const int lb = (k - 1) & 1;
+      if (!mbar_wait(&bars[1 + lb], (ph >> lb) & 1u)) {
         record_error(a.err, 0x20u);
-        ok = false;
-        break;
+      } else {
+        tc_fence_after();
+        const int imp = image_of(a, prev);
+        split_epilogue<NT>(a.img[imp], a.bias, prev - a.img[imp].tile_start, tmem + (uint32_t)(lb * NT), nt * NT,
+                           COUT);
       }
-      phase ^= 1u;
-      tc_fence_after();
-      split_epilogue<NT>(a.img[im], a.bias, lt, tmem, nt * NT, COUT);
-      tc_fence_before();
-      buf ^= 1;
     }
   } else {
 #pragma unroll 1
