@@ -622,12 +622,13 @@ static nsl_status predict(nsl_ctx* c, const float* guide, int width, int height,
       const int elem = tc_elem_of(precision);
       const size_t need = net_tc_workspace_bytes(c->max_w, c->max_h, elem);
       if (need > c->ws_bytes) {
-        // the split-BF16 network keeps binary32 activations: grow the workspace once
+        // the split-BF16 network keeps binary32 activations: grow the workspace
+        // once (the old one stays if the allocation fails)
         NSL_CUDA_TRY(cudaStreamSynchronize(s));
+        void* bigger = nullptr;
+        NSL_CUDA_TRY(cudaMalloc(&bigger, need));
         cudaFree(c->ws);
-        c->ws = nullptr;
-        c->ws_bytes = 0;
-        NSL_CUDA_TRY(cudaMalloc(&c->ws, need));
+        c->ws = bigger;
         c->ws_bytes = need;
       }
       if (!c->wtc[elem]) {
