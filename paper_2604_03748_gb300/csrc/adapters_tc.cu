@@ -2,14 +2,18 @@
 // convolutions on the tensor cores (tcgen05 kind::f16, FP16 operands, FP32
 // accumulation in TMEM); used by the tensor-core network paths.
 //
-// Pass 1, per 16x8 tile (persistent CTAs of 256 threads): the 18x10 halo of F
-// is normalised (LayerNorm without its affine, which is folded into pw1) into
-// FP16 A planes (rows = halo pixels, padded to two M = 128 tiles); in two
-// rounds of two adapters, one MMA per M tile applies their pw1 (N = 2 x 32,
-// K = 16), the accumulators go to shared memory (zero outside the image: the
-// depthwise convolution pads its input with zeros), and the SIMT cores run the
-// depthwise 3x3 and the simple gate, each thread one 8-pixel column for two
-// gated channels, writing x1 and the tile's per-channel sums.
+// Pass 1, per 16x8 tile (persistent CTAs of 256 threads): pw1 (a 1x1
+// convolution) followed by the depthwise 3x3 is one linear map, a 3x3
+// convolution from the 16 normalised channels to the 128 pw1 channels of the
+// four adapters with weights dw[o, tap] * W1[o, c], plus the bias
+// dw_b[o] + b1[o] * (sum of dw[o, tap] over the taps inside the image: the
+// depthwise convolution pads its input, pw1's output, with zeros).  The 18x10
+// halo of F is normalised (LayerNorm without its affine, which is folded into
+// pw1) into FP16 A planes stored column by column, so that each tap is the
+// same planes shifted by whole rows; nine MMAs (M = 128 pixels, N = 128,
+// K = 16) accumulate the convolution in TMEM, and the epilogue adds the bias,
+// applies the simple gate, writes x1 and reduces the tile's per-channel sums
+// with warp shuffles.
 // Pass 2, per 128 pixels: three chained MMAs with block-diagonal weights (the
 // four adapters side by side): pw2 on att * x1 (K = 64, N = 64), ffn1 on
 // LN2(y) (N = 128), and on the gate g the heads folded through ffn2 (N = 16,
@@ -33,19 +37,21 @@ constexpr int C = kC0;                  // 16 channels per adapter
 constexpr int kTW = 16, kTH = 8;        // pass-1 tile: same tiling as the SIMT pass 1
 constexpr int kHW = kTW + 2, kHH = kTH + 2;
 constexpr int kHalo = kHW * kHH;        // 180
-constexpr int kRows = 256;              // A rows: halo pixels padded to 2 x 128
-constexpr int kChS = 184;               // words per gate pair of the pw1 buffer (the two half-
-                                        // warps of a warp, two pairs apart, land 16 banks apart)
-
-// pass-1 shared memory (bytes); pw1 runs in two rounds of two adapters (N = 64)
+// pass-1 halo, column by column: A row 10 hx + hy holds halo pixel (hx, hy), so
+// M row m = 8 x + y (output pixel (x, y) of the tile) of tap (dx, dy) is A row
+// m + 10 (x + dx) - 8 x + dy: eight-row groups (one output column each) 160
+// bytes apart, the tap a shift of 10 dx + dy rows
 constexpr int kP1Threads = 256;
-constexpr int kP1A = 0;                                   // 2 planes x 256 rows x 16 B
-constexpr int kP1B = kP1A + 2 * kRows * 16;               // pw1 B operand, 128 x 32 B
-constexpr int kP1Pw = kP1B + 128 * 32;                    // pw1 output of one round: [32 gate pairs][kChS] half2
-constexpr int kP1Dw = kP1Pw + 32 * kChS * 4;              // pw1 bias [128] + dw weights [128][9] + dw bias [128]
-constexpr int kP1In = kP1Dw + (128 * 9 + 128 + 128) * 4;  // inside flags [192]
-constexpr int kP1Bar = kP1In + 192;
-constexpr int kP1Smem = kP1Bar + 16;
+constexpr int kP1Plane = kHalo * 16;                      // one 8-channel plane, 2880 B
+constexpr int kP1A = 0;                                   // 2 planes
+constexpr int kP1B = kP1A + 2 * kP1Plane;                 // 9 taps x (128 rows x 32 B)
+constexpr int kP1Par = kP1B + 9 * 128 * 32;               // biases and depthwise weights (floats)
+constexpr int kP1ParN = 128 + 128 + 128 * 9 + 128;        // [bias of interior pixels][b1][dw 128 x 9][dw_b]
+constexpr int kP1Red = kP1Par + kP1ParN * 4;              // warp sums [8 warps][32]
+constexpr int kP1Bar = kP1Red + 8 * 32 * 4;               // mbarriers: MMAs, weights; TMEM slot
+constexpr int kP1Smem = kP1Bar + 32;
+constexpr int kP1WBytes = 9 * 128 * 32;
+static_assert(kP1B % 128 == 0 && kP1Par % 16 == 0, "pass-1 shared-memory alignment");
 
 // pass-2 shared memory (bytes)
 constexpr int kP2W2 = 0;                  // 64 x 64 block-diagonal
@@ -55,12 +61,14 @@ constexpr int kP2A = kP2Hd + 16 * 64 * 2;  // 8 planes x 128 rows x 16 B
 constexpr int kP2Par = kP2A + 8 * 128 * 16;
 constexpr int kP2ParN = 64 + 64 + 128 + 16 + 128;   // b2, beta, fb1, head constant, head on y
 constexpr int kP2Att = kP2Par + kP2ParN * 4;
-constexpr int kP2Bar = kP2Att + 64 * 4;
-constexpr int kP2Smem = kP2Bar + 16;
+constexpr int kP2Bar = kP2Att + 64 * 4;   // mbarriers: MMAs, weights; TMEM slot
+constexpr int kP2Smem = kP2Bar + 32;
+static_assert(kP2F1 % 16 == 0 && kP2Hd % 16 == 0 && kP2Par % 16 == 0 && (kP2ParN * 4) % 16 == 0,
+              "pass-2 bulk copy alignment");
 
 struct AdapterTcDev {
-  const uint8_t* b1;   // pass-1 B operand (4096 B)
-  const float* p1f;    // [pw1 bias 128][dw weights 128 x 9][dw bias 128]
+  const uint8_t* b9;   // pass-1 B operands of the nine taps (9 x 4096 B)
+  const float* p1f;    // kP1ParN floats
   const uint8_t* w2;   // 8192 B
   const uint8_t* f1;   // 16384 B
   const uint8_t* hd;   // 2048 B: the heads folded through ffn2 and gamma
@@ -141,34 +149,23 @@ __device__ __forceinline__ int find_group(const int* start, int n, int t) {
   return lo;
 }
 
-__device__ __forceinline__ void copy_to_smem(uint8_t* dst, const void* src, int bytes) {
-  for (int i = threadIdx.x * 16; i < bytes; i += blockDim.x * 16)
-    *reinterpret_cast<uint4*>(dst + i) = __ldg(reinterpret_cast<const uint4*>(static_cast<const uint8_t*>(src) + i));
-}
-
 template <typename TA>
-__global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_constant__ AdGroup<TA> G,
+__global__ void __launch_bounds__(kP1Threads, 4) adapters_p1_tc(const __grid_constant__ AdGroup<TA> G,
                                                              const AdapterTcDev W, unsigned int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* A = smem + kP1A;
-  __half2* pw = reinterpret_cast<__half2*>(smem + kP1Pw);   // gate pairs (o, o + 16) of a round
-  const float* b1s = reinterpret_cast<const float*>(smem + kP1Dw);
+  const float* cin = reinterpret_cast<const float*>(smem + kP1Par);   // bias of interior pixels
+  const float* b1s = cin + 128;
   const float* dww = b1s + 128;
   const float* dwb = dww + 128 * 9;
-  uint8_t* inside = smem + kP1In;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP1Bar);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP1Bar + 8);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  float* red = reinterpret_cast<float*>(smem + kP1Red);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP1Bar);       // [0] the MMAs, [1] the weights
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP1Bar + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  copy_to_smem(smem + kP1B, W.b1, 128 * 32);
-  copy_to_smem(smem + kP1Dw, W.p1f, (128 + 128 * 9 + 128) * 4);
-  // A rows 180..255 stay zero (finite operands for the unused accumulator rows)
-  for (int r = kHalo + tid; r < kRows; r += kP1Threads) {
-    *reinterpret_cast<uint4*>(A + r * 16) = make_uint4(0, 0, 0, 0);
-    *reinterpret_cast<uint4*>(A + kRows * 16 + r * 16) = make_uint4(0, 0, 0, 0);
-  }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(slot, 128);
@@ -176,16 +173,51 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  if (tid == 0) {
+    // the weights with bulk copies (pieces of at most 32 KB), while the
+    // previous kernel may still run
+    mbar_expect_tx(&bar[1], (uint32_t)(kP1WBytes + kP1ParN * 4));
+    bulk_g2s(smem + kP1B, W.b9, 32768u, &bar[1]);
+    bulk_g2s(smem + kP1B + 32768, W.b9 + 32768, (uint32_t)(kP1WBytes - 32768), &bar[1]);
+    bulk_g2s(smem + kP1Par, W.p1f, (uint32_t)(kP1ParN * 4), &bar[1]);
+  }
   pdl_wait();      // F comes from the last convolution
   pdl_trigger();
-  constexpr uint32_t idesc = idesc_f16kind(0u, 128, 64);
+  constexpr uint32_t idesc = idesc_f16kind(0u, 128, 128);
   const int total = G.tile_start[G.nimg];
   uint32_t phase = 0;
-  bool ok = true;
-  // TMEM rows: warp w reads lanes 32 (w % 4) .. +31; warps 0-3 take M tile 0
-  // (halo rows 0..127), warps 4-7 M tile 1 (rows 128..255)
-  const int mt = warp >> 2, row = mt * 128 + (tid & 127);
+  bool ok = __syncthreads_and(mbar_wait(&bar[1], 0u) ? 1 : 0) != 0;
+  if (!ok) record_error(err, 0x100u);
 
+  // halo staging: thread hp < 180 loads halo pixel (hp % 18, hp / 18) (row by
+  // row, so a warp reads contiguous NHWC rows) and stores it column by column;
+  // the next tile's loads are issued before the current tile's epilogue
+  constexpr int RF = C * (int)sizeof(TA) / 16;   // 16-byte loads per F row
+  const int hx = tid % kHW, hy = tid / kHW;
+  uint4 raw[RF];
+  bool rin = false;
+  auto fetch = [&](int t) {
+    rin = false;
+    if (tid >= kHalo || t >= total) return;
+    const int k = find_group(G.tile_start, G.nimg, t);
+    const AdapterImg<TA>& im = G.img[k];
+    const int lt = t - G.tile_start[k];
+    const int ntx = (im.W + kTW - 1) / kTW;
+    const int x = (lt % ntx) * kTW + hx - 1, y = (lt / ntx) * kTH + hy - 1;
+    rin = x >= 0 && x < im.W && y >= 0 && y < im.H;
+    if (rin) {
+      const uint4* p = reinterpret_cast<const uint4*>(im.F + ((size_t)y * im.W + x) * C);
+#pragma unroll
+      for (int q = 0; q < RF; ++q) raw[q] = __ldg(p + q);
+    }
+  };
+
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (M rows = pixels) and
+  // the columns of adapters 2 (w / 4) and 2 (w / 4) + 1
+  const int qt = warp & 3, hp2 = warp >> 2;
+  const int m = qt * 32 + lane;                  // M row = 8 x + y
+
+  fetch(blockIdx.x);
 #pragma unroll 1
   for (int t = blockIdx.x; ok && t < total; t += gridDim.x) {
     if (t + (int)gridDim.x >= total) pdl_trigger_last();
@@ -194,130 +226,105 @@ __global__ void __launch_bounds__(kP1Threads) adapters_p1_tc(const __grid_consta
     const int lt = t - G.tile_start[k];
     const int ntx = (im.W + kTW - 1) / kTW;
     const int x0 = (lt % ntx) * kTW, y0 = (lt / ntx) * kTH;
-    __syncthreads();  // the previous tile's readers of A and inside are done
-    for (int hp = tid; hp < kHalo; hp += kP1Threads) {
-      const int y = y0 + hp / kHW - 1, x = x0 + hp % kHW - 1;
-      const bool in = y >= 0 && y < im.H && x >= 0 && x < im.W;
+    // this tile's halo into A (the previous tile's MMAs have completed)
+    if (tid < kHalo) {
       float v[C], n[C];
-      if (in) {
-        load_row<TA, C>(im.F + ((size_t)y * im.W + x) * C, v);
-      } else {
+      const TA* h = reinterpret_cast<const TA*>(raw);
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] = 0.f;
-      }
+      for (int c = 0; c < C; ++c) v[c] = rin ? tof<TA>(h[c]) : 0.f;
       norm16(v, n);
-      *reinterpret_cast<uint4*>(A + hp * 16) = pack8h(n);
-      *reinterpret_cast<uint4*>(A + kRows * 16 + hp * 16) = pack8h(n + 8);
-      inside[hp] = in ? 1 : 0;
+      const int r = hx * kHH + hy;
+      *reinterpret_cast<uint4*>(A + r * 16) = pack8h(n);
+      *reinterpret_cast<uint4*>(A + kP1Plane + r * 16) = pack8h(n + 8);
     }
-    // two rounds: adapters (0, 1), then (2, 3)
-#pragma unroll 1
-    for (int rd = 0; rd < 2; ++rd) {
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();  // A is staged; the previous round's readers of pw are done
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t ab = smem_u32(A), bb = smem_u32(smem + kP1B) + (uint32_t)(rd * 64 * 16);
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-          mma_f16kind(tmem + (uint32_t)(i * 64), smem_desc(ab + (uint32_t)(i * 128 * 16), kRows * 16, 128),
-                      smem_desc(bb, 128 * 16, 128), idesc, 0u);
-        mma_commit(bar);
-      }
-      ok = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
-      if (!ok) {
-        record_error(err, 0x100u);
-        break;
-      }
-      phase ^= 1u;
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();  // A is staged; the previous tile's TMEM and warp-sum readers are done
+    if (tid == 0) {
       tc_fence_after();
-      // accumulators -> pw (+ bias; zero outside the image): round channel
-      // al * 32 + o is pw1 output 64 rd + al * 32 + o; outputs o and o + 16 of
-      // adapter 2 rd + al (the gate's two halves) share one half2 word
-      {
-        const bool inrow = row < kHalo;
-        const bool keep = inrow && inside[inrow ? row : 0];
+      const uint32_t ab = smem_u32(A), bb = smem_u32(smem + kP1B);
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        mma_f16kind(tmem, smem_desc(ab + (uint32_t)((dx * kHH + dy) * 16), kP1Plane, kHH * 16),
+                    smem_desc(bb + (uint32_t)(tap * 128 * 32), 128 * 16, 128), idesc, tap > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar[0]);
+    }
+    fetch(t + (int)gridDim.x);
+    ok = __syncthreads_and(mbar_wait(&bar[0], phase) ? 1 : 0) != 0;
+    if (!ok) {
+      record_error(err, 0x100u);
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    {
+      const int px = x0 + (m >> 3), py = y0 + (m & 7);
+      const bool valid = px < im.W && py < im.H;
+      const bool interior = px >= 1 && px + 1 < im.W && py >= 1 && py + 1 < im.H;
+      // taps inside the image (bit 3 dy + dx), for the pw1 bias at the border
+      unsigned inmask = 0;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int qx = px + tap % 3 - 1, qy = py + tap / 3 - 1;
+        if (qx >= 0 && qx < im.W && qy >= 0 && qy < im.H) inmask |= 1u << tap;
+      }
+      const size_t npix = (size_t)im.H * im.W, pix = (size_t)py * im.W + px;
 #pragma unroll 1
-        for (int al = 0; al < 2; ++al) {
-          float v0[16], v1[16];
-          const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * 64 + al * 32);
-          tmem_ld16(t0, v0);
-          tmem_ld16(t0 + 16, v1);
-          if (inrow) {
-            const float* bb = b1s + rd * 64 + al * 32;
+      for (int al = 0; al < 2; ++al) {
+        const int a = 2 * hp2 + al;
+        float d0[16], d1[16];
+        const uint32_t ta = tmem + ((uint32_t)(qt * 32) << 16) + (uint32_t)(a * 32);
+        tmem_ld16(ta, d0);
+        tmem_ld16(ta + 16, d1);
 #pragma unroll
-            for (int o = 0; o < 16; ++o)
-              pw[(al * 16 + o) * kChS + row] =
-                  keep ? __floats2half2_rn(v0[o] + bb[o], v1[o] + bb[16 + o]) : __floats2half2_rn(0.f, 0.f);
-          }
-        }
-      }
-      tc_fence_before();
-      __syncthreads();
-      // depthwise 3x3 + simple gate: thread = (channel group g in 0..15, column
-      // x); group g covers adapter a = 2 rd + g / 8 and gated channels
-      // (g % 8) * 2, +1 of it, with their partners +16
-      {
-        const int g = tid >> 4, x = tid & 15, al = g >> 3, a = 2 * rd + al, j0 = (g & 7) * 2;
-        const int px = x0 + x;
-        float gv[2][kTH];
-        float sums[2];
+        for (int j = 0; j < 16; ++j) {
+          const int o0 = a * 32 + j, o1 = o0 + 16;
+          float c0 = cin[o0], c1 = cin[o1];
+          if (!interior) {
+            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const int o = j0 + jj;                             // gated channel of the adapter
-          const int cg0 = rd * 64 + al * 32 + o, cg1 = cg0 + 16;  // global pw1 channels of the pair
-          float d0[kTH], d1[kTH];
-#pragma unroll
-          for (int y = 0; y < kTH; ++y) {
-            d0[y] = dwb[cg0];
-            d1[y] = dwb[cg1];
-          }
-          const __half2* q = pw + (al * 16 + o) * kChS + x;
-#pragma unroll
-          for (int r = 0; r < kHH; ++r) {
-            const __half2 w0 = q[r * kHW], w1 = q[r * kHW + 1], w2 = q[r * kHW + 2];
-            const float u0 = __low2float(w0), u1 = __low2float(w1), u2 = __low2float(w2);
-            const float v0 = __high2float(w0), v1 = __high2float(w1), v2 = __high2float(w2);
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-              const int y = r - ky;
-              if (y >= 0 && y < kTH) {
-                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 0], u0, d0[y]);
-                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 1], u1, d0[y]);
-                d0[y] = fmaf(dww[cg0 * 9 + ky * 3 + 2], u2, d0[y]);
-                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 0], v0, d1[y]);
-                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 1], v1, d1[y]);
-                d1[y] = fmaf(dww[cg1 * 9 + ky * 3 + 2], v2, d1[y]);
+            for (int tap = 0; tap < 9; ++tap)
+              if (inmask >> tap & 1u) {
+                s0 += dww[o0 * 9 + tap];
+                s1 += dww[o1 * 9 + tap];
               }
-            }
+            c0 = fmaf(b1s[o0], s0, dwb[o0]);
+            c1 = fmaf(b1s[o1], s1, dwb[o1]);
           }
-          float sm = 0.f;
+          d0[j] = (d0[j] + c0) * (d1[j] + c1);     // the simple gate
+        }
+        if (valid) {
+          uint4* dst = reinterpret_cast<uint4*>(im.x1 + x1_index((int)npix, (int)pix, a * C));
+          dst[0] = pack8h(d0);
+          dst[npix] = pack8h(d0 + 8);              // the next 8-channel plane
+        }
+        // the tile's per-channel sums: halve the 16 values across lane bits
+        // 4..1 (lane l ends with channel (l >> 1) & 15), then add the lane pair
 #pragma unroll
-          for (int y = 0; y < kTH; ++y) {
-            const bool valid = px < im.W && y0 + y < im.H;
-            gv[jj][y] = d0[y] * d1[y];
-            sm += valid ? gv[jj][y] : 0.f;
+        for (int j = 0; j < 16; ++j) d0[j] = valid ? d0[j] : 0.f;
+#pragma unroll
+        for (int w = 8, b = 16; w >= 1; w >>= 1, b >>= 1) {
+          const bool up = (lane & b) != 0;
+#pragma unroll
+          for (int i = 0; i < w; ++i) {
+            const float keep = up ? d0[i + w] : d0[i];
+            const float give = up ? d0[i] : d0[i + w];
+            d0[i] = keep + __shfl_xor_sync(0xffffffffu, give, b);
           }
-          sums[jj] = sm;
         }
-#pragma unroll
-        for (int y = 0; y < kTH; ++y) {
-          if (px < im.W && y0 + y < im.H) {
-            __align__(4) __half o[2] = {__float2half_rn(gv[0][y]), __float2half_rn(gv[1][y])};
-            *reinterpret_cast<uint32_t*>(im.x1 + x1_index(im.H * im.W, (y0 + y) * im.W + px, a * C + j0)) =
-                *reinterpret_cast<const uint32_t*>(o);
-          }
-        }
-        // per-channel tile sums over the 16 columns of the group (a half-warp), fixed tree
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          float sm = sums[jj];
-#pragma unroll
-          for (int off = 8; off > 0; off >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, off);
-          if (x == 0) im.partial[(size_t)lt * (4 * C) + a * C + j0 + jj] = sm;
-        }
+        d0[0] += __shfl_xor_sync(0xffffffffu, d0[0], 1);
+        if ((lane & 1) == 0) red[warp * 32 + al * 16 + (lane >> 1)] = d0[0];
       }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 4 * C) {
+      // channel tid: adapter pair tid / 32, the four lane quarters in order
+      const int h = tid >> 5, l = tid & 31;
+      const float* r = red + h * 4 * 32 + l;
+      im.partial[(size_t)lt * (4 * C) + tid] = ((r[0] + r[32]) + r[64]) + r[96];
     }
   }
   tc_fence_before();
@@ -344,16 +351,13 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
   const float* hc = fb1 + 128;     // folded head constant [8]
   const float* hy = hc + 16;       // head weights on y [8][16] (head j reads adapter j / 2)
   float* att = reinterpret_cast<float*>(smem + kP2Att);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP2Bar);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP2Bar + 8);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP2Bar);   // [0] the MMAs, [1] the weights
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP2Bar + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  copy_to_smem(smem + kP2W2, W.w2, 64 * 64 * 2);
-  copy_to_smem(smem + kP2F1, W.f1, 128 * 64 * 2);
-  copy_to_smem(smem + kP2Hd, W.hd, 16 * 64 * 2);
-  copy_to_smem(smem + kP2Par, W.p2f, kP2ParN * 4);
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(slot, 128);
@@ -361,12 +365,20 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  if (tid == 0) {
+    // the weights with bulk copies, while the previous kernel may still run
+    mbar_expect_tx(&bar[1], (uint32_t)(64 * 64 * 2 + 128 * 64 * 2 + 16 * 64 * 2 + kP2ParN * 4));
+    bulk_g2s(smem + kP2W2, W.w2, 64u * 64u * 2u, &bar[1]);
+    bulk_g2s(smem + kP2F1, W.f1, 128u * 64u * 2u, &bar[1]);
+    bulk_g2s(smem + kP2Hd, W.hd, 16u * 64u * 2u, &bar[1]);
+    bulk_g2s(smem + kP2Par, W.p2f, (uint32_t)(kP2ParN * 4), &bar[1]);
+  }
   const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
   const uint32_t ab = smem_u32(A);
   const int total = G.px_start[G.nimg];
   constexpr int plane_of[8] = {4, 5, 0, 1, 2, 3, 6, 7};   // head column -> output plane
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = __syncthreads_and(mbar_wait(&bar[1], 0u) ? 1 : 0) != 0;
 
   // one GEMM stage: D[0, n) = A(K = 64) x B(n rows), then wait
   auto stage = [&](const uint8_t* b, int n, uint32_t idesc) -> bool {
@@ -381,9 +393,9 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
         mma_f16kind(tmem, smem_desc(ab + (uint32_t)(kk * 2 * 2048), 2048, 128),
                     smem_desc(bb + (uint32_t)(kk * n * 32), (uint32_t)(n * 16), 128), idesc,
                     kk > 0 ? 1u : 0u);
-      mma_commit(bar);
+      mma_commit(&bar[0]);
     }
-    const bool done = __syncthreads_and(mbar_wait(bar, phase) ? 1 : 0) != 0;
+    const bool done = __syncthreads_and(mbar_wait(&bar[0], phase) ? 1 : 0) != 0;
     phase ^= 1u;
     tc_fence_after();
     return done;
@@ -414,7 +426,7 @@ __global__ void __launch_bounds__(128) adapters_p2_tc(const __grid_constant__ Ad
   fetch(blockIdx.x);
 
 #pragma unroll 1
-  for (int blk = blockIdx.x; blk < total; blk += gridDim.x) {
+  for (int blk = blockIdx.x; ok && blk < total; blk += gridDim.x) {
     if (blk + (int)gridDim.x >= total) pdl_trigger_last();
     const int k = find_group(G.px_start, G.nimg, blk);
     const AdapterImg<TA>& im = G.img[k];
@@ -534,14 +546,28 @@ AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* er
   const AdapterP2& p2 = prm.p2;
   std::vector<float> m;
   std::vector<uint8_t> pk;
-  // pw1 of the four adapters: row 32a + o, K = the 16 normalised channels
-  m.assign(128 * 16, 0.f);
-  for (int a = 0; a < 4; ++a)
-    for (int o = 0; o < 32; ++o)
-      for (int c = 0; c < 16; ++c) m[(size_t)(a * 32 + o) * 16 + c] = p1.w1[a][o][c];
-  pack_b(m, 128, 16, pk);
-  w->dev.b1 = static_cast<const uint8_t*>(up(pk.data(), pk.size()));
+  // pw1 and the depthwise 3x3 as one 3x3 convolution: tap (dx, dy) (index
+  // 3 dy + dx), row 32a + o (pw1 channel o of adapter a), K = the 16 normalised
+  // channels, weight dw[o, tap] * W1[o, c] (the product in double, rounded once)
+  std::vector<uint8_t> b9;
+  for (int tap = 0; tap < 9; ++tap) {
+    m.assign(128 * 16, 0.f);
+    for (int a = 0; a < 4; ++a)
+      for (int o = 0; o < 32; ++o)
+        for (int c = 0; c < 16; ++c)
+          m[(size_t)(a * 32 + o) * 16 + c] = (float)((double)p1.dww[a][o][tap] * (double)p1.w1[a][o][c]);
+    pack_b(m, 128, 16, pk);
+    b9.insert(b9.end(), pk.begin(), pk.end());
+  }
+  w->dev.b9 = static_cast<const uint8_t*>(up(b9.data(), b9.size()));
+  // [bias of an interior pixel: dw_b + b1 * (sum of the nine taps)][b1][dw][dw_b]
   std::vector<float> f1s;
+  for (int a = 0; a < 4; ++a)
+    for (int o = 0; o < 32; ++o) {
+      double sw = 0.0;
+      for (int k = 0; k < 9; ++k) sw += p1.dww[a][o][k];
+      f1s.push_back((float)((double)p1.dwb[a][o] + (double)p1.b1[a][o] * sw));
+    }
   for (int a = 0; a < 4; ++a)
     for (int o = 0; o < 32; ++o) f1s.push_back(p1.b1[a][o]);
   for (int a = 0; a < 4; ++a)
