@@ -7,7 +7,9 @@
 // convolution from the 16 normalised channels to the 128 pw1 channels of the
 // four adapters with weights dw[o, tap] * W1[o, c], plus the bias
 // dw_b[o] + b1[o] * (sum of dw[o, tap] over the taps inside the image: the
-// depthwise convolution pads its input, pw1's output, with zeros).  The 18x10
+// depthwise convolution pads its input, pw1's output, with zeros), read from a
+// table of the 16 cases of a pixel's missing left, right, top and bottom
+// neighbours.  The 18x10
 // halo of F is normalised (LayerNorm without its affine, which is folded into
 // pw1) into FP16 A planes stored column by column, so that each tap is the
 // same planes shifted by whole rows; nine MMAs (M = 128 pixels, N = 128,
@@ -46,7 +48,7 @@ constexpr int kP1Plane = kHalo * 16;                      // one 8-channel plane
 constexpr int kP1A = 0;                                   // 2 planes
 constexpr int kP1B = kP1A + 2 * kP1Plane;                 // 9 taps x (128 rows x 32 B)
 constexpr int kP1Par = kP1B + 9 * 128 * 32;               // biases and depthwise weights (floats)
-constexpr int kP1ParN = 128 + 128 + 128 * 9 + 128;        // [bias of interior pixels][b1][dw 128 x 9][dw_b]
+constexpr int kP1ParN = 16 * 128;                         // bias [edge case][128] (case 0: interior)
 constexpr int kP1Red = kP1Par + kP1ParN * 4;              // warp sums [8 warps][32]
 constexpr int kP1Bar = kP1Red + 8 * 32 * 4;               // mbarriers: MMAs, weights; TMEM slot
 constexpr int kP1Smem = kP1Bar + 32;
@@ -154,10 +156,7 @@ __global__ void __launch_bounds__(kP1Threads, 4) adapters_p1_tc(const __grid_con
                                                              const AdapterTcDev W, unsigned int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* A = smem + kP1A;
-  const float* cin = reinterpret_cast<const float*>(smem + kP1Par);   // bias of interior pixels
-  const float* b1s = cin + 128;
-  const float* dww = b1s + 128;
-  const float* dwb = dww + 128 * 9;
+  const float* btab = reinterpret_cast<const float*>(smem + kP1Par);   // bias [edge case][128]
   float* red = reinterpret_cast<float*>(smem + kP1Red);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kP1Bar);       // [0] the MMAs, [1] the weights
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + kP1Bar + 16);
@@ -262,14 +261,8 @@ __global__ void __launch_bounds__(kP1Threads, 4) adapters_p1_tc(const __grid_con
     {
       const int px = x0 + (m >> 3), py = y0 + (m & 7);
       const bool valid = px < im.W && py < im.H;
-      const bool interior = px >= 1 && px + 1 < im.W && py >= 1 && py + 1 < im.H;
-      // taps inside the image (bit 3 dy + dx), for the pw1 bias at the border
-      unsigned inmask = 0;
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int qx = px + tap % 3 - 1, qy = py + tap / 3 - 1;
-        if (qx >= 0 && qx < im.W && qy >= 0 && qy < im.H) inmask |= 1u << tap;
-      }
+      // edge case: bit 0 no left neighbour, 1 no right, 2 no upper, 3 no lower
+      const int ec = (px < 1 ? 1 : 0) | (px + 1 >= im.W ? 2 : 0) | (py < 1 ? 4 : 0) | (py + 1 >= im.H ? 8 : 0);
       const size_t npix = (size_t)im.H * im.W, pix = (size_t)py * im.W + px;
 #pragma unroll 1
       for (int al = 0; al < 2; ++al) {
@@ -278,22 +271,14 @@ __global__ void __launch_bounds__(kP1Threads, 4) adapters_p1_tc(const __grid_con
         const uint32_t ta = tmem + ((uint32_t)(qt * 32) << 16) + (uint32_t)(a * 32);
         tmem_ld16(ta, d0);
         tmem_ld16(ta + 16, d1);
+        const float4* bt = reinterpret_cast<const float4*>(btab + ec * 128 + a * 32);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int o0 = a * 32 + j, o1 = o0 + 16;
-          float c0 = cin[o0], c1 = cin[o1];
-          if (!interior) {
-            float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
-              if (inmask >> tap & 1u) {
-                s0 += dww[o0 * 9 + tap];
-                s1 += dww[o1 * 9 + tap];
-              }
-            c0 = fmaf(b1s[o0], s0, dwb[o0]);
-            c1 = fmaf(b1s[o1], s1, dwb[o1]);
-          }
-          d0[j] = (d0[j] + c0) * (d1[j] + c1);     // the simple gate
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 c0 = bt[j4], c1 = bt[4 + j4];
+          d0[4 * j4 + 0] = (d0[4 * j4 + 0] + c0.x) * (d1[4 * j4 + 0] + c1.x);   // the simple gate
+          d0[4 * j4 + 1] = (d0[4 * j4 + 1] + c0.y) * (d1[4 * j4 + 1] + c1.y);
+          d0[4 * j4 + 2] = (d0[4 * j4 + 2] + c0.z) * (d1[4 * j4 + 2] + c1.z);
+          d0[4 * j4 + 3] = (d0[4 * j4 + 3] + c0.w) * (d1[4 * j4 + 3] + c1.w);
         }
         if (valid) {
           uint4* dst = reinterpret_cast<uint4*>(im.x1 + x1_index((int)npix, (int)pix, a * C));
@@ -560,21 +545,21 @@ AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* er
     b9.insert(b9.end(), pk.begin(), pk.end());
   }
   w->dev.b9 = static_cast<const uint8_t*>(up(b9.data(), b9.size()));
-  // [bias of an interior pixel: dw_b + b1 * (sum of the nine taps)][b1][dw][dw_b]
+  // the bias of each edge case e (bit 0: no left neighbour, 1: no right,
+  // 2: no upper, 3: no lower): dw_b + b1 * (sum of the taps inside)
   std::vector<float> f1s;
-  for (int a = 0; a < 4; ++a)
-    for (int o = 0; o < 32; ++o) {
-      double sw = 0.0;
-      for (int k = 0; k < 9; ++k) sw += p1.dww[a][o][k];
-      f1s.push_back((float)((double)p1.dwb[a][o] + (double)p1.b1[a][o] * sw));
-    }
-  for (int a = 0; a < 4; ++a)
-    for (int o = 0; o < 32; ++o) f1s.push_back(p1.b1[a][o]);
-  for (int a = 0; a < 4; ++a)
-    for (int o = 0; o < 32; ++o)
-      for (int k = 0; k < 9; ++k) f1s.push_back(p1.dww[a][o][k]);
-  for (int a = 0; a < 4; ++a)
-    for (int o = 0; o < 32; ++o) f1s.push_back(p1.dwb[a][o]);
+  for (int e = 0; e < 16; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int o = 0; o < 32; ++o) {
+        double sw = 0.0;
+        for (int dy = 0; dy < 3; ++dy)
+          for (int dx = 0; dx < 3; ++dx) {
+            const bool in = !((dx == 0 && (e & 1)) || (dx == 2 && (e & 2)) || (dy == 0 && (e & 4)) ||
+                              (dy == 2 && (e & 8)));
+            if (in) sw += p1.dww[a][o][dy * 3 + dx];
+          }
+        f1s.push_back((float)((double)p1.dwb[a][o] + (double)p1.b1[a][o] * sw));
+      }
   w->dev.p1f = static_cast<const float*>(up(f1s.data(), f1s.size() * 4));
   // block-diagonal pass-2 weights: input channel a*16 + ci feeds only adapter a
   m.assign(64 * 64, 0.f);
