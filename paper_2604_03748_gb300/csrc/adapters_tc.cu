@@ -127,9 +127,10 @@ __device__ __forceinline__ void norm16(const float* x, float* y) {
 // x1 (the gated depthwise output of the four adapters, 64 channels) is stored
 // as eight planes of 16-byte chunks: plane q holds channels 8q .. 8q+7 of every
 // pixel.  Pass 2's thread-per-pixel loads of one chunk are then 512
-// contiguous bytes per warp, and pass 1's column-per-thread stores of a
-// channel pair span 256 bytes per half-warp (NHWC rows of 128 bytes spread
-// both over 16-32 lines per warp instruction).
+// contiguous bytes per warp, and pass 1's pixel-per-thread 16-byte stores
+// cover 64 contiguous bytes in each of the 8 image rows of a warp's 4 x 8
+// pixels (NHWC rows of 128 bytes would spread both over 32 lines per warp
+// instruction).
 __device__ __forceinline__ size_t x1_index(int npix, int pix, int ch) {
   return ((size_t)(ch >> 3) * npix + pix) * 8 + (ch & 7);
 }

@@ -372,8 +372,9 @@ struct AdapterImg {
 template <typename TA>
 cudaError_t adapters_reduce_only_group(const AdapterParamSet& prm, const AdapterImg<TA>* imgs, int n,
                                        cudaStream_t s);
-// tensor-core adapters (adapters_tc.cu): pw1 / pw2 / ffn1 / ffn2 / heads on
-// tcgen05 with FP16 operands; same tiling and partial layout as the SIMT ones
+// tensor-core adapters (adapters_tc.cu): pw1 with the depthwise 3x3 (as one
+// 3x3 convolution), pw2, ffn1 and the heads folded through ffn2 on tcgen05
+// with FP16 operands; same tiling and partial layout as the SIMT ones
 struct AdapterTcWeights;
 AdapterTcWeights* adapters_tc_create(const AdapterParamSet& prm, cudaError_t* err);
 void adapters_tc_destroy(AdapterTcWeights* w);
